@@ -1,0 +1,98 @@
+"""Analytic level-set functions H and their gradients (Sec. 5.1).
+
+Omega = {H < 0}; Gamma = {H = 0}; n = grad H / |grad H| (outward from Omega).
+Kind codes and parameter layouts are the ones in ``workloads``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import workloads as W
+
+
+def H(kind: int, p, X: np.ndarray) -> np.ndarray:
+    """Level-set value at points X (..., d)."""
+    if kind == W.LS_ELLIPSE:
+        cx, cy, a, b, th = p[:5]
+        x = X[..., 0] - cx
+        y = X[..., 1] - cy
+        c, s = np.cos(th), np.sin(th)
+        u = (x * c + y * s) / a
+        v = (y * c - x * s) / b
+        return u * u + v * v - 1.0
+    if kind == W.LS_STAR:
+        cx, cy, r0, amp, k = p[:5]
+        x = X[..., 0] - cx
+        y = X[..., 1] - cy
+        r = np.sqrt(x * x + y * y)
+        th = np.arctan2(y, x)
+        return r - r0 - amp * np.sin(k * th)
+    if kind == W.LS_ELLIPSOID:
+        cx, cy, cz, a, b, c = p[:6]
+        u = (X[..., 0] - cx) / a
+        v = (X[..., 1] - cy) / b
+        w = (X[..., 2] - cz) / c
+        return u * u + v * v + w * w - 1.0
+    if kind == W.LS_TORUS:
+        big, small = p[:2]
+        x, y, z = X[..., 0], X[..., 1], X[..., 2]
+        rho = np.sqrt(x * x + y * y)
+        t = rho - big
+        return t * t + z * z - small * small
+    if kind == W.LS_MOLECULE:
+        r, level, na = p[0], p[1], int(p[2])
+        acc = np.zeros(X.shape[:-1])
+        for k in range(na):
+            cx, cy, cz = p[3 + 3 * k: 6 + 3 * k]
+            dx = X[..., 0] - cx
+            dy = X[..., 1] - cy
+            dz = X[..., 2] - cz
+            acc = acc + np.exp(-(dx * dx + dy * dy + dz * dz) / (r * r))
+        return level - acc
+    raise ValueError(f"unknown level-set kind {kind}")
+
+
+def grad_H(kind: int, p, X: np.ndarray) -> np.ndarray:
+    """Analytic gradient of H at points X (..., d)."""
+    if kind == W.LS_ELLIPSE:
+        cx, cy, a, b, th = p[:5]
+        x = X[..., 0] - cx
+        y = X[..., 1] - cy
+        c, s = np.cos(th), np.sin(th)
+        u = (x * c + y * s) / a
+        v = (y * c - x * s) / b
+        gx = 2.0 * u * (c / a) + 2.0 * v * (-s / b)
+        gy = 2.0 * u * (s / a) + 2.0 * v * (c / b)
+        return np.stack([gx, gy], -1)
+    if kind == W.LS_STAR:
+        cx, cy, r0, amp, k = p[:5]
+        x = X[..., 0] - cx
+        y = X[..., 1] - cy
+        r2 = x * x + y * y
+        r = np.sqrt(r2)
+        th = np.arctan2(y, x)
+        dth = amp * k * np.cos(k * th)
+        gx = x / r + dth * y / r2
+        gy = y / r - dth * x / r2
+        return np.stack([gx, gy], -1)
+    if kind == W.LS_ELLIPSOID:
+        cx, cy, cz, a, b, c = p[:6]
+        return np.stack([2.0 * (X[..., 0] - cx) / (a * a),
+                         2.0 * (X[..., 1] - cy) / (b * b),
+                         2.0 * (X[..., 2] - cz) / (c * c)], -1)
+    if kind == W.LS_TORUS:
+        big, small = p[:2]
+        x, y, z = X[..., 0], X[..., 1], X[..., 2]
+        rho = np.sqrt(x * x + y * y)
+        f = 2.0 * (rho - big) / rho
+        return np.stack([f * x, f * y, 2.0 * z], -1)
+    if kind == W.LS_MOLECULE:
+        r, level, na = p[0], p[1], int(p[2])
+        g = np.zeros(X.shape)
+        for k in range(na):
+            cx, cy, cz = p[3 + 3 * k: 6 + 3 * k]
+            d = X - np.array([cx, cy, cz])
+            e = np.exp(-np.sum(d * d, -1) / (r * r))
+            g = g + (2.0 / (r * r)) * e[..., None] * d
+        return g
+    raise ValueError(f"unknown level-set kind {kind}")

@@ -1,0 +1,329 @@
+"""Seeded synthetic workloads for the correction-function KFBI solver.
+
+This module holds only problem *inputs*: level-set specifications (kind code +
+parameter vector), manufactured exact solutions, the data those solutions induce
+at given interface points (Dirichlet data g_D, jumps g1 = [u] and
+g2 = [sigma d_n u]) and on grid nodes (right-hand sides f and their Laplacians),
+and the seeded instance draws of the batched and learned workloads.  It contains
+none of the method's arithmetic (no classification, no collocation, no finite
+differences, no box solve), so both the CPU oracle and the CUDA path may import
+it without sharing any of the method.
+
+Sign conventions follow Sec. 2 and Sec. 5 of the paper: the level set H is
+negative inside Omega (the "+" side), the unit normal n = grad H / |grad H|
+points out of Omega, and jumps are [v] = v(inside) - v(outside).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Level-set kind codes (values shared with the C header's kfbi_levelset_kind).
+LS_ELLIPSE = 1      # 2D: p = [cx, cy, a, b, theta]
+LS_STAR = 2         # 2D: p = [cx, cy, R0, A, k]; r = R0 + A sin(k theta)
+LS_ELLIPSOID = 3    # 3D: p = [cx, cy, cz, a, b, c]
+LS_TORUS = 4        # 3D: p = [R, r] (axis z, centred at the origin)
+LS_MOLECULE = 5     # 3D: p = [r, level, n_atoms, x1, y1, z1, x2, ...]
+
+# Problem kinds (shared with kfbi_problem_kind).
+KIND_DIRICHLET = 0  # interior Dirichlet BVP, eq. (bie-D)
+KIND_INTERFACE_MU = 1  # two-medium interface problem, kappa = 0, mu-form BIE
+
+BOX_DST = 0
+BOX_MG = 1
+PREC_FP64 = 0
+PREC_MIXED = 1
+
+
+@dataclass
+class Workload:
+    """One synthetic problem: geometry, coefficients and manufactured solution."""
+
+    name: str
+    dim: int
+    n: int
+    lo: float
+    hi: float
+    ls_kind: int
+    ls_params: list
+    kind: int
+    sigma_in: float = 1.0
+    sigma_out: float = 1.0
+    kappa: float = 0.0
+    order: int = 4
+    cos_alpha: float | None = None
+    exact: str = ""
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def h(self) -> float:
+        return (self.hi - self.lo) / self.n
+
+    def cosa(self) -> float:
+        """cos(alpha) of the overlapping surface decomposition.  2D: 0.707, just
+        inside the admissible range alpha > 45 deg, which reproduces the paper's
+        Table 1 point counts N_b; 3D: 0.4."""
+        if self.cos_alpha is not None:
+            return self.cos_alpha
+        return 0.707 if self.dim == 2 else 0.4
+
+
+# ---------------------------------------------------------------------------
+# Manufactured solutions.  Each returns callables u(X), grad u(X), lap u(X) for
+# points X of shape (..., d).  They are the data of the synthetic problems.
+# ---------------------------------------------------------------------------
+
+def _sol_exp_sin():
+    # u = e^x sin y (harmonic)
+    u = lambda X: np.exp(X[..., 0]) * np.sin(X[..., 1])
+    g = lambda X: np.stack([np.exp(X[..., 0]) * np.sin(X[..., 1]),
+                            np.exp(X[..., 0]) * np.cos(X[..., 1])], -1)
+    lap = lambda X: np.zeros(X.shape[:-1])
+    return u, g, lap
+
+
+def _sol_paper_table1():
+    # u = exp(x) sin(cos(pi/3) x + sin(pi/3) y); lap u = 2 cos(pi/3) e^x cos(.)
+    ca, sa = math.cos(math.pi / 3), math.sin(math.pi / 3)
+    arg = lambda X: ca * X[..., 0] + sa * X[..., 1]
+    u = lambda X: np.exp(X[..., 0]) * np.sin(arg(X))
+    g = lambda X: np.stack([np.exp(X[..., 0]) * (np.sin(arg(X)) + ca * np.cos(arg(X))),
+                            np.exp(X[..., 0]) * sa * np.cos(arg(X))], -1)
+    lap = lambda X: 2.0 * ca * np.exp(X[..., 0]) * np.cos(arg(X))
+    return u, g, lap
+
+
+def _sol_sin_cos():
+    # u = sin x cos y; lap u = -2 u
+    u = lambda X: np.sin(X[..., 0]) * np.cos(X[..., 1])
+    g = lambda X: np.stack([np.cos(X[..., 0]) * np.cos(X[..., 1]),
+                            -np.sin(X[..., 0]) * np.sin(X[..., 1])], -1)
+    lap = lambda X: -2.0 * np.sin(X[..., 0]) * np.cos(X[..., 1])
+    return u, g, lap
+
+
+def _sol_r2():
+    # u = |x|^2 ; lap u = 2 d
+    u = lambda X: np.sum(X * X, axis=-1)
+    g = lambda X: 2.0 * X
+    lap = lambda X: np.full(X.shape[:-1], 2.0 * X.shape[-1])
+    return u, g, lap
+
+
+def _sol_exp3():
+    # u = e^{x+y+z}/10 ; lap u = 3 u
+    u = lambda X: np.exp(X[..., 0] + X[..., 1] + X[..., 2]) / 10.0
+    g = lambda X: np.repeat(u(X)[..., None], 3, axis=-1)
+    lap = lambda X: 3.0 * u(X)
+    return u, g, lap
+
+
+def _sol_zero(d):
+    u = lambda X: np.zeros(X.shape[:-1])
+    g = lambda X: np.zeros(X.shape)
+    lap = lambda X: np.zeros(X.shape[:-1])
+    return u, g, lap
+
+
+def _sol_harmonic3(amps):
+    # u = sum_k a_k h_k with h in {1, x, y, z, xy, yz, zx, x^2 - y^2}
+    a = np.asarray(amps, dtype=np.float64)
+
+    def u(X):
+        x, y, z = X[..., 0], X[..., 1], X[..., 2]
+        return (a[0] + a[1] * x + a[2] * y + a[3] * z + a[4] * x * y + a[5] * y * z
+                + a[6] * z * x + a[7] * (x * x - y * y))
+
+    def g(X):
+        x, y, z = X[..., 0], X[..., 1], X[..., 2]
+        gx = a[1] + a[4] * y + a[6] * z + 2 * a[7] * x
+        gy = a[2] + a[4] * x + a[5] * z - 2 * a[7] * y
+        gz = a[3] + a[5] * y + a[6] * x
+        return np.stack([gx, gy, gz], -1)
+
+    lap = lambda X: np.zeros(X.shape[:-1])
+    return u, g, lap
+
+
+def solutions(w: Workload):
+    """(u_in, grad_in, lap_in), (u_out, grad_out, lap_out) of a workload."""
+    e = w.exact
+    if e == "exp_sin":
+        s = _sol_exp_sin()
+        return s, _sol_zero(2)
+    if e == "paper_table1":
+        return _sol_paper_table1(), _sol_zero(2)
+    if e == "sincos_r2":
+        return _sol_sin_cos(), _sol_r2()
+    if e == "exp3":
+        return _sol_exp3(), _sol_zero(3)
+    if e == "harmonic3":
+        return _sol_harmonic3(w.extra["amps"]), _sol_zero(3)
+    raise ValueError(f"unknown exact solution {e!r}")
+
+
+def grid_coords(w: Workload) -> np.ndarray:
+    """Node coordinates x_i = lo + i h, shape (N+1,)*d + (d,), axis d-1 fastest."""
+    n = w.n
+    i = np.arange(n + 1)
+    x = w.lo + i * w.h
+    mesh = np.meshgrid(*([x] * w.dim), indexing="ij")
+    return np.stack(mesh, -1)
+
+
+def grid_data(w: Workload):
+    """Right-hand-side grids of the physical PDE on each side.
+
+    Returns dict with f_in, f_out (= sigma_side * lap u_side - kappa u_side, the f of
+    eqs. (BVP)/(IFP), smoothly extended to the whole box), their Laplacians
+    lapf_in, lapf_out (for the h^2/12 Lap f term of eqs. (9p-cds)/(27p-cds)),
+    the exact solution on both sides, and the outer boundary values g_B.
+    Laplacians of f are formed from the closed forms of the solutions.
+    """
+    X = grid_coords(w)
+    (ui, gi, li), (uo, go, lo_) = solutions(w)
+    d = w.dim
+    if w.kind == KIND_DIRICHLET:
+        s, k = w.sigma_in, w.kappa
+        f_in = s * li(X) - k * ui(X)
+        f_out = np.zeros_like(f_in)
+        lapf_in = _lap_of_f(w, X, inside=True)
+        lapf_out = np.zeros_like(f_in)
+        u_out_grid = np.zeros_like(f_in)
+    else:
+        f_in = w.sigma_in * li(X)
+        f_out = w.sigma_out * lo_(X)
+        lapf_in = _lap_of_f(w, X, inside=True)
+        lapf_out = _lap_of_f(w, X, inside=False)
+        u_out_grid = uo(X)
+    gb = np.zeros_like(f_in)
+    bmask = np.zeros(f_in.shape, dtype=bool)
+    for ax in range(d):
+        sl0 = [slice(None)] * d
+        sl0[ax] = 0
+        sl1 = [slice(None)] * d
+        sl1[ax] = -1
+        bmask[tuple(sl0)] = True
+        bmask[tuple(sl1)] = True
+    if w.kind == KIND_INTERFACE_MU:
+        gb[bmask] = u_out_grid[bmask]
+    return dict(f_in=f_in, f_out=f_out, lapf_in=lapf_in, lapf_out=lapf_out,
+                u_in=ui(X), u_out=u_out_grid, g_b=gb)
+
+
+def _lap_of_f(w: Workload, X, inside: bool):
+    """Closed-form Laplacian of the physical f on one side."""
+    e = w.exact
+    if e in ("exp_sin", "harmonic3"):
+        return np.zeros(X.shape[:-1])
+    if e == "paper_table1":
+        # f = lap u = 2 ca e^x cos(arg); lap(e^x cos(arg)) = 2 e^x * (-ca sin(arg)) + 0
+        ca, sa = math.cos(math.pi / 3), math.sin(math.pi / 3)
+        arg = ca * X[..., 0] + sa * X[..., 1]
+        return w.sigma_in * 2.0 * ca * (-2.0 * ca * np.exp(X[..., 0]) * np.sin(arg))
+    if e == "sincos_r2":
+        if inside:  # f = sigma_in * (-2 sin x cos y); lap = sigma_in * 4 sin x cos y
+            return w.sigma_in * 4.0 * np.sin(X[..., 0]) * np.cos(X[..., 1])
+        return np.zeros(X.shape[:-1])
+    if e == "exp3":  # f = (3 - kappa) u sigma-scaled; lap f = 3 f
+        u = np.exp(X[..., 0] + X[..., 1] + X[..., 2]) / 10.0
+        return 3.0 * (w.sigma_in * 3.0 - w.kappa) * u
+    raise ValueError(e)
+
+
+def boundary_data(w: Workload, pts: np.ndarray, normals: np.ndarray):
+    """Interface data at points with unit normals (outward from Omega).
+
+    Dirichlet BVP: returns (g_D, None).  Interface problem: returns
+    (g1, g2) with g1 = u_in - u_out and g2 = sigma_in d_n u_in - sigma_out d_n u_out,
+    the jump conditions of eq. (IFP-bc).
+    """
+    (ui, gi, _), (uo, go, _) = solutions(w)
+    if w.kind == KIND_DIRICHLET:
+        return ui(pts), None
+    g1 = ui(pts) - uo(pts)
+    g2 = (w.sigma_in * np.sum(gi(pts) * normals, -1)
+          - w.sigma_out * np.sum(go(pts) * normals, -1))
+    return g1, g2
+
+
+def exact_grid(w: Workload, inside_mask: np.ndarray) -> np.ndarray:
+    """Exact solution on the grid, side chosen by the given inside mask."""
+    X = grid_coords(w)
+    (ui, _, _), (uo, _, _) = solutions(w)
+    return np.where(inside_mask, ui(X), uo(X))
+
+
+# ---------------------------------------------------------------------------
+# The configured workloads.
+# ---------------------------------------------------------------------------
+
+def ellipse_dirichlet_2d(n: int = 64) -> Workload:
+    """2D interior Dirichlet Poisson BVP: x^2/0.36 + y^2/0.16 < 1, u = e^x sin y."""
+    return Workload("ellipse_dirichlet_2d", 2, n, -1.0, 1.0, LS_ELLIPSE,
+                    [0.0, 0.0, 0.6, 0.4, 0.0], KIND_DIRICHLET, exact="exp_sin")
+
+
+def paper_table1_2d(n: int = 64) -> Workload:
+    """The paper's first 2D example (Sec. 7.1.1): rotated ellipse a=1, b=0.5,
+    theta=-pi/6 in [-1.2, 1.2]^2 with u = exp(x) sin(cos(pi/3)x + sin(pi/3)y)."""
+    return Workload("paper_table1_2d", 2, n, -1.2, 1.2, LS_ELLIPSE,
+                    [0.0, 0.0, 1.0, 0.5, -math.pi / 6], KIND_DIRICHLET,
+                    exact="paper_table1")
+
+
+def flower_interface_2d(n: int = 256, contrast: float = 1000.0) -> Workload:
+    """2D Poisson interface problem, flower r = 0.5 + 0.1 sin(5 theta),
+    sigma_in/sigma_out = contrast, u_in = sin x cos y, u_out = x^2 + y^2."""
+    return Workload("flower_interface_2d", 2, n, -1.0, 1.0, LS_STAR,
+                    [0.0, 0.0, 0.5, 0.1, 5.0], KIND_INTERFACE_MU,
+                    sigma_in=contrast, sigma_out=1.0, exact="sincos_r2")
+
+
+def torus_helmholtz_3d(n: int = 128) -> Workload:
+    """3D Dirichlet modified-Helmholtz BVP (kappa = 1) inside the torus
+    (sqrt(x^2+y^2) - 0.5)^2 + z^2 < 0.2^2, u = e^{x+y+z}/10."""
+    return Workload("torus_helmholtz_3d", 3, n, -1.0, 1.0, LS_TORUS, [0.5, 0.2],
+                    KIND_DIRICHLET, kappa=1.0, exact="exp3")
+
+
+def star_batch_2d(count: int = 64, seed: int = 5965, sizes=(128, 256, 512, 1024)):
+    """Batched star-interface instances: R0~U[0.4,0.6], A~U[0,0.15], k~U{3..7},
+    contrast = 10^U[0,3], N ~ U(sizes), drawn in that order per instance."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        r0 = rng.uniform(0.4, 0.6)
+        a = rng.uniform(0.0, 0.15)
+        k = int(rng.integers(3, 8))
+        contrast = 10.0 ** rng.uniform(0.0, 3.0)
+        n = int(rng.choice(np.asarray(sizes)))
+        out.append(Workload(f"star_{i}", 2, n, -1.0, 1.0, LS_STAR,
+                            [0.0, 0.0, r0, a, float(k)], KIND_INTERFACE_MU,
+                            sigma_in=contrast, sigma_out=1.0, exact="sincos_r2"))
+    return out
+
+
+def ellipsoid_harmonic_3d(rng: np.random.Generator, n: int = 256,
+                          contrast: float = 10.0) -> Workload:
+    """Ellipsoid interface with axes ~U[0.3,0.7]^3, contrast 10, and interior
+    solution a random sum of 8 harmonic polynomials (amplitudes N(0,1)),
+    exterior solution 0."""
+    axes = rng.uniform(0.3, 0.7, size=3)
+    amps = rng.standard_normal(8)
+    return Workload("ellipsoid_harmonic_3d", 3, n, -1.0, 1.0, LS_ELLIPSOID,
+                    [0.0, 0.0, 0.0, *axes.tolist()], KIND_INTERFACE_MU,
+                    sigma_in=contrast, sigma_out=1.0, exact="harmonic3",
+                    extra={"amps": amps.tolist()})
+
+
+def sine_grid_rhs(dim: int, n: int, seed: int) -> np.ndarray:
+    """Seeded random interior right-hand side for box-solve tests, shape (N+1,)*d
+    with zero boundary layer."""
+    rng = np.random.default_rng(seed)
+    r = np.zeros((n + 1,) * dim)
+    inner = tuple(slice(1, n) for _ in range(dim))
+    r[inner] = rng.standard_normal((n - 1,) * dim)
+    return r
