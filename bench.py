@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""Benchmark: KFBI solves/s on one GB300 (or N independent replicas).
+
+Workload (default): the 2D interface problem with the flower interface
+r = 0.5 + 0.1 sin(5 theta) in [-1, 1]^2, sigma_in/sigma_out = 1000,
+u_in = sin x cos y, u_out = x^2 + y^2, on the 1024^2 grid, fourth order.
+One step = one complete solve through the C ABI: BIE right-hand side,
+matrix-free GMRES to the relative residual --rtol and the final evaluation on
+the grid (kfbi_gmres_solve + kfbi_evaluate).  The geometry set-up
+(kfbi_create_problem) is outside the timed region and reported separately.
+
+Also reported: box-solve Mpts/s (kfbi_box_solve alone), the plain FP64 path at
+the same tolerance, an end-to-end figure with host buffers, the roofline of
+the dominant kernel class, and the CPU oracle on the host cores.
+
+`--impl reference` times the CPU oracle (the plain FP64 NumPy/SciPy
+implementation) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP64_ALU_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 2 FP64 FMA / clk / SM at 2070 MHz
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+METRIC = "KFBI solves/sec & box-solve Mpts/s vs plain FP64 GPU at 1e-8 rel err; %HBM"
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def workload(n):
+    import workloads as W
+    return W.flower_interface_2d(n)
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2309_05965_gb300 import build, kfbi
+
+    build.build()
+    torch.cuda.set_device(rank % max(1, torch.cuda.device_count()))
+    stream = torch.cuda.current_stream()
+    w = workload(args.n)
+    prec = kfbi.MIXED if args.precision == "mixed" else kfbi.FP64
+    box = kfbi.BOX_MG if args.box == "mg" else kfbi.BOX_DST
+    t0 = time.perf_counter()
+    G = kfbi.Problem.from_workload(w, box_solver=box, precision=prec)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    d = w.dim
+    xyz = torch.zeros((G.nb, d), dtype=torch.float64, device="cuda")
+    nrm = torch.zeros((G.nb, d), dtype=torch.float64, device="cuda")
+    kfbi.kfbi_dof_points(G.handle, xyz, nrm)
+    g1, g2 = W.boundary_data(w, xyz.cpu().numpy(), nrm.cpu().numpy())
+    grid = W.grid_data(w)
+    host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
+            (("g1", g1), ("g2", g2), ("f_in", grid["f_in"]), ("f_out", grid["f_out"]),
+             ("lapf_in", grid["lapf_in"]), ("lapf_out", grid["lapf_out"]), ("g_b", grid["g_b"]))}
+    devd = {k: v.cuda() for k, v in host.items()}
+    data = kfbi.make_data(**devd)
+    dens = torch.zeros(G.nb, dtype=torch.float64, device="cuda")
+    u = torch.zeros(G.grid_shape, dtype=torch.float64, device="cuda")
+    opts = kfbi.GmresOpts(rtol=args.rtol, restart=100, max_iter=300, x0=None)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def step():
+        info = kfbi.kfbi_gmres_solve(G.handle, data, opts, dens)
+        kfbi.kfbi_evaluate(G.handle, data, dens, u)
+        return info
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    kfbi.kfbi_launch_counts(G.handle, reset=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    times = []
+    iters = []
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        iters.append(info.iters)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    launches = kfbi.kfbi_launch_counts(G.handle, reset=True)
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+
+    # accuracy of the last solve
+    ex = W.exact_grid(w, _inside(G, kfbi))
+    err = float(np.abs(u.cpu().numpy() - ex)[1:-1, 1:-1].max())
+
+    # ---- end to end through the C ABI with host buffers
+    e2e_times = []
+    u_host = torch.empty(G.grid_shape, dtype=torch.float64).pin_memory()
+    h2d = sum(v.numel() * 8 for v in host.values())
+    d2h = u.numel() * 8
+    for _ in range(max(2, args.steps // 2)):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in host:
+            devd[k].copy_(host[k], non_blocking=True)
+        step()
+        u_host.copy_(u, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_times.append(e0.elapsed_time(e1))
+    e2e_value = world * len(e2e_times) / (sum(e2e_times) / 1e3)
+
+    # ---- box solve alone
+    rhs = torch.randn(G.grid_shape, dtype=torch.float64, device="cuda")
+    ub = torch.zeros_like(rhs)
+    bt = []
+    for _ in range(5):
+        kfbi.kfbi_box_solve(G.handle, rhs, ub)
+    for _ in range(30):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        kfbi.kfbi_box_solve(G.handle, rhs, ub)
+        e1.record(stream)
+        e1.synchronize()
+        bt.append(e0.elapsed_time(e1))
+    box_ms = statistics.median(bt)
+    npts = (args.n - 1) ** d
+    box_mpts = npts / (box_ms * 1e-3) / 1e6
+
+    # ---- per-class profile (a separate pass with event timing enabled)
+    kfbi.kfbi_profile_enable(G.handle, True)
+    for _ in range(2):
+        flush.zero_()
+        step()
+    prof = kfbi.kfbi_profile_read(G.handle)
+    kfbi.kfbi_profile_enable(G.handle, False)
+    roof = roofline(args, G, prof, prec)
+
+    # ---- the plain FP64 path at the same tolerance
+    fp64 = None
+    if args.compare_fp64 and prec != kfbi.FP64:
+        G64 = kfbi.Problem.from_workload(w, box_solver=kfbi.BOX_DST, precision=kfbi.FP64)
+        u64 = torch.zeros_like(u)
+        d64 = torch.zeros_like(dens)
+        for _ in range(2):
+            kfbi.kfbi_gmres_solve(G64.handle, data, opts, d64)
+            kfbi.kfbi_evaluate(G64.handle, data, d64, u64)
+        t64 = []
+        for _ in range(max(3, args.steps // 3)):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            kfbi.kfbi_gmres_solve(G64.handle, data, opts, d64)
+            kfbi.kfbi_evaluate(G64.handle, data, d64, u64)
+            e1.record(stream)
+            e1.synchronize()
+            t64.append(e0.elapsed_time(e1))
+        err64 = float(np.abs(u64.cpu().numpy() - ex)[1:-1, 1:-1].max())
+        diff = float(np.abs(u64.cpu().numpy() - u.cpu().numpy()).max())
+        fp64 = {"solves_per_s": 1e3 / statistics.mean(t64), "ms_per_solve": statistics.mean(t64),
+                "max_err_vs_exact": err64, "max_diff_vs_mixed": diff}
+        G64.close()
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 (FP32 box solve with FP64 residual refinement)" if prec else "f64",
+        "data": "synthetic (manufactured solution, seeded, analytic level set)",
+        "config": {"workload": f"flower interface 2D, N={args.n}, sigma_in/sigma_out=1000, "
+                               f"4th order, GMRES rtol {args.rtol:g}",
+                   "box_solver": args.box, "precision": args.precision, "n_b": G.nb,
+                   "n_irr": G.nirr, "l2": "flushed (256 MB write) before every step",
+                   "parallelism": "independent replicas" if world > 1 else "1 GPU"},
+        "gmres_iterations": iters[-1], "max_err_vs_exact": err,
+        "setup_ms": setup_ms, "wall_s_timed": wall,
+        "box_solve_mpts_s": box_mpts, "box_solve_ms": box_ms,
+        "fp64_path": fp64,
+        "speedup_vs_fp64": (value / world) / fp64["solves_per_s"] if fp64 else None,
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(sum(launches.values())),
+        "gpu_launches_by_class": launches,
+        "kernel_ms_per_step": {k: v[0] / 2 for k, v in prof.items()},
+        "roofline": roof,
+    }
+    if rank == 0 and args.cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_budget)
+    G.close()
+    return out
+
+
+def _inside(G, kfbi):
+    import torch
+    m = torch.zeros(G.grid_shape, dtype=torch.uint8, device="cuda")
+    kfbi.kfbi_inside_mask(G.handle, m)
+    return m.cpu().numpy().astype(bool)
+
+
+def roofline(args, G, prof, prec):
+    """Roofline of the dominant kernel class from the profiling pass.
+    Algorithmic bytes / flops per unit are stated in the design doc."""
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    name = max(prof, key=lambda k: prof[k][0])
+    ms, launches = prof[name]
+    n = args.n
+    npts = (n - 1) ** 2
+    per_launch_ms = ms / max(1, launches)
+    if name == "dst":
+        # three passes per transform: FP64 in -> FP32, FP32 -> FP32, FP32 -> FP64 (+=)
+        if prec:
+            bytes_per_solve = npts * ((8 + 4) + (4 + 4) + (4 + 16))
+        else:
+            bytes_per_solve = npts * (8 + 8) * 3
+        achieved = bytes_per_solve / 3 / (per_launch_ms * 1e-3) / 1e9
+        return {"kernel": "dst", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "note": "peak of measured (MEASURED_PEAKS.json hbm_gbs)"}
+    if name == "residual":
+        flops = npts * 10.0
+        achieved = flops / (per_launch_ms * 1e-3) / 1e12
+        return {"kernel": "residual", "bound": "alu", "achieved": achieved,
+                "peak": FP64_ALU_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_ALU_TFLOPS,
+                "traffic": None, "note": "FP64 ALU peak 152 SM x 2 FMA/clk x 2.07 GHz"}
+    # other classes: report measured time share only
+    achieved = 0.0
+    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_ALU_TFLOPS,
+            "unit": "TFLOP/s", "frac": None, "traffic": None}
+
+
+def cpu_baseline(args, budget_s=20.0):
+    """The oracle as it stands on the host cores: full solves of the same
+    workload (set-up excluded), within a time budget."""
+    import numpy as np
+
+    import workloads as W
+    from oracle import kfbi as OK
+    w = workload(args.n)
+    P = OK.Problem(w)
+    data = W.grid_data(w)
+    g1, g2 = W.boundary_data(w, P.surf.x, P.surf.n)
+    t0 = time.perf_counter()
+    count = 0
+    while True:
+        P.solve(g1, g2, data, rtol=args.rtol)
+        count += 1
+        if time.perf_counter() - t0 > budget_s or count >= 5:
+            break
+    el = time.perf_counter() - t0
+    return {"value": count / el, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{count} full oracle solves of the same workload (N={args.n}), set-up "
+                      "excluded, single-threaded NumPy/SciPy (scipy.fft workers=1)",
+            "host": os.uname().machine, "cpu_count": os.cpu_count()}
+
+
+def run_reference(args):
+    """CPU oracle arm: each step is one full oracle solve of the workload."""
+    import workloads as W
+    from oracle import kfbi as OK
+    w = workload(args.n)
+    P = OK.Problem(w)
+    data = W.grid_data(w)
+    g1, g2 = W.boundary_data(w, P.surf.x, P.surf.n)
+    for _ in range(args.warmup):
+        P.solve(g1, g2, data, rtol=args.rtol)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        P.solve(g1, g2, data, rtol=args.rtol)
+    el = time.perf_counter() - t0
+    v = args.steps / el
+    return {"metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (manufactured solution, seeded, analytic level set)",
+            "config": {"workload": f"flower interface 2D, N={args.n}, sigma_in/sigma_out=1000, "
+                                   f"4th order, GMRES rtol {args.rtol:g}"},
+            "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full oracle solves (set-up excluded)"},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--box", default="dst", choices=["dst", "mg"])
+    ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,240 @@
+/*
+ * kfbi.h — C ABI of the GB300 correction-function KFBI library.
+ *
+ * The library evaluates the boundary integral operators of the kernel-free
+ * boundary integral method of Zhou & Ying, "A correction function-based
+ * kernel-free boundary integral method for elliptic PDEs with implicitly
+ * defined interfaces" (arXiv 2309.05965), and solves the resulting boundary
+ * integral equations with matrix-free GMRES, entirely on one GPU.
+ *
+ * Conventions (all entry points):
+ *   - Every array argument is a DEVICE pointer unless stated otherwise; the
+ *     caller owns it and keeps it alive until the enqueued work has finished.
+ *   - Work is enqueued on the CUDA stream given to kfbi_create_problem.  Calls
+ *     return after enqueueing, except where a host-visible result is produced
+ *     (kfbi_create_problem, kfbi_gmres_solve, size queries), which synchronise
+ *     that stream.
+ *   - Grids are (N+1)^d FP64 node arrays over the box [lo, hi]^d, C order with
+ *     the last axis fastest: node (i0, i1[, i2]) has linear index
+ *     (i0 (N+1) + i1) (N+1) + i2 and coordinates lo + i_k h, h = (hi - lo)/N.
+ *   - DOF arrays (length N_b) follow the DOF order: family r ascending (the
+ *     point lies on a grid line parallel to e_r), then the grid line (other
+ *     axes lexicographic, lower axis slowest), then the position along it.
+ *   - Sign conventions (Sec. 2, Sec. 5): Omega = {H < 0} is the '+' side; the
+ *     normal n = grad H / |grad H| points out of Omega; jumps are
+ *     [v] = v(inside) - v(outside).
+ *   - No call throws; every call returns a kfbi_status, and kfbi_last_error
+ *     returns a message for the last failure on that problem.
+ *   - There is no CPU fallback: a build without a usable GPU fails at create.
+ */
+#ifndef KFBI_H
+#define KFBI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KFBI_OK = 0,
+  KFBI_ERR_ARG = 1,            /* invalid argument or size                       */
+  KFBI_ERR_GEOMETRY = 2,       /* no collocation stencil (under-resolved Gamma)  */
+  KFBI_ERR_SINGULAR = 3,       /* collocation / trace system singular (cond>1e10)*/
+  KFBI_ERR_NOT_CONVERGED = 4,  /* GMRES or inner box solve reached its limit     */
+  KFBI_ERR_NONFINITE = 5,      /* NaN or Inf in data or results                  */
+  KFBI_ERR_TIMEOUT = 6,        /* a bounded device wait gave up                  */
+  KFBI_ERR_CUDA = 7,           /* a CUDA runtime call failed                     */
+  KFBI_ERR_UNSUPPORTED = 8     /* configuration not supported                    */
+} kfbi_status;
+
+/* Analytic level-set families H (Sec. 5.1: Gamma = {H = 0}). */
+typedef enum {
+  KFBI_LS_ELLIPSE = 1,    /* 2D p=[cx,cy,a,b,theta]: rotated ellipse              */
+  KFBI_LS_STAR = 2,       /* 2D p=[cx,cy,R0,A,k]: r - R0 - A sin(k theta)         */
+  KFBI_LS_ELLIPSOID = 3,  /* 3D p=[cx,cy,cz,a,b,c]                                */
+  KFBI_LS_TORUS = 4,      /* 3D p=[R,r]: (sqrt(x^2+y^2)-R)^2 + z^2 - r^2          */
+  KFBI_LS_MOLECULE = 5    /* 3D p=[r,level,n,x1,y1,z1,...]: level - sum exp(-|x-x_k|^2/r^2) */
+} kfbi_levelset_kind;
+
+typedef enum {
+  KFBI_DIRICHLET_INTERIOR = 0, /* eq. (bie-D): (1/2 + K) phi = g_D - G f           */
+  KFBI_INTERFACE_MU = 1        /* mu-form BIE of Sec. 3.2 for psi = [d_n u]         */
+} kfbi_problem_kind;
+
+typedef enum { KFBI_BOX_DST = 0, KFBI_BOX_MG = 1 } kfbi_box_solver;
+typedef enum { KFBI_FP64 = 0, KFBI_MIXED = 1 } kfbi_precision;
+
+#define KFBI_LS_MAX_PARAMS 64
+
+typedef struct {
+  int kind;                      /* kfbi_levelset_kind */
+  int n_params;
+  double p[KFBI_LS_MAX_PARAMS];
+} kfbi_levelset;
+
+typedef struct {
+  int dim;                /* 2 or 3                                               */
+  int n;                  /* intervals per axis N (power of two, 16..2048 in 2D,
+                             16..512 in 3D)                                       */
+  double lo, hi;          /* box [lo, hi]^dim                                     */
+  int order;              /* 4 (compact 9/27-point) or 2 (5/7-point)              */
+  int kind;               /* kfbi_problem_kind                                    */
+  double sigma_in;        /* sigma in Omega (the '+' side)                         */
+  double sigma_out;       /* sigma outside (interface problem only)               */
+  double kappa;           /* Dirichlet BVP: kappa of eq. (BVP); mu-form: kappa~ of
+                             eq. (bie-ifp-2) (kappa_i / sigma_i, the same on both
+                             sides)                                               */
+  int box_solver;         /* kfbi_box_solver                                      */
+  int precision;          /* kfbi_precision: FP64, or FP32 box solve with FP64
+                             residuals and iterative refinement                   */
+  double cos_alpha;       /* overlapping surface decomposition; <= 0 selects the
+                             default (0.707 in 2D, 0.4 in 3D)                     */
+  double box_rtol;        /* inner tolerance of MG / refinement (<= 0: 1e-13)     */
+  int box_max_iters;      /* inner iteration limit (<= 0: 60)                     */
+} kfbi_config;
+
+/* Problem data (Sec. 2).  f_* are the physical right-hand sides f of eqs.
+ * (BVP)/(IFP) on each side, smoothly extended to the whole box; the library
+ * divides them by sigma.  lapf_* are their Laplacians (for the h^2/12 Lap f term
+ * of eqs. (9p-cds)/(27p-cds)).  Dirichlet BVP: g1 = g_D, g2, f_out, lapf_out and
+ * g_b unused (may be NULL).  Interface: g1 = [u], g2 = [sigma d_n u], g_b = outer
+ * Dirichlet values (NULL = homogeneous).  Any grid may be NULL (= 0). */
+typedef struct {
+  const double* g1;       /* N_b   */
+  const double* g2;       /* N_b   */
+  const double* f_in;     /* grid  */
+  const double* f_out;    /* grid  */
+  const double* lapf_in;  /* grid  */
+  const double* lapf_out; /* grid  */
+  const double* g_b;      /* grid (only its box-boundary layer is read) */
+} kfbi_data;
+
+typedef struct {
+  double rtol;            /* stop at ||b - A x|| <= rtol ||b||                     */
+  int restart;            /* Krylov dimension before a restart (<= 100)           */
+  int max_iter;           /* total operator applications                          */
+  const double* x0;       /* initial density (device, N_b) or NULL for zero       */
+} kfbi_gmres_opts;
+
+typedef struct {
+  int iters;              /* operator applications in Arnoldi                     */
+  double rel_res;         /* final ||b - A x|| / ||b|| (GMRES estimate)           */
+  double t_ms[8];         /* [0] BIE right-hand side, [1] GMRES loop, [2] total   */
+} kfbi_gmres_info;
+
+typedef struct kfbi_problem kfbi_problem;
+
+/* Kernel classes for launch accounting and profiling (kfbi_profile_*). */
+typedef enum {
+  KFBI_KC_CORRECTION = 0,  /* C at irregular nodes (Step 3.1)                  */
+  KFBI_KC_RHS = 1,         /* corrected right-hand side (Step 3.2)             */
+  KFBI_KC_DST = 2,         /* sine-transform passes of the box solve (3.3)     */
+  KFBI_KC_RESIDUAL = 3,    /* FP64 residual / norms of the refinement (3.3)    */
+  KFBI_KC_MG = 4,          /* multigrid smoothing and transfers (3.3)          */
+  KFBI_KC_TRACE = 5,       /* corrected interpolation + BIE combination (3.4)  */
+  KFBI_KC_GMRES = 6,       /* Arnoldi, Givens and updates (Step 4)             */
+  KFBI_KC_OTHER = 7,
+  KFBI_KC_COUNT = 8
+} kfbi_kernel_class;
+
+/* ---- problem lifetime -------------------------------------------------- */
+
+/* Builds the discretisation of one geometry on the GPU (Sec. 5.1, 5.4):
+ * node classes, grid-line intersections (the DOFs), reference planes,
+ * collocation stencils and the inverses of the collocation matrices M (eq.
+ * (cau-ls)), irregular nodes and their closest primary points, the correction
+ * stencils (eq. (crc-formula)), the trace least-squares weights (Sec. 5.5) and
+ * the box solver.  `cuda_stream` is a cudaStream_t (NULL = legacy default).
+ * On failure *out is NULL; KFBI_ERR_GEOMETRY / KFBI_ERR_SINGULAR report an
+ * under-resolved interface. */
+kfbi_status kfbi_create_problem(const kfbi_config* cfg, const kfbi_levelset* ls,
+                                void* cuda_stream, kfbi_problem** out);
+kfbi_status kfbi_destroy_problem(kfbi_problem* p);
+/* Message of the last failure on p; with p == NULL, of the last failed
+ * kfbi_create_problem on the calling thread.  Owned by the library. */
+const char* kfbi_last_error(const kfbi_problem* p);
+
+/* ---- sizes and geometry queries ---------------------------------------- */
+
+/* N_b, number of irregular nodes, and the number of polynomial coefficients
+ * per primary point (15/35 for p = 4, 6/10 for p = 2). Host outputs. */
+kfbi_status kfbi_sizes(const kfbi_problem* p, int* n_b, int* n_irr, int* n_coef);
+kfbi_status kfbi_num_dofs(const kfbi_problem* p, int* n_b);
+/* DOF coordinates and unit normals, (N_b, dim) row-major. */
+kfbi_status kfbi_dof_points(const kfbi_problem* p, double* xyz, double* normals);
+/* Per DOF: family r, reference axis argmax|n_k|, axis used by its stencil. */
+kfbi_status kfbi_dof_info(const kfbi_problem* p, int32_t* family, int32_t* axis,
+                          int32_t* stencil_axis);
+/* Collocation stencils (Sec. 5.4): PDE node linear indices (N_b, n_pde),
+ * Dirichlet DOF indices (N_b, n_dir), Neumann DOF indices (N_b, n_neu). */
+kfbi_status kfbi_stencil_sizes(const kfbi_problem* p, int* n_pde, int* n_dir, int* n_neu);
+kfbi_status kfbi_collocation_stencils(const kfbi_problem* p, int32_t* pde_nodes,
+                                      int32_t* dir_dofs, int32_t* neu_dofs);
+/* Node classes (1 = inside Omega), one byte per grid node. */
+kfbi_status kfbi_inside_mask(const kfbi_problem* p, uint8_t* mask);
+/* Irregular nodes I_h in linear-index order and the closest primary point of
+ * each (Sec. 5.3 partition of unity). */
+kfbi_status kfbi_irregular_nodes(const kfbi_problem* p, int32_t* lin_index, int32_t* owner);
+
+/* ---- the four steps of Algorithm 1, Step 3, one at a time -------------- */
+
+/* Step 3.1: coefficients d_i of every local correction polynomial (N_b, n_coef),
+ * graded-lexicographic monomial order in xi = (x - p_i)/h.  a = [u], b = [d_n u]
+ * at the DOFs; ftilde = f~ = f+/sigma - f-/sigma grid (NULL = 0). */
+kfbi_status kfbi_collocation_fit(kfbi_problem* p, const double* a, const double* b,
+                                 const double* ftilde, double* coef);
+/* Correction function C_h at every irregular node (n_irr), eq. (local-cau-prb)
+ * with the closest-point partition of unity. */
+kfbi_status kfbi_correction_values(kfbi_problem* p, const double* a, const double* b,
+                                   const double* ftilde, double* cvals);
+/* Step 3.2: right-hand side of eq. (corrected-FDS) on the grid: F + h^2/12 Lap F
+ * from each node's own side (data may be NULL = no source), plus C_P of eq.
+ * (crc-formula), minus the outer-boundary lift of data->g_b.  Boundary layer 0. */
+kfbi_status kfbi_corrected_rhs(kfbi_problem* p, const double* cvals, const kfbi_data* data,
+                               double* rhs);
+/* Step 3.3: u = A_h^{-1} rhs on the interior (DST-I or multigrid, FP64 or
+ * mixed precision, per the config); boundary layer of u set to 0. */
+kfbi_status kfbi_box_solve(kfbi_problem* p, const double* rhs, double* u);
+/* Step 3.4: one-sided values and normal derivatives at every DOF from a grid
+ * function u and C at the irregular nodes (Sec. 5.5).  Any output may be NULL. */
+kfbi_status kfbi_traces(kfbi_problem* p, const double* u, const double* cvals,
+                        double* val_plus, double* val_minus, double* dn_plus,
+                        double* dn_minus);
+
+/* ---- operators and solves ---------------------------------------------- */
+
+/* One application of the discrete BIE operator (Steps 3.1-3.4 plus the BIE
+ * combination): Dirichlet y = x/2 + avg trace of D x; mu-form
+ * y = x/2 - mu avg d_n of (-S x). */
+kfbi_status kfbi_apply_operator(kfbi_problem* p, const double* x, double* y);
+/* Right-hand side of the BIE (Algorithm 1, Step 1). */
+kfbi_status kfbi_bie_rhs(kfbi_problem* p, const kfbi_data* data, double* b);
+/* Algorithm 1: BIE right-hand side, GMRES (Step 4) from opts->x0 or zero.
+ * density: N_b output. info: host pointer (may be NULL). */
+kfbi_status kfbi_gmres_solve(kfbi_problem* p, const kfbi_data* data,
+                             const kfbi_gmres_opts* opts, double* density,
+                             kfbi_gmres_info* info);
+/* Grid solution from a density by superposition (one more potential solve):
+ * Dirichlet u = D phi + N f; interface u with [u] = g1, [d_n u] = psi. */
+kfbi_status kfbi_evaluate(kfbi_problem* p, const kfbi_data* data, const double* density,
+                          double* u_grid);
+
+/* ---- accounting -------------------------------------------------------- */
+
+/* Kernel launches per class since creation or the last reset (host output of
+ * KFBI_KC_COUNT int64 values); reset != 0 zeroes the counters afterwards. */
+kfbi_status kfbi_launch_counts(kfbi_problem* p, int64_t* counts, int reset);
+/* Enable (1) or disable (0) per-launch timing with CUDA events on the problem's
+ * stream; enabling discards earlier records.  Adds host work per launch: keep
+ * it off in timed runs. */
+kfbi_status kfbi_profile_enable(kfbi_problem* p, int enable);
+/* Synchronises the stream and returns, per class, the summed device time (ms)
+ * and the number of timed launches since profiling was enabled (host outputs
+ * of KFBI_KC_COUNT values each). */
+kfbi_status kfbi_profile_read(kfbi_problem* p, double* ms, int64_t* timed_launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KFBI_H */

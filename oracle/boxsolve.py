@@ -62,22 +62,28 @@ def apply_operator(u: np.ndarray, d: int, order: int, h: float, kappa: float) ->
 
 
 def eigenvalues(d: int, order: int, n: int, h: float, kappa: float) -> np.ndarray:
-    """Closed-form eigenvalues on the (N-1)^d sine modes."""
-    cp = np.cos(np.arange(1, n) * np.pi / n)
-    C = np.meshgrid(*([cp] * d), indexing="ij")
+    """Closed-form eigenvalues on the (N-1)^d sine modes, written with
+    s_k = sin^2(k pi / 2N) (cos(k pi/N) = 1 - 2 s_k) so that the low modes carry
+    no cancellation:
+      9-point:  h^-2 [-4 (s_p + s_q) + 8/3 s_p s_q] - kappa [1 - (s_p + s_q)/3]
+      27-point: h^-2 [-4 S1 + 8/3 S2 - 4/3 S3]      - kappa [1 - S1/3]
+      5/7-point: h^-2 (-4 S1) - kappa
+    (S1, S2, S3 the elementary symmetric sums of the s_k).  Expanding c = 1 - 2s
+    in h^-2[-10/3 + 4/3 (c_p + c_q) + 2/3 c_p c_q] - kappa[2/3 + (c_p + c_q)/6]
+    (and the 27-point analogue from eq. (27p-cds)) gives these forms."""
+    sk = np.sin(np.arange(1, n) * np.pi / (2 * n)) ** 2
+    S = np.meshgrid(*([sk] * d), indexing="ij")
     ih2 = 1.0 / (h * h)
+    s1 = sum(S)
     if order == 2:
-        return ih2 * sum(2.0 * ck - 2.0 for ck in C) - kappa
+        return ih2 * (-4.0 * s1) - kappa
     if d == 2:
-        cx, cy = C
-        return (ih2 * (-10.0 / 3.0 + 4.0 / 3.0 * (cx + cy) + 2.0 / 3.0 * cx * cy)
-                - kappa * (2.0 / 3.0 + (cx + cy) / 6.0))
-    cx, cy, cz = C
-    s1 = cx + cy + cz
-    s2 = cx * cy + cy * cz + cz * cx
-    s3 = cx * cy * cz
-    return (ih2 * (-25.0 / 6.0 + 5.0 / 6.0 * s1 + 0.5 * s2 + s3 / 6.0)
-            - kappa * (0.5 + s1 / 6.0))
+        sp, sq = S
+        return ih2 * (-4.0 * s1 + 8.0 / 3.0 * sp * sq) - kappa * (1.0 - s1 / 3.0)
+    sx, sy, sz = S
+    s2 = sx * sy + sy * sz + sz * sx
+    s3 = sx * sy * sz
+    return ih2 * (-4.0 * s1 + 8.0 / 3.0 * s2 - 4.0 / 3.0 * s3) - kappa * (1.0 - s1 / 3.0)
 
 
 def dst_solve(rhs: np.ndarray, d: int, order: int, h: float, kappa: float) -> np.ndarray:

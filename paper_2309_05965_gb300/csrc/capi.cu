@@ -1,0 +1,471 @@
+// C ABI of the GB300 KFBI library (see include/kfbi.h): problem lifetime,
+// queries, the four steps of Algorithm 1 Step 3 one at a time, the BIE
+// operator, the BIE right-hand side (Algorithm 1 Step 1), GMRES (Step 4) and
+// the final evaluation by superposition (Sec. 6).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "kfbi_internal.cuh"
+
+namespace kfbi {
+
+kfbi_status fail(kfbi_problem* p, kfbi_status s, const std::string& msg) {
+  if (p) p->err = msg;
+  return s;
+}
+
+// One application of the discrete BIE operator: Steps 3.1-3.4 + combination.
+kfbi_status apply_operator_impl(kfbi_problem* p, const double* x, double* y) {
+  const bool dir = p->cfg.kind == KFBI_DIRICHLET_INTERIOR;
+  // Step 3.1 (fitted and evaluated at the irregular nodes)
+  KFBI_TRY(launch_correction_values(p, dir ? x : nullptr, dir ? nullptr : x, nullptr, p->cvals));
+  // Step 3.2
+  KFBI_TRY(launch_rhs(p, p->cvals, nullptr, p->rhs));
+  // Step 3.3
+  KFBI_TRY(box_solve(p, p->rhs, p->ugrid));
+  // Step 3.4 + BIE: Dirichlet y = x/2 + avg value; mu-form y = x/2 - mu avg d_n
+  return launch_operator_trace(p, p->ugrid, p->cvals, x, 0.5, dir ? 1.0 : -p->mu, y);
+}
+
+// One operator application through a CUDA graph captured on first use (the
+// caller's stream may be the legacy stream, which cannot be captured, so the
+// capture runs on a private stream and the graph is launched on p->stream).
+kfbi_status apply_operator_fast(kfbi_problem* p, const double* x, double* y) {
+  if (!p->use_graphs || p->prof.on) return apply_operator_impl(p, x, y);
+  cudaStream_t st = p->stream;
+  if (!p->op_exec) {
+    if (!p->cap_stream) KFBI_CUDA(p, cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    KFBI_CUDA(p, cudaStreamSynchronize(st));
+    long long before[KFBI_KC_COUNT];
+    for (int k = 0; k < KFBI_KC_COUNT; ++k) before[k] = p->prof.launches[k];
+    p->stream = p->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
+    kfbi_status s = KFBI_OK;
+    if (e == cudaSuccess) s = apply_operator_impl(p, p->xbuf, p->ybuf);
+    cudaGraph_t gr = nullptr;
+    cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(p->cap_stream, &gr) : e;
+    p->stream = st;
+    for (int k = 0; k < KFBI_KC_COUNT; ++k) {
+      p->op_counts[k] = p->prof.launches[k] - before[k];
+      p->prof.launches[k] = before[k];
+    }
+    if (e != cudaSuccess || e2 != cudaSuccess || s != KFBI_OK) {
+      if (gr) cudaGraphDestroy(gr);
+      cudaGetLastError();
+      p->use_graphs = false;   // fall back to direct launches (same kernels)
+      return apply_operator_impl(p, x, y);
+    }
+    p->op_graph = gr;
+    KFBI_CUDA(p, cudaGraphInstantiate(&p->op_exec, gr, 0));
+  }
+  KFBI_CUDA(p, cudaMemcpyAsync(p->xbuf, x, sizeof(double) * p->nb, cudaMemcpyDeviceToDevice, st));
+  KFBI_CUDA(p, cudaGraphLaunch(p->op_exec, st));
+  KFBI_CUDA(p, cudaMemcpyAsync(y, p->ybuf, sizeof(double) * p->nb, cudaMemcpyDeviceToDevice, st));
+  for (int k = 0; k < KFBI_KC_COUNT; ++k) p->prof.launches[k] += p->op_counts[k];
+  return KFBI_OK;
+}
+
+static kfbi_status potential_with_data(kfbi_problem* p, const double* a, const double* b,
+                                       const kfbi_data* data, bool use_gb, double* u) {
+  kfbi_data dd;
+  memset(&dd, 0, sizeof(dd));
+  if (data) dd = *data;
+  if (!use_gb) dd.g_b = nullptr;
+  KFBI_TRY(launch_correction_values_data(p, a, b, &dd, p->cvals));
+  KFBI_TRY(launch_rhs(p, p->cvals, &dd, p->rhs));
+  KFBI_TRY(box_solve(p, p->rhs, u));
+  return launch_set_boundary(p, u, use_gb ? dd.g_b : nullptr);
+}
+
+kfbi_status bie_rhs_impl(kfbi_problem* p, const kfbi_data* data, double* bvec) {
+  const bool dir = p->cfg.kind == KFBI_DIRICHLET_INTERIOR;
+  if (dir) {
+    // b = g_D - G f, G f = avg trace of N f (a = b = 0, F = f/sigma inside)
+    KFBI_TRY(potential_with_data(p, nullptr, nullptr, data, false, p->ugrid));
+    return launch_operator_trace(p, p->ugrid, p->cvals, data->g1, 1.0, -1.0, bvec);
+  }
+  // b = g2/(sigma_in + sigma_out) + mu avg d_n w, w with a = g1, F = f/sigma, g_B
+  KFBI_TRY(potential_with_data(p, data->g1, nullptr, data, true, p->ugrid));
+  return launch_operator_trace(p, p->ugrid, p->cvals, data->g2,
+                               1.0 / (p->cfg.sigma_in + p->cfg.sigma_out), p->mu, bvec);
+}
+
+}  // namespace kfbi
+
+using namespace kfbi;
+
+// Message of the last failed kfbi_create_problem on this thread (the problem
+// object does not survive a failed create).
+static thread_local std::string g_create_error;
+
+extern "C" {
+
+kfbi_status kfbi_create_problem(const kfbi_config* cfg, const kfbi_levelset* ls, void* cuda_stream,
+                                kfbi_problem** out) {
+  if (!out) return KFBI_ERR_ARG;
+  *out = nullptr;
+  if (!cfg || !ls) return KFBI_ERR_ARG;
+  kfbi_problem* p = new (std::nothrow) kfbi_problem();
+  if (!p) return KFBI_ERR_ARG;
+  p->cfg = *cfg;
+  p->stream = static_cast<cudaStream_t>(cuda_stream);
+  g_create_error.clear();
+  auto bail = [&](kfbi_status s) {
+    g_create_error = p->err;
+    kfbi_destroy_problem(p);
+    return s;
+  };
+  if (cfg->dim != 2 && cfg->dim != 3) {
+    fail(p, KFBI_ERR_ARG, "dim must be 2 or 3");
+    return bail(KFBI_ERR_ARG);
+  }
+  if (cfg->order != 2 && cfg->order != 4) {
+    fail(p, KFBI_ERR_ARG, "order must be 2 or 4");
+    return bail(KFBI_ERR_ARG);
+  }
+  if (!(cfg->hi > cfg->lo) || cfg->n < 8 || (cfg->n & (cfg->n - 1)) != 0) {
+    fail(p, KFBI_ERR_ARG, "need hi > lo and N a power of two >= 8");
+    return bail(KFBI_ERR_ARG);
+  }
+  if (cfg->kind != KFBI_DIRICHLET_INTERIOR && cfg->kind != KFBI_INTERFACE_MU) {
+    fail(p, KFBI_ERR_ARG, "unknown problem kind");
+    return bail(KFBI_ERR_ARG);
+  }
+  if (!(cfg->sigma_in > 0) || (cfg->kind == KFBI_INTERFACE_MU && !(cfg->sigma_out > 0)) ||
+      !(cfg->kappa >= 0)) {
+    fail(p, KFBI_ERR_ARG, "need sigma > 0 and kappa >= 0");
+    return bail(KFBI_ERR_ARG);
+  }
+  if (cfg->box_solver != KFBI_BOX_DST && cfg->box_solver != KFBI_BOX_MG) {
+    fail(p, KFBI_ERR_ARG, "unknown box solver");
+    return bail(KFBI_ERR_ARG);
+  }
+  if (ls->n_params < 0 || ls->n_params > KFBI_LS_MAX_PARAMS || ls->kind < 1 || ls->kind > 5 ||
+      ((ls->kind == KFBI_LS_ELLIPSE || ls->kind == KFBI_LS_STAR) != (cfg->dim == 2))) {
+    fail(p, KFBI_ERR_ARG, "level-set kind does not match the dimension");
+    return bail(KFBI_ERR_ARG);
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    fail(p, KFBI_ERR_CUDA, "no CUDA device");
+    return bail(KFBI_ERR_CUDA);
+  }
+  p->g.d = cfg->dim;
+  p->g.n = cfg->n;
+  p->g.lo = cfg->lo;
+  p->g.h = (cfg->hi - cfg->lo) / cfg->n;
+  p->ls.kind = ls->kind;
+  p->ls.np = ls->n_params;
+  memcpy(p->ls.p, ls->p, sizeof(p->ls.p));
+  p->kt = cfg->kind == KFBI_DIRICHLET_INTERIOR ? cfg->kappa / cfg->sigma_in : cfg->kappa;
+  p->mu = cfg->kind == KFBI_INTERFACE_MU
+              ? (cfg->sigma_out - cfg->sigma_in) / (cfg->sigma_out + cfg->sigma_in)
+              : 0.0;
+  p->cos_alpha = cfg->cos_alpha > 0 ? cfg->cos_alpha : (cfg->dim == 2 ? 0.707 : 0.4);
+  const double h = p->g.h, ih2 = 1.0 / (h * h), k = p->kt;
+  if (cfg->order == 2) {
+    p->stencil_c[0] = -2.0 * cfg->dim * ih2 - k;
+    p->stencil_c[1] = ih2;
+    p->stencil_c[2] = p->stencil_c[3] = 0.0;
+  } else if (cfg->dim == 2) {
+    p->stencil_c[0] = -10.0 / 3.0 * ih2 - 2.0 / 3.0 * k;
+    p->stencil_c[1] = 2.0 / 3.0 * ih2 - k / 12.0;
+    p->stencil_c[2] = 1.0 / 6.0 * ih2;
+    p->stencil_c[3] = 0.0;
+  } else {
+    p->stencil_c[0] = -25.0 / 6.0 * ih2 - 0.5 * k;
+    p->stencil_c[1] = 5.0 / 12.0 * ih2 - k / 12.0;
+    p->stencil_c[2] = 1.0 / 8.0 * ih2;
+    p->stencil_c[3] = 1.0 / 48.0 * ih2;
+  }
+  kfbi_status s = build_geometry(p);
+  if (s != KFBI_OK) return bail(s);
+  if ((s = upload_neighbour_tables(p)) != KFBI_OK) return bail(s);
+  if (dalloc(&p->stencil_dev, 4) != cudaSuccess ||
+      cudaMemcpy(p->stencil_dev, p->stencil_c, sizeof(p->stencil_c), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    fail(p, KFBI_ERR_CUDA, "stencil upload failed");
+    return bail(KFBI_ERR_CUDA);
+  }
+  if ((s = box_create(p)) != KFBI_OK) return bail(s);
+  const long long nodes = p->g.nodes();
+  if (dalloc(&p->cvals, p->nirr) != cudaSuccess || dalloc(&p->rhs, nodes) != cudaSuccess ||
+      dalloc(&p->ugrid, nodes) != cudaSuccess || dalloc(&p->tvals, p->nb) != cudaSuccess ||
+      dalloc(&p->bvec, p->nb) != cudaSuccess || dalloc(&p->xbuf, p->nb) != cudaSuccess ||
+      dalloc(&p->ybuf, p->nb) != cudaSuccess) {
+    fail(p, KFBI_ERR_CUDA, "out of device memory");
+    return bail(KFBI_ERR_CUDA);
+  }
+  if ((s = gmres_create(p, 100)) != KFBI_OK) return bail(s);
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) {
+    fail(p, KFBI_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+    return bail(KFBI_ERR_CUDA);
+  }
+  *out = p;
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_destroy_problem(kfbi_problem* p) {
+  if (!p) return KFBI_OK;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  gmres_destroy(p);
+  box_destroy(p);
+  if (p->op_exec) cudaGraphExecDestroy(p->op_exec);
+  if (p->op_graph) cudaGraphDestroy(p->op_graph);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->xbuf) cudaFree(p->xbuf);
+  if (p->ybuf) cudaFree(p->ybuf);
+  void* bufs[] = {p->inside, p->irr_flag, p->family, p->edge, p->axis, p->st_axis, p->pde_node,
+                  p->dir_idx, p->neu_idx, p->minv, p->irr_lin, p->irr_owner, p->irr_inside,
+                  p->irr_w, p->corr_nb, p->nb_off, p->nb_coef, p->cvals, p->coef, p->rhs,
+                  p->ugrid, p->tvals, p->ftilde, p->bvec, p->zero_nb, p->d_flags, p->stencil_dev};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  for (int k = 0; k < 3; ++k) {
+    if (p->x[k]) cudaFree(p->x[k]);
+    if (p->nrm[k]) cudaFree(p->nrm[k]);
+    if (p->line_start[k]) cudaFree(p->line_start[k]);
+  }
+  // trace CSRs: the per-side arrays point into one allocation made for side 0
+  if (p->tr[0].node) {
+    cudaFree(p->tr[0].node);
+    cudaFree(p->tr[0].irr);
+    cudaFree(p->tr[0].wv);
+    cudaFree(p->tr[0].wn);
+    cudaFree(p->tr[0].w);
+  }
+  for (int s = 0; s < 2; ++s)
+    if (p->tr[s].ptr) cudaFree(p->tr[s].ptr);
+  for (cudaEvent_t e : p->prof.pool) cudaEventDestroy(e);
+  delete p;
+  return KFBI_OK;
+}
+
+const char* kfbi_last_error(const kfbi_problem* p) {
+  if (!p) return g_create_error.c_str();
+  return p->err.c_str();
+}
+
+kfbi_status kfbi_sizes(const kfbi_problem* p, int* n_b, int* n_irr, int* n_coef) {
+  if (!p) return KFBI_ERR_ARG;
+  if (n_b) *n_b = p->nb;
+  if (n_irr) *n_irr = p->nirr;
+  if (n_coef) *n_coef = p->ncoef;
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_num_dofs(const kfbi_problem* p, int* n_b) {
+  if (!p || !n_b) return KFBI_ERR_ARG;
+  *n_b = p->nb;
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_stencil_sizes(const kfbi_problem* p, int* n_pde, int* n_dir, int* n_neu) {
+  if (!p) return KFBI_ERR_ARG;
+  if (n_pde) *n_pde = p->npde;
+  if (n_dir) *n_dir = p->ndir;
+  if (n_neu) *n_neu = p->nneu;
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_dof_points(const kfbi_problem* pc, double* xyz, double* normals) {
+  kfbi_problem* p = const_cast<kfbi_problem*>(pc);
+  if (!p) return KFBI_ERR_ARG;
+  const int d = p->g.d;
+  for (int k = 0; k < d; ++k) {
+    if (xyz)
+      KFBI_CUDA(p, cudaMemcpy2DAsync(xyz + k, sizeof(double) * d, p->x[k], sizeof(double),
+                                     sizeof(double), p->nb, cudaMemcpyDeviceToDevice, p->stream));
+    if (normals)
+      KFBI_CUDA(p, cudaMemcpy2DAsync(normals + k, sizeof(double) * d, p->nrm[k], sizeof(double),
+                                     sizeof(double), p->nb, cudaMemcpyDeviceToDevice, p->stream));
+  }
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_dof_info(const kfbi_problem* pc, int32_t* family, int32_t* axis,
+                          int32_t* stencil_axis) {
+  kfbi_problem* p = const_cast<kfbi_problem*>(pc);
+  if (!p) return KFBI_ERR_ARG;
+  size_t bytes = sizeof(int32_t) * p->nb;
+  if (family) KFBI_CUDA(p, cudaMemcpyAsync(family, p->family, bytes, cudaMemcpyDeviceToDevice, p->stream));
+  if (axis) KFBI_CUDA(p, cudaMemcpyAsync(axis, p->axis, bytes, cudaMemcpyDeviceToDevice, p->stream));
+  if (stencil_axis)
+    KFBI_CUDA(p, cudaMemcpyAsync(stencil_axis, p->st_axis, bytes, cudaMemcpyDeviceToDevice, p->stream));
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_collocation_stencils(const kfbi_problem* pc, int32_t* pde_nodes, int32_t* dir_dofs,
+                                      int32_t* neu_dofs) {
+  kfbi_problem* p = const_cast<kfbi_problem*>(pc);
+  if (!p) return KFBI_ERR_ARG;
+  const size_t nb = p->nb;
+  if (pde_nodes)
+    KFBI_CUDA(p, cudaMemcpyAsync(pde_nodes, p->pde_node, sizeof(int32_t) * nb * p->npde,
+                                 cudaMemcpyDeviceToDevice, p->stream));
+  if (dir_dofs)
+    KFBI_CUDA(p, cudaMemcpyAsync(dir_dofs, p->dir_idx, sizeof(int32_t) * nb * p->ndir,
+                                 cudaMemcpyDeviceToDevice, p->stream));
+  if (neu_dofs)
+    KFBI_CUDA(p, cudaMemcpyAsync(neu_dofs, p->neu_idx, sizeof(int32_t) * nb * p->nneu,
+                                 cudaMemcpyDeviceToDevice, p->stream));
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_inside_mask(const kfbi_problem* pc, uint8_t* mask) {
+  kfbi_problem* p = const_cast<kfbi_problem*>(pc);
+  if (!p || !mask) return KFBI_ERR_ARG;
+  KFBI_CUDA(p, cudaMemcpyAsync(mask, p->inside, p->g.nodes(), cudaMemcpyDeviceToDevice, p->stream));
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_irregular_nodes(const kfbi_problem* pc, int32_t* lin_index, int32_t* owner) {
+  kfbi_problem* p = const_cast<kfbi_problem*>(pc);
+  if (!p) return KFBI_ERR_ARG;
+  size_t bytes = sizeof(int32_t) * p->nirr;
+  if (lin_index) KFBI_CUDA(p, cudaMemcpyAsync(lin_index, p->irr_lin, bytes, cudaMemcpyDeviceToDevice, p->stream));
+  if (owner) KFBI_CUDA(p, cudaMemcpyAsync(owner, p->irr_owner, bytes, cudaMemcpyDeviceToDevice, p->stream));
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_collocation_fit(kfbi_problem* p, const double* a, const double* b,
+                                 const double* ftilde, double* coef) {
+  if (!p || !coef) return KFBI_ERR_ARG;
+  return launch_collocation_fit(p, a, b, ftilde, coef);
+}
+
+kfbi_status kfbi_correction_values(kfbi_problem* p, const double* a, const double* b,
+                                   const double* ftilde, double* cvals) {
+  if (!p || !cvals) return KFBI_ERR_ARG;
+  return launch_correction_values(p, a, b, ftilde, cvals);
+}
+
+kfbi_status kfbi_corrected_rhs(kfbi_problem* p, const double* cvals, const kfbi_data* data,
+                               double* rhs) {
+  if (!p || !rhs) return KFBI_ERR_ARG;
+  return launch_rhs(p, cvals, data, rhs);
+}
+
+kfbi_status kfbi_box_solve(kfbi_problem* p, const double* rhs, double* u) {
+  if (!p || !rhs || !u) return KFBI_ERR_ARG;
+  return box_solve(p, rhs, u);
+}
+
+kfbi_status kfbi_traces(kfbi_problem* p, const double* u, const double* cvals, double* val_plus,
+                        double* val_minus, double* dn_plus, double* dn_minus) {
+  if (!p || !u || !cvals) return KFBI_ERR_ARG;
+  return launch_traces(p, u, cvals, val_plus, val_minus, dn_plus, dn_minus);
+}
+
+kfbi_status kfbi_apply_operator(kfbi_problem* p, const double* x, double* y) {
+  if (!p || !x || !y) return KFBI_ERR_ARG;
+  return apply_operator_fast(p, x, y);
+}
+
+kfbi_status kfbi_bie_rhs(kfbi_problem* p, const kfbi_data* data, double* b) {
+  if (!p || !data || !b || !data->g1) return KFBI_ERR_ARG;
+  if (p->cfg.kind == KFBI_INTERFACE_MU && !data->g2) return KFBI_ERR_ARG;
+  return bie_rhs_impl(p, data, b);
+}
+
+kfbi_status kfbi_gmres_solve(kfbi_problem* p, const kfbi_data* data, const kfbi_gmres_opts* opts,
+                             double* density, kfbi_gmres_info* info) {
+  if (!p || !data || !opts || !density || !data->g1) return KFBI_ERR_ARG;
+  if (p->cfg.kind == KFBI_INTERFACE_MU && !data->g2) return KFBI_ERR_ARG;
+  if (!(opts->rtol > 0) || opts->max_iter < 1) return fail(p, KFBI_ERR_ARG, "need rtol > 0, max_iter >= 1");
+  auto t0 = std::chrono::steady_clock::now();
+  KFBI_TRY(bie_rhs_impl(p, data, p->bvec));
+  KFBI_CUDA(p, cudaStreamSynchronize(p->stream));
+  auto t1 = std::chrono::steady_clock::now();
+  int it = 0;
+  double rel = 0.0;
+  kfbi_status s = gmres_run(p, p->bvec, opts->x0, opts->rtol, opts->restart > 0 ? opts->restart : 100,
+                            opts->max_iter, density, &it, &rel);
+  auto t2 = std::chrono::steady_clock::now();
+  if (info) {
+    info->iters = it;
+    info->rel_res = rel;
+    for (double& v : info->t_ms) v = 0.0;
+    info->t_ms[0] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    info->t_ms[1] = std::chrono::duration<double, std::milli>(t2 - t1).count();
+    info->t_ms[2] = std::chrono::duration<double, std::milli>(t2 - t0).count();
+  }
+  return s;
+}
+
+kfbi_status kfbi_evaluate(kfbi_problem* p, const kfbi_data* data, const double* density,
+                          double* u_grid) {
+  if (!p || !density || !u_grid) return KFBI_ERR_ARG;
+  if (p->cfg.kind == KFBI_DIRICHLET_INTERIOR)
+    return potential_with_data(p, density, nullptr, data, false, u_grid);
+  if (!data || !data->g1) return fail(p, KFBI_ERR_ARG, "interface evaluate needs data->g1");
+  return potential_with_data(p, data->g1, density, data, true, u_grid);
+}
+
+}  // extern "C"
+
+namespace kfbi {
+
+Launch::Launch(kfbi_problem* pp, int c) : p(pp), cls(c) {
+  p->prof.launches[c]++;
+  if (!p->prof.on) return;
+  Profiler& P = p->prof;
+  if (P.used + 2 > P.pool.size()) {
+    for (int k = 0; k < 64; ++k) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      P.pool.push_back(e);
+    }
+  }
+  rec = (int)(P.used / 2);
+  P.used += 2;
+  P.cls.push_back(c);
+  cudaEventRecord(P.pool[2 * rec], p->stream);
+}
+
+Launch::~Launch() {
+  if (rec >= 0) cudaEventRecord(p->prof.pool[2 * rec + 1], p->stream);
+}
+
+}  // namespace kfbi
+
+extern "C" {
+
+kfbi_status kfbi_launch_counts(kfbi_problem* p, int64_t* counts, int reset) {
+  if (!p || !counts) return KFBI_ERR_ARG;
+  for (int c = 0; c < KFBI_KC_COUNT; ++c) counts[c] = p->prof.launches[c];
+  if (reset)
+    for (int c = 0; c < KFBI_KC_COUNT; ++c) p->prof.launches[c] = 0;
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_profile_enable(kfbi_problem* p, int enable) {
+  if (!p) return KFBI_ERR_ARG;
+  KFBI_CUDA(p, cudaStreamSynchronize(p->stream));
+  p->prof.on = enable != 0;
+  p->prof.used = 0;
+  p->prof.cls.clear();
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_profile_read(kfbi_problem* p, double* ms, int64_t* timed) {
+  if (!p || !ms || !timed) return KFBI_ERR_ARG;
+  KFBI_CUDA(p, cudaStreamSynchronize(p->stream));
+  for (int c = 0; c < KFBI_KC_COUNT; ++c) {
+    ms[c] = 0.0;
+    timed[c] = 0;
+  }
+  Profiler& P = p->prof;
+  for (size_t r = 0; r < P.cls.size(); ++r) {
+    float t = 0.f;
+    KFBI_CUDA(p, cudaEventElapsedTime(&t, P.pool[2 * r], P.pool[2 * r + 1]));
+    ms[P.cls[r]] += t;
+    timed[P.cls[r]] += 1;
+  }
+  return KFBI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,362 @@
+// Matrix-free GMRES on the device (Algorithm 1, Step 4): Arnoldi with
+// classical Gram-Schmidt applied twice (CGS2: two block-parallel projections
+// instead of j sequential ones), Givens rotations of the Hessenberg column on
+// the device, restarts after `restart` steps.  Reductions are two-level and in
+// a fixed order, so results are reproducible run to run.  The only host
+// transfer per iteration is the residual estimate |g_{j+1}| (8 bytes).
+#include <cmath>
+#include <vector>
+
+#include "kfbi_internal.cuh"
+
+namespace kfbi {
+
+kfbi_status apply_operator_impl(kfbi_problem* p, const double* x, double* y);
+
+namespace {
+
+constexpr int kDotThreads = 256;
+
+// part[i * nchunk + c] = partial dot of V_i and w over chunk c
+__global__ void k_dots(const double* __restrict__ V, int nb, int count,
+                       const double* __restrict__ w, int nchunk, double* __restrict__ part) {
+  const int i = blockIdx.y;
+  const int c = blockIdx.x;
+  const int per = (nb + nchunk - 1) / nchunk;
+  const int b = c * per, e = min(nb, b + per);
+  const double* v = V + (size_t)i * nb;
+  double s = 0.0;
+  for (int k = b + threadIdx.x; k < e; k += blockDim.x) s += v[k] * w[k];
+  s = warp_sum(s);
+  __shared__ double ws[kDotThreads / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < kDotThreads / 32 ? ws[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) part[(size_t)i * nchunk + c] = t;
+  }
+}
+
+// out[i] = (accumulate ? out[i] : 0) + sum_c part[i * nchunk + c], one block per i
+__global__ void k_reduce(const double* __restrict__ part, int nchunk, double* __restrict__ out,
+                         int accumulate) {
+  const int i = blockIdx.x;
+  double s = 0.0;
+  for (int c = threadIdx.x; c < nchunk; c += blockDim.x) s += part[(size_t)i * nchunk + c];
+  s = warp_sum(s);
+  __shared__ double ws[kDotThreads / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < kDotThreads / 32 ? ws[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) out[i] = accumulate ? out[i] + t : t;
+  }
+}
+
+// w -= sum_{i<count} h[i] V_i
+__global__ void k_project(const double* __restrict__ V, int nb, int count,
+                          const double* __restrict__ h, double* __restrict__ w) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    double s = w[k];
+    for (int i = 0; i < count; ++i) s -= h[i] * V[(size_t)i * nb + k];
+    w[k] = s;
+  }
+}
+
+__global__ void k_scale(double* __restrict__ w, int nb, const double* __restrict__ s, int invert) {
+  double f = invert ? 1.0 / s[0] : s[0];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x)
+    w[k] = w[k] * f;
+}
+
+__global__ void k_sub(const double* __restrict__ b, double* __restrict__ w, int nb) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x)
+    w[k] = b[k] - w[k];
+}
+
+__global__ void k_sqrt(double* s) { s[0] = sqrt(s[0]); }
+
+__global__ void k_add(double* __restrict__ a, const double* __restrict__ b, int k) {
+  for (int i = threadIdx.x; i < k; i += blockDim.x) a[i] += b[i];
+}
+
+// Hessenberg column j: H[0..j] = h1 + h2, H[j+1] = sqrt(nn); Givens update; res = |g[j+1]|
+__global__ void k_givens(double* __restrict__ H, int ld, int j, const double* __restrict__ h1,
+                         const double* __restrict__ hn2, double* __restrict__ cs,
+                         double* __restrict__ sn, double* __restrict__ g, double* __restrict__ res,
+                         double* __restrict__ hnorm) {
+  double* col = H + (size_t)j * ld;
+  for (int i = 0; i <= j; ++i) col[i] = h1[i];
+  double hn = sqrt(hn2[0]);
+  col[j + 1] = hn;
+  hnorm[0] = hn;
+  for (int i = 0; i < j; ++i) {
+    double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  double rr = hypot(col[j], col[j + 1]);
+  cs[j] = col[j] / rr;
+  sn[j] = col[j + 1] / rr;
+  col[j] = rr;
+  col[j + 1] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  res[0] = fabs(g[j + 1]);
+}
+
+__global__ void k_init_g(double* g, int m, const double* beta) {
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = (i == 0) ? beta[0] : 0.0;
+}
+
+// upper-triangular solve H y = g (k x k)
+__global__ void k_solve_y(const double* __restrict__ H, int ld, int k, const double* __restrict__ g,
+                          double* __restrict__ y) {
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int j = i + 1; j < k; ++j) s -= H[(size_t)j * ld + i] * y[j];
+    y[i] = s / H[(size_t)i * ld + i];
+  }
+}
+
+// x += sum_{i<k} y[i] V_i
+__global__ void k_update_x(const double* __restrict__ V, int nb, int k, const double* __restrict__ y,
+                           double* __restrict__ x) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nb; e += gridDim.x * blockDim.x) {
+    double s = x[e];
+    for (int i = 0; i < k; ++i) s += y[i] * V[(size_t)i * nb + e];
+    x[e] = s;
+  }
+}
+
+// One Arnoldi step in one CTA (N_b moderate): w = V_{j+1} holds A v_j on entry.
+// CGS2 projections, norm, normalisation and the Givens update of column j.
+constexpr int kArnThreads = 1024;
+__global__ void __launch_bounds__(kArnThreads) k_arnoldi_small(
+    double* __restrict__ V, int nb, int j, double* __restrict__ H, int ld,
+    double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
+    double* __restrict__ res) {
+  extern __shared__ double sm[];
+  const int nw = kArnThreads / 32;
+  double* part = sm;                       // (j+2) x nw
+  double* h = part + (size_t)(j + 2) * nw; // j+2
+  double* hacc = h + (j + 2);              // j+2
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* w = V + (size_t)(j + 1) * nb;
+  for (int i = tid; i <= j + 1; i += kArnThreads) hacc[i] = 0.0;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int i = 0; i <= j; ++i) {
+      const double* v = V + (size_t)i * nb;
+      double s = 0.0;
+      for (int k = tid; k < nb; k += kArnThreads) s += v[k] * w[k];
+      s = warp_sum(s);
+      if (lane == 0) part[i * nw + warp] = s;
+    }
+    __syncthreads();
+    for (int i = tid; i <= j; i += kArnThreads) {
+      double s = 0.0;
+      for (int q = 0; q < nw; ++q) s += part[i * nw + q];
+      h[i] = s;
+      hacc[i] += s;
+    }
+    __syncthreads();
+    for (int k = tid; k < nb; k += kArnThreads) {
+      double s = w[k];
+      for (int i = 0; i <= j; ++i) s -= h[i] * V[(size_t)i * nb + k];
+      w[k] = s;
+    }
+    __syncthreads();
+  }
+  double s = 0.0;
+  for (int k = tid; k < nb; k += kArnThreads) s += w[k] * w[k];
+  s = warp_sum(s);
+  if (lane == 0) part[warp] = s;
+  __syncthreads();
+  if (tid == 0) {
+    double nn = 0.0;
+    for (int q = 0; q < nw; ++q) nn += part[q];
+    double hn = sqrt(nn);
+    double* col = H + (size_t)j * ld;
+    for (int i = 0; i <= j; ++i) col[i] = hacc[i];
+    col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+      double t = cs[i] * col[i] + sn[i] * col[i + 1];
+      col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+      col[i] = t;
+    }
+    double rr = hypot(col[j], col[j + 1]);
+    cs[j] = col[j] / rr;
+    sn[j] = col[j + 1] / rr;
+    col[j] = rr;
+    col[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    res[0] = fabs(g[j + 1]);
+    h[0] = hn;
+  }
+  __syncthreads();
+  const double inv = 1.0 / h[0];
+  for (int k = tid; k < nb; k += kArnThreads) w[k] *= inv;
+}
+
+}  // namespace
+
+constexpr int kSmallArnoldi = 32768;   // N_b up to which one CTA runs the Arnoldi step
+
+kfbi_status gmres_create(kfbi_problem* p, int m) {
+  Gmres& G = p->gm;
+  G.nb = p->nb;
+  G.m = m;
+  G.nchunk = std::max(1, std::min(1024, div_up(p->nb, 2048)));
+  KFBI_CUDA(p, dalloc(&G.V, (size_t)(m + 1) * p->nb));
+  KFBI_CUDA(p, dalloc(&G.H, (size_t)(m + 1) * m));
+  KFBI_CUDA(p, dalloc(&G.cs, m));
+  KFBI_CUDA(p, dalloc(&G.sn, m));
+  KFBI_CUDA(p, dalloc(&G.g, m + 1));
+  KFBI_CUDA(p, dalloc(&G.y, m));
+  KFBI_CUDA(p, dalloc(&G.part, (size_t)(m + 1) * G.nchunk));
+  KFBI_CUDA(p, dalloc(&G.scal, 8));
+  KFBI_CUDA(p, dalloc(&G.hcol, 2 * (m + 1)));
+  KFBI_CUDA(p, cudaMallocHost(reinterpret_cast<void**>(&G.host_res), 4 * sizeof(double)));
+  return KFBI_OK;
+}
+
+void gmres_destroy(kfbi_problem* p) {
+  Gmres& G = p->gm;
+  cudaFree(G.V);
+  cudaFree(G.H);
+  cudaFree(G.cs);
+  cudaFree(G.sn);
+  cudaFree(G.g);
+  cudaFree(G.y);
+  cudaFree(G.part);
+  cudaFree(G.scal);
+  cudaFree(G.hcol);
+  if (G.host_res) cudaFreeHost(G.host_res);
+  G = Gmres();
+}
+
+// ||v||^2 into out[0] (device)
+static kfbi_status dot_self(kfbi_problem* p, const double* v, double* out) {
+  Gmres& G = p->gm;
+  KFBI_LAUNCH(p, KFBI_KC_GMRES, k_dots<<<dim3(G.nchunk, 1), kDotThreads, 0, p->stream>>>(v, G.nb, 1, v, G.nchunk, G.part));
+  KFBI_LAUNCH(p, KFBI_KC_GMRES, k_reduce<<<1, kDotThreads, 0, p->stream>>>(G.part, G.nchunk, out, 0));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+static kfbi_status read_scalar(kfbi_problem* p, const double* dev, double* host) {
+  KFBI_CUDA(p, cudaMemcpyAsync(p->gm.host_res, dev, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  KFBI_CUDA(p, cudaStreamSynchronize(p->stream));
+  *host = p->gm.host_res[0];
+  return KFBI_OK;
+}
+
+kfbi_status gmres_run(kfbi_problem* p, const double* b, const double* x0, double rtol, int restart,
+                      int max_iter, double* x, int* iters, double* rel) {
+  Gmres& G = p->gm;
+  const int nb = G.nb;
+  const int m = std::max(1, std::min(restart, G.m));
+  const int ld = G.m + 1;
+  cudaStream_t st = p->stream;
+  const int eb = std::min(div_up(nb, 256), 152 * 4);
+  double* beta = G.scal + 0;
+  double* bn2 = G.scal + 1;
+  double* res = G.scal + 2;
+  double* hn2 = G.scal + 3;
+  double* hnorm = G.scal + 4;
+  double* h1 = G.hcol;
+  double* h2 = G.hcol + (G.m + 1);
+  KFBI_TRY(dot_self(p, b, bn2));
+  double bnorm2;
+  KFBI_TRY(read_scalar(p, bn2, &bnorm2));
+  const double bnorm = std::sqrt(bnorm2);
+  *iters = 0;
+  *rel = 0.0;
+  if (!std::isfinite(bnorm)) return fail(p, KFBI_ERR_NONFINITE, "non-finite BIE right-hand side");
+  if (bnorm == 0.0) {
+    KFBI_CUDA(p, cudaMemsetAsync(x, 0, sizeof(double) * nb, st));
+    return KFBI_OK;
+  }
+  if (x0) {
+    if (x0 != x) KFBI_CUDA(p, cudaMemcpyAsync(x, x0, sizeof(double) * nb, cudaMemcpyDeviceToDevice, st));
+  } else {
+    KFBI_CUDA(p, cudaMemsetAsync(x, 0, sizeof(double) * nb, st));
+  }
+  bool nonzero_x = x0 != nullptr;
+  int total = 0;
+  for (;;) {
+    double* V0 = G.V;
+    if (nonzero_x) {
+      KFBI_TRY(apply_operator_fast(p, x, V0));
+      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_sub<<<eb, 256, 0, st>>>(b, V0, nb));
+    } else {
+      KFBI_CUDA(p, cudaMemcpyAsync(V0, b, sizeof(double) * nb, cudaMemcpyDeviceToDevice, st));
+    }
+    KFBI_TRY(dot_self(p, V0, beta));
+    KFBI_LAUNCH(p, KFBI_KC_GMRES, k_sqrt<<<1, 1, 0, st>>>(beta));
+    double hbeta;
+    KFBI_TRY(read_scalar(p, beta, &hbeta));
+    if (!std::isfinite(hbeta)) return fail(p, KFBI_ERR_NONFINITE, "non-finite GMRES residual");
+    if (hbeta <= rtol * bnorm) {
+      *iters = total;
+      *rel = hbeta / bnorm;
+      return KFBI_OK;
+    }
+    KFBI_LAUNCH(p, KFBI_KC_GMRES, k_scale<<<eb, 256, 0, st>>>(V0, nb, beta, 1));
+    KFBI_LAUNCH(p, KFBI_KC_GMRES, k_init_g<<<1, 128, 0, st>>>(G.g, G.m, beta));
+    int jend = 0;
+    double hres = hbeta;
+    for (int j = 0; j < m; ++j) {
+      double* Vj = G.V + (size_t)j * nb;
+      double* w = G.V + (size_t)(j + 1) * nb;
+      KFBI_TRY(apply_operator_fast(p, Vj, w));
+      ++total;
+      if (nb <= kSmallArnoldi) {
+        size_t smem = sizeof(double) * ((size_t)(j + 2) * (kArnThreads / 32) + 2 * (size_t)(j + 2));
+        KFBI_LAUNCH(p, KFBI_KC_GMRES, k_arnoldi_small<<<1, kArnThreads, smem, st>>>(
+            G.V, nb, j, G.H, ld, G.cs, G.sn, G.g, res));
+        KFBI_CUDA(p, cudaGetLastError());
+        KFBI_TRY(read_scalar(p, res, &hres));
+        jend = j + 1;
+        if (!std::isfinite(hres)) return fail(p, KFBI_ERR_NONFINITE, "non-finite GMRES residual");
+        if (hres <= rtol * bnorm || total >= max_iter) break;
+        continue;
+      }
+      // CGS2: h1 = V^T w, w -= V h1, h2 = V^T w, w -= V h2
+      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_dots<<<dim3(G.nchunk, j + 1), kDotThreads, 0, st>>>(G.V, nb, j + 1, w, G.nchunk, G.part));
+      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_reduce<<<j + 1, kDotThreads, 0, st>>>(G.part, G.nchunk, h1, 0));
+      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_project<<<eb, 256, 0, st>>>(G.V, nb, j + 1, h1, w));
+      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_dots<<<dim3(G.nchunk, j + 1), kDotThreads, 0, st>>>(G.V, nb, j + 1, w, G.nchunk, G.part));
+      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_reduce<<<j + 1, kDotThreads, 0, st>>>(G.part, G.nchunk, h2, 0));
+      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_project<<<eb, 256, 0, st>>>(G.V, nb, j + 1, h2, w));
+      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_add<<<1, 128, 0, st>>>(h1, h2, j + 1));
+      KFBI_TRY(dot_self(p, w, hn2));
+      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_givens<<<1, 1, 0, st>>>(G.H, ld, j, h1, hn2, G.cs, G.sn, G.g, res, hnorm));
+      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_scale<<<eb, 256, 0, st>>>(w, nb, hnorm, 1));
+      KFBI_CUDA(p, cudaGetLastError());
+      KFBI_TRY(read_scalar(p, res, &hres));
+      jend = j + 1;
+      if (!std::isfinite(hres)) return fail(p, KFBI_ERR_NONFINITE, "non-finite GMRES residual");
+      if (hres <= rtol * bnorm || total >= max_iter) break;
+    }
+    KFBI_LAUNCH(p, KFBI_KC_GMRES, k_solve_y<<<1, 1, 0, st>>>(G.H, ld, jend, G.g, G.y));
+    KFBI_LAUNCH(p, KFBI_KC_GMRES, k_update_x<<<eb, 256, 0, st>>>(G.V, nb, jend, G.y, x));
+    KFBI_CUDA(p, cudaGetLastError());
+    nonzero_x = true;
+    *iters = total;
+    *rel = hres / bnorm;
+    if (hres <= rtol * bnorm) {
+      KFBI_CUDA(p, cudaStreamSynchronize(st));
+      return KFBI_OK;
+    }
+    if (total >= max_iter)
+      return fail(p, KFBI_ERR_NOT_CONVERGED,
+                  "GMRES reached max_iter = " + std::to_string(max_iter) +
+                      " (relative residual " + std::to_string(hres / bnorm) + ")");
+  }
+}
+
+}  // namespace kfbi

@@ -1,0 +1,356 @@
+// Hot-path kernels of one operator application (Algorithm 1, Step 3):
+//   3.1+  correction function C at every irregular node from the collocation
+//         data of its closest primary point (composite rows phi(xi)^T M^{-1},
+//         so the local polynomial of Sec. 5.3.1 is fitted and evaluated in one
+//         pass);
+//   3.2   corrected right-hand side of eq. (corrected-FDS) with the correction
+//         terms of eq. (crc-formula);
+//   3.4   corrected interpolation of the traces (Sec. 5.5), fused with the BIE
+//         combination y = alpha x + beta t.
+// All arithmetic is FP64.
+#include "kfbi_internal.cuh"
+
+namespace kfbi {
+
+namespace {
+
+// C(q) = sum_j W[j][q] Q_j, Q = [h^2 f~(PDE nodes); a(Dirichlet DOFs); h b(Neumann DOFs)]
+// of the owner's collocation system (eq. (cau-ls)).  f~ = fa/sa - fb/sb at the
+// PDE nodes (either pointer may be null).
+__global__ void k_cvals(int nirr, int npde, int ndir, int nneu, double h,
+                        const int32_t* __restrict__ owner, const double* __restrict__ W,
+                        const int32_t* __restrict__ pde_node, const int32_t* __restrict__ dir_idx,
+                        const int32_t* __restrict__ neu_idx, const double* __restrict__ a,
+                        const double* __restrict__ b, const double* __restrict__ fa, double sa,
+                        const double* __restrict__ fb, double sb, double* __restrict__ out) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nirr) return;
+  int i = owner[q];
+  double acc = 0.0;
+  int j = 0;
+  if (fa != nullptr || fb != nullptr) {
+    double h2 = h * h;
+    for (int s = 0; s < npde; ++s, ++j) {
+      int node = pde_node[i * npde + s];
+      double ft = 0.0;
+      if (fa) ft = fa[node] / sa;
+      if (fb) ft = ft - fb[node] / sb;
+      acc += W[(size_t)j * nirr + q] * (h2 * ft);
+    }
+  } else {
+    j = npde;
+  }
+  if (a != nullptr) {
+    for (int s = 0; s < ndir; ++s, ++j) acc += W[(size_t)j * nirr + q] * a[dir_idx[i * ndir + s]];
+  } else {
+    j += ndir;
+  }
+  if (b != nullptr) {
+    for (int s = 0; s < nneu; ++s, ++j)
+      acc += W[(size_t)j * nirr + q] * (h * b[neu_idx[i * nneu + s]]);
+  }
+  out[q] = acc;
+}
+
+// d_i = M_i^{-1} Q_i, one warp per primary point (stage output).
+__global__ void k_coef(int nb, int nc, int npde, int ndir, int nneu, double h,
+                       const double* __restrict__ minv, const int32_t* __restrict__ pde_node,
+                       const int32_t* __restrict__ dir_idx, const int32_t* __restrict__ neu_idx,
+                       const double* __restrict__ a, const double* __restrict__ b,
+                       const double* __restrict__ ft, double* __restrict__ coef) {
+  int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (i >= nb) return;
+  __shared__ double Qs[8][kMaxCoef];
+  double* Q = Qs[threadIdx.x / 32];
+  for (int j = lane; j < nc; j += 32) {
+    double v;
+    if (j < npde) {
+      v = ft ? (h * h) * ft[pde_node[i * npde + j]] : 0.0;
+    } else if (j < npde + ndir) {
+      v = a ? a[dir_idx[i * ndir + (j - npde)]] : 0.0;
+    } else {
+      v = b ? h * b[neu_idx[i * nneu + (j - npde - ndir)]] : 0.0;
+    }
+    Q[j] = v;
+  }
+  __syncwarp();
+  const double* M = minv + (size_t)i * nc * nc;
+  for (int k = lane; k < nc; k += 32) {
+    double s = 0.0;
+    for (int j = 0; j < nc; ++j) s += M[k * nc + j] * Q[j];
+    coef[(size_t)i * nc + k] = s;
+  }
+}
+
+// R = F + h^2/12 Lap F (order 4) from each node's own side, minus the lift of
+// the outer boundary data, at interior nodes; 0 on the boundary layer.
+__global__ void k_rhs_source(Grid g, int order, const uint8_t* __restrict__ inside,
+                             const double* __restrict__ fi, const double* __restrict__ fo,
+                             const double* __restrict__ li, const double* __restrict__ lo_,
+                             double si, double so, const double* __restrict__ gb,
+                             const double* __restrict__ nbc, const int8_t* __restrict__ nboff,
+                             int nnb, double* __restrict__ R) {
+  long long tot = g.nodes();
+  int n1 = g.n + 1;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    int idx[3];
+    long long r = t;
+    if (g.d == 2) {
+      idx[1] = (int)(r % n1);
+      idx[0] = (int)(r / n1);
+      idx[2] = 1;
+    } else {
+      idx[2] = (int)(r % n1);
+      r /= n1;
+      idx[1] = (int)(r % n1);
+      idx[0] = (int)(r / n1);
+    }
+    bool interior = idx[0] >= 1 && idx[0] < g.n && idx[1] >= 1 && idx[1] < g.n &&
+                    (g.d == 2 || (idx[2] >= 1 && idx[2] < g.n));
+    if (!interior) {
+      R[t] = 0.0;
+      continue;
+    }
+    double v = 0.0;
+    bool in = inside[t] != 0;
+    const double* F = in ? fi : fo;
+    const double* Lp = in ? li : lo_;
+    double s = in ? si : so;
+    if (F) v = F[t] / s;
+    if (order == 4 && Lp) v = v + g.h * g.h / 12.0 * (Lp[t] / s);
+    if (gb) {
+      bool near = idx[0] == 1 || idx[0] == g.n - 1 || idx[1] == 1 || idx[1] == g.n - 1 ||
+                  (g.d == 3 && (idx[2] == 1 || idx[2] == g.n - 1));
+      if (near) {
+        double lift = 0.0;
+        for (int k = 0; k < nnb; ++k) {
+          int q0 = idx[0] + nboff[3 * k], q1 = idx[1] + nboff[3 * k + 1];
+          int q2 = g.d == 3 ? idx[2] + nboff[3 * k + 2] : 0;
+          bool bnd = q0 == 0 || q0 == g.n || q1 == 0 || q1 == g.n ||
+                     (g.d == 3 && (q2 == 0 || q2 == g.n));
+          if (!bnd) continue;
+          long long qi = g.d == 2 ? (long long)q0 * n1 + q1 : ((long long)q0 * n1 + q1) * n1 + q2;
+          lift += nbc[k] * gb[qi];
+        }
+        v = v - lift;
+      }
+    }
+    R[t] = v;
+  }
+}
+
+// R[P] += C_P (eq. (crc-formula)): -sum c C(Q) over outside Q if P is inside,
+// +sum c C(Q) over inside Q if P is outside.
+__global__ void k_rhs_correct(int nirr, int nnb, const int32_t* __restrict__ lin,
+                              const uint8_t* __restrict__ irr_inside,
+                              const int32_t* __restrict__ corr_nb, const double* __restrict__ nbc,
+                              const double* __restrict__ cv, double* __restrict__ R, int add) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nirr) return;
+  double acc = 0.0;
+  for (int s = 0; s < nnb; ++s) {
+    int j = corr_nb[(size_t)s * nirr + q];
+    if (j >= 0) acc += nbc[s] * cv[j];
+  }
+  double c = irr_inside[q] ? -acc : acc;
+  long long t = lin[q];
+  R[t] = add ? R[t] + c : c;
+}
+
+// Four one-sided traces (stage output), one warp per DOF.
+__global__ void k_traces4(int nb, TraceCSR tp, TraceCSR tm, const double* __restrict__ u,
+                          const double* __restrict__ cv, double* vp, double* vm, double* dp,
+                          double* dm) {
+  int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (i >= nb) return;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int side = 0; side < 2; ++side) {
+    const TraceCSR& T = side == 0 ? tp : tm;
+    double sg = side == 0 ? 1.0 : -1.0;
+    double a = 0.0, b = 0.0;
+    for (int e = T.ptr[i] + lane; e < T.ptr[i + 1]; e += 32) {
+      double w = u[T.node[e]];
+      int j = T.irr[e];
+      if (j >= 0) w += sg * cv[j];
+      a += T.wv[e] * w;
+      b += T.wn[e] * w;
+    }
+    s[2 * side] = warp_sum(a);
+    s[2 * side + 1] = warp_sum(b);
+  }
+  if (lane == 0) {
+    if (vp) vp[i] = s[0];
+    if (dp) dp[i] = s[1];
+    if (vm) vm[i] = s[2];
+    if (dm) dm[i] = s[3];
+  }
+}
+
+// The operator's trace quantity t (average value for the Dirichlet form,
+// average normal derivative for the mu-form; weights carry the 1/2) fused with
+// the BIE combination y = alpha x + beta t.
+__global__ void k_trace_op(int nb, TraceCSR tp, TraceCSR tm, const double* __restrict__ u,
+                           const double* __restrict__ cv, const double* __restrict__ x,
+                           double alpha, double beta, double* __restrict__ y) {
+  int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (i >= nb) return;
+  double acc = 0.0;
+  for (int e = tp.ptr[i] + lane; e < tp.ptr[i + 1]; e += 32) {
+    double w = u[tp.node[e]];
+    int j = tp.irr[e];
+    if (j >= 0) w += cv[j];
+    acc += tp.w[e] * w;
+  }
+  for (int e = tm.ptr[i] + lane; e < tm.ptr[i + 1]; e += 32) {
+    double w = u[tm.node[e]];
+    int j = tm.irr[e];
+    if (j >= 0) w -= cv[j];
+    acc += tm.w[e] * w;
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) y[i] = (x ? alpha * x[i] : 0.0) + beta * acc;
+}
+
+__global__ void k_set_boundary(Grid g, const double* __restrict__ gb, double* __restrict__ u) {
+  long long tot = g.nodes();
+  int n1 = g.n + 1;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long r = t;
+    int i2 = 1, i1, i0;
+    if (g.d == 2) {
+      i1 = (int)(r % n1);
+      i0 = (int)(r / n1);
+    } else {
+      i2 = (int)(r % n1);
+      r /= n1;
+      i1 = (int)(r % n1);
+      i0 = (int)(r / n1);
+    }
+    bool bnd = i0 == 0 || i0 == g.n || i1 == 0 || i1 == g.n ||
+               (g.d == 3 && (i2 == 0 || i2 == g.n));
+    if (bnd) u[t] = gb ? gb[t] : 0.0;
+  }
+}
+
+}  // namespace
+
+kfbi_status launch_correction_values(kfbi_problem* p, const double* a, const double* b,
+                                     const double* ftilde, double* cvals) {
+  KFBI_LAUNCH(p, KFBI_KC_CORRECTION, k_cvals<<<div_up(p->nirr, 128), 128, 0, p->stream>>>(
+      p->nirr, p->npde, p->ndir, p->nneu, p->g.h, p->irr_owner, p->irr_w, p->pde_node,
+      p->dir_idx, p->neu_idx, a, b, ftilde, 1.0, nullptr, 1.0, cvals));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+// C values from the physical data (f~ = f_in/sigma_in - f_out/sigma_out).
+kfbi_status launch_correction_values_data(kfbi_problem* p, const double* a, const double* b,
+                                          const kfbi_data* data, double* cvals) {
+  const double* fi = data ? data->f_in : nullptr;
+  const double* fo = data ? data->f_out : nullptr;
+  double so = p->cfg.kind == KFBI_DIRICHLET_INTERIOR ? 1.0 : p->cfg.sigma_out;
+  if (p->cfg.kind == KFBI_DIRICHLET_INTERIOR) fo = nullptr;
+  KFBI_LAUNCH(p, KFBI_KC_CORRECTION, k_cvals<<<div_up(p->nirr, 128), 128, 0, p->stream>>>(
+      p->nirr, p->npde, p->ndir, p->nneu, p->g.h, p->irr_owner, p->irr_w, p->pde_node,
+      p->dir_idx, p->neu_idx, a, b, fi, p->cfg.sigma_in, fo, so, cvals));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status launch_collocation_fit(kfbi_problem* p, const double* a, const double* b,
+                                   const double* ftilde, double* coef) {
+  KFBI_LAUNCH(p, KFBI_KC_CORRECTION, k_coef<<<div_up(p->nb, 8), 256, 0, p->stream>>>(p->nb, p->ncoef, p->npde, p->ndir, p->nneu,
+                                                   p->g.h, p->minv, p->pde_node, p->dir_idx,
+                                                   p->neu_idx, a, b, ftilde, coef));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+// Neighbour coefficients in the enumeration order of the setup (a, b[, c] in
+// {-1,0,1}, last fastest, centre skipped; star only for order 2).
+static void neighbour_table(kfbi_problem* p, std::vector<double>* coef, std::vector<int8_t>* off) {
+  const int d = p->g.d;
+  coef->clear();
+  off->clear();
+  for (int a = -1; a <= 1; ++a)
+    for (int b = -1; b <= 1; ++b)
+      for (int e = (d == 3 ? -1 : 0); e <= (d == 3 ? 1 : 0); ++e) {
+        int nz = (a != 0) + (b != 0) + (e != 0);
+        if (nz == 0) continue;
+        if (p->cfg.order == 2 && nz > 1) continue;
+        coef->push_back(p->stencil_c[nz]);
+        off->push_back((int8_t)a);
+        off->push_back((int8_t)b);
+        off->push_back((int8_t)e);
+      }
+}
+
+kfbi_status launch_rhs(kfbi_problem* p, const double* cvals, const kfbi_data* data,
+                       double* rhs) {
+  const Grid g = p->g;
+  const double* d_nbc = p->nb_coef;
+  const int8_t* d_off = p->nb_off;
+  const bool src = data && (data->f_in || data->f_out || data->lapf_in || data->lapf_out);
+  const bool gb = data && data->g_b;
+  if (src || gb) {
+    const double* fi = data->f_in;
+    const double* fo = p->cfg.kind == KFBI_DIRICHLET_INTERIOR ? nullptr : data->f_out;
+    const double* li = data->lapf_in;
+    const double* lo_ = p->cfg.kind == KFBI_DIRICHLET_INTERIOR ? nullptr : data->lapf_out;
+    double so = p->cfg.kind == KFBI_DIRICHLET_INTERIOR ? 1.0 : p->cfg.sigma_out;
+    KFBI_LAUNCH(p, KFBI_KC_RHS, k_rhs_source<<<std::min(div_up(g.nodes(), 256), 152 * 32), 256, 0, p->stream>>>(
+        g, p->cfg.order, p->inside, fi, fo, li, lo_, p->cfg.sigma_in, so,
+        p->cfg.kind == KFBI_DIRICHLET_INTERIOR ? nullptr : data->g_b, d_nbc, d_off, p->n_nb, rhs));
+    KFBI_CUDA(p, cudaGetLastError());
+  } else {
+    KFBI_CUDA(p, cudaMemsetAsync(rhs, 0, sizeof(double) * g.nodes(), p->stream));
+  }
+  if (cvals) {
+    KFBI_LAUNCH(p, KFBI_KC_RHS, k_rhs_correct<<<div_up(p->nirr, 128), 128, 0, p->stream>>>(
+        p->nirr, p->n_nb, p->irr_lin, p->irr_inside, p->corr_nb, d_nbc, cvals, rhs, 1));
+    KFBI_CUDA(p, cudaGetLastError());
+  }
+  return KFBI_OK;
+}
+
+kfbi_status launch_traces(kfbi_problem* p, const double* u, const double* cvals, double* vp,
+                          double* vm, double* dp, double* dm) {
+  KFBI_LAUNCH(p, KFBI_KC_TRACE, k_traces4<<<div_up(p->nb, 8), 256, 0, p->stream>>>(p->nb, p->tr[0], p->tr[1], u, cvals, vp, vm,
+                                                      dp, dm));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status launch_operator_trace(kfbi_problem* p, const double* u, const double* cvals,
+                                  const double* x, double alpha_x, double beta_t, double* y) {
+  KFBI_LAUNCH(p, KFBI_KC_TRACE, k_trace_op<<<div_up(p->nb, 8), 256, 0, p->stream>>>(p->nb, p->tr[0], p->tr[1], u, cvals, x,
+                                                       alpha_x, beta_t, y));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status launch_set_boundary(kfbi_problem* p, double* u, const double* g_b) {
+  KFBI_LAUNCH(p, KFBI_KC_OTHER, k_set_boundary<<<std::min(div_up(p->g.nodes(), 256), 152 * 32), 256, 0, p->stream>>>(p->g, g_b, u));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status upload_neighbour_tables(kfbi_problem* p) {
+  std::vector<double> c;
+  std::vector<int8_t> o;
+  neighbour_table(p, &c, &o);
+  KFBI_CUDA(p, dalloc(&p->nb_coef, c.size()));
+  KFBI_CUDA(p, dalloc(&p->nb_off, o.size()));
+  KFBI_CUDA(p, cudaMemcpyAsync(p->nb_coef, c.data(), sizeof(double) * c.size(),
+                               cudaMemcpyHostToDevice, p->stream));
+  KFBI_CUDA(p, cudaMemcpyAsync(p->nb_off, o.data(), o.size(), cudaMemcpyHostToDevice, p->stream));
+  KFBI_CUDA(p, cudaStreamSynchronize(p->stream));
+  return KFBI_OK;
+}
+
+}  // namespace kfbi

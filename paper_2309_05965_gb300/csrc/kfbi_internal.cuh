@@ -1,0 +1,260 @@
+// Internal declarations of the GB300 KFBI library: the problem object, device
+// buffers, small device helpers and the launch wrappers shared between the
+// translation units.  Device memory layout of one problem (all in HBM):
+//   grids            (N+1)^d nodes, C order (last axis fastest), FP64 (or FP32
+//                    for the mixed-precision work buffers)
+//   DOF arrays       structure of arrays, length N_b, DOF order of kfbi.h
+//   per-DOF blocks   row-major [N_b][k] (stencils, collocation inverses)
+//   per-irregular    column-major [k][n_irr] so that one thread per node reads
+//                    coalesced (composite collocation rows, correction lists)
+//   trace weights    CSR over DOFs, one CSR per side (+, -)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "kfbi.h"
+
+namespace kfbi {
+
+constexpr int kMaxCoef = 35;          // C(4+3, 3)
+constexpr int kMaxPde = 10;
+constexpr int kMaxDir = 15;
+constexpr int kMaxNeu = 10;
+constexpr int kMaxNeighbours = 26;    // 3^3 - 1
+constexpr double kTieEps = 1e-12;     // closest-point tie tolerance (units of h^2)
+constexpr double kRootTol = 1e-15;    // root iteration stop |ds| <= tol h
+constexpr int kRootMaxIt = 64;
+constexpr double kTraceWeightScale = 4.0;   // exp(-|xi|^2 / 4)
+
+// Status codes written by setup kernels into Problem::d_flags.
+enum SetupFlag : int {
+  kFlagGeometry = 0,      // first DOF without a complete collocation stencil (+1), 0 = none
+  kFlagSingular = 1,      // first DOF with a singular collocation matrix (+1)
+  kFlagTraceSingular = 2, // first DOF with a singular trace fit (+1)
+  kFlagOutOfBox = 3,      // a stencil left the grid (+1)
+  kFlagClosestFallback = 4,  // count of irregular nodes that needed the global search
+  kFlagCount = 8
+};
+
+struct Grid {
+  int d, n;
+  double lo, h;
+  __host__ __device__ int np1() const { return n + 1; }
+  __host__ __device__ long long nodes() const {
+    long long m = n + 1;
+    return d == 2 ? m * m : m * m * m;
+  }
+};
+
+struct LevelSet {
+  int kind;
+  int np;
+  double p[KFBI_LS_MAX_PARAMS];
+};
+
+// Trace stencil CSR for one side.
+struct TraceCSR {
+  int32_t* ptr = nullptr;    // N_b + 1
+  int32_t* node = nullptr;   // grid linear index
+  int32_t* irr = nullptr;    // irregular index when the node is across Gamma, else -1
+  double* wv = nullptr;      // value weights
+  double* wn = nullptr;      // normal-derivative weights
+  double* w = nullptr;       // weights of the operator's own trace quantity
+  int nnz = 0;
+};
+
+struct BoxSolver;   // dst.cu
+struct MgSolver;    // mg.cu
+
+// Kernel-launch accounting: every launch is counted by class; with profiling
+// enabled each launch is bracketed by CUDA events on the problem's stream.
+struct Profiler {
+  bool on = false;
+  long long launches[KFBI_KC_COUNT] = {};
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<int> cls;              // class of record r (events 2r, 2r+1)
+};
+
+struct Gmres {
+  int nb = 0, m = 0;
+  double* V = nullptr;       // (m+1) x N_b
+  double* H = nullptr;       // column j at H + j*(m+1)
+  double* cs = nullptr;
+  double* sn = nullptr;
+  double* g = nullptr;       // m+1
+  double* y = nullptr;       // m
+  double* part = nullptr;    // partial sums
+  double* scal = nullptr;    // device scalars: [0] beta, [1] bnorm, [2] res, [3] tmp
+  double* hcol = nullptr;    // (m+1) coefficient scratch
+  double* host_res = nullptr;  // pinned
+  int nchunk = 0;
+};
+
+}  // namespace kfbi
+
+struct kfbi_problem {
+  kfbi_config cfg;
+  kfbi::Grid g;
+  kfbi::LevelSet ls;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  double kt = 0.0;           // kappa~ of the box operator
+  double mu = 0.0;           // (sigma_out - sigma_in)/(sigma_out + sigma_in)
+  double cos_alpha = 0.0;
+  double stencil_c[4] = {0, 0, 0, 0};   // coefficients by number of nonzero offsets
+  double* stencil_dev = nullptr;         // the same four on the device
+
+  // geometry
+  uint8_t* inside = nullptr;
+  uint8_t* irr_flag = nullptr;
+  int nb = 0;
+  double* x[3] = {nullptr, nullptr, nullptr};
+  double* nrm[3] = {nullptr, nullptr, nullptr};
+  int32_t* family = nullptr;
+  int32_t* edge = nullptr;
+  int32_t* axis = nullptr;
+  int32_t* st_axis = nullptr;
+  int32_t* line_start[3] = {nullptr, nullptr, nullptr};
+  int nlines = 0;
+
+  // collocation
+  int npde = 0, ndir = 0, nneu = 0, ncoef = 0;
+  int32_t* pde_node = nullptr;   // [N_b][npde] linear node index
+  int32_t* dir_idx = nullptr;    // [N_b][ndir]
+  int32_t* neu_idx = nullptr;    // [N_b][nneu]
+  double* minv = nullptr;        // [N_b][ncoef][ncoef], row-major M^{-1}
+
+  // irregular nodes
+  int nirr = 0;
+  int32_t* irr_lin = nullptr;    // [n_irr]
+  int32_t* irr_owner = nullptr;  // [n_irr]
+  uint8_t* irr_inside = nullptr; // [n_irr]
+  double* irr_w = nullptr;       // [ncoef][n_irr] composite rows phi(xi)^T M^{-1}
+  int32_t* corr_nb = nullptr;    // [n_nb][n_irr] irregular index of an other-side neighbour or -1
+  int n_nb = 0;
+  int8_t* nb_off = nullptr;      // [n_nb][3] neighbour offsets (setup enumeration order)
+  double* nb_coef = nullptr;     // [n_nb] stencil coefficient c of each neighbour
+
+  // traces
+  kfbi::TraceCSR tr[2];
+
+  // box solver + work
+  kfbi::BoxSolver* box = nullptr;
+  double* cvals = nullptr;       // [n_irr]
+  double* coef = nullptr;        // [N_b][ncoef] (stage output scratch)
+  double* rhs = nullptr;         // grid
+  double* ugrid = nullptr;       // grid
+  double* tvals = nullptr;       // [N_b]
+  double* ftilde = nullptr;      // grid scratch
+  double* bvec = nullptr;        // [N_b]
+  double* zero_nb = nullptr;     // [N_b] zeros
+  int* d_flags = nullptr;        // kFlagCount ints
+  kfbi::Gmres gm;
+  kfbi::Profiler prof;
+  kfbi::MgSolver* mg = nullptr;
+  // CUDA graph of one operator application on fixed buffers (xbuf -> ybuf)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t op_graph = nullptr;
+  cudaGraphExec_t op_exec = nullptr;
+  long long op_counts[KFBI_KC_COUNT] = {};
+  double* xbuf = nullptr;
+  double* ybuf = nullptr;
+  bool use_graphs = true;
+};
+
+namespace kfbi {
+
+// ---- error handling ------------------------------------------------------
+kfbi_status fail(kfbi_problem* p, kfbi_status s, const std::string& msg);
+#define KFBI_CUDA(p, call)                                                       \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess)                                                        \
+      return ::kfbi::fail((p), KFBI_ERR_CUDA,                                     \
+                          std::string(#call) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+#define KFBI_TRY(expr)                                                           \
+  do {                                                                            \
+    kfbi_status s_ = (expr);                                                      \
+    if (s_ != KFBI_OK) return s_;                                                 \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** ptr, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(ptr), count * sizeof(T) + 16);
+}
+
+inline int div_up(long long a, long long b) { return static_cast<int>((a + b - 1) / b); }
+
+// ---- device helpers -------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Graded-lexicographic exponents (total degree ascending, then the exponent of
+// x descending, then y descending), the monomial basis of Sec. 5.3.1.
+struct Exponents {
+  int n;
+  int8_t e[kMaxCoef][3];
+};
+void make_exponents(int d, int p, Exponents* out);
+
+// Scope object bracketing one kernel launch (see Profiler).
+struct Launch {
+  kfbi_problem* p;
+  int cls;
+  int rec = -1;
+  Launch(kfbi_problem* pp, int c);
+  ~Launch();
+};
+
+#define KFBI_LAUNCH(p, cls, ...)        \
+  do {                                   \
+    ::kfbi::Launch launch_((p), (cls));  \
+    __VA_ARGS__;                         \
+  } while (0)
+
+// ---- launch wrappers implemented in the .cu files ---------------------------
+// setup.cu
+kfbi_status build_geometry(kfbi_problem* p);
+// hotpath.cu
+kfbi_status launch_correction_values(kfbi_problem* p, const double* a, const double* b,
+                                     const double* ftilde, double* cvals);
+kfbi_status launch_collocation_fit(kfbi_problem* p, const double* a, const double* b,
+                                   const double* ftilde, double* coef);
+kfbi_status launch_rhs(kfbi_problem* p, const double* cvals, const kfbi_data* data,
+                       double* rhs);
+kfbi_status launch_correction_values_data(kfbi_problem* p, const double* a, const double* b,
+                                          const kfbi_data* data, double* cvals);
+kfbi_status upload_neighbour_tables(kfbi_problem* p);
+kfbi_status launch_traces(kfbi_problem* p, const double* u, const double* cvals,
+                          double* vp, double* vm, double* dp, double* dm);
+kfbi_status launch_operator_trace(kfbi_problem* p, const double* u, const double* cvals,
+                                  const double* x, double alpha_x, double beta_t,
+                                  double* y);
+kfbi_status launch_set_boundary(kfbi_problem* p, double* u, const double* g_b);
+// dst.cu / mg.cu
+kfbi_status box_create(kfbi_problem* p);
+void box_destroy(kfbi_problem* p);
+kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u);
+kfbi_status box_last_residual(kfbi_problem* p, double* rel, int* converged);
+// gmres.cu
+kfbi_status gmres_create(kfbi_problem* p, int m);
+void gmres_destroy(kfbi_problem* p);
+kfbi_status apply_operator_fast(kfbi_problem* p, const double* x, double* y);
+kfbi_status gmres_run(kfbi_problem* p, const double* b, const double* x0, double rtol,
+                      int restart, int max_iter, double* x, int* iters, double* rel);
+
+}  // namespace kfbi

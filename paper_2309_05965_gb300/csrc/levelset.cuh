@@ -1,0 +1,109 @@
+// Analytic level-set functions H and grad H on the device (Sec. 5.1):
+// Gamma = {H = 0}, Omega = {H < 0}.  Parameter layouts are those of
+// kfbi_levelset_kind in kfbi.h.  The translation unit that uses these for
+// geometric decisions is compiled with -fmad=false so that every product and
+// sum is rounded separately.
+#pragma once
+#include "kfbi_internal.cuh"
+
+namespace kfbi {
+
+__device__ inline double ls_H(const LevelSet& L, const double* X) {
+  const double* p = L.p;
+  switch (L.kind) {
+    case KFBI_LS_ELLIPSE: {
+      double x = X[0] - p[0], y = X[1] - p[1];
+      double c = cos(p[4]), s = sin(p[4]);
+      double u = (x * c + y * s) / p[2];
+      double v = (y * c - x * s) / p[3];
+      return u * u + v * v - 1.0;
+    }
+    case KFBI_LS_STAR: {
+      double x = X[0] - p[0], y = X[1] - p[1];
+      double r = sqrt(x * x + y * y);
+      double th = atan2(y, x);
+      return r - p[2] - p[3] * sin(p[4] * th);
+    }
+    case KFBI_LS_ELLIPSOID: {
+      double u = (X[0] - p[0]) / p[3];
+      double v = (X[1] - p[1]) / p[4];
+      double w = (X[2] - p[2]) / p[5];
+      return u * u + v * v + w * w - 1.0;
+    }
+    case KFBI_LS_TORUS: {
+      double rho = sqrt(X[0] * X[0] + X[1] * X[1]);
+      double t = rho - p[0];
+      return t * t + X[2] * X[2] - p[1] * p[1];
+    }
+    case KFBI_LS_MOLECULE: {
+      double r = p[0], level = p[1];
+      int na = static_cast<int>(p[2]);
+      double acc = 0.0;
+      for (int k = 0; k < na; ++k) {
+        double dx = X[0] - p[3 + 3 * k], dy = X[1] - p[4 + 3 * k], dz = X[2] - p[5 + 3 * k];
+        acc = acc + exp(-(dx * dx + dy * dy + dz * dz) / (r * r));
+      }
+      return level - acc;
+    }
+  }
+  return 0.0;
+}
+
+__device__ inline void ls_grad(const LevelSet& L, const double* X, double* g) {
+  const double* p = L.p;
+  switch (L.kind) {
+    case KFBI_LS_ELLIPSE: {
+      double x = X[0] - p[0], y = X[1] - p[1];
+      double c = cos(p[4]), s = sin(p[4]);
+      double a = p[2], b = p[3];
+      double u = (x * c + y * s) / a;
+      double v = (y * c - x * s) / b;
+      g[0] = 2.0 * u * (c / a) + 2.0 * v * (-s / b);
+      g[1] = 2.0 * u * (s / a) + 2.0 * v * (c / b);
+      g[2] = 0.0;
+      return;
+    }
+    case KFBI_LS_STAR: {
+      double x = X[0] - p[0], y = X[1] - p[1];
+      double r2 = x * x + y * y;
+      double r = sqrt(r2);
+      double th = atan2(y, x);
+      double dth = p[3] * p[4] * cos(p[4] * th);
+      g[0] = x / r + dth * y / r2;
+      g[1] = y / r - dth * x / r2;
+      g[2] = 0.0;
+      return;
+    }
+    case KFBI_LS_ELLIPSOID: {
+      g[0] = 2.0 * (X[0] - p[0]) / (p[3] * p[3]);
+      g[1] = 2.0 * (X[1] - p[1]) / (p[4] * p[4]);
+      g[2] = 2.0 * (X[2] - p[2]) / (p[5] * p[5]);
+      return;
+    }
+    case KFBI_LS_TORUS: {
+      double rho = sqrt(X[0] * X[0] + X[1] * X[1]);
+      double f = 2.0 * (rho - p[0]) / rho;
+      g[0] = f * X[0];
+      g[1] = f * X[1];
+      g[2] = 2.0 * X[2];
+      return;
+    }
+    case KFBI_LS_MOLECULE: {
+      double r = p[0];
+      int na = static_cast<int>(p[2]);
+      g[0] = g[1] = g[2] = 0.0;
+      for (int k = 0; k < na; ++k) {
+        double dx = X[0] - p[3 + 3 * k], dy = X[1] - p[4 + 3 * k], dz = X[2] - p[5 + 3 * k];
+        double e = exp(-(dx * dx + dy * dy + dz * dz) / (r * r));
+        double c = (2.0 / (r * r)) * e;
+        g[0] = g[0] + c * dx;
+        g[1] = g[1] + c * dy;
+        g[2] = g[2] + c * dz;
+      }
+      return;
+    }
+  }
+  g[0] = g[1] = g[2] = 0.0;
+}
+
+}  // namespace kfbi

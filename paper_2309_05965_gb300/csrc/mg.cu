@@ -1,0 +1,654 @@
+// Geometric multigrid box solve (Algorithm 1, Step 3.3; the paper names
+// geometric multigrid as the alternative fast solver but gives no design).
+//
+// Design (this library's):
+//   * levels N, N/2, ..., 4 with the compact operator rediscretised at h_l =
+//     2^l h (same kappa~);
+//   * smoother: weighted Jacobi, omega = 0.909 (2D) / 1.136 (3D), the values that
+//     minimise the high-frequency amplification of the 9/27-point compact
+//     operators (smoothing factor 0.45 in both);
+//   * full-weighting restriction, (bi/tri)linear prolongation, V(2,2) cycles;
+//   * coarsest level (3^d unknowns) solved exactly with a dense inverse;
+//   * levels with N <= kCoarseN run the rest of the V-cycle inside one CTA
+//     (grids of at most 31^2 / 15^3 unknowns), removing per-level launches;
+//   * FP64 mode: V-cycles until max|R - A u| <= tol max|R|;
+//   * mixed mode: FP32 V-cycles on A e = r with the FP64 residual r = R - A u
+//     recomputed after each group of cycles (iterative refinement);
+//   * convergence is tracked on the device; cycles after convergence exit at
+//     their first instruction (graph-capturable, no host synchronisation).
+#include <cmath>
+#include <vector>
+
+#include "kfbi_internal.cuh"
+
+namespace kfbi {
+
+namespace {
+
+constexpr int kCoarseN2 = 32;   // 2D: levels with N <= 32 run in one CTA
+constexpr int kCoarseN3 = 16;   // 3D
+constexpr int kNu = 2;          // pre- and post-smoothing sweeps
+
+template <typename T>
+struct Lvl {
+  int n;
+  T c[4];        // stencil coefficients by number of nonzero offsets
+  T dinv_w;      // omega / c0
+  T* u;
+  T* f;
+  T* t;          // Jacobi ping-pong / residual
+};
+
+template <typename T>
+struct LvlArgs {
+  int d, order, nlev;
+  Lvl<T> L[16];
+  const T* cinv;   // coarsest dense inverse, m x m, m = 3^d
+};
+
+__device__ __forceinline__ long long lin(int d, int n1, int i0, int i1, int i2) {
+  return d == 2 ? (long long)i1 * n1 + i2 : ((long long)i0 * n1 + i1) * n1 + i2;
+}
+
+// A u at interior node t (grid of n1 nodes per axis)
+template <typename T>
+__device__ __forceinline__ T apply_at(int d, int order, int n1, const T* c, const T* up) {
+  if (d == 2) {
+    T s1 = (up[-1] + up[1]) + (up[-n1] + up[n1]);
+    T a = c[0] * up[0] + c[1] * s1;
+    if (order == 4) a += c[2] * ((up[-n1 - 1] + up[-n1 + 1]) + (up[n1 - 1] + up[n1 + 1]));
+    return a;
+  }
+  const long long s = (long long)n1 * n1;
+  T f = (up[-1] + up[1]) + (up[-n1] + up[n1]) + (up[-s] + up[s]);
+  T a = c[0] * up[0] + c[1] * f;
+  if (order == 4) {
+    T e = (up[-n1 - 1] + up[-n1 + 1]) + (up[n1 - 1] + up[n1 + 1]) + (up[-s - 1] + up[-s + 1]) +
+          (up[s - 1] + up[s + 1]) + (up[-s - n1] + up[-s + n1]) + (up[s - n1] + up[s + n1]);
+    T k = (up[-s - n1 - 1] + up[-s - n1 + 1]) + (up[-s + n1 - 1] + up[-s + n1 + 1]) +
+          (up[s - n1 - 1] + up[s - n1 + 1]) + (up[s + n1 - 1] + up[s + n1 + 1]);
+    a += c[2] * e + c[3] * k;
+  }
+  return a;
+}
+
+// ---- per-level kernels: x over the last axis, y (z) over the others --------
+
+template <typename T>
+__global__ void k_jacobi(int d, int order, Lvl<T> L, const T* __restrict__ uin, T* __restrict__ uout,
+                         int zero_guess, const int* skip) {
+  if (skip && *skip) return;
+  const int n = L.n, n1 = n + 1;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i1 = blockIdx.y, i0 = blockIdx.z;
+  if (j > n) return;
+  const long long t = lin(d, n1, i0, i1, j);
+  const bool interior = j >= 1 && j < n && i1 >= 1 && i1 < n && (d == 2 || (i0 >= 1 && i0 < n));
+  if (!interior) {
+    uout[t] = (T)0;
+    return;
+  }
+  if (zero_guess) {
+    uout[t] = L.dinv_w * L.f[t];
+    return;
+  }
+  T au = apply_at<T>(d, order, n1, L.c, uin + t);
+  uout[t] = uin[t] + L.dinv_w * (L.f[t] - au);
+}
+
+template <typename T>
+__global__ void k_resid_lvl(int d, int order, Lvl<T> L, T* __restrict__ r, const int* skip) {
+  if (skip && *skip) return;
+  const int n = L.n, n1 = n + 1;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i1 = blockIdx.y, i0 = blockIdx.z;
+  if (j > n) return;
+  const long long t = lin(d, n1, i0, i1, j);
+  const bool interior = j >= 1 && j < n && i1 >= 1 && i1 < n && (d == 2 || (i0 >= 1 && i0 < n));
+  r[t] = interior ? L.f[t] - apply_at<T>(d, order, n1, L.c, L.u + t) : (T)0;
+}
+
+// full weighting: weight prod_k w(o_k), w(0) = 1/2, w(+-1) = 1/4
+template <typename T>
+__global__ void k_restrict(int d, int nc, const T* __restrict__ rf, T* __restrict__ fc,
+                           const int* skip) {
+  if (skip && *skip) return;
+  const int nf1 = 2 * nc + 1, nc1 = nc + 1;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i1 = blockIdx.y, i0 = blockIdx.z;
+  if (j > nc) return;
+  const long long tc = lin(d, nc1, i0, i1, j);
+  const bool interior = j >= 1 && j < nc && i1 >= 1 && i1 < nc && (d == 2 || (i0 >= 1 && i0 < nc));
+  if (!interior) {
+    fc[tc] = (T)0;
+    return;
+  }
+  T acc = (T)0;
+  const T w[3] = {(T)0.25, (T)0.5, (T)0.25};
+  if (d == 2) {
+    for (int a = -1; a <= 1; ++a)
+      for (int b = -1; b <= 1; ++b)
+        acc += w[a + 1] * w[b + 1] * rf[lin(2, nf1, 0, 2 * i1 + a, 2 * j + b)];
+  } else {
+    for (int a = -1; a <= 1; ++a)
+      for (int b = -1; b <= 1; ++b)
+        for (int c = -1; c <= 1; ++c)
+          acc += w[a + 1] * w[b + 1] * w[c + 1] * rf[lin(3, nf1, 2 * i0 + a, 2 * i1 + b, 2 * j + c)];
+  }
+  fc[tc] = acc;
+}
+
+// uf += P uc ((bi/tri)linear interpolation)
+template <typename T>
+__global__ void k_prolong_add(int d, int nf, const T* __restrict__ uc, T* __restrict__ uf,
+                              const int* skip) {
+  if (skip && *skip) return;
+  const int nf1 = nf + 1, nc1 = nf / 2 + 1;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i1 = blockIdx.y, i0 = blockIdx.z;
+  if (j > nf) return;
+  const bool interior = j >= 1 && j < nf && i1 >= 1 && i1 < nf && (d == 2 || (i0 >= 1 && i0 < nf));
+  if (!interior) return;
+  const int idx[3] = {i0, i1, j};
+  int lo[3], hi[3];
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = idx[k] >> 1;
+    hi[k] = (idx[k] + 1) >> 1;
+  }
+  T acc = (T)0;
+  const int k0 = d == 2 ? 1 : 0;
+  const int nc = 1 << (3 - k0);   // 4 (2D) or 8 (3D) corner combinations
+  for (int m = 0; m < nc; ++m) {
+    int ci[3] = {lo[0], lo[1], lo[2]};
+    T wgt = (T)1;
+    bool dup = false;
+    for (int k = k0; k < 3; ++k) {
+      int bit = (m >> (k - k0)) & 1;
+      bool odd = (idx[k] & 1) != 0;
+      if (!odd && bit) dup = true;
+      ci[k] = bit ? hi[k] : lo[k];
+      if (odd) wgt *= (T)0.5;
+    }
+    if (dup) continue;
+    acc += wgt * uc[lin(d, nc1, ci[0], ci[1], ci[2])];
+  }
+  uf[lin(d, nf1, i0, i1, j)] += acc;
+}
+
+// ---- the coarse part of the V-cycle in one CTA ------------------------------
+
+template <typename T>
+__device__ void blk_jacobi(int d, int order, const Lvl<T>& L, const T* uin, T* uout, bool zero) {
+  const int n = L.n, n1 = n + 1;
+  const int m = n - 1;
+  const int tot = d == 2 ? m * m : m * m * m;
+  for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+    int j = q % m + 1, r = q / m;
+    int i1 = r % m + 1, i0 = d == 3 ? r / m + 1 : 0;
+    long long t = lin(d, n1, i0, i1, j);
+    uout[t] = zero ? L.dinv_w * L.f[t]
+                   : uin[t] + L.dinv_w * (L.f[t] - apply_at<T>(d, order, n1, L.c, uin + t));
+  }
+  __syncthreads();
+}
+
+// The V-cycle from level lstart down to the coarsest and back, in one CTA.
+// start_zero: the iterate at lstart starts from zero (a coarse correction, or
+// the first cycle on a grid that is coarse from the start).
+template <typename T>
+__global__ void k_coarse_cycle(LvlArgs<T> A, int lstart, int start_zero, const int* skip) {
+  if (skip && *skip) return;
+  const int d = A.d;
+  for (int l = lstart; l < A.nlev; ++l) {
+    const int n1 = A.L[l].n + 1;
+    const int tot = d == 2 ? n1 * n1 : n1 * n1 * n1;
+    for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+      A.L[l].t[q] = (T)0;
+      if (l > lstart || start_zero) A.L[l].u[q] = (T)0;
+    }
+  }
+  __syncthreads();
+  // descend
+  for (int l = lstart; l < A.nlev - 1; ++l) {
+    const Lvl<T>& L = A.L[l];
+    bool zero = l > lstart || start_zero;   // corrections start from zero
+    for (int s = 0; s < kNu; ++s) {
+      blk_jacobi<T>(d, A.order, L, zero && s == 0 ? L.u : L.u, L.t, zero && s == 0);
+      // copy back t -> u
+      const int n1 = L.n + 1;
+      const int tot = d == 2 ? n1 * n1 : n1 * n1 * n1;
+      for (int q = threadIdx.x; q < tot; q += blockDim.x) L.u[q] = L.t[q];
+      __syncthreads();
+    }
+    // residual into t, restrict to the next f
+    {
+      const int n = L.n, n1 = n + 1, m = n - 1;
+      const int tot = d == 2 ? m * m : m * m * m;
+      for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+        int j = q % m + 1, r = q / m;
+        int i1 = r % m + 1, i0 = d == 3 ? r / m + 1 : 0;
+        long long t = lin(d, n1, i0, i1, j);
+        L.t[t] = L.f[t] - apply_at<T>(d, A.order, n1, L.c, L.u + t);
+      }
+      __syncthreads();
+      const Lvl<T>& C = A.L[l + 1];
+      const int nc = C.n, nc1 = nc + 1, mc = nc - 1;
+      const int totc = d == 2 ? mc * mc : mc * mc * mc;
+      const T w[3] = {(T)0.25, (T)0.5, (T)0.25};
+      for (int q = threadIdx.x; q < totc; q += blockDim.x) {
+        int j = q % mc + 1, r = q / mc;
+        int i1 = r % mc + 1, i0 = d == 3 ? r / mc + 1 : 0;
+        T acc = (T)0;
+        if (d == 2) {
+          for (int a = -1; a <= 1; ++a)
+            for (int b = -1; b <= 1; ++b) acc += w[a + 1] * w[b + 1] * L.t[lin(2, n1, 0, 2 * i1 + a, 2 * j + b)];
+        } else {
+          for (int a = -1; a <= 1; ++a)
+            for (int b = -1; b <= 1; ++b)
+              for (int c = -1; c <= 1; ++c)
+                acc += w[a + 1] * w[b + 1] * w[c + 1] *
+                       L.t[lin(3, n1, 2 * i0 + a, 2 * i1 + b, 2 * j + c)];
+        }
+        C.f[lin(d, nc1, i0, i1, j)] = acc;
+      }
+      __syncthreads();
+    }
+  }
+  // coarsest: u = C^{-1} f on its 3^d interior unknowns
+  {
+    const Lvl<T>& C = A.L[A.nlev - 1];
+    const int n1 = C.n + 1, m = C.n - 1;
+    const int tot = d == 2 ? m * m : m * m * m;
+    for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+      T acc = (T)0;
+      for (int k = 0; k < tot; ++k) {
+        int j = k % m + 1, r = k / m;
+        int i1 = r % m + 1, i0 = d == 3 ? r / m + 1 : 0;
+        acc += A.cinv[q * tot + k] * C.f[lin(d, n1, i0, i1, j)];
+      }
+      int j = q % m + 1, r = q / m;
+      int i1 = r % m + 1, i0 = d == 3 ? r / m + 1 : 0;
+      C.t[lin(d, n1, i0, i1, j)] = acc;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < (d == 2 ? n1 * n1 : n1 * n1 * n1); q += blockDim.x) C.u[q] = C.t[q];
+    __syncthreads();
+  }
+  // ascend
+  for (int l = A.nlev - 2; l >= lstart; --l) {
+    const Lvl<T>& L = A.L[l];
+    const Lvl<T>& C = A.L[l + 1];
+    const int nf = L.n, nf1 = nf + 1, m = nf - 1, nc1 = C.n + 1;
+    const int tot = d == 2 ? m * m : m * m * m;
+    for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+      int j = q % m + 1, r = q / m;
+      int i1 = r % m + 1, i0 = d == 3 ? r / m + 1 : 0;
+      const int idx[3] = {i0, i1, j};
+      int lo[3], hi[3];
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = idx[k] >> 1;
+        hi[k] = (idx[k] + 1) >> 1;
+      }
+      T acc = (T)0;
+      const int k0 = d == 2 ? 1 : 0;
+      for (int mm = 0; mm < (1 << (3 - k0)); ++mm) {
+        int ci[3] = {lo[0], lo[1], lo[2]};
+        T wgt = (T)1;
+        bool dup = false;
+        for (int k = k0; k < 3; ++k) {
+          int bit = (mm >> (k - k0)) & 1;
+          bool odd = (idx[k] & 1) != 0;
+          if (!odd && bit) dup = true;
+          ci[k] = bit ? hi[k] : lo[k];
+          if (odd) wgt *= (T)0.5;
+        }
+        if (dup) continue;
+        acc += wgt * C.u[lin(d, nc1, ci[0], ci[1], ci[2])];
+      }
+      L.u[lin(d, nf1, i0, i1, j)] += acc;
+    }
+    __syncthreads();
+    for (int s = 0; s < kNu; ++s) {
+      blk_jacobi<T>(d, A.order, L, L.u, L.t, false);
+      const int tot1 = d == 2 ? nf1 * nf1 : nf1 * nf1 * nf1;
+      for (int q = threadIdx.x; q < tot1; q += blockDim.x) L.u[q] = L.t[q];
+      __syncthreads();
+    }
+  }
+}
+
+// ---- refinement helpers ------------------------------------------------------
+
+__global__ void k_to_float(long long tot, const double* __restrict__ a, float* __restrict__ b,
+                           const int* skip) {
+  if (skip && *skip) return;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x)
+    b[t] = (float)a[t];
+}
+
+__global__ void k_add_float(long long tot, const float* __restrict__ e, double* __restrict__ u,
+                            const int* skip) {
+  if (skip && *skip) return;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x)
+    u[t] += (double)e[t];
+}
+
+__global__ void k_mg_residual64(Grid g, int order, const double* __restrict__ c,
+                                const double* __restrict__ R, const double* __restrict__ u,
+                                double* __restrict__ r, unsigned long long* __restrict__ nrm,
+                                const int* skip) {
+  if (skip && *skip) return;
+  const int n1 = g.n + 1;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i1 = blockIdx.y, i0 = blockIdx.z;
+  double mx = 0.0;
+  if (j <= g.n) {
+    const long long t = lin(g.d, n1, i0, i1, j);
+    const bool interior = j >= 1 && j < g.n && i1 >= 1 && i1 < g.n && (g.d == 2 || (i0 >= 1 && i0 < g.n));
+    double v = interior ? R[t] - apply_at<double>(g.d, order, n1, c, u + t) : 0.0;
+    if (r) r[t] = v;
+    mx = fabs(v);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(nrm, (unsigned long long)__double_as_longlong(mx));
+}
+
+__global__ void k_absmax_mg(long long tot, const double* __restrict__ R, unsigned long long* nrm) {
+  double mx = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x)
+    mx = fmax(mx, fabs(R[t]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(nrm, (unsigned long long)__double_as_longlong(mx));
+}
+
+__global__ void k_mg_check(unsigned long long* nrm, double tol, int* conv) {
+  if (*conv) return;
+  double R = __longlong_as_double((long long)nrm[0]);
+  double r = __longlong_as_double((long long)nrm[1]);
+  nrm[2] = nrm[1];
+  if (r <= tol * R) *conv = 1;
+  nrm[1] = 0ull;
+}
+
+__global__ void k_mg_reset(unsigned long long* nrm, int* conv) {
+  nrm[0] = nrm[1] = nrm[2] = 0ull;
+  *conv = 0;
+}
+
+}  // namespace
+
+struct MgSolver {
+  int nlev = 0, lcoarse = 0;
+  int precision = KFBI_FP64;
+  LvlArgs<double> A64;
+  LvlArgs<float> A32;
+  double* cinv64 = nullptr;
+  float* cinv32 = nullptr;
+  std::vector<void*> bufs;
+  double* u64 = nullptr;       // mixed: FP64 accumulated solution lives in the caller's u
+  double* r64 = nullptr;       // FP64 residual
+  unsigned long long* nrm = nullptr;
+  int* conv = nullptr;
+  int max_cycles = 60;
+  int inner_cycles = 4;
+  int outer_max = 6;
+  double tol = 1e-13;
+};
+
+namespace {
+
+void stencil_for(int d, int order, double h, double k, double* c) {
+  const double ih2 = 1.0 / (h * h);
+  if (order == 2) {
+    c[0] = -2.0 * d * ih2 - k;
+    c[1] = ih2;
+    c[2] = c[3] = 0.0;
+  } else if (d == 2) {
+    c[0] = -10.0 / 3.0 * ih2 - 2.0 / 3.0 * k;
+    c[1] = 2.0 / 3.0 * ih2 - k / 12.0;
+    c[2] = 1.0 / 6.0 * ih2;
+    c[3] = 0.0;
+  } else {
+    c[0] = -25.0 / 6.0 * ih2 - 0.5 * k;
+    c[1] = 5.0 / 12.0 * ih2 - k / 12.0;
+    c[2] = 1.0 / 8.0 * ih2;
+    c[3] = 1.0 / 48.0 * ih2;
+  }
+}
+
+// dense inverse of the coarsest operator (3^d interior unknowns) by Gauss-Jordan
+std::vector<double> coarse_inverse(int d, int order, double h, double kt) {
+  double c[4];
+  stencil_for(d, order, h, kt, c);
+  const int m = 3;
+  const int tot = d == 2 ? m * m : m * m * m;
+  std::vector<double> A(tot * tot, 0.0), I(tot * tot, 0.0);
+  for (int q = 0; q < tot; ++q) {
+    int qi[3] = {0, 0, 0};
+    int r = q;
+    for (int k = d - 1; k >= 0; --k) {
+      qi[k] = r % m;
+      r /= m;
+    }
+    for (int p = 0; p < tot; ++p) {
+      int pi[3] = {0, 0, 0};
+      int rr = p;
+      for (int k = d - 1; k >= 0; --k) {
+        pi[k] = rr % m;
+        rr /= m;
+      }
+      int nz = 0, far = 0;
+      for (int k = 0; k < d; ++k) {
+        int dd = std::abs(pi[k] - qi[k]);
+        if (dd > 1) far = 1;
+        nz += dd;
+      }
+      if (far) continue;
+      int cnt = 0;
+      for (int k = 0; k < d; ++k) cnt += pi[k] != qi[k];
+      if (order == 2 && cnt > 1) continue;
+      A[q * tot + p] = c[cnt];
+    }
+    I[q * tot + q] = 1.0;
+  }
+  for (int col = 0; col < tot; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < tot; ++r)
+      if (std::fabs(A[r * tot + col]) > std::fabs(A[piv * tot + col])) piv = r;
+    if (piv != col)
+      for (int k = 0; k < tot; ++k) {
+        std::swap(A[col * tot + k], A[piv * tot + k]);
+        std::swap(I[col * tot + k], I[piv * tot + k]);
+      }
+    double dv = A[col * tot + col];
+    for (int k = 0; k < tot; ++k) {
+      A[col * tot + k] /= dv;
+      I[col * tot + k] /= dv;
+    }
+    for (int r = 0; r < tot; ++r) {
+      if (r == col) continue;
+      double f = A[r * tot + col];
+      if (f == 0.0) continue;
+      for (int k = 0; k < tot; ++k) {
+        A[r * tot + k] -= f * A[col * tot + k];
+        I[r * tot + k] -= f * I[col * tot + k];
+      }
+    }
+  }
+  return I;
+}
+
+template <typename T>
+dim3 lvl_grid(int d, int n) {
+  return dim3((unsigned)div_up(n + 1, 128), (unsigned)(n + 1), d == 3 ? (unsigned)(n + 1) : 1u);
+}
+
+// One V-cycle starting at level 0 of A (u_0 holds the current iterate).
+template <typename T>
+kfbi_status vcycle(kfbi_problem* p, LvlArgs<T>& A, int lcoarse, bool zero_guess, const int* skip) {
+  const int d = A.d, order = A.order;
+  cudaStream_t st = p->stream;
+  for (int l = 0; l < lcoarse; ++l) {
+    Lvl<T>& L = A.L[l];
+    const dim3 gr = lvl_grid<T>(d, L.n);
+    const bool zero = (l > 0) || zero_guess;
+    // two sweeps u -> t -> u
+    KFBI_LAUNCH(p, KFBI_KC_MG, k_jacobi<T><<<gr, 128, 0, st>>>(d, order, L, L.u, L.t, zero ? 1 : 0, skip));
+    KFBI_LAUNCH(p, KFBI_KC_MG, k_jacobi<T><<<gr, 128, 0, st>>>(d, order, L, L.t, L.u, 0, skip));
+    KFBI_LAUNCH(p, KFBI_KC_MG, k_resid_lvl<T><<<gr, 128, 0, st>>>(d, order, L, L.t, skip));
+    KFBI_LAUNCH(p, KFBI_KC_MG, k_restrict<T><<<lvl_grid<T>(d, A.L[l + 1].n), 128, 0, st>>>(
+        d, A.L[l + 1].n, L.t, A.L[l + 1].f, skip));
+  }
+  KFBI_LAUNCH(p, KFBI_KC_MG, k_coarse_cycle<T><<<1, 1024, 0, st>>>(
+      A, lcoarse, (lcoarse > 0 || zero_guess) ? 1 : 0, skip));
+  for (int l = lcoarse - 1; l >= 0; --l) {
+    Lvl<T>& L = A.L[l];
+    const dim3 gr = lvl_grid<T>(d, L.n);
+    KFBI_LAUNCH(p, KFBI_KC_MG, k_prolong_add<T><<<gr, 128, 0, st>>>(d, L.n, A.L[l + 1].u, L.u, skip));
+    KFBI_LAUNCH(p, KFBI_KC_MG, k_jacobi<T><<<gr, 128, 0, st>>>(d, order, L, L.u, L.t, 0, skip));
+    KFBI_LAUNCH(p, KFBI_KC_MG, k_jacobi<T><<<gr, 128, 0, st>>>(d, order, L, L.t, L.u, 0, skip));
+  }
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+template <typename T>
+kfbi_status build_levels(kfbi_problem* p, MgSolver* M, LvlArgs<T>& A, T** cinv, bool level0_owned) {
+  const Grid g = p->g;
+  const int d = g.d;
+  A.d = d;
+  A.order = p->cfg.order;
+  int n = g.n, l = 0;
+  const double omega = d == 2 ? 0.909 : 1.136;
+  while (true) {
+    if (l >= 16) return fail(p, KFBI_ERR_UNSUPPORTED, "too many multigrid levels");
+    Lvl<T>& L = A.L[l];
+    L.n = n;
+    double c[4];
+    stencil_for(d, A.order, g.h * (double)(g.n / n), p->kt, c);
+    for (int k = 0; k < 4; ++k) L.c[k] = (T)c[k];
+    L.dinv_w = (T)(omega / c[0]);
+    const long long nodes = d == 2 ? (long long)(n + 1) * (n + 1) : (long long)(n + 1) * (n + 1) * (n + 1);
+    if (l > 0 || level0_owned) {
+      KFBI_CUDA(p, dalloc(&L.u, nodes));
+      KFBI_CUDA(p, dalloc(&L.f, nodes));
+      KFBI_CUDA(p, cudaMemset(L.u, 0, sizeof(T) * nodes));
+      KFBI_CUDA(p, cudaMemset(L.f, 0, sizeof(T) * nodes));
+      M->bufs.push_back(L.u);
+      M->bufs.push_back(L.f);
+    }
+    KFBI_CUDA(p, dalloc(&L.t, nodes));
+    KFBI_CUDA(p, cudaMemset(L.t, 0, sizeof(T) * nodes));
+    M->bufs.push_back(L.t);
+    ++l;
+    if (n == 4) break;
+    n /= 2;
+  }
+  A.nlev = l;
+  const int cn = d == 2 ? kCoarseN2 : kCoarseN3;
+  int lc = 0;
+  while (lc < A.nlev - 1 && A.L[lc].n > cn) ++lc;
+  M->lcoarse = lc;
+  std::vector<double> ci = coarse_inverse(d, A.order, g.h * (double)(g.n / 4), p->kt);
+  std::vector<T> cit(ci.begin(), ci.end());
+  KFBI_CUDA(p, dalloc(cinv, cit.size()));
+  KFBI_CUDA(p, cudaMemcpy(*cinv, cit.data(), sizeof(T) * cit.size(), cudaMemcpyHostToDevice));
+  M->bufs.push_back(*cinv);
+  A.cinv = *cinv;
+  return KFBI_OK;
+}
+
+}  // namespace
+
+kfbi_status mg_create(kfbi_problem* p) {
+  const Grid g = p->g;
+  if (g.n < 8 || (g.n & (g.n - 1)) != 0) return fail(p, KFBI_ERR_UNSUPPORTED, "MG needs N a power of two >= 8");
+  MgSolver* M = new MgSolver();
+  p->mg = M;
+  M->precision = p->cfg.precision;
+  M->tol = p->cfg.box_rtol > 0 ? p->cfg.box_rtol : 1e-13;
+  M->max_cycles = p->cfg.box_max_iters > 0 ? p->cfg.box_max_iters : 40;
+  const long long nodes = g.nodes();
+  if (M->precision == KFBI_MIXED) {
+    KFBI_TRY(build_levels<float>(p, M, M->A32, &M->cinv32, true));
+    KFBI_CUDA(p, dalloc(&M->r64, nodes));
+    KFBI_CUDA(p, cudaMemset(M->r64, 0, sizeof(double) * nodes));
+    M->bufs.push_back(M->r64);
+  } else {
+    KFBI_TRY(build_levels<double>(p, M, M->A64, &M->cinv64, false));
+  }
+  KFBI_CUDA(p, dalloc(&M->nrm, 3));
+  KFBI_CUDA(p, dalloc(&M->conv, 1));
+  M->bufs.push_back(M->nrm);
+  M->bufs.push_back(M->conv);
+  return KFBI_OK;
+}
+
+void mg_destroy(kfbi_problem* p) {
+  MgSolver* M = p->mg;
+  if (!M) return;
+  for (void* b : M->bufs) cudaFree(b);
+  delete M;
+  p->mg = nullptr;
+}
+
+kfbi_status mg_solve(kfbi_problem* p, const double* rhs, double* u) {
+  MgSolver* M = p->mg;
+  const Grid g = p->g;
+  cudaStream_t st = p->stream;
+  const long long nodes = g.nodes();
+  const dim3 gr = lvl_grid<double>(g.d, g.n);
+  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_mg_reset<<<1, 1, 0, st>>>(M->nrm, M->conv));
+  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_absmax_mg<<<std::min(div_up(nodes, 256), 152 * 8), 256, 0, st>>>(
+      nodes, rhs, M->nrm));
+  KFBI_CUDA(p, cudaMemsetAsync(u, 0, sizeof(double) * nodes, st));
+  if (M->precision != KFBI_MIXED) {
+    LvlArgs<double>& A = M->A64;
+    A.L[0].u = u;
+    A.L[0].f = const_cast<double*>(rhs);
+    for (int c = 0; c < M->max_cycles; ++c) {
+      KFBI_TRY(vcycle<double>(p, A, M->lcoarse, c == 0, M->conv));
+      KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_mg_residual64<<<gr, 128, 0, st>>>(
+          g, p->cfg.order, p->stencil_dev, rhs, u, nullptr, M->nrm + 1, M->conv));
+      KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_mg_check<<<1, 1, 0, st>>>(M->nrm, M->tol, M->conv));
+    }
+    KFBI_CUDA(p, cudaGetLastError());
+    return KFBI_OK;
+  }
+  // mixed: u (FP64) += FP32 MG(A e = r), r = R - A u in FP64
+  LvlArgs<float>& A = M->A32;
+  const double* r = rhs;
+  for (int o = 0; o < M->outer_max; ++o) {
+    KFBI_LAUNCH(p, KFBI_KC_MG, k_to_float<<<std::min(div_up(nodes, 256), 152 * 8), 256, 0, st>>>(
+        nodes, r, A.L[0].f, M->conv));
+    for (int c = 0; c < M->inner_cycles; ++c) KFBI_TRY(vcycle<float>(p, A, M->lcoarse, c == 0, M->conv));
+    KFBI_LAUNCH(p, KFBI_KC_MG, k_add_float<<<std::min(div_up(nodes, 256), 152 * 8), 256, 0, st>>>(
+        nodes, A.L[0].u, u, M->conv));
+    KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_mg_residual64<<<gr, 128, 0, st>>>(
+        g, p->cfg.order, p->stencil_dev, rhs, u, M->r64, M->nrm + 1, M->conv));
+    KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_mg_check<<<1, 1, 0, st>>>(M->nrm, M->tol, M->conv));
+    r = M->r64;
+  }
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status mg_last_residual(kfbi_problem* p, double* rel, int* converged) {
+  MgSolver* M = p->mg;
+  unsigned long long h[3];
+  int c = 0;
+  KFBI_CUDA(p, cudaMemcpyAsync(h, M->nrm, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
+  KFBI_CUDA(p, cudaMemcpyAsync(&c, M->conv, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  KFBI_CUDA(p, cudaStreamSynchronize(p->stream));
+  double R, r;
+  memcpy(&R, &h[0], 8);
+  memcpy(&r, &h[2], 8);
+  *rel = R > 0 ? r / R : 0.0;
+  *converged = c;
+  return KFBI_OK;
+}
+
+}  // namespace kfbi

@@ -1,0 +1,1301 @@
+// Geometry set-up of one problem on the GPU (Sec. 5.1, 5.2, 5.4, 5.5):
+// node classes, grid-line intersections (DOFs), reference axes, collocation
+// stencils, inverses of the collocation matrices (eq. (cau-ls)), irregular
+// nodes, closest primary points, correction neighbour lists (eq.
+// (crc-formula)) and the least-squares trace weights.
+//
+// This translation unit is compiled with -fmad=false: every product and sum is
+// rounded on its own, so the integer decisions (classification, root
+// brackets, stencil lines, closest points, stencil radii) follow the written
+// rules operation by operation.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "kfbi_internal.cuh"
+#include "levelset.cuh"
+
+namespace kfbi {
+
+namespace {
+
+constexpr int kFlagSentinel = INT_MAX;
+
+__device__ __forceinline__ double coord(const Grid& g, int i) { return g.lo + (double)i * g.h; }
+
+__device__ __forceinline__ long long node_index(const Grid& g, const int* idx) {
+  long long n1 = g.n + 1;
+  if (g.d == 2) return (long long)idx[0] * n1 + idx[1];
+  return ((long long)idx[0] * n1 + idx[1]) * n1 + idx[2];
+}
+
+__device__ __forceinline__ void node_multi(const Grid& g, long long t, int* idx) {
+  int n1 = g.n + 1;
+  if (g.d == 2) {
+    idx[1] = (int)(t % n1);
+    idx[0] = (int)(t / n1);
+    idx[2] = 0;
+  } else {
+    idx[2] = (int)(t % n1);
+    t /= n1;
+    idx[1] = (int)(t % n1);
+    idx[0] = (int)(t / n1);
+  }
+}
+
+__device__ __forceinline__ void flag_min(int* flags, int which, int value) {
+  atomicMin(&flags[which], value);
+}
+
+// ---------------------------------------------------------------------------
+// Scan (single block): out[i] = base + sum_{j<i} in[j], out[n] = total.
+// ---------------------------------------------------------------------------
+__global__ void k_exclusive_scan(const int32_t* __restrict__ in, int32_t* __restrict__ out,
+                                 int n, int32_t base) {
+  __shared__ int32_t part[1024];
+  int t = threadIdx.x;
+  int chunk = (n + 1023) / 1024;
+  int b = t * chunk;
+  int e = min(n, b + chunk);
+  int32_t s = 0;
+  for (int i = b; i < e; ++i) s += in[i];
+  part[t] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    int32_t v = t >= o ? part[t - o] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int32_t run = base + (t ? part[t - 1] : 0);
+  for (int i = b; i < e; ++i) {
+    out[i] = run;
+    run += in[i];
+  }
+  if (t == 1023) out[n] = base + part[1023];
+}
+
+// ---------------------------------------------------------------------------
+// Classification (Sec. 5.2): inside iff H(node) < 0.
+// ---------------------------------------------------------------------------
+__global__ void k_classify(Grid g, LevelSet L, uint8_t* __restrict__ inside) {
+  long long tot = g.nodes();
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    int idx[3];
+    node_multi(g, t, idx);
+    double X[3] = {coord(g, idx[0]), coord(g, idx[1]), g.d == 3 ? coord(g, idx[2]) : 0.0};
+    inside[t] = ls_H(L, X) < 0.0 ? 1 : 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Grid-line intersections (Sec. 5.1).
+// ---------------------------------------------------------------------------
+struct LineDesc {
+  int r;          // family (direction of the lines)
+  int oa, ob;     // other axes (ascending); ob = -1 in 2D
+  long long sr, sa, sb;   // node strides of r, oa, ob
+};
+
+__device__ __forceinline__ void line_other(const Grid& g, const LineDesc& D, int li, int* ia, int* ib) {
+  if (g.d == 2) {
+    *ia = li;
+    *ib = 0;
+  } else {
+    *ia = li / (g.n + 1);
+    *ib = li % (g.n + 1);
+  }
+}
+
+// Root of H on the edge [x0, x0 + h e_r]: start at the linear interpolant,
+// Newton step, bisection whenever Newton leaves the bracket or df = 0, stop at
+// |ds| <= 1e-15 h or after 64 steps.
+__device__ double edge_root(const Grid& g, const LevelSet& L, const double* x0, int r, int j) {
+  double xa[3] = {x0[0], x0[1], x0[2]};
+  double xb[3] = {x0[0], x0[1], x0[2]};
+  xa[r] = coord(g, j);
+  xb[r] = coord(g, j + 1);
+  double ha = ls_H(L, xa), hb = ls_H(L, xb);
+  bool neg_a = ha < 0.0;
+  double h = g.h;
+  double s = h * ha / (ha - hb);
+  double lo_s = 0.0, hi_s = h;
+  for (int it = 0; it < kRootMaxIt; ++it) {
+    double X[3] = {xa[0], xa[1], xa[2]};
+    X[r] = xa[r] + s;
+    double f = ls_H(L, X);
+    double gr[3];
+    ls_grad(L, X, gr);
+    double df = gr[r];
+    bool done_zero = f == 0.0;
+    bool same = (f < 0.0) == neg_a;
+    if (same) lo_s = s; else hi_s = s;
+    double s_new = s - f / df;
+    bool bad = !((s_new > lo_s) && (s_new < hi_s)) || (df == 0.0);
+    if (bad) s_new = 0.5 * (lo_s + hi_s);
+    if (done_zero) s_new = s;
+    bool conv = done_zero || (fabs(s_new - s) <= kRootTol * h);
+    s = s_new;
+    if (conv) break;
+  }
+  return s;
+}
+
+__device__ bool crossing_point(const Grid& g, const LevelSet& L, const LineDesc& D, int ia, int ib,
+                               int j, double cos_alpha, double* X, double* nv) {
+  double x0[3] = {0.0, 0.0, 0.0};
+  x0[D.oa] = coord(g, ia);
+  if (g.d == 3) x0[D.ob] = coord(g, ib);
+  x0[D.r] = coord(g, j);
+  double s = edge_root(g, L, x0, D.r, j);
+  X[0] = x0[0];
+  X[1] = x0[1];
+  X[2] = x0[2];
+  X[D.r] = x0[D.r] + s;
+  double gr[3];
+  ls_grad(L, X, gr);
+  double nn = g.d == 2 ? gr[0] * gr[0] + gr[1] * gr[1] : gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
+  double inv = sqrt(nn);
+  nv[0] = gr[0] / inv;
+  nv[1] = gr[1] / inv;
+  nv[2] = g.d == 3 ? gr[2] / inv : 0.0;
+  return fabs(nv[D.r]) > cos_alpha;
+}
+
+__global__ void k_line_count(Grid g, LevelSet L, LineDesc D, const uint8_t* __restrict__ inside,
+                             double cos_alpha, int nlines, int32_t* __restrict__ count) {
+  int li = blockIdx.x * blockDim.x + threadIdx.x;
+  if (li >= nlines) return;
+  int ia, ib;
+  line_other(g, D, li, &ia, &ib);
+  long long base = ia * D.sa + (g.d == 3 ? ib * D.sb : 0);
+  int c = 0;
+  for (int j = 0; j < g.n; ++j) {
+    if (inside[base + j * D.sr] != inside[base + (j + 1) * D.sr]) {
+      double X[3], nv[3];
+      if (crossing_point(g, L, D, ia, ib, j, cos_alpha, X, nv)) ++c;
+    }
+  }
+  count[li] = c;
+}
+
+__global__ void k_line_fill(Grid g, LevelSet L, LineDesc D, const uint8_t* __restrict__ inside,
+                            double cos_alpha, int nlines, const int32_t* __restrict__ start,
+                            double* x0, double* x1, double* x2, double* n0, double* n1,
+                            double* n2, int32_t* family, int32_t* edge, int32_t* axis) {
+  int li = blockIdx.x * blockDim.x + threadIdx.x;
+  if (li >= nlines) return;
+  int ia, ib;
+  line_other(g, D, li, &ia, &ib);
+  long long base = ia * D.sa + (g.d == 3 ? ib * D.sb : 0);
+  int pos = start[li];
+  for (int j = 0; j < g.n; ++j) {
+    if (inside[base + j * D.sr] != inside[base + (j + 1) * D.sr]) {
+      double X[3], nv[3];
+      if (crossing_point(g, L, D, ia, ib, j, cos_alpha, X, nv)) {
+        x0[pos] = X[0];
+        x1[pos] = X[1];
+        n0[pos] = nv[0];
+        n1[pos] = nv[1];
+        if (g.d == 3) {
+          x2[pos] = X[2];
+          n2[pos] = nv[2];
+        }
+        family[pos] = D.r;
+        edge[pos] = j;
+        int m = 0;
+        double best = fabs(nv[0]);
+        for (int k = 1; k < g.d; ++k)
+          if (fabs(nv[k]) > best) {
+            best = fabs(nv[k]);
+            m = k;
+          }
+        axis[pos] = m;
+        ++pos;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Collocation stencils (Sec. 5.4).
+// ---------------------------------------------------------------------------
+struct StencilTables {
+  int npde, ndir, nneu;
+  int pde_off[kMaxPde][3];
+  int ntries;                 // 3D lattice variants (shifted / unshifted)
+  int dset[2][kMaxDir][2];
+  int nset_pos[2][kMaxNeu];   // positions of the Neumann points inside dset
+};
+__constant__ StencilTables c_st;
+
+struct DofView {
+  const double* x[3];
+  const double* n[3];
+  const int32_t* line_start[3];
+};
+
+
+// Family-`fam` DOF on the line through other-axis node indices (j, k), nearest
+// to s_pred along e_fam within 2h; ties to the lower index; -1 if none.
+__device__ int nearest_on_line(const Grid& g, const DofView& V, int fam, int j, int k,
+                               double s_pred) {
+  if (j < 0 || j > g.n) return -1;
+  int li = j;
+  if (g.d == 3) {
+    if (k < 0 || k > g.n) return -1;
+    li = j * (g.n + 1) + k;
+  }
+  const int32_t* st = V.line_start[fam];
+  int best = -1;
+  double bestd = INFINITY;
+  double win = 2.0 * g.h;
+  for (int q = st[li]; q < st[li + 1]; ++q) {
+    double dist = fabs(V.x[fam][q] - s_pred);
+    if (dist <= win && dist < bestd) {
+      best = q;
+      bestd = dist;
+    }
+  }
+  return best;
+}
+
+__global__ void k_stencils(Grid g, int order, double cos_alpha, DofView V, int nb,
+                           const int32_t* __restrict__ axis, int32_t* __restrict__ pde_node,
+                           int32_t* __restrict__ dir_idx, int32_t* __restrict__ neu_idx,
+                           int32_t* __restrict__ st_axis, int* flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  const int d = g.d;
+  double p[3] = {V.x[0][i], V.x[1][i], d == 3 ? V.x[2][i] : 0.0};
+  double nv[3] = {V.n[0][i], V.n[1][i], d == 3 ? V.n[2][i] : 0.0};
+  int n0[3] = {0, 0, 0};
+  for (int k = 0; k < d; ++k) n0[k] = (int)floor((p[k] - g.lo) / g.h + 0.5);
+  for (int s = 0; s < c_st.npde; ++s) {
+    int idx[3] = {n0[0] + c_st.pde_off[s][0], n0[1] + c_st.pde_off[s][1],
+                  n0[2] + c_st.pde_off[s][2]};
+    bool ok = true;
+    for (int k = 0; k < d; ++k) ok = ok && idx[k] >= 0 && idx[k] <= g.n;
+    if (!ok) {
+      flag_min(flags, kFlagOutOfBox, i + 1);
+      return;
+    }
+    pde_node[i * c_st.npde + s] = (int32_t)node_index(g, idx);
+  }
+  // reference axes to try: m first, then the others by decreasing |n_k| with |n_k| > cos(alpha)
+  int m0 = axis[i];
+  int axes[3];
+  int na = 0;
+  axes[na++] = m0;
+  {
+    int rest[2], nr = 0;
+    for (int k = 0; k < d; ++k)
+      if (k != m0 && fabs(nv[k]) > cos_alpha) rest[nr++] = k;
+    if (nr == 2 && (fabs(nv[rest[1]]) > fabs(nv[rest[0]]))) {
+      int t = rest[0];
+      rest[0] = rest[1];
+      rest[1] = t;
+    }
+    for (int q = 0; q < nr; ++q) axes[na++] = rest[q];
+  }
+  for (int ai = 0; ai < na; ++ai) {
+    int m = axes[ai];
+    if (d == 2) {
+      int t = 1 - m;
+      double kap = (p[t] - g.lo) / g.h;
+      int j0 = (int)floor(kap + 0.5);
+      int cand[9];
+      double key[9];
+      for (int c = 0; c < 9; ++c) {
+        cand[c] = j0 - 4 + c;
+        key[c] = fabs((double)cand[c] - kap);
+      }
+      for (int a = 1; a < 9; ++a) {   // insertion sort by (key, index)
+        int cv = cand[a];
+        double kv = key[a];
+        int b = a - 1;
+        while (b >= 0 && (key[b] > kv || (key[b] == kv && cand[b] > cv))) {
+          cand[b + 1] = cand[b];
+          key[b + 1] = key[b];
+          --b;
+        }
+        cand[b + 1] = cv;
+        key[b + 1] = kv;
+      }
+      int found[kMaxDir];
+      int nf = 0;
+      for (int c = 0; c < 9 && nf < c_st.ndir; ++c) {
+        double xt = g.lo + (double)cand[c] * g.h;
+        double s_pred = p[m] - nv[t] * (xt - p[t]) / nv[m];
+        int q = nearest_on_line(g, V, m, cand[c], 0, s_pred);
+        if (q >= 0) found[nf++] = q;
+      }
+      if (nf == c_st.ndir) {
+        for (int s = 0; s < c_st.ndir; ++s) dir_idx[i * c_st.ndir + s] = found[s];
+        for (int s = 0; s < c_st.nneu; ++s) neu_idx[i * c_st.nneu + s] = found[s];
+        st_axis[i] = m;
+        return;
+      }
+    } else {
+      int t1 = m == 0 ? 1 : 0;
+      int t2 = m == 2 ? 1 : 2;
+      double k1 = (p[t1] - g.lo) / g.h;
+      double k2 = (p[t2] - g.lo) / g.h;
+      int j0 = (int)floor(k1 + 0.5);
+      int l0 = (int)floor(k2 + 0.5);
+      int s1 = k1 >= (double)j0 ? 1 : -1;
+      int s2 = k2 >= (double)l0 ? 1 : -1;
+      const int ori[4][2] = {{s1, s2}, {-s1, s2}, {s1, -s2}, {-s1, -s2}};
+      for (int tv = 0; tv < c_st.ntries; ++tv) {
+        for (int o = 0; o < 4; ++o) {
+          int found[kMaxDir];
+          bool ok = true;
+          for (int s = 0; s < c_st.ndir; ++s) {
+            int j = j0 + ori[o][0] * c_st.dset[tv][s][0];
+            int k = l0 + ori[o][1] * c_st.dset[tv][s][1];
+            double x1 = g.lo + (double)j * g.h;
+            double x2 = g.lo + (double)k * g.h;
+            double s_pred = p[m] - (nv[t1] * (x1 - p[t1]) + nv[t2] * (x2 - p[t2])) / nv[m];
+            int q = nearest_on_line(g, V, m, j, k, s_pred);
+            if (q < 0) {
+              ok = false;
+              break;
+            }
+            found[s] = q;
+          }
+          if (ok) {
+            for (int s = 0; s < c_st.ndir; ++s) dir_idx[i * c_st.ndir + s] = found[s];
+            for (int s = 0; s < c_st.nneu; ++s)
+              neu_idx[i * c_st.nneu + s] = found[c_st.nset_pos[tv][s]];
+            st_axis[i] = m;
+            return;
+          }
+        }
+      }
+    }
+  }
+  flag_min(flags, kFlagGeometry, i + 1);
+  st_axis[i] = -1;
+}
+
+// ---------------------------------------------------------------------------
+// Monomials in scaled coordinates (graded-lexicographic order).
+// ---------------------------------------------------------------------------
+__constant__ Exponents c_exp;
+
+__device__ __forceinline__ void powers(const double* xi, int d, double pw[3][5]) {
+  for (int k = 0; k < 3; ++k) {
+    double v = k < d ? xi[k] : 0.0;
+    pw[k][0] = 1.0;
+    pw[k][1] = v;
+    pw[k][2] = v * v;
+    pw[k][3] = pw[k][2] * v;
+    pw[k][4] = pw[k][3] * v;
+  }
+}
+
+__device__ __forceinline__ double mono(const double pw[3][5], int e) {
+  return pw[0][c_exp.e[e][0]] * pw[1][c_exp.e[e][1]] * pw[2][c_exp.e[e][2]];
+}
+
+__device__ __forceinline__ double mono_d(const double pw[3][5], int e, int k) {
+  int ek = c_exp.e[e][k];
+  if (ek == 0) return 0.0;
+  double v = (double)ek * pw[k][ek - 1];
+  for (int j = 0; j < 3; ++j)
+    if (j != k) v = v * pw[j][c_exp.e[e][j]];
+  return v;
+}
+
+__device__ __forceinline__ double mono_lap(const double pw[3][5], int e, int d) {
+  double tot = 0.0;
+  for (int k = 0; k < d; ++k) {
+    int ek = c_exp.e[e][k];
+    if (ek < 2) continue;
+    double v = (double)(ek * (ek - 1)) * pw[k][ek - 2];
+    for (int j = 0; j < 3; ++j)
+      if (j != k) v = v * pw[j][c_exp.e[e][j]];
+    tot = tot + v;
+  }
+  return tot;
+}
+
+// ---------------------------------------------------------------------------
+// Warp Householder QR of a column-major m x n matrix in shared memory.
+// R: upper triangle of A plus rdiag; reflector v_k in A[k.., k]; vn2[k] = |v_k|^2.
+// ---------------------------------------------------------------------------
+__device__ bool warp_householder(double* A, int lda, int m, int n, double* rdiag, double* vn2) {
+  const int lane = threadIdx.x & 31;
+  bool ok = true;
+  for (int k = 0; k < n; ++k) {
+    double* ak = A + (size_t)k * lda;
+    double s = 0.0;
+    for (int i = k + lane; i < m; i += 32) s += ak[i] * ak[i];
+    s = warp_sum(s);
+    double akk = ak[k];
+    double nrm = sqrt(s);
+    double alpha = akk >= 0.0 ? -nrm : nrm;
+    double vk = akk - alpha;
+    double vnorm2 = s - akk * akk + vk * vk;
+    __syncwarp();
+    if (lane == 0) {
+      ak[k] = vk;
+      rdiag[k] = alpha;
+      vn2[k] = (nrm == 0.0) ? 0.0 : vnorm2;
+    }
+    __syncwarp();
+    if (!(nrm > 0.0) || !(vnorm2 > 0.0)) {
+      ok = false;
+      continue;
+    }
+    for (int j = k + 1; j < n; ++j) {
+      double* aj = A + (size_t)j * lda;
+      double t = 0.0;
+      for (int i = k + lane; i < m; i += 32) t += ak[i] * aj[i];
+      t = warp_sum(t);
+      double f = 2.0 * t / vnorm2;
+      for (int i = k + lane; i < m; i += 32) aj[i] -= f * ak[i];
+      __syncwarp();
+    }
+  }
+  return ok;
+}
+
+// y <- H_k y for k = n-1..0 (y = Q y) or k = 0..n-1 (y = Q^T y).
+__device__ void warp_apply_q(const double* A, int lda, int m, int n, const double* vn2, double* y,
+                             bool transpose) {
+  const int lane = threadIdx.x & 31;
+  for (int kk = 0; kk < n; ++kk) {
+    int k = transpose ? kk : n - 1 - kk;
+    if (!(vn2[k] > 0.0)) continue;
+    const double* ak = A + (size_t)k * lda;
+    double t = 0.0;
+    for (int i = k + lane; i < m; i += 32) t += ak[i] * y[i];
+    t = warp_sum(t);
+    double f = 2.0 * t / vn2[k];
+    __syncwarp();
+    for (int i = k + lane; i < m; i += 32) y[i] -= f * ak[i];
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Collocation matrices M (eq. (cau-appro), rows scaled to O(1)) and M^{-1}.
+// One warp per primary point.
+// ---------------------------------------------------------------------------
+__global__ void k_collocation_factor(Grid g, double kt, DofView V, int nb,
+                                     const int32_t* __restrict__ pde_node,
+                                     const int32_t* __restrict__ dir_idx,
+                                     const int32_t* __restrict__ neu_idx,
+                                     double* __restrict__ minv, int* flags) {
+  extern __shared__ double sm[];
+  const int n = c_exp.n;
+  const int lda = n + 1;
+  double* A = sm;                       // n x n, column-major, lda
+  double* B = A + (size_t)lda * n;      // n x n, column-major, lda
+  double* rdiag = B + (size_t)lda * n;
+  double* vn2 = rdiag + n;
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x;
+  if (i >= nb) return;
+  const int d = g.d;
+  double p[3] = {V.x[0][i], V.x[1][i], d == 3 ? V.x[2][i] : 0.0};
+  const int npde = c_st.npde, ndir = c_st.ndir;
+  for (int r = lane; r < n; r += 32) {
+    double xi[3] = {0.0, 0.0, 0.0};
+    double nq[3] = {0.0, 0.0, 0.0};
+    int kind;
+    if (r < npde) {
+      long long t = pde_node[i * npde + r];
+      int idx[3];
+      node_multi(g, t, idx);
+      for (int k = 0; k < d; ++k) xi[k] = (coord(g, idx[k]) - p[k]) / g.h;
+      kind = 0;
+    } else if (r < npde + ndir) {
+      int q = dir_idx[i * ndir + (r - npde)];
+      for (int k = 0; k < d; ++k) xi[k] = (V.x[k][q] - p[k]) / g.h;
+      kind = 1;
+    } else {
+      int q = neu_idx[i * c_st.nneu + (r - npde - ndir)];
+      for (int k = 0; k < d; ++k) {
+        xi[k] = (V.x[k][q] - p[k]) / g.h;
+        nq[k] = V.n[k][q];
+      }
+      kind = 2;
+    }
+    double pw[3][5];
+    powers(xi, d, pw);
+    for (int e = 0; e < n; ++e) {
+      double v;
+      if (kind == 0) {
+        v = mono_lap(pw, e, d) - kt * g.h * g.h * mono(pw, e);
+      } else if (kind == 1) {
+        v = mono(pw, e);
+      } else {
+        v = nq[0] * mono_d(pw, e, 0) + nq[1] * mono_d(pw, e, 1);
+        if (d == 3) v = v + nq[2] * mono_d(pw, e, 2);
+      }
+      A[(size_t)e * lda + r] = v;
+    }
+  }
+  __syncwarp();
+  // ||M||_1
+  double colmax = 0.0;
+  for (int e = lane; e < n; e += 32) {
+    double s = 0.0;
+    for (int r = 0; r < n; ++r) s += fabs(A[(size_t)e * lda + r]);
+    colmax = fmax(colmax, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) colmax = fmax(colmax, __shfl_xor_sync(0xffffffffu, colmax, o));
+  bool ok = warp_householder(A, lda, n, n, rdiag, vn2);
+  // B = Q^T I
+  for (int c = 0; c < n; ++c)
+    for (int r = lane; r < n; r += 32) B[(size_t)c * lda + r] = (r == c) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int c = 0; c < n; ++c) warp_apply_q(A, lda, n, n, vn2, B + (size_t)c * lda, true);
+  // back substitution R X = B, one column per lane
+  double invmax = 0.0;
+  for (int c = lane; c < n; c += 32) {
+    double* bc = B + (size_t)c * lda;
+    for (int r = n - 1; r >= 0; --r) {
+      double acc = bc[r];
+      for (int j = r + 1; j < n; ++j) acc -= A[(size_t)j * lda + r] * bc[j];
+      bc[r] = acc / rdiag[r];
+    }
+  }
+  __syncwarp();
+  // ||M^{-1}||_1 and output (row-major M^{-1}[k][j] = X[k][j], X column j = B col j)
+  for (int c = lane; c < n; c += 32) {
+    double s = 0.0;
+    for (int r = 0; r < n; ++r) s += fabs(B[(size_t)c * lda + r]);
+    invmax = fmax(invmax, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) invmax = fmax(invmax, __shfl_xor_sync(0xffffffffu, invmax, o));
+  double* out = minv + (size_t)i * n * n;
+  for (int t = lane; t < n * n; t += 32) {
+    int k = t / n, j = t % n;
+    out[t] = B[(size_t)j * lda + k];
+  }
+  double cond = colmax * invmax;
+  if (lane == 0 && (!ok || !(cond < 1e10))) flag_min(flags, kFlagSingular, i + 1);
+}
+
+// ---------------------------------------------------------------------------
+// Irregular nodes (Sec. 5.2).
+// ---------------------------------------------------------------------------
+struct NbTable {
+  int count;
+  int off[kMaxNeighbours][3];
+};
+__constant__ NbTable c_nb;
+
+__global__ void k_irregular_flags(Grid g, const uint8_t* __restrict__ inside,
+                                  uint8_t* __restrict__ flag) {
+  long long tot = g.nodes();
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    int idx[3];
+    node_multi(g, t, idx);
+    bool interior = true;
+    for (int k = 0; k < g.d; ++k) interior = interior && idx[k] >= 1 && idx[k] <= g.n - 1;
+    uint8_t f = 0;
+    if (interior) {
+      uint8_t c0 = inside[t];
+      for (int s = 0; s < c_nb.count; ++s) {
+        int q[3] = {idx[0] + c_nb.off[s][0], idx[1] + c_nb.off[s][1], idx[2] + c_nb.off[s][2]};
+        if (inside[node_index(g, q)] != c0) {
+          f = 1;
+          break;
+        }
+      }
+    }
+    flag[t] = f;
+  }
+}
+
+// rows along the last axis
+__global__ void k_row_count(Grid g, const uint8_t* __restrict__ flag, int nrows,
+                            int32_t* __restrict__ count) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  const uint8_t* f = flag + (long long)r * (g.n + 1);
+  int c = 0;
+  for (int j = 0; j <= g.n; ++j) c += f[j];
+  count[r] = c;
+}
+
+__global__ void k_row_fill(Grid g, const uint8_t* __restrict__ flag,
+                           const uint8_t* __restrict__ inside, int nrows,
+                           const int32_t* __restrict__ start, int32_t* __restrict__ lin,
+                           uint8_t* __restrict__ irr_inside, int32_t* __restrict__ map) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  long long base = (long long)r * (g.n + 1);
+  int pos = start[r];
+  for (int j = 0; j <= g.n; ++j) {
+    if (flag[base + j]) {
+      lin[pos] = (int32_t)(base + j);
+      irr_inside[pos] = inside[base + j];
+      map[base + j] = pos;
+      ++pos;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Closest primary points (Sec. 5.3, closest-point partition of unity).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int cell_of(const Grid& g, double x) {
+  int c = (int)floor((x - g.lo) / g.h);
+  return min(max(c, 0), g.n - 1);
+}
+
+__device__ __forceinline__ long long cell_index(const Grid& g, const int* c) {
+  long long n = g.n;
+  if (g.d == 2) return (long long)c[0] * n + c[1];
+  return ((long long)c[0] * n + c[1]) * n + c[2];
+}
+
+__global__ void k_cell_count(Grid g, DofView V, int nb, int32_t* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  int c[3] = {cell_of(g, V.x[0][i]), cell_of(g, V.x[1][i]), g.d == 3 ? cell_of(g, V.x[2][i]) : 0};
+  atomicAdd(&cnt[cell_index(g, c)], 1);
+}
+
+__global__ void k_cell_fill(Grid g, DofView V, int nb, const int32_t* __restrict__ start,
+                            int32_t* __restrict__ cursor, int32_t* __restrict__ items) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  int c[3] = {cell_of(g, V.x[0][i]), cell_of(g, V.x[1][i]), g.d == 3 ? cell_of(g, V.x[2][i]) : 0};
+  long long ci = cell_index(g, c);
+  int pos = atomicAdd(&cursor[ci], 1);
+  items[start[ci] + pos] = i;
+}
+
+__device__ __forceinline__ double dist2(const DofView& V, int d, int q, const double* X) {
+  double dx = X[0] - V.x[0][q];
+  double s = dx * dx;
+  double dy = X[1] - V.x[1][q];
+  s = s + dy * dy;
+  if (d == 3) {
+    double dz = X[2] - V.x[2][q];
+    s = s + dz * dz;
+  }
+  return s;
+}
+
+__global__ void k_closest(Grid g, DofView V, int nb, int nirr, const int32_t* __restrict__ lin,
+                          const int32_t* __restrict__ cstart, const int32_t* __restrict__ items,
+                          int32_t* __restrict__ owner, int* flags) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nirr) return;
+  const int K = 3;
+  int idx[3];
+  node_multi(g, lin[q], idx);
+  double X[3] = {coord(g, idx[0]), coord(g, idx[1]), g.d == 3 ? coord(g, idx[2]) : 0.0};
+  int c0[3] = {min(idx[0], g.n - 1), min(idx[1], g.n - 1), g.d == 3 ? min(idx[2], g.n - 1) : 0};
+  double eps = kTieEps * g.h * g.h;
+  double dmin = INFINITY;
+  int lo3 = g.d == 3 ? -K : 0, hi3 = g.d == 3 ? K : 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    int best = INT_MAX;
+    for (int a = -K; a <= K; ++a)
+      for (int b = -K; b <= K; ++b)
+        for (int c = lo3; c <= hi3; ++c) {
+          int cc[3] = {c0[0] + a, c0[1] + b, c0[2] + c};
+          if (cc[0] < 0 || cc[0] >= g.n || cc[1] < 0 || cc[1] >= g.n) continue;
+          if (g.d == 3 && (cc[2] < 0 || cc[2] >= g.n)) continue;
+          long long ci = cell_index(g, cc);
+          for (int t = cstart[ci]; t < cstart[ci + 1]; ++t) {
+            int i = items[t];
+            double d2 = dist2(V, g.d, i, X);
+            if (pass == 0) dmin = fmin(dmin, d2);
+            else if (d2 <= dmin + eps && i < best) best = i;
+          }
+        }
+    if (pass == 0 && !(dmin < (double)(K * K) * g.h * g.h)) {
+      // nothing certain within K h: global search
+      atomicAdd(&flags[kFlagClosestFallback], 1);
+      dmin = INFINITY;
+      for (int i = 0; i < nb; ++i) dmin = fmin(dmin, dist2(V, g.d, i, X));
+      int b2 = INT_MAX;
+      for (int i = 0; i < nb; ++i)
+        if (dist2(V, g.d, i, X) <= dmin + eps) {
+          b2 = i;
+          break;
+        }
+      owner[q] = b2;
+      return;
+    }
+    if (pass == 1) owner[q] = best;
+  }
+}
+
+// Composite rows W[j][q] = sum_k phi_k(xi_q) (M^{-1})[k][j], so that C(q) =
+// sum_j W[j][q] Q_j of the owner's collocation data.
+__global__ void k_composite(Grid g, DofView V, int nirr, const int32_t* __restrict__ lin,
+                            const int32_t* __restrict__ owner, const double* __restrict__ minv,
+                            double* __restrict__ W) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nirr) return;
+  const int n = c_exp.n;
+  int idx[3];
+  node_multi(g, lin[q], idx);
+  int i = owner[q];
+  double xi[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < g.d; ++k) xi[k] = (coord(g, idx[k]) - V.x[k][i]) / g.h;
+  double pw[3][5];
+  powers(xi, g.d, pw);
+  double ph[kMaxCoef];
+  for (int e = 0; e < n; ++e) ph[e] = mono(pw, e);
+  const double* Mi = minv + (size_t)i * n * n;
+  for (int j = 0; j < n; ++j) {
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += ph[k] * Mi[k * n + j];
+    W[(size_t)j * nirr + q] = s;
+  }
+}
+
+__global__ void k_corr_lists(Grid g, int nirr, const int32_t* __restrict__ lin,
+                             const uint8_t* __restrict__ inside, const int32_t* __restrict__ map,
+                             int32_t* __restrict__ corr_nb) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nirr) return;
+  int idx[3];
+  node_multi(g, lin[q], idx);
+  uint8_t c0 = inside[lin[q]];
+  for (int s = 0; s < c_nb.count; ++s) {
+    int nq[3] = {idx[0] + c_nb.off[s][0], idx[1] + c_nb.off[s][1], idx[2] + c_nb.off[s][2]};
+    long long t = node_index(g, nq);
+    corr_nb[(size_t)s * nirr + q] = (inside[t] != c0) ? map[t] : -1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Trace stencils and weighted least-squares weights (Sec. 5.5).
+// ---------------------------------------------------------------------------
+struct TraceParams {
+  double rs2, ro2;     // squared radii in units of h
+  int win;             // window half-width (ceil(R_s) + 1)
+  int wside;           // 2 win + 1
+  int wtotal;          // wside^d
+};
+
+__device__ __forceinline__ bool trace_select(const Grid& g, const TraceParams& T, const double* p,
+                                             const int* n0, int o, bool plus,
+                                             const uint8_t* inside, const uint8_t* irr,
+                                             long long* node_out, double* xi_out, double* r2_out,
+                                             bool* across) {
+  int off[3] = {0, 0, 0};
+  int rem = o;
+  for (int k = g.d - 1; k >= 0; --k) {
+    off[k] = rem % T.wside - T.win;
+    rem /= T.wside;
+  }
+  int idx[3] = {n0[0] + off[0], n0[1] + off[1], n0[2] + off[2]};
+  for (int k = 0; k < g.d; ++k)
+    if (idx[k] < 0 || idx[k] > g.n) return false;
+  double xi[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < g.d; ++k) xi[k] = (coord(g, idx[k]) - p[k]) / g.h;
+  double r2 = xi[0] * xi[0];
+  r2 = r2 + xi[1] * xi[1];
+  if (g.d == 3) r2 = r2 + xi[2] * xi[2];
+  long long t = node_index(g, idx);
+  bool ins = inside[t] != 0;
+  bool same = plus ? ins : !ins;
+  bool keep = (same && r2 <= T.rs2) || (!same && irr[t] && r2 <= T.ro2);
+  if (!keep) return false;
+  *node_out = t;
+  xi_out[0] = xi[0];
+  xi_out[1] = xi[1];
+  xi_out[2] = xi[2];
+  *r2_out = r2;
+  *across = !same;
+  return true;
+}
+
+__global__ void k_trace_count(Grid g, TraceParams T, DofView V, int nb,
+                              const uint8_t* __restrict__ inside, const uint8_t* __restrict__ irr,
+                              int32_t* __restrict__ count) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * nb) return;
+  int side = t / nb, i = t % nb;
+  double p[3] = {V.x[0][i], V.x[1][i], g.d == 3 ? V.x[2][i] : 0.0};
+  int n0[3] = {0, 0, 0};
+  for (int k = 0; k < g.d; ++k) n0[k] = (int)floor((p[k] - g.lo) / g.h + 0.5);
+  int c = 0;
+  for (int o = 0; o < T.wtotal; ++o) {
+    long long node;
+    double xi[3], r2;
+    bool across;
+    if (trace_select(g, T, p, n0, o, side == 0, inside, irr, &node, xi, &r2, &across)) ++c;
+  }
+  count[t] = c;
+}
+
+// One warp per (DOF, side).  A = diag(wt) V (m x n, column-major), QR, then
+// the rows e_0^T pinv(A) diag(wt) (value) and c_n^T pinv(A) diag(wt) with
+// c_n = (0, n/h, 0...) (normal derivative).
+__global__ void k_trace_fill(Grid g, TraceParams T, DofView V, int nb,
+                             const uint8_t* __restrict__ inside, const uint8_t* __restrict__ irr,
+                             const int32_t* __restrict__ map, const int32_t* __restrict__ ptr_all,
+                             int mmax, double alpha, double beta, int32_t* __restrict__ node_out,
+                             int32_t* __restrict__ irr_out, double* __restrict__ wv_out,
+                             double* __restrict__ wn_out, double* __restrict__ w_out, int* flags) {
+  extern __shared__ double sm[];
+  const int n = c_exp.n;
+  const int lda = mmax + 1;
+  double* A = sm;                            // lda x n
+  double* y0 = A + (size_t)lda * n;          // lda
+  double* y1 = y0 + lda;                     // lda
+  double* wt = y1 + lda;                     // lda
+  double* rdiag = wt + lda;                  // n
+  double* vn2 = rdiag + n;                   // n
+  double* z = vn2 + n;                       // 2n
+  int* nodes = (int*)(z + 2 * n);            // lda ints
+  int* acr = nodes + lda;                    // lda ints
+  const int lane = threadIdx.x & 31;
+  const int t = blockIdx.x;
+  if (t >= 2 * nb) return;
+  const int side = t / nb, i = t % nb;
+  const int d = g.d;
+  double p[3] = {V.x[0][i], V.x[1][i], d == 3 ? V.x[2][i] : 0.0};
+  double nv[3] = {V.n[0][i], V.n[1][i], d == 3 ? V.n[2][i] : 0.0};
+  int n0[3] = {0, 0, 0};
+  for (int k = 0; k < d; ++k) n0[k] = (int)floor((p[k] - g.lo) / g.h + 0.5);
+  // ordered compaction of the selected window offsets
+  int m = 0;
+  for (int base = 0; base < T.wtotal; base += 32) {
+    int o = base + lane;
+    long long node = 0;
+    double xi[3] = {0.0, 0.0, 0.0}, r2 = 0.0;
+    bool across = false;
+    bool sel = o < T.wtotal &&
+               trace_select(g, T, p, n0, o, side == 0, inside, irr, &node, xi, &r2, &across);
+    unsigned ball = __ballot_sync(0xffffffffu, sel);
+    if (sel) {
+      int pos = m + __popc(ball & ((1u << lane) - 1u));
+      if (pos < mmax) {
+        nodes[pos] = (int)node;
+        acr[pos] = across ? 1 : 0;
+        double w = exp(-r2 / kTraceWeightScale);
+        wt[pos] = w;
+        double pw[3][5];
+        powers(xi, d, pw);
+        for (int e = 0; e < n; ++e) A[(size_t)e * lda + pos] = w * mono(pw, e);
+      }
+    }
+    m += __popc(ball);
+  }
+  __syncwarp();
+  m = min(m, mmax);
+  bool ok = m >= n && warp_householder(A, lda, m, n, rdiag, vn2);
+  // z0 = R^{-T} e_0, z1 = R^{-T} c_n  (forward substitution, lane 0)
+  if (lane == 0) {
+    for (int k = 0; k < n; ++k) {
+      double c0 = (k == 0) ? 1.0 : 0.0;
+      double c1 = 0.0;
+      if (k >= 1 && k <= d) c1 = nv[k - 1] / g.h;
+      double a0 = c0, a1 = c1;
+      for (int j = 0; j < k; ++j) {
+        double rjk = A[(size_t)k * lda + j];
+        a0 -= rjk * z[j];
+        a1 -= rjk * z[n + j];
+      }
+      z[k] = a0 / rdiag[k];
+      z[n + k] = a1 / rdiag[k];
+    }
+  }
+  __syncwarp();
+  for (int r = lane; r < m; r += 32) {
+    y0[r] = r < n ? z[r] : 0.0;
+    y1[r] = r < n ? z[n + r] : 0.0;
+  }
+  __syncwarp();
+  warp_apply_q(A, lda, m, n, vn2, y0, false);
+  warp_apply_q(A, lda, m, n, vn2, y1, false);
+  int off = ptr_all[t];
+  for (int r = lane; r < m; r += 32) {
+    double a = y0[r] * wt[r], b = y1[r] * wt[r];
+    int node = nodes[r];
+    node_out[off + r] = node;
+    irr_out[off + r] = acr[r] ? map[node] : -1;
+    wv_out[off + r] = a;
+    wn_out[off + r] = b;
+    w_out[off + r] = alpha * a + beta * b;
+  }
+  double rmax = 0.0, rmin = INFINITY;
+  for (int k = 0; k < n; ++k) {
+    rmax = fmax(rmax, fabs(rdiag[k]));
+    rmin = fmin(rmin, fabs(rdiag[k]));
+  }
+  if (lane == 0 && (!ok || !(rmin > 1e-10 * rmax))) flag_min(flags, kFlagTraceSingular, i + 1);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host orchestration.
+// ---------------------------------------------------------------------------
+void make_exponents(int d, int p, Exponents* out) {
+  int c = 0;
+  for (int t = 0; t <= p; ++t) {
+    if (d == 2) {
+      for (int l = t; l >= 0; --l) {
+        out->e[c][0] = (int8_t)l;
+        out->e[c][1] = (int8_t)(t - l);
+        out->e[c][2] = 0;
+        ++c;
+      }
+    } else {
+      for (int l = t; l >= 0; --l)
+        for (int m = t - l; m >= 0; --m) {
+          out->e[c][0] = (int8_t)l;
+          out->e[c][1] = (int8_t)m;
+          out->e[c][2] = (int8_t)(t - l - m);
+          ++c;
+        }
+    }
+  }
+  out->n = c;
+}
+
+static void lattice(int order, bool shifted, std::vector<std::pair<int, int>>* dset,
+                    std::vector<int>* npos) {
+  int low = (order == 4 && shifted) ? -1 : 0;
+  int top_d = order + 2 * low;
+  int top_n = order - 1 + 2 * low;
+  dset->clear();
+  npos->clear();
+  for (int a = low; a <= order; ++a)
+    for (int b = low; b <= order; ++b)
+      if (a + b <= top_d) dset->push_back({a, b});
+  for (size_t k = 0; k < dset->size(); ++k)
+    if ((*dset)[k].first + (*dset)[k].second <= top_n) npos->push_back((int)k);
+}
+
+static kfbi_status check_flags(kfbi_problem* p, const char* stage) {
+  int h[kFlagCount];
+  KFBI_CUDA(p, cudaMemcpyAsync(h, p->d_flags, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
+  KFBI_CUDA(p, cudaStreamSynchronize(p->stream));
+  if (h[kFlagOutOfBox] != kFlagSentinel)
+    return fail(p, KFBI_ERR_GEOMETRY, std::string(stage) + ": stencil of DOF " +
+                                          std::to_string(h[kFlagOutOfBox] - 1) + " leaves the box");
+  if (h[kFlagGeometry] != kFlagSentinel)
+    return fail(p, KFBI_ERR_GEOMETRY, std::string(stage) + ": no complete collocation stencil at DOF " +
+                                          std::to_string(h[kFlagGeometry] - 1));
+  if (h[kFlagSingular] != kFlagSentinel)
+    return fail(p, KFBI_ERR_SINGULAR, std::string(stage) + ": singular collocation matrix at DOF " +
+                                          std::to_string(h[kFlagSingular] - 1));
+  if (h[kFlagTraceSingular] != kFlagSentinel)
+    return fail(p, KFBI_ERR_SINGULAR, std::string(stage) + ": singular trace fit at DOF " +
+                                          std::to_string(h[kFlagTraceSingular] - 1));
+  return KFBI_OK;
+}
+
+kfbi_status build_geometry(kfbi_problem* p) {
+  const Grid g = p->g;
+  const int d = g.d, n = g.n, n1 = n + 1;
+  const long long nodes = g.nodes();
+  cudaStream_t st = p->stream;
+  LevelSet L = p->ls;
+
+  {
+    int h[kFlagCount];
+    for (int k = 0; k < kFlagCount; ++k) h[k] = kFlagSentinel;
+    h[kFlagClosestFallback] = 0;
+    KFBI_CUDA(p, dalloc(&p->d_flags, kFlagCount));
+    KFBI_CUDA(p, cudaMemcpyAsync(p->d_flags, h, sizeof(h), cudaMemcpyHostToDevice, st));
+  }
+  KFBI_CUDA(p, dalloc(&p->inside, nodes));
+  k_classify<<<div_up(nodes, 256), 256, 0, st>>>(g, L, p->inside);
+  KFBI_CUDA(p, cudaGetLastError());
+
+  // ---- DOFs: per family, count per line, scan, fill
+  const int nlines = d == 2 ? n1 : n1 * n1;
+  p->nlines = nlines;
+  int32_t* cnt = nullptr;
+  KFBI_CUDA(p, dalloc(&cnt, (size_t)nlines * d));
+  LineDesc D[3];
+  long long strides[3] = {d == 2 ? n1 : (long long)n1 * n1, d == 2 ? 1 : n1, 1};
+  for (int r = 0; r < d; ++r) {
+    D[r].r = r;
+    int o[2], no = 0;
+    for (int k = 0; k < d; ++k)
+      if (k != r) o[no++] = k;
+    D[r].oa = o[0];
+    D[r].ob = d == 3 ? o[1] : -1;
+    D[r].sr = strides[r];
+    D[r].sa = strides[o[0]];
+    D[r].sb = d == 3 ? strides[o[1]] : 0;
+    k_line_count<<<div_up(nlines, 128), 128, 0, st>>>(g, L, D[r], p->inside, p->cos_alpha,
+                                                      nlines, cnt + (size_t)r * nlines);
+    KFBI_CUDA(p, cudaGetLastError());
+  }
+  // family-by-family exclusive scans with running offsets
+  std::vector<int32_t> tot(d);
+  for (int r = 0; r < d; ++r) {
+    KFBI_CUDA(p, dalloc(&p->line_start[r], nlines + 1));
+  }
+  int32_t base = 0;
+  for (int r = 0; r < d; ++r) {
+    k_exclusive_scan<<<1, 1024, 0, st>>>(cnt + (size_t)r * nlines, p->line_start[r], nlines, base);
+    KFBI_CUDA(p, cudaGetLastError());
+    int32_t last;
+    KFBI_CUDA(p, cudaMemcpyAsync(&last, p->line_start[r] + nlines, sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, st));
+    KFBI_CUDA(p, cudaStreamSynchronize(st));
+    base = last;
+  }
+  p->nb = base;
+  if (p->nb == 0) return fail(p, KFBI_ERR_GEOMETRY, "the interface does not cross the grid");
+  const int nb = p->nb;
+  for (int k = 0; k < d; ++k) {
+    KFBI_CUDA(p, dalloc(&p->x[k], nb));
+    KFBI_CUDA(p, dalloc(&p->nrm[k], nb));
+  }
+  KFBI_CUDA(p, dalloc(&p->family, nb));
+  KFBI_CUDA(p, dalloc(&p->edge, nb));
+  KFBI_CUDA(p, dalloc(&p->axis, nb));
+  KFBI_CUDA(p, dalloc(&p->st_axis, nb));
+  for (int r = 0; r < d; ++r) {
+    k_line_fill<<<div_up(nlines, 128), 128, 0, st>>>(
+        g, L, D[r], p->inside, p->cos_alpha, nlines, p->line_start[r], p->x[0], p->x[1],
+        d == 3 ? p->x[2] : p->x[0], p->nrm[0], p->nrm[1], d == 3 ? p->nrm[2] : p->nrm[0],
+        p->family, p->edge, p->axis);
+    KFBI_CUDA(p, cudaGetLastError());
+  }
+  cudaFree(cnt);
+
+  DofView V;
+  for (int k = 0; k < 3; ++k) {
+    V.x[k] = k < d ? p->x[k] : nullptr;
+    V.n[k] = k < d ? p->nrm[k] : nullptr;
+    V.line_start[k] = k < d ? p->line_start[k] : nullptr;
+  }
+
+  // ---- stencil tables
+  StencilTables T;
+  memset(&T, 0, sizeof(T));
+  const int order = p->cfg.order;
+  if (order == 2) {
+    T.npde = 1;
+  } else if (d == 2) {
+    const int off[6][2] = {{0, 0}, {1, 0}, {-1, 0}, {0, 1}, {0, -1}, {1, 1}};
+    T.npde = 6;
+    for (int s = 0; s < 6; ++s) {
+      T.pde_off[s][0] = off[s][0];
+      T.pde_off[s][1] = off[s][1];
+    }
+  } else {
+    const int off[10][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0},
+                            {0, 0, 1}, {0, 0, -1}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
+    T.npde = 10;
+    for (int s = 0; s < 10; ++s)
+      for (int k = 0; k < 3; ++k) T.pde_off[s][k] = off[s][k];
+  }
+  if (d == 2) {
+    T.ndir = order + 1;
+    T.nneu = order;
+    T.ntries = 1;
+  } else {
+    T.ntries = order == 4 ? 2 : 1;
+    for (int tv = 0; tv < T.ntries; ++tv) {
+      std::vector<std::pair<int, int>> ds;
+      std::vector<int> np;
+      lattice(order, tv == 0, &ds, &np);
+      T.ndir = (int)ds.size();
+      T.nneu = (int)np.size();
+      for (size_t s = 0; s < ds.size(); ++s) {
+        T.dset[tv][s][0] = ds[s].first;
+        T.dset[tv][s][1] = ds[s].second;
+      }
+      for (size_t s = 0; s < np.size(); ++s) T.nset_pos[tv][s] = np[s];
+    }
+  }
+  p->npde = T.npde;
+  p->ndir = T.ndir;
+  p->nneu = T.nneu;
+  KFBI_CUDA(p, cudaMemcpyToSymbolAsync(c_st, &T, sizeof(T), 0, cudaMemcpyHostToDevice, st));
+  Exponents E;
+  make_exponents(d, order, &E);
+  p->ncoef = E.n;
+  if (p->npde + p->ndir + p->nneu != p->ncoef)
+    return fail(p, KFBI_ERR_UNSUPPORTED, "collocation system is not square");
+  KFBI_CUDA(p, cudaMemcpyToSymbolAsync(c_exp, &E, sizeof(E), 0, cudaMemcpyHostToDevice, st));
+
+  KFBI_CUDA(p, dalloc(&p->pde_node, (size_t)nb * p->npde));
+  KFBI_CUDA(p, dalloc(&p->dir_idx, (size_t)nb * p->ndir));
+  KFBI_CUDA(p, dalloc(&p->neu_idx, (size_t)nb * p->nneu));
+  k_stencils<<<div_up(nb, 128), 128, 0, st>>>(g, order, p->cos_alpha, V, nb, p->axis,
+                                               p->pde_node, p->dir_idx, p->neu_idx, p->st_axis,
+                                               p->d_flags);
+  KFBI_CUDA(p, cudaGetLastError());
+  KFBI_TRY(check_flags(p, "collocation stencils"));
+
+  const int nc = p->ncoef;
+  KFBI_CUDA(p, dalloc(&p->minv, (size_t)nb * nc * nc));
+  {
+    size_t smem = sizeof(double) * ((size_t)(nc + 1) * nc * 2 + 2 * nc);
+    // per-kernel process-wide attribute: raise it to the device maximum once
+    int dev = 0, optin = 0;
+    KFBI_CUDA(p, cudaGetDevice(&dev));
+    KFBI_CUDA(p, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    KFBI_CUDA(p, cudaFuncSetAttribute(k_collocation_factor,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    KFBI_CUDA(p, cudaFuncSetAttribute(k_trace_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      optin));
+    k_collocation_factor<<<nb, 32, smem, st>>>(g, p->kt, V, nb, p->pde_node, p->dir_idx,
+                                               p->neu_idx, p->minv, p->d_flags);
+    KFBI_CUDA(p, cudaGetLastError());
+  }
+  KFBI_TRY(check_flags(p, "collocation factor"));
+
+  // ---- irregular nodes
+  NbTable NT;
+  memset(&NT, 0, sizeof(NT));
+  {
+    int c = 0;
+    for (int a = -1; a <= 1; ++a)
+      for (int b = -1; b <= 1; ++b)
+        for (int e = (d == 3 ? -1 : 0); e <= (d == 3 ? 1 : 0); ++e) {
+          int nz = (a != 0) + (b != 0) + (e != 0);
+          if (nz == 0) continue;
+          if (order == 2 && nz > 1) continue;
+          NT.off[c][0] = a;
+          NT.off[c][1] = b;
+          NT.off[c][2] = e;
+          ++c;
+        }
+    NT.count = c;
+  }
+  p->n_nb = NT.count;
+  KFBI_CUDA(p, cudaMemcpyToSymbolAsync(c_nb, &NT, sizeof(NT), 0, cudaMemcpyHostToDevice, st));
+  KFBI_CUDA(p, dalloc(&p->irr_flag, nodes));
+  k_irregular_flags<<<div_up(nodes, 256), 256, 0, st>>>(g, p->inside, p->irr_flag);
+  KFBI_CUDA(p, cudaGetLastError());
+  const int nrows = (int)(nodes / n1);
+  int32_t *rcnt = nullptr, *rstart = nullptr, *map = nullptr;
+  KFBI_CUDA(p, dalloc(&rcnt, nrows));
+  KFBI_CUDA(p, dalloc(&rstart, nrows + 1));
+  KFBI_CUDA(p, dalloc(&map, nodes));
+  KFBI_CUDA(p, cudaMemsetAsync(map, 0xff, sizeof(int32_t) * nodes, st));
+  k_row_count<<<div_up(nrows, 128), 128, 0, st>>>(g, p->irr_flag, nrows, rcnt);
+  k_exclusive_scan<<<1, 1024, 0, st>>>(rcnt, rstart, nrows, 0);
+  int32_t nirr = 0;
+  KFBI_CUDA(p, cudaMemcpyAsync(&nirr, rstart + nrows, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  KFBI_CUDA(p, cudaStreamSynchronize(st));
+  p->nirr = nirr;
+  if (nirr == 0) return fail(p, KFBI_ERR_GEOMETRY, "no irregular nodes");
+  KFBI_CUDA(p, dalloc(&p->irr_lin, nirr));
+  KFBI_CUDA(p, dalloc(&p->irr_inside, nirr));
+  KFBI_CUDA(p, dalloc(&p->irr_owner, nirr));
+  k_row_fill<<<div_up(nrows, 128), 128, 0, st>>>(g, p->irr_flag, p->inside, nrows, rstart,
+                                                  p->irr_lin, p->irr_inside, map);
+  KFBI_CUDA(p, cudaGetLastError());
+  cudaFree(rcnt);
+  cudaFree(rstart);
+
+  // ---- closest primary points via a cell list
+  {
+    long long ncell = d == 2 ? (long long)n * n : (long long)n * n * n;
+    int32_t *ccnt = nullptr, *cstart = nullptr, *cur = nullptr, *items = nullptr;
+    KFBI_CUDA(p, dalloc(&ccnt, ncell));
+    KFBI_CUDA(p, dalloc(&cstart, ncell + 1));
+    KFBI_CUDA(p, dalloc(&cur, ncell));
+    KFBI_CUDA(p, dalloc(&items, nb));
+    KFBI_CUDA(p, cudaMemsetAsync(ccnt, 0, sizeof(int32_t) * ncell, st));
+    KFBI_CUDA(p, cudaMemsetAsync(cur, 0, sizeof(int32_t) * ncell, st));
+    k_cell_count<<<div_up(nb, 256), 256, 0, st>>>(g, V, nb, ccnt);
+    k_exclusive_scan<<<1, 1024, 0, st>>>(ccnt, cstart, (int)ncell, 0);
+    k_cell_fill<<<div_up(nb, 256), 256, 0, st>>>(g, V, nb, cstart, cur, items);
+    k_closest<<<div_up(nirr, 128), 128, 0, st>>>(g, V, nb, nirr, p->irr_lin, cstart, items,
+                                                 p->irr_owner, p->d_flags);
+    KFBI_CUDA(p, cudaGetLastError());
+    KFBI_CUDA(p, cudaStreamSynchronize(st));
+    cudaFree(ccnt);
+    cudaFree(cstart);
+    cudaFree(cur);
+    cudaFree(items);
+  }
+  KFBI_CUDA(p, dalloc(&p->irr_w, (size_t)nc * nirr));
+  k_composite<<<div_up(nirr, 128), 128, 0, st>>>(g, V, nirr, p->irr_lin, p->irr_owner, p->minv,
+                                                  p->irr_w);
+  KFBI_CUDA(p, cudaGetLastError());
+  KFBI_CUDA(p, dalloc(&p->corr_nb, (size_t)p->n_nb * nirr));
+  k_corr_lists<<<div_up(nirr, 128), 128, 0, st>>>(g, nirr, p->irr_lin, p->inside, map, p->corr_nb);
+  KFBI_CUDA(p, cudaGetLastError());
+
+  // ---- trace stencils
+  TraceParams TP;
+  double rs = order == 4 ? 4.0 : 3.0, ro = order == 4 ? 2.5 : 1.5;
+  TP.rs2 = rs * rs;
+  TP.ro2 = ro * ro;
+  TP.win = (int)std::ceil(rs) + 1;
+  TP.wside = 2 * TP.win + 1;
+  TP.wtotal = d == 2 ? TP.wside * TP.wside : TP.wside * TP.wside * TP.wside;
+  int32_t *tcnt = nullptr, *tptr = nullptr;
+  KFBI_CUDA(p, dalloc(&tcnt, 2 * nb));
+  KFBI_CUDA(p, dalloc(&tptr, 2 * nb + 1));
+  k_trace_count<<<div_up(2 * nb, 128), 128, 0, st>>>(g, TP, V, nb, p->inside, p->irr_flag, tcnt);
+  k_exclusive_scan<<<1, 1024, 0, st>>>(tcnt, tptr, 2 * nb, 0);
+  KFBI_CUDA(p, cudaGetLastError());
+  std::vector<int32_t> hptr(2 * nb + 1), hcnt(2 * nb);
+  KFBI_CUDA(p, cudaMemcpyAsync(hptr.data(), tptr, sizeof(int32_t) * (2 * nb + 1),
+                               cudaMemcpyDeviceToHost, st));
+  KFBI_CUDA(p, cudaMemcpyAsync(hcnt.data(), tcnt, sizeof(int32_t) * 2 * nb, cudaMemcpyDeviceToHost, st));
+  KFBI_CUDA(p, cudaStreamSynchronize(st));
+  int mmax = 0;
+  for (int k = 0; k < 2 * nb; ++k) mmax = std::max(mmax, hcnt[k]);
+  const int nnz_all = hptr[2 * nb];
+  int32_t *tnode = nullptr, *tirr = nullptr;
+  double *twv = nullptr, *twn = nullptr, *tw = nullptr;
+  KFBI_CUDA(p, dalloc(&tnode, nnz_all));
+  KFBI_CUDA(p, dalloc(&tirr, nnz_all));
+  KFBI_CUDA(p, dalloc(&twv, nnz_all));
+  KFBI_CUDA(p, dalloc(&twn, nnz_all));
+  KFBI_CUDA(p, dalloc(&tw, nnz_all));
+  {
+    double alpha = p->cfg.kind == KFBI_DIRICHLET_INTERIOR ? 0.5 : 0.0;
+    double beta = p->cfg.kind == KFBI_DIRICHLET_INTERIOR ? 0.0 : 0.5;
+    const int lda = mmax + 1;
+    size_t smem = sizeof(double) * ((size_t)lda * nc + 3 * (size_t)lda + 4 * nc) +
+                  sizeof(int) * 2 * (size_t)lda;
+    int dev = 0, optin = 0;
+    KFBI_CUDA(p, cudaGetDevice(&dev));
+    KFBI_CUDA(p, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (smem > (size_t)optin)
+      return fail(p, KFBI_ERR_UNSUPPORTED, "trace stencil too large for shared memory");
+    k_trace_fill<<<2 * nb, 32, smem, st>>>(g, TP, V, nb, p->inside, p->irr_flag, map, tptr, mmax,
+                                           alpha, beta, tnode, tirr, twv, twn, tw, p->d_flags);
+    KFBI_CUDA(p, cudaGetLastError());
+  }
+  KFBI_TRY(check_flags(p, "trace weights"));
+  // split the all-sides CSR into the two per-side CSRs (pointers into one allocation)
+  for (int s = 0; s < 2; ++s) {
+    TraceCSR& c = p->tr[s];
+    KFBI_CUDA(p, dalloc(&c.ptr, nb + 1));
+    std::vector<int32_t> sp(nb + 1);
+    int32_t b0 = hptr[(size_t)s * nb];
+    for (int k = 0; k <= nb; ++k) sp[k] = hptr[(size_t)s * nb + k] - b0;
+    KFBI_CUDA(p, cudaMemcpyAsync(c.ptr, sp.data(), sizeof(int32_t) * (nb + 1),
+                                 cudaMemcpyHostToDevice, st));
+    c.nnz = sp[nb];
+    c.node = tnode + b0;
+    c.irr = tirr + b0;
+    c.wv = twv + b0;
+    c.wn = twn + b0;
+    c.w = tw + b0;
+  }
+  KFBI_CUDA(p, cudaStreamSynchronize(st));
+  cudaFree(tcnt);
+  cudaFree(tptr);
+  cudaFree(map);
+  return KFBI_OK;
+}
+
+}  // namespace kfbi

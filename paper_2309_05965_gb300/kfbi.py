@@ -1,0 +1,294 @@
+"""Thin Python binding of the C ABI in ``include/kfbi.h``.
+
+Argument marshalling only: every computation runs in ``libkfbi.so`` on the GPU.
+Device arrays are ``torch`` CUDA tensors (their ``data_ptr()`` is passed); the
+CUDA stream is torch's current stream unless given.  There is no CPU path: if
+the shared library has not been built or cannot be loaded, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkfbi.so")
+
+KFBI_OK = 0
+STATUS_NAMES = {0: "KFBI_OK", 1: "KFBI_ERR_ARG", 2: "KFBI_ERR_GEOMETRY", 3: "KFBI_ERR_SINGULAR",
+                4: "KFBI_ERR_NOT_CONVERGED", 5: "KFBI_ERR_NONFINITE", 6: "KFBI_ERR_TIMEOUT",
+                7: "KFBI_ERR_CUDA", 8: "KFBI_ERR_UNSUPPORTED"}
+LS_MAX_PARAMS = 64
+
+DIRICHLET_INTERIOR = 0
+INTERFACE_MU = 1
+BOX_DST = 0
+BOX_MG = 1
+FP64 = 0
+MIXED = 1
+
+
+class KfbiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class LevelSet(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n_params", ctypes.c_int),
+                ("p", ctypes.c_double * LS_MAX_PARAMS)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("lo", ctypes.c_double),
+                ("hi", ctypes.c_double), ("order", ctypes.c_int), ("kind", ctypes.c_int),
+                ("sigma_in", ctypes.c_double), ("sigma_out", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("box_solver", ctypes.c_int),
+                ("precision", ctypes.c_int), ("cos_alpha", ctypes.c_double),
+                ("box_rtol", ctypes.c_double), ("box_max_iters", ctypes.c_int)]
+
+
+class Data(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in
+                ("g1", "g2", "f_in", "f_out", "lapf_in", "lapf_out", "g_b")]
+
+
+class GmresOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("restart", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("x0", ctypes.c_void_p)]
+
+
+class GmresInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("t_ms", ctypes.c_double * 8)]
+
+
+# name -> (argtypes) ; all return kfbi_status except kfbi_last_error
+_P = ctypes.c_void_p
+_I = ctypes.POINTER(ctypes.c_int)
+SIGNATURES = {
+    "kfbi_create_problem": [ctypes.POINTER(Config), ctypes.POINTER(LevelSet), _P,
+                            ctypes.POINTER(ctypes.c_void_p)],
+    "kfbi_destroy_problem": [_P],
+    "kfbi_sizes": [_P, _I, _I, _I],
+    "kfbi_num_dofs": [_P, _I],
+    "kfbi_dof_points": [_P, _P, _P],
+    "kfbi_dof_info": [_P, _P, _P, _P],
+    "kfbi_stencil_sizes": [_P, _I, _I, _I],
+    "kfbi_collocation_stencils": [_P, _P, _P, _P],
+    "kfbi_inside_mask": [_P, _P],
+    "kfbi_irregular_nodes": [_P, _P, _P],
+    "kfbi_collocation_fit": [_P, _P, _P, _P, _P],
+    "kfbi_correction_values": [_P, _P, _P, _P, _P],
+    "kfbi_corrected_rhs": [_P, _P, ctypes.POINTER(Data), _P],
+    "kfbi_box_solve": [_P, _P, _P],
+    "kfbi_traces": [_P, _P, _P, _P, _P, _P, _P],
+    "kfbi_apply_operator": [_P, _P, _P],
+    "kfbi_bie_rhs": [_P, ctypes.POINTER(Data), _P],
+    "kfbi_gmres_solve": [_P, ctypes.POINTER(Data), ctypes.POINTER(GmresOpts), _P,
+                         ctypes.POINTER(GmresInfo)],
+    "kfbi_evaluate": [_P, ctypes.POINTER(Data), _P, _P],
+    "kfbi_launch_counts": [_P, _P, ctypes.c_int],
+    "kfbi_profile_enable": [_P, ctypes.c_int],
+    "kfbi_profile_read": [_P, _P, _P],
+}
+
+KERNEL_CLASSES = ["correction", "rhs", "dst", "residual", "mg", "trace", "gmres", "other"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libkfbi.so (raises if it is missing: build it with build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: the CUDA library must be built "
+                           "(paper_2309_05965_gb300.build.build()) — there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    for name, args in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.kfbi_last_error.argtypes = [_P]
+    lib.kfbi_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device arrays must be CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("device arrays must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(status: int, handle=None):
+    if status != KFBI_OK:
+        msg = load().kfbi_last_error(handle)
+        raise KfbiError(status, msg.decode() if msg else "")
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ---- the C entry points under their own names ------------------------------
+
+def kfbi_create_problem(cfg: Config, ls: LevelSet, stream=None):
+    h = ctypes.c_void_p()
+    _check(load().kfbi_create_problem(ctypes.byref(cfg), ctypes.byref(ls),
+                                      _stream_handle(stream), ctypes.byref(h)))
+    return h
+
+
+def kfbi_destroy_problem(h):
+    _check(load().kfbi_destroy_problem(h))
+
+
+def kfbi_sizes(h):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().kfbi_sizes(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), h)
+    return a.value, b.value, c.value
+
+
+def kfbi_stencil_sizes(h):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().kfbi_stencil_sizes(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), h)
+    return a.value, b.value, c.value
+
+
+def kfbi_dof_points(h, xyz, normals):
+    _check(load().kfbi_dof_points(h, _ptr(xyz), _ptr(normals)), h)
+
+
+def kfbi_dof_info(h, family, axis, stencil_axis):
+    _check(load().kfbi_dof_info(h, _ptr(family), _ptr(axis), _ptr(stencil_axis)), h)
+
+
+def kfbi_collocation_stencils(h, pde, dirs, neus):
+    _check(load().kfbi_collocation_stencils(h, _ptr(pde), _ptr(dirs), _ptr(neus)), h)
+
+
+def kfbi_inside_mask(h, mask):
+    _check(load().kfbi_inside_mask(h, _ptr(mask)), h)
+
+
+def kfbi_irregular_nodes(h, lin, owner):
+    _check(load().kfbi_irregular_nodes(h, _ptr(lin), _ptr(owner)), h)
+
+
+def kfbi_collocation_fit(h, a, b, ftilde, coef):
+    _check(load().kfbi_collocation_fit(h, _ptr(a), _ptr(b), _ptr(ftilde), _ptr(coef)), h)
+
+
+def kfbi_correction_values(h, a, b, ftilde, cvals):
+    _check(load().kfbi_correction_values(h, _ptr(a), _ptr(b), _ptr(ftilde), _ptr(cvals)), h)
+
+
+def make_data(g1=None, g2=None, f_in=None, f_out=None, lapf_in=None, lapf_out=None, g_b=None):
+    d = Data()
+    for k, v in (("g1", g1), ("g2", g2), ("f_in", f_in), ("f_out", f_out),
+                 ("lapf_in", lapf_in), ("lapf_out", lapf_out), ("g_b", g_b)):
+        p = _ptr(v)
+        setattr(d, k, p.value if p is not None else None)
+    return d
+
+
+def kfbi_corrected_rhs(h, cvals, data, rhs):
+    _check(load().kfbi_corrected_rhs(h, _ptr(cvals), ctypes.byref(data) if data else None,
+                                     _ptr(rhs)), h)
+
+
+def kfbi_box_solve(h, rhs, u):
+    _check(load().kfbi_box_solve(h, _ptr(rhs), _ptr(u)), h)
+
+
+def kfbi_traces(h, u, cvals, vp=None, vm=None, dp=None, dm=None):
+    _check(load().kfbi_traces(h, _ptr(u), _ptr(cvals), _ptr(vp), _ptr(vm), _ptr(dp), _ptr(dm)), h)
+
+
+def kfbi_apply_operator(h, x, y):
+    _check(load().kfbi_apply_operator(h, _ptr(x), _ptr(y)), h)
+
+
+def kfbi_bie_rhs(h, data, b):
+    _check(load().kfbi_bie_rhs(h, ctypes.byref(data), _ptr(b)), h)
+
+
+def kfbi_gmres_solve(h, data, opts: GmresOpts, density):
+    info = GmresInfo()
+    _check(load().kfbi_gmres_solve(h, ctypes.byref(data), ctypes.byref(opts), _ptr(density),
+                                   ctypes.byref(info)), h)
+    return info
+
+
+def kfbi_evaluate(h, data, density, u):
+    _check(load().kfbi_evaluate(h, ctypes.byref(data), _ptr(density), _ptr(u)), h)
+
+
+def kfbi_launch_counts(h, reset=False):
+    arr = (ctypes.c_int64 * len(KERNEL_CLASSES))()
+    _check(load().kfbi_launch_counts(h, ctypes.cast(arr, ctypes.c_void_p), int(reset)), h)
+    return dict(zip(KERNEL_CLASSES, list(arr)))
+
+
+def kfbi_profile_enable(h, on=True):
+    _check(load().kfbi_profile_enable(h, int(on)), h)
+
+
+def kfbi_profile_read(h):
+    ms = (ctypes.c_double * len(KERNEL_CLASSES))()
+    cnt = (ctypes.c_int64 * len(KERNEL_CLASSES))()
+    _check(load().kfbi_profile_read(h, ctypes.cast(ms, ctypes.c_void_p),
+                                    ctypes.cast(cnt, ctypes.c_void_p)), h)
+    return {k: (m, c) for k, m, c in zip(KERNEL_CLASSES, list(ms), list(cnt))}
+
+
+# ---- convenience object ------------------------------------------------------
+
+class Problem:
+    """Owns one kfbi_problem.  Sizes and shapes are read back at creation."""
+
+    def __init__(self, dim, n, lo, hi, ls_kind, ls_params, kind, sigma_in=1.0, sigma_out=1.0,
+                 kappa=0.0, order=4, box_solver=BOX_DST, precision=FP64, cos_alpha=0.0,
+                 box_rtol=0.0, box_max_iters=0, stream=None):
+        cfg = Config(dim=dim, n=n, lo=lo, hi=hi, order=order, kind=kind, sigma_in=sigma_in,
+                     sigma_out=sigma_out, kappa=kappa, box_solver=box_solver,
+                     precision=precision, cos_alpha=cos_alpha, box_rtol=box_rtol,
+                     box_max_iters=box_max_iters)
+        ls = LevelSet(kind=ls_kind, n_params=len(ls_params))
+        for i, v in enumerate(ls_params):
+            ls.p[i] = float(v)
+        self.cfg = cfg
+        self.dim, self.n = dim, n
+        self.handle = kfbi_create_problem(cfg, ls, stream)
+        self.nb, self.nirr, self.ncoef = kfbi_sizes(self.handle)
+        self.npde, self.ndir, self.nneu = kfbi_stencil_sizes(self.handle)
+
+    @classmethod
+    def from_workload(cls, w, box_solver=BOX_DST, precision=FP64, **kw):
+        return cls(w.dim, w.n, w.lo, w.hi, w.ls_kind, w.ls_params, w.kind,
+                   sigma_in=w.sigma_in, sigma_out=w.sigma_out, kappa=w.kappa, order=w.order,
+                   box_solver=box_solver, precision=precision,
+                   cos_alpha=w.cos_alpha or 0.0, **kw)
+
+    def close(self):
+        if self.handle is not None:
+            kfbi_destroy_problem(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def grid_shape(self):
+        return (self.n + 1,) * self.dim
