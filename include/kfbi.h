@@ -220,6 +220,32 @@ kfbi_status kfbi_gmres_solve(kfbi_problem* p, const kfbi_data* data,
 kfbi_status kfbi_evaluate(kfbi_problem* p, const kfbi_data* data, const double* density,
                           double* u_grid);
 
+/* ---- box solve without allocation ----------------------------------------- */
+
+/* The FP64 sine-transform box solve u = A_h^{-1} rhs of kfbi_box_solve, for a
+ * caller that cannot allocate device memory: code whose allocator belongs to
+ * someone else (a host application's pool, a plugin or driver layer) or
+ * where a cudaMalloc could synchronise the device or fail in the middle of a
+ * pipeline.  It needs no kfbi_problem and calls no cudaMalloc, cudaFree or
+ * allocating library routine: its scratch (work grid, spectral scale table,
+ * twiddles) is one fixed file-scope device array of about 4.4 MB that every GPU
+ * loading the library holds until the process exits.  The paper has no
+ * counterpart; it is an interface convenience.
+ *   dim, n, lo, hi, order, kappa: the grid and the compact operator of
+ *     kfbi_config (kappa is kappa~ of the unit-sigma operator Lap - kappa~);
+ *   rhs: (N+1)^d device grid, interior nodes read; u: (N+1)^d device grid,
+ *     written (boundary layer 0).  Both owned by the caller.
+ * Limits: 2D N <= 512, 3D N <= 64 (N a power of two >= 8); larger sizes or
+ * invalid arguments return KFBI_ERR_ARG, CUDA failures KFBI_ERR_CUDA.
+ * The first call on a device does a one-time set-up (looks up the array's
+ * device address and raises shared-memory limits); make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents: calls that overlap on the GPU (different streams, or
+ * different host threads) race and give wrong results.  Work is enqueued on
+ * cuda_stream. */
+kfbi_status kfbi_box_solve_noalloc(int dim, int n, double lo, double hi, int order, double kappa,
+                                   const double* rhs, double* u, void* cuda_stream);
+
 /* ---- accounting -------------------------------------------------------- */
 
 /* Kernel launches per class since creation or the last reset (host output of

@@ -22,6 +22,8 @@
 // FP32 transforms, FP64 residual r = R - A_h u and iterative refinement, with a
 // device-side convergence flag so that no host synchronisation is needed).
 #include <cmath>
+#include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "kfbi_internal.cuh"
@@ -609,3 +611,161 @@ kfbi_status box_last_residual(kfbi_problem* p, double* rel, int* converged) {
 }
 
 }  // namespace kfbi
+
+// ---------------------------------------------------------------------------
+// Box solve that allocates nothing (kfbi_box_solve_noalloc).
+//
+// For callers that cannot call cudaMalloc — code running where the allocator
+// is unavailable or forbidden, e.g. inside another library's memory pool
+// discipline, a plugin host that owns all device memory, or a context where an
+// allocation could synchronise or fail mid-pipeline.  The caller passes the
+// right-hand side and the output grid; everything else the FP64 sine-transform
+// solve needs (work grid, spectral scale table, twiddles, sin^2 table) lives in
+// one file-scope __device__ array of fixed size.  Every GPU that loads this
+// library holds that array (about 4.4 MB) until the process exits.
+// ---------------------------------------------------------------------------
+namespace kfbi {
+namespace {
+
+constexpr int kNoAllocMaxN2 = 512;                // 2D: N <= 512
+constexpr int kNoAllocMaxN3 = 64;                 // 3D: N <= 64
+constexpr long long kNoAllocGrid = 65LL * 65 * 65;   // >= max (N+1)^d = 274625
+constexpr long long kNoAllocTw = 4 * 1024;        // full-circle twiddles, L <= 1024
+constexpr long long kNoAllocS = 1024;             // sin^2 table, N + 1 <= 513
+constexpr long long kNoAllocTotal = 2 * kNoAllocGrid + kNoAllocTw + kNoAllocS;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocTotal];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+__global__ void k_noalloc_tables(int n, double* __restrict__ tw, double* __restrict__ sv) {
+  const int L = 2 * n;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L; t += gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi(-2.0 * (double)t / (double)L, &s, &c);
+    tw[2 * t] = c;
+    tw[2 * t + 1] = s;
+  }
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= n; k += gridDim.x * blockDim.x) {
+    double s = sinpi((double)k / (2.0 * n));
+    sv[k] = s * s;
+  }
+}
+
+template <int P>
+void noalloc_pass(const PassArgs& A, int npairs, int na, cudaStream_t st) {
+  dim3 grid((unsigned)((npairs + P - 1) / P), (unsigned)na);
+  size_t smem = sizeof(Cx<double>) * (size_t)(2 * A.n) * P * 2;
+  k_dst_pass<double, P><<<grid, 256, smem, st>>>(A);
+}
+
+void noalloc_launch(const PassArgs& A, int npairs, int na, cudaStream_t st, int pmin) {
+  const int P = std::max(pmin, 1024 / (2 * A.n));
+  if (P >= 8) noalloc_pass<8>(A, npairs, na, st);
+  else if (P >= 4) noalloc_pass<4>(A, npairs, na, st);
+  else if (P >= 2) noalloc_pass<2>(A, npairs, na, st);
+  else noalloc_pass<1>(A, npairs, na, st);
+}
+
+}  // namespace
+
+}  // namespace kfbi
+
+extern "C" kfbi_status kfbi_box_solve_noalloc(int dim, int n, double lo, double hi, int order,
+                                              double kappa, const double* rhs, double* u,
+                                              void* cuda_stream) {
+  using namespace kfbi;
+  if ((dim != 2 && dim != 3) || (order != 2 && order != 4) || !(hi > lo) || !(kappa >= 0.0) ||
+      !rhs || !u || n < 8 || (n & (n - 1)) != 0)
+    return KFBI_ERR_ARG;
+  if ((dim == 2 && n > kNoAllocMaxN2) || (dim == 3 && n > kNoAllocMaxN3))
+    return KFBI_ERR_ARG;   // beyond the fixed scratch: 2D N <= 512, 3D N <= 64
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return KFBI_ERR_CUDA;
+  double* base = nullptr;
+  {
+    // one-time set-up per device: the array's device address (a host-side
+    // reference to it is only a stand-in) and the shared-memory limits
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      double* ptr = nullptr;
+      if (cudaGetSymbolAddress(reinterpret_cast<void**>(&ptr), g_noalloc_scratch) != cudaSuccess ||
+          !ptr)
+        return KFBI_ERR_CUDA;
+      int optin = 0;
+      if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return KFBI_ERR_CUDA;
+      if (cudaFuncSetAttribute(k_dst_pass<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
+          cudaFuncSetAttribute(k_dst_pass<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
+          cudaFuncSetAttribute(k_dst_pass<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
+          cudaFuncSetAttribute(k_dst_pass<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
+        return KFBI_ERR_CUDA;
+      g_noalloc_ptr[dev] = ptr;
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  double* work = base;
+  double* scale = base + kNoAllocGrid;
+  double* tw = base + 2 * kNoAllocGrid;
+  double* sv = tw + kNoAllocTw;
+  const double h = (hi - lo) / n;
+  const double kt = kappa;
+  const double gh2 = (dim == 2 ? (2.0 / n) * (2.0 / n) : (2.0 / n) * (2.0 / n) * (2.0 / n)) * h * h;
+  const long long m = n - 1;
+  const long long nm = dim == 2 ? m * m : m * m * m;
+  const long long nodes = dim == 2 ? (long long)(n + 1) * (n + 1) : (long long)(n + 1) * (n + 1) * (n + 1);
+  // the tables depend on N and kappa, so every call rebuilds them
+  k_noalloc_tables<<<4, 256, 0, st>>>(n, tw, sv);
+  k_scale_table<<<std::min(div_up(nm, 256), 152 * 16), 256, 0, st>>>(dim, order, n, kt * h * h, gh2, sv, scale);
+  if (cudaMemsetAsync(u, 0, sizeof(double) * nodes, st) != cudaSuccess) return KFBI_ERR_CUDA;
+  PassArgs A;
+  memset(&A, 0, sizeof(A));
+  A.n = n;
+  int logL = 0;
+  while ((1 << logL) < 2 * n) ++logL;
+  A.logL = logL;
+  A.tw = tw;
+  A.scale64 = scale;
+  A.d = dim;
+  A.order = order;
+  const int npairs = n / 2;
+  const int n1 = n + 1;
+  auto io = [&](const void* s, void* d, int d64) {
+    A.src = s;
+    A.src64 = 1;
+    A.dst = d;
+    A.dst64 = d64;
+    A.accumulate = 0;
+  };
+  if (dim == 2) {
+    io(rhs, work, 1);
+    A.sa = 0; A.sb = n1; A.es = 1; A.fused = 0;
+    noalloc_launch(A, npairs, 1, st, 1);
+    io(work, work, 1);
+    A.sa = 0; A.sb = 1; A.es = n1; A.fused = 1;
+    noalloc_launch(A, npairs, 1, st, 2);
+    io(work, u, 1);
+    A.sa = 0; A.sb = n1; A.es = 1; A.fused = 0;
+    noalloc_launch(A, npairs, 1, st, 1);
+  } else {
+    const long long s0 = (long long)n1 * n1;
+    io(rhs, work, 1);
+    A.sa = s0; A.sb = n1; A.es = 1; A.fused = 0;
+    noalloc_launch(A, npairs, n - 1, st, 1);
+    io(work, work, 1);
+    A.sa = s0; A.sb = 1; A.es = n1;
+    noalloc_launch(A, npairs, n - 1, st, 2);
+    A.sa = n1; A.sb = 1; A.es = s0; A.fused = 1;
+    noalloc_launch(A, npairs, n - 1, st, 2);
+    A.fused = 0;
+    A.sa = s0; A.sb = 1; A.es = n1;
+    noalloc_launch(A, npairs, n - 1, st, 2);
+    io(work, u, 1);
+    A.sa = s0; A.sb = n1; A.es = 1;
+    noalloc_launch(A, npairs, n - 1, st, 1);
+  }
+  return cudaGetLastError() == cudaSuccess ? KFBI_OK : KFBI_ERR_CUDA;
+}

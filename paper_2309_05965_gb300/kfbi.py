@@ -87,6 +87,8 @@ SIGNATURES = {
     "kfbi_gmres_solve": [_P, ctypes.POINTER(Data), ctypes.POINTER(GmresOpts), _P,
                          ctypes.POINTER(GmresInfo)],
     "kfbi_evaluate": [_P, ctypes.POINTER(Data), _P, _P],
+    "kfbi_box_solve_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_int, ctypes.c_double, _P, _P, _P],
     "kfbi_launch_counts": [_P, _P, ctypes.c_int],
     "kfbi_profile_enable": [_P, ctypes.c_int],
     "kfbi_profile_read": [_P, _P, _P],
@@ -230,6 +232,12 @@ def kfbi_gmres_solve(h, data, opts: GmresOpts, density):
 
 def kfbi_evaluate(h, data, density, u):
     _check(load().kfbi_evaluate(h, ctypes.byref(data), _ptr(density), _ptr(u)), h)
+
+
+def kfbi_box_solve_noalloc(dim, n, lo, hi, order, kappa, rhs, u, stream=None):
+    """FP64 DST box solve with no device allocation (fixed library scratch)."""
+    _check(load().kfbi_box_solve_noalloc(dim, n, lo, hi, order, kappa, _ptr(rhs), _ptr(u),
+                                         _stream_handle(stream)))
 
 
 def kfbi_launch_counts(h, reset=False):
