@@ -117,7 +117,8 @@ def run_ours(args, rank, world):
     prec = kfbi.MIXED if args.precision == "mixed" else kfbi.FP64
     box = kfbi.BOX_MG if args.box == "mg" else kfbi.BOX_DST
     t0 = time.perf_counter()
-    G = kfbi.Problem.from_workload(w, box_solver=box, precision=prec)
+    G = kfbi.Problem.from_workload(w, box_solver=box, precision=prec,
+                                   box_rtol=args.box_rtol if prec == kfbi.MIXED else 0.0)
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
     d = w.dim
@@ -262,6 +263,7 @@ def run_ours(args, rank, world):
         "config": {"workload": f"flower interface 2D, N={args.n}, sigma_in/sigma_out=1000, "
                                f"4th order, GMRES rtol {args.rtol:g}",
                    "box_solver": args.box, "precision": args.precision, "n_b": G.nb,
+                   "box_rtol": args.box_rtol if prec == kfbi.MIXED else None,
                    "n_irr": G.nirr, "l2": "flushed (256 MB write) before every step",
                    "parallelism": "independent replicas" if world > 1 else "1 GPU"},
         "gmres_iterations": iters[-1], "max_err_vs_exact": err,
@@ -277,9 +279,128 @@ def run_ours(args, rank, world):
         "kernel_ms_per_step": {k: v[0] / 2 for k, v in prof.items()},
         "roofline": roof,
     }
+    G.close()
+    if args.batch > 0:
+        out["batched"] = batched(args, stream, flush)
     if rank == 0 and args.cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_budget)
-    G.close()
+    return out
+
+
+def batched(args, stream, flush):
+    """The batched workload: 64 seeded star-interface problems on grids drawn
+    from {128, 256, 512, 1024}^2 (an instance whose interface its drawn grid
+    cannot resolve moves to the next size), all solved by one batched GMRES
+    (kfbi_gmres_solve_batch) plus the per-instance evaluation.  Compared with
+    the same instances solved one after another by the plain FP64 path and by
+    the mixed path."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2309_05965_gb300 import kfbi
+    sizes = (128, 256, 512, 1024)
+    inst = []
+    bumped = 0
+    for w in W.star_batch_2d(count=args.batch, seed=5965, sizes=sizes):
+        drawn = w.n
+        for n in [s for s in sizes if s >= drawn]:
+            w.n = n
+            try:
+                G = kfbi.Problem.from_workload(w, precision=kfbi.MIXED, box_rtol=args.box_rtol)
+            except kfbi.KfbiError as e:
+                if e.status != 2:
+                    raise
+                continue
+            bumped += n != drawn
+            inst.append((w, G))
+            break
+    rows = []
+    for w, G in inst:
+        xyz = torch.zeros((G.nb, 2), dtype=torch.float64, device="cuda")
+        nrm = torch.zeros((G.nb, 2), dtype=torch.float64, device="cuda")
+        kfbi.kfbi_dof_points(G.handle, xyz, nrm)
+        g1, g2 = W.boundary_data(w, xyz.cpu().numpy(), nrm.cpu().numpy())
+        grid = W.grid_data(w)
+        keep = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in
+                (("g1", g1), ("g2", g2), ("f_in", grid["f_in"]), ("f_out", grid["f_out"]),
+                 ("lapf_in", grid["lapf_in"]), ("lapf_out", grid["lapf_out"]),
+                 ("g_b", grid["g_b"]))}
+        rows.append(dict(w=w, G=G, keep=keep, d=kfbi.make_data(**keep),
+                         x=torch.zeros(G.nb, dtype=torch.float64, device="cuda"),
+                         u=torch.zeros(G.grid_shape, dtype=torch.float64, device="cuda")))
+    opts = kfbi.GmresOpts(rtol=args.rtol, restart=100, max_iter=100, x0=None)
+    B = kfbi.Batch([r["G"] for r in rows])
+    datas = [r["d"] for r in rows]
+    xs = [r["x"] for r in rows]
+
+    def step():
+        infos = B.gmres_solve(datas, opts, xs)
+        for r in rows:
+            kfbi.kfbi_evaluate(r["G"].handle, r["d"], r["x"], r["u"])
+        return infos
+
+    def timed(fn, reps):
+        t = []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            t.append(e0.elapsed_time(e1))
+        return statistics.median(t)
+
+    for _ in range(2):
+        infos = step()
+    for r in rows:
+        kfbi.kfbi_launch_counts(r["G"].handle, reset=True)
+    ms_batch = timed(step, max(3, args.steps // 2))
+    errs = []
+    for r in rows:
+        ins = _inside(r["G"], kfbi)
+        ex = W.exact_grid(r["w"], ins)
+        errs.append(float(np.abs(r["u"].cpu().numpy() - ex)[1:-1, 1:-1].max()))
+
+    def sequential(prec_rows):
+        def fn():
+            for r, G in prec_rows:
+                kfbi.kfbi_gmres_solve(G.handle, r["d"], opts, r["x2"])
+                kfbi.kfbi_evaluate(G.handle, r["d"], r["x2"], r["u2"])
+        fn()
+        return timed(fn, 2)
+
+    for r in rows:
+        r["x2"] = torch.zeros_like(r["x"])
+        r["u2"] = torch.zeros_like(r["u"])
+    ms_mixed_seq = sequential([(r, r["G"]) for r in rows])
+    g64 = [kfbi.Problem.from_workload(r["w"], precision=kfbi.FP64) for r in rows]
+    ms_fp64_seq = sequential(list(zip(rows, g64)))
+    errs64 = []
+    for r in rows:
+        ins = _inside(r["G"], kfbi)
+        ex = W.exact_grid(r["w"], ins)
+        errs64.append(float(np.abs(r["u2"].cpu().numpy() - ex)[1:-1, 1:-1].max()))
+    for G in g64:
+        G.close()
+    ratio = [e / max(e64, 1e-300) for e, e64 in zip(errs, errs64)]
+    nsz = {}
+    for r in rows:
+        nsz[r["w"].n] = nsz.get(r["w"].n, 0) + 1
+    out = {"workload": f"{len(rows)} star-interface problems, grids {nsz}, contrast 10^U[0,3], "
+                       f"GMRES rtol {args.rtol:g}",
+           "instances": len(rows), "moved_to_finer_grid": bumped,
+           "solves_per_s": len(rows) / (ms_batch * 1e-3), "ms_per_batch": ms_batch,
+           "fp64_sequential_solves_per_s": len(rows) / (ms_fp64_seq * 1e-3),
+           "mixed_sequential_solves_per_s": len(rows) / (ms_mixed_seq * 1e-3),
+           "speedup_vs_fp64_sequential": ms_fp64_seq / ms_batch,
+           "gmres_iterations": [i.iters for i in infos],
+           "max_err_vs_exact": max(errs), "max_err_ratio_vs_fp64": max(ratio)}
+    B.close()
+    for r in rows:
+        r["G"].close()
     return out
 
 
@@ -383,11 +504,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--box-rtol", type=float, default=1e-11,
+                    help="inner tolerance of the mixed box solve (correction size)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--box", default="dst", choices=["dst", "mg"])
     ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--batch", type=int, default=64,
+                    help="instances of the batched star-interface workload (0: skip)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

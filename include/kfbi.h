@@ -220,6 +220,36 @@ kfbi_status kfbi_gmres_solve(kfbi_problem* p, const kfbi_data* data,
 kfbi_status kfbi_evaluate(kfbi_problem* p, const kfbi_data* data, const double* density,
                           double* u_grid);
 
+/* ---- batched solves ------------------------------------------------------ */
+
+/* Many independent problems solved together (different grids, interfaces and
+ * data), Algorithm 1 for each, with every GMRES iteration of all instances
+ * run as one replay of a captured CUDA graph: the correction values, RHS
+ * corrections, box solves and traces of all instances each run as one launch
+ * over all instances' work items.  The batch keeps pointers to the problems,
+ * which must outlive it and must not be used for other work while a batched
+ * solve runs (their operator buffers and box-solver scratch are shared).
+ * Requirements: at least one problem; all on one stream, of one dimension,
+ * with box_solver KFBI_BOX_DST, precision KFBI_MIXED, the same Krylov
+ * dimension, and N_b <= 32768 each; otherwise KFBI_ERR_UNSUPPORTED (message on
+ * problems[0]).  problems: host array of count handles; *out receives the
+ * batch (NULL on failure). */
+typedef struct kfbi_batch kfbi_batch;
+kfbi_status kfbi_create_batch(kfbi_problem* const* problems, int count, kfbi_batch** out);
+kfbi_status kfbi_destroy_batch(kfbi_batch* batch);
+/* Algorithm 1 for every instance k from a zero start: data[k] (host array of
+ * count kfbi_data with device pointers as in kfbi_gmres_solve), densities[k]
+ * (host array of count device pointers, N_b of instance k each, written),
+ * infos (host array of count, may be NULL; t_ms zeroed).  opts applies to
+ * every instance; opts->x0 must be NULL; there is no restart: an instance not
+ * converged within min(max_iter, restart, Krylov dimension) iterations makes
+ * the call return KFBI_ERR_NOT_CONVERGED after writing every density.
+ * Synchronises the stream once per iteration (one copy of the residual
+ * estimates of all instances). */
+kfbi_status kfbi_gmres_solve_batch(kfbi_batch* batch, const kfbi_data* data,
+                                   const kfbi_gmres_opts* opts, double* const* densities,
+                                   kfbi_gmres_info* infos);
+
 /* ---- box solve without allocation ----------------------------------------- */
 
 /* The FP64 sine-transform box solve u = A_h^{-1} rhs of kfbi_box_solve, for a

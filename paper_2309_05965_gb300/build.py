@@ -26,6 +26,7 @@ SOURCES = {
     "mg.cu": [],
     "gmres.cu": [],
     "capi.cu": [],
+    "batch.cu": [],
 }
 
 

@@ -46,7 +46,7 @@ struct BoxSolver {
   double* work64 = nullptr;   // grid of doubles
   float* work32 = nullptr;    // grid of floats
   double* res = nullptr;      // FP64 residual grid
-  unsigned long long* nrm = nullptr;   // [0] max|R|, [1] max|r| (accumulating), [2] last max|r|
+  unsigned long long* nrm = nullptr;   // [0] max|R| [1] max|r| [2] last max|delta| [3] max|delta| [4] max|u| [5] last max|u|
   int* conv = nullptr;        // device flag
   int refine_steps = 4;
   double tol = 1e-13;
@@ -71,6 +71,8 @@ struct PassArgs {
   int fused;
   int amode;                // 1 if the a index is a mode index of the scaling (3D)
   const int* skip;          // convergence flag (skip when *skip != 0), may be null
+  unsigned long long* corr_max;   // accumulate pass: max |correction|, max |u + correction|
+  float* delta_out;               // accumulate pass: also keep the FP32 correction (in place)
 };
 
 template <typename T>
@@ -172,19 +174,19 @@ __device__ Cx<T>* fft_stockham(Cx<T>* x, Cx<T>* y, int L, const Cx<T>* __restric
   return x;
 }
 
-// One DST-I pass over P line pairs per CTA (see file comment).
+// One DST-I pass over P line pairs (see file comment): line pairs starting at
+// b0 = 1 + 2 P bx of the line family a = by + 1.
 template <typename T, int P>
-__global__ void __launch_bounds__(256) k_dst_pass(PassArgs A) {
-  if (A.skip && *A.skip) return;
-  extern __shared__ unsigned char smraw[];
+__device__ __forceinline__ void dst_pass_device(const PassArgs& A, int bx, int by,
+                                                unsigned char* smraw) {
   Cx<T>* z = reinterpret_cast<Cx<T>*>(smraw);
   Cx<T>* zb = z + (size_t)P * 2 * A.n;      // ping-pong buffer
   const Cx<T>* tw = static_cast<const Cx<T>*>(A.tw);
   const int n = A.n;
   const int L = 2 * n;
   const int nm1 = n - 1;
-  const int a = blockIdx.y + 1;
-  const int b0 = 1 + 2 * P * blockIdx.x;
+  const int a = by + 1;
+  const int b0 = 1 + 2 * P * bx;
   const long long abase = (long long)a * A.sa;
   const bool contig = A.es == 1;
   const int nval = nm1 * 2 * P;
@@ -260,6 +262,7 @@ __global__ void __launch_bounds__(256) k_dst_pass(PassArgs A) {
     z = fft_stockham<T, P>(z, zb, L, tw);
   }
   // extract S_k = -Im(Z_k)/2 (first line) and Re(Z_k)/2 (second line) and store
+  float dmx = 0.f, umx = 0.f;
   for (int t = threadIdx.x; t < nval; t += blockDim.x) {
     int j, q;
     if (contig) {
@@ -277,10 +280,57 @@ __global__ void __launch_bounds__(256) k_dst_pass(PassArgs A) {
     long long off = abase + (long long)b * A.sb + (long long)j * A.es;
     if (A.dst64) {
       double* o = static_cast<double*>(A.dst);
-      o[off] = A.accumulate ? o[off] + (double)v : (double)v;
+      double nv = A.accumulate ? o[off] + (double)v : (double)v;
+      o[off] = nv;
+      if (A.delta_out) A.delta_out[off] = (float)v;
+      if (A.corr_max) {
+        dmx = fmaxf(dmx, fabsf((float)v));
+        umx = fmaxf(umx, fabsf((float)nv));
+      }
     } else {
       static_cast<float*>(A.dst)[off] = (float)v;
     }
+  }
+  if (A.corr_max) {
+    for (int o = 16; o > 0; o >>= 1) {
+      dmx = fmaxf(dmx, __shfl_xor_sync(0xffffffffu, dmx, o));
+      umx = fmaxf(umx, __shfl_xor_sync(0xffffffffu, umx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      // non-negative doubles order like their bit patterns
+      if (dmx > 0.f) atomicMax(A.corr_max, (unsigned long long)__double_as_longlong((double)dmx));
+      if (umx > 0.f) atomicMax(A.corr_max + 1, (unsigned long long)__double_as_longlong((double)umx));
+    }
+  }
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_dst_pass(PassArgs A) {
+  if (A.skip && *A.skip) return;
+  extern __shared__ unsigned char smraw[];
+  dst_pass_device<T, P>(A, blockIdx.x, blockIdx.y, smraw);
+}
+
+// Persistent batched pass over many independent grids (one pair per work
+// item): item -> instance by binary search in the prefix `start`, each
+// instance with its own PassArgs (its own N, pointers and convergence flag).
+template <typename T>
+__global__ void __launch_bounds__(256) k_dst_pass_batched(const PassArgs* __restrict__ args,
+                                                         const int* __restrict__ start, int ninst) {
+  extern __shared__ unsigned char smraw[];
+  const int total = start[ninst];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    int lo = 0, hi = ninst;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (start[mid] <= item) lo = mid; else hi = mid;
+    }
+    const PassArgs& A = args[lo];
+    if (A.skip && *A.skip) continue;
+    const int local = item - start[lo];
+    const int npx = A.n / 2;
+    dst_pass_device<T, 1>(A, local % npx, local / npx, smraw);
+    __syncthreads();
   }
 }
 
@@ -337,21 +387,23 @@ __global__ void k_absmax(long long tot, const double* __restrict__ R, unsigned l
   if ((threadIdx.x & 31) == 0) atomicMax(nrm, (unsigned long long)__double_as_longlong(mx));
 }
 
-// conv = (max|r| <= tol max|R|); keeps the last residual in nrm[2] and resets
-// the accumulation slot nrm[1] for the next step.
+// Refinement stop: conv = (max|delta_k| <= tol max|u_{k+1}|), the size of the
+// last FP32 correction against the solution (a residual test would sit on the
+// rounding floor eps cond(A_h) of the FP64 residual itself at large N).
+// Keeps the last ratio's terms in nrm[2..] and resets the accumulation slots.
 __global__ void k_check(unsigned long long* nrm, double tol, int* conv) {
   if (*conv) return;
-  double R = __longlong_as_double((long long)nrm[0]);
-  double r = __longlong_as_double((long long)nrm[1]);
-  nrm[2] = nrm[1];
-  if (r <= tol * R) *conv = 1;
-  nrm[1] = 0ull;
+  double dm = __longlong_as_double((long long)nrm[3]);
+  double um = __longlong_as_double((long long)nrm[4]);
+  nrm[2] = nrm[3];
+  nrm[5] = nrm[4];
+  if (dm <= tol * um) *conv = 1;
+  nrm[3] = 0ull;
+  nrm[4] = 0ull;
 }
 
 __global__ void k_zero_flags(unsigned long long* nrm, int* conv) {
-  nrm[0] = 0ull;
-  nrm[1] = 0ull;
-  nrm[2] = 0ull;
+  for (int k = 0; k < 6; ++k) nrm[k] = 0ull;
   *conv = 0;
 }
 
@@ -383,11 +435,19 @@ cudaError_t set_smem(int max_optin) {
                               max_optin);
 }
 
-// Runs the full DST solve of `src` (grid, FP64 or FP32) into `dst` (grid, FP64),
-// overwriting or accumulating.  Work buffer of type T.
+// The passes of one DST solve of `src` (grid, FP64 or FP32) into `dst` (grid,
+// FP64), overwriting or accumulating, with a work buffer of type T: the
+// argument block of each pass, the pairs-per-CTA floor (strided passes read
+// 2 P adjacent lines) and the number of line families.
+struct PassPlan {
+  PassArgs args[5];
+  int pmin[5];
+  int npass = 0, npairs = 0, na = 1;
+};
+
 template <typename T>
-kfbi_status dst_solve_t(kfbi_problem* p, const void* src, int src64, double* dst, int accumulate,
-                        const int* skip) {
+PassPlan plan_passes(kfbi_problem* p, const void* src, int src64, double* dst, int accumulate,
+                     const int* skip, unsigned long long* corr_max) {
   BoxSolver* B = p->box;
   const Grid g = p->g;
   const int n = g.n, n1 = n + 1;
@@ -408,51 +468,48 @@ kfbi_status dst_solve_t(kfbi_problem* p, const void* src, int src64, double* dst
   A.order = p->cfg.order;
   A.skip = skip;
   A.gscale = (g.d == 2 ? (2.0 / n) * (2.0 / n) : (2.0 / n) * (2.0 / n) * (2.0 / n)) * g.h * g.h;
-  const int npairs = n / 2;   // ceil((N-1)/2) for even N
   const int is64 = std::is_same<T, double>::value ? 1 : 0;
-  cudaStream_t st = p->stream;
-  auto set_io = [&](const void* s, int s64, void* d, int d64, int acc) {
-    A.src = s;
-    A.src64 = s64;
-    A.dst = d;
-    A.dst64 = d64;
-    A.accumulate = acc;
+  PassPlan P;
+  P.npairs = n / 2;   // ceil((N-1)/2) for even N
+  P.na = g.d == 2 ? 1 : n - 1;
+  auto add = [&](const void* s, int s64, void* d, int d64, int acc, long long sa, long long sb,
+                 long long es, int fused, int pmin) {
+    PassArgs& Q = P.args[P.npass];
+    Q = A;
+    Q.src = s;
+    Q.src64 = s64;
+    Q.dst = d;
+    Q.dst64 = d64;
+    Q.accumulate = acc;
+    Q.corr_max = (d64 && acc) ? corr_max : nullptr;
+    Q.sa = sa;
+    Q.sb = sb;
+    Q.es = es;
+    Q.fused = fused;
+    P.pmin[P.npass] = pmin;
+    ++P.npass;
   };
   if (g.d == 2) {
-    // pass 1: axis 1 (contiguous), lines b = i0
-    set_io(src, src64, work, is64, 0);
-    A.sa = 0; A.sb = n1; A.es = 1; A.fused = 0;
-    launch_pass<T>(p, A, npairs, 1, st, 1);
-    // pass 2: axis 0 (stride n1), lines b = i1 (adjacent), fused scaling
-    set_io(work, is64, work, is64, 0);
-    A.sa = 0; A.sb = 1; A.es = n1; A.fused = 1;
-    launch_pass<T>(p, A, npairs, 1, st, 2);
-    // pass 3: axis 1
-    set_io(work, is64, dst, 1, accumulate);
-    A.sa = 0; A.sb = n1; A.es = 1; A.fused = 0;
-    launch_pass<T>(p, A, npairs, 1, st, 1);
+    add(src, src64, work, is64, 0, 0, n1, 1, 0, 1);          // axis 1, lines b = i0
+    add(work, is64, work, is64, 0, 0, 1, n1, 1, 2);          // axis 0 fused, lines b = i1
+    add(work, is64, dst, 1, accumulate, 0, n1, 1, 0, 1);     // axis 1
   } else {
     const long long s0 = (long long)n1 * n1;
-    // pass 1: axis 2, lines (a = i0, b = i1)
-    set_io(src, src64, work, is64, 0);
-    A.sa = s0; A.sb = n1; A.es = 1; A.fused = 0;
-    launch_pass<T>(p, A, npairs, n - 1, st, 1);
-    // pass 2: axis 1, lines (a = i0, b = i2)
-    set_io(work, is64, work, is64, 0);
-    A.sa = s0; A.sb = 1; A.es = n1;
-    launch_pass<T>(p, A, npairs, n - 1, st, 2);
-    // pass 3: axis 0 fused, lines (a = i1, b = i2)
-    A.sa = n1; A.sb = 1; A.es = s0; A.fused = 1;
-    launch_pass<T>(p, A, npairs, n - 1, st, 2);
-    A.fused = 0;
-    // pass 4: axis 1
-    A.sa = s0; A.sb = 1; A.es = n1;
-    launch_pass<T>(p, A, npairs, n - 1, st, 2);
-    // pass 5: axis 2
-    set_io(work, is64, dst, 1, accumulate);
-    A.sa = s0; A.sb = n1; A.es = 1;
-    launch_pass<T>(p, A, npairs, n - 1, st, 1);
+    add(src, src64, work, is64, 0, s0, n1, 1, 0, 1);         // axis 2, lines (i0, i1)
+    add(work, is64, work, is64, 0, s0, 1, n1, 0, 2);         // axis 1, lines (i0, i2)
+    add(work, is64, work, is64, 0, n1, 1, s0, 1, 2);         // axis 0 fused, lines (i1, i2)
+    add(work, is64, work, is64, 0, s0, 1, n1, 0, 2);         // axis 1
+    add(work, is64, dst, 1, accumulate, s0, n1, 1, 0, 1);    // axis 2
   }
+  return P;
+}
+
+template <typename T>
+kfbi_status dst_solve_t(kfbi_problem* p, const void* src, int src64, double* dst, int accumulate,
+                        const int* skip, unsigned long long* corr_max = nullptr) {
+  PassPlan P = plan_passes<T>(p, src, src64, dst, accumulate, skip, corr_max);
+  for (int k = 0; k < P.npass; ++k)
+    launch_pass<T>(p, P.args[k], P.npairs, P.na, p->stream, P.pmin[k]);
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
 }
@@ -507,8 +564,10 @@ kfbi_status box_create(kfbi_problem* p) {
   const long long nodes = g.nodes();
   if (p->cfg.precision == KFBI_MIXED) {
     KFBI_CUDA(p, dalloc(&B->work32, nodes));
+    KFBI_CUDA(p, cudaMemset(B->work32, 0, sizeof(float) * nodes));
     KFBI_CUDA(p, dalloc(&B->res, nodes));
     KFBI_CUDA(p, cudaMemset(B->res, 0, sizeof(double) * nodes));
+
   } else {
     KFBI_CUDA(p, dalloc(&B->work64, nodes));
     const long long m = n - 1;
@@ -520,10 +579,10 @@ kfbi_status box_create(kfbi_problem* p) {
     KFBI_CUDA(p, cudaGetLastError());
     KFBI_CUDA(p, cudaDeviceSynchronize());
   }
-  KFBI_CUDA(p, dalloc(&B->nrm, 3));
+  KFBI_CUDA(p, dalloc(&B->nrm, 6));
   KFBI_CUDA(p, dalloc(&B->conv, 1));
   B->tol = p->cfg.box_rtol > 0 ? p->cfg.box_rtol : 1e-13;
-  B->refine_steps = p->cfg.box_max_iters > 0 ? std::min(p->cfg.box_max_iters, 8) : 4;
+  B->refine_steps = p->cfg.box_max_iters > 0 ? std::min(p->cfg.box_max_iters, 8) : 5;
   int dev = 0, optin = 0;
   KFBI_CUDA(p, cudaGetDevice(&dev));
   KFBI_CUDA(p, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -578,15 +637,20 @@ kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u) {
   KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_zero_flags<<<1, 1, 0, st>>>(B->nrm, B->conv));
   KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_absmax<<<std::min(div_up(nodes, 256), 152 * 8), 256, 0, st>>>(nodes, rhs, B->nrm));
   KFBI_CUDA(p, cudaGetLastError());
-  const double* src = rhs;
+  // u += delta_k = DST32(r_k); r_{k+1} = R - A_h u in FP64 every step.  (An
+  // update r_k - A_h delta_k with A_h delta_k in FP32 is not enough: delta_k is
+  // smooth, A_h delta_k cancels by ~cond(A_h), and its FP32 rounding is then as
+  // large as the residual itself.)
+  const dim3 rgrid((unsigned)div_up(g.n + 1, 128), (unsigned)(g.n + 1), g.d == 3 ? (unsigned)(g.n + 1) : 1u);
   for (int it = 0; it < B->refine_steps; ++it) {
-    KFBI_TRY(dst_solve_t<float>(p, src, 1, u, 1, B->conv));
-    dim3 rgrid((unsigned)div_up(g.n + 1, 128), (unsigned)(g.n + 1), g.d == 3 ? (unsigned)(g.n + 1) : 1u);
-    KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_residual<<<rgrid, 128, 0, st>>>(
-        g, p->cfg.order, p->stencil_dev, rhs, u, B->res, B->nrm + 1, B->conv));
+    KFBI_TRY(dst_solve_t<float>(p, it == 0 ? (const void*)rhs : (const void*)B->res, 1, u, 1, B->conv,
+                                B->nrm + 3));
     KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_check<<<1, 1, 0, st>>>(B->nrm, B->tol, B->conv));
+    if (it + 1 < B->refine_steps) {
+      KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_residual<<<rgrid, 128, 0, st>>>(
+          g, p->cfg.order, p->stencil_dev, rhs, u, B->res, B->nrm + 1, B->conv));
+    }
     KFBI_CUDA(p, cudaGetLastError());
-    src = B->res;
   }
   return KFBI_OK;
 }
@@ -595,17 +659,17 @@ kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u) {
 kfbi_status box_last_residual(kfbi_problem* p, double* rel, int* converged) {
   if (p->mg) return mg_last_residual(p, rel, converged);
   BoxSolver* B = p->box;
-  unsigned long long h[3] = {0, 0, 0};
+  unsigned long long h[6] = {0, 0, 0, 0, 0, 0};
   int c = 1;
   if (p->cfg.precision == KFBI_MIXED) {
     KFBI_CUDA(p, cudaMemcpyAsync(h, B->nrm, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
     KFBI_CUDA(p, cudaMemcpyAsync(&c, B->conv, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     KFBI_CUDA(p, cudaStreamSynchronize(p->stream));
   }
-  double R, r;
-  memcpy(&R, &h[0], 8);
-  memcpy(&r, &h[2], 8);
-  *rel = R > 0 ? r / R : 0.0;
+  double dm, um;
+  memcpy(&dm, &h[2], 8);
+  memcpy(&um, &h[5], 8);
+  *rel = um > 0 ? dm / um : 0.0;
   *converged = c;
   return KFBI_OK;
 }
@@ -769,3 +833,202 @@ extern "C" kfbi_status kfbi_box_solve_noalloc(int dim, int n, double lo, double 
   }
   return cudaGetLastError() == cudaSuccess ? KFBI_OK : KFBI_ERR_CUDA;
 }
+
+// ---------------------------------------------------------------------------
+// Batched mixed-precision box solve: many independent grids (different N) in
+// one launch per pass (persistent CTAs over all instances' line pairs) and one
+// launch per residual / check, with per-instance convergence flags.
+// ---------------------------------------------------------------------------
+namespace kfbi {
+namespace {
+
+struct ResDesc {
+  Grid g;
+  int order;
+  const double* c;
+  const double* R;
+  double* u;
+  double* r;
+  unsigned long long* nrm;
+  int* conv;
+  double tol;
+};
+
+__device__ __forceinline__ int find_inst(const int* start, int ninst, int item) {
+  int lo = 0, hi = ninst;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (start[mid] <= item) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// one grid row (last axis) per work item
+__global__ void k_residual_batched(const ResDesc* __restrict__ rd, const int* __restrict__ rstart, int ninst) {
+  const int total = rstart[ninst];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int inst = find_inst(rstart, ninst, item);
+    const ResDesc& D = rd[inst];
+    if (*D.conv) continue;
+    const Grid g = D.g;
+    const int n1 = g.n + 1;
+    const int row = item - rstart[inst];
+    const int i1 = row % n1, i0 = row / n1;   // 2D: i0 = 0
+    double mx = 0.0;
+    for (int j = threadIdx.x; j <= g.n; j += blockDim.x) {
+      const long long t = g.d == 2 ? (long long)i1 * n1 + j : ((long long)i0 * n1 + i1) * n1 + j;
+      const bool interior = j >= 1 && j < g.n && i1 >= 1 && i1 < g.n && (g.d == 2 || (i0 >= 1 && i0 < g.n));
+      if (!interior) {
+        D.r[t] = 0.0;
+        continue;
+      }
+      const double* up = D.u + t;
+      const double* c = D.c;
+      double acc;
+      if (g.d == 2) {
+        double s1 = (up[-1] + up[1]) + (up[-n1] + up[n1]);
+        acc = c[0] * up[0] + c[1] * s1;
+        if (D.order == 4) acc += c[2] * ((up[-n1 - 1] + up[-n1 + 1]) + (up[n1 - 1] + up[n1 + 1]));
+      } else {
+        const long long s = (long long)n1 * n1;
+        double f = (up[-1] + up[1]) + (up[-n1] + up[n1]) + (up[-s] + up[s]);
+        acc = c[0] * up[0] + c[1] * f;
+        if (D.order == 4) {
+          double e = (up[-n1 - 1] + up[-n1 + 1]) + (up[n1 - 1] + up[n1 + 1]) + (up[-s - 1] + up[-s + 1]) +
+                     (up[s - 1] + up[s + 1]) + (up[-s - n1] + up[-s + n1]) + (up[s - n1] + up[s + n1]);
+          double k = (up[-s - n1 - 1] + up[-s - n1 + 1]) + (up[-s + n1 - 1] + up[-s + n1 + 1]) +
+                     (up[s - n1 - 1] + up[s - n1 + 1]) + (up[s + n1 - 1] + up[s + n1 + 1]);
+          acc += c[2] * e + c[3] * k;
+        }
+      }
+      const double v = D.R[t] - acc;
+      D.r[t] = v;
+      mx = fmax(mx, fabs(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0.0)
+      atomicMax(D.nrm + 1, (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+__global__ void k_check_batched(const ResDesc* __restrict__ rd, int ninst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ninst) return;
+  const ResDesc& D = rd[i];
+  unsigned long long* nrm = D.nrm;
+  if (*D.conv) return;
+  double dm = __longlong_as_double((long long)nrm[3]);
+  double um = __longlong_as_double((long long)nrm[4]);
+  nrm[2] = nrm[3];
+  nrm[5] = nrm[4];
+  if (dm <= D.tol * um) *D.conv = 1;
+  nrm[3] = 0ull;
+  nrm[4] = 0ull;
+}
+
+// Reset the refinement state; instances flagged in `done` (outer iteration
+// finished) start as converged, so every pass and residual skips them.
+__global__ void k_zero_batched(const ResDesc* __restrict__ rd, int ninst, const int* __restrict__ done) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ninst) return;
+  for (int k = 0; k < 6; ++k) rd[i].nrm[k] = 0ull;
+  *rd[i].conv = done ? done[i] : 0;
+}
+
+}  // namespace
+
+struct BatchBox {
+  int ninst = 0, npass = 0, steps = 4;
+  PassArgs* dargs = nullptr;   // [npass + 1][ninst]: pass 0 from R, pass 0 from r, passes 1..
+  int* dstart = nullptr;       // [ninst + 1] line-pair work items
+  ResDesc* dres = nullptr;     // [ninst]
+  int* drstart = nullptr;      // [ninst + 1] residual rows
+  std::vector<double*> u, rhs;
+  std::vector<size_t> ubytes;
+  size_t smem = 0;
+  int grid = 0;
+};
+
+kfbi_status batch_box_create(kfbi_problem* p0, kfbi_problem* const* ps, int ninst,
+                             double* const* rhs, BatchBox** out) {
+  BatchBox* bb = new BatchBox();
+  *out = bb;
+  bb->ninst = ninst;
+  const int d = ps[0]->g.d;
+  std::vector<PassArgs> args;
+  std::vector<int> start(ninst + 1, 0), rstart(ninst + 1, 0);
+  std::vector<ResDesc> res(ninst);
+  std::vector<PassPlan> plans(ninst), plans_r(ninst);
+  int maxn = 0;
+  for (int i = 0; i < ninst; ++i) {
+    kfbi_problem* p = ps[i];
+    if (p->g.d != d || p->cfg.precision != KFBI_MIXED || p->box == nullptr || p->mg != nullptr)
+      return fail(p0, KFBI_ERR_UNSUPPORTED,
+                  "batched solves need mixed-precision DST problems of one dimension");
+    BoxSolver* B = p->box;
+    plans[i] = plan_passes<float>(p, rhs[i], 1, p->ugrid, 1, B->conv, B->nrm + 3);
+    plans_r[i] = plan_passes<float>(p, B->res, 1, p->ugrid, 1, B->conv, B->nrm + 3);
+    start[i + 1] = start[i] + plans[i].npairs * plans[i].na;
+    const int n1 = p->g.n + 1;
+    rstart[i + 1] = rstart[i] + (d == 2 ? n1 : n1 * n1);
+    res[i] = ResDesc{p->g, p->cfg.order, p->stencil_dev, rhs[i], p->ugrid, B->res, B->nrm, B->conv, B->tol};
+    maxn = std::max(maxn, p->g.n);
+    bb->steps = std::max(bb->steps, B->refine_steps);
+    bb->u.push_back(p->ugrid);
+    bb->rhs.push_back(rhs[i]);
+    bb->ubytes.push_back(sizeof(double) * (size_t)p->g.nodes());
+  }
+  bb->npass = plans[0].npass;
+  for (int v = 0; v <= bb->npass; ++v)
+    for (int i = 0; i < ninst; ++i)
+      args.push_back(v == 0 ? plans[i].args[0] : v == 1 ? plans_r[i].args[0] : plans[i].args[v - 1]);
+  KFBI_CUDA(p0, dalloc(&bb->dargs, args.size()));
+  KFBI_CUDA(p0, dalloc(&bb->dstart, ninst + 1));
+  KFBI_CUDA(p0, dalloc(&bb->dres, ninst));
+  KFBI_CUDA(p0, dalloc(&bb->drstart, ninst + 1));
+  KFBI_CUDA(p0, cudaMemcpy(bb->dargs, args.data(), sizeof(PassArgs) * args.size(), cudaMemcpyHostToDevice));
+  KFBI_CUDA(p0, cudaMemcpy(bb->dstart, start.data(), sizeof(int) * (ninst + 1), cudaMemcpyHostToDevice));
+  KFBI_CUDA(p0, cudaMemcpy(bb->dres, res.data(), sizeof(ResDesc) * ninst, cudaMemcpyHostToDevice));
+  KFBI_CUDA(p0, cudaMemcpy(bb->drstart, rstart.data(), sizeof(int) * (ninst + 1), cudaMemcpyHostToDevice));
+  bb->smem = sizeof(Cx<float>) * (size_t)(2 * maxn) * 2;
+  int dev = 0, optin = 0, sms = 0;
+  KFBI_CUDA(p0, cudaGetDevice(&dev));
+  KFBI_CUDA(p0, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  KFBI_CUDA(p0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  KFBI_CUDA(p0, cudaFuncSetAttribute(k_dst_pass_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  int per_sm = 0;
+  KFBI_CUDA(p0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dst_pass_batched<float>, 256, bb->smem));
+  bb->grid = sms * std::max(1, per_sm);
+  return KFBI_OK;
+}
+
+void batch_box_destroy(BatchBox* bb) {
+  if (!bb) return;
+  cudaFree(bb->dargs);
+  cudaFree(bb->dstart);
+  cudaFree(bb->dres);
+  cudaFree(bb->drstart);
+  delete bb;
+}
+
+// All instances not flagged in `done` (may be null): u_i = A_i^{-1} rhs_i by
+// FP32 transforms with FP64 refinement.
+kfbi_status batch_box_solve(kfbi_problem* p0, BatchBox* bb, const int* done, cudaStream_t st) {
+  const int ni = bb->ninst;
+  for (int i = 0; i < ni; ++i)   // grid sizes differ: one memset per instance
+    KFBI_CUDA(p0, cudaMemsetAsync(bb->u[i], 0, bb->ubytes[i], st));
+  KFBI_LAUNCH(p0, KFBI_KC_RESIDUAL, k_zero_batched<<<div_up(ni, 128), 128, 0, st>>>(bb->dres, ni, done));
+  for (int it = 0; it < bb->steps; ++it) {
+    for (int v = 0; v < bb->npass; ++v) {
+      const PassArgs* a = bb->dargs + (size_t)(v == 0 ? (it == 0 ? 0 : 1) : v + 1) * ni;
+      KFBI_LAUNCH(p0, KFBI_KC_DST, k_dst_pass_batched<float><<<bb->grid, 256, bb->smem, st>>>(a, bb->dstart, ni));
+    }
+    KFBI_LAUNCH(p0, KFBI_KC_RESIDUAL, k_check_batched<<<div_up(ni, 128), 128, 0, st>>>(bb->dres, ni));
+    if (it + 1 < bb->steps)
+      KFBI_LAUNCH(p0, KFBI_KC_RESIDUAL, k_residual_batched<<<bb->grid, 128, 0, st>>>(bb->dres, bb->drstart, ni));
+  }
+  KFBI_CUDA(p0, cudaGetLastError());
+  return KFBI_OK;
+}
+
+}  // namespace kfbi

@@ -134,11 +134,13 @@ __global__ void k_update_x(const double* __restrict__ V, int nb, int k, const do
 // One Arnoldi step in one CTA (N_b moderate): w = V_{j+1} holds A v_j on entry.
 // CGS2 projections, norm, normalisation and the Givens update of column j.
 constexpr int kArnThreads = 1024;
-__global__ void __launch_bounds__(kArnThreads) k_arnoldi_small(
-    double* __restrict__ V, int nb, int j, double* __restrict__ H, int ld,
-    double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
-    double* __restrict__ res) {
-  extern __shared__ double sm[];
+
+// One Arnoldi step by one CTA (N_b moderate): w = V_{j+1} holds A v_j on entry.
+// CGS2 projections (each warp owns whole dot products), norm, normalisation
+// and the Givens update of column j; res = |g_{j+1}|.
+__device__ void arnoldi_step(double* __restrict__ V, int nb, int j, double* __restrict__ H, int ld,
+                             double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
+                             double* __restrict__ res, double* sm) {
   const int nw = kArnThreads / 32;
   double* part = sm;                       // (j+2) x nw
   double* h = part + (size_t)(j + 2) * nw; // j+2
@@ -146,20 +148,17 @@ __global__ void __launch_bounds__(kArnThreads) k_arnoldi_small(
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double* w = V + (size_t)(j + 1) * nb;
   for (int i = tid; i <= j + 1; i += kArnThreads) hacc[i] = 0.0;
+  __syncthreads();
   for (int pass = 0; pass < 2; ++pass) {
-    for (int i = 0; i <= j; ++i) {
+    for (int i = warp; i <= j; i += nw) {
       const double* v = V + (size_t)i * nb;
       double s = 0.0;
-      for (int k = tid; k < nb; k += kArnThreads) s += v[k] * w[k];
+      for (int k = lane; k < nb; k += 32) s += v[k] * w[k];
       s = warp_sum(s);
-      if (lane == 0) part[i * nw + warp] = s;
-    }
-    __syncthreads();
-    for (int i = tid; i <= j; i += kArnThreads) {
-      double s = 0.0;
-      for (int q = 0; q < nw; ++q) s += part[i * nw + q];
-      h[i] = s;
-      hacc[i] += s;
+      if (lane == 0) {
+        h[i] = s;
+        hacc[i] += s;
+      }
     }
     __syncthreads();
     for (int k = tid; k < nb; k += kArnThreads) {
@@ -201,7 +200,104 @@ __global__ void __launch_bounds__(kArnThreads) k_arnoldi_small(
   for (int k = tid; k < nb; k += kArnThreads) w[k] *= inv;
 }
 
+__global__ void __launch_bounds__(kArnThreads) k_arnoldi_small(
+    double* __restrict__ V, int nb, int j, double* __restrict__ H, int ld,
+    double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
+    double* __restrict__ res) {
+  extern __shared__ double sm[];
+  arnoldi_step(V, nb, j, H, ld, cs, sn, g, res, sm);
+}
+
 }  // namespace
+
+// ---- batched Arnoldi over instances (iteration counters on the device) -------
+
+
+namespace {
+
+__global__ void k_copy_in_batched(const ArnDesc* __restrict__ D, const int* __restrict__ jdev,
+                                  const int* __restrict__ done) {
+  const int k = blockIdx.y;
+  if (done[k]) return;
+  const ArnDesc& a = D[k];
+  const double* v = a.V + (size_t)jdev[k] * a.nb;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < a.nb; e += gridDim.x * blockDim.x) a.x[e] = v[e];
+}
+
+__global__ void k_copy_out_batched(const ArnDesc* __restrict__ D, const int* __restrict__ jdev,
+                                   const int* __restrict__ done) {
+  const int k = blockIdx.y;
+  if (done[k]) return;
+  const ArnDesc& a = D[k];
+  if (jdev[k] + 1 > a.m) return;
+  double* v = a.V + (size_t)(jdev[k] + 1) * a.nb;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < a.nb; e += gridDim.x * blockDim.x) v[e] = a.y[e];
+}
+
+__global__ void __launch_bounds__(kArnThreads) k_arnoldi_batched(const ArnDesc* __restrict__ D,
+                                                                 int* __restrict__ jdev,
+                                                                 const int* __restrict__ done,
+                                                                 double* __restrict__ res_out) {
+  extern __shared__ double sm[];
+  const int k = blockIdx.x;
+  const ArnDesc& a = D[k];
+  const int j = jdev[k];
+  if (done[k] || j + 1 > a.m) {
+    if (threadIdx.x == 0) res_out[k] = a.res[0];
+    return;
+  }
+  arnoldi_step(a.V, a.nb, j, a.H, a.ld, a.cs, a.sn, a.g, a.res, sm);
+  if (threadIdx.x == 0) {
+    jdev[k] = j + 1;
+    res_out[k] = a.res[0];
+  }
+}
+
+}  // namespace
+
+kfbi_status batch_arnoldi_copy_in(kfbi_problem* p0, const ArnDesc* d, const int* jdev, const int* done,
+                                  int ninst, int maxnb, cudaStream_t st) {
+  KFBI_LAUNCH(p0, KFBI_KC_GMRES, k_copy_in_batched<<<dim3(div_up(maxnb, 256), ninst), 256, 0, st>>>(d, jdev, done));
+  KFBI_CUDA(p0, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status batch_arnoldi_step(kfbi_problem* p0, const ArnDesc* d, int* jdev, const int* done,
+                               double* res_out, int ninst, int maxnb, int m, cudaStream_t st) {
+  KFBI_LAUNCH(p0, KFBI_KC_GMRES, k_copy_out_batched<<<dim3(div_up(maxnb, 256), ninst), 256, 0, st>>>(d, jdev, done));
+  size_t smem = sizeof(double) * ((size_t)(m + 2) * (kArnThreads / 32) + 2 * (size_t)(m + 2));
+  KFBI_LAUNCH(p0, KFBI_KC_GMRES, k_arnoldi_batched<<<ninst, kArnThreads, smem, st>>>(d, jdev, done, res_out));
+  KFBI_CUDA(p0, cudaGetLastError());
+  return KFBI_OK;
+}
+
+// Initialise GMRES of instance p with zero start: V_0 = b/|b|, g = (|b|, 0, ...).
+kfbi_status gmres_init_zero(kfbi_problem* p, const double* b, double bnorm) {
+  Gmres& G = p->gm;
+  cudaStream_t st = p->stream;
+  const int eb = std::min(div_up(G.nb, 256), 152 * 4);
+  KFBI_CUDA(p, cudaMemcpyAsync(G.scal, &bnorm, sizeof(double), cudaMemcpyHostToDevice, st));
+  KFBI_CUDA(p, cudaMemcpyAsync(G.V, b, sizeof(double) * G.nb, cudaMemcpyDeviceToDevice, st));
+  KFBI_LAUNCH(p, KFBI_KC_GMRES, k_scale<<<eb, 256, 0, st>>>(G.V, G.nb, G.scal, 1));
+  KFBI_LAUNCH(p, KFBI_KC_GMRES, k_init_g<<<1, 128, 0, st>>>(G.g, G.m, G.scal));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status gmres_norm2(kfbi_problem* p, const double* v, double* out_dev) { return dot_self_pub(p, v, out_dev); }
+
+// x = sum_{i < k} y_i V_i after solving H y = g (k x k)
+kfbi_status gmres_finish(kfbi_problem* p, int k, double* x) {
+  Gmres& G = p->gm;
+  cudaStream_t st = p->stream;
+  const int eb = std::min(div_up(G.nb, 256), 152 * 4);
+  KFBI_CUDA(p, cudaMemsetAsync(x, 0, sizeof(double) * G.nb, st));
+  if (k <= 0) return KFBI_OK;
+  KFBI_LAUNCH(p, KFBI_KC_GMRES, k_solve_y<<<1, 1, 0, st>>>(G.H, G.m + 1, k, G.g, G.y));
+  KFBI_LAUNCH(p, KFBI_KC_GMRES, k_update_x<<<eb, 256, 0, st>>>(G.V, G.nb, k, G.y, x));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
 
 constexpr int kSmallArnoldi = 32768;   // N_b up to which one CTA runs the Arnoldi step
 
@@ -239,7 +335,8 @@ void gmres_destroy(kfbi_problem* p) {
 }
 
 // ||v||^2 into out[0] (device)
-static kfbi_status dot_self(kfbi_problem* p, const double* v, double* out) {
+static kfbi_status dot_self(kfbi_problem* p, const double* v, double* out) { return dot_self_pub(p, v, out); }
+kfbi_status dot_self_pub(kfbi_problem* p, const double* v, double* out) {
   Gmres& G = p->gm;
   KFBI_LAUNCH(p, KFBI_KC_GMRES, k_dots<<<dim3(G.nchunk, 1), kDotThreads, 0, p->stream>>>(v, G.nb, 1, v, G.nchunk, G.part));
   KFBI_LAUNCH(p, KFBI_KC_GMRES, k_reduce<<<1, kDotThreads, 0, p->stream>>>(G.part, G.nchunk, out, 0));

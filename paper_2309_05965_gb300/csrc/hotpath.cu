@@ -354,3 +354,194 @@ kfbi_status upload_neighbour_tables(kfbi_problem* p) {
 }
 
 }  // namespace kfbi
+
+// ---------------------------------------------------------------------------
+// Batched variants over many instances (flattened work, instance found by a
+// binary search in a prefix array).  Used by the batched GMRES of batch.cu.
+// ---------------------------------------------------------------------------
+namespace kfbi {
+
+struct BatchHot {
+  int ninst = 0;
+  void* dcv = nullptr;     // CvDesc[ninst]
+  void* dcorr = nullptr;   // CorrDesc[ninst]
+  void* dtr = nullptr;     // TrDesc[ninst]
+  int* dirr_start = nullptr;
+  int* ddof_start = nullptr;
+  int tot_irr = 0, tot_dof = 0;
+};
+
+namespace {
+
+struct CvDesc {
+  int nirr, npde, ndir, nneu;
+  double h;
+  const int32_t* owner;
+  const double* W;
+  const int32_t* dir_idx;
+  const int32_t* neu_idx;
+  const double* a;     // Dirichlet data (density of the Dirichlet form) or null
+  const double* b;     // Neumann data (density of the mu-form) or null
+  double* out;
+};
+
+struct CorrDesc {
+  int nirr, nnb;
+  const int32_t* lin;
+  const uint8_t* irr_inside;
+  const int32_t* corr_nb;
+  const double* nbc;
+  const double* cv;
+  double* R;
+};
+
+struct TrDesc {
+  int nb;
+  TraceCSR tp, tm;
+  const double* u;
+  const double* cv;
+  const double* x;
+  double alpha, beta;
+  double* y;
+};
+
+__device__ __forceinline__ int inst_of(const int* start, int ninst, int item) {
+  int lo = 0, hi = ninst;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (start[mid] <= item) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_cvals_batched(const CvDesc* __restrict__ D, const int* __restrict__ start, int ninst) {
+  const int item = blockIdx.x * blockDim.x + threadIdx.x;
+  if (item >= start[ninst]) return;
+  const int k = inst_of(start, ninst, item);
+  const CvDesc& c = D[k];
+  const int q = item - start[k];
+  const int i = c.owner[q];
+  double acc = 0.0;
+  int j = c.npde;
+  if (c.a) {
+    for (int s = 0; s < c.ndir; ++s, ++j) acc += c.W[(size_t)j * c.nirr + q] * c.a[c.dir_idx[i * c.ndir + s]];
+  } else {
+    j += c.ndir;
+  }
+  if (c.b) {
+    for (int s = 0; s < c.nneu; ++s, ++j)
+      acc += c.W[(size_t)j * c.nirr + q] * (c.h * c.b[c.neu_idx[i * c.nneu + s]]);
+  }
+  c.out[q] = acc;
+}
+
+// R[P] = C_P (the loop right-hand side is zero away from the irregular nodes)
+__global__ void k_rhs_correct_batched(const CorrDesc* __restrict__ D, const int* __restrict__ start,
+                                      int ninst) {
+  const int item = blockIdx.x * blockDim.x + threadIdx.x;
+  if (item >= start[ninst]) return;
+  const int k = inst_of(start, ninst, item);
+  const CorrDesc& c = D[k];
+  const int q = item - start[k];
+  double acc = 0.0;
+  for (int s = 0; s < c.nnb; ++s) {
+    const int j = c.corr_nb[(size_t)s * c.nirr + q];
+    if (j >= 0) acc += c.nbc[s] * c.cv[j];
+  }
+  c.R[c.lin[q]] = c.irr_inside[q] ? -acc : acc;
+}
+
+__global__ void k_trace_op_batched(const TrDesc* __restrict__ D, const int* __restrict__ start,
+                                   int ninst) {
+  const int item = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (item >= start[ninst]) return;
+  const int k = inst_of(start, ninst, item);
+  const TrDesc& t = D[k];
+  const int i = item - start[k];
+  double acc = 0.0;
+  for (int e = t.tp.ptr[i] + lane; e < t.tp.ptr[i + 1]; e += 32) {
+    double w = t.u[t.tp.node[e]];
+    const int j = t.tp.irr[e];
+    if (j >= 0) w += t.cv[j];
+    acc += t.tp.w[e] * w;
+  }
+  for (int e = t.tm.ptr[i] + lane; e < t.tm.ptr[i + 1]; e += 32) {
+    double w = t.u[t.tm.node[e]];
+    const int j = t.tm.irr[e];
+    if (j >= 0) w -= t.cv[j];
+    acc += t.tm.w[e] * w;
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) t.y[i] = t.alpha * t.x[i] + t.beta * acc;
+}
+
+}  // namespace
+
+kfbi_status batch_hot_create(kfbi_problem* p0, kfbi_problem* const* ps, int ninst, double* const* x,
+                             double* const* y, double* const* rhs, BatchHot** out) {
+  BatchHot* bh = new BatchHot();
+  *out = bh;
+  bh->ninst = ninst;
+  std::vector<CvDesc> cv(ninst);
+  std::vector<CorrDesc> co(ninst);
+  std::vector<TrDesc> tr(ninst);
+  std::vector<int> is(ninst + 1, 0), ds(ninst + 1, 0);
+  for (int k = 0; k < ninst; ++k) {
+    kfbi_problem* p = ps[k];
+    const bool dir = p->cfg.kind == KFBI_DIRICHLET_INTERIOR;
+    cv[k] = CvDesc{p->nirr, p->npde, p->ndir, p->nneu, p->g.h, p->irr_owner, p->irr_w,
+                   p->dir_idx, p->neu_idx, dir ? x[k] : nullptr, dir ? nullptr : x[k], p->cvals};
+    co[k] = CorrDesc{p->nirr, p->n_nb, p->irr_lin, p->irr_inside, p->corr_nb, p->nb_coef, p->cvals, rhs[k]};
+    tr[k] = TrDesc{p->nb, p->tr[0], p->tr[1], p->ugrid, p->cvals, x[k], 0.5, dir ? 1.0 : -p->mu, y[k]};
+    is[k + 1] = is[k] + p->nirr;
+    ds[k + 1] = ds[k] + p->nb;
+  }
+  bh->tot_irr = is[ninst];
+  bh->tot_dof = ds[ninst];
+  CvDesc* a = nullptr;
+  CorrDesc* b = nullptr;
+  TrDesc* c = nullptr;
+  KFBI_CUDA(p0, dalloc(&a, ninst));
+  KFBI_CUDA(p0, dalloc(&b, ninst));
+  KFBI_CUDA(p0, dalloc(&c, ninst));
+  KFBI_CUDA(p0, dalloc(&bh->dirr_start, ninst + 1));
+  KFBI_CUDA(p0, dalloc(&bh->ddof_start, ninst + 1));
+  bh->dcv = a;
+  bh->dcorr = b;
+  bh->dtr = c;
+  KFBI_CUDA(p0, cudaMemcpy(a, cv.data(), sizeof(CvDesc) * ninst, cudaMemcpyHostToDevice));
+  KFBI_CUDA(p0, cudaMemcpy(b, co.data(), sizeof(CorrDesc) * ninst, cudaMemcpyHostToDevice));
+  KFBI_CUDA(p0, cudaMemcpy(c, tr.data(), sizeof(TrDesc) * ninst, cudaMemcpyHostToDevice));
+  KFBI_CUDA(p0, cudaMemcpy(bh->dirr_start, is.data(), sizeof(int) * (ninst + 1), cudaMemcpyHostToDevice));
+  KFBI_CUDA(p0, cudaMemcpy(bh->ddof_start, ds.data(), sizeof(int) * (ninst + 1), cudaMemcpyHostToDevice));
+  return KFBI_OK;
+}
+
+void batch_hot_destroy(BatchHot* bh) {
+  if (!bh) return;
+  cudaFree(bh->dcv);
+  cudaFree(bh->dcorr);
+  cudaFree(bh->dtr);
+  cudaFree(bh->dirr_start);
+  cudaFree(bh->ddof_start);
+  delete bh;
+}
+
+kfbi_status batch_hot_cvals_rhs(kfbi_problem* p0, BatchHot* bh, cudaStream_t st) {
+  KFBI_LAUNCH(p0, KFBI_KC_CORRECTION, k_cvals_batched<<<div_up(bh->tot_irr, 128), 128, 0, st>>>(
+      static_cast<const CvDesc*>(bh->dcv), bh->dirr_start, bh->ninst));
+  KFBI_LAUNCH(p0, KFBI_KC_RHS, k_rhs_correct_batched<<<div_up(bh->tot_irr, 128), 128, 0, st>>>(
+      static_cast<const CorrDesc*>(bh->dcorr), bh->dirr_start, bh->ninst));
+  KFBI_CUDA(p0, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status batch_hot_trace(kfbi_problem* p0, BatchHot* bh, cudaStream_t st) {
+  KFBI_LAUNCH(p0, KFBI_KC_TRACE, k_trace_op_batched<<<div_up(bh->tot_dof, 8), 256, 0, st>>>(
+      static_cast<const TrDesc*>(bh->dtr), bh->ddof_start, bh->ninst));
+  KFBI_CUDA(p0, cudaGetLastError());
+  return KFBI_OK;
+}
+
+}  // namespace kfbi

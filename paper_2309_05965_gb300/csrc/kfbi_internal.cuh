@@ -256,5 +256,43 @@ void gmres_destroy(kfbi_problem* p);
 kfbi_status apply_operator_fast(kfbi_problem* p, const double* x, double* y);
 kfbi_status gmres_run(kfbi_problem* p, const double* b, const double* x0, double rtol,
                       int restart, int max_iter, double* x, int* iters, double* rel);
+kfbi_status dot_self_pub(kfbi_problem* p, const double* v, double* out);
+kfbi_status gmres_init_zero(kfbi_problem* p, const double* b, double bnorm);
+kfbi_status gmres_finish(kfbi_problem* p, int k, double* x);
+// capi.cu
+kfbi_status bie_rhs_impl(kfbi_problem* p, const kfbi_data* data, double* bvec);
+
+// ---- batched pieces (many independent problems in lockstep) -------------------
+// One GMRES instance as seen by the batched Arnoldi kernels.
+struct ArnDesc {
+  double* V;
+  int nb, m;
+  double* H;
+  int ld;
+  double* cs;
+  double* sn;
+  double* g;
+  double* res;
+  double* x;   // operator input buffer
+  double* y;   // operator output buffer
+};
+struct BatchBox;
+struct BatchHot;
+// dst.cu
+kfbi_status batch_box_create(kfbi_problem* p0, kfbi_problem* const* ps, int ninst,
+                             double* const* rhs, BatchBox** out);
+void batch_box_destroy(BatchBox* bb);
+kfbi_status batch_box_solve(kfbi_problem* p0, BatchBox* bb, const int* done, cudaStream_t st);
+// hotpath.cu
+kfbi_status batch_hot_create(kfbi_problem* p0, kfbi_problem* const* ps, int ninst, double* const* x,
+                             double* const* y, double* const* rhs, BatchHot** out);
+void batch_hot_destroy(BatchHot* bh);
+kfbi_status batch_hot_cvals_rhs(kfbi_problem* p0, BatchHot* bh, cudaStream_t st);
+kfbi_status batch_hot_trace(kfbi_problem* p0, BatchHot* bh, cudaStream_t st);
+// gmres.cu
+kfbi_status batch_arnoldi_copy_in(kfbi_problem* p0, const ArnDesc* d, const int* jdev, const int* done,
+                                  int ninst, int maxnb, cudaStream_t st);
+kfbi_status batch_arnoldi_step(kfbi_problem* p0, const ArnDesc* d, int* jdev, const int* done,
+                               double* res_out, int ninst, int maxnb, int m, cudaStream_t st);
 
 }  // namespace kfbi

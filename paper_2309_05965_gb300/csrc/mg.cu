@@ -327,12 +327,40 @@ __global__ void k_to_float(long long tot, const double* __restrict__ a, float* _
     b[t] = (float)a[t];
 }
 
+// u += e, with max|e| -> corr[0] and max|u| -> corr[1]
 __global__ void k_add_float(long long tot, const float* __restrict__ e, double* __restrict__ u,
-                            const int* skip) {
+                            unsigned long long* __restrict__ corr, const int* skip) {
   if (skip && *skip) return;
+  double em = 0.0, um = 0.0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-       t += (long long)gridDim.x * blockDim.x)
-    u[t] += (double)e[t];
+       t += (long long)gridDim.x * blockDim.x) {
+    double ev = (double)e[t];
+    double nv = u[t] + ev;
+    u[t] = nv;
+    em = fmax(em, fabs(ev));
+    um = fmax(um, fabs(nv));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    em = fmax(em, __shfl_xor_sync(0xffffffffu, em, o));
+    um = fmax(um, __shfl_xor_sync(0xffffffffu, um, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (em > 0.0) atomicMax(corr, (unsigned long long)__double_as_longlong(em));
+    if (um > 0.0) atomicMax(corr + 1, (unsigned long long)__double_as_longlong(um));
+  }
+}
+
+// mixed: conv = (max|e_k| <= tol max|u|), the FP32 cycles contract the error by
+// orders of magnitude per outer step, so the last correction bounds the error
+__global__ void k_mg_check_corr(unsigned long long* nrm, double tol, int* conv) {
+  if (*conv) return;
+  double em = __longlong_as_double((long long)nrm[6]);
+  double um = __longlong_as_double((long long)nrm[7]);
+  nrm[8] = nrm[6];
+  nrm[9] = nrm[7];
+  if (em <= tol * um) *conv = 1;
+  nrm[6] = 0ull;
+  nrm[7] = 0ull;
 }
 
 __global__ void k_mg_residual64(Grid g, int order, const double* __restrict__ c,
@@ -343,16 +371,23 @@ __global__ void k_mg_residual64(Grid g, int order, const double* __restrict__ c,
   const int n1 = g.n + 1;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i1 = blockIdx.y, i0 = blockIdx.z;
-  double mx = 0.0;
+  double mx = 0.0, ux = 0.0;
   if (j <= g.n) {
     const long long t = lin(g.d, n1, i0, i1, j);
     const bool interior = j >= 1 && j < g.n && i1 >= 1 && i1 < g.n && (g.d == 2 || (i0 >= 1 && i0 < g.n));
     double v = interior ? R[t] - apply_at<double>(g.d, order, n1, c, u + t) : 0.0;
     if (r) r[t] = v;
     mx = fabs(v);
+    ux = fabs(u[t]);
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(nrm, (unsigned long long)__double_as_longlong(mx));
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    ux = fmax(ux, __shfl_xor_sync(0xffffffffu, ux, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (mx > 0.0) atomicMax(nrm, (unsigned long long)__double_as_longlong(mx));
+    if (ux > 0.0) atomicMax(nrm + 2, (unsigned long long)__double_as_longlong(ux));
+  }
 }
 
 __global__ void k_absmax_mg(long long tot, const double* __restrict__ R, unsigned long long* nrm) {
@@ -364,17 +399,24 @@ __global__ void k_absmax_mg(long long tot, const double* __restrict__ R, unsigne
   if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(nrm, (unsigned long long)__double_as_longlong(mx));
 }
 
-__global__ void k_mg_check(unsigned long long* nrm, double tol, int* conv) {
+// FP64 V-cycles: stop at the normwise backward error max|r| <= tol (max|R| +
+// ||A||_inf max|u|) or when the residual stagnates (r_k > 0.7 r_{k-1}) at the
+// rounding floor eps ||A|| ||u|| of the FP64 residual.
+__global__ void k_mg_check(unsigned long long* nrm, double tol, double anorm, int* conv) {
   if (*conv) return;
   double R = __longlong_as_double((long long)nrm[0]);
   double r = __longlong_as_double((long long)nrm[1]);
-  nrm[2] = nrm[1];
-  if (r <= tol * R) *conv = 1;
+  double um = __longlong_as_double((long long)nrm[2]);
+  double rp = __longlong_as_double((long long)nrm[4]);
+  nrm[4] = nrm[1];
+  nrm[5] = nrm[2];
+  if (r <= tol * (R + anorm * um) || (rp > 0.0 && r > 0.7 * rp)) *conv = 1;
   nrm[1] = 0ull;
+  nrm[2] = 0ull;
 }
 
 __global__ void k_mg_reset(unsigned long long* nrm, int* conv) {
-  nrm[0] = nrm[1] = nrm[2] = 0ull;
+  for (int k = 0; k < 10; ++k) nrm[k] = 0ull;
   *conv = 0;
 }
 
@@ -396,6 +438,7 @@ struct MgSolver {
   int inner_cycles = 4;
   int outer_max = 6;
   double tol = 1e-13;
+  double anorm = 0.0;          // ||A_h||_inf = sum of |stencil coefficients|
 };
 
 namespace {
@@ -570,6 +613,7 @@ kfbi_status mg_create(kfbi_problem* p) {
   p->mg = M;
   M->precision = p->cfg.precision;
   M->tol = p->cfg.box_rtol > 0 ? p->cfg.box_rtol : 1e-13;
+  M->outer_max = p->cfg.box_max_iters > 0 ? std::min(p->cfg.box_max_iters, 12) : 8;
   M->max_cycles = p->cfg.box_max_iters > 0 ? p->cfg.box_max_iters : 40;
   const long long nodes = g.nodes();
   if (M->precision == KFBI_MIXED) {
@@ -580,7 +624,16 @@ kfbi_status mg_create(kfbi_problem* p) {
   } else {
     KFBI_TRY(build_levels<double>(p, M, M->A64, &M->cinv64, false));
   }
-  KFBI_CUDA(p, dalloc(&M->nrm, 3));
+  {
+    const double* c = p->stencil_c;
+    const int d = g.d;
+    double a = std::fabs(c[0]);
+    if (p->cfg.order == 2) a += 2 * d * std::fabs(c[1]);
+    else if (d == 2) a += 4 * std::fabs(c[1]) + 4 * std::fabs(c[2]);
+    else a += 6 * std::fabs(c[1]) + 12 * std::fabs(c[2]) + 8 * std::fabs(c[3]);
+    M->anorm = a;
+  }
+  KFBI_CUDA(p, dalloc(&M->nrm, 10));
   KFBI_CUDA(p, dalloc(&M->conv, 1));
   M->bufs.push_back(M->nrm);
   M->bufs.push_back(M->conv);
@@ -613,7 +666,7 @@ kfbi_status mg_solve(kfbi_problem* p, const double* rhs, double* u) {
       KFBI_TRY(vcycle<double>(p, A, M->lcoarse, c == 0, M->conv));
       KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_mg_residual64<<<gr, 128, 0, st>>>(
           g, p->cfg.order, p->stencil_dev, rhs, u, nullptr, M->nrm + 1, M->conv));
-      KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_mg_check<<<1, 1, 0, st>>>(M->nrm, M->tol, M->conv));
+      KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_mg_check<<<1, 1, 0, st>>>(M->nrm, M->tol, M->anorm, M->conv));
     }
     KFBI_CUDA(p, cudaGetLastError());
     return KFBI_OK;
@@ -626,10 +679,10 @@ kfbi_status mg_solve(kfbi_problem* p, const double* rhs, double* u) {
         nodes, r, A.L[0].f, M->conv));
     for (int c = 0; c < M->inner_cycles; ++c) KFBI_TRY(vcycle<float>(p, A, M->lcoarse, c == 0, M->conv));
     KFBI_LAUNCH(p, KFBI_KC_MG, k_add_float<<<std::min(div_up(nodes, 256), 152 * 8), 256, 0, st>>>(
-        nodes, A.L[0].u, u, M->conv));
+        nodes, A.L[0].u, u, M->nrm + 6, M->conv));
+    KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_mg_check_corr<<<1, 1, 0, st>>>(M->nrm, M->tol, M->conv));
     KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_mg_residual64<<<gr, 128, 0, st>>>(
         g, p->cfg.order, p->stencil_dev, rhs, u, M->r64, M->nrm + 1, M->conv));
-    KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_mg_check<<<1, 1, 0, st>>>(M->nrm, M->tol, M->conv));
     r = M->r64;
   }
   KFBI_CUDA(p, cudaGetLastError());
@@ -638,15 +691,22 @@ kfbi_status mg_solve(kfbi_problem* p, const double* rhs, double* u) {
 
 kfbi_status mg_last_residual(kfbi_problem* p, double* rel, int* converged) {
   MgSolver* M = p->mg;
-  unsigned long long h[3];
+  unsigned long long h[10];
   int c = 0;
   KFBI_CUDA(p, cudaMemcpyAsync(h, M->nrm, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
   KFBI_CUDA(p, cudaMemcpyAsync(&c, M->conv, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
   KFBI_CUDA(p, cudaStreamSynchronize(p->stream));
-  double R, r;
-  memcpy(&R, &h[0], 8);
-  memcpy(&r, &h[2], 8);
-  *rel = R > 0 ? r / R : 0.0;
+  double R, r, um;
+  if (M->precision == KFBI_MIXED) {
+    memcpy(&r, &h[8], 8);
+    memcpy(&um, &h[9], 8);
+    *rel = um > 0 ? r / um : 0.0;
+  } else {
+    memcpy(&R, &h[0], 8);
+    memcpy(&r, &h[4], 8);
+    memcpy(&um, &h[5], 8);
+    *rel = (R + M->anorm * um) > 0 ? r / (R + M->anorm * um) : 0.0;
+  }
   *converged = c;
   return KFBI_OK;
 }

@@ -87,6 +87,9 @@ SIGNATURES = {
     "kfbi_gmres_solve": [_P, ctypes.POINTER(Data), ctypes.POINTER(GmresOpts), _P,
                          ctypes.POINTER(GmresInfo)],
     "kfbi_evaluate": [_P, ctypes.POINTER(Data), _P, _P],
+    "kfbi_create_batch": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)],
+    "kfbi_destroy_batch": [_P],
+    "kfbi_gmres_solve_batch": [_P, _P, ctypes.POINTER(GmresOpts), _P, _P],
     "kfbi_box_solve_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                ctypes.c_int, ctypes.c_double, _P, _P, _P],
     "kfbi_launch_counts": [_P, _P, ctypes.c_int],
@@ -234,6 +237,31 @@ def kfbi_evaluate(h, data, density, u):
     _check(load().kfbi_evaluate(h, ctypes.byref(data), _ptr(density), _ptr(u)), h)
 
 
+def kfbi_create_batch(handles):
+    """Batch over problem handles (errors are reported on handles[0])."""
+    arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
+    b = ctypes.c_void_p()
+    _check(load().kfbi_create_batch(ctypes.cast(arr, ctypes.c_void_p), len(handles),
+                                    ctypes.byref(b)), handles[0])
+    return b
+
+
+def kfbi_destroy_batch(b):
+    _check(load().kfbi_destroy_batch(b))
+
+
+def kfbi_gmres_solve_batch(b, handles, datas, opts: GmresOpts, densities):
+    """Algorithm 1 for every instance; returns one GmresInfo per instance."""
+    n = len(handles)
+    darr = (Data * n)(*datas)
+    parr = (ctypes.c_void_p * n)(*[_ptr(x).value for x in densities])
+    infos = (GmresInfo * n)()
+    _check(load().kfbi_gmres_solve_batch(b, ctypes.cast(darr, ctypes.c_void_p), ctypes.byref(opts),
+                                         ctypes.cast(parr, ctypes.c_void_p),
+                                         ctypes.cast(infos, ctypes.c_void_p)), handles[0])
+    return list(infos)
+
+
 def kfbi_box_solve_noalloc(dim, n, lo, hi, order, kappa, rhs, u, stream=None):
     """FP64 DST box solve with no device allocation (fixed library scratch)."""
     _check(load().kfbi_box_solve_noalloc(dim, n, lo, hi, order, kappa, _ptr(rhs), _ptr(u),
@@ -300,3 +328,26 @@ class Problem:
     @property
     def grid_shape(self):
         return (self.n + 1,) * self.dim
+
+
+class Batch:
+    """Owns one kfbi_batch over Problem objects (kept alive by the batch)."""
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        self.handle = kfbi_create_batch([q.handle for q in self.problems])
+
+    def gmres_solve(self, datas, opts: GmresOpts, densities):
+        return kfbi_gmres_solve_batch(self.handle, [q.handle for q in self.problems], datas, opts,
+                                      densities)
+
+    def close(self):
+        if self.handle is not None:
+            kfbi_destroy_batch(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

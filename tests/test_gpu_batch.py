@@ -1,0 +1,133 @@
+"""Batched GMRES (many independent interface problems in lockstep) against the
+per-instance solve and the oracle.
+
+Instances are the seeded star-interface draws of the batched workload at two
+grid sizes; an instance whose interface the drawn grid cannot resolve (no
+complete collocation stencil) moves to the next size, on both sides alike."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import kfbi as OK
+from tests.gpu_util import empty, gpu_data, host, rel_err
+
+pytestmark = pytest.mark.gpu
+
+SIZES = (128, 256, 512)
+
+
+def _instances(count, seed=5965):
+    from paper_2309_05965_gb300 import build, kfbi
+    build.build()
+    out = []
+    for w in W.star_batch_2d(count=count, seed=seed, sizes=SIZES[:2]):
+        for n in [s for s in SIZES if s >= w.n]:
+            w.n = n
+            try:
+                G = kfbi.Problem.from_workload(w, precision=kfbi.MIXED)
+            except kfbi.KfbiError as e:
+                assert e.status == 2   # under-resolved: next size
+                continue
+            out.append((w, G))
+            break
+    return out
+
+
+_cache = {}
+
+
+def _setup():
+    if "inst" not in _cache:
+        inst = _instances(6)
+        rows = []
+        for w, G in inst:
+            P = OK.Problem(w)
+            data = W.grid_data(w)
+            g1, g2 = W.boundary_data(w, P.surf.x, P.surf.n)
+            d, keep = gpu_data(w, P, data, g1, g2)
+            rows.append(dict(w=w, G=G, P=P, data=data, g1=g1, g2=g2, d=d, keep=keep))
+        _cache["inst"] = rows
+    return _cache["inst"]
+
+
+def test_batch_matches_single_and_oracle():
+    """Each instance of one batched solve: the same iteration count as its own
+    solve (the residual estimates agree to rounding), the density within 1e-9
+    of it (both use FP32 transforms with FP64 refinement to 1e-11), a backward
+    error <= 1e-8 in the oracle's FP64 discrete system, and the evaluated
+    solution within discretisation accuracy of the exact one."""
+    from paper_2309_05965_gb300 import kfbi
+    rows = _setup()
+    assert len({r["w"].n for r in rows}) >= 2, "the batch must mix grid sizes"
+    opts = kfbi.GmresOpts(rtol=1e-10, restart=100, max_iter=100, x0=None)
+    singles = []
+    for r in rows:
+        x = empty(r["G"].nb)
+        info = kfbi.kfbi_gmres_solve(r["G"].handle, r["d"], opts, x)
+        singles.append((host(x), info.iters))
+    B = kfbi.Batch([r["G"] for r in rows])
+    dens = [empty(r["G"].nb) for r in rows]
+    infos = B.gmres_solve([r["d"] for r in rows], opts, dens)
+    for r, x, info, (xs, its) in zip(rows, dens, infos, singles):
+        xb = host(x)
+        assert abs(info.iters - its) <= 1, (r["w"].name, info.iters, its)
+        assert info.rel_res <= 1e-10
+        assert rel_err(xb, xs) < 1e-9, r["w"].name
+        P = r["P"]
+        b_ref = P.bie_rhs(r["g1"], r["g2"], r["data"])
+        res = np.linalg.norm(b_ref - P.apply(xb)) / np.linalg.norm(b_ref)
+        assert res < 1e-8, (r["w"].name, res)
+        u = empty(r["G"].grid_shape)
+        kfbi.kfbi_evaluate(r["G"].handle, r["d"], x, u)
+        ex = W.exact_grid(r["w"], P.inside)
+        w = r["w"]
+        inner = np.zeros(P.inside.shape, bool)
+        inner[tuple(slice(1, w.n) for _ in range(w.dim))] = True
+        assert np.abs(host(u) - ex)[inner].max() < 1e-3
+    # a second solve on the same batch (graph replayed, counters reset)
+    infos2 = B.gmres_solve([r["d"] for r in rows], opts, dens)
+    assert [i.iters for i in infos2] == [i.iters for i in infos]
+    B.close()
+
+
+def test_batch_edge_cases():
+    """One-instance batch; an instance with zero data (converged at start:
+    zero density, 0 iterations) beside a normal one; an iteration limit that
+    stops every instance (NOT_CONVERGED after all densities are written);
+    unsupported configurations are refused."""
+    from paper_2309_05965_gb300 import kfbi
+    rows = _setup()
+    r0, r1 = rows[0], rows[1]
+    opts = kfbi.GmresOpts(rtol=1e-10, restart=100, max_iter=100, x0=None)
+    x_single = empty(r0["G"].nb)
+    it_single = kfbi.kfbi_gmres_solve(r0["G"].handle, r0["d"], opts, x_single).iters
+    B1 = kfbi.Batch([r0["G"]])
+    x = empty(r0["G"].nb)
+    (info,) = B1.gmres_solve([r0["d"]], opts, [x])
+    assert abs(info.iters - it_single) <= 1
+    assert rel_err(host(x), host(x_single)) < 1e-9
+    B1.close()
+
+    z = {k: (v.clone().zero_() if v is not None else None) for k, v in r1["keep"].items()}
+    dz = kfbi.make_data(g1=z["g1"], g2=z["g2"], f_in=z["f_in"], f_out=z["f_out"],
+                        lapf_in=z["lapf_in"], lapf_out=z["lapf_out"], g_b=z["g_b"])
+    B2 = kfbi.Batch([r0["G"], r1["G"]])
+    xs = [empty(r0["G"].nb), empty(r1["G"].nb).fill_(7.0)]
+    infos = B2.gmres_solve([r0["d"], dz], opts, xs)
+    assert infos[1].iters == 0 and float(np.abs(host(xs[1])).max()) == 0.0
+    assert abs(infos[0].iters - it_single) <= 1
+    assert rel_err(host(xs[0]), host(x_single)) < 1e-9
+
+    short = kfbi.GmresOpts(rtol=1e-14, restart=100, max_iter=3, x0=None)
+    with pytest.raises(kfbi.KfbiError) as e:
+        B2.gmres_solve([r0["d"], r1["d"]], short, xs)
+    assert e.value.status == 4
+    assert float(np.abs(host(xs[1])).max()) > 0.0
+    B2.close()
+
+    w = rows[0]["w"]
+    G64 = kfbi.Problem.from_workload(w, precision=kfbi.FP64)
+    with pytest.raises(kfbi.KfbiError) as e:
+        kfbi.Batch([r0["G"], G64])
+    assert e.value.status == 8
+    G64.close()
