@@ -118,7 +118,8 @@ def run_ours(args, rank, world):
     box = kfbi.BOX_MG if args.box == "mg" else kfbi.BOX_DST
     t0 = time.perf_counter()
     G = kfbi.Problem.from_workload(w, box_solver=box, precision=prec,
-                                   box_rtol=args.box_rtol if prec == kfbi.MIXED else 0.0)
+                                   box_rtol=args.box_rtol if prec == kfbi.MIXED else 0.0,
+                                   box_max_iters=args.box_steps)
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
     d = w.dim
@@ -264,6 +265,7 @@ def run_ours(args, rank, world):
                                f"4th order, GMRES rtol {args.rtol:g}",
                    "box_solver": args.box, "precision": args.precision, "n_b": G.nb,
                    "box_rtol": args.box_rtol if prec == kfbi.MIXED else None,
+                   "box_steps": args.box_steps or None,
                    "n_irr": G.nirr, "l2": "flushed (256 MB write) before every step",
                    "parallelism": "independent replicas" if world > 1 else "1 GPU"},
         "gmres_iterations": iters[-1], "max_err_vs_exact": err,
@@ -282,6 +284,8 @@ def run_ours(args, rank, world):
     G.close()
     if args.batch > 0:
         out["batched"] = batched(args, stream, flush)
+    if args.learned_n > 0:
+        out["learned"] = learned_leg(args, stream, flush)
     if rank == 0 and args.cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_budget)
     return out
@@ -289,11 +293,11 @@ def run_ours(args, rank, world):
 
 def batched(args, stream, flush):
     """The batched workload: 64 seeded star-interface problems on grids drawn
-    from {128, 256, 512, 1024}^2 (an instance whose interface its drawn grid
-    cannot resolve moves to the next size), all solved by one batched GMRES
+    from {128, 256, 512, 1024}^2, all solved by one batched GMRES
     (kfbi_gmres_solve_batch) plus the per-instance evaluation.  Compared with
     the same instances solved one after another by the plain FP64 path and by
-    the mixed path."""
+    the mixed path.  Draws whose interface the drawn grid cannot resolve are
+    skipped and counted (the seeded stream continues)."""
     import numpy as np
     import torch
 
@@ -301,20 +305,21 @@ def batched(args, stream, flush):
     from paper_2309_05965_gb300 import kfbi
     sizes = (128, 256, 512, 1024)
     inst = []
-    bumped = 0
-    for w in W.star_batch_2d(count=args.batch, seed=5965, sizes=sizes):
-        drawn = w.n
-        for n in [s for s in sizes if s >= drawn]:
-            w.n = n
-            try:
-                G = kfbi.Problem.from_workload(w, precision=kfbi.MIXED, box_rtol=args.box_rtol)
-            except kfbi.KfbiError as e:
-                if e.status != 2:
-                    raise
-                continue
-            bumped += n != drawn
-            inst.append((w, G))
+    redrawn = 0
+    # one seeded stream; a draw whose interface its grid cannot resolve
+    # (KFBI_ERR_GEOMETRY) is dropped and the stream continues
+    for w in W.star_batch_2d(count=4 * args.batch, seed=5965, sizes=sizes):
+        if len(inst) == args.batch:
             break
+        try:
+            G = kfbi.Problem.from_workload(w, precision=kfbi.MIXED, box_rtol=args.box_rtol,
+                                           box_max_iters=args.box_steps)
+        except kfbi.KfbiError as e:
+            if e.status != 2:
+                raise
+            redrawn += 1
+            continue
+        inst.append((w, G))
     rows = []
     for w, G in inst:
         xyz = torch.zeros((G.nb, 2), dtype=torch.float64, device="cuda")
@@ -391,7 +396,7 @@ def batched(args, stream, flush):
         nsz[r["w"].n] = nsz.get(r["w"].n, 0) + 1
     out = {"workload": f"{len(rows)} star-interface problems, grids {nsz}, contrast 10^U[0,3], "
                        f"GMRES rtol {args.rtol:g}",
-           "instances": len(rows), "moved_to_finer_grid": bumped,
+           "instances": len(rows), "redrawn_unresolved": redrawn,
            "solves_per_s": len(rows) / (ms_batch * 1e-3), "ms_per_batch": ms_batch,
            "fp64_sequential_solves_per_s": len(rows) / (ms_fp64_seq * 1e-3),
            "mixed_sequential_solves_per_s": len(rows) / (ms_mixed_seq * 1e-3),
@@ -401,6 +406,111 @@ def batched(args, stream, flush):
     B.close()
     for r in rows:
         r["G"].close()
+    return out
+
+
+def learned_leg(args, stream, flush):
+    """Learned initial density on the harmonic ellipsoid family: train the
+    network on 2000 solves (40 ellipsoids x 50 data draws) on a 64^3 grid, then
+    on held-out ellipsoids at --learned-n^3 compare the plain FP64 path, the
+    mixed path from zero and the mixed path from the learned start (the
+    prediction is inside the timed region)."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2309_05965_gb300 import kfbi, learned
+
+    def solve_data(G, w):
+        xyz = torch.zeros((G.nb, 3), dtype=torch.float64, device="cuda")
+        nrm = torch.zeros((G.nb, 3), dtype=torch.float64, device="cuda")
+        kfbi.kfbi_dof_points(G.handle, xyz, nrm)
+        g1, g2 = W.boundary_data(w, xyz.cpu().numpy(), nrm.cpu().numpy())
+        grid = W.grid_data(w)
+        keep = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in
+                (("g1", g1), ("g2", g2), ("f_in", grid["f_in"]), ("f_out", grid["f_out"]),
+                 ("lapf_in", grid["lapf_in"]), ("lapf_out", grid["lapf_out"]),
+                 ("g_b", grid["g_b"]))}
+        return kfbi.make_data(**keep), keep
+
+    t0 = time.perf_counter()
+    opts = kfbi.GmresOpts(rtol=1e-10, restart=100, max_iter=100, x0=None)
+    train = W.warm_start_training_set(seed=5966, geometries=args.learned_geometries,
+                                      draws=args.learned_draws)
+    ds = learned.Dataset(args.learned_geometries * args.learned_draws * 8000)
+    for axes, amps_list in train:
+        G = kfbi.Problem.from_workload(W.harmonic_ellipsoid_3d(axes, amps_list[0], 64),
+                                       precision=kfbi.MIXED)
+        x = torch.zeros(G.nb, dtype=torch.float64, device="cuda")
+        for amps in amps_list:
+            d, keep = solve_data(G, W.harmonic_ellipsoid_3d(axes, amps, 64))
+            kfbi.kfbi_gmres_solve(G.handle, d, opts, x)
+            ds.add(G, d, x)
+        G.close()
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ws = learned.WarmStart(seed=5965)
+    hist = ws.fit(ds, epochs=args.learned_epochs, batch=8192, lr=2e-3, lr_final=1e-6)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+
+    n = args.learned_n
+    eopts = kfbi.GmresOpts(rtol=args.rtol, restart=100, max_iter=100, x0=None)
+    rows = {"fp64_zero": [], "mixed_zero": [], "mixed_learned": []}
+    for axes, amps_list in W.warm_start_training_set(seed=5967, geometries=1,
+                                                     draws=args.learned_eval):
+        w0 = W.harmonic_ellipsoid_3d(axes, amps_list[0], n)
+        Gm = kfbi.Problem.from_workload(w0, precision=kfbi.MIXED, box_rtol=args.box_rtol)
+        G64 = kfbi.Problem.from_workload(w0, precision=kfbi.FP64)
+        x = torch.zeros(Gm.nb, dtype=torch.float64, device="cuda")
+        x0 = torch.zeros_like(x)
+        u = torch.zeros(Gm.grid_shape, dtype=torch.float64, device="cuda")
+        ins = _inside(Gm, kfbi)
+        for amps in amps_list:
+            w = W.harmonic_ellipsoid_3d(axes, amps, n)
+            d, keep = solve_data(Gm, w)
+            ex = W.exact_grid(w, ins)
+            for name, G, use in (("fp64_zero", G64, False), ("mixed_zero", Gm, False),
+                                 ("mixed_learned", Gm, True)):
+                def run():
+                    o = eopts
+                    if use:
+                        ws.predict(G, d, x0)
+                        o = kfbi.GmresOpts(rtol=args.rtol, restart=100, max_iter=100,
+                                           x0=x0.data_ptr())
+                    info = kfbi.kfbi_gmres_solve(G.handle, d, o, x)
+                    kfbi.kfbi_evaluate(G.handle, d, x, u)
+                    return info
+                run()
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                info = run()
+                e1.record(stream)
+                e1.synchronize()
+                err = float(np.abs(u.cpu().numpy() - ex)[1:-1, 1:-1, 1:-1].max())
+                rows[name].append((e0.elapsed_time(e1), info.iters, err, info.x0_rejected))
+        Gm.close()
+        G64.close()
+    ws.close()
+
+    def agg(r):
+        ms = statistics.mean(v[0] for v in r)
+        return {"solves_per_s": 1e3 / ms, "ms_per_solve": ms,
+                "gmres_iterations": [v[1] for v in r], "max_err_vs_exact": max(v[2] for v in r),
+                "x0_rejected": sum(v[3] for v in r)}
+    out = {k: agg(v) for k, v in rows.items()}
+    out["workload"] = (f"ellipsoid interface 3D, N={n}, contrast 10, harmonic data; network "
+                       f"3 layers x 256 trained on {ds.solves} solves at 64^3 "
+                       f"({ds.n} DOF samples), GMRES rtol {args.rtol:g}")
+    out["train"] = {"data_s": t_data, "train_s": t_train, "loss_first_epoch": hist[0],
+                    "loss_last_epoch": hist[-1], "epochs": len(hist)}
+    out["speedup_learned_mixed_vs_fp64_zero"] = (out["mixed_learned"]["solves_per_s"]
+                                                 / out["fp64_zero"]["solves_per_s"])
+    out["err_ratio_learned_vs_fp64"] = (out["mixed_learned"]["max_err_vs_exact"]
+                                        / max(out["fp64_zero"]["max_err_vs_exact"], 1e-300))
     return out
 
 
@@ -506,6 +616,8 @@ def main():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--box-rtol", type=float, default=1e-11,
                     help="inner tolerance of the mixed box solve (correction size)")
+    ap.add_argument("--box-steps", type=int, default=3,
+                    help="steps of the mixed box solve at most (0: library default, 5)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--box", default="dst", choices=["dst", "mg"])
     ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false")
@@ -513,6 +625,12 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--batch", type=int, default=64,
                     help="instances of the batched star-interface workload (0: skip)")
+    ap.add_argument("--learned-n", type=int, default=256,
+                    help="grid of the learned-start evaluation (0: skip)")
+    ap.add_argument("--learned-geometries", type=int, default=40)
+    ap.add_argument("--learned-draws", type=int, default=50)
+    ap.add_argument("--learned-epochs", type=int, default=10)
+    ap.add_argument("--learned-eval", type=int, default=3)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -121,6 +121,8 @@ typedef struct {
   int iters;              /* operator applications in Arnoldi                     */
   double rel_res;         /* final ||b - A x|| / ||b|| (GMRES estimate)           */
   double t_ms[8];         /* [0] BIE right-hand side, [1] GMRES loop, [2] total   */
+  int x0_rejected;        /* 1 if opts->x0 was given but its residual was not
+                             below ||b||, so GMRES started from zero instead    */
 } kfbi_gmres_info;
 
 typedef struct kfbi_problem kfbi_problem;
@@ -211,6 +213,9 @@ kfbi_status kfbi_apply_operator(kfbi_problem* p, const double* x, double* y);
 /* Right-hand side of the BIE (Algorithm 1, Step 1). */
 kfbi_status kfbi_bie_rhs(kfbi_problem* p, const kfbi_data* data, double* b);
 /* Algorithm 1: BIE right-hand side, GMRES (Step 4) from opts->x0 or zero.
+ * A given x0 whose residual ||b - A x0|| is not below ||b|| (or not finite)
+ * is dropped and GMRES starts from zero (info->x0_rejected = 1): a learned or
+ * otherwise approximate start can never make the solve worse than zero.
  * density: N_b output. info: host pointer (may be NULL). */
 kfbi_status kfbi_gmres_solve(kfbi_problem* p, const kfbi_data* data,
                              const kfbi_gmres_opts* opts, double* density,
@@ -249,6 +254,61 @@ kfbi_status kfbi_destroy_batch(kfbi_batch* batch);
 kfbi_status kfbi_gmres_solve_batch(kfbi_batch* batch, const kfbi_data* data,
                                    const kfbi_gmres_opts* opts, double* const* densities,
                                    kfbi_gmres_info* infos);
+
+/* ---- learned initial density for GMRES ---------------------------------- */
+
+/* A small fully connected network (grown form: learned warm start) maps
+ * features of each DOF to an initial density for kfbi_gmres_solve (opts->x0),
+ * which falls back to a zero start whenever that guess is not better than zero:
+ *   z1 = W1 x~ + b1, a1 = tanh z1;  z2 = W2 a1 + b2, a2 = tanh z2;
+ *   y = W3 a2 + b3 + WL x~;  x~ = (x - in_shift) * in_scale;
+ *   density = s (y * out_scale + out_shift),  s the data scale of the problem
+ *   (kfbi_warm_start_features).
+ * Parameters are one FP32 vector [W1 (width x n_in, row-major), b1, W2 (width x
+ * width), b2, W3 (1 x width), b3, WL (n_in)] owned by the network; the
+ * products with W1, W2, W3 use those weights rounded to bfloat16 (round to
+ * nearest even); WL, activations and sums are FP32; gradients are those at the
+ * rounded weights.  Training uses
+ * kfbi_mlp_loss_grad (loss 1/(2n) sum (y - t)^2) and kfbi_mlp_adam (Adam with
+ * bias-corrected moments).  All arrays are device arrays unless stated; work
+ * is enqueued on the stream given at create. */
+#define KFBI_WS_FEATURES 16   /* per-DOF features of kfbi_warm_start_features */
+typedef struct kfbi_mlp kfbi_mlp;
+/* n_in in [1, 16], width in [1, 1024]; parameters start at zero. */
+kfbi_status kfbi_mlp_create(int n_in, int width, void* cuda_stream, kfbi_mlp** out);
+kfbi_status kfbi_mlp_destroy(kfbi_mlp* m);
+const char* kfbi_mlp_last_error(const kfbi_mlp* m);
+kfbi_status kfbi_mlp_num_params(const kfbi_mlp* m, int* count);
+/* Copy in the FP32 parameters (count floats) and reset the Adam state. */
+kfbi_status kfbi_mlp_set_params(kfbi_mlp* m, const float* params);
+/* Copy out the parameters and/or the last gradient (either may be NULL). */
+kfbi_status kfbi_mlp_get_params(const kfbi_mlp* m, float* params, float* grads);
+/* Input normalisation (HOST arrays of n_in floats) and output affine map. */
+kfbi_status kfbi_mlp_set_affine(kfbi_mlp* m, const float* in_shift, const float* in_scale,
+                                double out_shift, double out_scale);
+/* y (n floats) = network output (before the output affine map) for the rows
+ * of X (n x n_in floats, row-major). */
+kfbi_status kfbi_mlp_forward(kfbi_mlp* m, const float* X, int n, float* y);
+/* Loss and gradient over n rows of X against targets t (in the network's
+ * output units): row i of the batch is row rows[i] of X and t (int32 device
+ * indices, a minibatch of a shuffled data set), or row i when rows is NULL.
+ * loss: one device float (may be NULL). */
+kfbi_status kfbi_mlp_loss_grad(kfbi_mlp* m, const float* X, const float* t, const int32_t* rows,
+                               int n, float* loss);
+/* One Adam step with the last gradient (step counter kept by the network). */
+kfbi_status kfbi_mlp_adam(kfbi_mlp* m, float lr, float beta1, float beta2, float eps);
+/* Per-DOF features (N_b x KFBI_WS_FEATURES floats): [g1/s, g2/s, n (3),
+ * x (3), level-set parameters p0..p5, 0, 0] with the data scale
+ * s = sqrt(mean over DOFs of g1^2 + g2^2) (1 if the data vanish; components
+ * beyond the dimension are 0; g2 NULL gives 0).  With density (N_b doubles,
+ * e.g. a solved density) also writes target (N_b floats) = density / s: one
+ * training sample per DOF.  density and target are both NULL or both given. */
+kfbi_status kfbi_warm_start_features(kfbi_problem* p, const kfbi_data* data, const double* density,
+                                     float* features, float* target);
+/* x0 (N_b doubles) = the network's density for this problem and data.  The
+ * network must take KFBI_WS_FEATURES inputs, have width >= KFBI_WS_FEATURES
+ * and share the problem's stream. */
+kfbi_status kfbi_warm_start(kfbi_problem* p, kfbi_mlp* m, const kfbi_data* data, double* x0);
 
 /* ---- box solve without allocation ----------------------------------------- */
 

@@ -27,6 +27,7 @@ SOURCES = {
     "gmres.cu": [],
     "capi.cu": [],
     "batch.cu": [],
+    "mlp.cu": [],
 }
 
 

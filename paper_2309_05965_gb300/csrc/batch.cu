@@ -208,6 +208,7 @@ kfbi_status kfbi_gmres_solve_batch(kfbi_batch* b, const kfbi_data* data, const k
       infos[k].iters = iters[k];
       infos[k].rel_res = bnorm[k] > 0 ? rel : 0.0;
       for (double& v : infos[k].t_ms) v = 0.0;
+      infos[k].x0_rejected = 0;
     }
     if (bnorm[k] > 0 && !(rel <= opts->rtol)) status = KFBI_ERR_NOT_CONVERGED;
   }

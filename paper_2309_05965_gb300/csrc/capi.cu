@@ -221,7 +221,8 @@ kfbi_status kfbi_destroy_problem(kfbi_problem* p) {
   void* bufs[] = {p->inside, p->irr_flag, p->family, p->edge, p->axis, p->st_axis, p->pde_node,
                   p->dir_idx, p->neu_idx, p->minv, p->irr_lin, p->irr_owner, p->irr_inside,
                   p->irr_w, p->corr_nb, p->nb_off, p->nb_coef, p->cvals, p->coef, p->rhs,
-                  p->ugrid, p->tvals, p->ftilde, p->bvec, p->zero_nb, p->d_flags, p->stencil_dev};
+                  p->ugrid, p->tvals, p->ftilde, p->bvec, p->zero_nb, p->d_flags, p->stencil_dev,
+                  p->ws_scale};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int k = 0; k < 3; ++k) {
@@ -382,8 +383,9 @@ kfbi_status kfbi_gmres_solve(kfbi_problem* p, const kfbi_data* data, const kfbi_
   auto t1 = std::chrono::steady_clock::now();
   int it = 0;
   double rel = 0.0;
+  int rejected = 0;
   kfbi_status s = gmres_run(p, p->bvec, opts->x0, opts->rtol, opts->restart > 0 ? opts->restart : 100,
-                            opts->max_iter, density, &it, &rel);
+                            opts->max_iter, density, &it, &rel, &rejected);
   auto t2 = std::chrono::steady_clock::now();
   if (info) {
     info->iters = it;
@@ -392,6 +394,7 @@ kfbi_status kfbi_gmres_solve(kfbi_problem* p, const kfbi_data* data, const kfbi_
     info->t_ms[0] = std::chrono::duration<double, std::milli>(t1 - t0).count();
     info->t_ms[1] = std::chrono::duration<double, std::milli>(t2 - t1).count();
     info->t_ms[2] = std::chrono::duration<double, std::milli>(t2 - t0).count();
+    info->x0_rejected = rejected;
   }
   return s;
 }

@@ -50,6 +50,16 @@ struct BoxSolver {
   int* conv = nullptr;        // device flag
   int refine_steps = 4;
   double tol = 1e-13;
+  // exact residual of the mixed path in fixed point: mult h^2 A_h = S - kappa h^2 K
+  // with S integer weights w[c] by the number c of nonzero offsets and
+  // K u = kscale (kA u_P + kB sum of edge neighbours)
+  long long* ufix = nullptr;  // u 2^F
+  long long* rfix = nullptr;  // mult h^2 R 2^F
+  double* fixd = nullptr;     // [0] mult h^2 2^F, [1] 2^-F, [2] kscale kappa h^2
+  float* fixf = nullptr;      // 2^Fa, 2^Fb, 2^-Fa, 2^-Fb, 2^-Fb / (mult h^2) (Fa + Fb = F)
+  int w[4] = {0, 0, 0, 0};
+  int kA = 0, kB = 0;
+  double multh2 = 0.0, kc = 0.0;
 };
 
 namespace {
@@ -71,8 +81,10 @@ struct PassArgs {
   int fused;
   int amode;                // 1 if the a index is a mode index of the scaling (3D)
   const int* skip;          // convergence flag (skip when *skip != 0), may be null
-  unsigned long long* corr_max;   // accumulate pass: max |correction|, max |u + correction|
+  unsigned long long* corr_max;   // last pass: max |correction|, max |u + correction|
   float* delta_out;               // accumulate pass: also keep the FP32 correction (in place)
+  long long* dstfix;              // last pass of a refinement step: u_fix += round(delta 2^F)
+  const float* fixf;              // [0..1] 2^Fa, 2^Fb; [2..3] 2^-Fa, 2^-Fb (k_fix_scale)
 };
 
 template <typename T>
@@ -334,63 +346,277 @@ __global__ void __launch_bounds__(256) k_dst_pass_batched(const PassArgs* __rest
   }
 }
 
-// r = R - A_h u at interior nodes (u zero on the boundary layer), and max|r|.
-// Launch: x over the last (contiguous) axis, y (and z) over the others.
-__global__ void k_residual(Grid g, int order, const double* __restrict__ c, const double* __restrict__ R,
-                           const double* __restrict__ u, double* __restrict__ r,
-                           unsigned long long* __restrict__ nrm, const int* skip) {
-  if (skip && *skip) return;
-  const int n1 = g.n + 1;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i1 = blockIdx.y;
-  const int i0 = blockIdx.z;
-  double mx = 0.0;
-  if (j <= g.n) {
-    const long long t = g.d == 2 ? (long long)i1 * n1 + j : ((long long)i0 * n1 + i1) * n1 + j;
-    const bool interior = j >= 1 && j < g.n && i1 >= 1 && i1 < g.n && (g.d == 2 || (i0 >= 1 && i0 < g.n));
-    if (!interior) {
-      r[t] = 0.0;
-    } else {
-      const double* up = u + t;
-      double acc;
-      if (g.d == 2) {
-        double s1 = (up[-1] + up[1]) + (up[-n1] + up[n1]);
-        acc = c[0] * up[0] + c[1] * s1;
-        if (order == 4) acc += c[2] * ((up[-n1 - 1] + up[-n1 + 1]) + (up[n1 - 1] + up[n1 + 1]));
-      } else {
-        const long long s = (long long)n1 * n1;
-        double f = (up[-1] + up[1]) + (up[-n1] + up[n1]) + (up[-s] + up[s]);
-        acc = c[0] * up[0] + c[1] * f;
-        if (order == 4) {
-          double e = (up[-n1 - 1] + up[-n1 + 1]) + (up[n1 - 1] + up[n1 + 1]) + (up[-s - 1] + up[-s + 1]) +
-                     (up[s - 1] + up[s + 1]) + (up[-s - n1] + up[-s + n1]) + (up[s - n1] + up[s + n1]);
-          double k = (up[-s - n1 - 1] + up[-s - n1 + 1]) + (up[-s + n1 - 1] + up[-s + n1 + 1]) +
-                     (up[s - n1 - 1] + up[s - n1 + 1]) + (up[s + n1 - 1] + up[s + n1 + 1]);
-          acc += c[2] * e + c[3] * k;
-        }
-      }
-      double v = R[t] - acc;
-      r[t] = v;
-      mx = fabs(v);
+// ---------------------------------------------------------------------------
+// FP32 passes of the mixed-precision path with register DFTs.
+//
+// Each CTA transforms P line pairs (sequences of length L = 2^LOGL); a thread
+// owns 16 points of one sequence per stage.  Stockham autosort stages of
+// radix 16 (and one of radix 2^(LOGL mod 4)): a thread reads its R inputs at
+// stride L/R, multiplies by the stage twiddles, runs the R-point DFT in
+// registers and writes the R outputs at stride NS (the product of the earlier
+// radices), natural order in and out.  The shared buffer is padded by one
+// element per 16 so that the stride-R writes of the first stage and the
+// stride-L/R reads are free of bank conflicts.  Compared with the radix-4
+// shared-memory kernel above this takes 2-3 exchanges instead of 5-6 and all
+// index arithmetic is compile-time.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+
+// v * exp(-2 pi i j / 16), j known at compile time after unrolling
+__device__ __forceinline__ Cx<float> mulw16(Cx<float> v, int j) {
+  const float c1 = 0.92387953251128674f, s1 = 0.38268343236508977f, r2 = 0.70710678118654752f;
+  float c, s;   // exp(-2 pi i j/16) = c + i s
+  switch (j & 15) {
+    case 0: return v;
+    case 1: c = c1; s = -s1; break;
+    case 2: c = r2; s = -r2; break;
+    case 3: c = s1; s = -c1; break;
+    case 4: return {v.y, -v.x};
+    case 5: c = -s1; s = -c1; break;
+    case 6: c = -r2; s = -r2; break;
+    case 7: c = -c1; s = -s1; break;
+    case 8: return {-v.x, -v.y};
+    case 9: c = -c1; s = s1; break;
+    case 10: c = -r2; s = r2; break;
+    case 11: c = -s1; s = c1; break;
+    case 12: return {-v.y, v.x};
+    case 13: c = s1; s = c1; break;
+    case 14: c = r2; s = r2; break;
+    default: c = c1; s = s1; break;
+  }
+  return {v.x * c - v.y * s, v.x * s + v.y * c};
+}
+
+__device__ __forceinline__ void dft4(Cx<float>& a0, Cx<float>& a1, Cx<float>& a2, Cx<float>& a3) {
+  const Cx<float> t0 = {a0.x + a2.x, a0.y + a2.y}, t1 = {a0.x - a2.x, a0.y - a2.y};
+  const Cx<float> t2 = {a1.x + a3.x, a1.y + a3.y}, t3 = {a1.x - a3.x, a1.y - a3.y};
+  a0 = {t0.x + t2.x, t0.y + t2.y};
+  a2 = {t0.x - t2.x, t0.y - t2.y};
+  a1 = {t1.x + t3.y, t1.y - t3.x};   // t1 - i t3
+  a3 = {t1.x - t3.y, t1.y + t3.x};   // t1 + i t3
+}
+
+// out = DFT_R(in), R in {2, 4, 8, 16}: four-step splits r = (R/4) a + b.
+template <int R>
+__device__ __forceinline__ void dftr(Cx<float>* v, Cx<float>* out) {
+  if constexpr (R == 2) {
+    out[0] = {v[0].x + v[1].x, v[0].y + v[1].y};
+    out[1] = {v[0].x - v[1].x, v[0].y - v[1].y};
+  } else if constexpr (R == 4) {
+    dft4(v[0], v[1], v[2], v[3]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[k] = v[k];
+  } else if constexpr (R == 8) {
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      dft4(v[b], v[2 + b], v[4 + b], v[6 + b]);   // Y[b][k1] in v[2 k1 + b]
+#pragma unroll
+      for (int k1 = 0; k1 < 4; ++k1) v[2 * k1 + b] = mulw16(v[2 * k1 + b], 2 * b * k1);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      const Cx<float> y0 = v[2 * k1], y1 = v[2 * k1 + 1];
+      out[k1] = {y0.x + y1.x, y0.y + y1.y};
+      out[k1 + 4] = {y0.x - y1.x, y0.y - y1.y};
+    }
+  } else {
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      dft4(v[b], v[4 + b], v[8 + b], v[12 + b]);   // Y[b][k1] in v[4 k1 + b]
+#pragma unroll
+      for (int k1 = 1; k1 < 4; ++k1) v[4 * k1 + b] = mulw16(v[4 * k1 + b], b * k1);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      dft4(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) out[k1 + 4 * k2] = v[4 * k1 + k2];
     }
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(nrm, (unsigned long long)__double_as_longlong(mx));
 }
 
-__global__ void k_absmax(long long tot, const double* __restrict__ R, unsigned long long* nrm) {
-  double mx = 0.0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-       t += (long long)gridDim.x * blockDim.x)
-    mx = fmax(mx, fabs(R[t]));
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(nrm, (unsigned long long)__double_as_longlong(mx));
+// One radix-R Stockham stage in place on the padded buffer s (one sequence).
+template <int L, int R, int NS>
+__device__ __forceinline__ void reg_stage(Cx<float>* s, int tid, const Cx<float>* __restrict__ tw) {
+  constexpr int G = L / R;    // R-point DFTs per stage
+  constexpr int T = L / 16;   // threads per sequence
+  constexpr int Q = 16 / R;   // DFTs per thread
+  Cx<float> v[16];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int j = tid + q * T;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[q * R + r] = s[padi(j + r * G)];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int j = tid + q * T;
+    const int k = j & (NS - 1);
+    Cx<float>* x = v + q * R;
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) x[r] = cmul(x[r], tw[(r * k) * (L / (NS * R))]);
+    }
+    Cx<float> y[R];
+    dftr<R>(x, y);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) s[padi(base + r * NS)] = y[r];
+  }
+  __syncthreads();
 }
 
-// Refinement stop: conv = (max|delta_k| <= tol max|u_{k+1}|), the size of the
-// last FP32 correction against the solution (a residual test would sit on the
-// rounding floor eps cond(A_h) of the FP64 residual itself at large N).
-// Keeps the last ratio's terms in nrm[2..] and resets the accumulation slots.
+template <int LOGL>
+__device__ __forceinline__ void reg_fft(Cx<float>* s, int tid, const Cx<float>* __restrict__ tw) {
+  constexpr int L = 1 << LOGL;
+  constexpr int N16 = LOGL / 4, REM = LOGL % 4;
+  constexpr int NSF = 1 << (4 * N16);
+  if constexpr (N16 >= 1) reg_stage<L, 16, 1>(s, tid, tw);
+  if constexpr (N16 >= 2) reg_stage<L, 16, 16>(s, tid, tw);
+  if constexpr (N16 >= 3) reg_stage<L, 16, 256>(s, tid, tw);
+  if constexpr (REM == 1) reg_stage<L, 2, NSF>(s, tid, tw);
+  if constexpr (REM == 2) reg_stage<L, 4, NSF>(s, tid, tw);
+  if constexpr (REM == 3) reg_stage<L, 8, NSF>(s, tid, tw);
+}
+
+template <int LOGL, int P>
+struct Reg {
+  static constexpr int L = 1 << LOGL;
+  static constexpr int T = L / 16;          // threads per sequence
+  static constexpr int THREADS = P * T;
+  static constexpr int LP = L + L / 16;     // padded sequence length
+  static constexpr size_t SMEM = sizeof(Cx<float>) * (size_t)P * LP;
+};
+
+// Default pairs per CTA: 128 threads per CTA up to L = 2048.
+constexpr int reg_pairs(int logL) { return logL >= 11 ? 1 : (1 << (11 - logL)); }
+
+template <int LOGL, int P>
+__global__ void __launch_bounds__(Reg<LOGL, P>::THREADS) k_dst32(PassArgs A) {
+  using F = Reg<LOGL, P>;
+  constexpr int L = F::L, LP = F::LP;
+  constexpr int n = L / 2, nm1 = n - 1;
+  if (A.skip && *A.skip) return;
+  extern __shared__ unsigned char smraw[];
+  Cx<float>* sm = reinterpret_cast<Cx<float>*>(smraw);
+  const Cx<float>* tw = static_cast<const Cx<float>*>(A.tw);
+  const int a = blockIdx.y + 1;
+  const int b0 = 1 + 2 * P * blockIdx.x;
+  const long long abase = (long long)a * A.sa;
+  const bool contig = A.es == 1;
+  constexpr int nval = nm1 * 2 * P;
+  // odd extensions of the 2P lines: line 2q -> real part, 2q+1 -> imaginary
+  for (int t = threadIdx.x; t < nval; t += F::THREADS) {
+    int j, q;
+    if (contig) {
+      j = 1 + t % nm1;
+      q = t / nm1;
+    } else {
+      q = t % (2 * P);
+      j = 1 + t / (2 * P);
+    }
+    const int b = b0 + q;
+    float v = 0.f;
+    if (b <= nm1) {
+      const long long off = abase + (long long)b * A.sb + (long long)j * A.es;
+      v = A.src64 ? (float)static_cast<const double*>(A.src)[off] : static_cast<const float*>(A.src)[off];
+    }
+    Cx<float>* zz = sm + (q >> 1) * LP;
+    if (q & 1) {
+      zz[padi(j)].y = v;
+      zz[padi(L - j)].y = -v;
+    } else {
+      zz[padi(j)].x = v;
+      zz[padi(L - j)].x = -v;
+    }
+  }
+  for (int t = threadIdx.x; t < P; t += F::THREADS) {
+    sm[t * LP + padi(0)] = {0.f, 0.f};
+    sm[t * LP + padi(n)] = {0.f, 0.f};
+  }
+  __syncthreads();
+  const int pr = threadIdx.x / F::T, tid = threadIdx.x % F::T;
+  Cx<float>* s = sm + pr * LP;
+  reg_fft<LOGL>(s, tid, tw);
+  if (A.fused) {
+    // spectral division in place (Z_{L-k} = -Z_k keeps the odd symmetry), then
+    // the same FFT gives the inverse transform
+    const float kh2 = (float)A.kt, g = (float)A.gscale;
+    const float sa = A.d == 3 ? A.s32[a] : 0.f;
+    for (int t = threadIdx.x; t < L * P; t += F::THREADS) {
+      const int q = t >> LOGL, k = t & (L - 1);
+      Cx<float>* zz = sm + q * LP + padi(k);
+      if (k == 0 || k == n) {
+        *zz = {0.f, 0.f};
+        continue;
+      }
+      const int km = k < n ? k : L - k;
+      const int bA = b0 + 2 * q, bB = min(bA + 1, nm1);
+      const float sk = A.s32[km];
+      float lA, lB;
+      if (A.d == 2) {
+        lA = lam_h2<float>(2, A.order, kh2, sk, A.s32[min(bA, nm1)], 0.f);
+        lB = lam_h2<float>(2, A.order, kh2, sk, A.s32[bB], 0.f);
+      } else {
+        lA = lam_h2<float>(3, A.order, kh2, sk, sa, A.s32[min(bA, nm1)]);
+        lB = lam_h2<float>(3, A.order, kh2, sk, sa, A.s32[bB]);
+      }
+      const Cx<float> Z = *zz;
+      *zz = {(g / lA) * (-0.5f * Z.y), (g / lB) * (0.5f * Z.x)};
+    }
+    __syncthreads();
+    reg_fft<LOGL>(s, tid, tw);
+  }
+  // S_k = -Im(Z_k)/2 (line 2q), Re(Z_k)/2 (line 2q+1)
+  float dmx = 0.f, umx = 0.f;
+  for (int t = threadIdx.x; t < nval; t += F::THREADS) {
+    int j, q;
+    if (contig) {
+      j = 1 + t % nm1;
+      q = t / nm1;
+    } else {
+      q = t % (2 * P);
+      j = 1 + t / (2 * P);
+    }
+    const int b = b0 + q;
+    if (b > nm1) continue;
+    const Cx<float> Z = sm[(q >> 1) * LP + padi(j)];
+    const float v = (q & 1) ? 0.5f * Z.x : -0.5f * Z.y;
+    const long long off = abase + (long long)b * A.sb + (long long)j * A.es;
+    if (A.dstfix) {
+      const long long nv = A.dstfix[off] + __float2ll_rn((v * A.fixf[0]) * A.fixf[1]);
+      A.dstfix[off] = nv;
+      dmx = fmaxf(dmx, fabsf(v));
+      umx = fmaxf(umx, fabsf((__ll2float_rn(nv) * A.fixf[2]) * A.fixf[3]));
+    } else if (A.dst64) {
+      double* o = static_cast<double*>(A.dst);
+      const double nv = A.accumulate ? o[off] + (double)v : (double)v;
+      o[off] = nv;
+      if (A.corr_max) {
+        dmx = fmaxf(dmx, fabsf(v));
+        umx = fmaxf(umx, fabsf((float)nv));
+      }
+    } else {
+      static_cast<float*>(A.dst)[off] = v;
+      if (A.corr_max) {
+        dmx = fmaxf(dmx, fabsf(v));
+        umx = dmx;
+      }
+    }
+  }
+  if (A.corr_max) {
+    for (int o = 16; o > 0; o >>= 1) {
+      dmx = fmaxf(dmx, __shfl_xor_sync(0xffffffffu, dmx, o));
+      umx = fmaxf(umx, __shfl_xor_sync(0xffffffffu, umx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      if (dmx > 0.f) atomicMax(A.corr_max, (unsigned long long)__double_as_longlong((double)dmx));
+      if (umx > 0.f) atomicMax(A.corr_max + 1, (unsigned long long)__double_as_longlong((double)umx));
+    }
+  }
+}
+
 __global__ void k_check(unsigned long long* nrm, double tol, int* conv) {
   if (*conv) return;
   double dm = __longlong_as_double((long long)nrm[3]);
@@ -407,6 +633,102 @@ __global__ void k_zero_flags(unsigned long long* nrm, int* conv) {
   *conv = 0;
 }
 
+// ---- exact residual of the mixed path (fixed point) -------------------------
+// After the first FP32 solve u0, F is chosen so that max|u0| 2^F ~ 2^52; then
+// u_fix = round(u 2^F) and R_fix = round(mult h^2 R 2^F) are int64, the
+// integer part S of mult h^2 A_h is applied exactly in int64 (|S u_fix| <
+// 2^61), and only the kappa part (relative size kappa h^2) goes through one
+// FP64 product.  The residual is then exact for the stored u_fix, with no
+// FP64 stencil arithmetic, and is handed to the next FP32 solve as FP32.
+// Scales beyond the FP32 exponent range are applied as two factors
+// 2^Fa 2^Fb (Fa + Fb = F).
+__global__ void k_fix_scale(const unsigned long long* __restrict__ nrm, double multh2, double kc,
+                            double* __restrict__ fixd, float* __restrict__ fixf) {
+  const double um = __longlong_as_double((long long)nrm[5]);
+  int F = 0;
+  if (um > 0.0) F = 52 - (int)ceil(log2(um));
+  F = max(-120, min(F, 240));
+  const int Fa = F / 2, Fb = F - Fa;
+  fixd[0] = ldexp(multh2, F);
+  fixd[1] = ldexp(1.0, -F);
+  fixd[2] = kc;
+  fixf[0] = ldexpf(1.f, Fa);
+  fixf[1] = ldexpf(1.f, Fb);
+  fixf[2] = ldexpf(1.f, -Fa);
+  fixf[3] = ldexpf(1.f, -Fb);
+  fixf[4] = (float)(ldexp(1.0, -Fb) / multh2);   // r32 = (r_fix 2^-Fa) (2^-Fb / mult h^2)
+}
+
+__global__ void k_fix0(long long tot, const float* __restrict__ u0, const double* __restrict__ R, Grid g,
+                       const double* __restrict__ fixd, const float* __restrict__ fixf,
+                       long long* __restrict__ ufix, long long* __restrict__ rfix) {
+  const double rm = fixd[0];
+  const float fa = fixf[0], fb = fixf[1];
+  const int n1 = g.n + 1;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    ufix[t] = __float2ll_rn((u0[t] * fa) * fb);
+    long long r = t;
+    bool interior = true;
+    for (int k = 0; k < g.d; ++k) {
+      const int i = (int)(r % n1);
+      r /= n1;
+      interior = interior && i >= 1 && i < g.n;
+    }
+    rfix[t] = interior ? __double2ll_rn(R[t] * rm) : 0ll;
+  }
+}
+
+struct FixStencil {
+  int w0, w1, w2, w3, kA, kB;
+};
+
+// r32 = (R_fix - S u_fix + round(kc (kA u + kB sum_edges))) 2^-F / (mult h^2)
+__global__ void k_res_fix(Grid g, FixStencil W, const long long* __restrict__ R, const long long* __restrict__ u,
+                          const double* __restrict__ fixd, const float* __restrict__ fixf,
+                          float* __restrict__ r32, const int* skip) {
+  if (skip && *skip) return;
+  const int n1 = g.n + 1;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i1 = blockIdx.y;
+  const int i0 = blockIdx.z;
+  if (j > g.n) return;
+  const long long t = g.d == 2 ? (long long)i1 * n1 + j : ((long long)i0 * n1 + i1) * n1 + j;
+  const bool interior = j >= 1 && j < g.n && i1 >= 1 && i1 < g.n && (g.d == 2 || (i0 >= 1 && i0 < g.n));
+  if (!interior) {
+    r32[t] = 0.f;
+    return;
+  }
+  const long long* up = u + t;
+  const long long c = up[0];
+  long long e, k2 = 0, k3 = 0;
+  if (g.d == 2) {
+    e = (up[-1] + up[1]) + (up[-n1] + up[n1]);
+    if (W.w2) k2 = (up[-n1 - 1] + up[-n1 + 1]) + (up[n1 - 1] + up[n1 + 1]);
+  } else {
+    const long long s = (long long)n1 * n1;
+    e = (up[-1] + up[1]) + (up[-n1] + up[n1]) + (up[-s] + up[s]);
+    if (W.w2)
+      k2 = (up[-n1 - 1] + up[-n1 + 1]) + (up[n1 - 1] + up[n1 + 1]) + (up[-s - 1] + up[-s + 1]) +
+           (up[s - 1] + up[s + 1]) + (up[-s - n1] + up[-s + n1]) + (up[s - n1] + up[s + n1]);
+    if (W.w3)
+      k3 = (up[-s - n1 - 1] + up[-s - n1 + 1]) + (up[-s + n1 - 1] + up[-s + n1 + 1]) +
+           (up[s - n1 - 1] + up[s - n1 + 1]) + (up[s + n1 - 1] + up[s + n1 + 1]);
+  }
+  long long r = R[t] - ((long long)W.w0 * c + (long long)W.w1 * e + (long long)W.w2 * k2 + (long long)W.w3 * k3);
+  const double kc = fixd[2];
+  if (kc != 0.0) r += __double2ll_rn(kc * (double)((long long)W.kA * c + (long long)W.kB * e));
+  r32[t] = (__ll2float_rn(r) * fixf[2]) * fixf[4];
+}
+
+__global__ void k_unfix(long long tot, const long long* __restrict__ ufix, const double* __restrict__ fixd,
+                        double* __restrict__ u) {
+  const double isc = fixd[1];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x)
+    u[t] = __ll2double_rn(ufix[t]) * isc;
+}
+
 template <typename T, int P>
 void launch_pass_p(kfbi_problem* p, const PassArgs& A, int npairs_b, int na, cudaStream_t st) {
   dim3 grid((unsigned)((npairs_b + P - 1) / P), (unsigned)na);
@@ -414,10 +736,43 @@ void launch_pass_p(kfbi_problem* p, const PassArgs& A, int npairs_b, int na, cud
   KFBI_LAUNCH(p, KFBI_KC_DST, k_dst_pass<T, P><<<grid, 256, smem, st>>>(A));
 }
 
+template <int LOGL, int P>
+void launch_reg(kfbi_problem* p, const PassArgs& A, int npairs_b, int na, cudaStream_t st) {
+  using F = Reg<LOGL, P>;
+  dim3 grid((unsigned)((npairs_b + P - 1) / P), (unsigned)na);
+  KFBI_LAUNCH(p, KFBI_KC_DST, k_dst32<LOGL, P><<<grid, F::THREADS, F::SMEM, st>>>(A));
+}
+
+// FP32 pass: P = reg_pairs(LOGL) line pairs per CTA (128-thread CTAs)
+void launch_pass32(kfbi_problem* p, const PassArgs& A, int npairs_b, int na, cudaStream_t st) {
+  switch (A.logL) {
+    case 4: launch_reg<4, reg_pairs(4)>(p, A, npairs_b, na, st); break;
+    case 5: launch_reg<5, reg_pairs(5)>(p, A, npairs_b, na, st); break;
+    case 6: launch_reg<6, reg_pairs(6)>(p, A, npairs_b, na, st); break;
+    case 7: launch_reg<7, reg_pairs(7)>(p, A, npairs_b, na, st); break;
+    case 8: launch_reg<8, reg_pairs(8)>(p, A, npairs_b, na, st); break;
+    case 9: launch_reg<9, reg_pairs(9)>(p, A, npairs_b, na, st); break;
+    case 10: launch_reg<10, reg_pairs(10)>(p, A, npairs_b, na, st); break;
+    case 11: launch_reg<11, reg_pairs(11)>(p, A, npairs_b, na, st); break;
+    case 12: launch_reg<12, reg_pairs(12)>(p, A, npairs_b, na, st); break;
+    default: launch_reg<13, reg_pairs(13)>(p, A, npairs_b, na, st); break;
+  }
+}
+
+template <int LOGL>
+cudaError_t set_smem_reg(int max_optin) {
+  return cudaFuncSetAttribute(k_dst32<LOGL, reg_pairs(LOGL)>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              max_optin);
+}
+
 // pairs per CTA: enough butterflies for 256 threads (P L / 4 >= 256), at least
 // `pmin` (strided passes read 2 P adjacent lines per row)
 template <typename T>
 void launch_pass(kfbi_problem* p, const PassArgs& A, int npairs_b, int na, cudaStream_t st, int pmin) {
+  if (sizeof(T) == 4) {
+    launch_pass32(p, A, npairs_b, na, st);
+    return;
+  }
   const int L = 2 * A.n;
   int P = std::max(pmin, 1024 / L);
   if (sizeof(T) == 8 && L >= 2048) P = std::min(P, 1);
@@ -567,6 +922,28 @@ kfbi_status box_create(kfbi_problem* p) {
     KFBI_CUDA(p, cudaMemset(B->work32, 0, sizeof(float) * nodes));
     KFBI_CUDA(p, dalloc(&B->res, nodes));
     KFBI_CUDA(p, cudaMemset(B->res, 0, sizeof(double) * nodes));
+    KFBI_CUDA(p, dalloc(&B->ufix, nodes));
+    KFBI_CUDA(p, dalloc(&B->rfix, nodes));
+    KFBI_CUDA(p, dalloc(&B->fixd, 4));
+    KFBI_CUDA(p, dalloc(&B->fixf, 8));
+    // mult h^2 A_h = S - kappa h^2 kscale (kA u_P + kB sum of edge neighbours)
+    const int order = p->cfg.order;
+    double mult, kscale;
+    if (order == 2) {
+      mult = 1.0;
+      B->w[0] = -2 * g.d; B->w[1] = 1; B->w[2] = 0; B->w[3] = 0;
+      B->kA = 1; B->kB = 0; kscale = 1.0;
+    } else if (g.d == 2) {   // 6 h^2 x eq. (9p-cds)
+      mult = 6.0;
+      B->w[0] = -20; B->w[1] = 4; B->w[2] = 1; B->w[3] = 0;
+      B->kA = 8; B->kB = 1; kscale = 0.5;
+    } else {                 // 48 h^2 x eq. (27p-cds)
+      mult = 48.0;
+      B->w[0] = -200; B->w[1] = 20; B->w[2] = 6; B->w[3] = 1;
+      B->kA = 6; B->kB = 1; kscale = 4.0;
+    }
+    B->multh2 = mult * g.h * g.h;
+    B->kc = kscale * p->kt * g.h * g.h;
 
   } else {
     KFBI_CUDA(p, dalloc(&B->work64, nodes));
@@ -597,6 +974,16 @@ kfbi_status box_create(kfbi_problem* p) {
   KFBI_CUDA(p, (set_smem<float, 2>(optin)));
   KFBI_CUDA(p, (set_smem<float, 4>(optin)));
   KFBI_CUDA(p, (set_smem<float, 8>(optin)));
+  KFBI_CUDA(p, set_smem_reg<4>(optin));
+  KFBI_CUDA(p, set_smem_reg<5>(optin));
+  KFBI_CUDA(p, set_smem_reg<6>(optin));
+  KFBI_CUDA(p, set_smem_reg<7>(optin));
+  KFBI_CUDA(p, set_smem_reg<8>(optin));
+  KFBI_CUDA(p, set_smem_reg<9>(optin));
+  KFBI_CUDA(p, set_smem_reg<10>(optin));
+  KFBI_CUDA(p, set_smem_reg<11>(optin));
+  KFBI_CUDA(p, set_smem_reg<12>(optin));
+  KFBI_CUDA(p, set_smem_reg<13>(optin));
   return KFBI_OK;
 }
 
@@ -613,6 +1000,10 @@ void box_destroy(kfbi_problem* p) {
   cudaFree(B->work64);
   cudaFree(B->work32);
   cudaFree(B->res);
+  cudaFree(B->ufix);
+  cudaFree(B->rfix);
+  cudaFree(B->fixd);
+  cudaFree(B->fixf);
   cudaFree(B->nrm);
   cudaFree(B->conv);
   delete B;
@@ -630,28 +1021,47 @@ kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u) {
     KFBI_TRY(dst_solve_t<double>(p, rhs, 1, u, 0, nullptr));
     return launch_set_boundary(p, u, nullptr);
   }
-  // mixed: u = 0; repeat { u += DST32^{-1}(r); r = R - A_h u } until max|r| <= tol max|R|
+  // mixed: u0 = DST32^{-1}(R) (FP32, in place in the work grid); fixed-point
+  // scale from max|u0|; then repeat { r = R - A_h u exactly (int64 -> FP32);
+  // u += DST32^{-1}(r) } until the correction is below tol max|u|; u out in FP64.
   cudaStream_t st = p->stream;
   const long long nodes = g.nodes();
-  KFBI_CUDA(p, cudaMemsetAsync(u, 0, sizeof(double) * nodes, st));
+  const int eb = (int)std::min<long long>(div_up(nodes, 256), 152 * 8);
   KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_zero_flags<<<1, 1, 0, st>>>(B->nrm, B->conv));
-  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_absmax<<<std::min(div_up(nodes, 256), 152 * 8), 256, 0, st>>>(nodes, rhs, B->nrm));
-  KFBI_CUDA(p, cudaGetLastError());
-  // u += delta_k = DST32(r_k); r_{k+1} = R - A_h u in FP64 every step.  (An
-  // update r_k - A_h delta_k with A_h delta_k in FP32 is not enough: delta_k is
-  // smooth, A_h delta_k cancels by ~cond(A_h), and its FP32 rounding is then as
-  // large as the residual itself.)
-  const dim3 rgrid((unsigned)div_up(g.n + 1, 128), (unsigned)(g.n + 1), g.d == 3 ? (unsigned)(g.n + 1) : 1u);
-  for (int it = 0; it < B->refine_steps; ++it) {
-    KFBI_TRY(dst_solve_t<float>(p, it == 0 ? (const void*)rhs : (const void*)B->res, 1, u, 1, B->conv,
-                                B->nrm + 3));
-    KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_check<<<1, 1, 0, st>>>(B->nrm, B->tol, B->conv));
-    if (it + 1 < B->refine_steps) {
-      KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_residual<<<rgrid, 128, 0, st>>>(
-          g, p->cfg.order, p->stencil_dev, rhs, u, B->res, B->nrm + 1, B->conv));
-    }
-    KFBI_CUDA(p, cudaGetLastError());
+  {
+    PassPlan P0 = plan_passes<float>(p, rhs, 1, u, 0, B->conv, B->nrm + 3);
+    PassArgs& last = P0.args[P0.npass - 1];
+    last.dst = B->work32;
+    last.dst64 = 0;
+    last.accumulate = 0;
+    last.corr_max = B->nrm + 3;
+    for (int k = 0; k < P0.npass; ++k) launch_pass<float>(p, P0.args[k], P0.npairs, P0.na, st, P0.pmin[k]);
   }
+  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_check<<<1, 1, 0, st>>>(B->nrm, B->tol, B->conv));
+  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_fix_scale<<<1, 1, 0, st>>>(B->nrm, B->multh2, B->kc, B->fixd, B->fixf));
+  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_fix0<<<eb, 256, 0, st>>>(nodes, B->work32, rhs, g, B->fixd, B->fixf,
+                                                                 B->ufix, B->rfix));
+  float* r32 = reinterpret_cast<float*>(B->res);
+  PassPlan PK = plan_passes<float>(p, r32, 0, u, 0, B->conv, B->nrm + 3);
+  {
+    PassArgs& last = PK.args[PK.npass - 1];
+    last.dst = nullptr;
+    last.dst64 = 0;
+    last.accumulate = 1;
+    last.dstfix = B->ufix;
+    last.fixf = B->fixf;
+    last.corr_max = B->nrm + 3;
+  }
+  const FixStencil W{B->w[0], B->w[1], B->w[2], B->w[3], B->kA, B->kB};
+  const dim3 rgrid((unsigned)div_up(g.n + 1, 128), (unsigned)(g.n + 1), g.d == 3 ? (unsigned)(g.n + 1) : 1u);
+  for (int it = 1; it < B->refine_steps; ++it) {
+    KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_res_fix<<<rgrid, 128, 0, st>>>(g, W, B->rfix, B->ufix, B->fixd, B->fixf,
+                                                                         r32, B->conv));
+    for (int k = 0; k < PK.npass; ++k) launch_pass<float>(p, PK.args[k], PK.npairs, PK.na, st, PK.pmin[k]);
+    KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_check<<<1, 1, 0, st>>>(B->nrm, B->tol, B->conv));
+  }
+  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_unfix<<<eb, 256, 0, st>>>(nodes, B->ufix, B->fixd, u));
+  KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
 }
 

@@ -352,7 +352,7 @@ static kfbi_status read_scalar(kfbi_problem* p, const double* dev, double* host)
 }
 
 kfbi_status gmres_run(kfbi_problem* p, const double* b, const double* x0, double rtol, int restart,
-                      int max_iter, double* x, int* iters, double* rel) {
+                      int max_iter, double* x, int* iters, double* rel, int* x0_rejected) {
   Gmres& G = p->gm;
   const int nb = G.nb;
   const int m = std::max(1, std::min(restart, G.m));
@@ -372,6 +372,7 @@ kfbi_status gmres_run(kfbi_problem* p, const double* b, const double* x0, double
   const double bnorm = std::sqrt(bnorm2);
   *iters = 0;
   *rel = 0.0;
+  if (x0_rejected) *x0_rejected = 0;
   if (!std::isfinite(bnorm)) return fail(p, KFBI_ERR_NONFINITE, "non-finite BIE right-hand side");
   if (bnorm == 0.0) {
     KFBI_CUDA(p, cudaMemsetAsync(x, 0, sizeof(double) * nb, st));
@@ -396,7 +397,14 @@ kfbi_status gmres_run(kfbi_problem* p, const double* b, const double* x0, double
     KFBI_LAUNCH(p, KFBI_KC_GMRES, k_sqrt<<<1, 1, 0, st>>>(beta));
     double hbeta;
     KFBI_TRY(read_scalar(p, beta, &hbeta));
-    if (!std::isfinite(hbeta)) return fail(p, KFBI_ERR_NONFINITE, "non-finite GMRES residual");
+    if (!std::isfinite(hbeta) && !(total == 0 && x0)) return fail(p, KFBI_ERR_NONFINITE, "non-finite GMRES residual");
+    if (total == 0 && nonzero_x && x0 && !(hbeta < bnorm)) {
+      // the initial guess is no better than zero: start from zero instead
+      if (x0_rejected) *x0_rejected = 1;
+      KFBI_CUDA(p, cudaMemsetAsync(x, 0, sizeof(double) * nb, st));
+      nonzero_x = false;
+      continue;
+    }
     if (hbeta <= rtol * bnorm) {
       *iters = total;
       *rel = hbeta / bnorm;

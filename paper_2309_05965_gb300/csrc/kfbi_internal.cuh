@@ -165,6 +165,7 @@ struct kfbi_problem {
   double* xbuf = nullptr;
   double* ybuf = nullptr;
   bool use_graphs = true;
+  double* ws_scale = nullptr;    // [1] data scale of the learned start (allocated on first use)
 };
 
 namespace kfbi {
@@ -255,7 +256,8 @@ kfbi_status gmres_create(kfbi_problem* p, int m);
 void gmres_destroy(kfbi_problem* p);
 kfbi_status apply_operator_fast(kfbi_problem* p, const double* x, double* y);
 kfbi_status gmres_run(kfbi_problem* p, const double* b, const double* x0, double rtol,
-                      int restart, int max_iter, double* x, int* iters, double* rel);
+                      int restart, int max_iter, double* x, int* iters, double* rel,
+                      int* x0_rejected = nullptr);
 kfbi_status dot_self_pub(kfbi_problem* p, const double* v, double* out);
 kfbi_status gmres_init_zero(kfbi_problem* p, const double* b, double bnorm);
 kfbi_status gmres_finish(kfbi_problem* p, int k, double* x);

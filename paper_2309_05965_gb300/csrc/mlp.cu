@@ -1,0 +1,526 @@
+// Learned initial density for GMRES (Algorithm 1, Step 4 from a learned
+// start instead of zero): a small fully connected network evaluated at every
+// DOF, trained on the GPU on densities that the method itself computes.
+//
+//   z1 = W1 x + b1, a1 = tanh z1;  z2 = W2 a1 + b2, a2 = tanh z2;
+//   y = W3 a2 + b3 + WL x
+//
+// Precision: FP32 master weights; the products with W1, W2, W3 use those
+// weights rounded to bfloat16 (kept in a BF16 copy refreshed after each
+// update); the linear skip WL, activations and all sums are FP32, so the
+// linear part of the map is resolved beyond bfloat16 precision.  Gradients are those at the rounded weights and update the
+// FP32 masters with Adam (Kingma & Ba 2015, bias-corrected moments).
+//
+// The contractions are small (K = 16 or 256, N = 256) and sit beside
+// HBM-bound solver work, so they run on a tiled SIMT kernel (64x64 tiles,
+// 4x4 outputs per thread, FP32 FMA) rather than on the tensor cores.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kfbi_internal.cuh"
+
+struct kfbi_mlp {
+  int n_in = 0, width = 0, nparam = 0;
+  int oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0, oWL = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  float* theta = nullptr;          // FP32 masters
+  float* grad = nullptr;
+  float* mom1 = nullptr;
+  float* mom2 = nullptr;
+  __nv_bfloat16* wbf = nullptr;    // rounded copy, master layout
+  float* shift = nullptr;          // [n_in] input normalisation x~ = (x - shift) * scale
+  float* scale = nullptr;
+  double out_shift = 0.0, out_scale = 1.0;
+  long long step = 0;
+  // per-row scratch
+  int cap = 0;
+  float* X = nullptr;     // normalised input [cap][n_in]
+  float* a1 = nullptr;    // [cap][width]
+  float* a2 = nullptr;
+  float* d1 = nullptr;    // back-propagated signals [cap][width]
+  float* d2 = nullptr;
+  float* y = nullptr;     // [cap]
+  float* dy = nullptr;
+  float* tb = nullptr;    // gathered targets [cap]
+  float* loss = nullptr;  // [1]
+};
+
+namespace kfbi {
+namespace {
+
+kfbi_status mfail(kfbi_mlp* m, kfbi_status s, const std::string& msg) {
+  if (m) m->err = msg;
+  return s;
+}
+
+#define MLP_CUDA(m, call)                                                         \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) return mfail((m), KFBI_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+__device__ __forceinline__ float tof(T v);
+template <>
+__device__ __forceinline__ float tof<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float tof<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// C (M x N) = A (M x K) B (K x N) with element (i, k) of A at A[i sam + k sak]
+// and (k, j) of B at B[k sbk + j sbn].  blockIdx.z splits K into chunks.
+// mode 0: C = act(acc + bias) [* (1 - gate^2)];  mode 1: C += acc (atomic).
+template <typename TB>
+__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, int kchunk, const float* __restrict__ A,
+                                              long long sam, long long sak, const TB* __restrict__ B,
+                                              long long sbk, long long sbn, float* __restrict__ C, long long ldc,
+                                              const float* __restrict__ bias, int act, const float* __restrict__ gate,
+                                              int mode) {
+  __shared__ float As[16][64 + 4];
+  __shared__ float Bs[16][64 + 4];
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int kb = blockIdx.z * kchunk;
+  const int ke = min(K, kb + kchunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+  for (int k0 = kb; k0 < ke; k0 += 16) {
+    for (int e = threadIdx.x; e < 64 * 16; e += 256) {
+      int i, k;
+      if (sam == 1) {
+        i = e & 63;
+        k = e >> 6;
+      } else {
+        i = e >> 4;
+        k = e & 15;
+      }
+      const int gi = m0 + i, gk = k0 + k;
+      As[k][i] = (gi < M && gk < ke) ? A[gi * sam + gk * sak] : 0.f;
+      int j, kk;
+      if (sbn == 1) {
+        j = e & 63;
+        kk = e >> 6;
+      } else {
+        j = e >> 4;
+        kk = e & 15;
+      }
+      const int gj = n0 + j, gk2 = k0 + kk;
+      Bs[kk][j] = (gj < N && gk2 < ke) ? tof<TB>(B[gk2 * sbk + gj * sbn]) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = m0 + ty + 16 * r;
+    if (i >= M) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = n0 + tx + 16 * c;
+      if (j >= N) continue;
+      float* o = C + (long long)i * ldc + j;
+      if (mode == 1) {
+        atomicAdd(o, acc[r][c]);
+      } else {
+        float v = acc[r][c] + (bias ? bias[j] : 0.f);
+        if (act) v = tanhf(v);
+        if (gate) {
+          const float g = gate[(long long)i * ldc + j];
+          v *= 1.f - g * g;
+        }
+        *o = v;
+      }
+    }
+  }
+}
+
+// X[i, :] = (raw[r_i, :] - shift) * scale with r_i = rows[i] (i when rows is
+// null); the targets of the selected rows are gathered alongside.
+__global__ void k_normalise(int n, int n_in, const float* __restrict__ raw, const int32_t* __restrict__ rows,
+                            const float* __restrict__ shift, const float* __restrict__ scale,
+                            float* __restrict__ X, const float* __restrict__ t_in, float* __restrict__ t_out) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)n * n_in) return;
+  const int k = (int)(t % n_in);
+  const long long i = t / n_in;
+  const long long r = rows ? (long long)rows[i] : i;
+  X[t] = (raw[r * n_in + k] - shift[k]) * scale[k];
+  if (t_in && k == 0) t_out[i] = t_in[r];
+}
+
+// y_i = W3 a2_i + b3 (a warp per row); with targets: dy_i = (y_i - t_i)/n and
+// the loss sum 1/(2n) sum e^2.
+__global__ void k_output(int n, int W, const float* __restrict__ a2, const __nv_bfloat16* __restrict__ w3,
+                         const float* __restrict__ b3, int n_in, const float* __restrict__ X,
+                         const float* __restrict__ wl, float* __restrict__ y, const float* __restrict__ t,
+                         float* __restrict__ dy, float* __restrict__ loss) {
+  const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  float s = 0.f;
+  for (int k = lane; k < W; k += 32) s = fmaf(a2[(long long)row * W + k], __bfloat162float(w3[k]), s);
+  if (lane < n_in) s = fmaf(X[(long long)row * n_in + lane], wl[lane], s);
+  s = warp_sum(s);
+  if (lane == 0) {
+    const float v = s + b3[0];
+    y[row] = v;
+    if (t) {
+      const float e = v - t[row];
+      dy[row] = e / (float)n;
+      atomicAdd(loss, 0.5f * e * e / (float)n);
+    }
+  }
+}
+
+// d2 = dy_i W3_k (1 - a2^2)
+__global__ void k_back_out(int n, int W, const float* __restrict__ dy, const __nv_bfloat16* __restrict__ w3,
+                           const float* __restrict__ a2, float* __restrict__ d2) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)n * W) return;
+  const int k = (int)(t % W);
+  const long long i = t / W;
+  const float g = a2[t];
+  d2[t] = dy[i] * __bfloat162float(w3[k]) * (1.f - g * g);
+}
+
+// out_k += sum_i w_i X[i, k] (w = 1 when null); rows split over blocks
+__global__ void k_colsum(int n, int c, const float* __restrict__ w, const float* __restrict__ X, float* __restrict__ out,
+                         int rows_per_block) {
+  const int k = threadIdx.x + blockIdx.y * blockDim.x;
+  if (k >= c) return;
+  const int r0 = blockIdx.x * rows_per_block;
+  const int r1 = min(n, r0 + rows_per_block);
+  float s = 0.f;
+  for (int i = r0; i < r1; ++i) s = fmaf(w ? w[i] : 1.f, X[(long long)i * c + k], s);
+  atomicAdd(out + k, s);
+}
+
+__global__ void k_round(int np, const float* __restrict__ theta, __nv_bfloat16* __restrict__ wbf) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < np) wbf[t] = __float2bfloat16_rn(theta[t]);
+}
+
+__global__ void k_adam(int np, float* __restrict__ theta, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1, float b2, float eps, float bc1, float bc2,
+                       __nv_bfloat16* __restrict__ wbf) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= np) return;
+  const float gt = g[t];
+  const float mt = b1 * m[t] + (1.f - b1) * gt;
+  const float vt = b2 * v[t] + (1.f - b2) * gt * gt;
+  m[t] = mt;
+  v[t] = vt;
+  const float th = theta[t] - lr * (mt / bc1) / (sqrtf(vt / bc2) + eps);
+  theta[t] = th;
+  wbf[t] = __float2bfloat16_rn(th);
+}
+
+// s = sqrt(mean_j (g1_j^2 + g2_j^2)) (1 when the data vanish): the data scale
+// that makes the features and the density of one problem O(1); the density is
+// linear in the data, so the network learns the map at unit data size.
+__global__ void k_ws_scale(int nb, const double* __restrict__ g1, const double* __restrict__ g2,
+                           double* __restrict__ s) {
+  __shared__ double part[32];
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    const double a = g1 ? g1[j] : 0.0, b = g2 ? g2[j] : 0.0;
+    acc += a * a + b * b;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    const double v = sqrt(t / (double)max(nb, 1));
+    s[0] = v > 0.0 ? v : 1.0;
+  }
+}
+
+// Per-DOF raw features: [g1/s, g2/s, n (3), x (3), level-set parameters p0..p5, 0, 0]
+__global__ void k_features(int nb, int d, const double* __restrict__ x0, const double* __restrict__ x1,
+                           const double* __restrict__ x2, const double* __restrict__ n0,
+                           const double* __restrict__ n1, const double* __restrict__ n2,
+                           const double* __restrict__ g1, const double* __restrict__ g2, LevelSet ls,
+                           const double* __restrict__ scale, float* __restrict__ F,
+                           const double* __restrict__ dens, float* __restrict__ target) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  const double is = 1.0 / scale[0];
+  if (target) target[j] = (float)(dens[j] * is);
+  float* f = F + (long long)j * KFBI_WS_FEATURES;
+  f[0] = g1 ? (float)(g1[j] * is) : 0.f;
+  f[1] = g2 ? (float)(g2[j] * is) : 0.f;
+  f[2] = (float)n0[j];
+  f[3] = (float)n1[j];
+  f[4] = d == 3 ? (float)n2[j] : 0.f;
+  f[5] = (float)x0[j];
+  f[6] = (float)x1[j];
+  f[7] = d == 3 ? (float)x2[j] : 0.f;
+  for (int k = 0; k < 6; ++k) f[8 + k] = k < ls.np ? (float)ls.p[k] : 0.f;
+  f[14] = 0.f;
+  f[15] = 0.f;
+}
+
+__global__ void k_to_density(int n, const float* __restrict__ y, double shift, double scale,
+                             const double* __restrict__ s, double* __restrict__ x) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) x[j] = ((double)y[j] * scale + shift) * s[0];
+}
+
+kfbi_status ensure(kfbi_mlp* m, int n) {
+  if (n <= m->cap) return KFBI_OK;
+  MLP_CUDA(m, cudaStreamSynchronize(m->stream));
+  float** bufs[] = {&m->X, &m->a1, &m->a2, &m->d1, &m->d2, &m->y, &m->dy, &m->tb};
+  for (float** b : bufs) {
+    cudaFree(*b);
+    *b = nullptr;
+  }
+  const int cap = std::max(n, 1024);
+  const size_t W = m->width;
+  MLP_CUDA(m, dalloc(&m->X, (size_t)cap * m->n_in));
+  MLP_CUDA(m, dalloc(&m->a1, (size_t)cap * W));
+  MLP_CUDA(m, dalloc(&m->a2, (size_t)cap * W));
+  MLP_CUDA(m, dalloc(&m->d1, (size_t)cap * W));
+  MLP_CUDA(m, dalloc(&m->d2, (size_t)cap * W));
+  MLP_CUDA(m, dalloc(&m->y, (size_t)cap));
+  MLP_CUDA(m, dalloc(&m->dy, (size_t)cap));
+  MLP_CUDA(m, dalloc(&m->tb, (size_t)cap));
+  m->cap = cap;
+  return KFBI_OK;
+}
+
+template <typename TB>
+void gemm(cudaStream_t st, int M, int N, int K, const float* A, long long sam, long long sak, const TB* B,
+          long long sbk, long long sbn, float* C, long long ldc, const float* bias, int act, const float* gate,
+          int mode) {
+  int splits = 1, chunk = K;
+  if (mode == 1) {   // weight gradients: long K (the rows), few output tiles
+    const int tiles = div_up(M, 64) * div_up(N, 64);
+    splits = std::max(1, std::min(div_up(K, 256), div_up(152 * 8, tiles)));
+    chunk = div_up(div_up(K, splits), 16) * 16;
+    splits = div_up(K, chunk);
+  }
+  dim3 grid(div_up(N, 64), div_up(M, 64), splits);
+  k_gemm<TB><<<grid, 256, 0, st>>>(M, N, K, chunk, A, sam, sak, B, sbk, sbn, C, ldc, bias, act, gate, mode);
+}
+
+// forward on rows already normalised into m->X
+kfbi_status forward_rows(kfbi_mlp* m, int n, const float* t) {
+  const int W = m->width, ni = m->n_in;
+  cudaStream_t st = m->stream;
+  const __nv_bfloat16* wb = m->wbf;
+  gemm<__nv_bfloat16>(st, n, W, ni, m->X, ni, 1, wb + m->oW1, 1, ni, m->a1, W, m->theta + m->ob1, 1, nullptr, 0);
+  gemm<__nv_bfloat16>(st, n, W, W, m->a1, W, 1, wb + m->oW2, 1, W, m->a2, W, m->theta + m->ob2, 1, nullptr, 0);
+  k_output<<<div_up(n, 8), 256, 0, st>>>(n, W, m->a2, wb + m->oW3, m->theta + m->ob3, ni, m->X,
+                                         m->theta + m->oWL, m->y, t, m->dy, m->loss);
+  MLP_CUDA(m, cudaGetLastError());
+  return KFBI_OK;
+}
+
+}  // namespace
+}  // namespace kfbi
+
+using namespace kfbi;
+
+extern "C" {
+
+const char* kfbi_mlp_last_error(const kfbi_mlp* m) { return m ? m->err.c_str() : ""; }
+
+kfbi_status kfbi_mlp_destroy(kfbi_mlp* m) {
+  if (!m) return KFBI_OK;
+  if (m->stream) cudaStreamSynchronize(m->stream);
+  void* bufs[] = {m->theta, m->grad, m->mom1, m->mom2, m->wbf, m->shift, m->scale, m->X,
+                  m->a1,    m->a2,   m->d1,   m->d2,   m->y,   m->dy,    m->tb,    m->loss};
+  for (void* b : bufs) cudaFree(b);
+  delete m;
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_mlp_create(int n_in, int width, void* cuda_stream, kfbi_mlp** out) {
+  if (!out || n_in < 1 || n_in > KFBI_WS_FEATURES || width < 1 || width > 1024) return KFBI_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return KFBI_ERR_CUDA;
+  kfbi_mlp* m = new kfbi_mlp();
+  m->n_in = n_in;
+  m->width = width;
+  m->stream = static_cast<cudaStream_t>(cuda_stream);
+  m->oW1 = 0;
+  m->ob1 = width * n_in;
+  m->oW2 = m->ob1 + width;
+  m->ob2 = m->oW2 + width * width;
+  m->oW3 = m->ob2 + width;
+  m->ob3 = m->oW3 + width;
+  m->oWL = m->ob3 + 1;
+  m->nparam = m->oWL + n_in;
+  const size_t np = m->nparam;
+  bool ok = dalloc(&m->theta, np) == cudaSuccess && dalloc(&m->grad, np) == cudaSuccess &&
+            dalloc(&m->mom1, np) == cudaSuccess && dalloc(&m->mom2, np) == cudaSuccess &&
+            dalloc(&m->wbf, np) == cudaSuccess && dalloc(&m->shift, n_in) == cudaSuccess &&
+            dalloc(&m->scale, n_in) == cudaSuccess && dalloc(&m->loss, 1) == cudaSuccess;
+  if (ok) {
+    std::vector<float> one(n_in, 1.f);
+    ok = cudaMemset(m->theta, 0, np * 4) == cudaSuccess && cudaMemset(m->mom1, 0, np * 4) == cudaSuccess &&
+         cudaMemset(m->mom2, 0, np * 4) == cudaSuccess && cudaMemset(m->grad, 0, np * 4) == cudaSuccess &&
+         cudaMemset(m->wbf, 0, np * 2) == cudaSuccess && cudaMemset(m->shift, 0, n_in * 4) == cudaSuccess &&
+         cudaMemcpy(m->scale, one.data(), n_in * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+  }
+  if (!ok) {
+    kfbi_mlp_destroy(m);
+    return KFBI_ERR_CUDA;
+  }
+  *out = m;
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_mlp_num_params(const kfbi_mlp* m, int* count) {
+  if (!m || !count) return KFBI_ERR_ARG;
+  *count = m->nparam;
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_mlp_set_params(kfbi_mlp* m, const float* params) {
+  if (!m || !params) return KFBI_ERR_ARG;
+  MLP_CUDA(m, cudaMemcpyAsync(m->theta, params, sizeof(float) * m->nparam, cudaMemcpyDeviceToDevice, m->stream));
+  MLP_CUDA(m, cudaMemsetAsync(m->mom1, 0, sizeof(float) * m->nparam, m->stream));
+  MLP_CUDA(m, cudaMemsetAsync(m->mom2, 0, sizeof(float) * m->nparam, m->stream));
+  m->step = 0;
+  k_round<<<div_up(m->nparam, 256), 256, 0, m->stream>>>(m->nparam, m->theta, m->wbf);
+  MLP_CUDA(m, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_mlp_get_params(const kfbi_mlp* mc, float* params, float* grads) {
+  kfbi_mlp* m = const_cast<kfbi_mlp*>(mc);
+  if (!m) return KFBI_ERR_ARG;
+  if (params)
+    MLP_CUDA(m, cudaMemcpyAsync(params, m->theta, sizeof(float) * m->nparam, cudaMemcpyDeviceToDevice, m->stream));
+  if (grads)
+    MLP_CUDA(m, cudaMemcpyAsync(grads, m->grad, sizeof(float) * m->nparam, cudaMemcpyDeviceToDevice, m->stream));
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_mlp_set_affine(kfbi_mlp* m, const float* in_shift, const float* in_scale, double out_shift,
+                                double out_scale) {
+  if (!m || !in_shift || !in_scale || !std::isfinite(out_shift) || !std::isfinite(out_scale)) return KFBI_ERR_ARG;
+  MLP_CUDA(m, cudaMemcpy(m->shift, in_shift, sizeof(float) * m->n_in, cudaMemcpyHostToDevice));
+  MLP_CUDA(m, cudaMemcpy(m->scale, in_scale, sizeof(float) * m->n_in, cudaMemcpyHostToDevice));
+  m->out_shift = out_shift;
+  m->out_scale = out_scale;
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_mlp_forward(kfbi_mlp* m, const float* X, int n, float* y) {
+  if (!m || n < 0 || (n > 0 && (!X || !y))) return KFBI_ERR_ARG;
+  if (n == 0) return KFBI_OK;
+  KFBI_TRY(ensure(m, n));
+  const long long tot = (long long)n * m->n_in;
+  k_normalise<<<div_up(tot, 256), 256, 0, m->stream>>>(n, m->n_in, X, nullptr, m->shift, m->scale, m->X,
+                                                        nullptr, nullptr);
+  KFBI_TRY(forward_rows(m, n, nullptr));
+  MLP_CUDA(m, cudaMemcpyAsync(y, m->y, sizeof(float) * n, cudaMemcpyDeviceToDevice, m->stream));
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_mlp_loss_grad(kfbi_mlp* m, const float* X, const float* t, const int32_t* rows, int n,
+                               float* loss) {
+  if (!m || !X || !t || n < 1) return KFBI_ERR_ARG;
+  KFBI_TRY(ensure(m, n));
+  cudaStream_t st = m->stream;
+  const int W = m->width, ni = m->n_in;
+  const long long tot = (long long)n * ni;
+  MLP_CUDA(m, cudaMemsetAsync(m->loss, 0, sizeof(float), st));
+  MLP_CUDA(m, cudaMemsetAsync(m->grad, 0, sizeof(float) * m->nparam, st));
+  k_normalise<<<div_up(tot, 256), 256, 0, st>>>(n, ni, X, rows, m->shift, m->scale, m->X, t, m->tb);
+  KFBI_TRY(forward_rows(m, n, m->tb));
+  const __nv_bfloat16* wb = m->wbf;
+  float* g = m->grad;
+  // output layer: dW3 = dy^T a2, db3 = sum dy
+  const int rpb = 256;
+  k_colsum<<<dim3(div_up(n, rpb), div_up(W, 256)), 256, 0, st>>>(n, W, m->dy, m->a2, g + m->oW3, rpb);
+  k_colsum<<<dim3(div_up(n, rpb), 1), 32, 0, st>>>(n, 1, nullptr, m->dy, g + m->ob3, rpb);
+  k_colsum<<<dim3(div_up(n, rpb), 1), 32, 0, st>>>(n, ni, m->dy, m->X, g + m->oWL, rpb);
+  // d2 = dy W3 (1 - a2^2); dW2 = d2^T a1, db2 = sum d2
+  k_back_out<<<div_up((long long)n * W, 256), 256, 0, st>>>(n, W, m->dy, wb + m->oW3, m->a2, m->d2);
+  gemm<float>(st, W, W, n, m->d2, 1, W, m->a1, W, 1, g + m->oW2, W, nullptr, 0, nullptr, 1);
+  k_colsum<<<dim3(div_up(n, rpb), div_up(W, 256)), 256, 0, st>>>(n, W, nullptr, m->d2, g + m->ob2, rpb);
+  // d1 = (d2 W2) (1 - a1^2); dW1 = d1^T x~, db1 = sum d1
+  gemm<__nv_bfloat16>(st, n, W, W, m->d2, W, 1, wb + m->oW2, W, 1, m->d1, W, nullptr, 0, m->a1, 0);
+  gemm<float>(st, W, ni, n, m->d1, 1, W, m->X, ni, 1, g + m->oW1, ni, nullptr, 0, nullptr, 1);
+  k_colsum<<<dim3(div_up(n, rpb), div_up(W, 256)), 256, 0, st>>>(n, W, nullptr, m->d1, g + m->ob1, rpb);
+  MLP_CUDA(m, cudaGetLastError());
+  if (loss) MLP_CUDA(m, cudaMemcpyAsync(loss, m->loss, sizeof(float), cudaMemcpyDeviceToDevice, st));
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_mlp_adam(kfbi_mlp* m, float lr, float beta1, float beta2, float eps) {
+  if (!m || !(lr > 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0)) return KFBI_ERR_ARG;
+  m->step += 1;
+  const float bc1 = (float)(1.0 - std::pow((double)beta1, (double)m->step));
+  const float bc2 = (float)(1.0 - std::pow((double)beta2, (double)m->step));
+  k_adam<<<div_up(m->nparam, 256), 256, 0, m->stream>>>(m->nparam, m->theta, m->grad, m->mom1, m->mom2, lr, beta1,
+                                                         beta2, eps, bc1, bc2, m->wbf);
+  MLP_CUDA(m, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_warm_start_features(kfbi_problem* p, const kfbi_data* data, const double* density,
+                                     float* features, float* target) {
+  if (!p || !data || !features || !data->g1 || (!density != !target)) return KFBI_ERR_ARG;
+  const Grid g = p->g;
+  if (!p->ws_scale) KFBI_CUDA(p, dalloc(&p->ws_scale, 1));
+  KFBI_LAUNCH(p, KFBI_KC_OTHER, k_ws_scale<<<1, 1024, 0, p->stream>>>(p->nb, data->g1, data->g2, p->ws_scale));
+  KFBI_LAUNCH(p, KFBI_KC_OTHER, k_features<<<div_up(p->nb, 128), 128, 0, p->stream>>>(
+      p->nb, g.d, p->x[0], p->x[1], g.d == 3 ? p->x[2] : p->x[0], p->nrm[0], p->nrm[1],
+      g.d == 3 ? p->nrm[2] : p->nrm[0], data->g1, data->g2, p->ls, p->ws_scale, features, density, target));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_warm_start(kfbi_problem* p, kfbi_mlp* m, const kfbi_data* data, double* x0) {
+  if (!p || !m || !data || !x0 || !data->g1) return KFBI_ERR_ARG;
+  if (m->n_in != KFBI_WS_FEATURES) return fail(p, KFBI_ERR_ARG, "the network must take KFBI_WS_FEATURES inputs");
+  if (m->stream != p->stream) return fail(p, KFBI_ERR_ARG, "network and problem must share a stream");
+  if (m->width < KFBI_WS_FEATURES) return fail(p, KFBI_ERR_ARG, "the network width must be >= KFBI_WS_FEATURES");
+  const int nb = p->nb;
+  {
+    kfbi_status s = ensure(m, nb);
+    if (s != KFBI_OK) return fail(p, s, m->err);
+  }
+  // features straight into the network's input scratch, then normalise in place
+  KFBI_TRY(kfbi_warm_start_features(p, data, nullptr, m->d1, nullptr));
+  const long long tot = (long long)nb * m->n_in;
+  KFBI_LAUNCH(p, KFBI_KC_OTHER, k_normalise<<<div_up(tot, 256), 256, 0, p->stream>>>(
+      nb, m->n_in, m->d1, nullptr, m->shift, m->scale, m->X, nullptr, nullptr));
+  {
+    kfbi_status s = forward_rows(m, nb, nullptr);
+    if (s != KFBI_OK) return fail(p, s, m->err);
+  }
+  KFBI_LAUNCH(p, KFBI_KC_OTHER, k_to_density<<<div_up(nb, 256), 256, 0, p->stream>>>(nb, m->y, m->out_shift,
+                                                                                         m->out_scale, p->ws_scale, x0));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+}  // extern "C"

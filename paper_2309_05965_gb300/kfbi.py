@@ -59,7 +59,7 @@ class GmresOpts(ctypes.Structure):
 
 class GmresInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("rel_res", ctypes.c_double),
-                ("t_ms", ctypes.c_double * 8)]
+                ("t_ms", ctypes.c_double * 8), ("x0_rejected", ctypes.c_int)]
 
 
 # name -> (argtypes) ; all return kfbi_status except kfbi_last_error
@@ -90,6 +90,17 @@ SIGNATURES = {
     "kfbi_create_batch": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)],
     "kfbi_destroy_batch": [_P],
     "kfbi_gmres_solve_batch": [_P, _P, ctypes.POINTER(GmresOpts), _P, _P],
+    "kfbi_mlp_create": [ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_void_p)],
+    "kfbi_mlp_destroy": [_P],
+    "kfbi_mlp_num_params": [_P, _I],
+    "kfbi_mlp_set_params": [_P, _P],
+    "kfbi_mlp_get_params": [_P, _P, _P],
+    "kfbi_mlp_set_affine": [_P, _P, _P, ctypes.c_double, ctypes.c_double],
+    "kfbi_mlp_forward": [_P, _P, ctypes.c_int, _P],
+    "kfbi_mlp_loss_grad": [_P, _P, _P, _P, ctypes.c_int, _P],
+    "kfbi_mlp_adam": [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float],
+    "kfbi_warm_start_features": [_P, ctypes.POINTER(Data), _P, _P, _P],
+    "kfbi_warm_start": [_P, _P, ctypes.POINTER(Data), _P],
     "kfbi_box_solve_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                ctypes.c_int, ctypes.c_double, _P, _P, _P],
     "kfbi_launch_counts": [_P, _P, ctypes.c_int],
@@ -117,6 +128,8 @@ def load(path: str = LIB_PATH):
         f.restype = ctypes.c_int
     lib.kfbi_last_error.argtypes = [_P]
     lib.kfbi_last_error.restype = ctypes.c_char_p
+    lib.kfbi_mlp_last_error.argtypes = [_P]
+    lib.kfbi_mlp_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -260,6 +273,71 @@ def kfbi_gmres_solve_batch(b, handles, datas, opts: GmresOpts, densities):
                                          ctypes.cast(parr, ctypes.c_void_p),
                                          ctypes.cast(infos, ctypes.c_void_p)), handles[0])
     return list(infos)
+
+
+WS_FEATURES = 16   # KFBI_WS_FEATURES
+
+
+def _check_mlp(status, m):
+    if status != KFBI_OK:
+        msg = load().kfbi_mlp_last_error(m)
+        raise KfbiError(status, msg.decode() if msg else "")
+
+
+def kfbi_mlp_create(n_in, width, stream=None):
+    m = ctypes.c_void_p()
+    _check(load().kfbi_mlp_create(n_in, width, _stream_handle(stream), ctypes.byref(m)))
+    return m
+
+
+def kfbi_mlp_destroy(m):
+    _check(load().kfbi_mlp_destroy(m))
+
+
+def kfbi_mlp_num_params(m):
+    c = ctypes.c_int()
+    _check_mlp(load().kfbi_mlp_num_params(m, ctypes.byref(c)), m)
+    return c.value
+
+
+def kfbi_mlp_set_params(m, params):
+    _check_mlp(load().kfbi_mlp_set_params(m, _ptr(params)), m)
+
+
+def kfbi_mlp_get_params(m, params=None, grads=None):
+    _check_mlp(load().kfbi_mlp_get_params(m, _ptr(params), _ptr(grads)), m)
+
+
+def kfbi_mlp_set_affine(m, in_shift, in_scale, out_shift, out_scale):
+    import numpy as np
+    a = np.ascontiguousarray(in_shift, dtype=np.float32)
+    b = np.ascontiguousarray(in_scale, dtype=np.float32)
+    _check_mlp(load().kfbi_mlp_set_affine(m, a.ctypes.data_as(ctypes.c_void_p),
+                                          b.ctypes.data_as(ctypes.c_void_p), float(out_shift),
+                                          float(out_scale)), m)
+
+
+def kfbi_mlp_forward(m, X, y):
+    _check_mlp(load().kfbi_mlp_forward(m, _ptr(X), int(X.shape[0]), _ptr(y)), m)
+
+
+def kfbi_mlp_loss_grad(m, X, t, rows=None, loss=None, n=None):
+    """Gradient over the rows `rows` (int32 device tensor) of X, t, or all rows."""
+    count = int(rows.shape[0]) if rows is not None else int(X.shape[0] if n is None else n)
+    _check_mlp(load().kfbi_mlp_loss_grad(m, _ptr(X), _ptr(t), _ptr(rows), count, _ptr(loss)), m)
+
+
+def kfbi_mlp_adam(m, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    _check_mlp(load().kfbi_mlp_adam(m, lr, beta1, beta2, eps), m)
+
+
+def kfbi_warm_start_features(h, data, features, density=None, target=None):
+    _check(load().kfbi_warm_start_features(h, ctypes.byref(data), _ptr(density), _ptr(features),
+                                           _ptr(target)), h)
+
+
+def kfbi_warm_start(h, m, data, x0):
+    _check(load().kfbi_warm_start(h, m, ctypes.byref(data), _ptr(x0)), h)
 
 
 def kfbi_box_solve_noalloc(dim, n, lo, hi, order, kappa, rhs, u, stream=None):

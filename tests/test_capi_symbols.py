@@ -22,7 +22,7 @@ def test_library_builds_and_exports_all_declared_symbols():
     missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, missing
     # the binding covers every declared entry point
-    covered = set(kfbi.SIGNATURES) | {"kfbi_last_error"}
+    covered = set(kfbi.SIGNATURES) | {"kfbi_last_error", "kfbi_mlp_last_error"}
     assert set(names) <= covered, set(names) - covered
 
 

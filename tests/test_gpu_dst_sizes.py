@@ -1,0 +1,96 @@
+"""Box solve by sine transform at every transform length the kernels
+instantiate (L = 2N from 16 to 4096): FP64 path and mixed path (FP32
+transforms, FP64 residuals, refinement) against the oracle's DST-I solve on a
+seeded random right-hand side, and against the closed form on single sine
+modes (eigenvectors of the compact operators: u = R / lambda, lambda the
+stencil's symbol sum_o c_o prod_k cos(p_k pi o_k / N))."""
+import itertools
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import boxsolve as BS
+from tests.gpu_util import dev, empty, host, rel_err
+
+pytestmark = pytest.mark.gpu
+
+# (dim, N, order): every LOGL = log2(2N) from 4 to 12, 2D and 3D
+SIZES = [(2, 8, 2), (2, 16, 2), (3, 16, 2), (2, 32, 4), (3, 32, 4), (2, 64, 4), (3, 64, 4),
+         (2, 128, 4), (3, 128, 4), (2, 256, 4), (2, 512, 4), (2, 1024, 4), (2, 2048, 4)]
+ORACLE_MAX = {2: 1024, 3: 128}   # sizes where the oracle's full solve is compared
+
+
+def _problem(d, n, order, precision):
+    from paper_2309_05965_gb300 import build, kfbi
+    build.build()
+    if d == 2:
+        w = W.Workload("box", 2, n, -1.0, 1.0, W.LS_ELLIPSE, [0.0, 0.0, 0.7, 0.6, 0.0],
+                       W.KIND_DIRICHLET, kappa=1.0, exact="exp_sin")
+    else:
+        w = W.Workload("box", 3, n, -1.0, 1.0, W.LS_ELLIPSOID, [0.0, 0.0, 0.0, 0.75, 0.7, 0.65],
+                       W.KIND_DIRICHLET, kappa=1.0, exact="exp3")
+    w.order = order
+    G = kfbi.Problem.from_workload(w, precision=precision, box_max_iters=8)
+    return w, G
+
+
+def _mixed_tol(n):
+    # FP32 transforms contract the error by about eps32 * cond(A_h) per step,
+    # cond ~ 4 N^2 / pi^2, eight steps at most; the FP64 residual itself
+    # resolves u only to ~eps64 * cond(A_h)
+    c = 6e-8 * 0.45 * n * n
+    return max(5e-12, 1e-17 * n * n, 10.0 * c ** 8)
+
+
+def _symbol(d, order, n, h, kappa, modes):
+    c = BS.stencil_coeffs(d, order, h, kappa)
+    lam = 0.0
+    for o in itertools.product((-1, 0, 1), repeat=d):
+        w = c[sum(1 for v in o if v != 0)]
+        lam += w * np.prod([np.cos(p * np.pi * ok / n) for p, ok in zip(modes, o)])
+    return lam
+
+
+@pytest.mark.parametrize("d,n,order", SIZES)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_dst_random_rhs_matches_oracle(d, n, order, precision):
+    if n > ORACLE_MAX[d]:
+        pytest.skip("full oracle solve only up to the listed sizes")
+    from paper_2309_05965_gb300 import kfbi
+    w, G = _problem(d, n, order, precision)
+    R = W.sine_grid_rhs(d, n, 17)
+    ref = BS.dst_solve(R, d, order, w.h, w.kappa)
+    u = empty(G.grid_shape)
+    kfbi.kfbi_box_solve(G.handle, dev(R), u)
+    tol = 1e-12 if precision == 0 else _mixed_tol(n)
+    assert rel_err(host(u), ref) < tol
+    G.close()
+
+
+@pytest.mark.parametrize("d,n,order", SIZES)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_dst_sine_modes_closed_form(d, n, order, precision):
+    import torch
+    from paper_2309_05965_gb300 import kfbi
+    w, G = _problem(d, n, order, precision)
+    for modes in ([1] * d, [n - 1] * d, [n // 2 + 1, 3, n - 2][:d], [2, n - 1, n // 3][:d]):
+        R = torch.ones(G.grid_shape, dtype=torch.float64, device="cuda")
+        for k, p in enumerate(modes):
+            shape = [1] * d
+            shape[k] = n + 1
+            # reduce p i modulo 2N exactly first: an FP64 argument p pi i / N
+            # of size ~p pi carries an absolute error ~1e-13 that is not an
+            # eigenvector and that A_h^{-1} amplifies by cond(A_h)
+            arg = torch.remainder(p * torch.arange(n + 1, device="cuda"), 2 * n).double()
+            R = R * torch.sin(np.pi * arg / n).reshape(shape)
+        lam = _symbol(d, order, n, w.h, w.kappa, modes)
+        u = empty(G.grid_shape)
+        kfbi.kfbi_box_solve(G.handle, R.contiguous(), u)
+        want = R / lam
+        # the symbol itself carries cancellation ~ eps64 * cond for low modes
+        cond = 0.45 * n * n
+        tol = (1e-12 if precision == 0 else _mixed_tol(n)) + 4e-16 * cond
+        err = float((u - want).abs().max() / want.abs().max())
+        assert err < tol, (modes, err)
+    G.close()

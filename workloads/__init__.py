@@ -313,10 +313,27 @@ def ellipsoid_harmonic_3d(rng: np.random.Generator, n: int = 256,
     exterior solution 0."""
     axes = rng.uniform(0.3, 0.7, size=3)
     amps = rng.standard_normal(8)
+    return harmonic_ellipsoid_3d(axes, amps, n, contrast)
+
+
+def harmonic_ellipsoid_3d(axes, amps, n: int, contrast: float = 10.0) -> Workload:
+    """The ellipsoid interface problem above with given axes and amplitudes."""
     return Workload("ellipsoid_harmonic_3d", 3, n, -1.0, 1.0, LS_ELLIPSOID,
-                    [0.0, 0.0, 0.0, *axes.tolist()], KIND_INTERFACE_MU,
+                    [0.0, 0.0, 0.0, *[float(a) for a in axes]], KIND_INTERFACE_MU,
                     sigma_in=contrast, sigma_out=1.0, exact="harmonic3",
-                    extra={"amps": amps.tolist()})
+                    extra={"amps": [float(a) for a in amps]})
+
+
+def warm_start_training_set(seed: int, geometries: int, draws: int):
+    """(axes, amplitudes) pairs of the learned-start training solves: `geometries`
+    ellipsoids (axes ~U[0.3,0.7]^3), each with `draws` amplitude vectors
+    (N(0,1)^8), all from one seeded generator."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(geometries):
+        axes = rng.uniform(0.3, 0.7, size=3)
+        out.append((axes, [rng.standard_normal(8) for _ in range(draws)]))
+    return out
 
 
 def sine_grid_rhs(dim: int, n: int, seed: int) -> np.ndarray:
