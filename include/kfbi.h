@@ -295,6 +295,10 @@ kfbi_status kfbi_mlp_forward(kfbi_mlp* m, const float* X, int n, float* y);
  * loss: one device float (may be NULL). */
 kfbi_status kfbi_mlp_loss_grad(kfbi_mlp* m, const float* X, const float* t, const int32_t* rows,
                                int n, float* loss);
+/* Parameter groups that kfbi_mlp_adam updates: bit 0 the nonlinear branch
+ * (W1, b1, W2, b2, W3), bit 1 the linear part (b3, WL); 3 = all (the
+ * default).  Resets the Adam moments and step counter. */
+kfbi_status kfbi_mlp_set_trainable(kfbi_mlp* m, int groups);
 /* One Adam step with the last gradient (step counter kept by the network). */
 kfbi_status kfbi_mlp_adam(kfbi_mlp* m, float lr, float beta1, float beta2, float eps);
 /* Per-DOF features (N_b x KFBI_WS_FEATURES floats): [g1/s, g2/s, n (3),

@@ -39,6 +39,7 @@ struct BoxSolver {
   int L = 0, logL = 0;
   double* tw64 = nullptr;     // L/2 twiddles exp(-2 pi i t / L)
   float* tw32 = nullptr;
+  float* twst = nullptr;      // FP32 stage twiddle tables (stage_twiddles)
   double* cosv = nullptr;     // cos(k pi / N), k = 0..N
   double* s64 = nullptr;      // sin^2(k pi / 2N), k = 0..N
   float* s32 = nullptr;
@@ -84,6 +85,7 @@ struct PassArgs {
   unsigned long long* corr_max;   // last pass: max |correction|, max |u + correction|
   float* delta_out;               // accumulate pass: also keep the FP32 correction (in place)
   long long* dstfix;              // last pass of a refinement step: u_fix += round(delta 2^F)
+  const void* twst;               // FP32 path: stage twiddle tables (stage_twiddles)
   const float* fixf;              // [0..1] 2^Fa, 2^Fb; [2..3] 2^-Fa, 2^-Fb (k_fix_scale)
 };
 
@@ -323,29 +325,6 @@ __global__ void __launch_bounds__(256) k_dst_pass(PassArgs A) {
   dst_pass_device<T, P>(A, blockIdx.x, blockIdx.y, smraw);
 }
 
-// Persistent batched pass over many independent grids (one pair per work
-// item): item -> instance by binary search in the prefix `start`, each
-// instance with its own PassArgs (its own N, pointers and convergence flag).
-template <typename T>
-__global__ void __launch_bounds__(256) k_dst_pass_batched(const PassArgs* __restrict__ args,
-                                                         const int* __restrict__ start, int ninst) {
-  extern __shared__ unsigned char smraw[];
-  const int total = start[ninst];
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    int lo = 0, hi = ninst;
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (start[mid] <= item) lo = mid; else hi = mid;
-    }
-    const PassArgs& A = args[lo];
-    if (A.skip && *A.skip) continue;
-    const int local = item - start[lo];
-    const int npx = A.n / 2;
-    dst_pass_device<T, 1>(A, local % npx, local / npx, smraw);
-    __syncthreads();
-  }
-}
-
 // ---------------------------------------------------------------------------
 // FP32 passes of the mixed-precision path with register DFTs.
 //
@@ -436,6 +415,8 @@ __device__ __forceinline__ void dftr(Cx<float>* v, Cx<float>* out) {
 }
 
 // One radix-R Stockham stage in place on the padded buffer s (one sequence).
+// tw is this stage's twiddle table T[r NS + k] = exp(-2 pi i r k / (NS R)):
+// the lanes of a warp have consecutive k, so each load is coalesced.
 template <int L, int R, int NS>
 __device__ __forceinline__ void reg_stage(Cx<float>* s, int tid, const Cx<float>* __restrict__ tw) {
   constexpr int G = L / R;    // R-point DFTs per stage
@@ -456,7 +437,10 @@ __device__ __forceinline__ void reg_stage(Cx<float>* s, int tid, const Cx<float>
     Cx<float>* x = v + q * R;
     if constexpr (NS > 1) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) x[r] = cmul(x[r], tw[(r * k) * (L / (NS * R))]);
+      for (int r = 1; r < R; ++r) {
+        const float2 w = __ldg(reinterpret_cast<const float2*>(tw) + r * NS + k);
+        x[r] = cmul(x[r], Cx<float>{w.x, w.y});
+      }
     }
     Cx<float> y[R];
     dftr<R>(x, y);
@@ -467,17 +451,61 @@ __device__ __forceinline__ void reg_stage(Cx<float>* s, int tid, const Cx<float>
   __syncthreads();
 }
 
+// Stage plan of length 2^LOGL: radix-16 stages, then one of radix 2^(LOGL mod 4).
+// The twiddle tables of the stages after the first lie back to back.
 template <int LOGL>
 __device__ __forceinline__ void reg_fft(Cx<float>* s, int tid, const Cx<float>* __restrict__ tw) {
   constexpr int L = 1 << LOGL;
   constexpr int N16 = LOGL / 4, REM = LOGL % 4;
   constexpr int NSF = 1 << (4 * N16);
+  constexpr int OFF3 = 16 * 16, OFFR = (N16 >= 2 ? 256 : 0) + (N16 >= 3 ? 16 * 256 : 0);
   if constexpr (N16 >= 1) reg_stage<L, 16, 1>(s, tid, tw);
   if constexpr (N16 >= 2) reg_stage<L, 16, 16>(s, tid, tw);
-  if constexpr (N16 >= 3) reg_stage<L, 16, 256>(s, tid, tw);
-  if constexpr (REM == 1) reg_stage<L, 2, NSF>(s, tid, tw);
-  if constexpr (REM == 2) reg_stage<L, 4, NSF>(s, tid, tw);
-  if constexpr (REM == 3) reg_stage<L, 8, NSF>(s, tid, tw);
+  if constexpr (N16 >= 3) reg_stage<L, 16, 256>(s, tid, tw + OFF3);
+  if constexpr (REM == 1) reg_stage<L, 2, NSF>(s, tid, tw + OFFR);
+  if constexpr (REM == 2) reg_stage<L, 4, NSF>(s, tid, tw + OFFR);
+  if constexpr (REM == 3) reg_stage<L, 8, NSF>(s, tid, tw + OFFR);
+}
+
+// Host copy of the same plan: the stage twiddle tables for length 2^logL.
+std::vector<float> stage_twiddles(int logL) {
+  const int L = 1 << logL;
+  std::vector<int> radix;
+  for (int k = 0; k < logL / 4; ++k) radix.push_back(16);
+  if (logL % 4) radix.push_back(1 << (logL % 4));
+  std::vector<float> out;
+  int ns = 1;
+  for (int R : radix) {
+    if (ns > 1)
+      for (int r = 0; r < R; ++r)
+        for (int k = 0; k < ns; ++k) {
+          const double ang = -2.0 * M_PI * (double)(r * k) / (double)(ns * R);
+          out.push_back((float)std::cos(ang));
+          out.push_back((float)std::sin(ang));
+        }
+    ns *= R;
+  }
+  (void)L;
+  if (out.empty()) out.assign(2, 0.f);
+  return out;
+}
+
+// round(x) as int64 for |x| < 2^62 from FP32 pieces: the 64-bit conversions
+// run on the FP64 pipe, which GB300 has at 1/64 of the FP32 rate
+__device__ __forceinline__ long long f2ll(float x) {
+  const float ax = fabsf(x);
+  const float hi = floorf(ax * 2.3283064365386963e-10f);   // ax / 2^32
+  const float lo = fmaf(hi, -4294967296.f, ax);            // ax - hi 2^32, exact, in [0, 2^32)
+  const long long r = ((long long)__float2uint_rz(hi) << 32) + (long long)__float2uint_rn(lo);
+  return x < 0.f ? -r : r;
+}
+
+// int64 -> FP32 (within 1 ulp) from 32-bit pieces of |v| (a two's-complement
+// split of a small negative v would cancel: -5 = -2^32 + (2^32 - 5))
+__device__ __forceinline__ float ll2f(long long v) {
+  const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const float m = fmaf(__uint2float_rn((unsigned)(a >> 32)), 4294967296.f, __uint2float_rn((unsigned)a));
+  return v < 0 ? -m : m;
 }
 
 template <int LOGL, int P>
@@ -490,45 +518,68 @@ struct Reg {
 };
 
 // Default pairs per CTA: 128 threads per CTA up to L = 2048.
-constexpr int reg_pairs(int logL) { return logL >= 11 ? 1 : (1 << (11 - logL)); }
+__host__ __device__ constexpr int reg_pairs(int logL) { return logL >= 11 ? 1 : (1 << (11 - logL)); }
 
+// One FP32 pass over the 2P lines b0 = 1 + 2 P bx ... of line family a = by + 1.
+// Offsets are 32-bit (grids up to 1025^3 nodes); each load/store item is one
+// complex pair (the same element of lines 2q and 2q+1).
 template <int LOGL, int P>
-__global__ void __launch_bounds__(Reg<LOGL, P>::THREADS) k_dst32(PassArgs A) {
+__device__ __forceinline__ void dst32_body(const PassArgs& A, int bx, int by, Cx<float>* sm) {
   using F = Reg<LOGL, P>;
   constexpr int L = F::L, LP = F::LP;
   constexpr int n = L / 2, nm1 = n - 1;
-  if (A.skip && *A.skip) return;
-  extern __shared__ unsigned char smraw[];
-  Cx<float>* sm = reinterpret_cast<Cx<float>*>(smraw);
-  const Cx<float>* tw = static_cast<const Cx<float>*>(A.tw);
-  const int a = blockIdx.y + 1;
-  const int b0 = 1 + 2 * P * blockIdx.x;
-  const long long abase = (long long)a * A.sa;
-  const bool contig = A.es == 1;
-  constexpr int nval = nm1 * 2 * P;
-  // odd extensions of the 2P lines: line 2q -> real part, 2q+1 -> imaginary
-  for (int t = threadIdx.x; t < nval; t += F::THREADS) {
-    int j, q;
+  const Cx<float>* tw = static_cast<const Cx<float>*>(A.twst);
+  const int a = by + 1;
+  const int b0 = 1 + 2 * P * bx;
+  const int sa = (int)A.sa, sb = (int)A.sb, es = (int)A.es;
+  const int abase = a * sa;
+  const bool contig = es == 1;
+  constexpr int nitem = nm1 * P;                      // (element, pair) items
+  constexpr int NIT = (nitem + F::THREADS - 1) / F::THREADS;
+  // contiguous lines: element fastest (coalesced along each line); strided
+  // lines: pair fastest (the 2P adjacent lines of a row together)
+  auto coords = [&](int t, int& j, int& q) {
     if (contig) {
       j = 1 + t % nm1;
       q = t / nm1;
     } else {
-      q = t % (2 * P);
-      j = 1 + t / (2 * P);
+      q = t % P;
+      j = 1 + t / P;
     }
-    const int b = b0 + q;
-    float v = 0.f;
-    if (b <= nm1) {
-      const long long off = abase + (long long)b * A.sb + (long long)j * A.es;
-      v = A.src64 ? (float)static_cast<const double*>(A.src)[off] : static_cast<const float*>(A.src)[off];
+  };
+  {
+    float2 vals[NIT];
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+      const int t = threadIdx.x + it * F::THREADS;
+      int j, q;
+      coords(t < nitem ? t : 0, j, q);
+      const int bA = b0 + 2 * q;
+      const int off = abase + bA * sb + j * es;
+      float2 v = {0.f, 0.f};
+      if (t < nitem && bA <= nm1) {
+        if (A.src64) {
+          const double* src = static_cast<const double*>(A.src);
+          v.x = (float)__ldg(src + off);
+          if (bA + 1 <= nm1) v.y = (float)__ldg(src + off + sb);
+        } else {
+          const float* src = static_cast<const float*>(A.src);
+          v.x = __ldg(src + off);
+          if (bA + 1 <= nm1) v.y = __ldg(src + off + sb);
+        }
+      }
+      vals[it] = v;
     }
-    Cx<float>* zz = sm + (q >> 1) * LP;
-    if (q & 1) {
-      zz[padi(j)].y = v;
-      zz[padi(L - j)].y = -v;
-    } else {
-      zz[padi(j)].x = v;
-      zz[padi(L - j)].x = -v;
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+      const int t = threadIdx.x + it * F::THREADS;
+      if (t < nitem) {
+        int j, q;
+        coords(t, j, q);
+        Cx<float>* zz = sm + q * LP;
+        zz[padi(j)] = {vals[it].x, vals[it].y};
+        zz[padi(L - j)] = {-vals[it].x, -vals[it].y};
+      }
     }
   }
   for (int t = threadIdx.x; t < P; t += F::THREADS) {
@@ -543,7 +594,7 @@ __global__ void __launch_bounds__(Reg<LOGL, P>::THREADS) k_dst32(PassArgs A) {
     // spectral division in place (Z_{L-k} = -Z_k keeps the odd symmetry), then
     // the same FFT gives the inverse transform
     const float kh2 = (float)A.kt, g = (float)A.gscale;
-    const float sa = A.d == 3 ? A.s32[a] : 0.f;
+    const float sa3 = A.d == 3 ? A.s32[a] : 0.f;
     for (int t = threadIdx.x; t < L * P; t += F::THREADS) {
       const int q = t >> LOGL, k = t & (L - 1);
       Cx<float>* zz = sm + q * LP + padi(k);
@@ -559,50 +610,94 @@ __global__ void __launch_bounds__(Reg<LOGL, P>::THREADS) k_dst32(PassArgs A) {
         lA = lam_h2<float>(2, A.order, kh2, sk, A.s32[min(bA, nm1)], 0.f);
         lB = lam_h2<float>(2, A.order, kh2, sk, A.s32[bB], 0.f);
       } else {
-        lA = lam_h2<float>(3, A.order, kh2, sk, sa, A.s32[min(bA, nm1)]);
-        lB = lam_h2<float>(3, A.order, kh2, sk, sa, A.s32[bB]);
+        lA = lam_h2<float>(3, A.order, kh2, sk, sa3, A.s32[min(bA, nm1)]);
+        lB = lam_h2<float>(3, A.order, kh2, sk, sa3, A.s32[bB]);
       }
       const Cx<float> Z = *zz;
-      *zz = {(g / lA) * (-0.5f * Z.y), (g / lB) * (0.5f * Z.x)};
+      *zz = {__fdividef(g, lA) * (-0.5f * Z.y), __fdividef(g, lB) * (0.5f * Z.x)};
     }
     __syncthreads();
     reg_fft<LOGL>(s, tid, tw);
   }
-  // S_k = -Im(Z_k)/2 (line 2q), Re(Z_k)/2 (line 2q+1)
+  // S_k = -Im(Z_k)/2 (line 2q), Re(Z_k)/2 (line 2q+1); in the accumulating
+  // modes all old values are loaded before the first store
   float dmx = 0.f, umx = 0.f;
-  for (int t = threadIdx.x; t < nval; t += F::THREADS) {
-    int j, q;
-    if (contig) {
-      j = 1 + t % nm1;
-      q = t / nm1;
-    } else {
-      q = t % (2 * P);
-      j = 1 + t / (2 * P);
+  {
+    float2 vals[NIT];
+    int offs[NIT];
+    bool hasB[NIT];
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+      const int t = threadIdx.x + it * F::THREADS;
+      int j, q;
+      coords(t < nitem ? t : 0, j, q);
+      const int bA = b0 + 2 * q;
+      offs[it] = (t < nitem && bA <= nm1) ? abase + bA * sb + j * es : -1;
+      hasB[it] = bA + 1 <= nm1;
+      const Cx<float> Z = sm[q * LP + padi(j)];
+      vals[it] = {-0.5f * Z.y, 0.5f * Z.x};
     }
-    const int b = b0 + q;
-    if (b > nm1) continue;
-    const Cx<float> Z = sm[(q >> 1) * LP + padi(j)];
-    const float v = (q & 1) ? 0.5f * Z.x : -0.5f * Z.y;
-    const long long off = abase + (long long)b * A.sb + (long long)j * A.es;
     if (A.dstfix) {
-      const long long nv = A.dstfix[off] + __float2ll_rn((v * A.fixf[0]) * A.fixf[1]);
-      A.dstfix[off] = nv;
-      dmx = fmaxf(dmx, fabsf(v));
-      umx = fmaxf(umx, fabsf((__ll2float_rn(nv) * A.fixf[2]) * A.fixf[3]));
+      long long oldA[NIT], oldB[NIT];
+#pragma unroll
+      for (int it = 0; it < NIT; ++it) {
+        oldA[it] = offs[it] >= 0 ? A.dstfix[offs[it]] : 0ll;
+        oldB[it] = (offs[it] >= 0 && hasB[it]) ? A.dstfix[offs[it] + sb] : 0ll;
+      }
+      const float fa = A.fixf[0], fb = A.fixf[1], ia = A.fixf[2], ib = A.fixf[3];
+#pragma unroll
+      for (int it = 0; it < NIT; ++it) {
+        if (offs[it] >= 0) {
+          const long long nA = oldA[it] + f2ll((vals[it].x * fa) * fb);
+          A.dstfix[offs[it]] = nA;
+          dmx = fmaxf(dmx, fabsf(vals[it].x));
+          umx = fmaxf(umx, fabsf((ll2f(nA) * ia) * ib));
+          if (hasB[it]) {
+            const long long nB = oldB[it] + f2ll((vals[it].y * fa) * fb);
+            A.dstfix[offs[it] + sb] = nB;
+            dmx = fmaxf(dmx, fabsf(vals[it].y));
+            umx = fmaxf(umx, fabsf((ll2f(nB) * ia) * ib));
+          }
+        }
+      }
     } else if (A.dst64) {
       double* o = static_cast<double*>(A.dst);
-      const double nv = A.accumulate ? o[off] + (double)v : (double)v;
-      o[off] = nv;
-      if (A.corr_max) {
-        dmx = fmaxf(dmx, fabsf(v));
-        umx = fmaxf(umx, fabsf((float)nv));
+      double oldA[NIT], oldB[NIT];
+#pragma unroll
+      for (int it = 0; it < NIT; ++it) {
+        const bool acc = offs[it] >= 0 && A.accumulate;
+        oldA[it] = acc ? o[offs[it]] : 0.0;
+        oldB[it] = (acc && hasB[it]) ? o[offs[it] + sb] : 0.0;
+      }
+#pragma unroll
+      for (int it = 0; it < NIT; ++it) {
+        if (offs[it] >= 0) {
+          const double nA = oldA[it] + (double)vals[it].x;
+          o[offs[it]] = nA;
+          dmx = fmaxf(dmx, fabsf(vals[it].x));
+          umx = fmaxf(umx, fabsf((float)nA));
+          if (hasB[it]) {
+            const double nB = oldB[it] + (double)vals[it].y;
+            o[offs[it] + sb] = nB;
+            dmx = fmaxf(dmx, fabsf(vals[it].y));
+            umx = fmaxf(umx, fabsf((float)nB));
+          }
+        }
       }
     } else {
-      static_cast<float*>(A.dst)[off] = v;
-      if (A.corr_max) {
-        dmx = fmaxf(dmx, fabsf(v));
-        umx = dmx;
+      float* o = static_cast<float*>(A.dst);
+#pragma unroll
+      for (int it = 0; it < NIT; ++it) {
+        if (offs[it] >= 0) {
+          o[offs[it]] = vals[it].x;
+          dmx = fmaxf(dmx, fabsf(vals[it].x));
+          if (hasB[it]) {
+            o[offs[it] + sb] = vals[it].y;
+            dmx = fmaxf(dmx, fabsf(vals[it].y));
+          }
+        }
       }
+      umx = dmx;
     }
   }
   if (A.corr_max) {
@@ -614,6 +709,56 @@ __global__ void __launch_bounds__(Reg<LOGL, P>::THREADS) k_dst32(PassArgs A) {
       if (dmx > 0.f) atomicMax(A.corr_max, (unsigned long long)__double_as_longlong((double)dmx));
       if (umx > 0.f) atomicMax(A.corr_max + 1, (unsigned long long)__double_as_longlong((double)umx));
     }
+  }
+}
+
+template <int LOGL, int P>
+__global__ void __launch_bounds__(Reg<LOGL, P>::THREADS) k_dst32(PassArgs A) {
+  if (A.skip && *A.skip) return;
+  extern __shared__ unsigned char smraw[];
+  dst32_body<LOGL, P>(A, blockIdx.x, blockIdx.y, reinterpret_cast<Cx<float>*>(smraw));
+}
+
+// Each length compiled on its own (not inlined into the dispatching kernel, so
+// that the register allocation of one length does not spill another).
+template <int LOGL>
+__device__ __noinline__ void dst32_item(const PassArgs& A, int bx, int by, Cx<float>* sm) {
+  dst32_body<LOGL, reg_pairs(LOGL)>(A, bx, by, sm);
+}
+
+// Persistent FP32 pass over many independent grids: every transform length
+// up to L = 2048 uses 128 threads and 17.4 KB per work item (P L / 16 = 128
+// with P = reg_pairs(LOGL)), so one kernel takes the work items of all
+// instances (item -> instance by binary search in `start`) and dispatches on
+// the instance's LOGL.
+__global__ void __launch_bounds__(128) k_dst32_batched(const PassArgs* __restrict__ args,
+                                                       const int* __restrict__ start, int ninst) {
+  extern __shared__ unsigned char smraw[];
+  Cx<float>* sm = reinterpret_cast<Cx<float>*>(smraw);
+  const int total = start[ninst];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    int lo = 0, hi = ninst;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (start[mid] <= item) lo = mid; else hi = mid;
+    }
+    const PassArgs& A = args[lo];
+    if (A.skip && *A.skip) continue;
+    const int local = item - start[lo];
+    const int p = reg_pairs(A.logL);
+    const int nbx = (A.n / 2 + p - 1) / p;
+    const int bx = local % nbx, by = local / nbx;
+    switch (A.logL) {
+      case 4: dst32_item<4>(A, bx, by, sm); break;
+      case 5: dst32_item<5>(A, bx, by, sm); break;
+      case 6: dst32_item<6>(A, bx, by, sm); break;
+      case 7: dst32_item<7>(A, bx, by, sm); break;
+      case 8: dst32_item<8>(A, bx, by, sm); break;
+      case 9: dst32_item<9>(A, bx, by, sm); break;
+      case 10: dst32_item<10>(A, bx, by, sm); break;
+      default: dst32_item<11>(A, bx, by, sm); break;
+    }
+    __syncthreads();
   }
 }
 
@@ -667,7 +812,7 @@ __global__ void k_fix0(long long tot, const float* __restrict__ u0, const double
   const int n1 = g.n + 1;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
        t += (long long)gridDim.x * blockDim.x) {
-    ufix[t] = __float2ll_rn((u0[t] * fa) * fb);
+    ufix[t] = f2ll((u0[t] * fa) * fb);
     long long r = t;
     bool interior = true;
     for (int k = 0; k < g.d; ++k) {
@@ -683,6 +828,24 @@ struct FixStencil {
   int w0, w1, w2, w3, kA, kB;
 };
 
+// S u of the integer stencil and the kappa combination kA u_P + kB e, with
+// the weights of the three operators as compile-time shifts and adds (64-bit
+// integer multiplies go to the FP64 pipe)
+__device__ __forceinline__ long long fix_apply(const FixStencil& W, long long c, long long e, long long k2,
+                                               long long k3, long long& m) {
+  if (W.w0 == -20) {          // 2D 4th order: -20 c + 4 e + k2; kappa: 8 c + e
+    m = (c << 3) + e;
+    return ((e - ((c << 2) + c)) << 2) + k2;
+  }
+  if (W.w0 == -200) {         // 3D 4th order: -200 c + 20 e + 6 k2 + k3; kappa: 6 c + e
+    m = ((c << 2) + (c << 1)) + e;
+    const long long t = ((e << 2) + e) - ((c << 5) + (c << 4) + (c << 1));   // 5 e - 50 c
+    return (t << 2) + ((k2 << 2) + (k2 << 1)) + k3;
+  }
+  m = c;                      // 2nd order: -2 d c + e; kappa: c
+  return W.w0 == -4 ? e - (c << 2) : e - ((c << 2) + (c << 1));
+}
+
 // r32 = (R_fix - S u_fix + round(kc (kA u + kB sum_edges))) 2^-F / (mult h^2)
 __global__ void k_res_fix(Grid g, FixStencil W, const long long* __restrict__ R, const long long* __restrict__ u,
                           const double* __restrict__ fixd, const float* __restrict__ fixf,
@@ -693,7 +856,8 @@ __global__ void k_res_fix(Grid g, FixStencil W, const long long* __restrict__ R,
   const int i1 = blockIdx.y;
   const int i0 = blockIdx.z;
   if (j > g.n) return;
-  const long long t = g.d == 2 ? (long long)i1 * n1 + j : ((long long)i0 * n1 + i1) * n1 + j;
+  // 32-bit offsets: grids of up to 1025^3 nodes
+  const int t = g.d == 2 ? i1 * n1 + j : (i0 * n1 + i1) * n1 + j;
   const bool interior = j >= 1 && j < g.n && i1 >= 1 && i1 < g.n && (g.d == 2 || (i0 >= 1 && i0 < g.n));
   if (!interior) {
     r32[t] = 0.f;
@@ -706,7 +870,7 @@ __global__ void k_res_fix(Grid g, FixStencil W, const long long* __restrict__ R,
     e = (up[-1] + up[1]) + (up[-n1] + up[n1]);
     if (W.w2) k2 = (up[-n1 - 1] + up[-n1 + 1]) + (up[n1 - 1] + up[n1 + 1]);
   } else {
-    const long long s = (long long)n1 * n1;
+    const int s = n1 * n1;
     e = (up[-1] + up[1]) + (up[-n1] + up[n1]) + (up[-s] + up[s]);
     if (W.w2)
       k2 = (up[-n1 - 1] + up[-n1 + 1]) + (up[n1 - 1] + up[n1 + 1]) + (up[-s - 1] + up[-s + 1]) +
@@ -715,10 +879,11 @@ __global__ void k_res_fix(Grid g, FixStencil W, const long long* __restrict__ R,
       k3 = (up[-s - n1 - 1] + up[-s - n1 + 1]) + (up[-s + n1 - 1] + up[-s + n1 + 1]) +
            (up[s - n1 - 1] + up[s - n1 + 1]) + (up[s + n1 - 1] + up[s + n1 + 1]);
   }
-  long long r = R[t] - ((long long)W.w0 * c + (long long)W.w1 * e + (long long)W.w2 * k2 + (long long)W.w3 * k3);
+  long long m;
+  long long r = R[t] - fix_apply(W, c, e, k2, k3, m);
   const double kc = fixd[2];
-  if (kc != 0.0) r += __double2ll_rn(kc * (double)((long long)W.kA * c + (long long)W.kB * e));
-  r32[t] = (__ll2float_rn(r) * fixf[2]) * fixf[4];
+  if (kc != 0.0) r += __double2ll_rn(kc * (double)m);
+  r32[t] = (ll2f(r) * fixf[2]) * fixf[4];
 }
 
 __global__ void k_unfix(long long tot, const long long* __restrict__ ufix, const double* __restrict__ fixd,
@@ -814,6 +979,7 @@ PassPlan plan_passes(kfbi_problem* p, const void* src, int src64, double* dst, i
   A.n = n;
   A.logL = B->logL;
   A.tw = tw;
+  A.twst = B->twst;
   A.cosv = B->cosv;
   A.s32 = B->s32;
   A.scale64 = B->scale64;
@@ -915,6 +1081,11 @@ kfbi_status box_create(kfbi_problem* p) {
   KFBI_CUDA(p, dalloc(&B->cosv, n + 1));
   KFBI_CUDA(p, cudaMemcpy(B->tw64, tw.data(), sizeof(double) * 2 * B->L, cudaMemcpyHostToDevice));
   KFBI_CUDA(p, cudaMemcpy(B->tw32, tw32.data(), sizeof(float) * 2 * B->L, cudaMemcpyHostToDevice));
+  {
+    const std::vector<float> ts = stage_twiddles(B->logL);
+    KFBI_CUDA(p, dalloc(&B->twst, ts.size()));
+    KFBI_CUDA(p, cudaMemcpy(B->twst, ts.data(), sizeof(float) * ts.size(), cudaMemcpyHostToDevice));
+  }
   KFBI_CUDA(p, cudaMemcpy(B->cosv, cs.data(), sizeof(double) * (n + 1), cudaMemcpyHostToDevice));
   const long long nodes = g.nodes();
   if (p->cfg.precision == KFBI_MIXED) {
@@ -993,6 +1164,7 @@ void box_destroy(kfbi_problem* p) {
   if (!B) return;
   cudaFree(B->tw64);
   cudaFree(B->tw32);
+  cudaFree(B->twst);
   cudaFree(B->cosv);
   cudaFree(B->s64);
   cudaFree(B->s32);
@@ -1245,23 +1417,29 @@ extern "C" kfbi_status kfbi_box_solve_noalloc(int dim, int n, double lo, double 
 }
 
 // ---------------------------------------------------------------------------
-// Batched mixed-precision box solve: many independent grids (different N) in
-// one launch per pass (persistent CTAs over all instances' line pairs) and one
-// launch per residual / check, with per-instance convergence flags.
+// Batched mixed-precision box solve: many independent grids (different N),
+// the same steps as the single solve (FP32 solve, fixed-point scale, exact
+// residual, FP32 corrections), each step one launch over all instances: the
+// passes by persistent CTAs over all instances' line pairs, the grid kernels
+// over all instances' rows, with per-instance convergence flags.
 // ---------------------------------------------------------------------------
 namespace kfbi {
 namespace {
 
-struct ResDesc {
+struct BoxDesc {
   Grid g;
-  int order;
-  const double* c;
-  const double* R;
-  double* u;
-  double* r;
+  FixStencil W;
+  double multh2, kc, tol;
+  const double* R;         // right-hand side (FP64 grid)
+  double* u;               // solution (FP64 grid)
+  const float* u0;         // first FP32 solve (the work grid)
+  long long* ufix;
+  long long* rfix;
+  float* r32;
+  double* fixd;
+  float* fixf;
   unsigned long long* nrm;
   int* conv;
-  double tol;
 };
 
 __device__ __forceinline__ int find_inst(const int* start, int ninst, int item) {
@@ -1273,90 +1451,115 @@ __device__ __forceinline__ int find_inst(const int* start, int ninst, int item) 
   return lo;
 }
 
-// one grid row (last axis) per work item
-__global__ void k_residual_batched(const ResDesc* __restrict__ rd, const int* __restrict__ rstart, int ninst) {
-  const int total = rstart[ninst];
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    const int inst = find_inst(rstart, ninst, item);
-    const ResDesc& D = rd[inst];
-    if (*D.conv) continue;
-    const Grid g = D.g;
-    const int n1 = g.n + 1;
-    const int row = item - rstart[inst];
-    const int i1 = row % n1, i0 = row / n1;   // 2D: i0 = 0
-    double mx = 0.0;
-    for (int j = threadIdx.x; j <= g.n; j += blockDim.x) {
-      const long long t = g.d == 2 ? (long long)i1 * n1 + j : ((long long)i0 * n1 + i1) * n1 + j;
-      const bool interior = j >= 1 && j < g.n && i1 >= 1 && i1 < g.n && (g.d == 2 || (i0 >= 1 && i0 < g.n));
-      if (!interior) {
-        D.r[t] = 0.0;
-        continue;
-      }
-      const double* up = D.u + t;
-      const double* c = D.c;
-      double acc;
-      if (g.d == 2) {
-        double s1 = (up[-1] + up[1]) + (up[-n1] + up[n1]);
-        acc = c[0] * up[0] + c[1] * s1;
-        if (D.order == 4) acc += c[2] * ((up[-n1 - 1] + up[-n1 + 1]) + (up[n1 - 1] + up[n1 + 1]));
-      } else {
-        const long long s = (long long)n1 * n1;
-        double f = (up[-1] + up[1]) + (up[-n1] + up[n1]) + (up[-s] + up[s]);
-        acc = c[0] * up[0] + c[1] * f;
-        if (D.order == 4) {
-          double e = (up[-n1 - 1] + up[-n1 + 1]) + (up[n1 - 1] + up[n1 + 1]) + (up[-s - 1] + up[-s + 1]) +
-                     (up[s - 1] + up[s + 1]) + (up[-s - n1] + up[-s + n1]) + (up[s - n1] + up[s + n1]);
-          double k = (up[-s - n1 - 1] + up[-s - n1 + 1]) + (up[-s + n1 - 1] + up[-s + n1 + 1]) +
-                     (up[s - n1 - 1] + up[s - n1 + 1]) + (up[s + n1 - 1] + up[s + n1 + 1]);
-          acc += c[2] * e + c[3] * k;
-        }
-      }
-      const double v = D.R[t] - acc;
-      D.r[t] = v;
-      mx = fmax(mx, fabs(v));
-    }
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0 && mx > 0.0)
-      atomicMax(D.nrm + 1, (unsigned long long)__double_as_longlong(mx));
-  }
-}
-
-__global__ void k_check_batched(const ResDesc* __restrict__ rd, int ninst) {
+// instance state reset; instances flagged in `done` (outer iteration
+// finished) start as converged, so every pass and residual skips them
+__global__ void k_zero_batched(const BoxDesc* __restrict__ D, int ninst, const int* __restrict__ done) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ninst) return;
-  const ResDesc& D = rd[i];
-  unsigned long long* nrm = D.nrm;
-  if (*D.conv) return;
-  double dm = __longlong_as_double((long long)nrm[3]);
-  double um = __longlong_as_double((long long)nrm[4]);
+  for (int k = 0; k < 6; ++k) D[i].nrm[k] = 0ull;
+  *D[i].conv = done ? done[i] : 0;
+}
+
+__global__ void k_check_batched(const BoxDesc* __restrict__ D, int ninst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ninst) return;
+  unsigned long long* nrm = D[i].nrm;
+  if (*D[i].conv) return;
+  const double dm = __longlong_as_double((long long)nrm[3]);
+  const double um = __longlong_as_double((long long)nrm[4]);
   nrm[2] = nrm[3];
   nrm[5] = nrm[4];
-  if (dm <= D.tol * um) *D.conv = 1;
+  if (dm <= D[i].tol * um) *D[i].conv = 1;
   nrm[3] = 0ull;
   nrm[4] = 0ull;
 }
 
-// Reset the refinement state; instances flagged in `done` (outer iteration
-// finished) start as converged, so every pass and residual skips them.
-__global__ void k_zero_batched(const ResDesc* __restrict__ rd, int ninst, const int* __restrict__ done) {
+__global__ void k_fix_scale_batched(const BoxDesc* __restrict__ D, int ninst) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ninst) return;
-  for (int k = 0; k < 6; ++k) rd[i].nrm[k] = 0ull;
-  *rd[i].conv = done ? done[i] : 0;
+  const double um = __longlong_as_double((long long)D[i].nrm[5]);
+  int F = 0;
+  if (um > 0.0) F = 52 - (int)ceil(log2(um));
+  F = max(-120, min(F, 240));
+  const int Fa = F / 2, Fb = F - Fa;
+  double* fd = D[i].fixd;
+  float* ff = D[i].fixf;
+  fd[0] = ldexp(D[i].multh2, F);
+  fd[1] = ldexp(1.0, -F);
+  fd[2] = D[i].kc;
+  ff[0] = ldexpf(1.f, Fa);
+  ff[1] = ldexpf(1.f, Fb);
+  ff[2] = ldexpf(1.f, -Fa);
+  ff[3] = ldexpf(1.f, -Fb);
+  ff[4] = (float)(ldexp(1.0, -Fb) / D[i].multh2);
+}
+
+// grid kernels over all instances' rows (one row of the last axis per item);
+// mode 0: u_fix = round(u0 2^F), R_fix = round(mult h^2 R 2^F);
+// mode 1: exact residual -> r32 (skips converged instances);
+// mode 2: u = u_fix 2^-F.
+__global__ void k_rows_batched(const BoxDesc* __restrict__ D, const int* __restrict__ rstart, int ninst, int mode) {
+  const int total = rstart[ninst];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int inst = find_inst(rstart, ninst, item);
+    const BoxDesc& B = D[inst];
+    if (mode == 1 && *B.conv) continue;
+    const Grid g = B.g;
+    const int n1 = g.n + 1;
+    const int row = item - rstart[inst];
+    const int i1 = row % n1, i0 = row / n1;   // 2D: i0 = 0
+    const bool row_in = i1 >= 1 && i1 < g.n && (g.d == 2 || (i0 >= 1 && i0 < g.n));
+    const int base = g.d == 2 ? i1 * n1 : (i0 * n1 + i1) * n1;
+    for (int j = threadIdx.x; j <= g.n; j += blockDim.x) {
+      const int t = base + j;
+      const bool interior = row_in && j >= 1 && j < g.n;
+      if (mode == 0) {
+        const float* ff = B.fixf;
+        B.ufix[t] = f2ll((B.u0[t] * ff[0]) * ff[1]);
+        B.rfix[t] = interior ? __double2ll_rn(B.R[t] * B.fixd[0]) : 0ll;
+      } else if (mode == 2) {
+        B.u[t] = __ll2double_rn(B.ufix[t]) * B.fixd[1];
+      } else {
+        if (!interior) {
+          B.r32[t] = 0.f;
+          continue;
+        }
+        const long long* up = B.ufix + t;
+        const FixStencil W = B.W;
+        const long long c = up[0];
+        long long e, k2 = 0, k3 = 0;
+        if (g.d == 2) {
+          e = (up[-1] + up[1]) + (up[-n1] + up[n1]);
+          if (W.w2) k2 = (up[-n1 - 1] + up[-n1 + 1]) + (up[n1 - 1] + up[n1 + 1]);
+        } else {
+          const int s = n1 * n1;
+          e = (up[-1] + up[1]) + (up[-n1] + up[n1]) + (up[-s] + up[s]);
+          if (W.w2)
+            k2 = (up[-n1 - 1] + up[-n1 + 1]) + (up[n1 - 1] + up[n1 + 1]) + (up[-s - 1] + up[-s + 1]) +
+                 (up[s - 1] + up[s + 1]) + (up[-s - n1] + up[-s + n1]) + (up[s - n1] + up[s + n1]);
+          if (W.w3)
+            k3 = (up[-s - n1 - 1] + up[-s - n1 + 1]) + (up[-s + n1 - 1] + up[-s + n1 + 1]) +
+                 (up[s - n1 - 1] + up[s - n1 + 1]) + (up[s + n1 - 1] + up[s + n1 + 1]);
+        }
+        long long m;
+        long long r = B.rfix[t] - fix_apply(W, c, e, k2, k3, m);
+        const double kc = B.fixd[2];
+        if (kc != 0.0) r += __double2ll_rn(kc * (double)m);
+        B.r32[t] = (ll2f(r) * B.fixf[2]) * B.fixf[4];
+      }
+    }
+  }
 }
 
 }  // namespace
 
 struct BatchBox {
-  int ninst = 0, npass = 0, steps = 4;
-  PassArgs* dargs = nullptr;   // [npass + 1][ninst]: pass 0 from R, pass 0 from r, passes 1..
-  int* dstart = nullptr;       // [ninst + 1] line-pair work items
-  ResDesc* dres = nullptr;     // [ninst]
-  int* drstart = nullptr;      // [ninst + 1] residual rows
-  std::vector<double*> u, rhs;
-  std::vector<size_t> ubytes;
-  size_t smem = 0;
-  int grid = 0;
+  int ninst = 0, npass = 0, steps = 3;
+  PassArgs* dargs = nullptr;   // [2 npass][ninst]: step 0 passes, then refinement-step passes
+  int* dstart = nullptr;       // [ninst + 1] pass work items
+  BoxDesc* dbox = nullptr;     // [ninst]
+  int* drstart = nullptr;      // [ninst + 1] grid rows
+  int grid = 0, rgrid = 0;
 };
 
 kfbi_status batch_box_create(kfbi_problem* p0, kfbi_problem* const* ps, int ninst,
@@ -1365,50 +1568,64 @@ kfbi_status batch_box_create(kfbi_problem* p0, kfbi_problem* const* ps, int nins
   *out = bb;
   bb->ninst = ninst;
   const int d = ps[0]->g.d;
-  std::vector<PassArgs> args;
+  std::vector<PassPlan> plan0(ninst), plank(ninst);
   std::vector<int> start(ninst + 1, 0), rstart(ninst + 1, 0);
-  std::vector<ResDesc> res(ninst);
-  std::vector<PassPlan> plans(ninst), plans_r(ninst);
-  int maxn = 0;
+  std::vector<BoxDesc> box(ninst);
   for (int i = 0; i < ninst; ++i) {
     kfbi_problem* p = ps[i];
-    if (p->g.d != d || p->cfg.precision != KFBI_MIXED || p->box == nullptr || p->mg != nullptr)
+    if (p->g.d != d || p->cfg.precision != KFBI_MIXED || p->box == nullptr || p->mg != nullptr ||
+        p->box->logL > 11)
       return fail(p0, KFBI_ERR_UNSUPPORTED,
-                  "batched solves need mixed-precision DST problems of one dimension");
+                  "batched solves need mixed-precision DST problems of one dimension with N <= 1024");
     BoxSolver* B = p->box;
-    plans[i] = plan_passes<float>(p, rhs[i], 1, p->ugrid, 1, B->conv, B->nrm + 3);
-    plans_r[i] = plan_passes<float>(p, B->res, 1, p->ugrid, 1, B->conv, B->nrm + 3);
-    start[i + 1] = start[i] + plans[i].npairs * plans[i].na;
+    float* r32 = reinterpret_cast<float*>(B->res);
+    plan0[i] = plan_passes<float>(p, rhs[i], 1, p->ugrid, 0, B->conv, B->nrm + 3);
+    {
+      PassArgs& last = plan0[i].args[plan0[i].npass - 1];
+      last.dst = B->work32;
+      last.dst64 = 0;
+      last.accumulate = 0;
+      last.corr_max = B->nrm + 3;
+    }
+    plank[i] = plan_passes<float>(p, r32, 0, p->ugrid, 0, B->conv, B->nrm + 3);
+    {
+      PassArgs& last = plank[i].args[plank[i].npass - 1];
+      last.dst = nullptr;
+      last.dst64 = 0;
+      last.accumulate = 1;
+      last.dstfix = B->ufix;
+      last.fixf = B->fixf;
+      last.corr_max = B->nrm + 3;
+    }
+    const int pp = reg_pairs(B->logL);
+    start[i + 1] = start[i] + ((plan0[i].npairs + pp - 1) / pp) * plan0[i].na;
     const int n1 = p->g.n + 1;
     rstart[i + 1] = rstart[i] + (d == 2 ? n1 : n1 * n1);
-    res[i] = ResDesc{p->g, p->cfg.order, p->stencil_dev, rhs[i], p->ugrid, B->res, B->nrm, B->conv, B->tol};
-    maxn = std::max(maxn, p->g.n);
-    bb->steps = std::max(bb->steps, B->refine_steps);
-    bb->u.push_back(p->ugrid);
-    bb->rhs.push_back(rhs[i]);
-    bb->ubytes.push_back(sizeof(double) * (size_t)p->g.nodes());
+    box[i] = BoxDesc{p->g, FixStencil{B->w[0], B->w[1], B->w[2], B->w[3], B->kA, B->kB}, B->multh2, B->kc, B->tol,
+                     rhs[i], p->ugrid, B->work32, B->ufix, B->rfix, r32, B->fixd, B->fixf, B->nrm, B->conv};
   }
-  bb->npass = plans[0].npass;
-  for (int v = 0; v <= bb->npass; ++v)
+  bb->steps = 0;
+  for (int i = 0; i < ninst; ++i) bb->steps = std::max(bb->steps, ps[i]->box->refine_steps);
+  bb->npass = plan0[0].npass;
+  std::vector<PassArgs> args;
+  for (int v = 0; v < 2 * bb->npass; ++v)
     for (int i = 0; i < ninst; ++i)
-      args.push_back(v == 0 ? plans[i].args[0] : v == 1 ? plans_r[i].args[0] : plans[i].args[v - 1]);
+      args.push_back(v < bb->npass ? plan0[i].args[v] : plank[i].args[v - bb->npass]);
   KFBI_CUDA(p0, dalloc(&bb->dargs, args.size()));
   KFBI_CUDA(p0, dalloc(&bb->dstart, ninst + 1));
-  KFBI_CUDA(p0, dalloc(&bb->dres, ninst));
+  KFBI_CUDA(p0, dalloc(&bb->dbox, ninst));
   KFBI_CUDA(p0, dalloc(&bb->drstart, ninst + 1));
   KFBI_CUDA(p0, cudaMemcpy(bb->dargs, args.data(), sizeof(PassArgs) * args.size(), cudaMemcpyHostToDevice));
   KFBI_CUDA(p0, cudaMemcpy(bb->dstart, start.data(), sizeof(int) * (ninst + 1), cudaMemcpyHostToDevice));
-  KFBI_CUDA(p0, cudaMemcpy(bb->dres, res.data(), sizeof(ResDesc) * ninst, cudaMemcpyHostToDevice));
+  KFBI_CUDA(p0, cudaMemcpy(bb->dbox, box.data(), sizeof(BoxDesc) * ninst, cudaMemcpyHostToDevice));
   KFBI_CUDA(p0, cudaMemcpy(bb->drstart, rstart.data(), sizeof(int) * (ninst + 1), cudaMemcpyHostToDevice));
-  bb->smem = sizeof(Cx<float>) * (size_t)(2 * maxn) * 2;
-  int dev = 0, optin = 0, sms = 0;
+  int dev = 0, sms = 0;
   KFBI_CUDA(p0, cudaGetDevice(&dev));
-  KFBI_CUDA(p0, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   KFBI_CUDA(p0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  KFBI_CUDA(p0, cudaFuncSetAttribute(k_dst_pass_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   int per_sm = 0;
-  KFBI_CUDA(p0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dst_pass_batched<float>, 256, bb->smem));
+  KFBI_CUDA(p0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dst32_batched, 128, Reg<11, 1>::SMEM));
   bb->grid = sms * std::max(1, per_sm);
+  bb->rgrid = sms * 8;
   return KFBI_OK;
 }
 
@@ -1416,27 +1633,32 @@ void batch_box_destroy(BatchBox* bb) {
   if (!bb) return;
   cudaFree(bb->dargs);
   cudaFree(bb->dstart);
-  cudaFree(bb->dres);
+  cudaFree(bb->dbox);
   cudaFree(bb->drstart);
   delete bb;
 }
 
-// All instances not flagged in `done` (may be null): u_i = A_i^{-1} rhs_i by
-// FP32 transforms with FP64 refinement.
+// All instances not flagged in `done` (may be null): u_i = A_i^{-1} rhs_i by the
+// mixed-precision steps of box_solve, every step one launch over all instances.
 kfbi_status batch_box_solve(kfbi_problem* p0, BatchBox* bb, const int* done, cudaStream_t st) {
   const int ni = bb->ninst;
-  for (int i = 0; i < ni; ++i)   // grid sizes differ: one memset per instance
-    KFBI_CUDA(p0, cudaMemsetAsync(bb->u[i], 0, bb->ubytes[i], st));
-  KFBI_LAUNCH(p0, KFBI_KC_RESIDUAL, k_zero_batched<<<div_up(ni, 128), 128, 0, st>>>(bb->dres, ni, done));
-  for (int it = 0; it < bb->steps; ++it) {
-    for (int v = 0; v < bb->npass; ++v) {
-      const PassArgs* a = bb->dargs + (size_t)(v == 0 ? (it == 0 ? 0 : 1) : v + 1) * ni;
-      KFBI_LAUNCH(p0, KFBI_KC_DST, k_dst_pass_batched<float><<<bb->grid, 256, bb->smem, st>>>(a, bb->dstart, ni));
-    }
-    KFBI_LAUNCH(p0, KFBI_KC_RESIDUAL, k_check_batched<<<div_up(ni, 128), 128, 0, st>>>(bb->dres, ni));
-    if (it + 1 < bb->steps)
-      KFBI_LAUNCH(p0, KFBI_KC_RESIDUAL, k_residual_batched<<<bb->grid, 128, 0, st>>>(bb->dres, bb->drstart, ni));
+  const size_t smem = Reg<11, 1>::SMEM;
+  const int cb = div_up(ni, 128);
+  KFBI_LAUNCH(p0, KFBI_KC_RESIDUAL, k_zero_batched<<<cb, 128, 0, st>>>(bb->dbox, ni, done));
+  for (int v = 0; v < bb->npass; ++v)
+    KFBI_LAUNCH(p0, KFBI_KC_DST, k_dst32_batched<<<bb->grid, 128, smem, st>>>(bb->dargs + (size_t)v * ni,
+                                                                               bb->dstart, ni));
+  KFBI_LAUNCH(p0, KFBI_KC_RESIDUAL, k_check_batched<<<cb, 128, 0, st>>>(bb->dbox, ni));
+  KFBI_LAUNCH(p0, KFBI_KC_RESIDUAL, k_fix_scale_batched<<<cb, 128, 0, st>>>(bb->dbox, ni));
+  KFBI_LAUNCH(p0, KFBI_KC_RESIDUAL, k_rows_batched<<<bb->rgrid, 128, 0, st>>>(bb->dbox, bb->drstart, ni, 0));
+  for (int it = 1; it < bb->steps; ++it) {
+    KFBI_LAUNCH(p0, KFBI_KC_RESIDUAL, k_rows_batched<<<bb->rgrid, 128, 0, st>>>(bb->dbox, bb->drstart, ni, 1));
+    for (int v = 0; v < bb->npass; ++v)
+      KFBI_LAUNCH(p0, KFBI_KC_DST, k_dst32_batched<<<bb->grid, 128, smem, st>>>(
+          bb->dargs + (size_t)(bb->npass + v) * ni, bb->dstart, ni));
+    KFBI_LAUNCH(p0, KFBI_KC_RESIDUAL, k_check_batched<<<cb, 128, 0, st>>>(bb->dbox, ni));
   }
+  KFBI_LAUNCH(p0, KFBI_KC_RESIDUAL, k_rows_batched<<<bb->rgrid, 128, 0, st>>>(bb->dbox, bb->drstart, ni, 2));
   KFBI_CUDA(p0, cudaGetLastError());
   return KFBI_OK;
 }

@@ -38,6 +38,7 @@ struct kfbi_mlp {
   float* scale = nullptr;
   double out_shift = 0.0, out_scale = 1.0;
   long long step = 0;
+  int train_lo = 0, train_hi = 0;  // parameters that Adam updates: [train_lo, train_hi)
   // per-row scratch
   int cap = 0;
   float* X = nullptr;     // normalised input [cap][n_in]
@@ -220,11 +221,11 @@ __global__ void k_round(int np, const float* __restrict__ theta, __nv_bfloat16* 
   if (t < np) wbf[t] = __float2bfloat16_rn(theta[t]);
 }
 
-__global__ void k_adam(int np, float* __restrict__ theta, const float* __restrict__ g, float* __restrict__ m,
+__global__ void k_adam(int lo, int hi, float* __restrict__ theta, const float* __restrict__ g, float* __restrict__ m,
                        float* __restrict__ v, float lr, float b1, float b2, float eps, float bc1, float bc2,
                        __nv_bfloat16* __restrict__ wbf) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= np) return;
+  const int t = lo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= hi) return;
   const float gt = g[t];
   const float mt = b1 * m[t] + (1.f - b1) * gt;
   const float vt = b2 * v[t] + (1.f - b2) * gt * gt;
@@ -374,6 +375,8 @@ kfbi_status kfbi_mlp_create(int n_in, int width, void* cuda_stream, kfbi_mlp** o
   m->ob3 = m->oW3 + width;
   m->oWL = m->ob3 + 1;
   m->nparam = m->oWL + n_in;
+  m->train_lo = 0;
+  m->train_hi = m->nparam;
   const size_t np = m->nparam;
   bool ok = dalloc(&m->theta, np) == cudaSuccess && dalloc(&m->grad, np) == cudaSuccess &&
             dalloc(&m->mom1, np) == cudaSuccess && dalloc(&m->mom2, np) == cudaSuccess &&
@@ -408,6 +411,18 @@ kfbi_status kfbi_mlp_set_params(kfbi_mlp* m, const float* params) {
   m->step = 0;
   k_round<<<div_up(m->nparam, 256), 256, 0, m->stream>>>(m->nparam, m->theta, m->wbf);
   MLP_CUDA(m, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_mlp_set_trainable(kfbi_mlp* m, int groups) {
+  if (!m || groups < 0 || groups > 3) return KFBI_ERR_ARG;
+  // the nonlinear branch [W1, b1, W2, b2, W3] precedes the linear part [b3, WL]
+  m->train_lo = (groups & 1) ? 0 : m->ob3;
+  m->train_hi = (groups & 2) ? m->nparam : m->ob3;
+  if (groups == 0) m->train_lo = m->train_hi = 0;
+  MLP_CUDA(m, cudaMemsetAsync(m->mom1, 0, sizeof(float) * m->nparam, m->stream));
+  MLP_CUDA(m, cudaMemsetAsync(m->mom2, 0, sizeof(float) * m->nparam, m->stream));
+  m->step = 0;
   return KFBI_OK;
 }
 
@@ -479,8 +494,10 @@ kfbi_status kfbi_mlp_adam(kfbi_mlp* m, float lr, float beta1, float beta2, float
   m->step += 1;
   const float bc1 = (float)(1.0 - std::pow((double)beta1, (double)m->step));
   const float bc2 = (float)(1.0 - std::pow((double)beta2, (double)m->step));
-  k_adam<<<div_up(m->nparam, 256), 256, 0, m->stream>>>(m->nparam, m->theta, m->grad, m->mom1, m->mom2, lr, beta1,
-                                                         beta2, eps, bc1, bc2, m->wbf);
+  const int cnt = m->train_hi - m->train_lo;
+  if (cnt <= 0) return KFBI_OK;
+  k_adam<<<div_up(cnt, 256), 256, 0, m->stream>>>(m->train_lo, m->train_hi, m->theta, m->grad, m->mom1, m->mom2,
+                                                   lr, beta1, beta2, eps, bc1, bc2, m->wbf);
   MLP_CUDA(m, cudaGetLastError());
   return KFBI_OK;
 }

@@ -99,6 +99,7 @@ SIGNATURES = {
     "kfbi_mlp_forward": [_P, _P, ctypes.c_int, _P],
     "kfbi_mlp_loss_grad": [_P, _P, _P, _P, ctypes.c_int, _P],
     "kfbi_mlp_adam": [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float],
+    "kfbi_mlp_set_trainable": [_P, ctypes.c_int],
     "kfbi_warm_start_features": [_P, ctypes.POINTER(Data), _P, _P, _P],
     "kfbi_warm_start": [_P, _P, ctypes.POINTER(Data), _P],
     "kfbi_box_solve_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -325,6 +326,13 @@ def kfbi_mlp_loss_grad(m, X, t, rows=None, loss=None, n=None):
     """Gradient over the rows `rows` (int32 device tensor) of X, t, or all rows."""
     count = int(rows.shape[0]) if rows is not None else int(X.shape[0] if n is None else n)
     _check_mlp(load().kfbi_mlp_loss_grad(m, _ptr(X), _ptr(t), _ptr(rows), count, _ptr(loss)), m)
+
+
+MLP_BRANCH, MLP_LINEAR = 1, 2
+
+
+def kfbi_mlp_set_trainable(m, groups):
+    _check_mlp(load().kfbi_mlp_set_trainable(m, groups), m)
 
 
 def kfbi_mlp_adam(m, lr, beta1=0.9, beta2=0.999, eps=1e-8):

@@ -72,9 +72,12 @@ class WarmStart:
         return np.concatenate(parts).astype(np.float32)
 
     def fit(self, ds: Dataset, epochs: int = 8, batch: int = 4096, lr: float = 1e-3,
-            lr_final: float = 1e-6):
-        """Normalise inputs and targets from the data set, then minibatch Adam
-        (learning rate decayed geometrically from lr to lr_final).  Returns the
+            lr_final: float = 1e-6, linear_epochs: int = 3, floor: float = 1e-7):
+        """Normalise inputs and targets from the data set, then minibatch Adam in
+        two phases: the linear part alone (b3, WL: a least-squares fit of the
+        density on the features), then, if its loss is above `floor`, the whole
+        network with the nonlinear branch starting from zero output.  Learning
+        rates decay geometrically to lr_final within each phase.  Returns the
         mean loss of each epoch (normalised target units)."""
         import torch
         n = ds.n
@@ -87,23 +90,33 @@ class WarmStart:
         kfbi.kfbi_mlp_set_affine(self.handle, mu, scale, tmu, tsd)
         tn = torch.from_numpy(((th - tmu) / tsd).astype(np.float32)).cuda()
         rng = np.random.default_rng(self.seed + 1)
-        steps = epochs * max(1, n // batch)
-        decay = (lr_final / lr) ** (1.0 / max(1, steps - 1))
         loss = torch.zeros(1, dtype=torch.float32, device="cuda")
-        hist = []
-        k = 0
         nbatch = max(1, n // batch)
-        for _ in range(epochs):
-            order = torch.from_numpy(rng.permutation(n).astype(np.int32)).cuda()
-            seen = []
-            for b in range(nbatch):
-                rows = order[b * batch:(b + 1) * batch]
-                kfbi.kfbi_mlp_loss_grad(self.handle, ds.X, tn, rows=rows, loss=loss)
-                kfbi.kfbi_mlp_adam(self.handle, lr * decay ** k)
-                k += 1
-                if b % 16 == 0 or b == nbatch - 1:   # sample the loss (a host read)
-                    seen.append(float(loss.item()))
-            hist.append(float(np.mean(seen)))
+        hist = []
+
+        def phase(groups, ne, lr0):
+            kfbi.kfbi_mlp_set_trainable(self.handle, groups)
+            steps = ne * nbatch
+            decay = (lr_final / lr0) ** (1.0 / max(1, steps - 1))
+            k = 0
+            for _ in range(ne):
+                order = torch.from_numpy(rng.permutation(n).astype(np.int32)).cuda()
+                seen = []
+                for b in range(nbatch):
+                    rows = order[b * batch:(b + 1) * batch]
+                    kfbi.kfbi_mlp_loss_grad(self.handle, ds.X, tn, rows=rows, loss=loss)
+                    kfbi.kfbi_mlp_adam(self.handle, lr0 * decay ** k)
+                    k += 1
+                    if b % 16 == 0 or b == nbatch - 1:   # sample the loss (a host read)
+                        seen.append(float(loss.item()))
+                hist.append(float(np.mean(seen)))
+
+        phase(kfbi.MLP_LINEAR, linear_epochs, 10.0 * lr)
+        self.linear_loss = hist[-1]
+        self.branch_trained = self.linear_loss > floor
+        if self.branch_trained:
+            phase(kfbi.MLP_BRANCH | kfbi.MLP_LINEAR, epochs, lr)
+        kfbi.kfbi_mlp_set_trainable(self.handle, kfbi.MLP_BRANCH | kfbi.MLP_LINEAR)
         return hist
 
     def predict(self, problem: "kfbi.Problem", data, x0):
