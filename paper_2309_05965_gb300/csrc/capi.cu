@@ -199,7 +199,7 @@ kfbi_status kfbi_create_problem(const kfbi_config* cfg, const kfbi_levelset* ls,
     fail(p, KFBI_ERR_CUDA, "out of device memory");
     return bail(KFBI_ERR_CUDA);
   }
-  if ((s = gmres_create(p, 100)) != KFBI_OK) return bail(s);
+  if ((s = gmres_create(p, kMaxKrylov)) != KFBI_OK) return bail(s);
   if (cudaStreamSynchronize(p->stream) != cudaSuccess) {
     fail(p, KFBI_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
     return bail(KFBI_ERR_CUDA);

@@ -255,6 +255,112 @@ __global__ void __launch_bounds__(kArnThreads) k_arnoldi_batched(const ArnDesc* 
 
 }  // namespace
 
+namespace {
+
+// ---- one GMRES iteration as a graph (moderate N_b) ----------------------------
+// CGS2 across many CTAs with the step index j on the device: the Arnoldi step
+// of one CTA is bound by that SM's FP64 rate (2 FMA/clk), so the projections
+// run on every SM and the Givens update on one CTA.
+constexpr int kCgsThreads = 256;
+
+// h[i] = V_i . V_{j+1} for i <= j (CTA i; CTAs beyond j exit)
+__global__ void __launch_bounds__(kCgsThreads) k_cgs_dots(const double* __restrict__ V, int nb,
+                                                          const int* __restrict__ jdev, double* __restrict__ h) {
+  const int j = jdev[0];
+  const int i = blockIdx.x;
+  if (i > j) return;
+  const double* v = V + (size_t)i * nb;
+  const double* w = V + (size_t)(j + 1) * nb;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < nb; k += kCgsThreads) s += v[k] * w[k];
+  s = warp_sum(s);
+  __shared__ double ws[kCgsThreads / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kCgsThreads / 32; ++q) t += ws[q];
+    h[i] = t;
+  }
+}
+
+// V_{j+1} -= sum_{i <= j} h[i] V_i; with part: the CTA's sum of squares of the result
+__global__ void __launch_bounds__(kCgsThreads) k_cgs_update(double* __restrict__ V, int nb,
+                                                            const int* __restrict__ jdev,
+                                                            const double* __restrict__ h,
+                                                            double* __restrict__ part) {
+  const int j = jdev[0];
+  __shared__ double hs[kMaxKrylov + 1];
+  for (int i = threadIdx.x; i <= j; i += kCgsThreads) hs[i] = h[i];
+  __syncthreads();
+  double* w = V + (size_t)(j + 1) * nb;
+  double acc = 0.0;
+  for (int k = blockIdx.x * kCgsThreads + threadIdx.x; k < nb; k += gridDim.x * kCgsThreads) {
+    double s = w[k];
+    for (int i = 0; i <= j; ++i) s -= hs[i] * V[(size_t)i * nb + k];
+    w[k] = s;
+    acc += s * s;
+  }
+  if (!part) return;
+  acc = warp_sum(acc);
+  __shared__ double ws[kCgsThreads / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kCgsThreads / 32; ++q) t += ws[q];
+    part[blockIdx.x] = t;
+  }
+}
+
+// Hessenberg column j = h1 + h2, h_{j+1,j} = |V_{j+1}| (from the partials, in a
+// fixed order), Givens update, res = |g_{j+1}|, scal = 1/h_{j+1,j}, j <- j + 1
+__global__ void k_cgs_finish(double* __restrict__ H, int ld, double* __restrict__ cs, double* __restrict__ sn,
+                             double* __restrict__ g, double* __restrict__ res, const double* __restrict__ h1,
+                             const double* __restrict__ h2, const double* __restrict__ part, int npart,
+                             int* __restrict__ jdev, double* __restrict__ scal) {
+  __shared__ double ws[32];
+  double s = 0.0;
+  for (int c = threadIdx.x; c < npart; c += blockDim.x) s += part[c];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double nn = 0.0;
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) nn += ws[q];
+  const int j = jdev[0];
+  double* col = H + (size_t)j * ld;
+  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+  const double hn = sqrt(nn);
+  col[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double rr = hypot(col[j], col[j + 1]);
+  cs[j] = col[j] / rr;
+  sn[j] = col[j + 1] / rr;
+  col[j] = rr;
+  col[j + 1] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  res[0] = fabs(g[j + 1]);
+  scal[0] = 1.0 / hn;
+  jdev[0] = j + 1;
+}
+
+// V_j *= scal (j already advanced)
+__global__ void k_cgs_normalize(double* __restrict__ V, int nb, const int* __restrict__ jdev,
+                                const double* __restrict__ scal) {
+  const int j = jdev[0];
+  const double f = scal[0];
+  double* w = V + (size_t)j * nb;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) w[k] *= f;
+}
+
+}  // namespace
+
 kfbi_status batch_arnoldi_copy_in(kfbi_problem* p0, const ArnDesc* d, const int* jdev, const int* done,
                                   int ninst, int maxnb, cudaStream_t st) {
   KFBI_LAUNCH(p0, KFBI_KC_GMRES, k_copy_in_batched<<<dim3(div_up(maxnb, 256), ninst), 256, 0, st>>>(d, jdev, done));
@@ -316,6 +422,10 @@ kfbi_status gmres_create(kfbi_problem* p, int m) {
   KFBI_CUDA(p, dalloc(&G.scal, 8));
   KFBI_CUDA(p, dalloc(&G.hcol, 2 * (m + 1)));
   KFBI_CUDA(p, cudaMallocHost(reinterpret_cast<void**>(&G.host_res), 4 * sizeof(double)));
+  KFBI_CUDA(p, dalloc(&G.jdev, 2));
+  KFBI_CUDA(p, dalloc(&G.h1, m + 1));
+  KFBI_CUDA(p, dalloc(&G.h2, m + 1));
+  KFBI_CUDA(p, dalloc(&G.npart, 152 * 4));
   return KFBI_OK;
 }
 
@@ -331,6 +441,13 @@ void gmres_destroy(kfbi_problem* p) {
   cudaFree(G.scal);
   cudaFree(G.hcol);
   if (G.host_res) cudaFreeHost(G.host_res);
+  if (G.it_exec) cudaGraphExecDestroy(G.it_exec);
+  if (G.it_graph) cudaGraphDestroy(G.it_graph);
+  cudaFree(G.jdev);
+  cudaFree(G.h1);
+  cudaFree(G.h2);
+  cudaFree(G.npart);
+  cudaFree(G.desc);
   G = Gmres();
 }
 
@@ -348,6 +465,65 @@ static kfbi_status read_scalar(kfbi_problem* p, const double* dev, double* host)
   KFBI_CUDA(p, cudaMemcpyAsync(p->gm.host_res, dev, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
   KFBI_CUDA(p, cudaStreamSynchronize(p->stream));
   *host = p->gm.host_res[0];
+  return KFBI_OK;
+}
+
+// One GMRES iteration of problem p as a graph: x = V_j; y = A x (the operator's
+// kernels); V_{j+1} = y; CGS2 over all SMs; Givens; normalise; j <- j + 1.
+static kfbi_status iteration_graph(kfbi_problem* p) {
+  Gmres& G = p->gm;
+  if (G.it_exec) return KFBI_OK;
+  if (!p->cap_stream) KFBI_CUDA(p, cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+  if (!G.desc) {
+    ArnDesc d{G.V, G.nb, G.m, G.H, G.m + 1, G.cs, G.sn, G.g, G.scal + 2, p->xbuf, p->ybuf};
+    ArnDesc* dd = nullptr;
+    KFBI_CUDA(p, dalloc(&dd, 1));
+    KFBI_CUDA(p, cudaMemcpy(dd, &d, sizeof(d), cudaMemcpyHostToDevice));
+    G.desc = dd;
+  }
+  const int nb = G.nb;
+  const int eb = std::min(div_up(nb, kCgsThreads), 152 * 4);
+  cudaStream_t st = p->stream;
+  KFBI_CUDA(p, cudaStreamSynchronize(st));
+  long long before[KFBI_KC_COUNT];
+  for (int k = 0; k < KFBI_KC_COUNT; ++k) before[k] = p->prof.launches[k];
+  const bool prof = p->prof.on;
+  p->prof.on = false;
+  p->stream = p->cap_stream;
+  kfbi_status s = KFBI_OK;
+  cudaError_t e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const ArnDesc* d = static_cast<const ArnDesc*>(G.desc);
+    const int* done = G.jdev + 1;
+    s = batch_arnoldi_copy_in(p, d, G.jdev, done, 1, nb, p->stream);
+    if (s == KFBI_OK) s = apply_operator_impl(p, p->xbuf, p->ybuf);
+    if (s == KFBI_OK) {
+      cudaStream_t cs = p->stream;
+      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_copy_out_batched<<<dim3(div_up(nb, 256), 1), 256, 0, cs>>>(d, G.jdev, done));
+      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_cgs_dots<<<G.m + 1, kCgsThreads, 0, cs>>>(G.V, nb, G.jdev, G.h1));
+      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_cgs_update<<<eb, kCgsThreads, 0, cs>>>(G.V, nb, G.jdev, G.h1, nullptr));
+      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_cgs_dots<<<G.m + 1, kCgsThreads, 0, cs>>>(G.V, nb, G.jdev, G.h2));
+      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_cgs_update<<<eb, kCgsThreads, 0, cs>>>(G.V, nb, G.jdev, G.h2, G.npart));
+      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_cgs_finish<<<1, 256, 0, cs>>>(G.H, G.m + 1, G.cs, G.sn, G.g, G.scal + 2, G.h1,
+                                                                     G.h2, G.npart, eb, G.jdev, G.scal + 3));
+      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_cgs_normalize<<<eb, 256, 0, cs>>>(G.V, nb, G.jdev, G.scal + 3));
+    }
+  }
+  cudaGraph_t gr = nullptr;
+  cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(p->cap_stream, &gr) : e;
+  p->stream = st;
+  p->prof.on = prof;
+  for (int k = 0; k < KFBI_KC_COUNT; ++k) {
+    G.it_counts[k] = p->prof.launches[k] - before[k];
+    p->prof.launches[k] = before[k];
+  }
+  if (e != cudaSuccess || e2 != cudaSuccess || s != KFBI_OK) {
+    if (gr) cudaGraphDestroy(gr);
+    cudaGetLastError();
+    return s != KFBI_OK ? s : fail(p, KFBI_ERR_CUDA, "GMRES iteration capture failed");
+  }
+  G.it_graph = gr;
+  KFBI_CUDA(p, cudaGraphInstantiate(&G.it_exec, gr, 0));
   return KFBI_OK;
 }
 
@@ -414,9 +590,24 @@ kfbi_status gmres_run(kfbi_problem* p, const double* b, const double* x0, double
     KFBI_LAUNCH(p, KFBI_KC_GMRES, k_init_g<<<1, 128, 0, st>>>(G.g, G.m, beta));
     int jend = 0;
     double hres = hbeta;
+    const bool graph_it = nb <= kGraphArnoldi && p->use_graphs && !p->prof.on;
+    if (graph_it) {
+      KFBI_TRY(iteration_graph(p));
+      KFBI_CUDA(p, cudaMemsetAsync(G.jdev, 0, 2 * sizeof(int), st));
+    }
     for (int j = 0; j < m; ++j) {
       double* Vj = G.V + (size_t)j * nb;
       double* w = G.V + (size_t)(j + 1) * nb;
+      if (graph_it) {
+        KFBI_CUDA(p, cudaGraphLaunch(G.it_exec, st));
+        for (int k = 0; k < KFBI_KC_COUNT; ++k) p->prof.launches[k] += G.it_counts[k];
+        ++total;
+        KFBI_TRY(read_scalar(p, res, &hres));
+        jend = j + 1;
+        if (!std::isfinite(hres)) return fail(p, KFBI_ERR_NONFINITE, "non-finite GMRES residual");
+        if (hres <= rtol * bnorm || total >= max_iter) break;
+        continue;
+      }
       KFBI_TRY(apply_operator_fast(p, Vj, w));
       ++total;
       if (nb <= kSmallArnoldi) {

@@ -28,6 +28,8 @@ constexpr int kMaxNeighbours = 26;    // 3^3 - 1
 constexpr double kTieEps = 1e-12;     // closest-point tie tolerance (units of h^2)
 constexpr double kRootTol = 1e-15;    // root iteration stop |ds| <= tol h
 constexpr int kRootMaxIt = 64;
+constexpr int kMaxKrylov = 100;     // Krylov dimension of every problem (restart length)
+constexpr int kGraphArnoldi = 8192; // N_b up to which a GMRES iteration is one graph
 constexpr double kTraceWeightScale = 4.0;   // exp(-|xi|^2 / 4)
 
 // Status codes written by setup kernels into Problem::d_flags.
@@ -93,6 +95,16 @@ struct Gmres {
   double* hcol = nullptr;    // (m+1) coefficient scratch
   double* host_res = nullptr;  // pinned
   int nchunk = 0;
+  // one GMRES iteration (operator + Arnoldi step) as a CUDA graph with the
+  // step index on the device, for N_b <= kGraphArnoldi
+  int* jdev = nullptr;          // [0] j, [1] done flag (always 0 here)
+  double* h1 = nullptr;         // (m+1)
+  double* h2 = nullptr;         // (m+1)
+  double* npart = nullptr;      // partial norms (one per CTA of the update)
+  void* desc = nullptr;         // ArnDesc of this problem (device)
+  cudaGraphExec_t it_exec = nullptr;
+  cudaGraph_t it_graph = nullptr;
+  long long it_counts[KFBI_KC_COUNT] = {};
 };
 
 }  // namespace kfbi
