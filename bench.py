@@ -286,6 +286,8 @@ def run_ours(args, rank, world):
         out["batched"] = batched(args, stream, flush)
     if args.learned_n > 0:
         out["learned"] = learned_leg(args, stream, flush)
+    if args.threed_n > 0:
+        out["threed"] = threed_leg(args, stream, flush)
     if rank == 0 and args.cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_budget)
     return out
@@ -522,6 +524,99 @@ def learned_leg(args, stream, flush):
     return out
 
 
+def threed_leg(args, stream, flush):
+    """The 3D Dirichlet problem for modified Helmholtz (kappa = 1) with the
+    torus interface, u = e^(x+y+z)/10, 4th order, at --threed-n^3: geometric
+    multigrid (FP32 V(2,2) cycles, exact fixed-point residuals), the mixed DST
+    path and the plain FP64 DST path, each to GMRES rtol --rtol; plus the
+    multigrid's achieved bandwidth over one box solve."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2309_05965_gb300 import kfbi
+    n = args.threed_n
+    w = W.torus_helmholtz_3d(n)
+    grid = W.grid_data(w)
+    out = {"workload": f"torus Dirichlet 3D, N={n}, kappa=1, u=exp(x+y+z)/10, 4th order, "
+                       f"GMRES rtol {args.rtol:g}"}
+    opts = kfbi.GmresOpts(rtol=args.rtol, restart=100, max_iter=200, x0=None)
+    npts = (n - 1) ** 3
+    for name, box, prec in (("mg_mixed", kfbi.BOX_MG, kfbi.MIXED), ("dst_mixed", kfbi.BOX_DST, kfbi.MIXED),
+                            ("dst_fp64", kfbi.BOX_DST, kfbi.FP64)):
+        t0 = time.perf_counter()
+        G = kfbi.Problem.from_workload(w, box_solver=box, precision=prec,
+                                       box_max_iters=args.box_steps if prec == kfbi.MIXED else 0)
+        torch.cuda.synchronize()
+        setup = time.perf_counter() - t0
+        xyz = torch.zeros((G.nb, 3), dtype=torch.float64, device="cuda")
+        nrm = torch.zeros_like(xyz)
+        kfbi.kfbi_dof_points(G.handle, xyz, nrm)
+        g1, _ = W.boundary_data(w, xyz.cpu().numpy(), nrm.cpu().numpy())
+        keep = {"g1": torch.from_numpy(g1).cuda(),
+                "f_in": torch.from_numpy(np.ascontiguousarray(grid["f_in"])).cuda(),
+                "lapf_in": torch.from_numpy(np.ascontiguousarray(grid["lapf_in"])).cuda()}
+        d = kfbi.make_data(**keep)
+        x = torch.zeros(G.nb, dtype=torch.float64, device="cuda")
+        u = torch.zeros(G.grid_shape, dtype=torch.float64, device="cuda")
+
+        def step():
+            info = kfbi.kfbi_gmres_solve(G.handle, d, opts, x)
+            kfbi.kfbi_evaluate(G.handle, d, x, u)
+            return info
+        step()
+        ts = []
+        for _ in range(3):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = step()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ins = _inside(G, kfbi)
+        err = float(np.abs(u.cpu().numpy() - W.exact_grid(w, ins))[ins].max())
+        rhs = torch.randn(G.grid_shape, dtype=torch.float64, device="cuda")
+        ub = torch.zeros_like(rhs)
+        kfbi.kfbi_box_solve(G.handle, rhs, ub)
+        bt = []
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            kfbi.kfbi_box_solve(G.handle, rhs, ub)
+            e1.record(stream)
+            e1.synchronize()
+            bt.append(e0.elapsed_time(e1))
+        box_ms = statistics.median(bt)
+        r = {"solves_per_s": 1e3 / statistics.median(ts), "ms_per_solve": statistics.median(ts),
+             "gmres_iterations": info.iters, "max_err_vs_exact": err, "setup_s": setup, "n_b": G.nb,
+             "box_solve_ms": box_ms, "box_solve_mpts_s": npts / (box_ms * 1e-3) / 1e6}
+        if box == kfbi.BOX_MG:
+            # per-class device time of one box solve; V(2,2) algorithmic traffic per
+            # fine point per cycle: 4 sweeps x 12 B + residual 12 B + restriction 4.5 B
+            # + prolongation 8 B = 72.5 B, x 8/7 for the coarser levels (FP32)
+            kfbi.kfbi_profile_enable(G.handle, True)
+            kfbi.kfbi_box_solve(G.handle, rhs, ub)
+            prof = kfbi.kfbi_profile_read(G.handle)
+            kfbi.kfbi_profile_enable(G.handle, False)
+            mg_ms, mg_launches = prof["mg"]
+            steps = args.box_steps or 8
+            cycles = 4 * steps
+            achieved = npts * 72.5 * 8 / 7 * cycles / (mg_ms * 1e-3) / 1e9
+            peak = measured_peaks().get("hbm_gbs", 6800.0)
+            r["mg_roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                "frac": achieved / peak, "cycles": cycles, "mg_ms": mg_ms,
+                                "launches": mg_launches,
+                                "note": "upper bound on cycles (converged outer steps skip their work)"}
+        out[name] = r
+        G.close()
+    out["speedup_mixed_dst_vs_fp64"] = out["dst_mixed"]["solves_per_s"] / out["dst_fp64"]["solves_per_s"]
+    out["err_ratio_mg_mixed_vs_fp64"] = out["mg_mixed"]["max_err_vs_exact"] / out["dst_fp64"]["max_err_vs_exact"]
+    return out
+
+
 def _inside(G, kfbi):
     import torch
     m = torch.zeros(G.grid_shape, dtype=torch.uint8, device="cuda")
@@ -643,6 +738,8 @@ def main():
     ap.add_argument("--learned-draws", type=int, default=50)
     ap.add_argument("--learned-epochs", type=int, default=10)
     ap.add_argument("--learned-eval", type=int, default=3)
+    ap.add_argument("--threed-n", type=int, default=128,
+                    help="grid of the 3D torus workload (0: skip)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

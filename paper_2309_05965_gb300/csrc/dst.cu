@@ -787,9 +787,9 @@ __global__ void k_zero_flags(unsigned long long* nrm, int* conv) {
 // FP64 stencil arithmetic, and is handed to the next FP32 solve as FP32.
 // Scales beyond the FP32 exponent range are applied as two factors
 // 2^Fa 2^Fb (Fa + Fb = F).
-__global__ void k_fix_scale(const unsigned long long* __restrict__ nrm, double multh2, double kc,
+__global__ void k_fix_scale(const unsigned long long* __restrict__ umax, double multh2, double kc,
                             double* __restrict__ fixd, float* __restrict__ fixf) {
-  const double um = __longlong_as_double((long long)nrm[5]);
+  const double um = __longlong_as_double((long long)umax[0]);
   int F = 0;
   if (um > 0.0) F = 52 - (int)ceil(log2(um));
   F = max(-120, min(F, 240));
@@ -892,6 +892,42 @@ __global__ void k_unfix(long long tot, const long long* __restrict__ ufix, const
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
        t += (long long)gridDim.x * blockDim.x)
     u[t] = __ll2double_rn(ufix[t]) * isc;
+}
+
+// u_fix += round(e 2^F) over a grid; max|e| -> corr[0], max|u| -> corr[1]
+__global__ void k_fix_add(long long tot, const float* __restrict__ e, long long* __restrict__ ufix,
+                          const float* __restrict__ fixf, unsigned long long* __restrict__ corr, const int* skip) {
+  if (skip && *skip) return;
+  const float fa = fixf[0], fb = fixf[1], ia = fixf[2], ib = fixf[3];
+  float em = 0.f, um = 0.f;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const float ev = e[t];
+    const long long nv = ufix[t] + f2ll((ev * fa) * fb);
+    ufix[t] = nv;
+    em = fmaxf(em, fabsf(ev));
+    um = fmaxf(um, fabsf((ll2f(nv) * ia) * ib));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    em = fmaxf(em, __shfl_xor_sync(0xffffffffu, em, o));
+    um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (em > 0.f) atomicMax(corr, (unsigned long long)__double_as_longlong((double)em));
+    if (um > 0.f) atomicMax(corr + 1, (unsigned long long)__double_as_longlong((double)um));
+  }
+}
+
+// max|x| of an FP32 grid as FP64 bits -> out[0]
+__global__ void k_absmax32(long long tot, const float* __restrict__ x, unsigned long long* __restrict__ out,
+                           const int* skip) {
+  if (skip && *skip) return;
+  float m = 0.f;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(x[t]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, (unsigned long long)__double_as_longlong((double)m));
 }
 
 template <typename T, int P>
@@ -1210,7 +1246,7 @@ kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u) {
     for (int k = 0; k < P0.npass; ++k) launch_pass<float>(p, P0.args[k], P0.npairs, P0.na, st, P0.pmin[k]);
   }
   KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_check<<<1, 1, 0, st>>>(B->nrm, B->tol, B->conv));
-  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_fix_scale<<<1, 1, 0, st>>>(B->nrm, B->multh2, B->kc, B->fixd, B->fixf));
+  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_fix_scale<<<1, 1, 0, st>>>(B->nrm + 5, B->multh2, B->kc, B->fixd, B->fixf));
   KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_fix0<<<eb, 256, 0, st>>>(nodes, B->work32, rhs, g, B->fixd, B->fixf,
                                                                  B->ufix, B->rfix));
   float* r32 = reinterpret_cast<float*>(B->res);
@@ -1233,6 +1269,95 @@ kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u) {
     KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_check<<<1, 1, 0, st>>>(B->nrm, B->tol, B->conv));
   }
   KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_unfix<<<eb, 256, 0, st>>>(nodes, B->ufix, B->fixd, u));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+// ---- exact fixed-point refinement for other FP32 inner solvers (multigrid) ----
+struct FixState {
+  long long* ufix = nullptr;
+  long long* rfix = nullptr;
+  double* fixd = nullptr;
+  float* fixf = nullptr;
+  unsigned long long* umax = nullptr;
+  FixStencil W{};
+  double multh2 = 0.0, kc = 0.0;
+};
+
+kfbi_status fix_create(kfbi_problem* p, FixState** out) {
+  FixState* F = new FixState();
+  *out = F;
+  const Grid g = p->g;
+  const long long nodes = g.nodes();
+  KFBI_CUDA(p, dalloc(&F->ufix, nodes));
+  KFBI_CUDA(p, dalloc(&F->rfix, nodes));
+  KFBI_CUDA(p, dalloc(&F->fixd, 4));
+  KFBI_CUDA(p, dalloc(&F->fixf, 8));
+  KFBI_CUDA(p, dalloc(&F->umax, 1));
+  double mult, kscale;
+  if (p->cfg.order == 2) {
+    mult = 1.0;
+    F->W = FixStencil{-2 * g.d, 1, 0, 0, 1, 0};
+    kscale = 1.0;
+  } else if (g.d == 2) {
+    mult = 6.0;
+    F->W = FixStencil{-20, 4, 1, 0, 8, 1};
+    kscale = 0.5;
+  } else {
+    mult = 48.0;
+    F->W = FixStencil{-200, 20, 6, 1, 6, 1};
+    kscale = 4.0;
+  }
+  F->multh2 = mult * g.h * g.h;
+  F->kc = kscale * p->kt * g.h * g.h;
+  return KFBI_OK;
+}
+
+void fix_destroy(FixState* F) {
+  if (!F) return;
+  cudaFree(F->ufix);
+  cudaFree(F->rfix);
+  cudaFree(F->fixd);
+  cudaFree(F->fixf);
+  cudaFree(F->umax);
+  delete F;
+}
+
+// scale from max|u0|, then u_fix = round(u0 2^F), R_fix = round(mult h^2 R 2^F)
+kfbi_status fix_init(kfbi_problem* p, FixState* F, const float* u0, const double* R, cudaStream_t st) {
+  const long long nodes = p->g.nodes();
+  const int eb = (int)std::min<long long>(div_up(nodes, 256), 152 * 8);
+  KFBI_CUDA(p, cudaMemsetAsync(F->umax, 0, sizeof(unsigned long long), st));
+  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_absmax32<<<eb, 256, 0, st>>>(nodes, u0, F->umax, nullptr));
+  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_fix_scale<<<1, 1, 0, st>>>(F->umax, F->multh2, F->kc, F->fixd, F->fixf));
+  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_fix0<<<eb, 256, 0, st>>>(nodes, u0, R, p->g, F->fixd, F->fixf, F->ufix,
+                                                                 F->rfix));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status fix_residual(kfbi_problem* p, FixState* F, float* r32, const int* skip, cudaStream_t st) {
+  const Grid g = p->g;
+  const dim3 rgrid((unsigned)div_up(g.n + 1, 128), (unsigned)(g.n + 1), g.d == 3 ? (unsigned)(g.n + 1) : 1u);
+  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_res_fix<<<rgrid, 128, 0, st>>>(g, F->W, F->rfix, F->ufix, F->fixd, F->fixf,
+                                                                       r32, skip));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status fix_add(kfbi_problem* p, FixState* F, const float* e, unsigned long long* corr, const int* skip,
+                    cudaStream_t st) {
+  const long long nodes = p->g.nodes();
+  const int eb = (int)std::min<long long>(div_up(nodes, 256), 152 * 8);
+  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_fix_add<<<eb, 256, 0, st>>>(nodes, e, F->ufix, F->fixf, corr, skip));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status fix_out(kfbi_problem* p, FixState* F, double* u, cudaStream_t st) {
+  const long long nodes = p->g.nodes();
+  const int eb = (int)std::min<long long>(div_up(nodes, 256), 152 * 8);
+  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_unfix<<<eb, 256, 0, st>>>(nodes, F->ufix, F->fixd, u));
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
 }

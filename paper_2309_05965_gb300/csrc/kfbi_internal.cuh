@@ -263,6 +263,15 @@ kfbi_status box_create(kfbi_problem* p);
 void box_destroy(kfbi_problem* p);
 kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u);
 kfbi_status box_last_residual(kfbi_problem* p, double* rel, int* converged);
+// exact fixed-point refinement state (dst.cu), used by the mixed multigrid
+struct FixState;
+kfbi_status fix_create(kfbi_problem* p, FixState** out);
+void fix_destroy(FixState* F);
+kfbi_status fix_init(kfbi_problem* p, FixState* F, const float* u0, const double* R, cudaStream_t st);
+kfbi_status fix_residual(kfbi_problem* p, FixState* F, float* r32, const int* skip, cudaStream_t st);
+kfbi_status fix_add(kfbi_problem* p, FixState* F, const float* e, unsigned long long* corr, const int* skip,
+                    cudaStream_t st);
+kfbi_status fix_out(kfbi_problem* p, FixState* F, double* u, cudaStream_t st);
 // gmres.cu
 kfbi_status gmres_create(kfbi_problem* p, int m);
 void gmres_destroy(kfbi_problem* p);

@@ -327,29 +327,6 @@ __global__ void k_to_float(long long tot, const double* __restrict__ a, float* _
     b[t] = (float)a[t];
 }
 
-// u += e, with max|e| -> corr[0] and max|u| -> corr[1]
-__global__ void k_add_float(long long tot, const float* __restrict__ e, double* __restrict__ u,
-                            unsigned long long* __restrict__ corr, const int* skip) {
-  if (skip && *skip) return;
-  double em = 0.0, um = 0.0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-       t += (long long)gridDim.x * blockDim.x) {
-    double ev = (double)e[t];
-    double nv = u[t] + ev;
-    u[t] = nv;
-    em = fmax(em, fabs(ev));
-    um = fmax(um, fabs(nv));
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    em = fmax(em, __shfl_xor_sync(0xffffffffu, em, o));
-    um = fmax(um, __shfl_xor_sync(0xffffffffu, um, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    if (em > 0.0) atomicMax(corr, (unsigned long long)__double_as_longlong(em));
-    if (um > 0.0) atomicMax(corr + 1, (unsigned long long)__double_as_longlong(um));
-  }
-}
-
 // mixed: conv = (max|e_k| <= tol max|u|), the FP32 cycles contract the error by
 // orders of magnitude per outer step, so the last correction bounds the error
 __global__ void k_mg_check_corr(unsigned long long* nrm, double tol, int* conv) {
@@ -431,7 +408,7 @@ struct MgSolver {
   float* cinv32 = nullptr;
   std::vector<void*> bufs;
   double* u64 = nullptr;       // mixed: FP64 accumulated solution lives in the caller's u
-  double* r64 = nullptr;       // FP64 residual
+  FixState* fix = nullptr;     // mixed: exact fixed-point residual between FP32 solves
   unsigned long long* nrm = nullptr;
   int* conv = nullptr;
   int max_cycles = 60;
@@ -618,9 +595,7 @@ kfbi_status mg_create(kfbi_problem* p) {
   const long long nodes = g.nodes();
   if (M->precision == KFBI_MIXED) {
     KFBI_TRY(build_levels<float>(p, M, M->A32, &M->cinv32, true));
-    KFBI_CUDA(p, dalloc(&M->r64, nodes));
-    KFBI_CUDA(p, cudaMemset(M->r64, 0, sizeof(double) * nodes));
-    M->bufs.push_back(M->r64);
+    KFBI_TRY(fix_create(p, &M->fix));
   } else {
     KFBI_TRY(build_levels<double>(p, M, M->A64, &M->cinv64, false));
   }
@@ -644,6 +619,7 @@ void mg_destroy(kfbi_problem* p) {
   MgSolver* M = p->mg;
   if (!M) return;
   for (void* b : M->bufs) cudaFree(b);
+  fix_destroy(M->fix);
   delete M;
   p->mg = nullptr;
 }
@@ -655,10 +631,10 @@ kfbi_status mg_solve(kfbi_problem* p, const double* rhs, double* u) {
   const long long nodes = g.nodes();
   const dim3 gr = lvl_grid<double>(g.d, g.n);
   KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_mg_reset<<<1, 1, 0, st>>>(M->nrm, M->conv));
-  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_absmax_mg<<<std::min(div_up(nodes, 256), 152 * 8), 256, 0, st>>>(
-      nodes, rhs, M->nrm));
-  KFBI_CUDA(p, cudaMemsetAsync(u, 0, sizeof(double) * nodes, st));
   if (M->precision != KFBI_MIXED) {
+    KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_absmax_mg<<<std::min(div_up(nodes, 256), 152 * 8), 256, 0, st>>>(
+        nodes, rhs, M->nrm));
+    KFBI_CUDA(p, cudaMemsetAsync(u, 0, sizeof(double) * nodes, st));
     LvlArgs<double>& A = M->A64;
     A.L[0].u = u;
     A.L[0].f = const_cast<double*>(rhs);
@@ -671,20 +647,20 @@ kfbi_status mg_solve(kfbi_problem* p, const double* rhs, double* u) {
     KFBI_CUDA(p, cudaGetLastError());
     return KFBI_OK;
   }
-  // mixed: u (FP64) += FP32 MG(A e = r), r = R - A u in FP64
+  // mixed: u0 = FP32 MG(R); then u is kept in fixed point and each outer step
+  // solves A e = r with r = R - A_h u exact (integer stencil), e by FP32 V-cycles
   LvlArgs<float>& A = M->A32;
-  const double* r = rhs;
-  for (int o = 0; o < M->outer_max; ++o) {
-    KFBI_LAUNCH(p, KFBI_KC_MG, k_to_float<<<std::min(div_up(nodes, 256), 152 * 8), 256, 0, st>>>(
-        nodes, r, A.L[0].f, M->conv));
+  KFBI_LAUNCH(p, KFBI_KC_MG, k_to_float<<<std::min(div_up(nodes, 256), 152 * 8), 256, 0, st>>>(
+      nodes, rhs, A.L[0].f, nullptr));
+  for (int c = 0; c < M->inner_cycles; ++c) KFBI_TRY(vcycle<float>(p, A, M->lcoarse, c == 0, nullptr));
+  KFBI_TRY(fix_init(p, M->fix, A.L[0].u, rhs, st));
+  for (int o = 1; o < M->outer_max; ++o) {
+    KFBI_TRY(fix_residual(p, M->fix, A.L[0].f, M->conv, st));
     for (int c = 0; c < M->inner_cycles; ++c) KFBI_TRY(vcycle<float>(p, A, M->lcoarse, c == 0, M->conv));
-    KFBI_LAUNCH(p, KFBI_KC_MG, k_add_float<<<std::min(div_up(nodes, 256), 152 * 8), 256, 0, st>>>(
-        nodes, A.L[0].u, u, M->nrm + 6, M->conv));
+    KFBI_TRY(fix_add(p, M->fix, A.L[0].u, M->nrm + 6, M->conv, st));
     KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_mg_check_corr<<<1, 1, 0, st>>>(M->nrm, M->tol, M->conv));
-    KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_mg_residual64<<<gr, 128, 0, st>>>(
-        g, p->cfg.order, p->stencil_dev, rhs, u, M->r64, M->nrm + 1, M->conv));
-    r = M->r64;
   }
+  KFBI_TRY(fix_out(p, M->fix, u, st));
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
 }
