@@ -72,41 +72,97 @@ __device__ __forceinline__ T apply_at(int d, int order, int n1, const T* c, cons
   return a;
 }
 
-// ---- per-level kernels: x over the last axis, y (z) over the others --------
+// ---- marching stencil sweeps ------------------------------------------------
+// A thread owns one line along the slowest axis (a column (i1, j) in 3D, a
+// column j in 2D) and marches along it, keeping three consecutive slices of
+// the per-slice sums in registers:
+//   3D slice k: centre C, in-plane edge sum S1 (4), in-plane corner sum S2 (4);
+//     A u = c0 C(k) + c1 (S1(k) + C(k-1) + C(k+1)) + c2 (S2(k) + S1(k-1) + S1(k+1))
+//           + c3 (S2(k-1) + S2(k+1));
+//   2D row k: centre C, horizontal pair H;
+//     A u = c0 C(k) + c1 (H(k) + C(k-1) + C(k+1)) + c2 (H(k-1) + H(k+1)).
+// Each new slice costs 9 (3D) / 3 (2D) loads instead of 27 / 9 per point.
+// mode 0: Jacobi uout = uin + w D^-1 (f - A uin) (zero_guess: uout = w D^-1 f);
+// mode 1: residual r = f - A u.  Only interior nodes are written (boundary
+// nodes of every level buffer are zero from allocation and never written).
+constexpr int kMarchX = 128;
+constexpr int kMarchZ = 16;   // slices per thread
 
 template <typename T>
-__global__ void k_jacobi(int d, int order, Lvl<T> L, const T* __restrict__ uin, T* __restrict__ uout,
-                         int zero_guess, const int* skip) {
+struct Slice {
+  T C, S1, S2;
+};
+
+template <typename T>
+__device__ __forceinline__ Slice<T> slice3(const T* __restrict__ u, int t, int n1) {
+  const T* p = u + t;
+  Slice<T> s;
+  s.C = p[0];
+  s.S1 = (p[-1] + p[1]) + (p[-n1] + p[n1]);
+  s.S2 = (p[-n1 - 1] + p[-n1 + 1]) + (p[n1 - 1] + p[n1 + 1]);
+  return s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMarchX) k_march(int d, Lvl<T> L, const T* __restrict__ uin, T* __restrict__ out,
+                                                   int mode, int zero_guess, const int* skip) {
   if (skip && *skip) return;
   const int n = L.n, n1 = n + 1;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i1 = blockIdx.y, i0 = blockIdx.z;
-  if (j > n) return;
-  const long long t = lin(d, n1, i0, i1, j);
-  const bool interior = j >= 1 && j < n && i1 >= 1 && i1 < n && (d == 2 || (i0 >= 1 && i0 < n));
-  if (!interior) {
-    uout[t] = (T)0;
+  const int j = 1 + blockIdx.x * kMarchX + threadIdx.x;
+  if (j >= n) return;
+  const T c0 = L.c[0], c1 = L.c[1], c2 = L.c[2], c3 = L.c[3];
+  if (d == 2) {
+    const int k0 = 1 + blockIdx.y * kMarchZ, k1 = min(n, k0 + kMarchZ);
+    if (zero_guess) {
+      for (int k = k0; k < k1; ++k) out[k * n1 + j] = L.dinv_w * L.f[k * n1 + j];
+      return;
+    }
+    int t = (k0 - 1) * n1 + j;
+    T Cm = uin[t], Hm = uin[t - 1] + uin[t + 1];
+    t += n1;
+    T C0 = uin[t], H0 = uin[t - 1] + uin[t + 1];
+    for (int k = k0; k < k1; ++k, t += n1) {
+      const T Cp = uin[t + n1], Hp = uin[t + n1 - 1] + uin[t + n1 + 1];
+      const T au = c0 * C0 + c1 * (H0 + Cm + Cp) + c2 * (Hm + Hp);
+      const T f = L.f[t];
+      out[t] = mode == 0 ? C0 + L.dinv_w * (f - au) : f - au;
+      Cm = C0; Hm = H0;
+      C0 = Cp; H0 = Hp;
+    }
     return;
   }
+  const int i1 = 1 + blockIdx.y;
+  const int k0 = 1 + blockIdx.z * kMarchZ, k1 = min(n, k0 + kMarchZ);
+  const int plane = n1 * n1;
   if (zero_guess) {
-    uout[t] = L.dinv_w * L.f[t];
+    for (int k = k0; k < k1; ++k) {
+      const int t = (k * n1 + i1) * n1 + j;
+      out[t] = L.dinv_w * L.f[t];
+    }
     return;
   }
-  T au = apply_at<T>(d, order, n1, L.c, uin + t);
-  uout[t] = uin[t] + L.dinv_w * (L.f[t] - au);
+  int t = ((k0 - 1) * n1 + i1) * n1 + j;
+  Slice<T> m = slice3(uin, t, n1);
+  t += plane;
+  Slice<T> c = slice3(uin, t, n1);
+  for (int k = k0; k < k1; ++k, t += plane) {
+    const Slice<T> q = slice3(uin, t + plane, n1);
+    const T au = c0 * c.C + c1 * (c.S1 + m.C + q.C) + c2 * (c.S2 + m.S1 + q.S1) + c3 * (m.S2 + q.S2);
+    const T f = L.f[t];
+    out[t] = mode == 0 ? c.C + L.dinv_w * (f - au) : f - au;
+    m = c;
+    c = q;
+  }
 }
 
 template <typename T>
-__global__ void k_resid_lvl(int d, int order, Lvl<T> L, T* __restrict__ r, const int* skip) {
-  if (skip && *skip) return;
-  const int n = L.n, n1 = n + 1;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i1 = blockIdx.y, i0 = blockIdx.z;
-  if (j > n) return;
-  const long long t = lin(d, n1, i0, i1, j);
-  const bool interior = j >= 1 && j < n && i1 >= 1 && i1 < n && (d == 2 || (i0 >= 1 && i0 < n));
-  r[t] = interior ? L.f[t] - apply_at<T>(d, order, n1, L.c, L.u + t) : (T)0;
+dim3 march_grid(int d, int n) {
+  const unsigned gx = (unsigned)div_up(n - 1, kMarchX);
+  const unsigned gz = (unsigned)div_up(n - 1, kMarchZ);
+  return d == 2 ? dim3(gx, gz, 1) : dim3(gx, (unsigned)(n - 1), gz);
 }
+
+// ---- per-level transfer kernels: x over the last axis, y (z) over the others ----
 
 // full weighting: weight prod_k w(o_k), w(0) = 1/2, w(+-1) = 1/4
 template <typename T>
@@ -515,10 +571,11 @@ kfbi_status vcycle(kfbi_problem* p, LvlArgs<T>& A, int lcoarse, bool zero_guess,
     Lvl<T>& L = A.L[l];
     const dim3 gr = lvl_grid<T>(d, L.n);
     const bool zero = (l > 0) || zero_guess;
-    // two sweeps u -> t -> u
-    KFBI_LAUNCH(p, KFBI_KC_MG, k_jacobi<T><<<gr, 128, 0, st>>>(d, order, L, L.u, L.t, zero ? 1 : 0, skip));
-    KFBI_LAUNCH(p, KFBI_KC_MG, k_jacobi<T><<<gr, 128, 0, st>>>(d, order, L, L.t, L.u, 0, skip));
-    KFBI_LAUNCH(p, KFBI_KC_MG, k_resid_lvl<T><<<gr, 128, 0, st>>>(d, order, L, L.t, skip));
+    // two sweeps u -> t -> u, then the residual into t
+    const dim3 mg_ = march_grid<T>(d, L.n);
+    KFBI_LAUNCH(p, KFBI_KC_MG, k_march<T><<<mg_, kMarchX, 0, st>>>(d, L, L.u, L.t, 0, zero ? 1 : 0, skip));
+    KFBI_LAUNCH(p, KFBI_KC_MG, k_march<T><<<mg_, kMarchX, 0, st>>>(d, L, L.t, L.u, 0, 0, skip));
+    KFBI_LAUNCH(p, KFBI_KC_MG, k_march<T><<<mg_, kMarchX, 0, st>>>(d, L, L.u, L.t, 1, 0, skip));
     KFBI_LAUNCH(p, KFBI_KC_MG, k_restrict<T><<<lvl_grid<T>(d, A.L[l + 1].n), 128, 0, st>>>(
         d, A.L[l + 1].n, L.t, A.L[l + 1].f, skip));
   }
@@ -528,8 +585,9 @@ kfbi_status vcycle(kfbi_problem* p, LvlArgs<T>& A, int lcoarse, bool zero_guess,
     Lvl<T>& L = A.L[l];
     const dim3 gr = lvl_grid<T>(d, L.n);
     KFBI_LAUNCH(p, KFBI_KC_MG, k_prolong_add<T><<<gr, 128, 0, st>>>(d, L.n, A.L[l + 1].u, L.u, skip));
-    KFBI_LAUNCH(p, KFBI_KC_MG, k_jacobi<T><<<gr, 128, 0, st>>>(d, order, L, L.u, L.t, 0, skip));
-    KFBI_LAUNCH(p, KFBI_KC_MG, k_jacobi<T><<<gr, 128, 0, st>>>(d, order, L, L.t, L.u, 0, skip));
+    const dim3 mg_ = march_grid<T>(d, L.n);
+    KFBI_LAUNCH(p, KFBI_KC_MG, k_march<T><<<mg_, kMarchX, 0, st>>>(d, L, L.u, L.t, 0, 0, skip));
+    KFBI_LAUNCH(p, KFBI_KC_MG, k_march<T><<<mg_, kMarchX, 0, st>>>(d, L, L.t, L.u, 0, 0, skip));
   }
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;

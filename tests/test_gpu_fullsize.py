@@ -1,0 +1,144 @@
+"""Full-size checks at the benchmark's workloads and launch configuration.
+
+* Flower interface, 1024^2 (the benchmark's main workload): the FP64 path
+  against the oracle element by element (operator on a seeded density), and
+  the benchmark's mixed configuration (3 box-solve steps) against the oracle
+  through what the method is judged on: the solution's error against the exact
+  solution within 1.1x the oracle's, at the benchmark's GMRES tolerance.
+* Torus, 3D, 128^3 (the oracle's set-up there takes minutes): properties that
+  hold at any size - every box solver reproduces single sine modes in closed
+  form, the mixed and multigrid solutions have the FP64 path's error against
+  the exact solution within 1.1x, and that error falls at fourth order from
+  128^3 to 256^3."""
+import itertools
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import boxsolve as BS
+from oracle import kfbi as OK
+from tests.gpu_util import dev, empty, gpu_data, host, rel_err
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+_flower = {}
+
+
+def _flower_pair():
+    if not _flower:
+        from paper_2309_05965_gb300 import build, kfbi
+        build.build()
+        w = W.flower_interface_2d(1024)
+        P = OK.Problem(w)
+        data = W.grid_data(w)
+        g1, g2 = W.boundary_data(w, P.surf.x, P.surf.n)
+        _flower.update(w=w, P=P, data=data, g1=g1, g2=g2)
+    return _flower
+
+
+def test_flower1024_fp64_operator_and_solution():
+    from paper_2309_05965_gb300 import kfbi
+    F = _flower_pair()
+    w, P = F["w"], F["P"]
+    G = kfbi.Problem.from_workload(w, precision=kfbi.FP64)
+    assert G.nb == P.nb
+    x = np.random.default_rng(11).standard_normal(P.nb)
+    y = empty(G.nb)
+    kfbi.kfbi_apply_operator(G.handle, dev(x), y)
+    assert rel_err(host(y), P.apply(x)) < 1e-10
+    d, keep = gpu_data(w, P, F["data"], F["g1"], F["g2"])
+    dens = empty(G.nb)
+    kfbi.kfbi_gmres_solve(G.handle, d, kfbi.GmresOpts(rtol=1e-8, restart=100, max_iter=100), dens)
+    xg = host(dens)
+    b = P.bie_rhs(F["g1"], F["g2"], F["data"])
+    assert np.linalg.norm(b - P.apply(xg)) / np.linalg.norm(b) < 1e-7
+    G.close()
+
+
+def test_flower1024_mixed_bench_configuration_error():
+    """Mixed DST with the benchmark's 3 steps: error vs exact within 1.1x of
+    the oracle's own FP64 solve at the same GMRES tolerance."""
+    from paper_2309_05965_gb300 import kfbi
+    F = _flower_pair()
+    w, P = F["w"], F["P"]
+    x_ref, _, _ = OK.gmres(P.apply, P.bie_rhs(F["g1"], F["g2"], F["data"]), rtol=1e-8)
+    u_ref = P.evaluate(x_ref, F["g1"], F["data"])
+    ex = W.exact_grid(w, P.inside)
+    e_ref = np.abs(u_ref - ex)[1:-1, 1:-1].max()
+    G = kfbi.Problem.from_workload(w, precision=kfbi.MIXED, box_rtol=1e-11, box_max_iters=3)
+    d, keep = gpu_data(w, P, F["data"], F["g1"], F["g2"])
+    dens = empty(G.nb)
+    kfbi.kfbi_gmres_solve(G.handle, d, kfbi.GmresOpts(rtol=1e-8, restart=100, max_iter=100), dens)
+    u = empty(G.grid_shape)
+    kfbi.kfbi_evaluate(G.handle, d, dens, u)
+    e = np.abs(host(u) - ex)[1:-1, 1:-1].max()
+    assert e <= 1.1 * e_ref, (e, e_ref)
+    G.close()
+
+
+def _torus(n, box, prec, steps=0):
+    from paper_2309_05965_gb300 import build, kfbi
+    build.build()
+    w = W.torus_helmholtz_3d(n)
+    G = kfbi.Problem.from_workload(w, box_solver=box, precision=prec, box_max_iters=steps)
+    return w, G
+
+
+def _torus_error(w, G):
+    import torch
+    from paper_2309_05965_gb300 import kfbi
+    xyz = torch.zeros((G.nb, 3), dtype=torch.float64, device="cuda")
+    nrm = torch.zeros_like(xyz)
+    kfbi.kfbi_dof_points(G.handle, xyz, nrm)
+    g1, _ = W.boundary_data(w, xyz.cpu().numpy(), nrm.cpu().numpy())
+    grid = W.grid_data(w)
+    keep = {"g1": dev(g1), "f_in": dev(grid["f_in"]), "lapf_in": dev(grid["lapf_in"])}
+    d = kfbi.make_data(**keep)
+    dens = empty(G.nb)
+    kfbi.kfbi_gmres_solve(G.handle, d, kfbi.GmresOpts(rtol=1e-10, restart=100, max_iter=100), dens)
+    u = empty(G.grid_shape)
+    kfbi.kfbi_evaluate(G.handle, d, dens, u)
+    m = empty(G.grid_shape, "u8")
+    kfbi.kfbi_inside_mask(G.handle, m)
+    ins = host(m).astype(bool)
+    return float(np.abs(host(u) - W.exact_grid(w, ins))[ins].max())
+
+
+def test_torus128_box_solvers_on_sine_modes():
+    import torch
+    from paper_2309_05965_gb300 import kfbi
+    n = 128
+    for box, prec in ((kfbi.BOX_DST, kfbi.FP64), (kfbi.BOX_DST, kfbi.MIXED), (kfbi.BOX_MG, kfbi.MIXED)):
+        w, G = _torus(n, box, prec)
+        c = BS.stencil_coeffs(3, 4, w.h, w.kappa)
+        for modes in ([1, 1, 1], [n - 1, 2, n // 2 + 3]):
+            lam = sum(c[sum(1 for v in o if v)] * np.prod([np.cos(p * np.pi * ok / n) for p, ok in zip(modes, o)])
+                      for o in itertools.product((-1, 0, 1), repeat=3))
+            R = torch.ones(G.grid_shape, dtype=torch.float64, device="cuda")
+            for k, p in enumerate(modes):
+                shape = [1, 1, 1]
+                shape[k] = n + 1
+                arg = torch.remainder(p * torch.arange(n + 1, device="cuda"), 2 * n).double()
+                R = R * torch.sin(np.pi * arg / n).reshape(shape)
+            u = empty(G.grid_shape)
+            kfbi.kfbi_box_solve(G.handle, R.contiguous(), u)
+            err = float((u - R / lam).abs().max() / (R / lam).abs().max())
+            assert err < 1e-10, (box, prec, modes, err)
+        G.close()
+
+
+def test_torus_mixed_and_multigrid_errors_and_order():
+    from paper_2309_05965_gb300 import kfbi
+    errs = {}
+    for n in (128, 256):
+        for key, box, prec, steps in (("fp64", kfbi.BOX_DST, kfbi.FP64, 0), ("mixed", kfbi.BOX_DST, kfbi.MIXED, 3),
+                                      ("mg", kfbi.BOX_MG, kfbi.MIXED, 3)):
+            w, G = _torus(n, box, prec, steps)
+            errs[(key, n)] = _torus_error(w, G)
+            G.close()
+    for n in (128, 256):
+        assert errs[("mixed", n)] <= 1.1 * errs[("fp64", n)], errs
+        assert errs[("mg", n)] <= 1.1 * errs[("fp64", n)], errs
+    order = np.log2(errs[("fp64", 128)] / errs[("fp64", 256)])
+    assert order > 3.5, (order, errs)
