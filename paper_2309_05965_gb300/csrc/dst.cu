@@ -490,22 +490,130 @@ std::vector<float> stage_twiddles(int logL) {
   return out;
 }
 
-// round(x) as int64 for |x| < 2^62 from FP32 pieces: the 64-bit conversions
-// run on the FP64 pipe, which GB300 has at 1/64 of the FP32 rate
+// ---- 64-bit fixed-point arithmetic on 32-bit pieces ---------------------------
+// On GB300 the 64-bit integer adds, 64-bit address arithmetic and the
+// integer-to-float conversions run on the FP64 pipe (2 per clock per SM);
+// these helpers keep every step on the 32-bit integer and FP32 pipes: adds
+// with an explicit carry, shifts as funnel shifts, conversions through 16- and
+// 32-bit pieces.
+__device__ __forceinline__ void split64(long long v, unsigned& lo, unsigned& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(v));
+}
+__device__ __forceinline__ long long join64(unsigned lo, unsigned hi) {
+  long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
+  return r;
+}
+__device__ __forceinline__ long long add64(long long a, long long b) {
+  unsigned al, ah, bl, bh, rl, rh;
+  split64(a, al, ah);
+  split64(b, bl, bh);
+  asm("add.cc.u32 %0, %2, %4;\n\taddc.u32 %1, %3, %5;" : "=r"(rl), "=r"(rh) : "r"(al), "r"(ah), "r"(bl), "r"(bh));
+  return join64(rl, rh);
+}
+__device__ __forceinline__ long long sub64(long long a, long long b) {
+  unsigned al, ah, bl, bh, rl, rh;
+  split64(a, al, ah);
+  split64(b, bl, bh);
+  asm("sub.cc.u32 %0, %2, %4;\n\tsubc.u32 %1, %3, %5;" : "=r"(rl), "=r"(rh) : "r"(al), "r"(ah), "r"(bl), "r"(bh));
+  return join64(rl, rh);
+}
+template <int K>
+__device__ __forceinline__ long long shl64(long long a) {
+  unsigned l, h;
+  split64(a, l, h);
+  return join64(l << K, __funnelshift_l(l, h, K));
+}
+__device__ __forceinline__ void neg32pair(unsigned& l, unsigned& h) {
+  asm("sub.cc.u32 %0, 0, %2;\n\tsubc.u32 %1, 0, %3;" : "=r"(l), "=r"(h) : "r"(l), "r"(h));
+}
+
+// round(x) as int64 for |x| < 2^62
 __device__ __forceinline__ long long f2ll(float x) {
   const float ax = fabsf(x);
   const float hi = floorf(ax * 2.3283064365386963e-10f);   // ax / 2^32
   const float lo = fmaf(hi, -4294967296.f, ax);            // ax - hi 2^32, exact, in [0, 2^32)
-  const long long r = ((long long)__float2uint_rz(hi) << 32) + (long long)__float2uint_rn(lo);
-  return x < 0.f ? -r : r;
+  unsigned l = __float2uint_rn(lo), h = __float2uint_rz(hi);
+  if (x < 0.f) neg32pair(l, h);
+  return join64(l, h);
 }
 
-// int64 -> FP32 (within 1 ulp) from 32-bit pieces of |v| (a two's-complement
-// split of a small negative v would cancel: -5 = -2^32 + (2^32 - 5))
+// x in [0, 2^16) -> FP32 exactly without a conversion instruction: 2^23 + x
+// has x as its low mantissa bits
+__device__ __forceinline__ float u16f(unsigned x) {
+  return __int_as_float(0x4B000000 | (int)x) - 8388608.f;
+}
+
+// int64 -> FP32 (within 2 ulp) from four 16-bit pieces of |v|
 __device__ __forceinline__ float ll2f(long long v) {
-  const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
-  const float m = fmaf(__uint2float_rn((unsigned)(a >> 32)), 4294967296.f, __uint2float_rn((unsigned)a));
-  return v < 0 ? -m : m;
+  unsigned l, h;
+  split64(v, l, h);
+  const bool neg = (int)h < 0;
+  if (neg) neg32pair(l, h);
+  float m = fmaf(u16f(h >> 16), 65536.f, u16f(h & 0xffffu));
+  m = fmaf(m, 65536.f, u16f(l >> 16));
+  m = fmaf(m, 65536.f, u16f(l & 0xffffu));
+  return neg ? -m : m;
+}
+
+// int64 -> FP64 (round half up) by assembling the bits
+__device__ __forceinline__ double ll2d(long long v) {
+  unsigned l, h;
+  split64(v, l, h);
+  const unsigned sign = h & 0x80000000u;
+  if (sign) neg32pair(l, h);
+  if ((h | l) == 0u) return 0.0;
+  const int lz = h ? __clz(h) : 32 + __clz(l);
+  if (lz >= 32) {                      // normalise: bit 63 set
+    h = l << (lz - 32);
+    l = 0u;
+  } else if (lz > 0) {
+    h = __funnelshift_l(l, h, lz);
+    l <<= lz;
+  }
+  int E = 1086 - lz;                   // the value is (h:l) 2^-lz, top bit worth 2^(63 - lz)
+  unsigned cy;
+  asm("add.cc.u32 %0, %0, 1024;\n\taddc.cc.u32 %1, %1, 0;\n\taddc.u32 %2, 0, 0;" : "+r"(l), "+r"(h), "=r"(cy));
+  if (cy) {                            // rounded up to 2^64
+    h = 0x80000000u;
+    l = 0u;
+    E += 1;
+  }
+  const unsigned mh = (h >> 11) & 0xfffffu;
+  const unsigned ml = (h << 21) | (l >> 11);
+  return __hiloint2double((int)(sign | ((unsigned)E << 20) | mh), (int)ml);
+}
+
+// round(x 2^F) as int64 for |x 2^F| < 2^62, from the bits of x (no FP64 arithmetic)
+__device__ __forceinline__ long long d2ll_pow2(double x, int F) {
+  unsigned lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(x));
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  if (e == 0) return 0;                       // zero (subnormals are far below the scale)
+  unsigned ml = lo, mh = (hi & 0xfffffu) | 0x100000u;   // 53-bit significand m, x = m 2^(e - 1075)
+  const int sft = e - 1075 + F;
+  unsigned rl, rh;
+  if (sft >= 0) {
+    const int k = min(sft, 31);
+    rh = __funnelshift_l(ml, mh, k);
+    rl = ml << k;
+  } else {
+    const int k = -sft;
+    if (k > 54) return 0;
+    // add 2^(k-1), then shift right by k: round half up
+    const unsigned al = k - 1 < 32 ? (1u << (k - 1)) : 0u;
+    const unsigned ah = k - 1 < 32 ? 0u : (1u << (k - 1 - 32));
+    asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, %3;" : "+r"(ml), "+r"(mh) : "r"(al), "r"(ah));
+    if (k < 32) {
+      rl = __funnelshift_r(ml, mh, k);
+      rh = mh >> k;
+    } else {
+      rl = mh >> (k - 32);
+      rh = 0u;
+    }
+  }
+  if (hi >> 31) neg32pair(rl, rh);
+  return join64(rl, rh);
 }
 
 template <int LOGL, int P>
@@ -648,12 +756,12 @@ __device__ __forceinline__ void dst32_body(const PassArgs& A, int bx, int by, Cx
 #pragma unroll
       for (int it = 0; it < NIT; ++it) {
         if (offs[it] >= 0) {
-          const long long nA = oldA[it] + f2ll((vals[it].x * fa) * fb);
+          const long long nA = add64(oldA[it], f2ll((vals[it].x * fa) * fb));
           A.dstfix[offs[it]] = nA;
           dmx = fmaxf(dmx, fabsf(vals[it].x));
           umx = fmaxf(umx, fabsf((ll2f(nA) * ia) * ib));
           if (hasB[it]) {
-            const long long nB = oldB[it] + f2ll((vals[it].y * fa) * fb);
+            const long long nB = add64(oldB[it], f2ll((vals[it].y * fa) * fb));
             A.dstfix[offs[it] + sb] = nB;
             dmx = fmaxf(dmx, fabsf(vals[it].y));
             umx = fmaxf(umx, fabsf((ll2f(nB) * ia) * ib));
@@ -787,31 +895,37 @@ __global__ void k_zero_flags(unsigned long long* nrm, int* conv) {
 // FP64 stencil arithmetic, and is handed to the next FP32 solve as FP32.
 // Scales beyond the FP32 exponent range are applied as two factors
 // 2^Fa 2^Fb (Fa + Fb = F).
-__global__ void k_fix_scale(const unsigned long long* __restrict__ umax, double multh2, double kc,
-                            double* __restrict__ fixd, float* __restrict__ fixf) {
-  const double um = __longlong_as_double((long long)umax[0]);
+__device__ __forceinline__ void fix_scale_body(const unsigned long long* __restrict__ umax, double multh2,
+                                               double kc, double* __restrict__ fixd, float* __restrict__ fixf) {
+  // U = u 2^F / (mult h^2) with max|U| ~ 2^52; R_fix = R 2^F (an exact power of two)
+  const double um = __longlong_as_double((long long)umax[0]) / multh2;
   int F = 0;
   if (um > 0.0) F = 52 - (int)ceil(log2(um));
   F = max(-120, min(F, 240));
   const int Fa = F / 2, Fb = F - Fa;
-  fixd[0] = ldexp(multh2, F);
-  fixd[1] = ldexp(1.0, -F);
+  fixd[1] = ldexp(multh2, -F);                  // u = U mult h^2 2^-F
   fixd[2] = kc;
-  fixf[0] = ldexpf(1.f, Fa);
-  fixf[1] = ldexpf(1.f, Fb);
-  fixf[2] = ldexpf(1.f, -Fa);
-  fixf[3] = ldexpf(1.f, -Fb);
-  fixf[4] = (float)(ldexp(1.0, -Fb) / multh2);   // r32 = (r_fix 2^-Fa) (2^-Fb / mult h^2)
+  fixd[3] = (double)F;
+  fixf[0] = ldexpf(1.f, Fa);                    // U = (u 2^Fa) (2^Fb / mult h^2)
+  fixf[1] = (float)(ldexp(1.0, Fb) / multh2);
+  fixf[2] = ldexpf(1.f, -Fa);                   // u = (U 2^-Fa) (mult h^2 2^-Fb); r = (r_fix 2^-Fa) 2^-Fb
+  fixf[3] = (float)ldexp(multh2, -Fb);
+  fixf[4] = ldexpf(1.f, -Fb);
+}
+
+__global__ void k_fix_scale(const unsigned long long* __restrict__ umax, double multh2, double kc,
+                            double* __restrict__ fixd, float* __restrict__ fixf) {
+  fix_scale_body(umax, multh2, kc, fixd, fixf);
 }
 
 __global__ void k_fix0(long long tot, const float* __restrict__ u0, const double* __restrict__ R, Grid g,
                        const double* __restrict__ fixd, const float* __restrict__ fixf,
                        long long* __restrict__ ufix, long long* __restrict__ rfix) {
-  const double rm = fixd[0];
+  const int F = (int)fixd[3];
   const float fa = fixf[0], fb = fixf[1];
   const int n1 = g.n + 1;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-       t += (long long)gridDim.x * blockDim.x) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < (int)tot;
+       t += gridDim.x * blockDim.x) {
     ufix[t] = f2ll((u0[t] * fa) * fb);
     long long r = t;
     bool interior = true;
@@ -820,7 +934,7 @@ __global__ void k_fix0(long long tot, const float* __restrict__ u0, const double
       r /= n1;
       interior = interior && i >= 1 && i < g.n;
     }
-    rfix[t] = interior ? __double2ll_rn(R[t] * rm) : 0ll;
+    rfix[t] = interior ? d2ll_pow2(R[t], F) : 0ll;
   }
 }
 
@@ -828,22 +942,46 @@ struct FixStencil {
   int w0, w1, w2, w3, kA, kB;
 };
 
-// S u of the integer stencil and the kappa combination kA u_P + kB e, with
-// the weights of the three operators as compile-time shifts and adds (64-bit
-// integer multiplies go to the FP64 pipe)
+// S U of the integer stencil and the kappa combination kA U_P + kB e, with
+// the weights of the three operators as shifts and adds on 32-bit pieces
 __device__ __forceinline__ long long fix_apply(const FixStencil& W, long long c, long long e, long long k2,
                                                long long k3, long long& m) {
   if (W.w0 == -20) {          // 2D 4th order: -20 c + 4 e + k2; kappa: 8 c + e
-    m = (c << 3) + e;
-    return ((e - ((c << 2) + c)) << 2) + k2;
+    m = add64(shl64<3>(c), e);
+    return add64(shl64<2>(sub64(e, add64(shl64<2>(c), c))), k2);
   }
   if (W.w0 == -200) {         // 3D 4th order: -200 c + 20 e + 6 k2 + k3; kappa: 6 c + e
-    m = ((c << 2) + (c << 1)) + e;
-    const long long t = ((e << 2) + e) - ((c << 5) + (c << 4) + (c << 1));   // 5 e - 50 c
-    return (t << 2) + ((k2 << 2) + (k2 << 1)) + k3;
+    m = add64(add64(shl64<2>(c), shl64<1>(c)), e);
+    const long long fifty_c = add64(add64(shl64<5>(c), shl64<4>(c)), shl64<1>(c));
+    const long long t = sub64(add64(shl64<2>(e), e), fifty_c);           // 5 e - 50 c
+    return add64(add64(shl64<2>(t), add64(shl64<2>(k2), shl64<1>(k2))), k3);
   }
   m = c;                      // 2nd order: -2 d c + e; kappa: c
-  return W.w0 == -4 ? e - (c << 2) : e - ((c << 2) + (c << 1));
+  return W.w0 == -4 ? sub64(e, shl64<2>(c)) : sub64(e, add64(shl64<2>(c), shl64<1>(c)));
+}
+
+// the 9/27 neighbour sums of a fixed-point grid at index t (32-bit indices)
+#define FIX_NEIGHBOURS(U)                                                                                       \
+  const long long c = U(0);                                                                                     \
+  long long e, k2 = 0, k3 = 0;                                                                                  \
+  if (g.d == 2) {                                                                                               \
+    e = add64(add64(U(-1), U(1)), add64(U(-n1), U(n1)));                                                        \
+    if (W.w2) k2 = add64(add64(U(-n1 - 1), U(-n1 + 1)), add64(U(n1 - 1), U(n1 + 1)));                           \
+  } else {                                                                                                      \
+    const int s3 = n1 * n1;                                                                                     \
+    e = add64(add64(add64(U(-1), U(1)), add64(U(-n1), U(n1))), add64(U(-s3), U(s3)));                           \
+    if (W.w2)                                                                                                   \
+      k2 = add64(add64(add64(add64(U(-n1 - 1), U(-n1 + 1)), add64(U(n1 - 1), U(n1 + 1))),                       \
+                       add64(add64(U(-s3 - 1), U(-s3 + 1)), add64(U(s3 - 1), U(s3 + 1)))),                      \
+                 add64(add64(U(-s3 - n1), U(-s3 + n1)), add64(U(s3 - n1), U(s3 + n1))));                        \
+    if (W.w3)                                                                                                   \
+      k3 = add64(add64(add64(U(-s3 - n1 - 1), U(-s3 - n1 + 1)), add64(U(-s3 + n1 - 1), U(-s3 + n1 + 1))),       \
+                 add64(add64(U(s3 - n1 - 1), U(s3 - n1 + 1)), add64(U(s3 + n1 - 1), U(s3 + n1 + 1))));          \
+  }
+
+// kc != 0 without an FP64 compare
+__device__ __forceinline__ bool nonzero_d(double x) {
+  return (((unsigned)__double2hiint(x) & 0x7fffffffu) | (unsigned)__double2loint(x)) != 0u;
 }
 
 // r32 = (R_fix - S u_fix + round(kc (kA u + kB sum_edges))) 2^-F / (mult h^2)
@@ -863,35 +1001,22 @@ __global__ void k_res_fix(Grid g, FixStencil W, const long long* __restrict__ R,
     r32[t] = 0.f;
     return;
   }
-  const long long* up = u + t;
-  const long long c = up[0];
-  long long e, k2 = 0, k3 = 0;
-  if (g.d == 2) {
-    e = (up[-1] + up[1]) + (up[-n1] + up[n1]);
-    if (W.w2) k2 = (up[-n1 - 1] + up[-n1 + 1]) + (up[n1 - 1] + up[n1 + 1]);
-  } else {
-    const int s = n1 * n1;
-    e = (up[-1] + up[1]) + (up[-n1] + up[n1]) + (up[-s] + up[s]);
-    if (W.w2)
-      k2 = (up[-n1 - 1] + up[-n1 + 1]) + (up[n1 - 1] + up[n1 + 1]) + (up[-s - 1] + up[-s + 1]) +
-           (up[s - 1] + up[s + 1]) + (up[-s - n1] + up[-s + n1]) + (up[s - n1] + up[s + n1]);
-    if (W.w3)
-      k3 = (up[-s - n1 - 1] + up[-s - n1 + 1]) + (up[-s + n1 - 1] + up[-s + n1 + 1]) +
-           (up[s - n1 - 1] + up[s - n1 + 1]) + (up[s + n1 - 1] + up[s + n1 + 1]);
-  }
+#define UP(o) u[t + (o)]
+  FIX_NEIGHBOURS(UP)
+#undef UP
   long long m;
-  long long r = R[t] - fix_apply(W, c, e, k2, k3, m);
+  long long r = sub64(R[t], fix_apply(W, c, e, k2, k3, m));
   const double kc = fixd[2];
-  if (kc != 0.0) r += __double2ll_rn(kc * (double)m);
+  if (nonzero_d(kc)) r = add64(r, __double2ll_rn(kc * (double)m));
   r32[t] = (ll2f(r) * fixf[2]) * fixf[4];
 }
 
 __global__ void k_unfix(long long tot, const long long* __restrict__ ufix, const double* __restrict__ fixd,
                         double* __restrict__ u) {
   const double isc = fixd[1];
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-       t += (long long)gridDim.x * blockDim.x)
-    u[t] = __ll2double_rn(ufix[t]) * isc;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < (int)tot;
+       t += gridDim.x * blockDim.x)
+    u[t] = ll2d(ufix[t]) * isc;
 }
 
 // u_fix += round(e 2^F) over a grid; max|e| -> corr[0], max|u| -> corr[1]
@@ -900,10 +1025,10 @@ __global__ void k_fix_add(long long tot, const float* __restrict__ e, long long*
   if (skip && *skip) return;
   const float fa = fixf[0], fb = fixf[1], ia = fixf[2], ib = fixf[3];
   float em = 0.f, um = 0.f;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-       t += (long long)gridDim.x * blockDim.x) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < (int)tot;
+       t += gridDim.x * blockDim.x) {
     const float ev = e[t];
-    const long long nv = ufix[t] + f2ll((ev * fa) * fb);
+    const long long nv = add64(ufix[t], f2ll((ev * fa) * fb));
     ufix[t] = nv;
     em = fmaxf(em, fabsf(ev));
     um = fmaxf(um, fabsf((ll2f(nv) * ia) * ib));
@@ -923,8 +1048,8 @@ __global__ void k_absmax32(long long tot, const float* __restrict__ x, unsigned 
                            const int* skip) {
   if (skip && *skip) return;
   float m = 0.f;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-       t += (long long)gridDim.x * blockDim.x)
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < (int)tot;
+       t += gridDim.x * blockDim.x)
     m = fmaxf(m, fabsf(x[t]));
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, (unsigned long long)__double_as_longlong((double)m));
@@ -1602,21 +1727,7 @@ __global__ void k_check_batched(const BoxDesc* __restrict__ D, int ninst) {
 __global__ void k_fix_scale_batched(const BoxDesc* __restrict__ D, int ninst) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ninst) return;
-  const double um = __longlong_as_double((long long)D[i].nrm[5]);
-  int F = 0;
-  if (um > 0.0) F = 52 - (int)ceil(log2(um));
-  F = max(-120, min(F, 240));
-  const int Fa = F / 2, Fb = F - Fa;
-  double* fd = D[i].fixd;
-  float* ff = D[i].fixf;
-  fd[0] = ldexp(D[i].multh2, F);
-  fd[1] = ldexp(1.0, -F);
-  fd[2] = D[i].kc;
-  ff[0] = ldexpf(1.f, Fa);
-  ff[1] = ldexpf(1.f, Fb);
-  ff[2] = ldexpf(1.f, -Fa);
-  ff[3] = ldexpf(1.f, -Fb);
-  ff[4] = (float)(ldexp(1.0, -Fb) / D[i].multh2);
+  fix_scale_body(D[i].nrm + 5, D[i].multh2, D[i].kc, D[i].fixd, D[i].fixf);
 }
 
 // grid kernels over all instances' rows (one row of the last axis per item);
@@ -1641,35 +1752,23 @@ __global__ void k_rows_batched(const BoxDesc* __restrict__ D, const int* __restr
       if (mode == 0) {
         const float* ff = B.fixf;
         B.ufix[t] = f2ll((B.u0[t] * ff[0]) * ff[1]);
-        B.rfix[t] = interior ? __double2ll_rn(B.R[t] * B.fixd[0]) : 0ll;
+        B.rfix[t] = interior ? d2ll_pow2(B.R[t], (int)B.fixd[3]) : 0ll;
       } else if (mode == 2) {
-        B.u[t] = __ll2double_rn(B.ufix[t]) * B.fixd[1];
+        B.u[t] = ll2d(B.ufix[t]) * B.fixd[1];
       } else {
         if (!interior) {
           B.r32[t] = 0.f;
           continue;
         }
-        const long long* up = B.ufix + t;
         const FixStencil W = B.W;
-        const long long c = up[0];
-        long long e, k2 = 0, k3 = 0;
-        if (g.d == 2) {
-          e = (up[-1] + up[1]) + (up[-n1] + up[n1]);
-          if (W.w2) k2 = (up[-n1 - 1] + up[-n1 + 1]) + (up[n1 - 1] + up[n1 + 1]);
-        } else {
-          const int s = n1 * n1;
-          e = (up[-1] + up[1]) + (up[-n1] + up[n1]) + (up[-s] + up[s]);
-          if (W.w2)
-            k2 = (up[-n1 - 1] + up[-n1 + 1]) + (up[n1 - 1] + up[n1 + 1]) + (up[-s - 1] + up[-s + 1]) +
-                 (up[s - 1] + up[s + 1]) + (up[-s - n1] + up[-s + n1]) + (up[s - n1] + up[s + n1]);
-          if (W.w3)
-            k3 = (up[-s - n1 - 1] + up[-s - n1 + 1]) + (up[-s + n1 - 1] + up[-s + n1 + 1]) +
-                 (up[s - n1 - 1] + up[s - n1 + 1]) + (up[s + n1 - 1] + up[s + n1 + 1]);
-        }
+        const long long* ub = B.ufix;
+#define UP(o) ub[t + (o)]
+        FIX_NEIGHBOURS(UP)
+#undef UP
         long long m;
-        long long r = B.rfix[t] - fix_apply(W, c, e, k2, k3, m);
+        long long r = sub64(B.rfix[t], fix_apply(W, c, e, k2, k3, m));
         const double kc = B.fixd[2];
-        if (kc != 0.0) r += __double2ll_rn(kc * (double)m);
+        if (nonzero_d(kc)) r = add64(r, __double2ll_rn(kc * (double)m));
         B.r32[t] = (ll2f(r) * B.fixf[2]) * B.fixf[4];
       }
     }

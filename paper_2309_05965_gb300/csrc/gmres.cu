@@ -315,10 +315,14 @@ __global__ void __launch_bounds__(kCgsThreads) k_cgs_update(double* __restrict__
 
 // Hessenberg column j = h1 + h2, h_{j+1,j} = |V_{j+1}| (from the partials, in a
 // fixed order), Givens update, res = |g_{j+1}|, scal = 1/h_{j+1,j}, j <- j + 1
+// With use_cond (the body of the device-driven loop): the loop continues while
+// res > thr and j + 1 < jdev[2], so it ends after at most jdev[2] iterations
+// whatever the residual (NaN included).
 __global__ void k_cgs_finish(double* __restrict__ H, int ld, double* __restrict__ cs, double* __restrict__ sn,
                              double* __restrict__ g, double* __restrict__ res, const double* __restrict__ h1,
                              const double* __restrict__ h2, const double* __restrict__ part, int npart,
-                             int* __restrict__ jdev, double* __restrict__ scal) {
+                             int* __restrict__ jdev, double* __restrict__ scal, cudaGraphConditionalHandle cond,
+                             int use_cond, const double* __restrict__ thr) {
   __shared__ double ws[32];
   double s = 0.0;
   for (int c = threadIdx.x; c < npart; c += blockDim.x) s += part[c];
@@ -348,6 +352,7 @@ __global__ void k_cgs_finish(double* __restrict__ H, int ld, double* __restrict_
   res[0] = fabs(g[j + 1]);
   scal[0] = 1.0 / hn;
   jdev[0] = j + 1;
+  if (use_cond) cudaGraphSetConditional(cond, (res[0] > thr[0] && j + 1 < jdev[2]) ? 1u : 0u);
 }
 
 // V_j *= scal (j already advanced)
@@ -422,7 +427,8 @@ kfbi_status gmres_create(kfbi_problem* p, int m) {
   KFBI_CUDA(p, dalloc(&G.scal, 8));
   KFBI_CUDA(p, dalloc(&G.hcol, 2 * (m + 1)));
   KFBI_CUDA(p, cudaMallocHost(reinterpret_cast<void**>(&G.host_res), 4 * sizeof(double)));
-  KFBI_CUDA(p, dalloc(&G.jdev, 2));
+  KFBI_CUDA(p, dalloc(&G.jdev, 4));
+  KFBI_CUDA(p, cudaMemset(G.jdev, 0, 4 * sizeof(int)));
   KFBI_CUDA(p, dalloc(&G.h1, m + 1));
   KFBI_CUDA(p, dalloc(&G.h2, m + 1));
   KFBI_CUDA(p, dalloc(&G.npart, 152 * 4));
@@ -443,6 +449,8 @@ void gmres_destroy(kfbi_problem* p) {
   if (G.host_res) cudaFreeHost(G.host_res);
   if (G.it_exec) cudaGraphExecDestroy(G.it_exec);
   if (G.it_graph) cudaGraphDestroy(G.it_graph);
+  if (G.loop_exec) cudaGraphExecDestroy(G.loop_exec);
+  if (G.loop_graph) cudaGraphDestroy(G.loop_graph);
   cudaFree(G.jdev);
   cudaFree(G.h1);
   cudaFree(G.h2);
@@ -468,11 +476,34 @@ static kfbi_status read_scalar(kfbi_problem* p, const double* dev, double* host)
   return KFBI_OK;
 }
 
-// One GMRES iteration of problem p as a graph: x = V_j; y = A x (the operator's
-// kernels); V_{j+1} = y; CGS2 over all SMs; Givens; normalise; j <- j + 1.
-static kfbi_status iteration_graph(kfbi_problem* p) {
+// The kernels of one GMRES iteration of problem p on its stream: x = V_j;
+// y = A x (the operator's kernels); V_{j+1} = y; CGS2 over all SMs; Givens;
+// normalise; j <- j + 1.  With use_cond the finish kernel also sets the
+// condition of the enclosing device-driven loop.
+static kfbi_status iteration_body(kfbi_problem* p, cudaGraphConditionalHandle cond, int use_cond) {
   Gmres& G = p->gm;
-  if (G.it_exec) return KFBI_OK;
+  const int nb = G.nb;
+  const int eb = std::min(div_up(nb, kCgsThreads), 152 * 4);
+  const ArnDesc* d = static_cast<const ArnDesc*>(G.desc);
+  const int* done = G.jdev + 1;
+  KFBI_TRY(batch_arnoldi_copy_in(p, d, G.jdev, done, 1, nb, p->stream));
+  KFBI_TRY(apply_operator_impl(p, p->xbuf, p->ybuf));
+  cudaStream_t cs = p->stream;
+  KFBI_LAUNCH(p, KFBI_KC_GMRES, k_copy_out_batched<<<dim3(div_up(nb, 256), 1), 256, 0, cs>>>(d, G.jdev, done));
+  KFBI_LAUNCH(p, KFBI_KC_GMRES, k_cgs_dots<<<G.m + 1, kCgsThreads, 0, cs>>>(G.V, nb, G.jdev, G.h1));
+  KFBI_LAUNCH(p, KFBI_KC_GMRES, k_cgs_update<<<eb, kCgsThreads, 0, cs>>>(G.V, nb, G.jdev, G.h1, nullptr));
+  KFBI_LAUNCH(p, KFBI_KC_GMRES, k_cgs_dots<<<G.m + 1, kCgsThreads, 0, cs>>>(G.V, nb, G.jdev, G.h2));
+  KFBI_LAUNCH(p, KFBI_KC_GMRES, k_cgs_update<<<eb, kCgsThreads, 0, cs>>>(G.V, nb, G.jdev, G.h2, G.npart));
+  KFBI_LAUNCH(p, KFBI_KC_GMRES, k_cgs_finish<<<1, 256, 0, cs>>>(G.H, G.m + 1, G.cs, G.sn, G.g, G.scal + 2, G.h1,
+                                                                 G.h2, G.npart, eb, G.jdev, G.scal + 3, cond,
+                                                                 use_cond, G.scal + 5));
+  KFBI_LAUNCH(p, KFBI_KC_GMRES, k_cgs_normalize<<<eb, 256, 0, cs>>>(G.V, nb, G.jdev, G.scal + 3));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+static kfbi_status ensure_desc(kfbi_problem* p) {
+  Gmres& G = p->gm;
   if (!p->cap_stream) KFBI_CUDA(p, cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
   if (!G.desc) {
     ArnDesc d{G.V, G.nb, G.m, G.H, G.m + 1, G.cs, G.sn, G.g, G.scal + 2, p->xbuf, p->ybuf};
@@ -481,8 +512,14 @@ static kfbi_status iteration_graph(kfbi_problem* p) {
     KFBI_CUDA(p, cudaMemcpy(dd, &d, sizeof(d), cudaMemcpyHostToDevice));
     G.desc = dd;
   }
-  const int nb = G.nb;
-  const int eb = std::min(div_up(nb, kCgsThreads), 152 * 4);
+  return KFBI_OK;
+}
+
+// Capture iteration_body on the private stream, into `into` when given
+// (cudaStreamBeginCaptureToGraph), else into a new graph returned in *out.
+static kfbi_status capture_body(kfbi_problem* p, cudaGraph_t into, cudaGraph_t* out,
+                                cudaGraphConditionalHandle cond, int use_cond) {
+  Gmres& G = p->gm;
   cudaStream_t st = p->stream;
   KFBI_CUDA(p, cudaStreamSynchronize(st));
   long long before[KFBI_KC_COUNT];
@@ -491,24 +528,10 @@ static kfbi_status iteration_graph(kfbi_problem* p) {
   p->prof.on = false;
   p->stream = p->cap_stream;
   kfbi_status s = KFBI_OK;
-  cudaError_t e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    const ArnDesc* d = static_cast<const ArnDesc*>(G.desc);
-    const int* done = G.jdev + 1;
-    s = batch_arnoldi_copy_in(p, d, G.jdev, done, 1, nb, p->stream);
-    if (s == KFBI_OK) s = apply_operator_impl(p, p->xbuf, p->ybuf);
-    if (s == KFBI_OK) {
-      cudaStream_t cs = p->stream;
-      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_copy_out_batched<<<dim3(div_up(nb, 256), 1), 256, 0, cs>>>(d, G.jdev, done));
-      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_cgs_dots<<<G.m + 1, kCgsThreads, 0, cs>>>(G.V, nb, G.jdev, G.h1));
-      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_cgs_update<<<eb, kCgsThreads, 0, cs>>>(G.V, nb, G.jdev, G.h1, nullptr));
-      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_cgs_dots<<<G.m + 1, kCgsThreads, 0, cs>>>(G.V, nb, G.jdev, G.h2));
-      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_cgs_update<<<eb, kCgsThreads, 0, cs>>>(G.V, nb, G.jdev, G.h2, G.npart));
-      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_cgs_finish<<<1, 256, 0, cs>>>(G.H, G.m + 1, G.cs, G.sn, G.g, G.scal + 2, G.h1,
-                                                                     G.h2, G.npart, eb, G.jdev, G.scal + 3));
-      KFBI_LAUNCH(p, KFBI_KC_GMRES, k_cgs_normalize<<<eb, 256, 0, cs>>>(G.V, nb, G.jdev, G.scal + 3));
-    }
-  }
+  cudaError_t e = into ? cudaStreamBeginCaptureToGraph(p->cap_stream, into, nullptr, nullptr, 0,
+                                                       cudaStreamCaptureModeThreadLocal)
+                       : cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) s = iteration_body(p, cond, use_cond);
   cudaGraph_t gr = nullptr;
   cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(p->cap_stream, &gr) : e;
   p->stream = st;
@@ -518,13 +541,64 @@ static kfbi_status iteration_graph(kfbi_problem* p) {
     p->prof.launches[k] = before[k];
   }
   if (e != cudaSuccess || e2 != cudaSuccess || s != KFBI_OK) {
-    if (gr) cudaGraphDestroy(gr);
+    if (gr && !into) cudaGraphDestroy(gr);
     cudaGetLastError();
     return s != KFBI_OK ? s : fail(p, KFBI_ERR_CUDA, "GMRES iteration capture failed");
   }
+  *out = gr;
+  return KFBI_OK;
+}
+
+// One GMRES iteration of problem p as a graph, replayed once per iteration.
+static kfbi_status iteration_graph(kfbi_problem* p) {
+  Gmres& G = p->gm;
+  if (G.it_exec) return KFBI_OK;
+  KFBI_TRY(ensure_desc(p));
+  cudaGraph_t gr = nullptr;
+  KFBI_TRY(capture_body(p, nullptr, &gr, 0, 0));
   G.it_graph = gr;
   KFBI_CUDA(p, cudaGraphInstantiate(&G.it_exec, gr, 0));
   return KFBI_OK;
+}
+
+// The whole Arnoldi cycle on the device: a conditional WHILE node whose body is
+// one iteration; the finish kernel ends the loop when the residual estimate
+// reaches the threshold or after the iteration limit jdev[2], so the host
+// synchronises once per cycle instead of once per iteration.  Returns false
+// (the caller then replays the single-iteration graph) if the driver refuses
+// conditional nodes.
+static bool loop_graph(kfbi_problem* p) {
+  Gmres& G = p->gm;
+  if (G.loop_exec) return true;
+  if (G.loop_failed) return false;
+  G.loop_failed = true;
+  if (ensure_desc(p) != KFBI_OK) return false;
+  cudaGraph_t g = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
+  cudaGraphConditionalHandle h;
+  cudaGraphNodeParams np = {};
+  cudaGraphNode_t node;
+  bool ok = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  if (ok) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess;
+  }
+  cudaGraph_t body = ok ? np.conditional.phGraph_out[0] : nullptr;
+  cudaGraph_t captured = nullptr;
+  if (ok) ok = capture_body(p, body, &captured, h, 1) == KFBI_OK;
+  if (ok) ok = cudaGraphInstantiate(&G.loop_exec, g, 0) == cudaSuccess;
+  if (!ok) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    G.loop_exec = nullptr;
+    return false;
+  }
+  G.loop_graph = g;
+  G.loop_failed = false;
+  return true;
 }
 
 kfbi_status gmres_run(kfbi_problem* p, const double* b, const double* x0, double rtol, int restart,
@@ -591,11 +665,30 @@ kfbi_status gmres_run(kfbi_problem* p, const double* b, const double* x0, double
     int jend = 0;
     double hres = hbeta;
     const bool graph_it = nb <= kGraphArnoldi && p->use_graphs && !p->prof.on;
-    if (graph_it) {
+    if (graph_it && loop_graph(p)) {
+      // one launch runs the cycle: at most min(m, max_iter - total) iterations
+      const int jmax = std::min(m, max_iter - total);
+      const int head[3] = {0, 0, jmax};
+      const double thr = rtol * bnorm;
+      KFBI_CUDA(p, cudaMemcpyAsync(G.jdev, head, sizeof(head), cudaMemcpyHostToDevice, st));
+      KFBI_CUDA(p, cudaMemcpyAsync(G.scal + 5, &thr, sizeof(double), cudaMemcpyHostToDevice, st));
+      KFBI_CUDA(p, cudaGraphLaunch(G.loop_exec, st));
+      int jdone = 0;
+      KFBI_CUDA(p, cudaMemcpyAsync(G.host_res, res, sizeof(double), cudaMemcpyDeviceToHost, st));
+      KFBI_CUDA(p, cudaMemcpyAsync(&jdone, G.jdev, sizeof(int), cudaMemcpyDeviceToHost, st));
+      KFBI_CUDA(p, cudaStreamSynchronize(st));
+      hres = G.host_res[0];
+      if (jdone < 1 || jdone > jmax) return fail(p, KFBI_ERR_CUDA, "device-driven GMRES loop lost its step count");
+      for (int k = 0; k < KFBI_KC_COUNT; ++k) p->prof.launches[k] += G.it_counts[k] * jdone;
+      total += jdone;
+      jend = jdone;
+      if (!std::isfinite(hres)) return fail(p, KFBI_ERR_NONFINITE, "non-finite GMRES residual");
+    } else if (graph_it) {
       KFBI_TRY(iteration_graph(p));
-      KFBI_CUDA(p, cudaMemsetAsync(G.jdev, 0, 2 * sizeof(int), st));
+      KFBI_CUDA(p, cudaMemsetAsync(G.jdev, 0, 3 * sizeof(int), st));
     }
-    for (int j = 0; j < m; ++j) {
+    const bool stepwise = !(graph_it && G.loop_exec);
+    for (int j = 0; stepwise && j < m; ++j) {
       double* Vj = G.V + (size_t)j * nb;
       double* w = G.V + (size_t)(j + 1) * nb;
       if (graph_it) {

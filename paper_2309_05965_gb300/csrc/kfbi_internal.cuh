@@ -97,13 +97,17 @@ struct Gmres {
   int nchunk = 0;
   // one GMRES iteration (operator + Arnoldi step) as a CUDA graph with the
   // step index on the device, for N_b <= kGraphArnoldi
-  int* jdev = nullptr;          // [0] j, [1] done flag (always 0 here)
+  int* jdev = nullptr;          // [0] j, [1] done flag (always 0 here), [2] iteration limit
   double* h1 = nullptr;         // (m+1)
   double* h2 = nullptr;         // (m+1)
   double* npart = nullptr;      // partial norms (one per CTA of the update)
   void* desc = nullptr;         // ArnDesc of this problem (device)
   cudaGraphExec_t it_exec = nullptr;
   cudaGraph_t it_graph = nullptr;
+  // the whole Arnoldi cycle as a conditional WHILE node around that iteration
+  cudaGraphExec_t loop_exec = nullptr;
+  cudaGraph_t loop_graph = nullptr;
+  bool loop_failed = false;
   long long it_counts[KFBI_KC_COUNT] = {};
 };
 
