@@ -870,7 +870,7 @@ __global__ void __launch_bounds__(128) k_dst32_batched(const PassArgs* __restric
   }
 }
 
-__global__ void k_check(unsigned long long* nrm, double tol, int* conv) {
+__device__ __forceinline__ void check_body(unsigned long long* nrm, double tol, int* conv) {
   if (*conv) return;
   double dm = __longlong_as_double((long long)nrm[3]);
   double um = __longlong_as_double((long long)nrm[4]);
@@ -880,6 +880,8 @@ __global__ void k_check(unsigned long long* nrm, double tol, int* conv) {
   nrm[3] = 0ull;
   nrm[4] = 0ull;
 }
+
+__global__ void k_check(unsigned long long* nrm, double tol, int* conv) { check_body(nrm, tol, conv); }
 
 __global__ void k_zero_flags(unsigned long long* nrm, int* conv) {
   for (int k = 0; k < 6; ++k) nrm[k] = 0ull;
@@ -916,6 +918,13 @@ __device__ __forceinline__ void fix_scale_body(const unsigned long long* __restr
 __global__ void k_fix_scale(const unsigned long long* __restrict__ umax, double multh2, double kc,
                             double* __restrict__ fixd, float* __restrict__ fixf) {
   fix_scale_body(umax, multh2, kc, fixd, fixf);
+}
+
+// the check after the first FP32 solve and the fixed-point scale from its max|u|
+__global__ void k_check_scale(unsigned long long* nrm, double tol, int* conv, double multh2, double kc,
+                              double* __restrict__ fixd, float* __restrict__ fixf) {
+  check_body(nrm, tol, conv);
+  fix_scale_body(nrm + 5, multh2, kc, fixd, fixf);
 }
 
 __global__ void k_fix0(long long tot, const float* __restrict__ u0, const double* __restrict__ R, Grid g,
@@ -1011,8 +1020,10 @@ __global__ void k_res_fix(Grid g, FixStencil W, const long long* __restrict__ R,
   r32[t] = (ll2f(r) * fixf[2]) * fixf[4];
 }
 
+// u = U mult h^2 2^-F; with nrm, the check of the last correction step too
 __global__ void k_unfix(long long tot, const long long* __restrict__ ufix, const double* __restrict__ fixd,
-                        double* __restrict__ u) {
+                        double* __restrict__ u, unsigned long long* nrm, double tol, int* conv) {
+  if (nrm && blockIdx.x == 0 && threadIdx.x == 0) check_body(nrm, tol, conv);
   const double isc = fixd[1];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < (int)tot;
        t += gridDim.x * blockDim.x)
@@ -1370,8 +1381,8 @@ kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u) {
     last.corr_max = B->nrm + 3;
     for (int k = 0; k < P0.npass; ++k) launch_pass<float>(p, P0.args[k], P0.npairs, P0.na, st, P0.pmin[k]);
   }
-  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_check<<<1, 1, 0, st>>>(B->nrm, B->tol, B->conv));
-  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_fix_scale<<<1, 1, 0, st>>>(B->nrm + 5, B->multh2, B->kc, B->fixd, B->fixf));
+  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_check_scale<<<1, 1, 0, st>>>(B->nrm, B->tol, B->conv, B->multh2, B->kc,
+                                                                      B->fixd, B->fixf));
   KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_fix0<<<eb, 256, 0, st>>>(nodes, B->work32, rhs, g, B->fixd, B->fixf,
                                                                  B->ufix, B->rfix));
   float* r32 = reinterpret_cast<float*>(B->res);
@@ -1391,9 +1402,12 @@ kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u) {
     KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_res_fix<<<rgrid, 128, 0, st>>>(g, W, B->rfix, B->ufix, B->fixd, B->fixf,
                                                                          r32, B->conv));
     for (int k = 0; k < PK.npass; ++k) launch_pass<float>(p, PK.args[k], PK.npairs, PK.na, st, PK.pmin[k]);
-    KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_check<<<1, 1, 0, st>>>(B->nrm, B->tol, B->conv));
+    if (it + 1 < B->refine_steps)   // the last step's check runs inside k_unfix
+      KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_check<<<1, 1, 0, st>>>(B->nrm, B->tol, B->conv));
   }
-  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_unfix<<<eb, 256, 0, st>>>(nodes, B->ufix, B->fixd, u));
+  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_unfix<<<eb, 256, 0, st>>>(nodes, B->ufix, B->fixd, u,
+                                                                  B->refine_steps > 1 ? B->nrm : nullptr, B->tol,
+                                                                  B->conv));
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
 }
@@ -1482,7 +1496,7 @@ kfbi_status fix_add(kfbi_problem* p, FixState* F, const float* e, unsigned long 
 kfbi_status fix_out(kfbi_problem* p, FixState* F, double* u, cudaStream_t st) {
   const long long nodes = p->g.nodes();
   const int eb = (int)std::min<long long>(div_up(nodes, 256), 152 * 8);
-  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_unfix<<<eb, 256, 0, st>>>(nodes, F->ufix, F->fixd, u));
+  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_unfix<<<eb, 256, 0, st>>>(nodes, F->ufix, F->fixd, u, nullptr, 0.0, nullptr));
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
 }
