@@ -109,6 +109,27 @@ __device__ __forceinline__ R lam_h2(int d, int order, R kh2, R sp, R sq, R sr) {
   return (R)-4 * s1 + (R)(8.0 / 3.0) * s2 - (R)(4.0 / 3.0) * s3 - kh2 * ((R)1 - s1 / (R)3);
 }
 
+// lambda h^2 = alpha + beta s_k along a line of the fused pass, the other
+// indices' s fixed (sq = s of the slow mode index in 3D, sr = s of the line):
+// the expansions of lam_h2 in s_p = s_k.  alpha < 0 (in 3D -4 (sq + sr)
+// outweighs 8/3 sq sr), and beta > 0 only where beta <= kappa h^2 / 3 <= |alpha|,
+// so alpha + beta s_k does not cancel.
+__device__ __forceinline__ void lam_affine(int d, int order, float kh2, float sq, float sr, float& alpha,
+                                           float& beta) {
+  const float q = d == 2 ? sr : sq + sr;
+  if (order == 2) {
+    alpha = -4.f * q - kh2;
+    beta = -4.f;
+  } else if (d == 2) {
+    alpha = -4.f * sr - kh2 * (1.f - sr / 3.f);
+    beta = -4.f + (8.f / 3.f) * sr + kh2 / 3.f;
+  } else {
+    const float p = sq * sr;
+    alpha = -4.f * q + (8.f / 3.f) * p - kh2 * (1.f - q / 3.f);
+    beta = -4.f + (8.f / 3.f) * q - (4.f / 3.f) * p + kh2 / 3.f;
+  }
+}
+
 __global__ void k_scale_table(int d, int order, int n, double kh2, double gh2,
                               const double* __restrict__ sv, double* __restrict__ out) {
   const long long m = n - 1;
@@ -699,30 +720,31 @@ __device__ __forceinline__ void dst32_body(const PassArgs& A, int bx, int by, Cx
   Cx<float>* s = sm + pr * LP;
   reg_fft<LOGL>(s, tid, tw);
   if (A.fused) {
-    // spectral division in place (Z_{L-k} = -Z_k keeps the odd symmetry), then
-    // the same FFT gives the inverse transform
+    // spectral division in place, then the same FFT gives the inverse
+    // transform.  lambda h^2 is affine in s_k along the line: alpha + beta s_k
+    // with alpha, beta fixed by the line's other mode indices.  Only k < n is
+    // divided; Z_{L-k} = -Z_k is written from it, so the rescaled sequence is
+    // exactly the odd extension of the next input.
     const float kh2 = (float)A.kt, g = (float)A.gscale;
+    const int bA = b0 + 2 * pr, bB = min(bA + 1, nm1);
     const float sa3 = A.d == 3 ? A.s32[a] : 0.f;
-    for (int t = threadIdx.x; t < L * P; t += F::THREADS) {
-      const int q = t >> LOGL, k = t & (L - 1);
-      Cx<float>* zz = sm + q * LP + padi(k);
-      if (k == 0 || k == n) {
-        *zz = {0.f, 0.f};
+    float alA, beA, alB, beB;
+    lam_affine(A.d, A.order, kh2, sa3, A.s32[min(bA, nm1)], alA, beA);
+    lam_affine(A.d, A.order, kh2, sa3, A.s32[bB], alB, beB);
+    const float gA = -0.5f * g, gB = 0.5f * g;
+#pragma unroll
+    for (int i = 0; i < n / F::T; ++i) {
+      const int k = tid + i * F::T;
+      if (k == 0) {
+        s[padi(0)] = {0.f, 0.f};
+        s[padi(n)] = {0.f, 0.f};
         continue;
       }
-      const int km = k < n ? k : L - k;
-      const int bA = b0 + 2 * q, bB = min(bA + 1, nm1);
-      const float sk = A.s32[km];
-      float lA, lB;
-      if (A.d == 2) {
-        lA = lam_h2<float>(2, A.order, kh2, sk, A.s32[min(bA, nm1)], 0.f);
-        lB = lam_h2<float>(2, A.order, kh2, sk, A.s32[bB], 0.f);
-      } else {
-        lA = lam_h2<float>(3, A.order, kh2, sk, sa3, A.s32[min(bA, nm1)]);
-        lB = lam_h2<float>(3, A.order, kh2, sk, sa3, A.s32[bB]);
-      }
-      const Cx<float> Z = *zz;
-      *zz = {__fdividef(g, lA) * (-0.5f * Z.y), __fdividef(g, lB) * (0.5f * Z.x)};
+      const float sk = A.s32[k];
+      const Cx<float> Z = s[padi(k)];
+      const Cx<float> V = {__fdividef(gA, fmaf(beA, sk, alA)) * Z.y, __fdividef(gB, fmaf(beB, sk, alB)) * Z.x};
+      s[padi(k)] = V;
+      s[padi(L - k)] = {-V.x, -V.y};
     }
     __syncthreads();
     reg_fft<LOGL>(s, tid, tw);
