@@ -87,6 +87,10 @@ struct PassArgs {
   long long* dstfix;              // last pass of a refinement step: u_fix += round(delta 2^F)
   const void* twst;               // FP32 path: stage twiddle tables (stage_twiddles)
   const float* fixf;              // [0..1] 2^Fa, 2^Fb; [2..3] 2^-Fa, 2^-Fb (k_fix_scale)
+  const double* fixd;             // [1] mult h^2 2^-F (with uout)
+  double* uout;                   // with dstfix: also u = u_fix mult h^2 2^-F in FP64
+  unsigned long long* zero_nrm;   // first pass of a mixed solve: CTA 0 clears nrm[0..5] and
+  int* zero_conv;                 // the convergence flag before anything reads them
 };
 
 template <typename T>
@@ -512,11 +516,11 @@ std::vector<float> stage_twiddles(int logL) {
 }
 
 // ---- 64-bit fixed-point arithmetic on 32-bit pieces ---------------------------
-// On GB300 the 64-bit integer adds, 64-bit address arithmetic and the
-// integer-to-float conversions run on the FP64 pipe (2 per clock per SM);
-// these helpers keep every step on the 32-bit integer and FP32 pipes: adds
-// with an explicit carry, shifts as funnel shifts, conversions through 16- and
-// 32-bit pieces.
+// On GB300 integer-to-float conversions (and FP64 divides and 64-bit integer
+// divides) issue to the FP64 pipe, 2 per clock per SM; these helpers keep the
+// fixed-point steps on the 32-bit integer and FP32 pipes: adds with an
+// explicit carry, shifts as funnel shifts, conversions through 16- and 32-bit
+// pieces.
 __device__ __forceinline__ void split64(long long v, unsigned& lo, unsigned& hi) {
   asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(v));
 }
@@ -560,9 +564,13 @@ __device__ __forceinline__ long long f2ll(float x) {
 }
 
 // x in [0, 2^16) -> FP32 exactly without a conversion instruction: 2^23 + x
-// has x as its low mantissa bits
+// has x as its low mantissa bits.  The bits go through an inline-asm move:
+// written as a plain bit cast, the compiler folds the subtraction back into
+// an integer-to-float conversion, which issues to the FP64 pipe on GB300.
 __device__ __forceinline__ float u16f(unsigned x) {
-  return __int_as_float(0x4B000000 | (int)x) - 8388608.f;
+  float f;
+  asm("mov.b32 %0, %1;" : "=f"(f) : "r"(0x4B000000u | x));
+  return f - 8388608.f;
 }
 
 // int64 -> FP32 (within 2 ulp) from four 16-bit pieces of |v|
@@ -657,6 +665,10 @@ __device__ __forceinline__ void dst32_body(const PassArgs& A, int bx, int by, Cx
   using F = Reg<LOGL, P>;
   constexpr int L = F::L, LP = F::LP;
   constexpr int n = L / 2, nm1 = n - 1;
+  if (A.zero_nrm && bx == 0 && by == 0 && threadIdx.x == 0) {
+    for (int k = 0; k < 6; ++k) A.zero_nrm[k] = 0ull;
+    *A.zero_conv = 0;
+  }
   const Cx<float>* tw = static_cast<const Cx<float>*>(A.twst);
   const int a = by + 1;
   const int b0 = 1 + 2 * P * bx;
@@ -775,16 +787,19 @@ __device__ __forceinline__ void dst32_body(const PassArgs& A, int bx, int by, Cx
         oldB[it] = (offs[it] >= 0 && hasB[it]) ? A.dstfix[offs[it] + sb] : 0ll;
       }
       const float fa = A.fixf[0], fb = A.fixf[1], ia = A.fixf[2], ib = A.fixf[3];
+      const double isc = A.uout ? A.fixd[1] : 0.0;
 #pragma unroll
       for (int it = 0; it < NIT; ++it) {
         if (offs[it] >= 0) {
           const long long nA = add64(oldA[it], f2ll((vals[it].x * fa) * fb));
           A.dstfix[offs[it]] = nA;
+          if (A.uout) A.uout[offs[it]] = ll2d(nA) * isc;
           dmx = fmaxf(dmx, fabsf(vals[it].x));
           umx = fmaxf(umx, fabsf((ll2f(nA) * ia) * ib));
           if (hasB[it]) {
             const long long nB = add64(oldB[it], f2ll((vals[it].y * fa) * fb));
             A.dstfix[offs[it] + sb] = nB;
+            if (A.uout) A.uout[offs[it] + sb] = ll2d(nB) * isc;
             dmx = fmaxf(dmx, fabsf(vals[it].y));
             umx = fmaxf(umx, fabsf((ll2f(nB) * ia) * ib));
           }
@@ -905,10 +920,6 @@ __device__ __forceinline__ void check_body(unsigned long long* nrm, double tol, 
 
 __global__ void k_check(unsigned long long* nrm, double tol, int* conv) { check_body(nrm, tol, conv); }
 
-__global__ void k_zero_flags(unsigned long long* nrm, int* conv) {
-  for (int k = 0; k < 6; ++k) nrm[k] = 0ull;
-  *conv = 0;
-}
 
 // ---- exact residual of the mixed path (fixed point) -------------------------
 // After the first FP32 solve u0, F is chosen so that max|u0| 2^F ~ 2^52; then
@@ -949,20 +960,26 @@ __global__ void k_check_scale(unsigned long long* nrm, double tol, int* conv, do
   fix_scale_body(nrm + 5, multh2, kc, fixd, fixf);
 }
 
+// u_fix = round(u0 2^F / (mult h^2)), R_fix = round(R 2^F); with u, also the
+// FP64 solution of the fixed-point u_fix (u0 is 0 on the boundary layer)
 __global__ void k_fix0(long long tot, const float* __restrict__ u0, const double* __restrict__ R, Grid g,
                        const double* __restrict__ fixd, const float* __restrict__ fixf,
-                       long long* __restrict__ ufix, long long* __restrict__ rfix) {
+                       long long* __restrict__ ufix, long long* __restrict__ rfix, double* __restrict__ u) {
   const int F = (int)fixd[3];
+  const double isc = fixd[1];
   const float fa = fixf[0], fb = fixf[1];
   const int n1 = g.n + 1;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < (int)tot;
        t += gridDim.x * blockDim.x) {
-    ufix[t] = f2ll((u0[t] * fa) * fb);
-    long long r = t;
+    const long long uf = f2ll((u0[t] * fa) * fb);
+    ufix[t] = uf;
+    if (u) u[t] = ll2d(uf) * isc;
+    int r = t;
     bool interior = true;
     for (int k = 0; k < g.d; ++k) {
-      const int i = (int)(r % n1);
-      r /= n1;
+      const int q = r / n1;
+      const int i = r - q * n1;
+      r = q;
       interior = interior && i >= 1 && i < g.n;
     }
     rfix[t] = interior ? d2ll_pow2(R[t], F) : 0ll;
@@ -1042,10 +1059,9 @@ __global__ void k_res_fix(Grid g, FixStencil W, const long long* __restrict__ R,
   r32[t] = (ll2f(r) * fixf[2]) * fixf[4];
 }
 
-// u = U mult h^2 2^-F; with nrm, the check of the last correction step too
+// u = U mult h^2 2^-F
 __global__ void k_unfix(long long tot, const long long* __restrict__ ufix, const double* __restrict__ fixd,
-                        double* __restrict__ u, unsigned long long* nrm, double tol, int* conv) {
-  if (nrm && blockIdx.x == 0 && threadIdx.x == 0) check_body(nrm, tol, conv);
+                        double* __restrict__ u) {
   const double isc = fixd[1];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < (int)tot;
        t += gridDim.x * blockDim.x)
@@ -1389,13 +1405,18 @@ kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u) {
   }
   // mixed: u0 = DST32^{-1}(R) (FP32, in place in the work grid); fixed-point
   // scale from max|u0|; then repeat { r = R - A_h u exactly (int64 -> FP32);
-  // u += DST32^{-1}(r) } until the correction is below tol max|u|; u out in FP64.
+  // u += DST32^{-1}(r) } until the correction is below tol max|u|.  The FP64
+  // output u is written with u_fix by the conversion kernel and by the last
+  // pass of every correction step, so it is current whichever step the
+  // convergence flag stops at; the check of the last step is left to the
+  // host-side diagnostics (box_last_residual), which read its maxima.
   cudaStream_t st = p->stream;
   const long long nodes = g.nodes();
   const int eb = (int)std::min<long long>(div_up(nodes, 256), 152 * 8);
-  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_zero_flags<<<1, 1, 0, st>>>(B->nrm, B->conv));
   {
-    PassPlan P0 = plan_passes<float>(p, rhs, 1, u, 0, B->conv, B->nrm + 3);
+    PassPlan P0 = plan_passes<float>(p, rhs, 1, u, 0, nullptr, B->nrm + 3);
+    P0.args[0].zero_nrm = B->nrm;
+    P0.args[0].zero_conv = B->conv;
     PassArgs& last = P0.args[P0.npass - 1];
     last.dst = B->work32;
     last.dst64 = 0;
@@ -1406,7 +1427,7 @@ kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u) {
   KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_check_scale<<<1, 1, 0, st>>>(B->nrm, B->tol, B->conv, B->multh2, B->kc,
                                                                       B->fixd, B->fixf));
   KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_fix0<<<eb, 256, 0, st>>>(nodes, B->work32, rhs, g, B->fixd, B->fixf,
-                                                                 B->ufix, B->rfix));
+                                                                 B->ufix, B->rfix, u));
   float* r32 = reinterpret_cast<float*>(B->res);
   PassPlan PK = plan_passes<float>(p, r32, 0, u, 0, B->conv, B->nrm + 3);
   {
@@ -1416,6 +1437,8 @@ kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u) {
     last.accumulate = 1;
     last.dstfix = B->ufix;
     last.fixf = B->fixf;
+    last.fixd = B->fixd;
+    last.uout = u;
     last.corr_max = B->nrm + 3;
   }
   const FixStencil W{B->w[0], B->w[1], B->w[2], B->w[3], B->kA, B->kB};
@@ -1424,12 +1447,9 @@ kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u) {
     KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_res_fix<<<rgrid, 128, 0, st>>>(g, W, B->rfix, B->ufix, B->fixd, B->fixf,
                                                                          r32, B->conv));
     for (int k = 0; k < PK.npass; ++k) launch_pass<float>(p, PK.args[k], PK.npairs, PK.na, st, PK.pmin[k]);
-    if (it + 1 < B->refine_steps)   // the last step's check runs inside k_unfix
+    if (it + 1 < B->refine_steps)
       KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_check<<<1, 1, 0, st>>>(B->nrm, B->tol, B->conv));
   }
-  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_unfix<<<eb, 256, 0, st>>>(nodes, B->ufix, B->fixd, u,
-                                                                  B->refine_steps > 1 ? B->nrm : nullptr, B->tol,
-                                                                  B->conv));
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
 }
@@ -1492,7 +1512,7 @@ kfbi_status fix_init(kfbi_problem* p, FixState* F, const float* u0, const double
   KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_absmax32<<<eb, 256, 0, st>>>(nodes, u0, F->umax, nullptr));
   KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_fix_scale<<<1, 1, 0, st>>>(F->umax, F->multh2, F->kc, F->fixd, F->fixf));
   KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_fix0<<<eb, 256, 0, st>>>(nodes, u0, R, p->g, F->fixd, F->fixf, F->ufix,
-                                                                 F->rfix));
+                                                                 F->rfix, nullptr));
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
 }
@@ -1518,7 +1538,7 @@ kfbi_status fix_add(kfbi_problem* p, FixState* F, const float* e, unsigned long 
 kfbi_status fix_out(kfbi_problem* p, FixState* F, double* u, cudaStream_t st) {
   const long long nodes = p->g.nodes();
   const int eb = (int)std::min<long long>(div_up(nodes, 256), 152 * 8);
-  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_unfix<<<eb, 256, 0, st>>>(nodes, F->ufix, F->fixd, u, nullptr, 0.0, nullptr));
+  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_unfix<<<eb, 256, 0, st>>>(nodes, F->ufix, F->fixd, u));
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
 }
@@ -1534,9 +1554,13 @@ kfbi_status box_last_residual(kfbi_problem* p, double* rel, int* converged) {
     KFBI_CUDA(p, cudaMemcpyAsync(&c, B->conv, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     KFBI_CUDA(p, cudaStreamSynchronize(p->stream));
   }
+  // the device checks every step but the last: with the flag unset after
+  // more than one step, the last step's maxima are still in h[3], h[4]
   double dm, um;
-  memcpy(&dm, &h[2], 8);
-  memcpy(&um, &h[5], 8);
+  const bool last_open = p->cfg.precision == KFBI_MIXED && !c && B->refine_steps > 1;
+  memcpy(&dm, &h[last_open ? 3 : 2], 8);
+  memcpy(&um, &h[last_open ? 4 : 5], 8);
+  if (last_open) c = dm <= B->tol * um ? 1 : 0;
   *rel = um > 0 ? dm / um : 0.0;
   *converged = c;
   return KFBI_OK;

@@ -84,28 +84,29 @@ __global__ void k_coef(int nb, int nc, int npde, int ndir, int nneu, double h,
 }
 
 // R = F + h^2/12 Lap F (order 4) from each node's own side, minus the lift of
-// the outer boundary data, at interior nodes; 0 on the boundary layer.
+// the outer boundary data, at interior nodes; 0 on the boundary layer.  The
+// coefficient divisions are reciprocals from the host and the node indices
+// are 32-bit (grids of up to 1025^3 nodes): FP64 divides and 64-bit integer
+// divides run as long FP64-pipe sequences on GB300.
 __global__ void k_rhs_source(Grid g, int order, const uint8_t* __restrict__ inside,
                              const double* __restrict__ fi, const double* __restrict__ fo,
                              const double* __restrict__ li, const double* __restrict__ lo_,
-                             double si, double so, const double* __restrict__ gb,
+                             double rsi, double rso, double h2_12, const double* __restrict__ gb,
                              const double* __restrict__ nbc, const int8_t* __restrict__ nboff,
                              int nnb, double* __restrict__ R) {
-  long long tot = g.nodes();
-  int n1 = g.n + 1;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-       t += (long long)gridDim.x * blockDim.x) {
+  const int tot = (int)g.nodes();
+  const int n1 = g.n + 1;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
     int idx[3];
-    long long r = t;
     if (g.d == 2) {
-      idx[1] = (int)(r % n1);
-      idx[0] = (int)(r / n1);
+      idx[1] = t % n1;
+      idx[0] = t / n1;
       idx[2] = 1;
     } else {
-      idx[2] = (int)(r % n1);
-      r /= n1;
-      idx[1] = (int)(r % n1);
-      idx[0] = (int)(r / n1);
+      const int r = t / n1;
+      idx[2] = t - r * n1;
+      idx[1] = r % n1;
+      idx[0] = r / n1;
     }
     bool interior = idx[0] >= 1 && idx[0] < g.n && idx[1] >= 1 && idx[1] < g.n &&
                     (g.d == 2 || (idx[2] >= 1 && idx[2] < g.n));
@@ -117,9 +118,9 @@ __global__ void k_rhs_source(Grid g, int order, const uint8_t* __restrict__ insi
     bool in = inside[t] != 0;
     const double* F = in ? fi : fo;
     const double* Lp = in ? li : lo_;
-    double s = in ? si : so;
-    if (F) v = F[t] / s;
-    if (order == 4 && Lp) v = v + g.h * g.h / 12.0 * (Lp[t] / s);
+    const double rs = in ? rsi : rso;
+    if (F) v = F[t] * rs;
+    if (order == 4 && Lp) v = v + h2_12 * (Lp[t] * rs);
     if (gb) {
       bool near = idx[0] == 1 || idx[0] == g.n - 1 || idx[1] == 1 || idx[1] == g.n - 1 ||
                   (g.d == 3 && (idx[2] == 1 || idx[2] == g.n - 1));
@@ -131,7 +132,7 @@ __global__ void k_rhs_source(Grid g, int order, const uint8_t* __restrict__ insi
           bool bnd = q0 == 0 || q0 == g.n || q1 == 0 || q1 == g.n ||
                      (g.d == 3 && (q2 == 0 || q2 == g.n));
           if (!bnd) continue;
-          long long qi = g.d == 2 ? (long long)q0 * n1 + q1 : ((long long)q0 * n1 + q1) * n1 + q2;
+          const int qi = g.d == 2 ? q0 * n1 + q1 : (q0 * n1 + q1) * n1 + q2;
           lift += nbc[k] * gb[qi];
         }
         v = v - lift;
@@ -216,20 +217,18 @@ __global__ void k_trace_op(int nb, TraceCSR tp, TraceCSR tm, const double* __res
 }
 
 __global__ void k_set_boundary(Grid g, const double* __restrict__ gb, double* __restrict__ u) {
-  long long tot = g.nodes();
-  int n1 = g.n + 1;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-       t += (long long)gridDim.x * blockDim.x) {
-    long long r = t;
+  const int tot = (int)g.nodes();
+  const int n1 = g.n + 1;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
     int i2 = 1, i1, i0;
     if (g.d == 2) {
-      i1 = (int)(r % n1);
-      i0 = (int)(r / n1);
+      i1 = t % n1;
+      i0 = t / n1;
     } else {
-      i2 = (int)(r % n1);
-      r /= n1;
-      i1 = (int)(r % n1);
-      i0 = (int)(r / n1);
+      const int r = t / n1;
+      i2 = t - r * n1;
+      i1 = r % n1;
+      i0 = r / n1;
     }
     bool bnd = i0 == 0 || i0 == g.n || i1 == 0 || i1 == g.n ||
                (g.d == 3 && (i2 == 0 || i2 == g.n));
@@ -304,7 +303,7 @@ kfbi_status launch_rhs(kfbi_problem* p, const double* cvals, const kfbi_data* da
     const double* lo_ = p->cfg.kind == KFBI_DIRICHLET_INTERIOR ? nullptr : data->lapf_out;
     double so = p->cfg.kind == KFBI_DIRICHLET_INTERIOR ? 1.0 : p->cfg.sigma_out;
     KFBI_LAUNCH(p, KFBI_KC_RHS, k_rhs_source<<<std::min(div_up(g.nodes(), 256), 152 * 32), 256, 0, p->stream>>>(
-        g, p->cfg.order, p->inside, fi, fo, li, lo_, p->cfg.sigma_in, so,
+        g, p->cfg.order, p->inside, fi, fo, li, lo_, 1.0 / p->cfg.sigma_in, 1.0 / so, g.h * g.h / 12.0,
         p->cfg.kind == KFBI_DIRICHLET_INTERIOR ? nullptr : data->g_b, d_nbc, d_off, p->n_nb, rhs));
     KFBI_CUDA(p, cudaGetLastError());
   } else {
