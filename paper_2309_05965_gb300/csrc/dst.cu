@@ -564,9 +564,9 @@ __device__ __forceinline__ long long f2ll(float x) {
 }
 
 // x in [0, 2^16) -> FP32 exactly without a conversion instruction: 2^23 + x
-// has x as its low mantissa bits.  The bits go through an inline-asm move:
-// written as a plain bit cast, the compiler folds the subtraction back into
-// an integer-to-float conversion, which issues to the FP64 pipe on GB300.
+// has x as its low mantissa bits.  The bits go through an inline-asm move so
+// that the compiler cannot fold the subtraction back into an integer-to-float
+// conversion instruction, which issues to the FP64 pipe on GB300.
 __device__ __forceinline__ float u16f(unsigned x) {
   float f;
   asm("mov.b32 %0, %1;" : "=f"(f) : "r"(0x4B000000u | x));
@@ -788,6 +788,9 @@ __device__ __forceinline__ void dst32_body(const PassArgs& A, int bx, int by, Cx
       }
       const float fa = A.fixf[0], fb = A.fixf[1], ia = A.fixf[2], ib = A.fixf[3];
       const double isc = A.uout ? A.fixd[1] : 0.0;
+      // max|u| for the convergence check from the high words of u_fix alone
+      // (|u_fix| ~ 2^52, so to 2^-20 relative), converted once per thread
+      unsigned umi = 0u;
 #pragma unroll
       for (int it = 0; it < NIT; ++it) {
         if (offs[it] >= 0) {
@@ -795,16 +798,17 @@ __device__ __forceinline__ void dst32_body(const PassArgs& A, int bx, int by, Cx
           A.dstfix[offs[it]] = nA;
           if (A.uout) A.uout[offs[it]] = ll2d(nA) * isc;
           dmx = fmaxf(dmx, fabsf(vals[it].x));
-          umx = fmaxf(umx, fabsf((ll2f(nA) * ia) * ib));
+          umi = max(umi, (unsigned)abs((int)(nA >> 32)));
           if (hasB[it]) {
             const long long nB = add64(oldB[it], f2ll((vals[it].y * fa) * fb));
             A.dstfix[offs[it] + sb] = nB;
             if (A.uout) A.uout[offs[it] + sb] = ll2d(nB) * isc;
             dmx = fmaxf(dmx, fabsf(vals[it].y));
-            umx = fmaxf(umx, fabsf((ll2f(nB) * ia) * ib));
+            umi = max(umi, (unsigned)abs((int)(nB >> 32)));
           }
         }
       }
+      umx = ((fmaf(u16f(umi >> 16), 65536.f, u16f(umi & 0xffffu)) * 4294967296.f) * ia) * ib;
     } else if (A.dst64) {
       double* o = static_cast<double*>(A.dst);
       double oldA[NIT], oldB[NIT];
@@ -1032,6 +1036,12 @@ __device__ __forceinline__ bool nonzero_d(double x) {
   return (((unsigned)__double2hiint(x) & 0x7fffffffu) | (unsigned)__double2loint(x)) != 0u;
 }
 
+// round(kc m), the kappa part of the fixed-point residual.  Not inlined: as an
+// inline branch the compiler evaluates its int64 -> FP64 conversion, product
+// and FP64 -> int64 conversion at every node even when kc = 0, and those
+// three FP64-pipe instructions per node bounded the residual kernel.
+__device__ __noinline__ long long kappa_term(double kc, long long m) { return __double2ll_rn(kc * (double)m); }
+
 // r32 = (R_fix - S u_fix + round(kc (kA u + kB sum_edges))) 2^-F / (mult h^2)
 __global__ void k_res_fix(Grid g, FixStencil W, const long long* __restrict__ R, const long long* __restrict__ u,
                           const double* __restrict__ fixd, const float* __restrict__ fixf,
@@ -1055,7 +1065,7 @@ __global__ void k_res_fix(Grid g, FixStencil W, const long long* __restrict__ R,
   long long m;
   long long r = sub64(R[t], fix_apply(W, c, e, k2, k3, m));
   const double kc = fixd[2];
-  if (nonzero_d(kc)) r = add64(r, __double2ll_rn(kc * (double)m));
+  if (nonzero_d(kc)) r = add64(r, kappa_term(kc, m));
   r32[t] = (ll2f(r) * fixf[2]) * fixf[4];
 }
 
@@ -1073,15 +1083,17 @@ __global__ void k_fix_add(long long tot, const float* __restrict__ e, long long*
                           const float* __restrict__ fixf, unsigned long long* __restrict__ corr, const int* skip) {
   if (skip && *skip) return;
   const float fa = fixf[0], fb = fixf[1], ia = fixf[2], ib = fixf[3];
-  float em = 0.f, um = 0.f;
+  float em = 0.f;
+  unsigned umi = 0u;   // max|u| from the high words of u_fix, as in the DST passes
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < (int)tot;
        t += gridDim.x * blockDim.x) {
     const float ev = e[t];
     const long long nv = add64(ufix[t], f2ll((ev * fa) * fb));
     ufix[t] = nv;
     em = fmaxf(em, fabsf(ev));
-    um = fmaxf(um, fabsf((ll2f(nv) * ia) * ib));
+    umi = max(umi, (unsigned)abs((int)(nv >> 32)));
   }
+  float um = ((fmaf(u16f(umi >> 16), 65536.f, u16f(umi & 0xffffu)) * 4294967296.f) * ia) * ib;
   for (int o = 16; o > 0; o >>= 1) {
     em = fmaxf(em, __shfl_xor_sync(0xffffffffu, em, o));
     um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, o));
@@ -1828,7 +1840,7 @@ __global__ void k_rows_batched(const BoxDesc* __restrict__ D, const int* __restr
         long long m;
         long long r = sub64(B.rfix[t], fix_apply(W, c, e, k2, k3, m));
         const double kc = B.fixd[2];
-        if (nonzero_d(kc)) r = add64(r, __double2ll_rn(kc * (double)m));
+        if (nonzero_d(kc)) r = add64(r, kappa_term(kc, m));
         B.r32[t] = (ll2f(r) * B.fixf[2]) * B.fixf[4];
       }
     }
