@@ -162,9 +162,181 @@ dim3 march_grid(int d, int n) {
   return d == 2 ? dim3(gx, gz, 1) : dim3(gx, (unsigned)(n - 1), gz);
 }
 
+// ---- 3D sweeps ----------------------------------------------------------------
+// First pre-smoothing sweep from a zero iterate: out = omega D^-1 f at the
+// interior nodes (a thread per (y, x) column over kz slices).
+template <typename T>
+__global__ void k_jacobi0_3(Lvl<T> L, T* __restrict__ out, int kz, const int* skip) {
+  if (skip && *skip) return;
+  const int n = L.n, n1 = n + 1, plane = n1 * n1;
+  const int x = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = 1 + blockIdx.y;
+  if (x >= n) return;
+  const int z0 = 1 + blockIdx.z * kz, z1 = min(n, z0 + kz);
+  const T dw = L.dinv_w;
+  for (int z = z0; z < z1; ++z) {
+    const int t = z * plane + y * n1 + x;
+    out[t] = dw * L.f[t];
+  }
+}
+
+// ---- register-blocked 3D sweep ---------------------------------------------
+// A thread owns one x-column and kRB consecutive y-rows and marches along z;
+// no shared memory and no barriers.  Per slice it loads the (kRB + 2) x 3
+// in-plane neighbourhood (rows y-1 .. y+kRB, columns x-1 .. x+1; a warp's
+// load of one row and offset is 32 consecutive words), forms the horizontal
+// pair sums once per row and the slice sums of its kRB rows from them (the
+// grouping of k_march), and keeps the slice sums of three slices in
+// registers.  The next slice's u and f loads are issued before the current
+// slice is computed and stored; f goes through a restrict pointer so that its
+// loads are not held behind the stores to out (with f read through the level
+// struct, each row's f load waited for the previous row's store: 72 against
+// 56 us per 256^3 sweep).  Measured alternatives, all slower at 256^3: a
+// shared-memory tiled sweep (halo tile staged per slice, one barrier per
+// slice; ~110 instructions per point, issue-bound), the same with cp.async
+// staging six slices deep, L2 prefetches ahead of the loads, two-slice-deep
+// register prefetch, 1, 2 or 8 rows per thread and persistent CTAs.
+constexpr int kRB = 4;           // rows per thread
+constexpr int kRX = 32;          // x-columns per CTA
+constexpr int kRY = 4;           // row groups per CTA (CTA = 32 x 16 columns)
+constexpr int kRThreads = kRX * kRY;
+
+template <typename T>
+__global__ void __launch_bounds__(kRThreads, sizeof(T) == 4 ? 6 : 3) k_sweep3r(Lvl<T> L, const T* __restrict__ uin, T* __restrict__ out,
+                                                         int mode, int kz, const int* skip) {
+  if (skip && *skip) return;
+  const int n = L.n, n1 = n + 1, plane = n1 * n1;
+  const int x = 1 + blockIdx.x * kRX + (threadIdx.x % kRX);
+  const int yb = 1 + blockIdx.y * (kRY * kRB) + (threadIdx.x / kRX) * kRB;
+  if (x >= n || yb >= n) return;
+  const int z0 = 1 + blockIdx.z * kz, z1 = min(n, z0 + kz);
+  const T c0 = L.c[0], c1 = L.c[1], c2 = L.c[2], c3 = L.c[3], dw = L.dinv_w;
+  // rows yb - 1 .. yb + kRB (those beyond the grid read as 0)
+  int roff[kRB + 2];
+  bool rok[kRB + 2];
+#pragma unroll
+  for (int r = 0; r < kRB + 2; ++r) {
+    rok[r] = yb - 1 + r <= n;
+    roff[r] = (yb - 1 + r) * n1 + x;
+  }
+  T raw[kRB + 2][3];
+  auto load = [&](int z) {
+    const T* s = uin + z * plane;
+#pragma unroll
+    for (int r = 0; r < kRB + 2; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) raw[r][c] = rok[r] ? s[roff[r] + c - 1] : (T)0;
+  };
+  T mC[kRB], mS1[kRB], mS2[kRB], cC[kRB], cS1[kRB], cS2[kRB];
+  auto sums = [&](T* C, T* S1, T* S2) {
+    T H[kRB + 2];
+#pragma unroll
+    for (int r = 0; r < kRB + 2; ++r) H[r] = raw[r][0] + raw[r][2];
+#pragma unroll
+    for (int r = 0; r < kRB; ++r) {
+      C[r] = raw[r + 1][1];
+      S1[r] = H[r + 1] + (raw[r][1] + raw[r + 2][1]);
+      S2[r] = H[r] + H[r + 2];
+    }
+  };
+  const T* __restrict__ fp = L.f;
+  T fcur[kRB], fnext[kRB];
+  auto loadf = [&](int z, T* dst) {
+    const int tb = z * plane + yb * n1 + x;
+#pragma unroll
+    for (int r = 0; r < kRB; ++r) dst[r] = (yb + r < n) ? fp[tb + r * n1] : (T)0;
+  };
+  loadf(z0, fcur);
+  load(z0 - 1);
+  sums(mC, mS1, mS2);
+  load(z0);
+  sums(cC, cS1, cS2);
+  load(z0 + 1);
+  for (int z = z0; z < z1; ++z) {
+    T qC[kRB], qS1[kRB], qS2[kRB];
+    sums(qC, qS1, qS2);
+    if (z + 1 < z1) {
+      load(z + 2);
+      loadf(z + 1, fnext);
+    }
+    const int t = z * plane + yb * n1 + x;
+#pragma unroll
+    for (int r = 0; r < kRB; ++r) {
+      if (yb + r < n) {
+        const T f = fcur[r];
+        const T au = c0 * cC[r] + c1 * (cS1[r] + mC[r] + qC[r]) + c2 * (cS2[r] + mS1[r] + qS1[r]) +
+                     c3 * (mS2[r] + qS2[r]);
+        out[t + r * n1] = mode == 0 ? cC[r] + dw * (f - au) : f - au;
+      }
+      mC[r] = cC[r];
+      mS1[r] = cS1[r];
+      mS2[r] = cS2[r];
+      cC[r] = qC[r];
+      cS1[r] = qS1[r];
+      cS2[r] = qS2[r];
+      fcur[r] = fnext[r];
+    }
+  }
+}
+
+// slices per thread of the column kernels (k_jacobi0_3, k_prolong3): 16, or
+// fewer where a level has too few columns to fill the GPU
+inline int column_kz(int n) {
+  const long long cols = (long long)div_up(n - 1, 128) * (n - 1);
+  int kz = 16;
+  while (kz > 1 && cols * div_up(n - 1, kz) < 1000) kz >>= 1;
+  return kz;
+}
+
+inline int sweep_r_kz(int n) {
+  const int cols = div_up(n - 1, kRX) * div_up(n - 1, kRY * kRB);
+  int kz = 1;
+  while (kz < 16 && kz < n - 1 && (long long)cols * div_up(n - 1, kz) > 2 * 152 * 6) kz <<= 1;
+  return kz;
+}
+
+// uf += P uc in 3D, a thread per fine (y, x) column marching along z: the
+// in-plane (bi)linear value of coarse slice k serves fine slices 2k - 1, 2k
+// and 2k + 1 (fine slice 2k takes it, 2k + 1 the mean of slices k and k + 1)
+template <typename T>
+__global__ void k_prolong3(int nf, const T* __restrict__ uc, T* __restrict__ uf, int kz, const int* skip) {
+  if (skip && *skip) return;
+  const int nf1 = nf + 1, nc1 = nf / 2 + 1, cplane = nc1 * nc1, plane = nf1 * nf1;
+  const int x = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = 1 + blockIdx.y;
+  if (x >= nf) return;
+  const int z0 = 1 + blockIdx.z * kz, z1 = min(nf, z0 + kz);
+  const int ox = x & 1, oy = y & 1;
+  const int cb = (y >> 1) * nc1 + (x >> 1);
+  const T w = (oy ? (T)0.5 : (T)1) * (ox ? (T)0.5 : (T)1);
+  auto inplane = [&](int k) -> T {
+    const T* c = uc + k * cplane + cb;
+    T s = c[0];
+    if (ox) s += c[1];
+    if (oy) s += ox ? c[nc1] + c[nc1 + 1] : c[nc1];
+    return w * s;
+  };
+  int k = z0 >> 1;
+  T vlo = inplane(k), vhi = inplane(k + 1);
+  T* __restrict__ p = uf + z0 * plane + y * nf1 + x;
+  T cur = p[0];
+  for (int z = z0; z < z1; ++z, p += plane) {
+    const T nxt = z + 1 < z1 ? p[plane] : (T)0;   // issued before this slice's store
+    if ((z >> 1) != k) {
+      k = z >> 1;
+      vlo = vhi;
+      vhi = inplane(k + 1);
+    }
+    const T v = (z & 1) ? (T)0.5 * (vlo + vhi) : vlo;
+    p[0] = cur + v;
+    cur = nxt;
+  }
+}
+
 // ---- per-level transfer kernels: x over the last axis, y (z) over the others ----
 
-// full weighting: weight prod_k w(o_k), w(0) = 1/2, w(+-1) = 1/4
+// full weighting: weight prod_k w(o_k), w(0) = 1/2, w(+-1) = 1/4 (32-bit
+// indices: grids of up to 1025^3 nodes)
 template <typename T>
 __global__ void k_restrict(int d, int nc, const T* __restrict__ rf, T* __restrict__ fc,
                            const int* skip) {
@@ -173,7 +345,7 @@ __global__ void k_restrict(int d, int nc, const T* __restrict__ rf, T* __restric
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i1 = blockIdx.y, i0 = blockIdx.z;
   if (j > nc) return;
-  const long long tc = lin(d, nc1, i0, i1, j);
+  const int tc = d == 2 ? i1 * nc1 + j : (i0 * nc1 + i1) * nc1 + j;
   const bool interior = j >= 1 && j < nc && i1 >= 1 && i1 < nc && (d == 2 || (i0 >= 1 && i0 < nc));
   if (!interior) {
     fc[tc] = (T)0;
@@ -182,19 +354,28 @@ __global__ void k_restrict(int d, int nc, const T* __restrict__ rf, T* __restric
   T acc = (T)0;
   const T w[3] = {(T)0.25, (T)0.5, (T)0.25};
   if (d == 2) {
+    const int base = (2 * i1) * nf1 + 2 * j;
+#pragma unroll
     for (int a = -1; a <= 1; ++a)
-      for (int b = -1; b <= 1; ++b)
-        acc += w[a + 1] * w[b + 1] * rf[lin(2, nf1, 0, 2 * i1 + a, 2 * j + b)];
+#pragma unroll
+      for (int b = -1; b <= 1; ++b) acc += w[a + 1] * w[b + 1] * rf[base + a * nf1 + b];
   } else {
+    const int base = ((2 * i0) * nf1 + 2 * i1) * nf1 + 2 * j;
+    const int pl = nf1 * nf1;
+#pragma unroll
     for (int a = -1; a <= 1; ++a)
+#pragma unroll
       for (int b = -1; b <= 1; ++b)
+#pragma unroll
         for (int c = -1; c <= 1; ++c)
-          acc += w[a + 1] * w[b + 1] * w[c + 1] * rf[lin(3, nf1, 2 * i0 + a, 2 * i1 + b, 2 * j + c)];
+          acc += w[a + 1] * w[b + 1] * w[c + 1] * rf[base + a * pl + b * nf1 + c];
   }
   fc[tc] = acc;
 }
 
-// uf += P uc ((bi/tri)linear interpolation)
+// uf += P uc ((bi/tri)linear interpolation): the coarse neighbours of a fine
+// node are lo = i >> 1 and lo + 1 along each axis with an odd index, weight
+// 1/2 per odd axis; 32-bit indices, the combination loop unrolled
 template <typename T>
 __global__ void k_prolong_add(int d, int nf, const T* __restrict__ uc, T* __restrict__ uf,
                               const int* skip) {
@@ -205,30 +386,31 @@ __global__ void k_prolong_add(int d, int nf, const T* __restrict__ uc, T* __rest
   if (j > nf) return;
   const bool interior = j >= 1 && j < nf && i1 >= 1 && i1 < nf && (d == 2 || (i0 >= 1 && i0 < nf));
   if (!interior) return;
-  const int idx[3] = {i0, i1, j};
-  int lo[3], hi[3];
-  for (int k = 0; k < 3; ++k) {
-    lo[k] = idx[k] >> 1;
-    hi[k] = (idx[k] + 1) >> 1;
-  }
+  const int o0 = d == 3 ? (i0 & 1) : 0, o1 = i1 & 1, o2 = j & 1;
+  T wgt = (T)1;
+  if (o0) wgt *= (T)0.5;
+  if (o1) wgt *= (T)0.5;
+  if (o2) wgt *= (T)0.5;
+  const int base = d == 2 ? (i1 >> 1) * nc1 + (j >> 1) : ((i0 >> 1) * nc1 + (i1 >> 1)) * nc1 + (j >> 1);
+  const int s0 = nc1 * nc1;
   T acc = (T)0;
-  const int k0 = d == 2 ? 1 : 0;
-  const int nc = 1 << (3 - k0);   // 4 (2D) or 8 (3D) corner combinations
-  for (int m = 0; m < nc; ++m) {
-    int ci[3] = {lo[0], lo[1], lo[2]};
-    T wgt = (T)1;
-    bool dup = false;
-    for (int k = k0; k < 3; ++k) {
-      int bit = (m >> (k - k0)) & 1;
-      bool odd = (idx[k] & 1) != 0;
-      if (!odd && bit) dup = true;
-      ci[k] = bit ? hi[k] : lo[k];
-      if (odd) wgt *= (T)0.5;
+  if (d == 2) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int b1 = m & 1, b2 = (m >> 1) & 1;
+      if ((b1 && !o1) || (b2 && !o2)) continue;
+      acc += wgt * uc[base + b1 * nc1 + b2];
     }
-    if (dup) continue;
-    acc += wgt * uc[lin(d, nc1, ci[0], ci[1], ci[2])];
+    uf[i1 * nf1 + j] += acc;
+  } else {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int b0 = m & 1, b1 = (m >> 1) & 1, b2 = (m >> 2) & 1;
+      if ((b0 && !o0) || (b1 && !o1) || (b2 && !o2)) continue;
+      acc += wgt * uc[base + b0 * s0 + b1 * nc1 + b2];
+    }
+    uf[(i0 * nf1 + i1) * nf1 + j] += acc;
   }
-  uf[lin(d, nf1, i0, i1, j)] += acc;
 }
 
 // ---- the coarse part of the V-cycle in one CTA ------------------------------
@@ -562,6 +744,35 @@ dim3 lvl_grid(int d, int n) {
   return dim3((unsigned)div_up(n + 1, 128), (unsigned)(n + 1), d == 3 ? (unsigned)(n + 1) : 1u);
 }
 
+// One smoothing (mode 0) or residual (mode 1) sweep on level L: the tiled
+// kernel in 3D, the marching kernel in 2D (2D levels are L2-resident).
+template <typename T>
+kfbi_status sweep(kfbi_problem* p, int d, const Lvl<T>& L, const T* uin, T* out, int mode, bool zero,
+                  const int* skip, const T* uc = nullptr) {
+  cudaStream_t st = p->stream;
+  if (d == 3) {
+    if (zero) {
+      const int jz = column_kz(L.n);
+      const dim3 jg((unsigned)div_up(L.n - 1, 128), (unsigned)(L.n - 1), (unsigned)div_up(L.n - 1, jz));
+      KFBI_LAUNCH(p, KFBI_KC_MG, k_jacobi0_3<T><<<jg, 128, 0, st>>>(L, out, jz, skip));
+      return KFBI_OK;
+    }
+    if (uc) {   // u += P uc first (the corrected u is then read by the sweep)
+      const int pz = column_kz(L.n);
+      const dim3 pg((unsigned)div_up(L.n - 1, 128), (unsigned)(L.n - 1), (unsigned)div_up(L.n - 1, pz));
+      KFBI_LAUNCH(p, KFBI_KC_MG, k_prolong3<T><<<pg, 128, 0, st>>>(L.n, uc, const_cast<T*>(uin), pz, skip));
+    }
+    const int rz = sweep_r_kz(L.n);
+    const dim3 rg((unsigned)div_up(L.n - 1, kRX), (unsigned)div_up(L.n - 1, kRY * kRB),
+                  (unsigned)div_up(L.n - 1, rz));
+    KFBI_LAUNCH(p, KFBI_KC_MG, k_sweep3r<T><<<rg, kRThreads, 0, st>>>(L, uin, out, mode, rz, skip));
+  } else {
+    KFBI_LAUNCH(p, KFBI_KC_MG, k_march<T><<<march_grid<T>(d, L.n), kMarchX, 0, st>>>(d, L, uin, out, mode,
+                                                                                       zero ? 1 : 0, skip));
+  }
+  return KFBI_OK;
+}
+
 // One V-cycle starting at level 0 of A (u_0 holds the current iterate).
 template <typename T>
 kfbi_status vcycle(kfbi_problem* p, LvlArgs<T>& A, int lcoarse, bool zero_guess, const int* skip) {
@@ -569,13 +780,11 @@ kfbi_status vcycle(kfbi_problem* p, LvlArgs<T>& A, int lcoarse, bool zero_guess,
   cudaStream_t st = p->stream;
   for (int l = 0; l < lcoarse; ++l) {
     Lvl<T>& L = A.L[l];
-    const dim3 gr = lvl_grid<T>(d, L.n);
     const bool zero = (l > 0) || zero_guess;
     // two sweeps u -> t -> u, then the residual into t
-    const dim3 mg_ = march_grid<T>(d, L.n);
-    KFBI_LAUNCH(p, KFBI_KC_MG, k_march<T><<<mg_, kMarchX, 0, st>>>(d, L, L.u, L.t, 0, zero ? 1 : 0, skip));
-    KFBI_LAUNCH(p, KFBI_KC_MG, k_march<T><<<mg_, kMarchX, 0, st>>>(d, L, L.t, L.u, 0, 0, skip));
-    KFBI_LAUNCH(p, KFBI_KC_MG, k_march<T><<<mg_, kMarchX, 0, st>>>(d, L, L.u, L.t, 1, 0, skip));
+    KFBI_TRY(sweep<T>(p, d, L, L.u, L.t, 0, zero, skip));
+    KFBI_TRY(sweep<T>(p, d, L, L.t, L.u, 0, false, skip));
+    KFBI_TRY(sweep<T>(p, d, L, L.u, L.t, 1, false, skip));
     KFBI_LAUNCH(p, KFBI_KC_MG, k_restrict<T><<<lvl_grid<T>(d, A.L[l + 1].n), 128, 0, st>>>(
         d, A.L[l + 1].n, L.t, A.L[l + 1].f, skip));
   }
@@ -583,11 +792,14 @@ kfbi_status vcycle(kfbi_problem* p, LvlArgs<T>& A, int lcoarse, bool zero_guess,
       A, lcoarse, (lcoarse > 0 || zero_guess) ? 1 : 0, skip));
   for (int l = lcoarse - 1; l >= 0; --l) {
     Lvl<T>& L = A.L[l];
-    const dim3 gr = lvl_grid<T>(d, L.n);
-    KFBI_LAUNCH(p, KFBI_KC_MG, k_prolong_add<T><<<gr, 128, 0, st>>>(d, L.n, A.L[l + 1].u, L.u, skip));
-    const dim3 mg_ = march_grid<T>(d, L.n);
-    KFBI_LAUNCH(p, KFBI_KC_MG, k_march<T><<<mg_, kMarchX, 0, st>>>(d, L, L.u, L.t, 0, 0, skip));
-    KFBI_LAUNCH(p, KFBI_KC_MG, k_march<T><<<mg_, kMarchX, 0, st>>>(d, L, L.t, L.u, 0, 0, skip));
+    if (d == 3) {   // prolongation folded into the first post-smoothing sweep
+      KFBI_TRY(sweep<T>(p, d, L, L.u, L.t, 0, false, skip, A.L[l + 1].u));
+    } else {
+      KFBI_LAUNCH(p, KFBI_KC_MG, k_prolong_add<T><<<lvl_grid<T>(d, L.n), 128, 0, st>>>(d, L.n, A.L[l + 1].u, L.u,
+                                                                                       skip));
+      KFBI_TRY(sweep<T>(p, d, L, L.u, L.t, 0, false, skip));
+    }
+    KFBI_TRY(sweep<T>(p, d, L, L.t, L.u, 0, false, skip));
   }
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
