@@ -6,7 +6,8 @@
 //     2^l h (same kappa~);
 //   * smoother: weighted Jacobi, omega = 0.909 (2D) / 1.136 (3D), the values that
 //     minimise the high-frequency amplification of the 9/27-point compact
-//     operators (smoothing factor 0.45 in both);
+//     operators (smoothing factor 0.45 in both); 4/5 and 6/7 for the 2nd-order
+//     5/7-point operators (smoothing factors 0.6 and 5/7);
 //   * full-weighting restriction, (bi/tri)linear prolongation, V(2,2) cycles;
 //   * coarsest level (3^d unknowns) solved exactly with a dense inverse;
 //   * levels with N <= kCoarseN run the rest of the V-cycle inside one CTA
@@ -812,7 +813,10 @@ kfbi_status build_levels(kfbi_problem* p, MgSolver* M, LvlArgs<T>& A, T** cinv, 
   A.d = d;
   A.order = p->cfg.order;
   int n = g.n, l = 0;
-  const double omega = d == 2 ? 0.909 : 1.136;
+  // weighted Jacobi: 0.909 / 1.136 for the compact 9-/27-point operators,
+  // 4/5 / 6/7 for the 5-/7-point ones (at the 27-point value the 7-point
+  // sweep amplifies the highest mode by |1 - 2 omega| > 1)
+  const double omega = A.order == 2 ? (d == 2 ? 0.8 : 6.0 / 7.0) : (d == 2 ? 0.909 : 1.136);
   while (true) {
     if (l >= 16) return fail(p, KFBI_ERR_UNSUPPORTED, "too many multigrid levels");
     Lvl<T>& L = A.L[l];
