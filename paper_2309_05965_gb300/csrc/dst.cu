@@ -1042,11 +1042,13 @@ __device__ __forceinline__ bool nonzero_d(double x) {
 // three FP64-pipe instructions per node bounded the residual kernel.
 __device__ __noinline__ long long kappa_term(double kc, long long m) { return __double2ll_rn(kc * (double)m); }
 
-// r32 = (R_fix - S u_fix + round(kc (kA u + kB sum_edges))) 2^-F / (mult h^2)
+// r32 = (R_fix - S u_fix + round(kc (kA u + kB sum_edges))) 2^-F / (mult h^2).
+// With uout: once the convergence flag is set, this step is skipped and the
+// kernel writes the FP64 solution of u_fix instead (the refinement passes
+// before the last write it only through the last step's final pass).
 __global__ void k_res_fix(Grid g, FixStencil W, const long long* __restrict__ R, const long long* __restrict__ u,
                           const double* __restrict__ fixd, const float* __restrict__ fixf,
-                          float* __restrict__ r32, const int* skip) {
-  if (skip && *skip) return;
+                          float* __restrict__ r32, const int* skip, double* __restrict__ uout) {
   const int n1 = g.n + 1;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i1 = blockIdx.y;
@@ -1054,6 +1056,10 @@ __global__ void k_res_fix(Grid g, FixStencil W, const long long* __restrict__ R,
   if (j > g.n) return;
   // 32-bit offsets: grids of up to 1025^3 nodes
   const int t = g.d == 2 ? i1 * n1 + j : (i0 * n1 + i1) * n1 + j;
+  if (skip && *skip) {
+    if (uout) uout[t] = ll2d(u[t]) * fixd[1];
+    return;
+  }
   const bool interior = j >= 1 && j < g.n && i1 >= 1 && i1 < g.n && (g.d == 2 || (i0 >= 1 && i0 < g.n));
   if (!interior) {
     r32[t] = 0.f;
@@ -1067,6 +1073,54 @@ __global__ void k_res_fix(Grid g, FixStencil W, const long long* __restrict__ R,
   const double kc = fixd[2];
   if (nonzero_d(kc)) r = add64(r, kappa_term(kc, m));
   r32[t] = (ll2f(r) * fixf[2]) * fixf[4];
+}
+
+// The same residual in 2D, a thread per column marching over kResRows rows
+// with a three-row window of centre values and horizontal pair sums (three
+// int64 loads per node instead of nine; integer sums are exact, so the
+// result is identical to k_res_fix's).  Grid: x over the columns 0..N, y over
+// row chunks of 0..N; with uout and the convergence flag set, it writes the
+// FP64 solution at every node instead.
+constexpr int kResRows = 4;
+__global__ void k_res_fix2(Grid g, FixStencil W, const long long* __restrict__ R, const long long* __restrict__ u,
+                           const double* __restrict__ fixd, const float* __restrict__ fixf,
+                           float* __restrict__ r32, const int* skip, double* __restrict__ uout) {
+  const int n = g.n, n1 = n + 1;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j > n) return;
+  const int i0 = blockIdx.y * kResRows, i1 = min(n1, i0 + kResRows);
+  if (skip && *skip) {
+    if (uout)
+      for (int i = i0; i < i1; ++i) uout[i * n1 + j] = ll2d(u[i * n1 + j]) * fixd[1];
+    return;
+  }
+  if (j < 1 || j >= n) return;   // boundary columns of r are never read
+  const int a = max(i0, 1), b = min(i1, n);
+  if (a >= b) return;
+  const double kc = fixd[2];
+  const float f2 = fixf[2], f4 = fixf[4];
+  const long long* p = u + (a - 1) * n1 + j;
+  long long mC = p[0], mH = add64(p[-1], p[1]);
+  p += n1;
+  long long cC = p[0], cH = add64(p[-1], p[1]);
+#pragma unroll
+  for (int k = 0; k < kResRows; ++k) {
+    const int i = a + k;
+    if (i >= b) break;
+    p += n1;
+    const long long qC = p[0], qH = add64(p[-1], p[1]);
+    const long long Ri = R[i * n1 + j];
+    const long long e = add64(cH, add64(mC, qC));   // edge neighbours
+    const long long k2 = add64(mH, qH);             // corners
+    long long m;
+    long long r = sub64(Ri, fix_apply(W, cC, e, k2, 0, m));
+    if (nonzero_d(kc)) r = add64(r, kappa_term(kc, m));
+    r32[i * n1 + j] = (ll2f(r) * f2) * f4;
+    mC = cC;
+    mH = cH;
+    cC = qC;
+    cH = qH;
+  }
 }
 
 // u = U mult h^2 2^-F
@@ -1418,9 +1472,10 @@ kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u) {
   // mixed: u0 = DST32^{-1}(R) (FP32, in place in the work grid); fixed-point
   // scale from max|u0|; then repeat { r = R - A_h u exactly (int64 -> FP32);
   // u += DST32^{-1}(r) } until the correction is below tol max|u|.  The FP64
-  // output u is written with u_fix by the conversion kernel and by the last
-  // pass of every correction step, so it is current whichever step the
-  // convergence flag stops at; the check of the last step is left to the
+  // output u is written once: by the last step's final pass, or, when the
+  // convergence flag stops the refinement earlier, by the next residual
+  // kernel in place of its skipped step (by the conversion kernel when there
+  // is no refinement step).  The check of the last step is left to the
   // host-side diagnostics (box_last_residual), which read its maxima.
   cudaStream_t st = p->stream;
   const long long nodes = g.nodes();
@@ -1439,7 +1494,8 @@ kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u) {
   KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_check_scale<<<1, 1, 0, st>>>(B->nrm, B->tol, B->conv, B->multh2, B->kc,
                                                                       B->fixd, B->fixf));
   KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_fix0<<<eb, 256, 0, st>>>(nodes, B->work32, rhs, g, B->fixd, B->fixf,
-                                                                 B->ufix, B->rfix, u));
+                                                                 B->ufix, B->rfix,
+                                                                 B->refine_steps > 1 ? nullptr : u));
   float* r32 = reinterpret_cast<float*>(B->res);
   PassPlan PK = plan_passes<float>(p, r32, 0, u, 0, B->conv, B->nrm + 3);
   {
@@ -1450,15 +1506,22 @@ kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u) {
     last.dstfix = B->ufix;
     last.fixf = B->fixf;
     last.fixd = B->fixd;
-    last.uout = u;
     last.corr_max = B->nrm + 3;
   }
+  PassPlan PL = PK;   // the last step's final pass also writes the FP64 solution
+  PL.args[PL.npass - 1].uout = u;
   const FixStencil W{B->w[0], B->w[1], B->w[2], B->w[3], B->kA, B->kB};
   const dim3 rgrid((unsigned)div_up(g.n + 1, 128), (unsigned)(g.n + 1), g.d == 3 ? (unsigned)(g.n + 1) : 1u);
+  const dim3 rgrid2((unsigned)div_up(g.n + 1, 128), (unsigned)div_up(g.n + 1, kResRows), 1u);
   for (int it = 1; it < B->refine_steps; ++it) {
-    KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_res_fix<<<rgrid, 128, 0, st>>>(g, W, B->rfix, B->ufix, B->fixd, B->fixf,
-                                                                         r32, B->conv));
-    for (int k = 0; k < PK.npass; ++k) launch_pass<float>(p, PK.args[k], PK.npairs, PK.na, st, PK.pmin[k]);
+    if (g.d == 2)
+      KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_res_fix2<<<rgrid2, 128, 0, st>>>(g, W, B->rfix, B->ufix, B->fixd,
+                                                                            B->fixf, r32, B->conv, u));
+    else
+      KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_res_fix<<<rgrid, 128, 0, st>>>(g, W, B->rfix, B->ufix, B->fixd, B->fixf,
+                                                                           r32, B->conv, u));
+    const PassPlan& P = it + 1 < B->refine_steps ? PK : PL;
+    for (int k = 0; k < P.npass; ++k) launch_pass<float>(p, P.args[k], P.npairs, P.na, st, P.pmin[k]);
     if (it + 1 < B->refine_steps)
       KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_check<<<1, 1, 0, st>>>(B->nrm, B->tol, B->conv));
   }
@@ -1533,7 +1596,7 @@ kfbi_status fix_residual(kfbi_problem* p, FixState* F, float* r32, const int* sk
   const Grid g = p->g;
   const dim3 rgrid((unsigned)div_up(g.n + 1, 128), (unsigned)(g.n + 1), g.d == 3 ? (unsigned)(g.n + 1) : 1u);
   KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_res_fix<<<rgrid, 128, 0, st>>>(g, F->W, F->rfix, F->ufix, F->fixd, F->fixf,
-                                                                       r32, skip));
+                                                                       r32, skip, nullptr));
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
 }
