@@ -9,18 +9,20 @@
 //
 // GB300 design.  A DST-I of length N-1 is a complex FFT of length L = 2N of the
 // odd extension; two real lines are packed as the real and imaginary parts of
-// one complex sequence (Z_k = -2i (A_k + i B_k)).  Each CTA transforms P such
-// pairs in shared memory with a radix-2 FFT:
-//   * edge passes: decimation in frequency (natural in, bit-reversed out);
-//   * the middle pass along the slowest axis: DIF, then the spectral division
-//     by the eigenvalue applied in place in bit-reversed order (the odd
-//     symmetry Z_{L-k} = -Z_k makes the rescaled sequence exactly the odd
-//     extension of the next input), then decimation in time (bit-reversed in,
-//     natural out) — no reordering pass.
-// 2D: 3 passes (axis 1, axis 0 fused, axis 1); 3D: 5 passes.  Each pass reads
-// and writes the grid once.  T = double (FP64 path) or float (mixed path:
-// FP32 transforms, FP64 residual r = R - A_h u and iterative refinement, with a
-// device-side convergence flag so that no host synchronisation is needed).
+// one complex sequence (Z_k = -2i (A_k + i B_k)).  A pass transforms every line
+// of one axis, each CTA P line pairs in shared memory, natural order in and
+// out (self-sorting Stockham FFTs):
+//   * FP64 path (k_dst_pass<double>): radix-4 stages (and one radix-2 stage)
+//     over the shared buffer, FP64-ALU bound on GB300;
+//   * FP32 path (k_dst32<LOGL, P>): a thread owns 16 points per stage,
+//     radix-16 register DFTs, per-stage twiddle tables, a padded buffer.
+// The pass along the slowest axis applies the spectral division in place
+// between the forward and the inverse transform (Z_{L-k} = -Z_k keeps the
+// rescaled sequence the odd extension of the next input), so 2D takes 3
+// passes (axis 1, axis 0 fused, axis 1) and 3D 5; each pass reads and writes
+// the grid once.  The mixed path (FP32 transforms) refines with an exact
+// fixed-point residual r = R - A_h u and a device-side convergence flag, so
+// no host synchronisation is needed.
 #include <cmath>
 #include <cstring>
 #include <mutex>
