@@ -94,3 +94,42 @@ def test_dst_sine_modes_closed_form(d, n, order, precision):
         err = float((u - want).abs().max() / want.abs().max())
         assert err < tol, (modes, err)
     G.close()
+
+
+@pytest.mark.parametrize("d,n,order", [(2, 256, 4), (3, 64, 4)])
+def test_mixed_output_paths(d, n, order):
+    """Where the mixed box solve writes its FP64 output: with no correction
+    step (the conversion kernel), after a refinement that stops early on the
+    convergence flag (the next residual kernel), and for a zero right-hand
+    side (flag set after the first solve: u = 0 exactly, boundary included)."""
+    import torch
+    from paper_2309_05965_gb300 import kfbi
+    R = W.sine_grid_rhs(d, n, 5)
+    w, G1 = _problem(d, n, order, 1)
+    G1.close()
+    ref = BS.dst_solve(R, d, order, w.h, w.kappa)
+    # one FP32 solve, no refinement: FP32-level accuracy
+    G = kfbi.Problem.from_workload(w, precision=kfbi.MIXED, box_max_iters=1)
+    u = empty(G.grid_shape).fill_(7.0)
+    kfbi.kfbi_box_solve(G.handle, dev(R), u)
+    e1 = rel_err(host(u), ref)
+    # one FP32 solve: error ~ eps32 cond(A_h) (cond ~ 0.45 N^2), not refined
+    assert 1e-12 < e1 < 10 * 6e-8 * 0.45 * n * n, e1
+    for ax in range(d):
+        assert np.all(np.take(host(u), [0, n], axis=ax) == 0.0)
+    G.close()
+    # up to 8 steps at tol 1e-13: stops early, the output comes from u_fix
+    G = kfbi.Problem.from_workload(w, precision=kfbi.MIXED, box_max_iters=8)
+    u = empty(G.grid_shape).fill_(7.0)
+    kfbi.kfbi_box_solve(G.handle, dev(R), u)
+    assert rel_err(host(u), ref) < _mixed_tol(n)
+    for ax in range(d):
+        assert np.all(np.take(host(u), [0, n], axis=ax) == 0.0)
+    # zero right-hand side on the same problem: exactly zero
+    u.fill_(7.0)
+    kfbi.kfbi_box_solve(G.handle, torch.zeros(G.grid_shape, dtype=torch.float64, device="cuda"), u)
+    assert float(u.abs().max()) == 0.0
+    # and a normal solve afterwards is unaffected by the converged state
+    kfbi.kfbi_box_solve(G.handle, dev(R), u)
+    assert rel_err(host(u), ref) < _mixed_tol(n)
+    G.close()
