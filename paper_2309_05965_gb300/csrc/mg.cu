@@ -192,7 +192,8 @@ __global__ void k_jacobi0_3(Lvl<T> L, T* __restrict__ out, int kz, const int* sk
 // slice is computed and stored; f goes through a restrict pointer so that its
 // loads are not held behind the stores to out (with f read through the level
 // struct, each row's f load waited for the previous row's store: 72 against
-// 56 us per 256^3 sweep).  Measured alternatives, all slower at 256^3: a
+// 56 us per 256^3 sweep); u through the read-only path and 8-slice z-chunks
+// (51 us, 3.9 TB/s).  Measured alternatives, all slower at 256^3: a
 // shared-memory tiled sweep (halo tile staged per slice, one barrier per
 // slice; ~110 instructions per point, issue-bound), the same with cp.async
 // staging six slices deep, L2 prefetches ahead of the loads, two-slice-deep
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(kRThreads, sizeof(T) == 4 ? 6 : 3) k_sweep3r(L
 #pragma unroll
     for (int r = 0; r < kRB + 2; ++r)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) raw[r][c] = rok[r] ? s[roff[r] + c - 1] : (T)0;
+      for (int c = 0; c < 3; ++c) raw[r][c] = rok[r] ? __ldg(s + roff[r] + c - 1) : (T)0;
   };
   T mC[kRB], mS1[kRB], mS2[kRB], cC[kRB], cS1[kRB], cS2[kRB];
   auto sums = [&](T* C, T* S1, T* S2) {
@@ -292,7 +293,7 @@ inline int column_kz(int n) {
 inline int sweep_r_kz(int n) {
   const int cols = div_up(n - 1, kRX) * div_up(n - 1, kRY * kRB);
   int kz = 1;
-  while (kz < 16 && kz < n - 1 && (long long)cols * div_up(n - 1, kz) > 2 * 152 * 6) kz <<= 1;
+  while (kz < 8 && kz < n - 1 && (long long)cols * div_up(n - 1, kz) > 2 * 152 * 6) kz <<= 1;
   return kz;
 }
 
