@@ -313,9 +313,9 @@ __global__ void k_prolong3(int nf, const T* __restrict__ uc, T* __restrict__ uf,
   const T w = (oy ? (T)0.5 : (T)1) * (ox ? (T)0.5 : (T)1);
   auto inplane = [&](int k) -> T {
     const T* c = uc + k * cplane + cb;
-    T s = c[0];
-    if (ox) s += c[1];
-    if (oy) s += ox ? c[nc1] + c[nc1 + 1] : c[nc1];
+    T s = __ldg(c);
+    if (ox) s += __ldg(c + 1);
+    if (oy) s += ox ? __ldg(c + nc1) + __ldg(c + nc1 + 1) : __ldg(c + nc1);
     return w * s;
   };
   int k = z0 >> 1;
@@ -338,16 +338,17 @@ __global__ void k_prolong3(int nf, const T* __restrict__ uc, T* __restrict__ uf,
 // ---- per-level transfer kernels: x over the last axis, y (z) over the others ----
 
 // full weighting: weight prod_k w(o_k), w(0) = 1/2, w(+-1) = 1/4 (32-bit
-// indices: grids of up to 1025^3 nodes)
+// indices: grids of up to 1025^3 nodes).  Threads run over the nodes of one
+// coarse slice (x fastest), blockIdx.y over the slices (3D).
 template <typename T>
 __global__ void k_restrict(int d, int nc, const T* __restrict__ rf, T* __restrict__ fc,
                            const int* skip) {
   if (skip && *skip) return;
   const int nf1 = 2 * nc + 1, nc1 = nc + 1;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i1 = blockIdx.y, i0 = blockIdx.z;
-  if (j > nc) return;
-  const int tc = d == 2 ? i1 * nc1 + j : (i0 * nc1 + i1) * nc1 + j;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nc1 * nc1) return;
+  const int i1 = q / nc1, j = q - i1 * nc1, i0 = blockIdx.y;
+  const int tc = d == 2 ? q : i0 * nc1 * nc1 + q;
   const bool interior = j >= 1 && j < nc && i1 >= 1 && i1 < nc && (d == 2 || (i0 >= 1 && i0 < nc));
   if (!interior) {
     fc[tc] = (T)0;
@@ -360,7 +361,7 @@ __global__ void k_restrict(int d, int nc, const T* __restrict__ rf, T* __restric
 #pragma unroll
     for (int a = -1; a <= 1; ++a)
 #pragma unroll
-      for (int b = -1; b <= 1; ++b) acc += w[a + 1] * w[b + 1] * rf[base + a * nf1 + b];
+      for (int b = -1; b <= 1; ++b) acc += w[a + 1] * w[b + 1] * __ldg(rf + base + a * nf1 + b);
   } else {
     const int base = ((2 * i0) * nf1 + 2 * i1) * nf1 + 2 * j;
     const int pl = nf1 * nf1;
@@ -370,7 +371,7 @@ __global__ void k_restrict(int d, int nc, const T* __restrict__ rf, T* __restric
       for (int b = -1; b <= 1; ++b)
 #pragma unroll
         for (int c = -1; c <= 1; ++c)
-          acc += w[a + 1] * w[b + 1] * w[c + 1] * rf[base + a * pl + b * nf1 + c];
+          acc += w[a + 1] * w[b + 1] * w[c + 1] * __ldg(rf + base + a * pl + b * nf1 + c);
   }
   fc[tc] = acc;
 }
@@ -787,7 +788,9 @@ kfbi_status vcycle(kfbi_problem* p, LvlArgs<T>& A, int lcoarse, bool zero_guess,
     KFBI_TRY(sweep<T>(p, d, L, L.u, L.t, 0, zero, skip));
     KFBI_TRY(sweep<T>(p, d, L, L.t, L.u, 0, false, skip));
     KFBI_TRY(sweep<T>(p, d, L, L.u, L.t, 1, false, skip));
-    KFBI_LAUNCH(p, KFBI_KC_MG, k_restrict<T><<<lvl_grid<T>(d, A.L[l + 1].n), 128, 0, st>>>(
+    const int nc1 = A.L[l + 1].n + 1;
+    const dim3 rg((unsigned)div_up((long long)nc1 * nc1, 128), d == 3 ? (unsigned)nc1 : 1u);
+    KFBI_LAUNCH(p, KFBI_KC_MG, k_restrict<T><<<rg, 128, 0, st>>>(
         d, A.L[l + 1].n, L.t, A.L[l + 1].f, skip));
   }
   KFBI_LAUNCH(p, KFBI_KC_MG, k_coarse_cycle<T><<<1, 1024, 0, st>>>(
