@@ -103,6 +103,19 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+def job_throughput(local_ms, units_per_rank, world, device="cuda"):
+    """Whole-job throughput of independent replicas: every rank processes
+    units_per_rank units, the slowest rank's time (max over ranks) bounds
+    the job.  Returns (max time in ms, units per second of all ranks)."""
+    total = float(local_ms)
+    if world > 1:
+        import torch
+        t = torch.tensor([total], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+    return total, world * units_per_rank / (total / 1e3)
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -171,13 +184,8 @@ def run_ours(args, rank, world):
         torch.distributed.barrier()
     clk = clocks.stop()
     launches = kfbi.kfbi_launch_counts(G.handle, reset=True)
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, value = job_throughput(sum(times), args.steps, world)
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
 
     # accuracy of the last solve
     ex = W.exact_grid(w, _inside(G, kfbi))
@@ -200,7 +208,7 @@ def run_ours(args, rank, world):
         e1.record(stream)
         e1.synchronize()
         e2e_times.append(e0.elapsed_time(e1))
-    e2e_value = world * len(e2e_times) / (sum(e2e_times) / 1e3)
+    _, e2e_value = job_throughput(sum(e2e_times), len(e2e_times), world)
 
     # ---- box solve alone
     rhs = torch.randn(G.grid_shape, dtype=torch.float64, device="cuda")
