@@ -28,7 +28,8 @@ namespace {
 
 constexpr int kCoarseN2 = 32;   // 2D: levels with N <= 32 run in one CTA
 constexpr int kCoarseN3 = 16;   // 3D
-constexpr int kNu = 2;          // pre- and post-smoothing sweeps
+constexpr int kNu = 2;          // pre- and post-smoothing sweeps (the kernels ping-pong u -> t -> u)
+static_assert(kNu == 2, "the sweeps alternate between u and t");
 
 template <typename T>
 struct Lvl {
@@ -453,14 +454,9 @@ __global__ void k_coarse_cycle(LvlArgs<T> A, int lstart, int start_zero, const i
   for (int l = lstart; l < A.nlev - 1; ++l) {
     const Lvl<T>& L = A.L[l];
     bool zero = l > lstart || start_zero;   // corrections start from zero
-    for (int s = 0; s < kNu; ++s) {
-      blk_jacobi<T>(d, A.order, L, zero && s == 0 ? L.u : L.u, L.t, zero && s == 0);
-      // copy back t -> u
-      const int n1 = L.n + 1;
-      const int tot = d == 2 ? n1 * n1 : n1 * n1 * n1;
-      for (int q = threadIdx.x; q < tot; q += blockDim.x) L.u[q] = L.t[q];
-      __syncthreads();
-    }
+    // two sweeps, u -> t -> u (kNu = 2)
+    blk_jacobi<T>(d, A.order, L, L.u, L.t, zero);
+    blk_jacobi<T>(d, A.order, L, L.t, L.u, false);
     // residual into t, restrict to the next f
     {
       const int n = L.n, n1 = n + 1, m = n - 1;
@@ -549,12 +545,8 @@ __global__ void k_coarse_cycle(LvlArgs<T> A, int lstart, int start_zero, const i
       L.u[lin(d, nf1, i0, i1, j)] += acc;
     }
     __syncthreads();
-    for (int s = 0; s < kNu; ++s) {
-      blk_jacobi<T>(d, A.order, L, L.u, L.t, false);
-      const int tot1 = d == 2 ? nf1 * nf1 : nf1 * nf1 * nf1;
-      for (int q = threadIdx.x; q < tot1; q += blockDim.x) L.u[q] = L.t[q];
-      __syncthreads();
-    }
+    blk_jacobi<T>(d, A.order, L, L.u, L.t, false);   // two sweeps, u -> t -> u (kNu = 2)
+    blk_jacobi<T>(d, A.order, L, L.t, L.u, false);
   }
 }
 
