@@ -1033,54 +1033,56 @@ __device__ __forceinline__ long long fix_apply(const FixStencil& W, long long c,
                  add64(add64(U(s3 - n1 - 1), U(s3 - n1 + 1)), add64(U(s3 + n1 - 1), U(s3 + n1 + 1))));          \
   }
 
-// kc != 0 without an FP64 compare
-__device__ __forceinline__ bool nonzero_d(double x) {
-  return (((unsigned)__double2hiint(x) & 0x7fffffffu) | (unsigned)__double2loint(x)) != 0u;
+
+// round(kc m), the kappa part of the fixed-point residual, in integers:
+// kc = K 2^-S with K the 64-bit left-aligned significand of kc (exact), so
+// kc m is the 128-bit product K |m| scaled by 2^-S and rounded at bit S (round
+// half away from zero).  No FP64 arithmetic: as an int64 -> FP64 conversion,
+// product and conversion back it cost three FP64-pipe instructions per node
+// (~80 us of FP64 pipe per 256^3 sweep), and as an inline FP64 branch the
+// compiler evaluated it even when kc = 0.
+struct KappaFix {
+  unsigned long long K;
+  int S, neg, zero;
+};
+__device__ __forceinline__ KappaFix kappa_fix(double kc) {
+  KappaFix f;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(kc);
+  const int E = (int)((b >> 52) & 0x7ff);
+  f.zero = (b & 0x7fffffffffffffffull) == 0ull || E == 0;
+  f.neg = (int)(b >> 63);
+  f.K = ((b & 0xfffffffffffffull) | 0x10000000000000ull) << 11;
+  f.S = 1086 - E;   // |kc| = K 2^(E - 1086)
+  return f;
+}
+// |kc| < 1 (kappa h^2 scaled by at most 4), so S > 64 and the quotient fits
+__device__ __forceinline__ long long kappa_int(const KappaFix& f, long long m) {
+  if (f.zero || m == 0) return 0ll;
+  const bool mneg = m < 0;
+  const unsigned long long a = mneg ? (unsigned long long)(-m) : (unsigned long long)m;
+  const unsigned long long hi = __umul64hi(a, f.K), lo = a * f.K;
+  const int S = f.S;
+  unsigned long long q;
+  if (S >= 128) {
+    q = 0ull;
+  } else if (S >= 64) {
+    const unsigned long long rb = S - 1 >= 64 ? (hi >> (S - 65)) & 1ull : (lo >> 63) & 1ull;
+    q = (S - 64 >= 64 ? 0ull : hi >> (S - 64)) + rb;
+  } else {
+    const unsigned long long rb = (lo >> (S - 1)) & 1ull;
+    q = ((hi << (64 - S)) | (lo >> S)) + rb;
+  }
+  const long long v = (long long)q;
+  return mneg != (bool)f.neg ? -v : v;
 }
 
-// round(kc m), the kappa part of the fixed-point residual.  Not inlined: as an
-// inline branch the compiler evaluates its int64 -> FP64 conversion, product
-// and FP64 -> int64 conversion at every node even when kc = 0, and those
-// three FP64-pipe instructions per node bounded the residual kernel.
-__device__ __noinline__ long long kappa_term(double kc, long long m) { return __double2ll_rn(kc * (double)m); }
 
-// r32 = (R_fix - S u_fix + round(kc (kA u + kB sum_edges))) 2^-F / (mult h^2).
-// With uout: once the convergence flag is set, this step is skipped and the
-// kernel writes the FP64 solution of u_fix instead (the refinement passes
-// before the last write it only through the last step's final pass).
-__global__ void k_res_fix(Grid g, FixStencil W, const long long* __restrict__ R, const long long* __restrict__ u,
-                          const double* __restrict__ fixd, const float* __restrict__ fixf,
-                          float* __restrict__ r32, const int* skip, double* __restrict__ uout) {
-  const int n1 = g.n + 1;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i1 = blockIdx.y;
-  const int i0 = blockIdx.z;
-  if (j > g.n) return;
-  // 32-bit offsets: grids of up to 1025^3 nodes
-  const int t = g.d == 2 ? i1 * n1 + j : (i0 * n1 + i1) * n1 + j;
-  if (skip && *skip) {
-    if (uout) uout[t] = ll2d(u[t]) * fixd[1];
-    return;
-  }
-  const bool interior = j >= 1 && j < g.n && i1 >= 1 && i1 < g.n && (g.d == 2 || (i0 >= 1 && i0 < g.n));
-  if (!interior) {
-    r32[t] = 0.f;
-    return;
-  }
-#define UP(o) u[t + (o)]
-  FIX_NEIGHBOURS(UP)
-#undef UP
-  long long m;
-  long long r = sub64(R[t], fix_apply(W, c, e, k2, k3, m));
-  const double kc = fixd[2];
-  if (nonzero_d(kc)) r = add64(r, kappa_term(kc, m));
-  r32[t] = (ll2f(r) * fixf[2]) * fixf[4];
-}
-
-// The same residual in 2D, a thread per column marching over kResRows rows
-// with a three-row window of centre values and horizontal pair sums (three
-// int64 loads per node instead of nine; integer sums are exact, so the
-// result is identical to k_res_fix's).  Grid: x over the columns 0..N, y over
+// The exact residual of the mixed box solve,
+//   r32 = (R_fix - S u_fix + round(kc (kA u + kB sum_edges))) 2^-F / (mult h^2),
+// in 2D: a thread per column marching over kResRows rows with a three-row
+// window of centre values and horizontal pair sums (three int64 loads per
+// node instead of nine; integer sums are exact, so the grouping of the
+// stencil sums does not change the result).  Grid: x over the columns 0..N, y over
 // row chunks of 0..N; with uout and the convergence flag set, it writes the
 // FP64 solution at every node instead.
 constexpr int kResRows = 4;
@@ -1099,7 +1101,7 @@ __global__ void k_res_fix2(Grid g, FixStencil W, const long long* __restrict__ R
   if (j < 1 || j >= n) return;   // boundary columns of r are never read
   const int a = max(i0, 1), b = min(i1, n);
   if (a >= b) return;
-  const double kc = fixd[2];
+  const KappaFix kf = kappa_fix(fixd[2]);
   const float f2 = fixf[2], f4 = fixf[4];
   const long long* p = u + (a - 1) * n1 + j;
   long long mC = p[0], mH = add64(p[-1], p[1]);
@@ -1116,12 +1118,138 @@ __global__ void k_res_fix2(Grid g, FixStencil W, const long long* __restrict__ R
     const long long k2 = add64(mH, qH);             // corners
     long long m;
     long long r = sub64(Ri, fix_apply(W, cC, e, k2, 0, m));
-    if (nonzero_d(kc)) r = add64(r, kappa_term(kc, m));
+    if (!kf.zero) r = add64(r, kappa_int(kf, m));
     r32[i * n1 + j] = (ll2f(r) * f2) * f4;
     mC = cC;
     mH = cH;
     cC = qC;
     cH = qH;
+  }
+}
+
+// The same residual in 3D, a thread per x-column and kR3 y-rows marching
+// along z over kz slices, with a three-slice window of int64 slice sums per
+// row (centre C, in-plane edge sum S1, in-plane corner sum S2): the 27-point
+// sums are e = S1 + C(z-1) + C(z+1), k2 = S2 + S1(z-1) + S1(z+1),
+// k3 = S2(z-1) + S2(z+1).  The next slice of u and R is loaded before the
+// current one is computed.  Integer sums are exact, so the grouping does not
+// change the result (checked bit for bit against the one-node 27-point form).  The grid covers every node 0..N per axis: interior nodes get
+// the residual; with uout and the convergence flag set, every node gets u.
+constexpr int kR3 = 2, kR3X = 32, kR3Y = 4, kR3Threads = kR3X * kR3Y;
+__global__ void __launch_bounds__(kR3Threads, 5) k_res_fix3(Grid g, FixStencil W, const long long* __restrict__ R,
+                                                            const long long* __restrict__ u,
+                                                            const double* __restrict__ fixd,
+                                                            const float* __restrict__ fixf, float* __restrict__ r32,
+                                                            const int* skip, double* __restrict__ uout, int kz) {
+  const int n = g.n, n1 = n + 1, plane = n1 * n1;
+  const int x = blockIdx.x * kR3X + (threadIdx.x % kR3X);
+  const int yb = blockIdx.y * (kR3Y * kR3) + (threadIdx.x / kR3X) * kR3;
+  if (x > n || yb > n) return;
+  const int z0 = blockIdx.z * kz, z1 = min(n1, z0 + kz);
+  if (skip && *skip) {
+    if (uout) {
+      const double isc = fixd[1];
+      for (int z = z0; z < z1; ++z)
+#pragma unroll
+        for (int r = 0; r < kR3; ++r)
+          if (yb + r <= n) {
+            const int t = z * plane + (yb + r) * n1 + x;
+            uout[t] = ll2d(u[t]) * isc;
+          }
+    }
+    return;
+  }
+  if (x < 1 || x >= n) return;   // boundary nodes of r are never read
+  const int za = max(z0, 1), zb = min(z1, n);
+  if (za >= zb) return;
+  const KappaFix kf = kappa_fix(fixd[2]);
+  const float f2 = fixf[2], f4 = fixf[4];
+  // rows yb - 1 .. yb + kR3 (outside 0..N read as 0 and feed no output)
+  int roff[kR3 + 2];
+  bool rok[kR3 + 2];
+#pragma unroll
+  for (int r = 0; r < kR3 + 2; ++r) {
+    const int y = yb - 1 + r;
+    rok[r] = y >= 0 && y <= n;
+    roff[r] = y * n1 + x;
+  }
+  bool out_ok[kR3];
+#pragma unroll
+  for (int r = 0; r < kR3; ++r) out_ok[r] = yb + r >= 1 && yb + r < n;
+  long long raw[kR3 + 2][3];
+  auto load = [&](int z) {
+    const long long* s = u + z * plane;
+#pragma unroll
+    for (int r = 0; r < kR3 + 2; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) raw[r][c] = rok[r] ? __ldg(s + roff[r] + c - 1) : 0ll;
+  };
+  long long Rcur[kR3], Rnext[kR3];
+  auto loadR = [&](int z, long long* dst) {
+#pragma unroll
+    for (int r = 0; r < kR3; ++r) dst[r] = out_ok[r] ? __ldg(R + z * plane + roff[r + 1]) : 0ll;
+  };
+  long long mC[kR3], mS1[kR3], mS2[kR3], cC[kR3], cS1[kR3], cS2[kR3];
+  auto sums = [&](long long* C, long long* S1, long long* S2) {
+    long long H[kR3 + 2];
+#pragma unroll
+    for (int r = 0; r < kR3 + 2; ++r) H[r] = add64(raw[r][0], raw[r][2]);
+#pragma unroll
+    for (int r = 0; r < kR3; ++r) {
+      C[r] = raw[r + 1][1];
+      S1[r] = add64(H[r + 1], add64(raw[r][1], raw[r + 2][1]));
+      S2[r] = add64(H[r], H[r + 2]);
+    }
+  };
+  loadR(za, Rcur);
+  load(za - 1);
+  sums(mC, mS1, mS2);
+  load(za);
+  sums(cC, cS1, cS2);
+  load(za + 1);
+  for (int z = za; z < zb; ++z) {
+    long long qC[kR3], qS1[kR3], qS2[kR3];
+    sums(qC, qS1, qS2);
+    if (z + 1 < zb) {
+      load(z + 2);
+      loadR(z + 1, Rnext);
+    }
+    const int tb = z * plane + yb * n1 + x;
+#pragma unroll
+    for (int r = 0; r < kR3; ++r) {
+      if (out_ok[r]) {
+        const long long e = add64(cS1[r], add64(mC[r], qC[r]));
+        const long long k2 = add64(cS2[r], add64(mS1[r], qS1[r]));
+        const long long k3 = add64(mS2[r], qS2[r]);
+        long long m;
+        long long res = sub64(Rcur[r], fix_apply(W, cC[r], e, k2, k3, m));
+        if (!kf.zero) res = add64(res, kappa_int(kf, m));
+        r32[tb + r * n1] = (ll2f(res) * f2) * f4;
+      }
+      mC[r] = cC[r];
+      mS1[r] = cS1[r];
+      mS2[r] = cS2[r];
+      cC[r] = qC[r];
+      cS1[r] = qS1[r];
+      cS2[r] = qS2[r];
+      Rcur[r] = Rnext[r];
+    }
+  }
+}
+
+// launch of the fixed-point residual for the grid's dimension
+void launch_res_fix(kfbi_problem* p, const Grid& g, const FixStencil& W, const long long* R, const long long* u,
+                    const double* fixd, const float* fixf, float* r32, const int* skip, double* uout,
+                    cudaStream_t st) {
+  if (g.d == 2) {
+    const dim3 grid((unsigned)div_up(g.n + 1, 128), (unsigned)div_up(g.n + 1, kResRows), 1u);
+    KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_res_fix2<<<grid, 128, 0, st>>>(g, W, R, u, fixd, fixf, r32, skip, uout));
+  } else {
+    const int kz = 16;
+    const dim3 grid((unsigned)div_up(g.n + 1, kR3X), (unsigned)div_up(g.n + 1, kR3Y * kR3),
+                    (unsigned)div_up(g.n + 1, kz));
+    KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_res_fix3<<<grid, kR3Threads, 0, st>>>(g, W, R, u, fixd, fixf, r32, skip,
+                                                                               uout, kz));
   }
 }
 
@@ -1513,15 +1641,8 @@ kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u) {
   PassPlan PL = PK;   // the last step's final pass also writes the FP64 solution
   PL.args[PL.npass - 1].uout = u;
   const FixStencil W{B->w[0], B->w[1], B->w[2], B->w[3], B->kA, B->kB};
-  const dim3 rgrid((unsigned)div_up(g.n + 1, 128), (unsigned)(g.n + 1), g.d == 3 ? (unsigned)(g.n + 1) : 1u);
-  const dim3 rgrid2((unsigned)div_up(g.n + 1, 128), (unsigned)div_up(g.n + 1, kResRows), 1u);
   for (int it = 1; it < B->refine_steps; ++it) {
-    if (g.d == 2)
-      KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_res_fix2<<<rgrid2, 128, 0, st>>>(g, W, B->rfix, B->ufix, B->fixd,
-                                                                            B->fixf, r32, B->conv, u));
-    else
-      KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_res_fix<<<rgrid, 128, 0, st>>>(g, W, B->rfix, B->ufix, B->fixd, B->fixf,
-                                                                           r32, B->conv, u));
+    launch_res_fix(p, g, W, B->rfix, B->ufix, B->fixd, B->fixf, r32, B->conv, u, st);
     const PassPlan& P = it + 1 < B->refine_steps ? PK : PL;
     for (int k = 0; k < P.npass; ++k) launch_pass<float>(p, P.args[k], P.npairs, P.na, st, P.pmin[k]);
     if (it + 1 < B->refine_steps)
@@ -1596,9 +1717,7 @@ kfbi_status fix_init(kfbi_problem* p, FixState* F, const float* u0, const double
 
 kfbi_status fix_residual(kfbi_problem* p, FixState* F, float* r32, const int* skip, cudaStream_t st) {
   const Grid g = p->g;
-  const dim3 rgrid((unsigned)div_up(g.n + 1, 128), (unsigned)(g.n + 1), g.d == 3 ? (unsigned)(g.n + 1) : 1u);
-  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_res_fix<<<rgrid, 128, 0, st>>>(g, F->W, F->rfix, F->ufix, F->fixd, F->fixf,
-                                                                       r32, skip, nullptr));
+  launch_res_fix(p, g, F->W, F->rfix, F->ufix, F->fixd, F->fixf, r32, skip, nullptr, st);
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
 }
@@ -1904,8 +2023,8 @@ __global__ void k_rows_batched(const BoxDesc* __restrict__ D, const int* __restr
 #undef UP
         long long m;
         long long r = sub64(B.rfix[t], fix_apply(W, c, e, k2, k3, m));
-        const double kc = B.fixd[2];
-        if (nonzero_d(kc)) r = add64(r, kappa_term(kc, m));
+        const KappaFix kf = kappa_fix(B.fixd[2]);
+        if (!kf.zero) r = add64(r, kappa_int(kf, m));
         B.r32[t] = (ll2f(r) * B.fixf[2]) * B.fixf[4];
       }
     }
