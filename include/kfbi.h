@@ -75,8 +75,10 @@ typedef struct {
 
 typedef struct {
   int dim;                /* 2 or 3                                               */
-  int n;                  /* intervals per axis N (power of two, 16..2048 in 2D,
-                             16..512 in 3D)                                       */
+  int n;                  /* intervals per axis N, a power of two: DST box solve
+                             2D 8..2048 (FP64) / 8..4096 (mixed), 3D 8..1024
+                             within device memory; multigrid from 8.  Larger
+                             sizes: KFBI_ERR_UNSUPPORTED at create          */
   double lo, hi;          /* box [lo, hi]^dim                                     */
   int order;              /* 4 (compact 9/27-point) or 2 (5/7-point)              */
   int kind;               /* kfbi_problem_kind                                    */

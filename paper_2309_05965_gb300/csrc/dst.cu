@@ -1540,9 +1540,16 @@ kfbi_status box_create(kfbi_problem* p) {
   int dev = 0, optin = 0;
   KFBI_CUDA(p, cudaGetDevice(&dev));
   KFBI_CUDA(p, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if ((size_t)optin < sizeof(Cx<double>) * (size_t)(2 * n) * 2 * std::max(1, 1024 / (2 * n)) ||
-      (size_t)optin < sizeof(Cx<float>) * (size_t)(2 * n) * 2 * std::max(2, 1024 / (2 * n)))
-    return fail(p, KFBI_ERR_UNSUPPORTED, "N too large for the shared-memory DST on this device");
+  // shared memory per CTA: the FP64 passes hold two length-2N buffers per
+  // line pair; the FP32 register passes one padded buffer per pair
+  const size_t need = p->cfg.precision == KFBI_MIXED
+                          ? sizeof(Cx<float>) * (size_t)reg_pairs(B->logL) * (size_t)(2 * n + (2 * n) / 16)
+                          : sizeof(Cx<double>) * (size_t)(2 * n) * 2 * std::max(1, 1024 / (2 * n));
+  if ((size_t)optin < need)
+    return fail(p, KFBI_ERR_UNSUPPORTED,
+                p->cfg.precision == KFBI_MIXED ? "N too large for the shared-memory DST on this device"
+                                               : "N too large for the FP64 shared-memory DST on this device "
+                                                 "(2D: N <= 2048; the mixed path goes to 4096)");
   KFBI_CUDA(p, (set_smem<double, 1>(optin)));
   KFBI_CUDA(p, (set_smem<double, 2>(optin)));
   KFBI_CUDA(p, (set_smem<double, 4>(optin)));

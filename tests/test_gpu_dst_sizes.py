@@ -133,3 +133,47 @@ def test_mixed_output_paths(d, n, order):
     kfbi.kfbi_box_solve(G.handle, dev(R), u)
     assert rel_err(host(u), ref) < _mixed_tol(n)
     G.close()
+
+
+def test_largest_2d_grid():
+    """N = 4096 in 2D (transform length 8192, the largest the library takes):
+    the FP64 passes' shared memory does not fit a CTA, so FP64 is refused at
+    create; the mixed path (one padded FP32 buffer per line pair) runs.  At
+    this size eps32 cond(A_h) ~ 0.45, so its refinement converges slowly for
+    high modes; low modes, whose FP32 solve is accurate, are reproduced in
+    closed form."""
+    import torch
+    from paper_2309_05965_gb300 import build, kfbi
+    build.build()
+    n = 4096
+    w = W.Workload("box", 2, n, -1.0, 1.0, W.LS_ELLIPSE, [0.0, 0.0, 0.7, 0.6, 0.0],
+                   W.KIND_DIRICHLET, kappa=1.0, exact="exp_sin")
+    with pytest.raises(kfbi.KfbiError) as e:
+        kfbi.Problem.from_workload(w, precision=kfbi.FP64)
+    assert e.value.status == 8
+    G = kfbi.Problem.from_workload(w, precision=kfbi.MIXED, box_max_iters=8)
+    for modes in ([1, 1], [3, 2], [5, 1]):
+        R = torch.ones(G.grid_shape, dtype=torch.float64, device="cuda")
+        for k, p in enumerate(modes):
+            shape = [1, 1]
+            shape[k] = n + 1
+            arg = torch.remainder(p * torch.arange(n + 1, device="cuda"), 2 * n).double()
+            R = R * torch.sin(np.pi * arg / n).reshape(shape)
+        lam = _symbol(2, 4, n, w.h, w.kappa, modes)
+        u = empty(G.grid_shape)
+        kfbi.kfbi_box_solve(G.handle, R.contiguous(), u)
+        err = float((u - R / lam).abs().max() / (R / lam).abs().max())
+        assert err < 1e-9, (modes, err)
+    # a high mode: bounded and finite (slow refinement, see above)
+    R = torch.ones(G.grid_shape, dtype=torch.float64, device="cuda")
+    for k, p in enumerate([n - 1, n // 2 + 1]):
+        shape = [1, 1]
+        shape[k] = n + 1
+        arg = torch.remainder(p * torch.arange(n + 1, device="cuda"), 2 * n).double()
+        R = R * torch.sin(np.pi * arg / n).reshape(shape)
+    lam = _symbol(2, 4, n, w.h, w.kappa, [n - 1, n // 2 + 1])
+    u = empty(G.grid_shape)
+    kfbi.kfbi_box_solve(G.handle, R.contiguous(), u)
+    assert bool(torch.isfinite(u).all())
+    assert float((u - R / lam).abs().max() / (R / lam).abs().max()) < 0.1
+    G.close()
