@@ -420,7 +420,8 @@ def batched(args, stream, flush):
            "max_err_vs_exact": max(errs), "max_err_ratio_vs_fp64": max(ratio),
            "max_err_ratio_mixed_sequential_vs_fp64": max(e / max(e64, 1e-300)
                                                          for e, e64 in zip(errs_mixed, errs64)),
-           "fp64_max_err_vs_exact": max(errs64)}
+           "fp64_max_err_vs_exact": max(errs64),
+           "tuned_tiles": dict(zip(("pass_ctas", "row_ctas"), B.tiles()))}
     B.close()
     for r in rows:
         r["G"].close()
@@ -634,7 +635,7 @@ def _inside(G, kfbi):
 
 def roofline(args, G, prof, prec):
     """Roofline of the dominant kernel class from the profiling pass.
-    Algorithmic bytes / flops per unit are stated in the design doc."""
+    Algorithmic bytes per interior point are counted below, pass by pass."""
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     name = max(prof, key=lambda k: prof[k][0])

@@ -242,8 +242,17 @@ kfbi_status kfbi_evaluate(kfbi_problem* p, const kfbi_data* data, const double* 
  * problems[0]).  problems: host array of count handles; *out receives the
  * batch (NULL on failure). */
 typedef struct kfbi_batch kfbi_batch;
+/* Creation also tunes the launch shapes of the batched box solve on the
+ * batch's own grids (kfbi_batch_tiles) and synchronises the stream. */
 kfbi_status kfbi_create_batch(kfbi_problem* const* problems, int count, kfbi_batch** out);
 kfbi_status kfbi_destroy_batch(kfbi_batch* batch);
+/* The launch shapes the autotuner picked at kfbi_create_batch: the CTA count
+ * of the persistent FP32 transform pass (half, once or twice the CTAs the GPU
+ * holds at once) and of the fixed-point row kernel (4, 8, 16 or 32 per SM),
+ * each the fastest of its candidates in timed batched box solves with a
+ * synthetic right-hand side.  The shapes only distribute work items; results
+ * do not depend on them.  Host integers out; KFBI_ERR_ARG on NULL. */
+kfbi_status kfbi_batch_tiles(const kfbi_batch* batch, int* pass_ctas, int* row_ctas);
 /* Algorithm 1 for every instance k from a zero start: data[k] (host array of
  * count kfbi_data with device pointers as in kfbi_gmres_solve), densities[k]
  * (host array of count device pointers, N_b of instance k each, written),

@@ -72,6 +72,12 @@ kfbi_status kfbi_destroy_batch(kfbi_batch* b) {
   return KFBI_OK;
 }
 
+kfbi_status kfbi_batch_tiles(const kfbi_batch* b, int* pass_ctas, int* row_ctas) {
+  if (!b || !pass_ctas || !row_ctas) return KFBI_ERR_ARG;
+  batch_box_tiles(b->bb, pass_ctas, row_ctas);
+  return KFBI_OK;
+}
+
 kfbi_status kfbi_create_batch(kfbi_problem* const* problems, int count, kfbi_batch** out) {
   if (!out || !problems || count < 1) return KFBI_ERR_ARG;
   *out = nullptr;
@@ -124,6 +130,18 @@ kfbi_status kfbi_create_batch(kfbi_problem* const* problems, int count, kfbi_bat
     return bail(fail(p0, KFBI_ERR_CUDA, "out of memory"));
   if (cudaMemcpy(b->darn, ad.data(), sizeof(ArnDesc) * count, cudaMemcpyHostToDevice) != cudaSuccess)
     return bail(fail(p0, KFBI_ERR_CUDA, "descriptor upload failed"));
+  // pick the box solve's launch shapes for this batch (before the capture,
+  // which records them), every instance active
+  if (cudaMemset(b->done, 0, sizeof(int) * count) != cudaSuccess)
+    return bail(fail(p0, KFBI_ERR_CUDA, "memset failed"));
+  {
+    // the tuning solves are set-up work: no per-launch timing events for them
+    const bool prof_on = p0->prof.on;
+    p0->prof.on = false;
+    s = batch_box_autotune(p0, b->bb, b->ps.data(), b->rhs_loop.data(), b->done, b->stream);
+    p0->prof.on = prof_on;
+    if (s != KFBI_OK) return bail(s);
+  }
   // capture one iteration of all instances
   if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
     return bail(fail(p0, KFBI_ERR_CUDA, "stream creation failed"));

@@ -2116,6 +2116,84 @@ kfbi_status batch_box_create(kfbi_problem* p0, kfbi_problem* const* ps, int nins
   return KFBI_OK;
 }
 
+namespace {
+// a deterministic non-zero right-hand side for timing (values in [-0.5, 0.5))
+__global__ void k_fill_pattern(long long tot, double* __restrict__ R) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x)
+    R[t] = (double)((unsigned)(t * 2654435761ull) % 1000u) * 1e-3 - 0.5;
+}
+}  // namespace
+
+// Autotuner of the batched box solve's launch shapes: the CTA count of the
+// persistent transform pass (half, once or twice the CTAs resident on the
+// GPU) and of the row kernel (4, 8, 16 or 32 CTAs per SM), each timed on the
+// batch's own grids (a synthetic right-hand side, one warm-up and two timed
+// box solves per candidate, CUDA events) and the fastest kept.  The shapes
+// change only how the work items are spread, not the arithmetic.  rhs is
+// zeroed again afterwards.
+kfbi_status batch_box_autotune(kfbi_problem* p0, BatchBox* bb, kfbi_problem* const* ps, double* const* rhs,
+                               const int* done, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  KFBI_CUDA(p0, cudaGetDevice(&dev));
+  KFBI_CUDA(p0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  for (int i = 0; i < bb->ninst; ++i) {
+    const long long tot = ps[i]->g.nodes();
+    k_fill_pattern<<<std::min(div_up(tot, 256), 8 * sms), 256, 0, st>>>(tot, rhs[i]);
+  }
+  KFBI_CUDA(p0, cudaGetLastError());
+  cudaEvent_t e0, e1;
+  KFBI_CUDA(p0, cudaEventCreate(&e0));
+  KFBI_CUDA(p0, cudaEventCreate(&e1));
+  auto time_solve = [&](float* ms) -> kfbi_status {
+    KFBI_TRY(batch_box_solve(p0, bb, done, st));
+    KFBI_CUDA(p0, cudaEventRecord(e0, st));
+    for (int r = 0; r < 2; ++r) KFBI_TRY(batch_box_solve(p0, bb, done, st));
+    KFBI_CUDA(p0, cudaEventRecord(e1, st));
+    KFBI_CUDA(p0, cudaEventSynchronize(e1));
+    KFBI_CUDA(p0, cudaEventElapsedTime(ms, e0, e1));
+    return KFBI_OK;
+  };
+  const int resident = bb->grid;   // batch_box_create: SMs x resident CTAs per SM
+  kfbi_status s = KFBI_OK;
+  float best = 1e30f;
+  int best_grid = resident;
+  for (int g : {std::max(1, resident / 2), resident, 2 * resident}) {
+    bb->grid = g;
+    float ms = 0.f;
+    if ((s = time_solve(&ms)) != KFBI_OK) break;
+    if (ms < best) {
+      best = ms;
+      best_grid = g;
+    }
+  }
+  bb->grid = best_grid;
+  best = 1e30f;
+  int best_rgrid = 8 * sms;
+  for (int per : {4, 8, 16, 32}) {
+    if (s != KFBI_OK) break;
+    bb->rgrid = per * sms;
+    float ms = 0.f;
+    if ((s = time_solve(&ms)) != KFBI_OK) break;
+    if (ms < best) {
+      best = ms;
+      best_rgrid = per * sms;
+    }
+  }
+  bb->rgrid = best_rgrid;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int i = 0; i < bb->ninst; ++i)
+    KFBI_CUDA(p0, cudaMemsetAsync(rhs[i], 0, sizeof(double) * ps[i]->g.nodes(), st));
+  KFBI_CUDA(p0, cudaStreamSynchronize(st));
+  return s;
+}
+
+void batch_box_tiles(const BatchBox* bb, int* pass_ctas, int* row_ctas) {
+  *pass_ctas = bb->grid;
+  *row_ctas = bb->rgrid;
+}
+
 void batch_box_destroy(BatchBox* bb) {
   if (!bb) return;
   cudaFree(bb->dargs);

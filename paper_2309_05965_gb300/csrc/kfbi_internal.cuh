@@ -309,6 +309,9 @@ struct BatchHot;
 kfbi_status batch_box_create(kfbi_problem* p0, kfbi_problem* const* ps, int ninst,
                              double* const* rhs, BatchBox** out);
 void batch_box_destroy(BatchBox* bb);
+kfbi_status batch_box_autotune(kfbi_problem* p0, BatchBox* bb, kfbi_problem* const* ps, double* const* rhs,
+                               const int* done, cudaStream_t st);
+void batch_box_tiles(const BatchBox* bb, int* pass_ctas, int* row_ctas);
 kfbi_status batch_box_solve(kfbi_problem* p0, BatchBox* bb, const int* done, cudaStream_t st);
 // hotpath.cu
 kfbi_status batch_hot_create(kfbi_problem* p0, kfbi_problem* const* ps, int ninst, double* const* x,

@@ -89,6 +89,7 @@ SIGNATURES = {
     "kfbi_evaluate": [_P, ctypes.POINTER(Data), _P, _P],
     "kfbi_create_batch": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)],
     "kfbi_destroy_batch": [_P],
+    "kfbi_batch_tiles": [_P, _I, _I],
     "kfbi_gmres_solve_batch": [_P, _P, ctypes.POINTER(GmresOpts), _P, _P],
     "kfbi_mlp_create": [ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_void_p)],
     "kfbi_mlp_destroy": [_P],
@@ -264,6 +265,13 @@ def kfbi_destroy_batch(b):
     _check(load().kfbi_destroy_batch(b))
 
 
+def kfbi_batch_tiles(b):
+    """(pass_ctas, row_ctas): the launch shapes chosen when the batch was created."""
+    pc, rc = ctypes.c_int(), ctypes.c_int()
+    _check(load().kfbi_batch_tiles(b, ctypes.byref(pc), ctypes.byref(rc)))
+    return pc.value, rc.value
+
+
 def kfbi_gmres_solve_batch(b, handles, datas, opts: GmresOpts, densities):
     """Algorithm 1 for every instance; returns one GmresInfo per instance."""
     n = len(handles)
@@ -426,6 +434,9 @@ class Batch:
     def gmres_solve(self, datas, opts: GmresOpts, densities):
         return kfbi_gmres_solve_batch(self.handle, [q.handle for q in self.problems], datas, opts,
                                       densities)
+
+    def tiles(self):
+        return kfbi_batch_tiles(self.handle)
 
     def close(self):
         if self.handle is not None:

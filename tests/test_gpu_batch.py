@@ -130,3 +130,34 @@ def test_batch_edge_cases():
         kfbi.Batch([r0["G"], G64])
     assert e.value.status == 8
     G64.close()
+
+
+def test_batch_tiles():
+    """The launch shapes tuned at batch creation are among the candidates
+    (transform pass: half, once or twice the resident CTAs; row kernel: 4, 8,
+    16 or 32 CTAs per SM).  The shapes only spread work items, so a second
+    batch over the same problems gives bit-identical densities, and the tuning
+    solves (which run on the instances' own buffers) leave a single-instance
+    solve afterwards bit-identical to one before."""
+    import torch
+    from paper_2309_05965_gb300 import kfbi
+    rows = _setup()[:3]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    opts = kfbi.GmresOpts(rtol=1e-10, restart=100, max_iter=100, x0=None)
+    x0 = empty(rows[0]["G"].nb)
+    kfbi.kfbi_gmres_solve(rows[0]["G"].handle, rows[0]["d"], opts, x0)
+    out = []
+    for _ in range(2):
+        B = kfbi.Batch([r["G"] for r in rows])
+        pass_ctas, row_ctas = B.tiles()
+        assert pass_ctas > 0 and (2 * pass_ctas) % sms == 0, pass_ctas
+        assert row_ctas % sms == 0 and row_ctas // sms in (4, 8, 16, 32), row_ctas
+        dens = [empty(r["G"].nb) for r in rows]
+        B.gmres_solve([r["d"] for r in rows], opts, dens)
+        out.append([host(x) for x in dens])
+        B.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+    x1 = empty(rows[0]["G"].nb)
+    kfbi.kfbi_gmres_solve(rows[0]["G"].handle, rows[0]["d"], opts, x1)
+    assert np.array_equal(host(x0), host(x1))

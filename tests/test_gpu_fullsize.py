@@ -3,7 +3,7 @@
 * Flower interface, 1024^2 (the benchmark's main workload): the FP64 path
   against the oracle element by element (operator on a seeded density), and
   the benchmark's mixed configuration (3 box-solve steps) against the oracle
-  through what the method is judged on: the solution's error against the exact
+  through what measures the method: the solution's error against the exact
   solution within 1.1x the oracle's, at the benchmark's GMRES tolerance.
 * Torus, 3D, 128^3 (the oracle's set-up there takes minutes): properties that
   hold at any size - every box solver reproduces single sine modes in closed
