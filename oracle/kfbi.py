@@ -25,6 +25,15 @@ Problem kinds:
         b     = g2/(sigma_in + sigma_out) + mu * avg d_n(w),
     where w has a = g1, the piecewise f/sigma and the outer data g_B, and
     avg = (d_n^+ + d_n^-)/2.  (K' psi is read as -avg d_n of -S psi.)
+  * interior Neumann BVP, eq. (bie-N): unknown psi at the DOFs (unit-sigma
+    form, psi = [d_n u] of u = -S psi + N f),
+        A psi = psi/2 - K' psi = psi/2 + avg d_n(v[psi]),
+        b     = g_N/sigma - d_n G f,   d_n G f = avg d_n of N f,
+    solution u = -S psi + N f.  For kappa~ = 0 the operator is singular (its
+    adjoint kills constants) and the solution is fixed up to a constant: as in
+    Sec. 7.2.1, b and every operator application have their mean subtracted.
+    Reading: the mean is the plain arithmetic mean over the N_b DOFs, and the
+    projection is applied only when kappa~ = 0.
 GMRES (Algorithm 1, Step 4): unrestarted up to `restart` steps, modified
 Gram-Schmidt Arnoldi, Givens rotations, stop at ||b - A x|| <= rtol ||b||.
 """
@@ -50,7 +59,7 @@ class Problem:
         self.d, self.n, self.order = d, n, w.order
         self.grid = G.Grid(d, n, w.lo, w.h)
         self.h = w.h
-        if w.kind == W.KIND_DIRICHLET:
+        if w.kind in (W.KIND_DIRICHLET, W.KIND_NEUMANN):
             self.kt = w.kappa / w.sigma_in
         else:
             self.kt = w.kappa
@@ -169,12 +178,20 @@ class Problem:
             return 0.5 * x + 0.5 * (vp + vm)
         u, cv, _, _ = self.potential(z, x)
         _, _, dp, dm = self.traces(u, cv)
+        if self.w.kind == W.KIND_NEUMANN:
+            return self.project(0.5 * x + 0.5 * (dp + dm))
         return 0.5 * x - self._mu() * 0.5 * (dp + dm)
+
+    def project(self, y: np.ndarray) -> np.ndarray:
+        """Neumann BVP with kappa~ = 0: remove the mean (Sec. 7.2.1)."""
+        if self.w.kind == W.KIND_NEUMANN and self.kt == 0.0:
+            return y - np.mean(y)
+        return y
 
     def unit_sigma_data(self, data):
         """Physical f on each side divided by sigma (eq. (bie-ifp-2))."""
         w = self.w
-        so = w.sigma_in if w.kind == W.KIND_DIRICHLET else w.sigma_out
+        so = w.sigma_in if w.kind in (W.KIND_DIRICHLET, W.KIND_NEUMANN) else w.sigma_out
         return (data["f_in"] / w.sigma_in, data["f_out"] / so,
                 data["lapf_in"] / w.sigma_in, data["lapf_out"] / so)
 
@@ -189,6 +206,10 @@ class Problem:
             vp, vm, _, _ = self.traces(u, cv)
             return g1 - 0.5 * (vp + vm)
         w = self.w
+        if w.kind == W.KIND_NEUMANN:
+            u, cv, _, _ = self.potential(z, z, Fi, np.zeros_like(Fo), Li, np.zeros_like(Lo))
+            _, _, dp, dm = self.traces(u, cv)
+            return self.project(g2 / w.sigma_in - 0.5 * (dp + dm))
         u, cv, _, _ = self.potential(g1, z, Fi, Fo, Li, Lo, data["g_b"])
         _, _, dp, dm = self.traces(u, cv)
         return g2 / (w.sigma_in + w.sigma_out) + self._mu() * 0.5 * (dp + dm)
@@ -200,6 +221,10 @@ class Problem:
             Fo = np.zeros_like(Fo)
             Lo = np.zeros_like(Lo)
             u, _, _, _ = self.potential(density, np.zeros(self.nb), Fi, Fo, Li, Lo)
+            return u
+        if self.w.kind == W.KIND_NEUMANN:
+            z = np.zeros_like(Fo)
+            u, _, _, _ = self.potential(np.zeros(self.nb), density, Fi, z, Li, z)
             return u
         u, _, _, _ = self.potential(g1, density, Fi, Fo, Li, Lo, data["g_b"])
         return u

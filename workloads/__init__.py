@@ -30,6 +30,7 @@ LS_MOLECULE = 5     # 3D: p = [r, level, n_atoms, x1, y1, z1, x2, ...]
 # Problem kinds (shared with kfbi_problem_kind).
 KIND_DIRICHLET = 0  # interior Dirichlet BVP, eq. (bie-D)
 KIND_INTERFACE_MU = 1  # two-medium interface problem, kappa = 0, mu-form BIE
+KIND_NEUMANN = 2    # interior Neumann BVP, eq. (bie-N)
 
 BOX_DST = 0
 BOX_MG = 1
@@ -120,6 +121,17 @@ def _sol_exp3():
     return u, g, lap
 
 
+def _sol_exp_cos3():
+    # u = e^z (cos 2x + cos 3y), the Neumann torus example of Sec. 7;
+    # lap u = e^z (-3 cos 2x - 8 cos 3y)
+    u = lambda X: np.exp(X[..., 2]) * (np.cos(2 * X[..., 0]) + np.cos(3 * X[..., 1]))
+    g = lambda X: np.stack([-2 * np.exp(X[..., 2]) * np.sin(2 * X[..., 0]),
+                            -3 * np.exp(X[..., 2]) * np.sin(3 * X[..., 1]),
+                            np.exp(X[..., 2]) * (np.cos(2 * X[..., 0]) + np.cos(3 * X[..., 1]))], -1)
+    lap = lambda X: np.exp(X[..., 2]) * (-3 * np.cos(2 * X[..., 0]) - 8 * np.cos(3 * X[..., 1]))
+    return u, g, lap
+
+
 def _sol_zero(d):
     u = lambda X: np.zeros(X.shape[:-1])
     g = lambda X: np.zeros(X.shape)
@@ -161,6 +173,8 @@ def solutions(w: Workload):
         return _sol_exp3(), _sol_zero(3)
     if e == "harmonic3":
         return _sol_harmonic3(w.extra["amps"]), _sol_zero(3)
+    if e == "exp_cos3":
+        return _sol_exp_cos3(), _sol_zero(3)
     raise ValueError(f"unknown exact solution {e!r}")
 
 
@@ -185,7 +199,7 @@ def grid_data(w: Workload):
     X = grid_coords(w)
     (ui, gi, li), (uo, go, lo_) = solutions(w)
     d = w.dim
-    if w.kind == KIND_DIRICHLET:
+    if w.kind in (KIND_DIRICHLET, KIND_NEUMANN):
         s, k = w.sigma_in, w.kappa
         f_in = s * li(X) - k * ui(X)
         f_out = np.zeros_like(f_in)
@@ -227,6 +241,11 @@ def _lap_of_f(w: Workload, X, inside: bool):
         if inside:  # f = sigma_in * (-2 sin x cos y); lap = sigma_in * 4 sin x cos y
             return w.sigma_in * 4.0 * np.sin(X[..., 0]) * np.cos(X[..., 1])
         return np.zeros(X.shape[:-1])
+    if e == "exp_cos3":  # f = sigma lap u - kappa u with lap(e^z cos kx) = (1 - k^2) e^z cos kx
+        ez = np.exp(X[..., 2])
+        c2, c3 = np.cos(2 * X[..., 0]), np.cos(3 * X[..., 1])
+        s, k = w.sigma_in, w.kappa
+        return s * ez * (9 * c2 + 64 * c3) - k * ez * (-3 * c2 - 8 * c3)
     if e == "exp3":  # f = (3 - kappa) u sigma-scaled; lap f = 3 f
         u = np.exp(X[..., 0] + X[..., 1] + X[..., 2]) / 10.0
         return 3.0 * (w.sigma_in * 3.0 - w.kappa) * u
@@ -236,13 +255,16 @@ def _lap_of_f(w: Workload, X, inside: bool):
 def boundary_data(w: Workload, pts: np.ndarray, normals: np.ndarray):
     """Interface data at points with unit normals (outward from Omega).
 
-    Dirichlet BVP: returns (g_D, None).  Interface problem: returns
+    Dirichlet BVP: returns (g_D, None).  Neumann BVP: returns
+    (None, g_N) with g_N = sigma d_n u.  Interface problem: returns
     (g1, g2) with g1 = u_in - u_out and g2 = sigma_in d_n u_in - sigma_out d_n u_out,
     the jump conditions of eq. (IFP-bc).
     """
     (ui, gi, _), (uo, go, _) = solutions(w)
     if w.kind == KIND_DIRICHLET:
         return ui(pts), None
+    if w.kind == KIND_NEUMANN:
+        return None, w.sigma_in * np.sum(gi(pts) * normals, -1)
     g1 = ui(pts) - uo(pts)
     g2 = (w.sigma_in * np.sum(gi(pts) * normals, -1)
           - w.sigma_out * np.sum(go(pts) * normals, -1))
@@ -287,6 +309,23 @@ def torus_helmholtz_3d(n: int = 128) -> Workload:
     (sqrt(x^2+y^2) - 0.5)^2 + z^2 < 0.2^2, u = e^{x+y+z}/10."""
     return Workload("torus_helmholtz_3d", 3, n, -1.0, 1.0, LS_TORUS, [0.5, 0.2],
                     KIND_DIRICHLET, kappa=1.0, exact="exp3")
+
+
+def neumann_torus_3d(n: int = 64, kappa: float = 0.0) -> Workload:
+    """The paper's 3D Neumann example (Sec. 7.2.1): torus (1 - sqrt(x^2+y^2))^2
+    + z^2 < 0.4^2 in [-1.5, 1.5]^3, u = e^z (cos 2x + cos 3y), Poisson
+    (kappa = 0, solution fixed up to a constant) or modified Helmholtz."""
+    return Workload("neumann_torus_3d", 3, n, -1.5, 1.5, LS_TORUS, [1.0, 0.4],
+                    KIND_NEUMANN, kappa=kappa, exact="exp_cos3")
+
+
+def neumann_ellipse_2d(n: int = 64, kappa: float = 0.0) -> Workload:
+    """2D interior Neumann BVP on the rotated ellipse of the paper's first
+    example; Poisson with that example's solution, or modified Helmholtz
+    (kappa > 0) with u = e^x sin y (harmonic, f = -kappa u)."""
+    return Workload("neumann_ellipse_2d", 2, n, -1.2, 1.2, LS_ELLIPSE,
+                    [0.0, 0.0, 1.0, 0.5, -math.pi / 6], KIND_NEUMANN, kappa=kappa,
+                    exact="paper_table1" if kappa == 0.0 else "exp_sin")
 
 
 def star_batch_2d(count: int = 64, seed: int = 5965, sizes=(128, 256, 512, 1024)):
