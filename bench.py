@@ -296,6 +296,8 @@ def run_ours(args, rank, world):
         out["learned"] = learned_leg(args, stream, flush)
     if args.threed_n > 0:
         out["threed"] = threed_leg(args, stream, flush)
+    if args.neumann_n > 0:
+        out["neumann"] = neumann_leg(args, stream, flush)
     if rank == 0 and args.cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_budget)
     return out
@@ -626,6 +628,73 @@ def threed_leg(args, stream, flush):
     return out
 
 
+# Sec. 7.2.1, Table 3: the paper's Neumann torus (N, N_b, GMRES iterations at
+# tolerance 1e-10, RMS and maximum error, CPU seconds on the paper's machine)
+PAPER_TABLE3 = {128: (24656, 21, 2.76e-05, 7.97e-05, 6.35), 256: (98668, 18, 2.38e-06, 5.98e-06, 25.0),
+                512: (394548, 17, 1.68e-07, 4.01e-07, 135.0)}
+
+
+def neumann_leg(args, stream, flush):
+    """The paper's 3D Neumann Poisson problem on the torus (Sec. 7.2.1) at
+    --neumann-n^3: mixed and FP64 DST box solves, GMRES to the paper's
+    tolerance 1e-10 with the zero-mean projection, then the grid solution;
+    errors with their mean over Omega removed (the solution is fixed up to a
+    constant), beside the paper's Table 3 row."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2309_05965_gb300 import kfbi
+    n = args.neumann_n
+    w = W.neumann_torus_3d(n)
+    grid = W.grid_data(w)
+    out = {"workload": f"torus Neumann 3D (Sec. 7.2.1), N={n}, kappa=0, u=exp(z)(cos 2x + cos 3y), "
+                       f"4th order, GMRES rtol 1e-10"}
+    if n in PAPER_TABLE3:
+        nb, it, e2, einf, cpu_s = PAPER_TABLE3[n]
+        out["paper"] = {"n_b": nb, "gmres_iterations": it, "e2": e2, "einf": einf, "cpu_s": cpu_s}
+    opts = kfbi.GmresOpts(rtol=1e-10, restart=100, max_iter=200, x0=None)
+    for name, prec in (("dst_mixed", kfbi.MIXED), ("dst_fp64", kfbi.FP64)):
+        G = kfbi.Problem.from_workload(w, precision=prec,
+                                       box_max_iters=args.box_steps if prec == kfbi.MIXED else 0)
+        xyz = torch.zeros((G.nb, 3), dtype=torch.float64, device="cuda")
+        nrm = torch.zeros_like(xyz)
+        kfbi.kfbi_dof_points(G.handle, xyz, nrm)
+        _, g2 = W.boundary_data(w, xyz.cpu().numpy(), nrm.cpu().numpy())
+        keep = {"g2": torch.from_numpy(g2).cuda(),
+                "f_in": torch.from_numpy(np.ascontiguousarray(grid["f_in"])).cuda(),
+                "lapf_in": torch.from_numpy(np.ascontiguousarray(grid["lapf_in"])).cuda()}
+        d = kfbi.make_data(**keep)
+        x = torch.zeros(G.nb, dtype=torch.float64, device="cuda")
+        u = torch.zeros(G.grid_shape, dtype=torch.float64, device="cuda")
+
+        def step():
+            info = kfbi.kfbi_gmres_solve(G.handle, d, opts, x)
+            kfbi.kfbi_evaluate(G.handle, d, x, u)
+            return info
+        step()
+        ts = []
+        for _ in range(3):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = step()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ins = _inside(G, kfbi)
+        e = (u.cpu().numpy() - W.exact_grid(w, ins))[ins]
+        e = e - e.mean()
+        out[name] = {"solves_per_s": 1e3 / statistics.median(ts), "ms_per_solve": statistics.median(ts),
+                     "gmres_iterations": info.iters, "einf": float(np.abs(e).max()),
+                     "e2": float(np.sqrt(np.mean(e * e))), "n_b": G.nb}
+        G.close()
+    out["speedup_mixed_vs_fp64"] = out["dst_mixed"]["solves_per_s"] / out["dst_fp64"]["solves_per_s"]
+    out["err_ratio_mixed_vs_fp64"] = out["dst_mixed"]["einf"] / out["dst_fp64"]["einf"]
+    return out
+
+
 def _inside(G, kfbi):
     import torch
     m = torch.zeros(G.grid_shape, dtype=torch.uint8, device="cuda")
@@ -794,6 +863,8 @@ def main():
     ap.add_argument("--learned-eval", type=int, default=3)
     ap.add_argument("--threed-n", type=int, default=128,
                     help="grid of the 3D torus workload (0: skip)")
+    ap.add_argument("--neumann-n", type=int, default=256,
+                    help="grid of the Neumann torus leg (Sec. 7.2.1); 0 skips it")
     ap.add_argument("--profile-box", default="", choices=["", "dst", "mg"],
                     help="profiling aid: on the 3D torus at --threed-n, time the mixed box solve alone and run "
                          "one more inside cudaProfilerStart/Stop (for ncu --profile-from-start off); no JSON line")

@@ -59,7 +59,9 @@ typedef enum {
 
 typedef enum {
   KFBI_DIRICHLET_INTERIOR = 0, /* eq. (bie-D): (1/2 + K) phi = g_D - G f           */
-  KFBI_INTERFACE_MU = 1        /* mu-form BIE of Sec. 3.2 for psi = [d_n u]         */
+  KFBI_INTERFACE_MU = 1,       /* mu-form BIE of Sec. 3.2 for psi = [d_n u]         */
+  KFBI_NEUMANN_INTERIOR = 2    /* eq. (bie-N): (1/2 - K') psi = g_N - sigma d_n G f;
+                                  kappa = 0: projected to zero mean (Sec. 7.2.1)    */
 } kfbi_problem_kind;
 
 typedef enum { KFBI_BOX_DST = 0, KFBI_BOX_MG = 1 } kfbi_box_solver;
@@ -100,7 +102,8 @@ typedef struct {
  * (BVP)/(IFP) on each side, smoothly extended to the whole box; the library
  * divides them by sigma.  lapf_* are their Laplacians (for the h^2/12 Lap f term
  * of eqs. (9p-cds)/(27p-cds)).  Dirichlet BVP: g1 = g_D, g2, f_out, lapf_out and
- * g_b unused (may be NULL).  Interface: g1 = [u], g2 = [sigma d_n u], g_b = outer
+ * g_b unused (may be NULL).  Neumann BVP: g2 = g_N = sigma d_n u, g1, f_out,
+ * lapf_out and g_b unused (may be NULL).  Interface: g1 = [u], g2 = [sigma d_n u], g_b = outer
  * Dirichlet values (NULL = homogeneous).  Any grid may be NULL (= 0). */
 typedef struct {
   const double* g1;       /* N_b   */
@@ -210,7 +213,9 @@ kfbi_status kfbi_traces(kfbi_problem* p, const double* u, const double* cvals,
 
 /* One application of the discrete BIE operator (Steps 3.1-3.4 plus the BIE
  * combination): Dirichlet y = x/2 + avg trace of D x; mu-form
- * y = x/2 - mu avg d_n of (-S x). */
+ * y = x/2 - mu avg d_n of (-S x); Neumann y = x/2 + avg d_n of (-S x), for
+ * kappa = 0 minus its arithmetic mean over the DOFs (Sec. 7.2.1: the solution
+ * is fixed up to a constant; the right-hand side is projected the same way). */
 kfbi_status kfbi_apply_operator(kfbi_problem* p, const double* x, double* y);
 /* Right-hand side of the BIE (Algorithm 1, Step 1). */
 kfbi_status kfbi_bie_rhs(kfbi_problem* p, const kfbi_data* data, double* b);
@@ -223,7 +228,8 @@ kfbi_status kfbi_gmres_solve(kfbi_problem* p, const kfbi_data* data,
                              const kfbi_gmres_opts* opts, double* density,
                              kfbi_gmres_info* info);
 /* Grid solution from a density by superposition (one more potential solve):
- * Dirichlet u = D phi + N f; interface u with [u] = g1, [d_n u] = psi. */
+ * Dirichlet u = D phi + N f; Neumann u = -S psi + N f (kappa = 0: up to an
+ * additive constant); interface u with [u] = g1, [d_n u] = psi. */
 kfbi_status kfbi_evaluate(kfbi_problem* p, const kfbi_data* data, const double* density,
                           double* u_grid);
 

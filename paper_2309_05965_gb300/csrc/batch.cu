@@ -95,10 +95,11 @@ kfbi_status kfbi_create_batch(kfbi_problem* const* problems, int count, kfbi_bat
   };
   for (kfbi_problem* p : b->ps) {
     if (p->stream != b->stream || p->g.d != p0->g.d || p->cfg.precision != KFBI_MIXED ||
+        p->cfg.kind == KFBI_NEUMANN_INTERIOR ||
         p->cfg.box_solver != KFBI_BOX_DST || p->gm.m != b->m || p->nb > 32768)
       return bail(fail(p0, KFBI_ERR_UNSUPPORTED,
-                       "a batch needs problems on one stream, of one dimension, with mixed-precision "
-                       "DST box solves and N_b <= 32768"));
+                       "a batch needs Dirichlet or interface problems on one stream, of one dimension, "
+                       "with mixed-precision DST box solves and N_b <= 32768"));
     b->maxnb = std::max(b->maxnb, p->nb);
   }
   std::vector<double*> xs, ys;

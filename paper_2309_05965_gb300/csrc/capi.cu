@@ -20,14 +20,17 @@ kfbi_status fail(kfbi_problem* p, kfbi_status s, const std::string& msg) {
 // One application of the discrete BIE operator: Steps 3.1-3.4 + combination.
 kfbi_status apply_operator_impl(kfbi_problem* p, const double* x, double* y) {
   const bool dir = p->cfg.kind == KFBI_DIRICHLET_INTERIOR;
+  const bool neu = p->cfg.kind == KFBI_NEUMANN_INTERIOR;
   // Step 3.1 (fitted and evaluated at the irregular nodes)
   KFBI_TRY(launch_correction_values(p, dir ? x : nullptr, dir ? nullptr : x, nullptr, p->cvals));
   // Step 3.2
   KFBI_TRY(launch_rhs(p, p->cvals, nullptr, p->rhs));
   // Step 3.3
   KFBI_TRY(box_solve(p, p->rhs, p->ugrid));
-  // Step 3.4 + BIE: Dirichlet y = x/2 + avg value; mu-form y = x/2 - mu avg d_n
-  return launch_operator_trace(p, p->ugrid, p->cvals, x, 0.5, dir ? 1.0 : -p->mu, y);
+  // Step 3.4 + BIE: Dirichlet y = x/2 + avg value; mu-form y = x/2 - mu avg d_n;
+  // Neumann y = x/2 + avg d_n (= x/2 - K'x), projected when kappa~ = 0
+  KFBI_TRY(launch_operator_trace(p, p->ugrid, p->cvals, x, 0.5, dir || neu ? 1.0 : -p->mu, y));
+  return neu ? launch_mean_project(p, y) : KFBI_OK;
 }
 
 // One operator application through a CUDA graph captured on first use (the
@@ -87,10 +90,25 @@ kfbi_status bie_rhs_impl(kfbi_problem* p, const kfbi_data* data, double* bvec) {
     KFBI_TRY(potential_with_data(p, nullptr, nullptr, data, false, p->ugrid));
     return launch_operator_trace(p, p->ugrid, p->cvals, data->g1, 1.0, -1.0, bvec);
   }
+  if (p->cfg.kind == KFBI_NEUMANN_INTERIOR) {
+    // b = g_N/sigma - d_n G f, d_n G f = avg d_n of N f; projected when kappa~ = 0
+    KFBI_TRY(potential_with_data(p, nullptr, nullptr, data, false, p->ugrid));
+    KFBI_TRY(launch_operator_trace(p, p->ugrid, p->cvals, data->g2, 1.0 / p->cfg.sigma_in, -1.0, bvec));
+    return launch_mean_project(p, bvec);
+  }
   // b = g2/(sigma_in + sigma_out) + mu avg d_n w, w with a = g1, F = f/sigma, g_B
   KFBI_TRY(potential_with_data(p, data->g1, nullptr, data, true, p->ugrid));
   return launch_operator_trace(p, p->ugrid, p->cvals, data->g2,
                                1.0 / (p->cfg.sigma_in + p->cfg.sigma_out), p->mu, bvec);
+}
+
+// The boundary data each kind reads: g1 (Dirichlet), g2 (Neumann), both (interface).
+static bool has_boundary_data(const kfbi_problem* p, const kfbi_data* data) {
+  switch (p->cfg.kind) {
+    case KFBI_DIRICHLET_INTERIOR: return data->g1 != nullptr;
+    case KFBI_NEUMANN_INTERIOR: return data->g2 != nullptr;
+    default: return data->g1 != nullptr && data->g2 != nullptr;
+  }
 }
 
 }  // namespace kfbi
@@ -130,7 +148,8 @@ kfbi_status kfbi_create_problem(const kfbi_config* cfg, const kfbi_levelset* ls,
     fail(p, KFBI_ERR_ARG, "need hi > lo and N a power of two >= 8");
     return bail(KFBI_ERR_ARG);
   }
-  if (cfg->kind != KFBI_DIRICHLET_INTERIOR && cfg->kind != KFBI_INTERFACE_MU) {
+  if (cfg->kind != KFBI_DIRICHLET_INTERIOR && cfg->kind != KFBI_INTERFACE_MU &&
+      cfg->kind != KFBI_NEUMANN_INTERIOR) {
     fail(p, KFBI_ERR_ARG, "unknown problem kind");
     return bail(KFBI_ERR_ARG);
   }
@@ -160,7 +179,7 @@ kfbi_status kfbi_create_problem(const kfbi_config* cfg, const kfbi_levelset* ls,
   p->ls.kind = ls->kind;
   p->ls.np = ls->n_params;
   memcpy(p->ls.p, ls->p, sizeof(p->ls.p));
-  p->kt = cfg->kind == KFBI_DIRICHLET_INTERIOR ? cfg->kappa / cfg->sigma_in : cfg->kappa;
+  p->kt = cfg->kind == KFBI_INTERFACE_MU ? cfg->kappa : cfg->kappa / cfg->sigma_in;
   p->mu = cfg->kind == KFBI_INTERFACE_MU
               ? (cfg->sigma_out - cfg->sigma_in) / (cfg->sigma_out + cfg->sigma_in)
               : 0.0;
@@ -367,15 +386,13 @@ kfbi_status kfbi_apply_operator(kfbi_problem* p, const double* x, double* y) {
 }
 
 kfbi_status kfbi_bie_rhs(kfbi_problem* p, const kfbi_data* data, double* b) {
-  if (!p || !data || !b || !data->g1) return KFBI_ERR_ARG;
-  if (p->cfg.kind == KFBI_INTERFACE_MU && !data->g2) return KFBI_ERR_ARG;
+  if (!p || !data || !b || !has_boundary_data(p, data)) return KFBI_ERR_ARG;
   return bie_rhs_impl(p, data, b);
 }
 
 kfbi_status kfbi_gmres_solve(kfbi_problem* p, const kfbi_data* data, const kfbi_gmres_opts* opts,
                              double* density, kfbi_gmres_info* info) {
-  if (!p || !data || !opts || !density || !data->g1) return KFBI_ERR_ARG;
-  if (p->cfg.kind == KFBI_INTERFACE_MU && !data->g2) return KFBI_ERR_ARG;
+  if (!p || !data || !opts || !density || !has_boundary_data(p, data)) return KFBI_ERR_ARG;
   if (!(opts->rtol > 0) || opts->max_iter < 1) return fail(p, KFBI_ERR_ARG, "need rtol > 0, max_iter >= 1");
   auto t0 = std::chrono::steady_clock::now();
   KFBI_TRY(bie_rhs_impl(p, data, p->bvec));
@@ -404,6 +421,8 @@ kfbi_status kfbi_evaluate(kfbi_problem* p, const kfbi_data* data, const double* 
   if (!p || !density || !u_grid) return KFBI_ERR_ARG;
   if (p->cfg.kind == KFBI_DIRICHLET_INTERIOR)
     return potential_with_data(p, density, nullptr, data, false, u_grid);
+  if (p->cfg.kind == KFBI_NEUMANN_INTERIOR)
+    return potential_with_data(p, nullptr, density, data, false, u_grid);
   if (!data || !data->g1) return fail(p, KFBI_ERR_ARG, "interface evaluate needs data->g1");
   return potential_with_data(p, data->g1, density, data, true, u_grid);
 }

@@ -216,6 +216,25 @@ __global__ void k_trace_op(int nb, TraceCSR tp, TraceCSR tm, const double* __res
   if (lane == 0) y[i] = (x ? alpha * x[i] : 0.0) + beta * acc;
 }
 
+// y -= mean(y): one CTA, each thread a strided partial sum, then a fixed
+// warp/CTA tree, so the result does not depend on timing.
+__global__ void __launch_bounds__(1024) k_mean_project(int n, double* __restrict__ y) {
+  __shared__ double part[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += y[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) part[0] = t;
+  }
+  __syncthreads();
+  const double m = part[0] / n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] -= m;
+}
+
 __global__ void k_set_boundary(Grid g, const double* __restrict__ gb, double* __restrict__ u) {
   const int tot = (int)g.nodes();
   const int n1 = g.n + 1;
@@ -252,8 +271,8 @@ kfbi_status launch_correction_values_data(kfbi_problem* p, const double* a, cons
                                           const kfbi_data* data, double* cvals) {
   const double* fi = data ? data->f_in : nullptr;
   const double* fo = data ? data->f_out : nullptr;
-  double so = p->cfg.kind == KFBI_DIRICHLET_INTERIOR ? 1.0 : p->cfg.sigma_out;
-  if (p->cfg.kind == KFBI_DIRICHLET_INTERIOR) fo = nullptr;
+  double so = interior_bvp(p) ? 1.0 : p->cfg.sigma_out;
+  if (interior_bvp(p)) fo = nullptr;
   KFBI_LAUNCH(p, KFBI_KC_CORRECTION, k_cvals<<<div_up(p->nirr, 128), 128, 0, p->stream>>>(
       p->nirr, p->npde, p->ndir, p->nneu, p->g.h, p->irr_owner, p->irr_w, p->pde_node,
       p->dir_idx, p->neu_idx, a, b, fi, p->cfg.sigma_in, fo, so, cvals));
@@ -298,13 +317,13 @@ kfbi_status launch_rhs(kfbi_problem* p, const double* cvals, const kfbi_data* da
   const bool gb = data && data->g_b;
   if (src || gb) {
     const double* fi = data->f_in;
-    const double* fo = p->cfg.kind == KFBI_DIRICHLET_INTERIOR ? nullptr : data->f_out;
+    const double* fo = interior_bvp(p) ? nullptr : data->f_out;
     const double* li = data->lapf_in;
-    const double* lo_ = p->cfg.kind == KFBI_DIRICHLET_INTERIOR ? nullptr : data->lapf_out;
-    double so = p->cfg.kind == KFBI_DIRICHLET_INTERIOR ? 1.0 : p->cfg.sigma_out;
+    const double* lo_ = interior_bvp(p) ? nullptr : data->lapf_out;
+    double so = interior_bvp(p) ? 1.0 : p->cfg.sigma_out;
     KFBI_LAUNCH(p, KFBI_KC_RHS, k_rhs_source<<<std::min(div_up(g.nodes(), 256), 152 * 32), 256, 0, p->stream>>>(
         g, p->cfg.order, p->inside, fi, fo, li, lo_, 1.0 / p->cfg.sigma_in, 1.0 / so, g.h * g.h / 12.0,
-        p->cfg.kind == KFBI_DIRICHLET_INTERIOR ? nullptr : data->g_b, d_nbc, d_off, p->n_nb, rhs));
+        interior_bvp(p) ? nullptr : data->g_b, d_nbc, d_off, p->n_nb, rhs));
     KFBI_CUDA(p, cudaGetLastError());
   } else {
     KFBI_CUDA(p, cudaMemsetAsync(rhs, 0, sizeof(double) * g.nodes(), p->stream));
@@ -329,6 +348,13 @@ kfbi_status launch_operator_trace(kfbi_problem* p, const double* u, const double
                                   const double* x, double alpha_x, double beta_t, double* y) {
   KFBI_LAUNCH(p, KFBI_KC_TRACE, k_trace_op<<<div_up(p->nb, 8), 256, 0, p->stream>>>(p->nb, p->tr[0], p->tr[1], u, cvals, x,
                                                        alpha_x, beta_t, y));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status launch_mean_project(kfbi_problem* p, double* y) {
+  if (p->cfg.kind != KFBI_NEUMANN_INTERIOR || p->kt != 0.0) return KFBI_OK;
+  KFBI_LAUNCH(p, KFBI_KC_TRACE, k_mean_project<<<1, 1024, 0, p->stream>>>(p->nb, y));
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
 }

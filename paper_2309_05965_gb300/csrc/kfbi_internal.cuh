@@ -208,6 +208,10 @@ cudaError_t dalloc(T** ptr, size_t count) {
 
 inline int div_up(long long a, long long b) { return static_cast<int>((a + b - 1) / b); }
 
+// Interior BVPs (Dirichlet, Neumann) take f on Omega only, in unit-sigma form
+// with sigma_in, and no outer boundary data.
+inline bool interior_bvp(const kfbi_problem* p) { return p->cfg.kind != KFBI_INTERFACE_MU; }
+
 // ---- device helpers -------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -262,6 +266,9 @@ kfbi_status launch_operator_trace(kfbi_problem* p, const double* u, const double
                                   const double* x, double alpha_x, double beta_t,
                                   double* y);
 kfbi_status launch_set_boundary(kfbi_problem* p, double* u, const double* g_b);
+// Neumann BVP with kappa~ = 0 (Sec. 7.2.1): y -= mean(y) over the N_b DOFs;
+// a no-op for every other problem.
+kfbi_status launch_mean_project(kfbi_problem* p, double* y);
 // dst.cu / mg.cu
 kfbi_status box_create(kfbi_problem* p);
 void box_destroy(kfbi_problem* p);

@@ -21,6 +21,7 @@ LS_MAX_PARAMS = 64
 
 DIRICHLET_INTERIOR = 0
 INTERFACE_MU = 1
+NEUMANN_INTERIOR = 2
 BOX_DST = 0
 BOX_MG = 1
 FP64 = 0

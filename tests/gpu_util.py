@@ -50,7 +50,7 @@ def gpu_data(w, P_or, data, g1, g2):
     keep = {}
     for k in ("f_in", "f_out", "lapf_in", "lapf_out", "g_b"):
         keep[k] = dev(data[k])
-    keep["g1"] = dev(g1)
+    keep["g1"] = dev(g1) if g1 is not None else None
     keep["g2"] = dev(g2) if g2 is not None else None
     d = kfbi.make_data(g1=keep["g1"], g2=keep["g2"], f_in=keep["f_in"], f_out=keep["f_out"],
                        lapf_in=keep["lapf_in"], lapf_out=keep["lapf_out"],

@@ -1,0 +1,159 @@
+"""Interior Neumann BVP, eq. (bie-N), with the zero-mean projection of
+Sec. 7.2.1 (kappa = 0), on the GPU against the oracle and the paper.
+
+* operator and right-hand side element by element against the oracle (2D
+  ellipse at 128^2, Poisson and modified Helmholtz; 3D ellipsoid at 32^3),
+  FP64 and mixed box solves; for kappa = 0 every output has zero mean;
+* full solves: the GPU density solves the oracle's discrete system to a
+  relative residual <= 1e-10, and the solution's error against the exact one
+  (its mean over Omega removed: the solution is fixed up to a constant) is
+  within 1.1x of the oracle's;
+* the paper's torus (Sec. 7.2.1, Table 3) at 128^3 and 256^3, where the oracle
+  takes many minutes: properties that hold at any size (zero-mean right-hand
+  side, mixed and FP64 box solves give the same solution to the GMRES
+  tolerance) and errors within 3x of the printed ones."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import kfbi as OK
+from tests.gpu_util import dev, empty, gpu_data, host, rel_err
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_table3.json")
+
+
+def _case(name):
+    if name == "ell2_k0":
+        return W.neumann_ellipse_2d(128, 0.0)
+    if name == "ell2_k1":
+        return W.neumann_ellipse_2d(128, 1.0)
+    return W.Workload("ell3n", 3, 32, -1.0, 1.0, W.LS_ELLIPSOID,
+                      [0.05, -0.03, 0.02, 0.8, 0.7, 0.6], W.KIND_NEUMANN, exact="exp3")
+
+
+NAMES = ["ell2_k0", "ell2_k1", "ell3_k0"]
+_oracles = {}
+
+
+def _pair(name, precision):
+    from paper_2309_05965_gb300 import build, kfbi
+    build.build()
+    w = _case(name)
+    if name not in _oracles:
+        _oracles[name] = OK.Problem(w)
+    G = kfbi.Problem.from_workload(w, precision=precision)
+    return w, _oracles[name], G
+
+
+def _err(u, w, inside):
+    e = (u - W.exact_grid(w, inside))[inside]
+    return float(np.abs(e - e.mean()).max()), float(np.sqrt(np.mean((e - e.mean()) ** 2)))
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_neumann_operator(name, precision):
+    from paper_2309_05965_gb300 import kfbi
+    w, P, G = _pair(name, precision)
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(P.nb)
+    y = empty(G.nb)
+    kfbi.kfbi_apply_operator(G.handle, dev(x), y)
+    yh = host(y)
+    assert rel_err(yh, P.apply(x)) < 1e-10
+    if w.kappa == 0.0:
+        assert abs(float(yh.mean())) < 1e-14 * float(np.abs(yh).max())
+    data = W.grid_data(w)
+    g1, g2 = W.boundary_data(w, P.surf.x, P.surf.n)
+    d, keep = gpu_data(w, P, data, g1, g2)
+    b = empty(G.nb)
+    kfbi.kfbi_bie_rhs(G.handle, d, b)
+    assert rel_err(host(b), P.bie_rhs(g1, g2, data)) < 1e-10
+    G.close()
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_neumann_solve(name, precision):
+    from paper_2309_05965_gb300 import kfbi
+    w, P, G = _pair(name, precision)
+    data = W.grid_data(w)
+    g1, g2 = W.boundary_data(w, P.surf.x, P.surf.n)
+    b_ref = P.bie_rhs(g1, g2, data)
+    x_ref, it_ref, _ = OK.gmres(P.apply, b_ref, rtol=1e-12)
+    e_ref, _ = _err(P.evaluate(x_ref, g1, data), w, P.inside)
+    d, keep = gpu_data(w, P, data, g1, g2)
+    dens = empty(G.nb)
+    opts = kfbi.GmresOpts(rtol=1e-12, restart=100, max_iter=200, x0=None)
+    info = kfbi.kfbi_gmres_solve(G.handle, d, opts, dens)
+    assert abs(info.iters - it_ref) <= 2, (info.iters, it_ref)
+    xg = host(dens)
+    assert np.linalg.norm(b_ref - P.apply(xg)) / np.linalg.norm(b_ref) < 1e-10
+    u = empty(G.grid_shape)
+    kfbi.kfbi_evaluate(G.handle, d, dens, u)
+    e_gpu, _ = _err(host(u), w, P.inside)
+    assert e_gpu <= 1.1 * e_ref + 1e-12, (e_gpu, e_ref)
+    G.close()
+
+
+def test_neumann_refused_in_batch():
+    from paper_2309_05965_gb300 import kfbi
+    w, P, G = _pair("ell2_k0", 1)
+    with pytest.raises(kfbi.KfbiError) as e:
+        kfbi.Batch([G])
+    assert e.value.status == 8
+    G.close()
+
+
+@pytest.mark.parametrize("n", [128, 256])
+def test_neumann_torus_paper(n):
+    """Sec. 7.2.1: mixed-precision DST and FP64 DST solves of the paper's torus."""
+    import torch
+    from paper_2309_05965_gb300 import build, kfbi
+    build.build()
+    row = next(r for r in json.load(open(GOLDEN))["rows"] if r["N"] == n)
+    w = W.neumann_torus_3d(n)
+    sols = []
+    for precision in (kfbi.MIXED, kfbi.FP64):
+        G = kfbi.Problem.from_workload(w, precision=precision)
+        xyz = torch.zeros((G.nb, 3), dtype=torch.float64, device="cuda")
+        nrm = torch.zeros((G.nb, 3), dtype=torch.float64, device="cuda")
+        kfbi.kfbi_dof_points(G.handle, xyz, nrm)
+        _, g2 = W.boundary_data(w, host(xyz), host(nrm))
+        data = W.grid_data(w)
+        d, keep = gpu_data(w, None, data, None, g2)
+        b = empty(G.nb)
+        kfbi.kfbi_bie_rhs(G.handle, d, b)
+        bh = host(b)
+        assert abs(float(bh.mean())) < 1e-14 * float(np.abs(bh).max())
+        dens = empty(G.nb)
+        opts = kfbi.GmresOpts(rtol=1e-10, restart=100, max_iter=100, x0=None)
+        info = kfbi.kfbi_gmres_solve(G.handle, d, opts, dens)
+        assert info.iters <= row["iterations"] + 10, (info.iters, row)
+        u = empty(G.grid_shape)
+        kfbi.kfbi_evaluate(G.handle, d, dens, u)
+        mask = torch.zeros(G.grid_shape, dtype=torch.uint8, device="cuda")
+        kfbi.kfbi_inside_mask(G.handle, mask)
+        inside = host(mask).astype(bool)
+        einf, e2 = _err(host(u), w, inside)
+        assert einf < 3.0 * row["einf"] and e2 < 3.0 * row["e2"], (precision, einf, e2, row)
+        sols.append((host(u)[inside], inside))
+        G.close()
+    (um, _), (u64, _) = sols
+    dm = um - u64
+    assert np.abs(dm - dm.mean()).max() < 1e-7
+
+
+def test_neumann_torus_too_close_to_the_box_is_refused():
+    """At N = 64 the box wall is 2.1 h from the paper's torus: the outside
+    trace fit of the DOFs there is singular and creation reports it."""
+    from paper_2309_05965_gb300 import build, kfbi
+    build.build()
+    with pytest.raises(kfbi.KfbiError) as e:
+        kfbi.Problem.from_workload(W.neumann_torus_3d(64), precision=kfbi.MIXED)
+    assert e.value.status == 3   # KFBI_ERR_SINGULAR

@@ -314,9 +314,13 @@ def torus_helmholtz_3d(n: int = 128) -> Workload:
 def neumann_torus_3d(n: int = 64, kappa: float = 0.0) -> Workload:
     """The paper's 3D Neumann example (Sec. 7.2.1): torus (1 - sqrt(x^2+y^2))^2
     + z^2 < 0.4^2 in [-1.5, 1.5]^3, u = e^z (cos 2x + cos 3y), Poisson
-    (kappa = 0, solution fixed up to a constant) or modified Helmholtz."""
+    (kappa = 0, solution fixed up to a constant) or modified Helmholtz.
+    cos(alpha) = 0.55, inside the admissible range (0, 1/sqrt(3)) of 3D: fewer
+    overlapping DOFs than 0.4 and a GMRES count at tolerance 1e-10 close to
+    the paper's.  At N = 64 the box wall lies 2.1 h from the torus, too close
+    for a one-sided outside trace fit (the library refuses that grid)."""
     return Workload("neumann_torus_3d", 3, n, -1.5, 1.5, LS_TORUS, [1.0, 0.4],
-                    KIND_NEUMANN, kappa=kappa, exact="exp_cos3")
+                    KIND_NEUMANN, kappa=kappa, cos_alpha=0.55, exact="exp_cos3")
 
 
 def neumann_ellipse_2d(n: int = 64, kappa: float = 0.0) -> Workload:
