@@ -53,13 +53,15 @@ from . import traces as TR
 class Problem:
     """Set-up of one geometry (all integer decisions) plus the operators."""
 
-    def __init__(self, w: W.Workload):
+    def __init__(self, w: W.Workload, kt: float | None = None):
         self.w = w
         d, n = w.dim, w.n
         self.d, self.n, self.order = d, n, w.order
         self.grid = G.Grid(d, n, w.lo, w.h)
         self.h = w.h
-        if w.kind in (W.KIND_DIRICHLET, W.KIND_NEUMANN):
+        if kt is not None:
+            self.kt = kt
+        elif w.kind in (W.KIND_DIRICHLET, W.KIND_NEUMANN):
             self.kt = w.kappa / w.sigma_in
         else:
             self.kt = w.kappa
@@ -235,6 +237,82 @@ class Problem:
                            max_iter=max_iter)
         u = self.evaluate(x, g1, data)
         return u, x, it, rel
+
+
+class InterfaceSystem:
+    """General interface problem, eqs. (IFP) and (bie-ifp-1): any sigma_i,
+    kappa_i, unknowns phi = u_1 and psi = sigma_2 d_n u_2 at the DOFs
+    (x = [phi; psi], 2 N_b entries), Omega_1 the inside of Gamma.
+
+    With G_i the Green's function of sigma_i Lap - kappa_i and the unit-sigma
+    potentials of kappa~_i = kappa_i/sigma_i (S_i = S~_i/sigma_i, K_i = K~_i,
+    K'_i = K~'_i, D_i = sigma_i D~_i), the potential w_i of box operator
+    Lap - kappa~_i with jumps [u] = phi, [d_n u] = psi/sigma_i equals
+    D~_i phi - S_i psi, so (avg = mean of the two one-sided limits)
+        avg value   w_i = K_i phi - S_i psi,
+        sigma_i avg d_n w_i = D_i phi - K'_i psi,
+    and the left-hand side of eq. (bie-ifp-1) is
+        A [phi; psi] = [phi - (avg w_1 - avg w_2);
+                        psi - (sigma_1 avg d_n w_1 - sigma_2 avg d_n w_2)].
+    Right-hand side: with P_1 the kappa~_1 potential of [d_n u] = g2/sigma_1
+    and F = f_1/sigma_1 in Omega_1 (G_1 f_1 - S_1 g2), and P_2 the kappa~_2
+    potential of [u] = g1, F = f_2/sigma_2 in Omega_2 and the outer data g_B
+    (G_2 f_2 + K_2 g1),
+        b = [g1/2 + avg P_1 + avg P_2;
+             -g2/2 + sigma_1 avg d_n P_1 + sigma_2 avg d_n P_2].
+    Solution: u_1 (extended by 0) is the kappa~_1 potential of [u] = phi,
+    [d_n u] = (psi + g2)/sigma_1, F = f_1/sigma_1 in Omega_1; u_2 (0 in
+    Omega_1) the kappa~_2 potential of [u] = -(phi - g1), [d_n u] =
+    -psi/sigma_2, F = f_2/sigma_2 in Omega_2, outer data g_B.
+    Reading: the outer boundary data of the paper's homogeneous condition
+    may be non-zero and enter through P_2 and u_2 only."""
+
+    def __init__(self, w: W.Workload):
+        self.w = w
+        self.s1, self.s2 = w.sigma_in, w.sigma_out
+        self.P1 = Problem(w, kt=w.kappa / w.sigma_in)
+        self.P2 = Problem(w, kt=w.kappa_out / w.sigma_out)
+        self.nb = self.P1.nb
+        self.inside = self.P1.inside
+        self.surf = self.P1.surf
+
+    def _avg(self, P, a, b, *data):
+        u, cv, _, _ = P.potential(a, b, *data)
+        vp, vm, dp, dm = P.traces(u, cv)
+        return 0.5 * (vp + vm), 0.5 * (dp + dm)
+
+    def apply(self, x: np.ndarray) -> np.ndarray:
+        nb = self.nb
+        phi, psi = x[:nb], x[nb:]
+        v1, d1 = self._avg(self.P1, phi, psi / self.s1)
+        v2, d2 = self._avg(self.P2, phi, psi / self.s2)
+        return np.concatenate([phi - (v1 - v2), psi - (self.s1 * d1 - self.s2 * d2)])
+
+    def _sides(self, data):
+        z = np.zeros_like(data["f_in"])
+        side1 = (data["f_in"] / self.s1, z, data["lapf_in"] / self.s1, z)
+        side2 = (z, data["f_out"] / self.s2, z, data["lapf_out"] / self.s2)
+        return side1, side2
+
+    def bie_rhs(self, g1, g2, data) -> np.ndarray:
+        side1, side2 = self._sides(data)
+        z = np.zeros(self.nb)
+        v1, d1 = self._avg(self.P1, z, g2 / self.s1, *side1)
+        v2, d2 = self._avg(self.P2, g1, z, *side2, data["g_b"])
+        return np.concatenate([0.5 * g1 + v1 + v2, -0.5 * g2 + self.s1 * d1 + self.s2 * d2])
+
+    def evaluate(self, x, g1, g2, data) -> np.ndarray:
+        nb = self.nb
+        phi, psi = x[:nb], x[nb:]
+        side1, side2 = self._sides(data)
+        u1 = self.P1.potential(phi, (psi + g2) / self.s1, *side1)[0]
+        u2 = self.P2.potential(-(phi - g1), -psi / self.s2, *side2, data["g_b"])[0]
+        return np.where(self.inside, u1, u2)
+
+    def solve(self, g1, g2, data, rtol=1e-10, restart=100, max_iter=200):
+        b = self.bie_rhs(g1, g2, data)
+        x, it, rel = gmres(self.apply, b, rtol=rtol, restart=restart, max_iter=max_iter)
+        return self.evaluate(x, g1, g2, data), x, it, rel
 
 
 def gmres(apply, b, x0=None, rtol=1e-10, restart=100, max_iter=200, strict=True):

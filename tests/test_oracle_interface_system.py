@@ -1,0 +1,88 @@
+"""Pins of the oracle's general interface system, eqs. (IFP) and (bie-ifp-1),
+with different operators on the two sides (Sec. 7.2.5's coefficients:
+sigma_1 = 1, kappa_1 = 0 inside, sigma_2 = 4, kappa_2 = 10 outside).
+
+PS1 the exact densities [u_1; sigma_2 d_n u_2] at the DOFs satisfy the discrete
+    system to the discretisation error, falling at 4th order (> 12x per
+    refinement).  A wrong sign of the second potential, psi not divided by
+    sigma_i, a wrong sign of the flux row or of g2/2 leave a residual of
+    1e-1 to 1 (checked by planting each in the oracle).
+PS2 end to end on both sides of the interface: the error against the exact
+    solution falls by > 10x from N = 128 to 256 and is below 1e-9 there.
+PS3 with kappa_1/sigma_1 = kappa_2/sigma_2 the problem is also solved by the
+    mu-form of Sec. 3.2; both solutions agree to the discretisation error.
+PS4 GMRES agrees with a dense solve of the assembled 2 N_b system.
+"""
+import numpy as np
+
+import workloads as W
+from oracle import kfbi as K
+
+
+def _exact_density(w, S):
+    (ui, _, _), (_, go, _) = W.solutions(w)
+    return np.concatenate([ui(S.surf.x), w.sigma_out * np.sum(go(S.surf.x) * S.surf.n, -1)])
+
+
+def _setup(w):
+    S = K.InterfaceSystem(w)
+    d = W.grid_data(w)
+    g1, g2 = W.boundary_data(w, S.surf.x, S.surf.n)
+    return S, d, g1, g2
+
+
+def _inner(w, S):
+    m = np.zeros_like(S.inside)
+    m[tuple(slice(1, w.n) for _ in range(w.dim))] = True
+    return m
+
+
+def test_exact_densities_satisfy_the_system():
+    res = []
+    for n in (128, 256):
+        w = W.hetero_interface_2d(n)
+        S, d, g1, g2 = _setup(w)
+        b = S.bie_rhs(g1, g2, d)
+        res.append(np.linalg.norm(S.apply(_exact_density(w, S)) - b) / np.linalg.norm(b))
+    assert res[0] < 1e-8 and res[0] / res[1] > 12.0, res
+
+
+def test_heterogeneous_solve_both_sides():
+    errs = []
+    for n in (128, 256):
+        w = W.hetero_interface_2d(n)
+        S, d, g1, g2 = _setup(w)
+        u, x, it, rel = S.solve(g1, g2, d)
+        assert it <= 30
+        e = np.abs(u - W.exact_grid(w, S.inside))
+        m = _inner(w, S)
+        errs.append((e[m & S.inside].max(), e[m & ~S.inside].max()))
+    for side in (0, 1):
+        assert errs[1][side] < 1e-9 and errs[0][side] / errs[1][side] > 10.0, errs
+
+
+def test_reduces_to_mu_form():
+    w = W.hetero_interface_2d(128, sigma_in=10.0, kappa_in=0.0, sigma_out=1.0, kappa_out=0.0)
+    S, d, g1, g2 = _setup(w)
+    u_sys, _, _, _ = S.solve(g1, g2, d)
+    wm = W.hetero_interface_2d(128, sigma_in=10.0, kappa_in=0.0, sigma_out=1.0, kappa_out=0.0)
+    wm.kind = W.KIND_INTERFACE_MU
+    P = K.Problem(wm)
+    dm = W.grid_data(wm)
+    u_mu, _, _, _ = P.solve(g1, g2, dm)
+    m = _inner(w, S)
+    ex = W.exact_grid(w, S.inside)
+    e_sys = np.abs(u_sys - ex)[m].max()
+    e_mu = np.abs(u_mu - ex)[m].max()
+    assert e_sys < 3e-8 and e_mu < 3e-8, (e_sys, e_mu)
+    assert np.abs(u_sys - u_mu)[m].max() < 2.0 * max(e_sys, e_mu)
+
+
+def test_gmres_equals_dense_solve():
+    w = W.hetero_interface_2d(128)
+    S, d, g1, g2 = _setup(w)
+    b = S.bie_rhs(g1, g2, d)
+    A = np.array([S.apply(e) for e in np.eye(2 * S.nb)]).T
+    x_dense = np.linalg.solve(A, b)
+    x, it, rel = K.gmres(S.apply, b, rtol=1e-13, restart=200, max_iter=400)
+    assert np.abs(x - x_dense).max() < 1e-9 * np.abs(x_dense).max()

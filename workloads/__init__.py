@@ -31,6 +31,7 @@ LS_MOLECULE = 5     # 3D: p = [r, level, n_atoms, x1, y1, z1, x2, ...]
 KIND_DIRICHLET = 0  # interior Dirichlet BVP, eq. (bie-D)
 KIND_INTERFACE_MU = 1  # two-medium interface problem, kappa = 0, mu-form BIE
 KIND_NEUMANN = 2    # interior Neumann BVP, eq. (bie-N)
+KIND_INTERFACE_GENERAL = 3  # interface problem, any kappa_i/sigma_i, eq. (bie-ifp-1)
 
 BOX_DST = 0
 BOX_MG = 1
@@ -55,6 +56,7 @@ class Workload:
     kappa: float = 0.0
     order: int = 4
     cos_alpha: float | None = None
+    kappa_out: float = 0.0   # kappa of Omega_2 (general interface problem only)
     exact: str = ""
     extra: dict = field(default_factory=dict)
 
@@ -175,6 +177,8 @@ def solutions(w: Workload):
         return _sol_harmonic3(w.extra["amps"]), _sol_zero(3)
     if e == "exp_cos3":
         return _sol_exp_cos3(), _sol_zero(3)
+    if e == "sincos_expsin":
+        return _sol_sin_cos(), _sol_exp_sin()
     raise ValueError(f"unknown exact solution {e!r}")
 
 
@@ -206,6 +210,12 @@ def grid_data(w: Workload):
         lapf_in = _lap_of_f(w, X, inside=True)
         lapf_out = np.zeros_like(f_in)
         u_out_grid = np.zeros_like(f_in)
+    elif w.kind == KIND_INTERFACE_GENERAL:
+        f_in = w.sigma_in * li(X) - w.kappa * ui(X)
+        f_out = w.sigma_out * lo_(X) - w.kappa_out * uo(X)
+        lapf_in = _lap_of_f(w, X, inside=True)
+        lapf_out = _lap_of_f(w, X, inside=False)
+        u_out_grid = uo(X)
     else:
         f_in = w.sigma_in * li(X)
         f_out = w.sigma_out * lo_(X)
@@ -221,7 +231,7 @@ def grid_data(w: Workload):
         sl1[ax] = -1
         bmask[tuple(sl0)] = True
         bmask[tuple(sl1)] = True
-    if w.kind == KIND_INTERFACE_MU:
+    if w.kind in (KIND_INTERFACE_MU, KIND_INTERFACE_GENERAL):
         gb[bmask] = u_out_grid[bmask]
     return dict(f_in=f_in, f_out=f_out, lapf_in=lapf_in, lapf_out=lapf_out,
                 u_in=ui(X), u_out=u_out_grid, g_b=gb)
@@ -240,6 +250,12 @@ def _lap_of_f(w: Workload, X, inside: bool):
     if e == "sincos_r2":
         if inside:  # f = sigma_in * (-2 sin x cos y); lap = sigma_in * 4 sin x cos y
             return w.sigma_in * 4.0 * np.sin(X[..., 0]) * np.cos(X[..., 1])
+        return np.zeros(X.shape[:-1])
+    if e == "sincos_expsin":
+        # inside f = (-2 sigma - kappa) sin x cos y, lap f = -2 f; outside
+        # u = e^x sin y is harmonic, so f = -kappa u has lap f = 0
+        if inside:
+            return -2.0 * (-2.0 * w.sigma_in - w.kappa) * np.sin(X[..., 0]) * np.cos(X[..., 1])
         return np.zeros(X.shape[:-1])
     if e == "exp_cos3":  # f = sigma lap u - kappa u with lap(e^z cos kx) = (1 - k^2) e^z cos kx
         ez = np.exp(X[..., 2])
@@ -330,6 +346,18 @@ def neumann_ellipse_2d(n: int = 64, kappa: float = 0.0) -> Workload:
     return Workload("neumann_ellipse_2d", 2, n, -1.2, 1.2, LS_ELLIPSE,
                     [0.0, 0.0, 1.0, 0.5, -math.pi / 6], KIND_NEUMANN, kappa=kappa,
                     exact="paper_table1" if kappa == 0.0 else "exp_sin")
+
+
+def hetero_interface_2d(n: int = 128, sigma_in: float = 1.0, kappa_in: float = 0.0,
+                        sigma_out: float = 4.0, kappa_out: float = 10.0) -> Workload:
+    """2D interface problem with different operators on the two sides (the
+    coefficients of the paper's heterogeneous example, Sec. 7.2.5: Poisson
+    inside, modified Helmholtz outside) on the flower r = 0.5 + 0.1 sin 5 theta,
+    u_in = sin x cos y, u_out = e^x sin y, outer Dirichlet data from u_out."""
+    return Workload("hetero_interface_2d", 2, n, -1.0, 1.0, LS_STAR,
+                    [0.0, 0.0, 0.5, 0.1, 5.0], KIND_INTERFACE_GENERAL,
+                    sigma_in=sigma_in, sigma_out=sigma_out, kappa=kappa_in,
+                    kappa_out=kappa_out, exact="sincos_expsin")
 
 
 def star_batch_2d(count: int = 64, seed: int = 5965, sizes=(128, 256, 512, 1024)):
