@@ -60,8 +60,10 @@ typedef enum {
 typedef enum {
   KFBI_DIRICHLET_INTERIOR = 0, /* eq. (bie-D): (1/2 + K) phi = g_D - G f           */
   KFBI_INTERFACE_MU = 1,       /* mu-form BIE of Sec. 3.2 for psi = [d_n u]         */
-  KFBI_NEUMANN_INTERIOR = 2    /* eq. (bie-N): (1/2 - K') psi = g_N - sigma d_n G f;
+  KFBI_NEUMANN_INTERIOR = 2,   /* eq. (bie-N): (1/2 - K') psi = g_N - sigma d_n G f;
                                   kappa = 0: projected to zero mean (Sec. 7.2.1)    */
+  KFBI_INTERFACE_GENERAL = 3   /* eq. (bie-ifp-1): any sigma_i, kappa_i; unknowns
+                                  [phi; psi] = [u_1; sigma_2 d_n u_2], 2 N_b values */
 } kfbi_problem_kind;
 
 typedef enum { KFBI_BOX_DST = 0, KFBI_BOX_MG = 1 } kfbi_box_solver;
@@ -96,6 +98,8 @@ typedef struct {
                              default (0.707 in 2D, 0.4 in 3D)                     */
   double box_rtol;        /* inner tolerance of MG / refinement (<= 0: 1e-13)     */
   int box_max_iters;      /* inner iteration limit (<= 0: 60)                     */
+  double kappa_out;       /* general interface problem: kappa_2 of Omega_2 (kappa
+                             is then kappa_1 of Omega_1); unused otherwise        */
 } kfbi_config;
 
 /* Problem data (Sec. 2).  f_* are the physical right-hand sides f of eqs.
@@ -212,7 +216,12 @@ kfbi_status kfbi_traces(kfbi_problem* p, const double* u, const double* cvals,
 /* ---- operators and solves ---------------------------------------------- */
 
 /* One application of the discrete BIE operator (Steps 3.1-3.4 plus the BIE
- * combination): Dirichlet y = x/2 + avg trace of D x; mu-form
+ * combination).  x and y hold N_b values, or 2 N_b ([phi; psi]) for the
+ * general interface problem, whose operator is the left-hand side of eq.
+ * (bie-ifp-1): with w_i the potential of box operator Lap - kappa_i/sigma_i
+ * and jumps [u] = phi, [d_n u] = psi/sigma_i, y = [phi - (avg w_1 - avg w_2);
+ * psi - (sigma_1 avg d_n w_1 - sigma_2 avg d_n w_2)] (two box solves).
+ * Dirichlet y = x/2 + avg trace of D x; mu-form
  * y = x/2 - mu avg d_n of (-S x); Neumann y = x/2 + avg d_n of (-S x), for
  * kappa = 0 minus its arithmetic mean over the DOFs (Sec. 7.2.1: the solution
  * is fixed up to a constant; the right-hand side is projected the same way). */
@@ -229,7 +238,10 @@ kfbi_status kfbi_gmres_solve(kfbi_problem* p, const kfbi_data* data,
                              kfbi_gmres_info* info);
 /* Grid solution from a density by superposition (one more potential solve):
  * Dirichlet u = D phi + N f; Neumann u = -S psi + N f (kappa = 0: up to an
- * additive constant); interface u with [u] = g1, [d_n u] = psi. */
+ * additive constant); interface u with [u] = g1, [d_n u] = psi; general
+ * interface problem: in Omega_1 the kappa_1 potential of [u] = phi,
+ * [d_n u] = (psi + g2)/sigma_1, f_1; in Omega_2 the kappa_2 potential of
+ * [u] = g1 - phi, [d_n u] = -psi/sigma_2, f_2 and g_b (two box solves). */
 kfbi_status kfbi_evaluate(kfbi_problem* p, const kfbi_data* data, const double* density,
                           double* u_grid);
 

@@ -95,7 +95,7 @@ kfbi_status kfbi_create_batch(kfbi_problem* const* problems, int count, kfbi_bat
   };
   for (kfbi_problem* p : b->ps) {
     if (p->stream != b->stream || p->g.d != p0->g.d || p->cfg.precision != KFBI_MIXED ||
-        p->cfg.kind == KFBI_NEUMANN_INTERIOR ||
+        (p->cfg.kind != KFBI_DIRICHLET_INTERIOR && p->cfg.kind != KFBI_INTERFACE_MU) ||
         p->cfg.box_solver != KFBI_BOX_DST || p->gm.m != b->m || p->nb > 32768)
       return bail(fail(p0, KFBI_ERR_UNSUPPORTED,
                        "a batch needs Dirichlet or interface problems on one stream, of one dimension, "

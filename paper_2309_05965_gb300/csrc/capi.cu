@@ -18,7 +18,34 @@ kfbi_status fail(kfbi_problem* p, kfbi_status s, const std::string& msg) {
 }
 
 // One application of the discrete BIE operator: Steps 3.1-3.4 + combination.
+// General interface kind: one potential per side operator with jumps
+// [u] = a, [d_n u] = b and no sources, then its four one-sided traces.
+static kfbi_status potential_traces(kfbi_problem* q, const double* a, const double* b, double* T) {
+  const int nb = q->nb;
+  KFBI_TRY(launch_correction_values(q, a, b, nullptr, q->cvals));
+  KFBI_TRY(launch_rhs(q, q->cvals, nullptr, q->rhs));
+  KFBI_TRY(box_solve(q, q->rhs, q->ugrid));
+  return launch_traces(q, q->ugrid, q->cvals, T, T + nb, T + 2 * nb, T + 3 * nb);
+}
+
+// eq. (bie-ifp-1), left-hand side: x = [phi; psi]; w_i has [u] = phi,
+// [d_n u] = psi/sigma_i under Lap - kappa_i/sigma_i;
+// y = [phi - (avg w_1 - avg w_2); psi - (sigma_1 avg d_n w_1 - sigma_2 avg d_n w_2)]
+static kfbi_status apply_general(kfbi_problem* p, const double* x, double* y) {
+  kfbi_problem* q = p->twin;
+  q->stream = p->stream;
+  const int nb = p->nb;
+  double* T = p->gen;
+  double* s = p->gen + 8 * (size_t)nb;
+  const double s1 = p->cfg.sigma_in, s2 = p->cfg.sigma_out;
+  KFBI_TRY(launch_gen_scale(p, x + nb, 1.0 / s1, 1.0 / s2, s, s + nb));
+  KFBI_TRY(potential_traces(p, x, s, T));
+  KFBI_TRY(potential_traces(q, x, s + nb, T + 4 * (size_t)nb));
+  return launch_gen_combine(p, x, 1.0, x + nb, 1.0, T, -1.0, 1.0, -s1, s2, y);
+}
+
 kfbi_status apply_operator_impl(kfbi_problem* p, const double* x, double* y) {
+  if (p->cfg.kind == KFBI_INTERFACE_GENERAL) return apply_general(p, x, y);
   const bool dir = p->cfg.kind == KFBI_DIRICHLET_INTERIOR;
   const bool neu = p->cfg.kind == KFBI_NEUMANN_INTERIOR;
   // Step 3.1 (fitted and evaluated at the irregular nodes)
@@ -64,9 +91,9 @@ kfbi_status apply_operator_fast(kfbi_problem* p, const double* x, double* y) {
     p->op_graph = gr;
     KFBI_CUDA(p, cudaGraphInstantiate(&p->op_exec, gr, 0));
   }
-  KFBI_CUDA(p, cudaMemcpyAsync(p->xbuf, x, sizeof(double) * p->nb, cudaMemcpyDeviceToDevice, st));
+  KFBI_CUDA(p, cudaMemcpyAsync(p->xbuf, x, sizeof(double) * p->nx, cudaMemcpyDeviceToDevice, st));
   KFBI_CUDA(p, cudaGraphLaunch(p->op_exec, st));
-  KFBI_CUDA(p, cudaMemcpyAsync(y, p->ybuf, sizeof(double) * p->nb, cudaMemcpyDeviceToDevice, st));
+  KFBI_CUDA(p, cudaMemcpyAsync(y, p->ybuf, sizeof(double) * p->nx, cudaMemcpyDeviceToDevice, st));
   for (int k = 0; k < KFBI_KC_COUNT; ++k) p->prof.launches[k] += p->op_counts[k];
   return KFBI_OK;
 }
@@ -83,7 +110,41 @@ static kfbi_status potential_with_data(kfbi_problem* p, const double* a, const d
   return launch_set_boundary(p, u, use_gb ? dd.g_b : nullptr);
 }
 
+// The data of each side of the general interface problem: f_1 (Omega_1) for
+// the kappa_1 operator; f_2 (Omega_2) and the outer values g_b for kappa_2.
+static void side_data(const kfbi_data* data, kfbi_data* d1, kfbi_data* d2) {
+  memset(d1, 0, sizeof(*d1));
+  memset(d2, 0, sizeof(*d2));
+  d1->f_in = data->f_in;
+  d1->lapf_in = data->lapf_in;
+  d2->f_out = data->f_out;
+  d2->lapf_out = data->lapf_out;
+  d2->g_b = data->g_b;
+}
+
+// eq. (bie-ifp-1), right-hand side: P_1 = kappa_1 potential of [d_n u] = g2/sigma_1
+// and f_1; P_2 = kappa_2 potential of [u] = g1, f_2 and g_b;
+// b = [g1/2 + avg P_1 + avg P_2; -g2/2 + sigma_1 avg d_n P_1 + sigma_2 avg d_n P_2]
+static kfbi_status bie_rhs_general(kfbi_problem* p, const kfbi_data* data, double* bvec) {
+  kfbi_problem* q = p->twin;
+  q->stream = p->stream;
+  const int nb = p->nb;
+  double* T = p->gen;
+  double* s = p->gen + 8 * (size_t)nb;
+  const double s1 = p->cfg.sigma_in, s2 = p->cfg.sigma_out;
+  kfbi_data d1, d2;
+  side_data(data, &d1, &d2);
+  KFBI_TRY(launch_gen_scale(p, data->g2, 1.0 / s1, 0.0, s, s + nb));
+  KFBI_TRY(potential_with_data(p, nullptr, s, &d1, false, p->ugrid));
+  KFBI_TRY(launch_traces(p, p->ugrid, p->cvals, T, T + nb, T + 2 * nb, T + 3 * nb));
+  KFBI_TRY(potential_with_data(q, data->g1, nullptr, &d2, true, q->ugrid));
+  KFBI_TRY(launch_traces(q, q->ugrid, q->cvals, T + 4 * (size_t)nb, T + 5 * (size_t)nb, T + 6 * (size_t)nb,
+                         T + 7 * (size_t)nb));
+  return launch_gen_combine(p, data->g1, 0.5, data->g2, -0.5, T, 1.0, 1.0, s1, s2, bvec);
+}
+
 kfbi_status bie_rhs_impl(kfbi_problem* p, const kfbi_data* data, double* bvec) {
+  if (p->cfg.kind == KFBI_INTERFACE_GENERAL) return bie_rhs_general(p, data, bvec);
   const bool dir = p->cfg.kind == KFBI_DIRICHLET_INTERIOR;
   if (dir) {
     // b = g_D - G f, G f = avg trace of N f (a = b = 0, F = f/sigma inside)
@@ -149,12 +210,13 @@ kfbi_status kfbi_create_problem(const kfbi_config* cfg, const kfbi_levelset* ls,
     return bail(KFBI_ERR_ARG);
   }
   if (cfg->kind != KFBI_DIRICHLET_INTERIOR && cfg->kind != KFBI_INTERFACE_MU &&
-      cfg->kind != KFBI_NEUMANN_INTERIOR) {
+      cfg->kind != KFBI_NEUMANN_INTERIOR && cfg->kind != KFBI_INTERFACE_GENERAL) {
     fail(p, KFBI_ERR_ARG, "unknown problem kind");
     return bail(KFBI_ERR_ARG);
   }
-  if (!(cfg->sigma_in > 0) || (cfg->kind == KFBI_INTERFACE_MU && !(cfg->sigma_out > 0)) ||
-      !(cfg->kappa >= 0)) {
+  const bool two_sides = cfg->kind == KFBI_INTERFACE_MU || cfg->kind == KFBI_INTERFACE_GENERAL;
+  if (!(cfg->sigma_in > 0) || (two_sides && !(cfg->sigma_out > 0)) || !(cfg->kappa >= 0) ||
+      (cfg->kind == KFBI_INTERFACE_GENERAL && !(cfg->kappa_out >= 0))) {
     fail(p, KFBI_ERR_ARG, "need sigma > 0 and kappa >= 0");
     return bail(KFBI_ERR_ARG);
   }
@@ -210,11 +272,28 @@ kfbi_status kfbi_create_problem(const kfbi_config* cfg, const kfbi_levelset* ls,
     return bail(KFBI_ERR_CUDA);
   }
   if ((s = box_create(p)) != KFBI_OK) return bail(s);
+  p->nx = cfg->kind == KFBI_INTERFACE_GENERAL ? 2 * p->nb : p->nb;
+  if (cfg->kind == KFBI_INTERFACE_GENERAL) {
+    // the kappa_2/sigma_2 operator: the same geometry set up once more with
+    // its own collocation matrices, RHS stencil and box solver
+    kfbi_config c2 = *cfg;
+    c2.kind = KFBI_INTERFACE_MU;
+    c2.kappa = cfg->kappa_out / cfg->sigma_out;
+    if ((s = kfbi_create_problem(&c2, ls, cuda_stream, &p->twin)) != KFBI_OK) {
+      fail(p, s, "kappa_2 operator: " + g_create_error);
+      return bail(s);
+    }
+    if (p->twin->nb != p->nb || p->twin->nirr != p->nirr) {
+      fail(p, KFBI_ERR_GEOMETRY, "the two side operators set up different DOFs");
+      return bail(KFBI_ERR_GEOMETRY);
+    }
+  }
   const long long nodes = p->g.nodes();
   if (dalloc(&p->cvals, p->nirr) != cudaSuccess || dalloc(&p->rhs, nodes) != cudaSuccess ||
       dalloc(&p->ugrid, nodes) != cudaSuccess || dalloc(&p->tvals, p->nb) != cudaSuccess ||
-      dalloc(&p->bvec, p->nb) != cudaSuccess || dalloc(&p->xbuf, p->nb) != cudaSuccess ||
-      dalloc(&p->ybuf, p->nb) != cudaSuccess) {
+      dalloc(&p->bvec, p->nx) != cudaSuccess || dalloc(&p->xbuf, p->nx) != cudaSuccess ||
+      dalloc(&p->ybuf, p->nx) != cudaSuccess ||
+      (p->cfg.kind == KFBI_INTERFACE_GENERAL && dalloc(&p->gen, 11 * (size_t)p->nb) != cudaSuccess)) {
     fail(p, KFBI_ERR_CUDA, "out of device memory");
     return bail(KFBI_ERR_CUDA);
   }
@@ -237,6 +316,8 @@ kfbi_status kfbi_destroy_problem(kfbi_problem* p) {
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->xbuf) cudaFree(p->xbuf);
   if (p->ybuf) cudaFree(p->ybuf);
+  if (p->gen) cudaFree(p->gen);
+  if (p->twin) kfbi_destroy_problem(p->twin);
   void* bufs[] = {p->inside, p->irr_flag, p->family, p->edge, p->axis, p->st_axis, p->pde_node,
                   p->dir_idx, p->neu_idx, p->minv, p->irr_lin, p->irr_owner, p->irr_inside,
                   p->irr_w, p->corr_nb, p->nb_off, p->nb_coef, p->cvals, p->coef, p->rhs,
@@ -423,6 +504,19 @@ kfbi_status kfbi_evaluate(kfbi_problem* p, const kfbi_data* data, const double* 
     return potential_with_data(p, density, nullptr, data, false, u_grid);
   if (p->cfg.kind == KFBI_NEUMANN_INTERIOR)
     return potential_with_data(p, nullptr, density, data, false, u_grid);
+  if (p->cfg.kind == KFBI_INTERFACE_GENERAL) {
+    if (!data || !data->g1 || !data->g2) return fail(p, KFBI_ERR_ARG, "interface evaluate needs g1 and g2");
+    kfbi_problem* q = p->twin;
+    q->stream = p->stream;
+    const int nb = p->nb;
+    double* s = p->gen + 8 * (size_t)nb;
+    kfbi_data d1, d2;
+    side_data(data, &d1, &d2);
+    KFBI_TRY(launch_gen_eval_prep(p, density, density + nb, data->g1, data->g2, s, s + nb, s + 2 * (size_t)nb));
+    KFBI_TRY(potential_with_data(p, density, s, &d1, false, u_grid));
+    KFBI_TRY(potential_with_data(q, s + 2 * (size_t)nb, s + nb, &d2, true, q->ugrid));
+    return launch_select_side(p, u_grid, q->ugrid);
+  }
   if (!data || !data->g1) return fail(p, KFBI_ERR_ARG, "interface evaluate needs data->g1");
   return potential_with_data(p, data->g1, density, data, true, u_grid);
 }

@@ -414,10 +414,10 @@ constexpr int kSmallArnoldi = 32768;   // N_b up to which one CTA runs the Arnol
 
 kfbi_status gmres_create(kfbi_problem* p, int m) {
   Gmres& G = p->gm;
-  G.nb = p->nb;
+  G.nb = p->nx;   // the BIE's unknowns (2 N_b for the general interface kind)
   G.m = m;
-  G.nchunk = std::max(1, std::min(1024, div_up(p->nb, 2048)));
-  KFBI_CUDA(p, dalloc(&G.V, (size_t)(m + 1) * p->nb));
+  G.nchunk = std::max(1, std::min(1024, div_up(G.nb, 2048)));
+  KFBI_CUDA(p, dalloc(&G.V, (size_t)(m + 1) * G.nb));
   KFBI_CUDA(p, dalloc(&G.H, (size_t)(m + 1) * m));
   KFBI_CUDA(p, dalloc(&G.cs, m));
   KFBI_CUDA(p, dalloc(&G.sn, m));

@@ -235,6 +235,44 @@ __global__ void __launch_bounds__(1024) k_mean_project(int n, double* __restrict
   for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] -= m;
 }
 
+// ---- general interface problem, eq. (bie-ifp-1) ----------------------------
+__global__ void k_gen_scale(int nb, const double* __restrict__ v, double s1, double s2,
+                            double* __restrict__ o1, double* __restrict__ o2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  const double x = v[i];
+  o1[i] = x * s1;
+  o2[i] = x * s2;
+}
+
+__global__ void k_gen_combine(int nb, const double* __restrict__ x1, double c1,
+                              const double* __restrict__ x2, double c2, const double* __restrict__ T,
+                              double a1, double a2, double b1, double b2, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  const double v1 = 0.5 * (T[i] + T[nb + i]), d1 = 0.5 * (T[2 * nb + i] + T[3 * nb + i]);
+  const double v2 = 0.5 * (T[4 * nb + i] + T[5 * nb + i]), d2 = 0.5 * (T[6 * nb + i] + T[7 * nb + i]);
+  y[i] = c1 * x1[i] + a1 * v1 + a2 * v2;
+  y[nb + i] = c2 * x2[i] + b1 * d1 + b2 * d2;
+}
+
+__global__ void k_gen_eval_prep(int nb, const double* __restrict__ phi, const double* __restrict__ psi,
+                                const double* __restrict__ g1, const double* __restrict__ g2, double r1,
+                                double r2, double* __restrict__ s1, double* __restrict__ s2,
+                                double* __restrict__ a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  s1[i] = (psi[i] + g2[i]) * r1;
+  s2[i] = -psi[i] * r2;
+  a[i] = g1[i] - phi[i];
+}
+
+__global__ void k_select_side(int tot, const uint8_t* __restrict__ inside, double* __restrict__ u,
+                              const double* __restrict__ u2) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x)
+    if (!inside[t]) u[t] = u2[t];
+}
+
 __global__ void k_set_boundary(Grid g, const double* __restrict__ gb, double* __restrict__ u) {
   const int tot = (int)g.nodes();
   const int n1 = g.n + 1;
@@ -355,6 +393,36 @@ kfbi_status launch_operator_trace(kfbi_problem* p, const double* u, const double
 kfbi_status launch_mean_project(kfbi_problem* p, double* y) {
   if (p->cfg.kind != KFBI_NEUMANN_INTERIOR || p->kt != 0.0) return KFBI_OK;
   KFBI_LAUNCH(p, KFBI_KC_TRACE, k_mean_project<<<1, 1024, 0, p->stream>>>(p->nb, y));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status launch_gen_scale(kfbi_problem* p, const double* v, double s1, double s2, double* out1,
+                             double* out2) {
+  KFBI_LAUNCH(p, KFBI_KC_OTHER, k_gen_scale<<<div_up(p->nb, 256), 256, 0, p->stream>>>(p->nb, v, s1, s2, out1, out2));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status launch_gen_combine(kfbi_problem* p, const double* x1, double c1, const double* x2, double c2,
+                               const double* T, double a1, double a2, double b1, double b2, double* y) {
+  KFBI_LAUNCH(p, KFBI_KC_TRACE, k_gen_combine<<<div_up(p->nb, 256), 256, 0, p->stream>>>(
+      p->nb, x1, c1, x2, c2, T, a1, a2, b1, b2, y));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status launch_gen_eval_prep(kfbi_problem* p, const double* phi, const double* psi, const double* g1,
+                                 const double* g2, double* s1, double* s2, double* a) {
+  KFBI_LAUNCH(p, KFBI_KC_OTHER, k_gen_eval_prep<<<div_up(p->nb, 256), 256, 0, p->stream>>>(
+      p->nb, phi, psi, g1, g2, 1.0 / p->cfg.sigma_in, 1.0 / p->cfg.sigma_out, s1, s2, a));
+  KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status launch_select_side(kfbi_problem* p, double* u, const double* u2) {
+  KFBI_LAUNCH(p, KFBI_KC_OTHER, k_select_side<<<std::min(div_up(p->g.nodes(), 256), 152 * 32), 256, 0, p->stream>>>(
+      (int)p->g.nodes(), p->inside, u, u2));
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
 }

@@ -182,6 +182,9 @@ struct kfbi_problem {
   double* ybuf = nullptr;
   bool use_graphs = true;
   double* ws_scale = nullptr;    // [1] data scale of the learned start (allocated on first use)
+  int nx = 0;                    // unknowns of the BIE: N_b, or 2 N_b for the general interface kind
+  kfbi_problem* twin = nullptr;  // general interface kind: the kappa_2/sigma_2 operator (owned)
+  double* gen = nullptr;         // general interface kind: 8 N_b traces + 3 N_b scaled data
 };
 
 namespace kfbi {
@@ -269,6 +272,19 @@ kfbi_status launch_set_boundary(kfbi_problem* p, double* u, const double* g_b);
 // Neumann BVP with kappa~ = 0 (Sec. 7.2.1): y -= mean(y) over the N_b DOFs;
 // a no-op for every other problem.
 kfbi_status launch_mean_project(kfbi_problem* p, double* y);
+// General interface kind (eq. (bie-ifp-1)): out1 = s1 v, out2 = s2 v
+// (N_b values); the combination y[i] = c1 x1[i] + a1 avgV_1 + a2 avgV_2,
+// y[N_b + i] = c2 x2[i] + b1 avgDn_1 + b2 avgDn_2 of the two trace sets
+// T = [vp1, vm1, dp1, dm1, vp2, vm2, dp2, dm2]; the evaluation data
+// s1 = (psi + g2)/sigma_1, s2 = -psi/sigma_2, a = g1 - phi; and the side
+// selection u = inside ? u : u2.
+kfbi_status launch_gen_scale(kfbi_problem* p, const double* v, double s1, double s2, double* out1,
+                             double* out2);
+kfbi_status launch_gen_combine(kfbi_problem* p, const double* x1, double c1, const double* x2, double c2,
+                               const double* T, double a1, double a2, double b1, double b2, double* y);
+kfbi_status launch_gen_eval_prep(kfbi_problem* p, const double* phi, const double* psi, const double* g1,
+                                 const double* g2, double* s1, double* s2, double* a);
+kfbi_status launch_select_side(kfbi_problem* p, double* u, const double* u2);
 // dst.cu / mg.cu
 kfbi_status box_create(kfbi_problem* p);
 void box_destroy(kfbi_problem* p);

@@ -517,6 +517,7 @@ kfbi_status kfbi_warm_start_features(kfbi_problem* p, const kfbi_data* data, con
 
 kfbi_status kfbi_warm_start(kfbi_problem* p, kfbi_mlp* m, const kfbi_data* data, double* x0) {
   if (!p || !m || !data || !x0 || !data->g1) return KFBI_ERR_ARG;
+  if (p->nx != p->nb) return fail(p, KFBI_ERR_UNSUPPORTED, "the learned start predicts one density per DOF");
   if (m->n_in != KFBI_WS_FEATURES) return fail(p, KFBI_ERR_ARG, "the network must take KFBI_WS_FEATURES inputs");
   if (m->stream != p->stream) return fail(p, KFBI_ERR_ARG, "network and problem must share a stream");
   if (m->width < KFBI_WS_FEATURES) return fail(p, KFBI_ERR_ARG, "the network width must be >= KFBI_WS_FEATURES");

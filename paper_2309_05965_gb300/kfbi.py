@@ -22,6 +22,7 @@ LS_MAX_PARAMS = 64
 DIRICHLET_INTERIOR = 0
 INTERFACE_MU = 1
 NEUMANN_INTERIOR = 2
+INTERFACE_GENERAL = 3
 BOX_DST = 0
 BOX_MG = 1
 FP64 = 0
@@ -45,7 +46,8 @@ class Config(ctypes.Structure):
                 ("sigma_in", ctypes.c_double), ("sigma_out", ctypes.c_double),
                 ("kappa", ctypes.c_double), ("box_solver", ctypes.c_int),
                 ("precision", ctypes.c_int), ("cos_alpha", ctypes.c_double),
-                ("box_rtol", ctypes.c_double), ("box_max_iters", ctypes.c_int)]
+                ("box_rtol", ctypes.c_double), ("box_max_iters", ctypes.c_int),
+                ("kappa_out", ctypes.c_double)]
 
 
 class Data(ctypes.Structure):
@@ -388,11 +390,11 @@ class Problem:
 
     def __init__(self, dim, n, lo, hi, ls_kind, ls_params, kind, sigma_in=1.0, sigma_out=1.0,
                  kappa=0.0, order=4, box_solver=BOX_DST, precision=FP64, cos_alpha=0.0,
-                 box_rtol=0.0, box_max_iters=0, stream=None):
+                 box_rtol=0.0, box_max_iters=0, stream=None, kappa_out=0.0):
         cfg = Config(dim=dim, n=n, lo=lo, hi=hi, order=order, kind=kind, sigma_in=sigma_in,
                      sigma_out=sigma_out, kappa=kappa, box_solver=box_solver,
                      precision=precision, cos_alpha=cos_alpha, box_rtol=box_rtol,
-                     box_max_iters=box_max_iters)
+                     box_max_iters=box_max_iters, kappa_out=kappa_out)
         ls = LevelSet(kind=ls_kind, n_params=len(ls_params))
         for i, v in enumerate(ls_params):
             ls.p[i] = float(v)
@@ -407,7 +409,7 @@ class Problem:
         return cls(w.dim, w.n, w.lo, w.hi, w.ls_kind, w.ls_params, w.kind,
                    sigma_in=w.sigma_in, sigma_out=w.sigma_out, kappa=w.kappa, order=w.order,
                    box_solver=box_solver, precision=precision,
-                   cos_alpha=w.cos_alpha or 0.0, **kw)
+                   cos_alpha=w.cos_alpha or 0.0, kappa_out=w.kappa_out, **kw)
 
     def close(self):
         if self.handle is not None:

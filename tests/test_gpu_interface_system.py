@@ -1,0 +1,104 @@
+"""General interface problem, eq. (bie-ifp-1) (KFBI_INTERFACE_GENERAL), on the
+GPU against the oracle: Sec. 7.2.5's coefficients (sigma_1 = 1, kappa_1 = 0
+inside; sigma_2 = 4, kappa_2 = 10 outside) on a 2D flower at 128^2 (data
+from u_1 = sin x cos y, u_2 = e^x sin y) and a 3D ellipsoid at 32^3 (u_1 =
+e^(x+y+z)/10, u_2 = 0), FP64 and mixed box solves.
+
+* operator and right-hand side element by element (2 N_b values);
+* full solves: iteration counts within 2, the GPU density solves the
+  oracle's discrete system to 1e-10, and the error against the exact solution
+  on each side within 1.1x of the oracle's;
+* batches and the learned start refuse this kind."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import kfbi as OK
+from tests.gpu_util import dev, empty, gpu_data, host, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(name):
+    if name == "flower2":
+        return W.hetero_interface_2d(128)
+    return W.Workload("ell3g", 3, 32, -1.0, 1.0, W.LS_ELLIPSOID,
+                      [0.05, -0.03, 0.02, 0.8, 0.7, 0.6], W.KIND_INTERFACE_GENERAL,
+                      sigma_in=1.0, sigma_out=4.0, kappa=0.0, kappa_out=10.0, exact="exp3")
+
+
+NAMES = ["flower2", "ell3"]
+_oracles = {}
+
+
+def _pair(name, precision):
+    from paper_2309_05965_gb300 import build, kfbi
+    build.build()
+    w = _case(name)
+    if name not in _oracles:
+        _oracles[name] = OK.InterfaceSystem(w)
+    return w, _oracles[name], kfbi.Problem.from_workload(w, precision=precision)
+
+
+def _side_errors(u, w, S):
+    e = np.abs(u - W.exact_grid(w, S.inside))
+    m = np.zeros_like(S.inside)
+    m[tuple(slice(1, w.n) for _ in range(w.dim))] = True
+    return float(e[m & S.inside].max()), float(e[m & ~S.inside].max())
+
+
+def _data(w, S):
+    data = W.grid_data(w)
+    g1, g2 = W.boundary_data(w, S.surf.x, S.surf.n)
+    d, keep = gpu_data(w, S, data, g1, g2)
+    return data, g1, g2, d, keep
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_general_operator_and_rhs(name, precision):
+    from paper_2309_05965_gb300 import kfbi
+    w, S, G = _pair(name, precision)
+    assert G.nb == S.nb
+    rng = np.random.default_rng(13)
+    x = rng.standard_normal(2 * S.nb)
+    y = empty(2 * S.nb)
+    kfbi.kfbi_apply_operator(G.handle, dev(x), y)
+    assert rel_err(host(y), S.apply(x)) < 1e-10
+    data, g1, g2, d, keep = _data(w, S)
+    b = empty(2 * S.nb)
+    kfbi.kfbi_bie_rhs(G.handle, d, b)
+    assert rel_err(host(b), S.bie_rhs(g1, g2, data)) < 1e-10
+    G.close()
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_general_solve(name, precision):
+    from paper_2309_05965_gb300 import kfbi
+    w, S, G = _pair(name, precision)
+    data, g1, g2, d, keep = _data(w, S)
+    b_ref = S.bie_rhs(g1, g2, data)
+    x_ref, it_ref, _ = OK.gmres(S.apply, b_ref, rtol=1e-12)
+    e_ref = _side_errors(S.evaluate(x_ref, g1, g2, data), w, S)
+    dens = empty(2 * S.nb)
+    opts = kfbi.GmresOpts(rtol=1e-12, restart=100, max_iter=200, x0=None)
+    info = kfbi.kfbi_gmres_solve(G.handle, d, opts, dens)
+    assert abs(info.iters - it_ref) <= 2, (info.iters, it_ref)
+    xg = host(dens)
+    assert np.linalg.norm(b_ref - S.apply(xg)) / np.linalg.norm(b_ref) < 1e-10
+    u = empty(G.grid_shape)
+    kfbi.kfbi_evaluate(G.handle, d, dens, u)
+    e_gpu = _side_errors(host(u), w, S)
+    for side in (0, 1):
+        assert e_gpu[side] <= 1.1 * e_ref[side] + 1e-12, (e_gpu, e_ref)
+    G.close()
+
+
+def test_general_refused_in_batch():
+    from paper_2309_05965_gb300 import kfbi
+    w, S, G = _pair("flower2", 1)
+    with pytest.raises(kfbi.KfbiError) as e:
+        kfbi.Batch([G])
+    assert e.value.status == 8
+    G.close()

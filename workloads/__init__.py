@@ -262,7 +262,9 @@ def _lap_of_f(w: Workload, X, inside: bool):
         c2, c3 = np.cos(2 * X[..., 0]), np.cos(3 * X[..., 1])
         s, k = w.sigma_in, w.kappa
         return s * ez * (9 * c2 + 64 * c3) - k * ez * (-3 * c2 - 8 * c3)
-    if e == "exp3":  # f = (3 - kappa) u sigma-scaled; lap f = 3 f
+    if e == "exp3":  # f = (3 - kappa) u sigma-scaled; lap f = 3 f (zero outside)
+        if not inside:
+            return np.zeros(X.shape[:-1])
         u = np.exp(X[..., 0] + X[..., 1] + X[..., 2]) / 10.0
         return 3.0 * (w.sigma_in * 3.0 - w.kappa) * u
     raise ValueError(e)
