@@ -298,6 +298,8 @@ def run_ours(args, rank, world):
         out["threed"] = threed_leg(args, stream, flush)
     if args.neumann_n > 0:
         out["neumann"] = neumann_leg(args, stream, flush)
+    if args.hetero_n > 0:
+        out["hetero"] = hetero_leg(args, stream, flush)
     if rank == 0 and args.cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_budget)
     return out
@@ -695,6 +697,65 @@ def neumann_leg(args, stream, flush):
     return out
 
 
+def hetero_leg(args, stream, flush):
+    """The general interface system (eq. (bie-ifp-1)) with Sec. 7.2.5's
+    heterogeneous coefficients on a sphere at --hetero-n^3: two box solves per
+    operator application over 2 N_b unknowns, mixed and FP64 DST, GMRES to
+    the paper's tolerance 1e-10, errors on each side of the interface."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2309_05965_gb300 import kfbi
+    n = args.hetero_n
+    w = W.hetero_sphere_3d(n)
+    grid = W.grid_data(w)
+    out = {"workload": f"sphere r=0.7 in [-1.5,1.5]^3, N={n}, sigma 1/4, kappa 0/10 (Sec. 7.2.5's "
+                       f"coefficients), general interface system, 4th order, GMRES rtol 1e-10"}
+    opts = kfbi.GmresOpts(rtol=1e-10, restart=100, max_iter=200, x0=None)
+    for name, prec in (("dst_mixed", kfbi.MIXED), ("dst_fp64", kfbi.FP64)):
+        G = kfbi.Problem.from_workload(w, precision=prec,
+                                       box_max_iters=args.box_steps if prec == kfbi.MIXED else 0)
+        xyz = torch.zeros((G.nb, 3), dtype=torch.float64, device="cuda")
+        nrm = torch.zeros_like(xyz)
+        kfbi.kfbi_dof_points(G.handle, xyz, nrm)
+        g1, g2 = W.boundary_data(w, xyz.cpu().numpy(), nrm.cpu().numpy())
+        keep = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in
+                (("g1", g1), ("g2", g2), ("f_in", grid["f_in"]), ("f_out", grid["f_out"]),
+                 ("lapf_in", grid["lapf_in"]), ("lapf_out", grid["lapf_out"]), ("g_b", grid["g_b"]))}
+        d = kfbi.make_data(**keep)
+        x = torch.zeros(2 * G.nb, dtype=torch.float64, device="cuda")
+        u = torch.zeros(G.grid_shape, dtype=torch.float64, device="cuda")
+
+        def step():
+            info = kfbi.kfbi_gmres_solve(G.handle, d, opts, x)
+            kfbi.kfbi_evaluate(G.handle, d, x, u)
+            return info
+        step()
+        ts = []
+        for _ in range(3):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = step()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ins = _inside(G, kfbi)
+        e = np.abs(u.cpu().numpy() - W.exact_grid(w, ins))
+        inner = np.zeros_like(ins)
+        inner[1:-1, 1:-1, 1:-1] = True
+        out[name] = {"solves_per_s": 1e3 / statistics.median(ts), "ms_per_solve": statistics.median(ts),
+                     "gmres_iterations": info.iters, "einf_inside": float(e[inner & ins].max()),
+                     "einf_outside": float(e[inner & ~ins].max()), "n_b": G.nb}
+        G.close()
+    out["speedup_mixed_vs_fp64"] = out["dst_mixed"]["solves_per_s"] / out["dst_fp64"]["solves_per_s"]
+    out["err_ratio_mixed_vs_fp64"] = max(
+        out["dst_mixed"][k] / out["dst_fp64"][k] for k in ("einf_inside", "einf_outside"))
+    return out
+
+
 def _inside(G, kfbi):
     import torch
     m = torch.zeros(G.grid_shape, dtype=torch.uint8, device="cuda")
@@ -865,6 +926,8 @@ def main():
                     help="grid of the 3D torus workload (0: skip)")
     ap.add_argument("--neumann-n", type=int, default=256,
                     help="grid of the Neumann torus leg (Sec. 7.2.1); 0 skips it")
+    ap.add_argument("--hetero-n", type=int, default=256,
+                    help="grid of the heterogeneous interface leg (Sec. 7.2.5's coefficients); 0 skips it")
     ap.add_argument("--profile-box", default="", choices=["", "dst", "mg"],
                     help="profiling aid: on the 3D torus at --threed-n, time the mixed box solve alone and run "
                          "one more inside cudaProfilerStart/Stop (for ncu --profile-from-start off); no JSON line")

@@ -179,6 +179,8 @@ def solutions(w: Workload):
         return _sol_exp_cos3(), _sol_zero(3)
     if e == "sincos_expsin":
         return _sol_sin_cos(), _sol_exp_sin()
+    if e == "exp3_harmonic3":
+        return _sol_exp3(), _sol_harmonic3(w.extra["amps"])
     raise ValueError(f"unknown exact solution {e!r}")
 
 
@@ -262,8 +264,8 @@ def _lap_of_f(w: Workload, X, inside: bool):
         c2, c3 = np.cos(2 * X[..., 0]), np.cos(3 * X[..., 1])
         s, k = w.sigma_in, w.kappa
         return s * ez * (9 * c2 + 64 * c3) - k * ez * (-3 * c2 - 8 * c3)
-    if e == "exp3":  # f = (3 - kappa) u sigma-scaled; lap f = 3 f (zero outside)
-        if not inside:
+    if e in ("exp3", "exp3_harmonic3"):  # f = (3 - kappa) u sigma-scaled; lap f = 3 f
+        if not inside:  # zero, or harmonic outside: f = -kappa u has lap f = 0
             return np.zeros(X.shape[:-1])
         u = np.exp(X[..., 0] + X[..., 1] + X[..., 2]) / 10.0
         return 3.0 * (w.sigma_in * 3.0 - w.kappa) * u
@@ -360,6 +362,18 @@ def hetero_interface_2d(n: int = 128, sigma_in: float = 1.0, kappa_in: float = 0
                     [0.0, 0.0, 0.5, 0.1, 5.0], KIND_INTERFACE_GENERAL,
                     sigma_in=sigma_in, sigma_out=sigma_out, kappa=kappa_in,
                     kappa_out=kappa_out, exact="sincos_expsin")
+
+
+def hetero_sphere_3d(n: int = 256) -> Workload:
+    """3D heterogeneous interface problem with Sec. 7.2.5's coefficients
+    (sigma_1 = 1, kappa_1 = 0 inside; sigma_2 = 4, kappa_2 = 10 outside) on one
+    sphere of radius 0.7 in [-1.5, 1.5]^3; u_1 = e^(x+y+z)/10, u_2 a fixed
+    harmonic quadratic, outer Dirichlet data from u_2."""
+    return Workload("hetero_sphere_3d", 3, n, -1.5, 1.5, LS_ELLIPSOID,
+                    [0.0, 0.0, 0.0, 0.7, 0.7, 0.7], KIND_INTERFACE_GENERAL,
+                    sigma_in=1.0, sigma_out=4.0, kappa=0.0, kappa_out=10.0,
+                    exact="exp3_harmonic3",
+                    extra={"amps": [0.3, 0.2, -0.1, 0.25, 0.15, -0.2, 0.1, 0.05]})
 
 
 def star_batch_2d(count: int = 64, seed: int = 5965, sizes=(128, 256, 512, 1024)):
