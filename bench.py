@@ -699,7 +699,7 @@ def neumann_leg(args, stream, flush):
 
 def hetero_leg(args, stream, flush):
     """The general interface system (eq. (bie-ifp-1)) with Sec. 7.2.5's
-    heterogeneous coefficients on a sphere at --hetero-n^3: two box solves per
+    heterogeneous coefficients and sphere centres (radius 0.6) at --hetero-n^3: two box solves per
     operator application over 2 N_b unknowns, mixed and FP64 DST, GMRES to
     the paper's tolerance 1e-10, errors on each side of the interface."""
     import numpy as np
@@ -708,10 +708,10 @@ def hetero_leg(args, stream, flush):
     import workloads as W
     from paper_2309_05965_gb300 import kfbi
     n = args.hetero_n
-    w = W.hetero_sphere_3d(n)
+    w = W.hetero_spheres_3d(n)
     grid = W.grid_data(w)
-    out = {"workload": f"sphere r=0.7 in [-1.5,1.5]^3, N={n}, sigma 1/4, kappa 0/10 (Sec. 7.2.5's "
-                       f"coefficients), general interface system, 4th order, GMRES rtol 1e-10"}
+    out = {"workload": f"three spheres r=0.6 at Sec. 7.2.5's centres in [-1.5,1.5]^3, N={n}, "
+                       f"sigma 1/4, kappa 0/10, general interface system, 4th order, GMRES rtol 1e-10"}
     opts = kfbi.GmresOpts(rtol=1e-10, restart=100, max_iter=200, x0=None)
     for name, prec in (("dst_mixed", kfbi.MIXED), ("dst_fp64", kfbi.FP64)):
         G = kfbi.Problem.from_workload(w, precision=prec,

@@ -39,6 +39,8 @@ def H(kind: int, p, X: np.ndarray) -> np.ndarray:
         rho = np.sqrt(x * x + y * y)
         t = rho - big
         return t * t + z * z - small * small
+    if kind in (W.LS_DISCS, W.LS_SPHERES):
+        return _nearest_ball(p, 2 if kind == W.LS_DISCS else 3, X)[1]
     if kind == W.LS_MOLECULE:
         r, level, na = p[0], p[1], int(p[2])
         acc = np.zeros(X.shape[:-1])
@@ -50,6 +52,28 @@ def H(kind: int, p, X: np.ndarray) -> np.ndarray:
             acc = acc + np.exp(-(dx * dx + dy * dy + dz * dz) / (r * r))
         return level - acc
     raise ValueError(f"unknown level-set kind {kind}")
+
+
+def _nearest_ball(p, d: int, X: np.ndarray):
+    """Union of n equal discs/balls (Sec. 5.1 with several interfaces): per
+    point the first centre with the smallest |X - c_k|^2 - r^2, and that value
+    (sums in the order x, y, z, then minus r^2)."""
+    r, n = p[0], int(p[1])
+    best = np.zeros(X.shape[:-1], dtype=np.int64)
+    bv = None
+    for k in range(n):
+        c = p[2 + d * k: 2 + d * (k + 1)]
+        v = (X[..., 0] - c[0]) * (X[..., 0] - c[0]) + (X[..., 1] - c[1]) * (X[..., 1] - c[1])
+        if d == 3:
+            v = v + (X[..., 2] - c[2]) * (X[..., 2] - c[2])
+        v = v - r * r
+        if bv is None:
+            bv = v
+        else:
+            take = v < bv
+            bv = np.where(take, v, bv)
+            best = np.where(take, k, best)
+    return best, bv
 
 
 def grad_H(kind: int, p, X: np.ndarray) -> np.ndarray:
@@ -86,6 +110,11 @@ def grad_H(kind: int, p, X: np.ndarray) -> np.ndarray:
         rho = np.sqrt(x * x + y * y)
         f = 2.0 * (rho - big) / rho
         return np.stack([f * x, f * y, 2.0 * z], -1)
+    if kind in (W.LS_DISCS, W.LS_SPHERES):
+        d = 2 if kind == W.LS_DISCS else 3
+        k, _ = _nearest_ball(p, d, X)
+        C = np.asarray(p[2: 2 + d * int(p[1])], dtype=np.float64).reshape(-1, d)[k]
+        return 2.0 * (X[..., :d] - C)
     if kind == W.LS_MOLECULE:
         r, level, na = p[0], p[1], int(p[2])
         g = np.zeros(X.shape)

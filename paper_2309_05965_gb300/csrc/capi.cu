@@ -224,8 +224,12 @@ kfbi_status kfbi_create_problem(const kfbi_config* cfg, const kfbi_levelset* ls,
     fail(p, KFBI_ERR_ARG, "unknown box solver");
     return bail(KFBI_ERR_ARG);
   }
-  if (ls->n_params < 0 || ls->n_params > KFBI_LS_MAX_PARAMS || ls->kind < 1 || ls->kind > 5 ||
-      ((ls->kind == KFBI_LS_ELLIPSE || ls->kind == KFBI_LS_STAR) != (cfg->dim == 2))) {
+  const bool ls2d = ls->kind == KFBI_LS_ELLIPSE || ls->kind == KFBI_LS_STAR || ls->kind == KFBI_LS_DISCS;
+  const bool balls = ls->kind == KFBI_LS_DISCS || ls->kind == KFBI_LS_SPHERES;
+  if (ls->n_params < 0 || ls->n_params > KFBI_LS_MAX_PARAMS || ls->kind < 1 || ls->kind > 7 ||
+      ls2d != (cfg->dim == 2) ||
+      (balls && (ls->n_params < 2 || !(ls->p[0] > 0) || ls->p[1] < 1 ||
+                 2 + cfg->dim * (int)ls->p[1] > ls->n_params))) {
     fail(p, KFBI_ERR_ARG, "level-set kind does not match the dimension");
     return bail(KFBI_ERR_ARG);
   }

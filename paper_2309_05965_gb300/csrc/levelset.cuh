@@ -8,9 +8,40 @@
 
 namespace kfbi {
 
+// Union of n equal discs (d = 2) or balls (d = 3): the first centre k with the
+// smallest |X - c_k|^2 - r^2, and that value.
+__device__ inline int ls_nearest_ball(const double* p, int d, const double* X, double* val) {
+  const double r = p[0];
+  const int n = static_cast<int>(p[1]);
+  int best = 0;
+  double bv = 0.0;
+  for (int k = 0; k < n; ++k) {
+    const double* c = p + 2 + d * k;
+    const double dx = X[0] - c[0], dy = X[1] - c[1];
+    double v = dx * dx + dy * dy;
+    if (d == 3) {
+      const double dz = X[2] - c[2];
+      v = v + dz * dz;
+    }
+    v = v - r * r;
+    if (k == 0 || v < bv) {
+      bv = v;
+      best = k;
+    }
+  }
+  *val = bv;
+  return best;
+}
+
 __device__ inline double ls_H(const LevelSet& L, const double* X) {
   const double* p = L.p;
   switch (L.kind) {
+    case KFBI_LS_DISCS:
+    case KFBI_LS_SPHERES: {
+      double v;
+      ls_nearest_ball(p, L.kind == KFBI_LS_DISCS ? 2 : 3, X, &v);
+      return v;
+    }
     case KFBI_LS_ELLIPSE: {
       double x = X[0] - p[0], y = X[1] - p[1];
       double c = cos(p[4]), s = sin(p[4]);
@@ -52,6 +83,16 @@ __device__ inline double ls_H(const LevelSet& L, const double* X) {
 __device__ inline void ls_grad(const LevelSet& L, const double* X, double* g) {
   const double* p = L.p;
   switch (L.kind) {
+    case KFBI_LS_DISCS:
+    case KFBI_LS_SPHERES: {
+      const int d = L.kind == KFBI_LS_DISCS ? 2 : 3;
+      double v;
+      const double* c = p + 2 + d * ls_nearest_ball(p, d, X, &v);
+      g[0] = 2.0 * (X[0] - c[0]);
+      g[1] = 2.0 * (X[1] - c[1]);
+      g[2] = d == 3 ? 2.0 * (X[2] - c[2]) : 0.0;
+      return;
+    }
     case KFBI_LS_ELLIPSE: {
       double x = X[0] - p[0], y = X[1] - p[1];
       double c = cos(p[4]), s = sin(p[4]);

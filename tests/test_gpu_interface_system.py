@@ -102,3 +102,46 @@ def test_general_refused_in_batch():
         kfbi.Batch([G])
     assert e.value.status == 8
     G.close()
+
+
+def test_three_spheres_heterogeneous():
+    """Sec. 7.2.5's coefficients and sphere centres (radius 0.6: separated
+    interfaces) at 128^3 and 256^3, where the oracle takes many minutes:
+    4th-order convergence on both sides (> 10x per refinement), mixed and
+    FP64 box solves giving the same solution to the GMRES tolerance, and
+    GMRES iteration counts independent of N (within 3)."""
+    import torch
+    from paper_2309_05965_gb300 import build, kfbi
+    build.build()
+    errs, its = [], []
+    for n in (128, 256):
+        w = W.hetero_spheres_3d(n)
+        grid = W.grid_data(w)
+        sols = []
+        for precision in (kfbi.MIXED, kfbi.FP64):
+            G = kfbi.Problem.from_workload(w, precision=precision)
+            xyz = torch.zeros((G.nb, 3), dtype=torch.float64, device="cuda")
+            nrm = torch.zeros((G.nb, 3), dtype=torch.float64, device="cuda")
+            kfbi.kfbi_dof_points(G.handle, xyz, nrm)
+            g1, g2 = W.boundary_data(w, host(xyz), host(nrm))
+            d, keep = gpu_data(w, None, grid, g1, g2)
+            dens = empty(2 * G.nb)
+            opts = kfbi.GmresOpts(rtol=1e-10, restart=100, max_iter=100, x0=None)
+            info = kfbi.kfbi_gmres_solve(G.handle, d, opts, dens)
+            u = empty(G.grid_shape)
+            kfbi.kfbi_evaluate(G.handle, d, dens, u)
+            mask = torch.zeros(G.grid_shape, dtype=torch.uint8, device="cuda")
+            kfbi.kfbi_inside_mask(G.handle, mask)
+            ins = host(mask).astype(bool)
+            e = np.abs(host(u) - W.exact_grid(w, ins))
+            inner = np.zeros_like(ins)
+            inner[1:-1, 1:-1, 1:-1] = True
+            sols.append((host(u), (float(e[inner & ins].max()), float(e[inner & ~ins].max())), info.iters))
+            G.close()
+        (um, em, im), (u64, e64, i64) = sols
+        assert np.abs(um - u64).max() < 1e-8
+        errs.append(em)
+        its.append(im)
+    for side in (0, 1):
+        assert errs[0][side] / errs[1][side] > 10.0, errs
+    assert abs(its[0] - its[1]) <= 3 and max(its) <= 30, its

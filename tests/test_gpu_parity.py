@@ -19,6 +19,7 @@ CASES = {
     "ellipse64": lambda: W.ellipse_dirichlet_2d(64),
     "table1_128": lambda: W.paper_table1_2d(128),
     "flower256": lambda: W.flower_interface_2d(256),
+    "discs128": lambda: W.discs_interface_2d(128),
     "ellipse_order2_helmholtz": None,
     "ellipsoid32": lambda: W.Workload("ell3", 3, 32, -1.0, 1.0, W.LS_ELLIPSOID,
                                       [0.05, -0.03, 0.02, 0.8, 0.7, 0.6], W.KIND_DIRICHLET,

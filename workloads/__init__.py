@@ -26,6 +26,8 @@ LS_STAR = 2         # 2D: p = [cx, cy, R0, A, k]; r = R0 + A sin(k theta)
 LS_ELLIPSOID = 3    # 3D: p = [cx, cy, cz, a, b, c]
 LS_TORUS = 4        # 3D: p = [R, r] (axis z, centred at the origin)
 LS_MOLECULE = 5     # 3D: p = [r, level, n_atoms, x1, y1, z1, x2, ...]
+LS_DISCS = 6        # 2D: p = [r, n, x1, y1, ...], union of n separated discs
+LS_SPHERES = 7      # 3D: p = [r, n, x1, y1, z1, ...], union of n separated balls
 
 # Problem kinds (shared with kfbi_problem_kind).
 KIND_DIRICHLET = 0  # interior Dirichlet BVP, eq. (bie-D)
@@ -373,6 +375,29 @@ def hetero_sphere_3d(n: int = 256) -> Workload:
                     [0.0, 0.0, 0.0, 0.7, 0.7, 0.7], KIND_INTERFACE_GENERAL,
                     sigma_in=1.0, sigma_out=4.0, kappa=0.0, kappa_out=10.0,
                     exact="exp3_harmonic3",
+                    extra={"amps": [0.3, 0.2, -0.1, 0.25, 0.15, -0.2, 0.1, 0.05]})
+
+
+def discs_interface_2d(n: int = 128, contrast: float = 10.0) -> Workload:
+    """2D Poisson interface problem with four disjoint interfaces: discs of
+    radius 0.25 centred at (+-0.45, +-0.45) (0.4 apart), sigma_in/sigma_out =
+    contrast, u_in = sin x cos y, u_out = x^2 + y^2."""
+    return Workload("discs_interface_2d", 2, n, -1.0, 1.0, LS_DISCS,
+                    [0.25, 4.0, -0.45, -0.45, 0.45, -0.45, -0.45, 0.45, 0.45, 0.45],
+                    KIND_INTERFACE_MU, sigma_in=contrast, sigma_out=1.0, exact="sincos_r2")
+
+
+def hetero_spheres_3d(n: int = 256) -> Workload:
+    """Sec. 7.2.5's heterogeneous problem (sigma_1 = 1, kappa_1 = 0 inside;
+    sigma_2 = 4, kappa_2 = 10 outside) with its three sphere centres
+    (0.5, 0.5, 0.5), (-0.5, -0.5, 0.5), (0.5, -0.5, -0.5) but radius 0.6
+    instead of 0.7 (the paper's spheres are 0.014 apart, which needs the
+    treatment of arbitrarily close interfaces); box [-1.5, 1.5]^3,
+    u_1 = e^(x+y+z)/10, u_2 a fixed harmonic quadratic."""
+    return Workload("hetero_spheres_3d", 3, n, -1.5, 1.5, LS_SPHERES,
+                    [0.6, 3.0, 0.5, 0.5, 0.5, -0.5, -0.5, 0.5, 0.5, -0.5, -0.5],
+                    KIND_INTERFACE_GENERAL, sigma_in=1.0, sigma_out=4.0, kappa=0.0,
+                    kappa_out=10.0, exact="exp3_harmonic3",
                     extra={"amps": [0.3, 0.2, -0.1, 0.25, 0.15, -0.2, 0.1, 0.05]})
 
 
