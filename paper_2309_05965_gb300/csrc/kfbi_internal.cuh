@@ -39,6 +39,7 @@ enum SetupFlag : int {
   kFlagTraceSingular = 2, // first DOF with a singular trace fit (+1)
   kFlagOutOfBox = 3,      // a stencil left the grid (+1)
   kFlagClosestFallback = 4,  // count of irregular nodes that needed the global search
+  kFlagMultiCross = 5,    // first grid node whose compact stencil spans two interfaces (+1)
   kFlagCount = 8
 };
 

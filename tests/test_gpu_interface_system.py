@@ -145,3 +145,17 @@ def test_three_spheres_heterogeneous():
     for side in (0, 1):
         assert errs[0][side] / errs[1][side] > 10.0, errs
     assert abs(its[0] - its[1]) <= 3 and max(its) <= 30, its
+
+
+def test_interfaces_closer_than_the_grid_are_refused():
+    """The paper's spheres of Sec. 7.2.5 (radius 0.7, 0.014 apart) at 128^3:
+    compact stencils span two spheres, which needs the treatment of
+    arbitrarily close interfaces; creation reports it instead of computing
+    those nodes' corrections from one interface."""
+    from paper_2309_05965_gb300 import build, kfbi
+    build.build()
+    w = W.hetero_spheres_3d(128)
+    w.ls_params = [0.7] + list(w.ls_params[1:])
+    with pytest.raises(kfbi.KfbiError) as e:
+        kfbi.Problem.from_workload(w, precision=kfbi.MIXED)
+    assert e.value.status == 2 and "two interfaces" in str(e.value), str(e.value)
