@@ -690,7 +690,8 @@ def neumann_leg(args, stream, flush):
         e = e - e.mean()
         out[name] = {"solves_per_s": 1e3 / statistics.median(ts), "ms_per_solve": statistics.median(ts),
                      "gmres_iterations": info.iters, "einf": float(np.abs(e).max()),
-                     "e2": float(np.sqrt(np.mean(e * e))), "n_b": G.nb}
+                     "e2": float(np.sqrt(np.mean(e * e))), "n_b": G.nb,
+                     "kernel_ms_by_class": _class_profile(G, kfbi, step)}
         G.close()
     out["speedup_mixed_vs_fp64"] = out["dst_mixed"]["solves_per_s"] / out["dst_fp64"]["solves_per_s"]
     out["err_ratio_mixed_vs_fp64"] = out["dst_mixed"]["einf"] / out["dst_fp64"]["einf"]
@@ -748,12 +749,23 @@ def hetero_leg(args, stream, flush):
         inner[1:-1, 1:-1, 1:-1] = True
         out[name] = {"solves_per_s": 1e3 / statistics.median(ts), "ms_per_solve": statistics.median(ts),
                      "gmres_iterations": info.iters, "einf_inside": float(e[inner & ins].max()),
-                     "einf_outside": float(e[inner & ~ins].max()), "n_b": G.nb}
+                     "einf_outside": float(e[inner & ~ins].max()), "n_b": G.nb,
+                     "kernel_ms_by_class": _class_profile(G, kfbi, step)}
         G.close()
     out["speedup_mixed_vs_fp64"] = out["dst_mixed"]["solves_per_s"] / out["dst_fp64"]["solves_per_s"]
     out["err_ratio_mixed_vs_fp64"] = max(
         out["dst_mixed"][k] / out["dst_fp64"][k] for k in ("einf_inside", "einf_outside"))
     return out
+
+
+def _class_profile(G, kfbi, step):
+    """Device time and launches per kernel class over one more step, from the
+    library's per-launch CUDA events (launches serialised by the events)."""
+    kfbi.kfbi_profile_enable(G.handle, True)
+    step()
+    prof = kfbi.kfbi_profile_read(G.handle)
+    kfbi.kfbi_profile_enable(G.handle, False)
+    return {k: {"ms": round(v[0], 4), "launches": int(v[1])} for k, v in prof.items() if v[1] > 0}
 
 
 def _inside(G, kfbi):

@@ -287,6 +287,7 @@ kfbi_status kfbi_create_problem(const kfbi_config* cfg, const kfbi_levelset* ls,
       fail(p, s, "kappa_2 operator: " + g_create_error);
       return bail(s);
     }
+    p->twin->parent = p;
     if (p->twin->nb != p->nb || p->twin->nirr != p->nirr) {
       fail(p, KFBI_ERR_GEOMETRY, "the two side operators set up different DOFs");
       return bail(KFBI_ERR_GEOMETRY);
@@ -529,7 +530,7 @@ kfbi_status kfbi_evaluate(kfbi_problem* p, const kfbi_data* data, const double* 
 
 namespace kfbi {
 
-Launch::Launch(kfbi_problem* pp, int c) : p(pp), cls(c) {
+Launch::Launch(kfbi_problem* pp, int c) : p(pp->parent ? pp->parent : pp), cls(c) {
   p->prof.launches[c]++;
   if (!p->prof.on) return;
   Profiler& P = p->prof;

@@ -185,6 +185,7 @@ struct kfbi_problem {
   double* ws_scale = nullptr;    // [1] data scale of the learned start (allocated on first use)
   int nx = 0;                    // unknowns of the BIE: N_b, or 2 N_b for the general interface kind
   kfbi_problem* twin = nullptr;  // general interface kind: the kappa_2/sigma_2 operator (owned)
+  kfbi_problem* parent = nullptr;  // set on a twin: its launches are counted and timed there
   double* gen = nullptr;         // general interface kind: 8 N_b traces + 3 N_b scaled data
 };
 
