@@ -71,13 +71,13 @@ kfbi_status apply_operator_fast(kfbi_problem* p, const double* x, double* y) {
     KFBI_CUDA(p, cudaStreamSynchronize(st));
     long long before[KFBI_KC_COUNT];
     for (int k = 0; k < KFBI_KC_COUNT; ++k) before[k] = p->prof.launches[k];
-    p->stream = p->cap_stream;
+    set_stream(p, p->cap_stream);
     cudaError_t e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
     kfbi_status s = KFBI_OK;
     if (e == cudaSuccess) s = apply_operator_impl(p, p->xbuf, p->ybuf);
     cudaGraph_t gr = nullptr;
     cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(p->cap_stream, &gr) : e;
-    p->stream = st;
+    set_stream(p, st);
     for (int k = 0; k < KFBI_KC_COUNT; ++k) {
       p->op_counts[k] = p->prof.launches[k] - before[k];
       p->prof.launches[k] = before[k];
@@ -314,6 +314,12 @@ kfbi_status kfbi_create_problem(const kfbi_config* cfg, const kfbi_levelset* ls,
 kfbi_status kfbi_destroy_problem(kfbi_problem* p) {
   if (!p) return KFBI_OK;
   if (p->stream) cudaStreamSynchronize(p->stream);
+  if (p->twin) {
+    // first, while the parent's streams exist; the twin works on the parent's stream
+    p->twin->stream = p->stream;
+    kfbi_destroy_problem(p->twin);
+    p->twin = nullptr;
+  }
   gmres_destroy(p);
   box_destroy(p);
   if (p->op_exec) cudaGraphExecDestroy(p->op_exec);
@@ -322,7 +328,6 @@ kfbi_status kfbi_destroy_problem(kfbi_problem* p) {
   if (p->xbuf) cudaFree(p->xbuf);
   if (p->ybuf) cudaFree(p->ybuf);
   if (p->gen) cudaFree(p->gen);
-  if (p->twin) kfbi_destroy_problem(p->twin);
   void* bufs[] = {p->inside, p->irr_flag, p->family, p->edge, p->axis, p->st_axis, p->pde_node,
                   p->dir_idx, p->neu_idx, p->minv, p->irr_lin, p->irr_owner, p->irr_inside,
                   p->irr_w, p->corr_nb, p->nb_off, p->nb_coef, p->cvals, p->coef, p->rhs,

@@ -526,7 +526,7 @@ static kfbi_status capture_body(kfbi_problem* p, cudaGraph_t into, cudaGraph_t* 
   for (int k = 0; k < KFBI_KC_COUNT; ++k) before[k] = p->prof.launches[k];
   const bool prof = p->prof.on;
   p->prof.on = false;
-  p->stream = p->cap_stream;
+  set_stream(p, p->cap_stream);
   kfbi_status s = KFBI_OK;
   cudaError_t e = into ? cudaStreamBeginCaptureToGraph(p->cap_stream, into, nullptr, nullptr, 0,
                                                        cudaStreamCaptureModeThreadLocal)
@@ -534,7 +534,7 @@ static kfbi_status capture_body(kfbi_problem* p, cudaGraph_t into, cudaGraph_t* 
   if (e == cudaSuccess) s = iteration_body(p, cond, use_cond);
   cudaGraph_t gr = nullptr;
   cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(p->cap_stream, &gr) : e;
-  p->stream = st;
+  set_stream(p, st);
   p->prof.on = prof;
   for (int k = 0; k < KFBI_KC_COUNT; ++k) {
     G.it_counts[k] = p->prof.launches[k] - before[k];

@@ -217,6 +217,13 @@ inline int div_up(long long a, long long b) { return static_cast<int>((a + b - 1
 // with sigma_in, and no outer boundary data.
 inline bool interior_bvp(const kfbi_problem* p) { return p->cfg.kind != KFBI_INTERFACE_MU; }
 
+// The stream a problem launches on, and its twin with it (graph captures
+// switch both to the capture stream and back).
+inline void set_stream(kfbi_problem* p, cudaStream_t s) {
+  p->stream = s;
+  if (p->twin) p->twin->stream = s;
+}
+
 // ---- device helpers -------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

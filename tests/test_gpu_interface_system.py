@@ -159,3 +159,20 @@ def test_interfaces_closer_than_the_grid_are_refused():
     with pytest.raises(kfbi.KfbiError) as e:
         kfbi.Problem.from_workload(w, precision=kfbi.MIXED)
     assert e.value.status == 2 and "two interfaces" in str(e.value), str(e.value)
+
+
+def test_general_operator_multigrid():
+    """The general system with the multigrid box solver on both side
+    operators (FP64 and mixed)."""
+    from paper_2309_05965_gb300 import kfbi
+    w, S, G0 = _pair("flower2", 0)
+    G0.close()
+    rng = np.random.default_rng(19)
+    x = rng.standard_normal(2 * S.nb)
+    ref = S.apply(x)
+    for precision in (0, 1):
+        G = kfbi.Problem.from_workload(w, box_solver=kfbi.BOX_MG, precision=precision)
+        y = empty(2 * S.nb)
+        kfbi.kfbi_apply_operator(G.handle, dev(x), y)
+        assert rel_err(host(y), ref) < 1e-9
+        G.close()

@@ -157,3 +157,21 @@ def test_neumann_torus_too_close_to_the_box_is_refused():
     with pytest.raises(kfbi.KfbiError) as e:
         kfbi.Problem.from_workload(W.neumann_torus_3d(64), precision=kfbi.MIXED)
     assert e.value.status == 3   # KFBI_ERR_SINGULAR
+
+
+def test_neumann_operator_multigrid():
+    """The same operator with the multigrid box solver (FP64 and mixed)."""
+    from paper_2309_05965_gb300 import kfbi
+    w = _case("ell2_k0")
+    if "ell2_k0" not in _oracles:
+        _oracles["ell2_k0"] = OK.Problem(w)
+    P = _oracles["ell2_k0"]
+    rng = np.random.default_rng(17)
+    x = rng.standard_normal(P.nb)
+    ref = P.apply(x)
+    for precision in (0, 1):
+        G = kfbi.Problem.from_workload(w, box_solver=kfbi.BOX_MG, precision=precision)
+        y = empty(G.nb)
+        kfbi.kfbi_apply_operator(G.handle, dev(x), y)
+        assert rel_err(host(y), ref) < 1e-9
+        G.close()
