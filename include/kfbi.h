@@ -229,13 +229,15 @@ kfbi_status kfbi_traces(kfbi_problem* p, const double* u, const double* cvals,
  * kappa = 0 minus its arithmetic mean over the DOFs (Sec. 7.2.1: the solution
  * is fixed up to a constant; the right-hand side is projected the same way). */
 kfbi_status kfbi_apply_operator(kfbi_problem* p, const double* x, double* y);
-/* Right-hand side of the BIE (Algorithm 1, Step 1). */
+/* Right-hand side of the BIE (Algorithm 1, Step 1): N_b values, 2 N_b for
+ * the general interface problem (the right-hand side of eq. (bie-ifp-1)). */
 kfbi_status kfbi_bie_rhs(kfbi_problem* p, const kfbi_data* data, double* b);
 /* Algorithm 1: BIE right-hand side, GMRES (Step 4) from opts->x0 or zero.
  * A given x0 whose residual ||b - A x0|| is not below ||b|| (or not finite)
  * is dropped and GMRES starts from zero (info->x0_rejected = 1): a learned or
  * otherwise approximate start can never make the solve worse than zero.
- * density: N_b output. info: host pointer (may be NULL). */
+ * density: N_b output (2 N_b, [phi; psi], for the general interface problem;
+ * opts->x0 likewise). info: host pointer (may be NULL). */
 kfbi_status kfbi_gmres_solve(kfbi_problem* p, const kfbi_data* data,
                              const kfbi_gmres_opts* opts, double* density,
                              kfbi_gmres_info* info);
