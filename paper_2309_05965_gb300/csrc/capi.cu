@@ -17,7 +17,6 @@ kfbi_status fail(kfbi_problem* p, kfbi_status s, const std::string& msg) {
   return s;
 }
 
-// One application of the discrete BIE operator: Steps 3.1-3.4 + combination.
 // General interface kind: one potential per side operator with jumps
 // [u] = a, [d_n u] = b and no sources, then its four one-sided traces.
 static kfbi_status potential_traces(kfbi_problem* q, const double* a, const double* b, double* T) {
@@ -44,6 +43,7 @@ static kfbi_status apply_general(kfbi_problem* p, const double* x, double* y) {
   return launch_gen_combine(p, x, 1.0, x + nb, 1.0, T, -1.0, 1.0, -s1, s2, y);
 }
 
+// One application of the discrete BIE operator: Steps 3.1-3.4 + combination.
 kfbi_status apply_operator_impl(kfbi_problem* p, const double* x, double* y) {
   if (p->cfg.kind == KFBI_INTERFACE_GENERAL) return apply_general(p, x, y);
   const bool dir = p->cfg.kind == KFBI_DIRICHLET_INTERIOR;
