@@ -11,7 +11,8 @@ solve, k-d tree) used as single steps and no blocking or fusion.
 
 Modules
 -------
-levelset     H and grad H of the analytic level-set families (Sec. 5.1)
+levelset     H and grad H of the analytic level-set families, including
+             unions of separated discs/spheres (Sec. 5.1)
 geometry     classification, grid-line intersections, overlapping surface
              decomposition, reference planes, collocation stencils (Sec. 5.1, 5.4)
 collocation  local Cauchy problem by collocation, M U = Q (Sec. 5.3, eqs.
@@ -20,7 +21,10 @@ boxsolve     compact 9/27-point schemes and their DST-I solve (Sec. 5.2)
 correction   correction function C_h, irregular nodes, corrected RHS
              (eqs. (corrected-FDS)/(crc-formula))
 traces       corrected interpolation of one-sided boundary data (Sec. 5.5)
-kfbi         BIE operators, GMRES, final evaluation (Sec. 3, 4, 6, Algorithm 1)
+kfbi         BIE operators (Dirichlet eq. (bie-D), Neumann eq. (bie-N) with the
+             zero-mean projection of Sec. 7.2.1, the mu-form, and the general
+             interface system eq. (bie-ifp-1) in ``InterfaceSystem``), GMRES,
+             final evaluation (Sec. 3, 4, 6, Algorithm 1)
 
 Parity status: the integer decisions of the conventions the paper leaves open
 (cos(alpha), stencil-line choice, closest-point ties, trace stencil) are pinned
