@@ -29,6 +29,8 @@ from dataclasses import dataclass
 
 import numpy as np
 
+import workloads as W
+
 from . import levelset as LS
 
 ROOT_MAX_IT = 64
@@ -233,6 +235,38 @@ class LineIndex:
 
 class GeometryError(RuntimeError):
     pass
+
+
+def check_separated(grid: Grid, kind: int, p, inside: np.ndarray) -> None:
+    """Unions of discs/balls: interfaces closer than the grid step are not
+    handled (they need the difference of two correction functions, the remark
+    on arbitrarily close interfaces in Sec. 5.2).  Rule: an inside node within
+    1.8 h of its ball's surface whose segment to an inside compact-stencil
+    neighbour has a sample at k/8 (k = 1..7) outside Omega means two
+    interfaces in one stencil; raise GeometryError."""
+    if kind not in (W.LS_DISCS, W.LS_SPHERES):
+        return
+    d, h, n = grid.dim, grid.h, grid.n
+    r = p[0]
+    idx = np.argwhere(inside)
+    X = grid.coord(idx)
+    _, v = LS._nearest_ball(p, d, X)
+    near = (r - np.sqrt(v + r * r)) <= 1.8 * h
+    idx, X = idx[near], X[near]
+    offs = np.stack(np.meshgrid(*([np.arange(-1, 2)] * d), indexing="ij"), -1).reshape(-1, d)
+    offs = offs[np.any(offs != 0, axis=1)]
+    for o in offs:
+        q = idx + o
+        ok = np.all((q >= 0) & (q <= n), axis=1)
+        ok[ok] = inside[tuple(q[ok].T)]
+        if not ok.any():
+            continue
+        base = X[ok]
+        for s in range(1, 8):
+            Y = base + (s * 0.125) * (o * h)
+            if np.any(~(LS.H(kind, p, Y) < 0.0)):
+                raise GeometryError("a compact stencil spans two interfaces "
+                                    "(interfaces closer than the grid step)")
 
 
 def collocation_stencil(grid: Grid, surf: Surface, lines: LineIndex, i: int,

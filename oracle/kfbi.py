@@ -67,6 +67,7 @@ class Problem:
             self.kt = w.kappa
         self.cos_alpha = w.cosa()
         self.inside = G.classify(self.grid, w.ls_kind, w.ls_params)
+        G.check_separated(self.grid, w.ls_kind, w.ls_params, self.inside)
         self.surf = G.surface_points(self.grid, w.ls_kind, w.ls_params,
                                      self.cos_alpha, self.inside)
         s = self.surf
