@@ -56,7 +56,8 @@ typedef enum {
   KFBI_LS_TORUS = 4,      /* 3D p=[R,r]: (sqrt(x^2+y^2)-R)^2 + z^2 - r^2          */
   KFBI_LS_MOLECULE = 5,   /* 3D p=[r,level,n,x1,y1,z1,...]: level - sum exp(-|x-x_k|^2/r^2) */
   KFBI_LS_DISCS = 6,      /* 2D p=[r,n,x1,y1,...]: min_k |x-x_k|^2 - r^2, n separated discs
-                             (interfaces closer than a few h: not handled)        */
+                             (a compact stencil spanning two discs: refused at
+                             create with KFBI_ERR_GEOMETRY)                       */
   KFBI_LS_SPHERES = 7     /* 3D p=[r,n,x1,y1,z1,...]: the same with balls          */
 } kfbi_levelset_kind;
 
