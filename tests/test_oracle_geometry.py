@@ -110,3 +110,47 @@ def test_gauss_lemma_constant_correction():
     u, _, _, _ = P.potential(np.ones(P.nb), np.zeros(P.nb))
     inner = tuple(slice(1, P.n) for _ in range(2))
     assert np.abs(u[inner] - P.inside[inner]).max() < 1e-11
+
+
+def test_molecule_single_atom_is_a_sphere():
+    """A one-atom Gaussian-sum surface level - exp(-|x - c|^2 / r^2) = 0 is the
+    sphere |x - c| = r sqrt(-ln level): the same node classes, DOFs (points,
+    families) and normals as the sphere written as an ellipsoid with equal
+    axes, up to the root tolerance."""
+    r, level, c = 0.45, 0.4, (0.03, -0.02, 0.05)
+    R = r * math.sqrt(-math.log(level))
+    g = G.Grid(3, 24, -1.0, 2.0 / 24)
+    mol = [r, level, 1.0, *c]
+    sph = [*c, R, R, R]
+    ins_m = G.classify(g, W.LS_MOLECULE, mol)
+    ins_s = G.classify(g, W.LS_ELLIPSOID, sph)
+    assert np.array_equal(ins_m, ins_s)
+    sm = G.surface_points(g, W.LS_MOLECULE, mol, 0.4, ins_m)
+    ss = G.surface_points(g, W.LS_ELLIPSOID, sph, 0.4, ins_s)
+    assert sm.nb == ss.nb and sm.nb > 100
+    assert np.array_equal(sm.family, ss.family)
+    assert np.abs(sm.x - ss.x).max() < 1e-13
+    assert np.abs(sm.n - ss.n).max() < 1e-12
+    # points on the sphere, normals radial
+    d = sm.x - np.asarray(c)
+    assert np.abs(np.linalg.norm(d, axis=1) - R).max() < 1e-13
+    assert np.abs(sm.n - d / R).max() < 1e-12
+
+
+def test_molecule_gradient_central_differences():
+    """The analytic gradient of a three-atom surface against central finite
+    differences of H (step 1e-5: error O(1e-10) for these Gaussians)."""
+    w = W.molecule_dirichlet_3d(64)
+    rng = np.random.default_rng(7)
+    X = rng.uniform(-0.8, 0.8, size=(200, 3))
+    g = LS.grad_H(w.ls_kind, w.ls_params, X)
+    e = 1e-5
+    fd = np.zeros_like(X)
+    for k in range(3):
+        dx = np.zeros(3)
+        dx[k] = e
+        fd[:, k] = (LS.H(w.ls_kind, w.ls_params, X + dx) - LS.H(w.ls_kind, w.ls_params, X - dx)) / (2 * e)
+    assert np.abs(g - fd).max() < 1e-8
+    # far from every atom H -> level (the sum of Gaussians vanishes)
+    far = LS.H(w.ls_kind, w.ls_params, np.array([[40.0, 0.0, 0.0]]))[0]
+    assert far == w.ls_params[1]

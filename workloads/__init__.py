@@ -401,6 +401,15 @@ def hetero_spheres_3d(n: int = 256) -> Workload:
                     extra={"amps": [0.3, 0.2, -0.1, 0.25, 0.15, -0.2, 0.1, 0.05]})
 
 
+def molecule_dirichlet_3d(n: int = 64) -> Workload:
+    """3D Dirichlet modified-Helmholtz BVP (kappa = 1) inside a three-atom
+    Gaussian-sum surface 0.5 - sum_k exp(-|x - x_k|^2 / 0.4^2) < 0 (atoms at
+    (+-0.3, 0, 0) and (0, 0.3, 0.1)), u = e^{x+y+z}/10."""
+    return Workload("molecule_dirichlet_3d", 3, n, -1.0, 1.0, LS_MOLECULE,
+                    [0.4, 0.5, 3.0, -0.3, 0.0, 0.0, 0.3, 0.0, 0.0, 0.0, 0.3, 0.1],
+                    KIND_DIRICHLET, kappa=1.0, exact="exp3")
+
+
 def star_batch_2d(count: int = 64, seed: int = 5965, sizes=(128, 256, 512, 1024)):
     """Batched star-interface instances: R0~U[0.4,0.6], A~U[0,0.15], k~U{3..7},
     contrast = 10^U[0,3], N ~ U(sizes), drawn in that order per instance."""
