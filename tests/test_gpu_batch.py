@@ -2,8 +2,9 @@
 per-instance solve and the oracle.
 
 Instances are the seeded star-interface draws of the batched workload on
-grids of 128^2 to 512^2; a draw whose interface its grid cannot resolve (no
-complete collocation stencil) is skipped and the seeded stream continues."""
+grids of 128^2 to 1024^2 (the sizes the batched benchmark draws); a draw whose
+interface its grid cannot resolve (no complete collocation stencil) is skipped
+and the seeded stream continues."""
 import numpy as np
 import pytest
 
@@ -13,7 +14,7 @@ from tests.gpu_util import empty, gpu_data, host, rel_err
 
 pytestmark = pytest.mark.gpu
 
-SIZES = (128, 256, 512)
+SIZES = (128, 256, 512, 1024)
 
 
 def _instances(count, seed=5965):
@@ -54,10 +55,20 @@ def test_batch_matches_single_and_oracle():
     solve (the residual estimates agree to rounding), the density within 1e-9
     of it (both use FP32 transforms with FP64 refinement to 1e-11), a backward
     error <= 1e-8 in the oracle's FP64 discrete system, and the evaluated
-    solution within discretisation accuracy of the exact one."""
+    solution within discretisation accuracy of the exact one.
+
+    Backward error in the oracle's FP64 system: b - A_o x = (b - A_m x) +
+    (A_m - A_o) x, with A_m the mixed operator GMRES ran on (FP32 transforms
+    refined to 1e-11).  The first term is GMRES's residual, <= rtol ||b||; the
+    second is measured directly (GPU mixed operator and oracle operator
+    applied to the same x) and is itself held to the operator parity bound
+    1e-10 ||A_o x||.  At contrast ~10^3, ||x|| ||A|| / ||b|| ~ cond(A) ~ 10^3,
+    so the second term, not GMRES, sets the oracle-system residual."""
     from paper_2309_05965_gb300 import kfbi
+    from tests.gpu_util import dev
     rows = _setup()
     assert len({r["w"].n for r in rows}) >= 2, "the batch must mix grid sizes"
+    assert any(r["w"].n == 1024 for r in rows), "the batch must hold a 1024^2 instance"
     opts = kfbi.GmresOpts(rtol=1e-10, restart=100, max_iter=100, x0=None)
     singles = []
     for r in rows:
@@ -74,8 +85,15 @@ def test_batch_matches_single_and_oracle():
         assert rel_err(xb, xs) < 1e-9, r["w"].name
         P = r["P"]
         b_ref = P.bie_rhs(r["g1"], r["g2"], r["data"])
-        res = np.linalg.norm(b_ref - P.apply(xb)) / np.linalg.norm(b_ref)
-        assert res < 1e-8, (r["w"].name, res)
+        Ao_x = P.apply(xb)
+        Am_x = empty(r["G"].nb)
+        kfbi.kfbi_apply_operator(r["G"].handle, dev(xb), Am_x)
+        Am_x = host(Am_x)
+        bn = np.linalg.norm(b_ref)
+        op_diff = np.linalg.norm(Am_x - Ao_x) / bn
+        assert np.abs(Am_x - Ao_x).max() <= 1e-10 * np.abs(Ao_x).max(), r["w"].name
+        res = np.linalg.norm(b_ref - Ao_x) / bn
+        assert res <= 1.5e-10 + 2.0 * op_diff, (r["w"].name, res, op_diff)
         u = empty(r["G"].grid_shape)
         kfbi.kfbi_evaluate(r["G"].handle, r["d"], x, u)
         ex = W.exact_grid(r["w"], P.inside)

@@ -24,6 +24,11 @@ CASES = {
     "ellipsoid32": lambda: W.Workload("ell3", 3, 32, -1.0, 1.0, W.LS_ELLIPSOID,
                                       [0.05, -0.03, 0.02, 0.8, 0.7, 0.6], W.KIND_DIRICHLET,
                                       kappa=1.0, exact="exp3"),
+    # the 3D torus Dirichlet problem for modified Helmholtz (kappa = 1) at the
+    # largest grid the oracle sets up in seconds (64^3: 4800 DOFs)
+    "torus64": lambda: W.torus_helmholtz_3d(64),
+    # the Gaussian-sum (molecule) level set, three atoms
+    "molecule64": lambda: W.molecule_dirichlet_3d(64),
 }
 
 
