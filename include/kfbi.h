@@ -211,6 +211,17 @@ kfbi_status kfbi_corrected_rhs(kfbi_problem* p, const double* cvals, const kfbi_
 /* Step 3.3: u = A_h^{-1} rhs on the interior (DST-I or multigrid, FP64 or
  * mixed precision, per the config); boundary layer of u set to 0. */
 kfbi_status kfbi_box_solve(kfbi_problem* p, const double* rhs, double* u);
+/* Diagnostics of the last box solve on p (Step 3.3; synchronises the stream;
+ * host outputs, each may be NULL): steps = FP32 solves of the mixed sine
+ * transform (the first plus every refinement step its convergence flag let
+ * run; 1 for the FP64 transform), outer steps of the mixed multigrid or 1 for
+ * the FP64 multigrid; cycles = V-cycles run (0 for the sine transform);
+ * rel_change = the last measured correction max|delta u| / max|u| (mixed) or
+ * normwise backward error (FP64 multigrid), 0 for the FP64 transform;
+ * converged = 1 if the inner tolerance was met.  The counts are those of the
+ * work that ran on the device, not of the launches enqueued. */
+kfbi_status kfbi_box_solve_info(kfbi_problem* p, int* steps, int* cycles, double* rel_change,
+                                int* converged);
 /* Step 3.4: one-sided values and normal derivatives at every DOF from a grid
  * function u and C at the irregular nodes (Sec. 5.5).  Any output may be NULL. */
 kfbi_status kfbi_traces(kfbi_problem* p, const double* u, const double* cvals,
@@ -363,7 +374,9 @@ kfbi_status kfbi_warm_start(kfbi_problem* p, kfbi_mlp* m, const kfbi_data* data,
  *   dim, n, lo, hi, order, kappa: the grid and the compact operator of
  *     kfbi_config (kappa is kappa~ of the unit-sigma operator Lap - kappa~);
  *   rhs: (N+1)^d device grid, interior nodes read; u: (N+1)^d device grid,
- *     written (boundary layer 0).  Both owned by the caller.
+ *     written (boundary layer 0).  Both owned by the caller; they must not
+ *     overlap (u is cleared before rhs is read): overlapping ranges return
+ *     KFBI_ERR_ARG.
  * Limits: 2D N <= 512, 3D N <= 64 (N a power of two >= 8); larger sizes or
  * invalid arguments return KFBI_ERR_ARG, CUDA failures KFBI_ERR_CUDA.
  * The first call on a device does a one-time set-up (looks up the array's

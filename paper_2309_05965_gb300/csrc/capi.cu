@@ -465,6 +465,20 @@ kfbi_status kfbi_box_solve(kfbi_problem* p, const double* rhs, double* u) {
   return box_solve(p, rhs, u);
 }
 
+kfbi_status kfbi_box_solve_info(kfbi_problem* p, int* steps, int* cycles, double* rel_change,
+                               int* converged) {
+  if (!p) return KFBI_ERR_ARG;
+  int s = 0, c = 0, conv = 0;
+  double rel = 0.0;
+  KFBI_TRY(box_steps(p, &s, &c));
+  KFBI_TRY(box_last_residual(p, &rel, &conv));
+  if (steps) *steps = s;
+  if (cycles) *cycles = c;
+  if (rel_change) *rel_change = rel;
+  if (converged) *converged = conv;
+  return KFBI_OK;
+}
+
 kfbi_status kfbi_traces(kfbi_problem* p, const double* u, const double* cvals, double* val_plus,
                         double* val_minus, double* dn_plus, double* dn_minus) {
   if (!p || !u || !cvals) return KFBI_ERR_ARG;

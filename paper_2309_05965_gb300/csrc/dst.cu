@@ -32,6 +32,14 @@
 
 namespace kfbi {
 
+// max(a, b) that returns NaN when either operand is NaN (fmaxf returns the
+// other operand): the norms of the mixed path must see a non-finite solve
+__device__ __forceinline__ float fmax_nan(float a, float b) {
+  float d;
+  asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+  return d;
+}
+
 template <typename T>
 struct Cx {
   T x, y;
@@ -91,7 +99,7 @@ struct PassArgs {
   const float* fixf;              // [0..1] 2^Fa, 2^Fb; [2..3] 2^-Fa, 2^-Fb (k_fix_scale)
   const double* fixd;             // [1] mult h^2 2^-F (with uout)
   double* uout;                   // with dstfix: also u = u_fix mult h^2 2^-F in FP64
-  unsigned long long* zero_nrm;   // first pass of a mixed solve: CTA 0 clears nrm[0..5] and
+  unsigned long long* zero_nrm;   // first pass of a mixed solve: CTA 0 clears nrm[0..6] and
   int* zero_conv;                 // the convergence flag before anything reads them
 };
 
@@ -325,8 +333,8 @@ __device__ __forceinline__ void dst_pass_device(const PassArgs& A, int bx, int b
       o[off] = nv;
       if (A.delta_out) A.delta_out[off] = (float)v;
       if (A.corr_max) {
-        dmx = fmaxf(dmx, fabsf((float)v));
-        umx = fmaxf(umx, fabsf((float)nv));
+        dmx = fmax_nan(dmx, fabsf((float)v));
+        umx = fmax_nan(umx, fabsf((float)nv));
       }
     } else {
       static_cast<float*>(A.dst)[off] = (float)v;
@@ -334,13 +342,13 @@ __device__ __forceinline__ void dst_pass_device(const PassArgs& A, int bx, int b
   }
   if (A.corr_max) {
     for (int o = 16; o > 0; o >>= 1) {
-      dmx = fmaxf(dmx, __shfl_xor_sync(0xffffffffu, dmx, o));
-      umx = fmaxf(umx, __shfl_xor_sync(0xffffffffu, umx, o));
+      dmx = fmax_nan(dmx, __shfl_xor_sync(0xffffffffu, dmx, o));
+      umx = fmax_nan(umx, __shfl_xor_sync(0xffffffffu, umx, o));
     }
     if ((threadIdx.x & 31) == 0) {
       // non-negative doubles order like their bit patterns
-      if (dmx > 0.f) atomicMax(A.corr_max, (unsigned long long)__double_as_longlong((double)dmx));
-      if (umx > 0.f) atomicMax(A.corr_max + 1, (unsigned long long)__double_as_longlong((double)umx));
+      if (!(dmx <= 0.f)) atomicMax(A.corr_max, (unsigned long long)__double_as_longlong((double)dmx));
+      if (!(umx <= 0.f)) atomicMax(A.corr_max + 1, (unsigned long long)__double_as_longlong((double)umx));
     }
   }
 }
@@ -668,7 +676,7 @@ __device__ __forceinline__ void dst32_body(const PassArgs& A, int bx, int by, Cx
   constexpr int L = F::L, LP = F::LP;
   constexpr int n = L / 2, nm1 = n - 1;
   if (A.zero_nrm && bx == 0 && by == 0 && threadIdx.x == 0) {
-    for (int k = 0; k < 6; ++k) A.zero_nrm[k] = 0ull;
+    for (int k = 0; k < 7; ++k) A.zero_nrm[k] = 0ull;
     *A.zero_conv = 0;
   }
   const Cx<float>* tw = static_cast<const Cx<float>*>(A.twst);
@@ -799,13 +807,13 @@ __device__ __forceinline__ void dst32_body(const PassArgs& A, int bx, int by, Cx
           const long long nA = add64(oldA[it], f2ll((vals[it].x * fa) * fb));
           A.dstfix[offs[it]] = nA;
           if (A.uout) A.uout[offs[it]] = ll2d(nA) * isc;
-          dmx = fmaxf(dmx, fabsf(vals[it].x));
+          dmx = fmax_nan(dmx, fabsf(vals[it].x));
           umi = max(umi, (unsigned)abs((int)(nA >> 32)));
           if (hasB[it]) {
             const long long nB = add64(oldB[it], f2ll((vals[it].y * fa) * fb));
             A.dstfix[offs[it] + sb] = nB;
             if (A.uout) A.uout[offs[it] + sb] = ll2d(nB) * isc;
-            dmx = fmaxf(dmx, fabsf(vals[it].y));
+            dmx = fmax_nan(dmx, fabsf(vals[it].y));
             umi = max(umi, (unsigned)abs((int)(nB >> 32)));
           }
         }
@@ -825,13 +833,13 @@ __device__ __forceinline__ void dst32_body(const PassArgs& A, int bx, int by, Cx
         if (offs[it] >= 0) {
           const double nA = oldA[it] + (double)vals[it].x;
           o[offs[it]] = nA;
-          dmx = fmaxf(dmx, fabsf(vals[it].x));
-          umx = fmaxf(umx, fabsf((float)nA));
+          dmx = fmax_nan(dmx, fabsf(vals[it].x));
+          umx = fmax_nan(umx, fabsf((float)nA));
           if (hasB[it]) {
             const double nB = oldB[it] + (double)vals[it].y;
             o[offs[it] + sb] = nB;
-            dmx = fmaxf(dmx, fabsf(vals[it].y));
-            umx = fmaxf(umx, fabsf((float)nB));
+            dmx = fmax_nan(dmx, fabsf(vals[it].y));
+            umx = fmax_nan(umx, fabsf((float)nB));
           }
         }
       }
@@ -841,10 +849,10 @@ __device__ __forceinline__ void dst32_body(const PassArgs& A, int bx, int by, Cx
       for (int it = 0; it < NIT; ++it) {
         if (offs[it] >= 0) {
           o[offs[it]] = vals[it].x;
-          dmx = fmaxf(dmx, fabsf(vals[it].x));
+          dmx = fmax_nan(dmx, fabsf(vals[it].x));
           if (hasB[it]) {
             o[offs[it] + sb] = vals[it].y;
-            dmx = fmaxf(dmx, fabsf(vals[it].y));
+            dmx = fmax_nan(dmx, fabsf(vals[it].y));
           }
         }
       }
@@ -853,12 +861,12 @@ __device__ __forceinline__ void dst32_body(const PassArgs& A, int bx, int by, Cx
   }
   if (A.corr_max) {
     for (int o = 16; o > 0; o >>= 1) {
-      dmx = fmaxf(dmx, __shfl_xor_sync(0xffffffffu, dmx, o));
-      umx = fmaxf(umx, __shfl_xor_sync(0xffffffffu, umx, o));
+      dmx = fmax_nan(dmx, __shfl_xor_sync(0xffffffffu, dmx, o));
+      umx = fmax_nan(umx, __shfl_xor_sync(0xffffffffu, umx, o));
     }
     if ((threadIdx.x & 31) == 0) {
-      if (dmx > 0.f) atomicMax(A.corr_max, (unsigned long long)__double_as_longlong((double)dmx));
-      if (umx > 0.f) atomicMax(A.corr_max + 1, (unsigned long long)__double_as_longlong((double)umx));
+      if (!(dmx <= 0.f)) atomicMax(A.corr_max, (unsigned long long)__double_as_longlong((double)dmx));
+      if (!(umx <= 0.f)) atomicMax(A.corr_max + 1, (unsigned long long)__double_as_longlong((double)umx));
     }
   }
 }
@@ -920,6 +928,7 @@ __device__ __forceinline__ void check_body(unsigned long long* nrm, double tol, 
   nrm[2] = nrm[3];
   nrm[5] = nrm[4];
   if (dm <= tol * um) *conv = 1;
+  else nrm[6] += 1ull;   // one more refinement step will run
   nrm[3] = 0ull;
   nrm[4] = 0ull;
 }
@@ -952,6 +961,17 @@ __device__ __forceinline__ void fix_scale_body(const unsigned long long* __restr
   fixf[2] = ldexpf(1.f, -Fa);                   // u = (U 2^-Fa) (mult h^2 2^-Fb); r = (r_fix 2^-Fa) 2^-Fb
   fixf[3] = (float)ldexp(multh2, -Fb);
   fixf[4] = ldexpf(1.f, -Fb);
+  if (!(um <= 1.7976931348623157e308)) {
+    // a NaN or infinite first solve (non-finite data): the integer
+    // conversions would turn it into finite values, so every conversion back
+    // to floating point yields NaN instead and the caller sees a non-finite
+    // result
+    const double qn = __longlong_as_double(0x7ff8000000000000LL);
+    fixd[1] = qn;
+    fixf[2] = __int_as_float(0x7fc00000);
+    fixf[3] = __int_as_float(0x7fc00000);
+    fixf[4] = __int_as_float(0x7fc00000);
+  }
 }
 
 __global__ void k_fix_scale(const unsigned long long* __restrict__ umax, double multh2, double kc,
@@ -1274,17 +1294,17 @@ __global__ void k_fix_add(long long tot, const float* __restrict__ e, long long*
     const float ev = e[t];
     const long long nv = add64(ufix[t], f2ll((ev * fa) * fb));
     ufix[t] = nv;
-    em = fmaxf(em, fabsf(ev));
+    em = fmax_nan(em, fabsf(ev));
     umi = max(umi, (unsigned)abs((int)(nv >> 32)));
   }
   float um = ((fmaf(u16f(umi >> 16), 65536.f, u16f(umi & 0xffffu)) * 4294967296.f) * ia) * ib;
   for (int o = 16; o > 0; o >>= 1) {
-    em = fmaxf(em, __shfl_xor_sync(0xffffffffu, em, o));
-    um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, o));
+    em = fmax_nan(em, __shfl_xor_sync(0xffffffffu, em, o));
+    um = fmax_nan(um, __shfl_xor_sync(0xffffffffu, um, o));
   }
   if ((threadIdx.x & 31) == 0) {
-    if (em > 0.f) atomicMax(corr, (unsigned long long)__double_as_longlong((double)em));
-    if (um > 0.f) atomicMax(corr + 1, (unsigned long long)__double_as_longlong((double)um));
+    if (!(em <= 0.f)) atomicMax(corr, (unsigned long long)__double_as_longlong((double)em));
+    if (!(um <= 0.f)) atomicMax(corr + 1, (unsigned long long)__double_as_longlong((double)um));
   }
 }
 
@@ -1295,9 +1315,9 @@ __global__ void k_absmax32(long long tot, const float* __restrict__ x, unsigned 
   float m = 0.f;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < (int)tot;
        t += gridDim.x * blockDim.x)
-    m = fmaxf(m, fabsf(x[t]));
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, (unsigned long long)__double_as_longlong((double)m));
+    m = fmax_nan(m, fabsf(x[t]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax_nan(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && !(m <= 0.f)) atomicMax(out, (unsigned long long)__double_as_longlong((double)m));
 }
 
 template <typename T, int P>
@@ -1533,7 +1553,7 @@ kfbi_status box_create(kfbi_problem* p) {
     KFBI_CUDA(p, cudaGetLastError());
     KFBI_CUDA(p, cudaDeviceSynchronize());
   }
-  KFBI_CUDA(p, dalloc(&B->nrm, 6));
+  KFBI_CUDA(p, dalloc(&B->nrm, 7));
   KFBI_CUDA(p, dalloc(&B->conv, 1));
   B->tol = p->cfg.box_rtol > 0 ? p->cfg.box_rtol : 1e-13;
   B->refine_steps = p->cfg.box_max_iters > 0 ? std::min(p->cfg.box_max_iters, 8) : 5;
@@ -1746,6 +1766,24 @@ kfbi_status fix_out(kfbi_problem* p, FixState* F, double* u, cudaStream_t st) {
   return KFBI_OK;
 }
 
+kfbi_status mg_steps(kfbi_problem* p, int* steps, int* cycles);
+
+// Refinement steps (FP32 solves) and V-cycles the last box solve executed:
+// the FP64 sine transform is one step and no cycle; the mixed transform
+// counts the first FP32 solve plus every correction step its convergence
+// flag let run; the multigrid counts are kept by its check kernels.
+kfbi_status box_steps(kfbi_problem* p, int* steps, int* cycles) {
+  if (p->mg) return mg_steps(p, steps, cycles);
+  *cycles = 0;
+  *steps = 1;
+  if (p->cfg.precision != KFBI_MIXED) return KFBI_OK;
+  unsigned long long c = 0;
+  KFBI_CUDA(p, cudaMemcpyAsync(&c, p->box->nrm + 6, sizeof(c), cudaMemcpyDeviceToHost, p->stream));
+  KFBI_CUDA(p, cudaStreamSynchronize(p->stream));
+  *steps = 1 + (int)std::min<unsigned long long>(c, (unsigned long long)p->box->refine_steps - 1);
+  return KFBI_OK;
+}
+
 // Host-visible diagnostics of the last mixed solve: max|R - A_h u| / max|R|.
 kfbi_status box_last_residual(kfbi_problem* p, double* rel, int* converged) {
   if (p->mg) return mg_last_residual(p, rel, converged);
@@ -1841,6 +1879,13 @@ extern "C" kfbi_status kfbi_box_solve_noalloc(int dim, int n, double lo, double 
     return KFBI_ERR_ARG;
   if ((dim == 2 && n > kNoAllocMaxN2) || (dim == 3 && n > kNoAllocMaxN3))
     return KFBI_ERR_ARG;   // beyond the fixed scratch: 2D N <= 512, 3D N <= 64
+  {
+    // u is cleared before rhs is read: overlapping grids would lose the input
+    const unsigned long long bytes =
+        sizeof(double) * (dim == 2 ? 1ULL * (n + 1) * (n + 1) : 1ULL * (n + 1) * (n + 1) * (n + 1));
+    const unsigned long long a = reinterpret_cast<uintptr_t>(rhs), b = reinterpret_cast<uintptr_t>(u);
+    if (a < b + bytes && b < a + bytes) return KFBI_ERR_ARG;
+  }
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return KFBI_ERR_CUDA;

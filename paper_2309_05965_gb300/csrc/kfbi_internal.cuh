@@ -299,6 +299,7 @@ kfbi_status box_create(kfbi_problem* p);
 void box_destroy(kfbi_problem* p);
 kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u);
 kfbi_status box_last_residual(kfbi_problem* p, double* rel, int* converged);
+kfbi_status box_steps(kfbi_problem* p, int* steps, int* cycles);
 // exact fixed-point refinement state (dst.cu), used by the mixed multigrid
 struct FixState;
 kfbi_status fix_create(kfbi_problem* p, FixState** out);

@@ -569,6 +569,7 @@ __global__ void k_mg_check_corr(unsigned long long* nrm, double tol, int* conv) 
   nrm[8] = nrm[6];
   nrm[9] = nrm[7];
   if (em <= tol * um) *conv = 1;
+  nrm[10] += 1ull;   // the outer step just checked ran
   nrm[6] = 0ull;
   nrm[7] = 0ull;
 }
@@ -621,12 +622,13 @@ __global__ void k_mg_check(unsigned long long* nrm, double tol, double anorm, in
   nrm[4] = nrm[1];
   nrm[5] = nrm[2];
   if (r <= tol * (R + anorm * um) || (rp > 0.0 && r > 0.7 * rp)) *conv = 1;
+  nrm[10] += 1ull;   // the V-cycle just checked ran
   nrm[1] = 0ull;
   nrm[2] = 0ull;
 }
 
 __global__ void k_mg_reset(unsigned long long* nrm, int* conv) {
-  for (int k = 0; k < 10; ++k) nrm[k] = 0ull;
+  for (int k = 0; k < 11; ++k) nrm[k] = 0ull;
   *conv = 0;
 }
 
@@ -878,7 +880,7 @@ kfbi_status mg_create(kfbi_problem* p) {
     else a += 6 * std::fabs(c[1]) + 12 * std::fabs(c[2]) + 8 * std::fabs(c[3]);
     M->anorm = a;
   }
-  KFBI_CUDA(p, dalloc(&M->nrm, 10));
+  KFBI_CUDA(p, dalloc(&M->nrm, 11));
   KFBI_CUDA(p, dalloc(&M->conv, 1));
   M->bufs.push_back(M->nrm);
   M->bufs.push_back(M->conv);
@@ -932,6 +934,24 @@ kfbi_status mg_solve(kfbi_problem* p, const double* rhs, double* u) {
   }
   KFBI_TRY(fix_out(p, M->fix, u, st));
   KFBI_CUDA(p, cudaGetLastError());
+  return KFBI_OK;
+}
+
+// Outer steps and V-cycles of the last multigrid box solve (mixed: the first
+// FP32 cycles plus every outer step that ran, inner_cycles V-cycles each;
+// FP64: the V-cycles that ran, one step).
+kfbi_status mg_steps(kfbi_problem* p, int* steps, int* cycles) {
+  MgSolver* M = p->mg;
+  unsigned long long c = 0;
+  KFBI_CUDA(p, cudaMemcpyAsync(&c, M->nrm + 10, sizeof(c), cudaMemcpyDeviceToHost, p->stream));
+  KFBI_CUDA(p, cudaStreamSynchronize(p->stream));
+  if (M->precision == KFBI_MIXED) {
+    *steps = 1 + (int)c;
+    *cycles = M->inner_cycles * *steps;
+  } else {
+    *steps = 1;
+    *cycles = (int)c;
+  }
   return KFBI_OK;
 }
 

@@ -108,6 +108,7 @@ SIGNATURES = {
     "kfbi_warm_start": [_P, _P, ctypes.POINTER(Data), _P],
     "kfbi_box_solve_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                ctypes.c_int, ctypes.c_double, _P, _P, _P],
+    "kfbi_box_solve_info": [_P, _P, _P, _P, _P],
     "kfbi_launch_counts": [_P, _P, ctypes.c_int],
     "kfbi_profile_enable": [_P, ctypes.c_int],
     "kfbi_profile_read": [_P, _P, _P],
@@ -357,6 +358,15 @@ def kfbi_warm_start_features(h, data, features, density=None, target=None):
 
 def kfbi_warm_start(h, m, data, x0):
     _check(load().kfbi_warm_start(h, m, ctypes.byref(data), _ptr(x0)), h)
+
+
+def kfbi_box_solve_info(h):
+    """(steps, cycles, rel_change, converged) of the last box solve on h."""
+    st, cy, cv = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    rel = ctypes.c_double()
+    _check(load().kfbi_box_solve_info(h, ctypes.byref(st), ctypes.byref(cy), ctypes.byref(rel),
+                                      ctypes.byref(cv)), h)
+    return st.value, cy.value, rel.value, cv.value
 
 
 def kfbi_box_solve_noalloc(dim, n, lo, hi, order, kappa, rhs, u, stream=None):
