@@ -47,6 +47,7 @@ from . import boxsolve as BS
 from . import collocation as CO
 from . import correction as CR
 from . import geometry as G
+from . import levelset as LS
 from . import traces as TR
 
 
@@ -66,9 +67,10 @@ class Problem:
         else:
             self.kt = w.kappa
         self.cos_alpha = w.cosa()
-        self.inside = G.classify(self.grid, w.ls_kind, w.ls_params)
-        G.check_separated(self.grid, w.ls_kind, w.ls_params, self.inside)
-        self.surf = G.surface_points(self.grid, w.ls_kind, w.ls_params,
+        lsp = LS.params(w)
+        self.inside = G.classify(self.grid, w.ls_kind, lsp)
+        G.check_separated(self.grid, w.ls_kind, lsp, self.inside)
+        self.surf = G.surface_points(self.grid, w.ls_kind, lsp,
                                      self.cos_alpha, self.inside)
         s = self.surf
         self.nb = s.nb

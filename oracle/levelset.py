@@ -10,8 +10,97 @@ import numpy as np
 import workloads as W
 
 
+class Sampled:
+    """A level-set function known by its values at the grid nodes (the
+    grid-sampled kind): samples of shape (N+1,)*d on [lo, lo + N h]^d.
+    Between nodes H is the tensor-product cubic Lagrange interpolant on the
+    4^d nodes around the point (O(h^4) away from the nodes, exact at them,
+    exact for every polynomial of degree <= 3 per axis)."""
+
+    def __init__(self, samples, lo: float, h: float):
+        self.samples = np.asarray(samples, dtype=np.float64)
+        self.d = self.samples.ndim
+        self.n = self.samples.shape[0] - 1
+        self.lo = float(lo)
+        self.h = float(h)
+
+
+def params(w):
+    """The level-set parameters of a workload as the functions below take them:
+    a Sampled object for the grid-sampled kind, the parameter list otherwise."""
+    if w.ls_kind == W.LS_GRID:
+        return Sampled(w.extra["samples"], w.lo, w.h)
+    return w.ls_params
+
+
+# Cubic Lagrange basis on the nodes t = -1, 0, 1, 2 of the cell [0, 1] and its
+# derivative (every product written out in the same order as on the GPU)
+def _lagrange(t):
+    tm1, tm2, tp1 = t - 1.0, t - 2.0, t + 1.0
+    w = [-(t * tm1 * tm2) / 6.0, (tp1 * tm1 * tm2) / 2.0, -(tp1 * t * tm2) / 2.0, (tp1 * t * tm1) / 6.0]
+    dw = [-(tm1 * tm2 + t * tm2 + t * tm1) / 6.0, (tm1 * tm2 + tp1 * tm2 + tp1 * tm1) / 2.0,
+          -(t * tm2 + tp1 * tm2 + tp1 * t) / 2.0, (t * tm1 + tp1 * tm1 + tp1 * t) / 6.0]
+    return w, dw
+
+
+def _cell(S: Sampled, xk):
+    """Per axis: the first of the four interpolation nodes i0 - 1 (i0 clamped
+    to [1, N - 2]) and the local coordinate t in the cell [i0, i0 + 1].  A
+    coordinate within 1e-10 (in units of h) of a node is taken as that node,
+    so H at a node is its sample exactly."""
+    u = (xk - S.lo) / S.h
+    k = np.rint(u)
+    u = np.where(np.abs(u - k) <= 1e-10, k, u)
+    i0 = np.clip(np.floor(u), 1, S.n - 2)
+    return i0.astype(np.int64) - 1, u - i0
+
+
+def _sampled(S: Sampled, X: np.ndarray, grad: bool):
+    X = np.asarray(X, dtype=np.float64)
+    shp = X.shape[:-1]
+    Xf = X.reshape(-1, S.d)
+    base, wts, dwts = [], [], []
+    for k in range(S.d):
+        b, t = _cell(S, Xf[:, k])
+        w, dw = _lagrange(t)
+        base.append(b)
+        wts.append(w)
+        dwts.append(dw)
+    val = np.zeros(Xf.shape[0])
+    g = np.zeros(Xf.shape)
+    if S.d == 2:
+        for a in range(4):
+            row = np.zeros(Xf.shape[0])
+            drow = np.zeros(Xf.shape[0])
+            for b in range(4):
+                v = S.samples[base[0] + a, base[1] + b]
+                row = row + wts[1][b] * v
+                drow = drow + dwts[1][b] * v
+            val = val + wts[0][a] * row
+            g[:, 0] = g[:, 0] + dwts[0][a] * row
+            g[:, 1] = g[:, 1] + wts[0][a] * drow
+    else:
+        for a in range(4):
+            for b in range(4):
+                row = np.zeros(Xf.shape[0])
+                drow = np.zeros(Xf.shape[0])
+                for c in range(4):
+                    v = S.samples[base[0] + a, base[1] + b, base[2] + c]
+                    row = row + wts[2][c] * v
+                    drow = drow + dwts[2][c] * v
+                wab = wts[0][a] * wts[1][b]
+                val = val + wab * row
+                g[:, 0] = g[:, 0] + (dwts[0][a] * wts[1][b]) * row
+                g[:, 1] = g[:, 1] + (wts[0][a] * dwts[1][b]) * row
+                g[:, 2] = g[:, 2] + wab * drow
+    g = g / S.h
+    return (g.reshape(shp + (S.d,)) if grad else val.reshape(shp))
+
+
 def H(kind: int, p, X: np.ndarray) -> np.ndarray:
     """Level-set value at points X (..., d)."""
+    if kind == W.LS_GRID:
+        return _sampled(p, X, False)
     if kind == W.LS_ELLIPSE:
         cx, cy, a, b, th = p[:5]
         x = X[..., 0] - cx
@@ -77,7 +166,10 @@ def _nearest_ball(p, d: int, X: np.ndarray):
 
 
 def grad_H(kind: int, p, X: np.ndarray) -> np.ndarray:
-    """Analytic gradient of H at points X (..., d)."""
+    """Analytic gradient of H at points X (..., d) (of the interpolant for
+    the grid-sampled kind)."""
+    if kind == W.LS_GRID:
+        return _sampled(p, X, True)
     if kind == W.LS_ELLIPSE:
         cx, cy, a, b, th = p[:5]
         x = X[..., 0] - cx
