@@ -78,3 +78,24 @@ def test_flux_data_match_finite_differences(make):
         ref = w.sigma_in * dn_i - w.sigma_out * dn_o
         assert np.abs(g1 - (ui(pts) - uo(pts))).max() < 1e-14
     assert np.abs(g2 - ref).max() < 1e-8
+
+
+def test_cubic_harmonics_are_harmonic_with_exact_gradients():
+    """The 16 degree <= 3 harmonics: Laplacian zero and gradient equal to
+    central differences (both to rounding), linearly independent."""
+    import numpy as np
+    import workloads as W
+    rng = np.random.default_rng(3)
+    X = rng.uniform(-1, 1, size=(50, 3))
+    H, G = W._cubic_harmonics(X)
+    e = 1e-4
+    lap = np.zeros_like(H)
+    for k in range(3):
+        d = np.zeros(3)
+        d[k] = e
+        Hp, _ = W._cubic_harmonics(X + d)
+        Hm, _ = W._cubic_harmonics(X - d)
+        assert np.abs((Hp - Hm) / (2 * e) - G[..., k]).max() < 1e-7
+        lap += (Hp - 2 * H + Hm) / (e * e)
+    assert np.abs(lap).max() < 1e-5
+    assert np.linalg.matrix_rank(H) == 16

@@ -28,6 +28,7 @@ LS_TORUS = 4        # 3D: p = [R, r] (axis z, centred at the origin)
 LS_MOLECULE = 5     # 3D: p = [r, level, n_atoms, x1, y1, z1, x2, ...]
 LS_DISCS = 6        # 2D: p = [r, n, x1, y1, ...], union of n separated discs
 LS_SPHERES = 7      # 3D: p = [r, n, x1, y1, z1, ...], union of n separated balls
+LS_GRID = 8         # H sampled at the grid nodes: p = [], samples in extra["samples"]
 
 # Problem kinds (shared with kfbi_problem_kind).
 KIND_DIRICHLET = 0  # interior Dirichlet BVP, eq. (bie-D)
@@ -163,6 +164,38 @@ def _sol_harmonic3(amps):
     return u, g, lap
 
 
+def _cubic_harmonics(X):
+    """The 16 harmonic polynomials of degree <= 3 in 3D and their gradients,
+    shapes (..., 16) and (..., 16, 3): 1; x, y, z; xy, yz, zx, x^2 - y^2,
+    2z^2 - x^2 - y^2; x^3 - 3xy^2, 3x^2 y - y^3, z(x^2 - y^2), xyz,
+    x(4z^2 - x^2 - y^2), y(4z^2 - x^2 - y^2), z(2z^2 - 3x^2 - 3y^2)."""
+    x, y, z = X[..., 0], X[..., 1], X[..., 2]
+    o, zr = np.ones_like(x), np.zeros_like(x)
+    h = [o, x, y, z, x * y, y * z, z * x, x * x - y * y, 2 * z * z - x * x - y * y,
+         x ** 3 - 3 * x * y * y, 3 * x * x * y - y ** 3, z * (x * x - y * y), x * y * z,
+         x * (4 * z * z - x * x - y * y), y * (4 * z * z - x * x - y * y),
+         z * (2 * z * z - 3 * x * x - 3 * y * y)]
+    gr = [(zr, zr, zr), (o, zr, zr), (zr, o, zr), (zr, zr, o),
+          (y, x, zr), (zr, z, y), (z, zr, x), (2 * x, -2 * y, zr), (-2 * x, -2 * y, 4 * z),
+          (3 * x * x - 3 * y * y, -6 * x * y, zr), (6 * x * y, 3 * x * x - 3 * y * y, zr),
+          (2 * x * z, -2 * y * z, x * x - y * y), (y * z, x * z, x * y),
+          (4 * z * z - 3 * x * x - y * y, -2 * x * y, 8 * x * z),
+          (-2 * x * y, 4 * z * z - x * x - 3 * y * y, 8 * y * z),
+          (-6 * x * z, -6 * y * z, 6 * z * z - 3 * x * x - 3 * y * y)]
+    H = np.stack(h, -1)
+    G = np.stack([np.stack(t, -1) for t in gr], -2)
+    return H, G
+
+
+def _sol_cubic(amps):
+    # u = sum_k a_k h_k over the 16 harmonics of degree <= 3
+    a = np.asarray(amps, dtype=np.float64)
+    u = lambda X: _cubic_harmonics(X)[0] @ a
+    g = lambda X: np.einsum("...kd,k->...d", _cubic_harmonics(X)[1], a)
+    lap = lambda X: np.zeros(X.shape[:-1])
+    return u, g, lap
+
+
 def solutions(w: Workload):
     """(u_in, grad_in, lap_in), (u_out, grad_out, lap_out) of a workload."""
     e = w.exact
@@ -183,6 +216,8 @@ def solutions(w: Workload):
         return _sol_sin_cos(), _sol_exp_sin()
     if e == "exp3_harmonic3":
         return _sol_exp3(), _sol_harmonic3(w.extra["amps"])
+    if e == "cubic_io":
+        return _sol_cubic(w.extra["amps_in"]), _sol_cubic(w.extra["amps_out"])
     raise ValueError(f"unknown exact solution {e!r}")
 
 
@@ -244,7 +279,7 @@ def grid_data(w: Workload):
 def _lap_of_f(w: Workload, X, inside: bool):
     """Closed-form Laplacian of the physical f on one side."""
     e = w.exact
-    if e in ("exp_sin", "harmonic3"):
+    if e in ("exp_sin", "harmonic3", "cubic_io"):
         return np.zeros(X.shape[:-1])
     if e == "paper_table1":
         # f = lap u = 2 ca e^x cos(arg); lap(e^x cos(arg)) = 2 e^x * (-ca sin(arg)) + 0
@@ -410,6 +445,37 @@ def molecule_dirichlet_3d(n: int = 64) -> Workload:
                     KIND_DIRICHLET, kappa=1.0, exact="exp3")
 
 
+def wobbly_samples(dim: int, n: int, lo: float, hi: float) -> np.ndarray:
+    """Node values of a smooth level-set function that no analytic kind
+    describes: 2D (x/0.62)^2 + (y/0.45)^2 + 0.25 sin(3x) sin(4y) - 1, 3D
+    (x/0.6)^2 + (y/0.5)^2 + (z/0.45)^2 + 0.2 sin(3x) sin(3y) cos(2z) - 1;
+    shape (N+1,)*d, axis d-1 fastest."""
+    h = (hi - lo) / n
+    x = lo + np.arange(n + 1) * h
+    X = np.stack(np.meshgrid(*([x] * dim), indexing="ij"), -1)
+    if dim == 2:
+        return ((X[..., 0] / 0.62) ** 2 + (X[..., 1] / 0.45) ** 2
+                + 0.25 * np.sin(3 * X[..., 0]) * np.sin(4 * X[..., 1]) - 1.0)
+    return ((X[..., 0] / 0.6) ** 2 + (X[..., 1] / 0.5) ** 2 + (X[..., 2] / 0.45) ** 2
+            + 0.2 * np.sin(3 * X[..., 0]) * np.sin(3 * X[..., 1]) * np.cos(2 * X[..., 2]) - 1.0)
+
+
+def sampled_interface_2d(n: int = 256, contrast: float = 10.0) -> Workload:
+    """2D Poisson interface problem whose interface is known only by grid
+    samples of a level-set function (wobbly_samples), sigma_in/sigma_out =
+    contrast, u_in = sin x cos y, u_out = x^2 + y^2."""
+    return Workload("sampled_interface_2d", 2, n, -1.0, 1.0, LS_GRID, [], KIND_INTERFACE_MU,
+                    sigma_in=contrast, sigma_out=1.0, exact="sincos_r2",
+                    extra={"samples": wobbly_samples(2, n, -1.0, 1.0)})
+
+
+def sampled_dirichlet_3d(n: int = 64) -> Workload:
+    """3D Dirichlet modified-Helmholtz BVP (kappa = 1) inside a surface known
+    only by grid samples (wobbly_samples), u = e^{x+y+z}/10."""
+    return Workload("sampled_dirichlet_3d", 3, n, -1.0, 1.0, LS_GRID, [], KIND_DIRICHLET,
+                    kappa=1.0, exact="exp3", extra={"samples": wobbly_samples(3, n, -1.0, 1.0)})
+
+
 def star_batch_2d(count: int = 64, seed: int = 5965, sizes=(128, 256, 512, 1024)):
     """Batched star-interface instances: R0~U[0.4,0.6], A~U[0,0.15], k~U{3..7},
     contrast = 10^U[0,3], N ~ U(sizes), drawn in that order per instance."""
@@ -455,6 +521,33 @@ def warm_start_training_set(seed: int, geometries: int, draws: int):
         axes = rng.uniform(0.3, 0.7, size=3)
         out.append((axes, [rng.standard_normal(8) for _ in range(draws)]))
     return out
+
+
+def cubic_field_amplitudes(seed: int = 5968):
+    """The fixed interior and exterior amplitudes of the learned-start family:
+    two draws of N(0,1)^16 from one seeded generator (interior first)."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(16), rng.standard_normal(16)
+
+
+def cubic_ellipsoid_3d(axes, n: int, contrast: float = 10.0) -> Workload:
+    """3D interface problem of the learned start: an ellipsoid with the given
+    axes in [-1, 1]^3, sigma_in/sigma_out = contrast, u_in and u_out fixed sums
+    of the 16 harmonics of degree <= 3 (cubic_field_amplitudes), outer Dirichlet
+    data from u_out.  The geometry varies from problem to problem, the fields
+    do not; the method is not exact for cubic fields, and with u_out != 0 the
+    density [d_n u] is not a multiple of the flux jump g2."""
+    a_in, a_out = cubic_field_amplitudes()
+    return Workload("cubic_ellipsoid_3d", 3, n, -1.0, 1.0, LS_ELLIPSOID,
+                    [0.0, 0.0, 0.0, *[float(a) for a in axes]], KIND_INTERFACE_MU,
+                    sigma_in=contrast, sigma_out=1.0, exact="cubic_io",
+                    extra={"amps_in": [float(v) for v in a_in], "amps_out": [float(v) for v in a_out]})
+
+
+def ellipsoid_axes(seed: int, count: int):
+    """`count` ellipsoid axis triples ~U[0.3, 0.7]^3 from one seeded generator."""
+    rng = np.random.default_rng(seed)
+    return [rng.uniform(0.3, 0.7, size=3) for _ in range(count)]
 
 
 def sine_grid_rhs(dim: int, n: int, seed: int) -> np.ndarray:
