@@ -58,7 +58,15 @@ typedef enum {
   KFBI_LS_DISCS = 6,      /* 2D p=[r,n,x1,y1,...]: min_k |x-x_k|^2 - r^2, n separated discs
                              (a compact stencil spanning two discs: refused at
                              create with KFBI_ERR_GEOMETRY)                       */
-  KFBI_LS_SPHERES = 7     /* 3D p=[r,n,x1,y1,z1,...]: the same with balls          */
+  KFBI_LS_SPHERES = 7,    /* 3D p=[r,n,x1,y1,z1,...]: the same with balls          */
+  KFBI_LS_GRID = 8        /* 2D or 3D: H known only by its values at the (N+1)^d
+                             nodes of the problem's grid (kfbi_levelset.samples, a
+                             sampled signed distance or any smooth level-set
+                             function); between nodes H is the tensor-product
+                             cubic Lagrange interpolant on the 4^d nodes around
+                             the point (its cell clamped to [1, N-2] per axis;
+                             a coordinate within 1e-10 h of a node is that
+                             node, so H at a node is its sample); p unused   */
 } kfbi_levelset_kind;
 
 typedef enum {
@@ -79,6 +87,9 @@ typedef struct {
   int kind;                      /* kfbi_levelset_kind */
   int n_params;
   double p[KFBI_LS_MAX_PARAMS];
+  const double* samples;         /* KFBI_LS_GRID: device array of the (N+1)^d node
+                                    values in grid order, copied at create (the
+                                    caller may free it afterwards); NULL otherwise */
 } kfbi_levelset;
 
 typedef struct {
@@ -265,17 +276,21 @@ kfbi_status kfbi_evaluate(kfbi_problem* p, const kfbi_data* data, const double* 
 /* ---- batched solves ------------------------------------------------------ */
 
 /* Many independent problems solved together (different grids, interfaces and
- * data), Algorithm 1 for each, with every GMRES iteration of all instances
- * run as one replay of a captured CUDA graph: the correction values, RHS
- * corrections, box solves and traces of all instances each run as one launch
- * over all instances' work items.  The batch keeps pointers to the problems,
- * which must outlive it and must not be used for other work while a batched
- * solve runs (their operator buffers and box-solver scratch are shared).
- * Requirements: at least one problem; all on one stream, of one dimension,
- * with box_solver KFBI_BOX_DST, precision KFBI_MIXED, the same Krylov
- * dimension, and N_b <= 32768 each; otherwise KFBI_ERR_UNSUPPORTED (message on
- * problems[0]).  problems: host array of count handles; *out receives the
- * batch (NULL on failure). */
+ * data), Algorithm 1 for each.  The right-hand sides of Step 1 and the final
+ * evaluations run as one batched box solve over all instances; the GMRES
+ * cycle of all instances is one launch of a captured CUDA graph: a
+ * conditional loop whose body is one iteration of every instance (correction
+ * values, RHS corrections, box solves and traces each one launch over all
+ * instances' work items, then the Arnoldi steps), ended on the device when
+ * every instance has converged or the iteration limit is reached.  The batch
+ * keeps pointers to the problems, which must outlive it and must not be used
+ * for other work while a batched call runs (their operator buffers and
+ * box-solver scratch are shared).
+ * Requirements: at least one problem; all of one kind (Dirichlet or mu-form
+ * interface), on one stream, of one dimension, with box_solver KFBI_BOX_DST,
+ * precision KFBI_MIXED, the same Krylov dimension, and N_b <= 32768 each;
+ * otherwise KFBI_ERR_UNSUPPORTED (message on problems[0]).  problems: host
+ * array of count handles; *out receives the batch (NULL on failure). */
 typedef struct kfbi_batch kfbi_batch;
 /* Creation also tunes the launch shapes of the batched box solve on the
  * batch's own grids (kfbi_batch_tiles) and synchronises the stream. */
@@ -288,18 +303,28 @@ kfbi_status kfbi_destroy_batch(kfbi_batch* batch);
  * synthetic right-hand side.  The shapes only distribute work items; results
  * do not depend on them.  Host integers out; KFBI_ERR_ARG on NULL. */
 kfbi_status kfbi_batch_tiles(const kfbi_batch* batch, int* pass_ctas, int* row_ctas);
-/* Algorithm 1 for every instance k from a zero start: data[k] (host array of
- * count kfbi_data with device pointers as in kfbi_gmres_solve), densities[k]
- * (host array of count device pointers, N_b of instance k each, written),
+/* Algorithm 1 for every instance k: data[k] (host array of count kfbi_data
+ * with device pointers as in kfbi_gmres_solve), x0s (host array of count
+ * device pointers, N_b of instance k each, or NULL entries / x0s NULL for a
+ * zero start: a start whose residual is not below ||b_k|| (or not finite)
+ * is dropped for the zero start, as in kfbi_gmres_solve, infos[k].x0_rejected),
+ * densities[k] (host array of count device pointers, N_b each, written),
  * infos (host array of count, may be NULL; t_ms zeroed).  opts applies to
  * every instance; opts->x0 must be NULL; there is no restart: an instance not
  * converged within min(max_iter, restart, Krylov dimension) iterations makes
- * the call return KFBI_ERR_NOT_CONVERGED after writing every density.
- * Synchronises the stream once per iteration (one copy of the residual
- * estimates of all instances). */
+ * the call return KFBI_ERR_NOT_CONVERGED after writing every density; NaN or
+ * Inf data: KFBI_ERR_NONFINITE.  Synchronises the stream three times per call
+ * (after the starts, after the GMRES cycle, at the end). */
 kfbi_status kfbi_gmres_solve_batch(kfbi_batch* batch, const kfbi_data* data,
-                                   const kfbi_gmres_opts* opts, double* const* densities,
-                                   kfbi_gmres_info* infos);
+                                   const kfbi_gmres_opts* opts, const double* const* x0s,
+                                   double* const* densities, kfbi_gmres_info* infos);
+/* kfbi_evaluate for every instance from its density, the box solves of all
+ * instances as one batched solve: u_grids[k] (host array of count device
+ * pointers, (N+1)^d of instance k each) receives instance k's grid solution;
+ * data and densities as in kfbi_gmres_solve_batch.  Enqueued on the batch's
+ * stream; no synchronisation. */
+kfbi_status kfbi_evaluate_batch(kfbi_batch* batch, const kfbi_data* data,
+                                const double* const* densities, double* const* u_grids);
 
 /* ---- learned initial density for GMRES ---------------------------------- */
 
@@ -308,8 +333,8 @@ kfbi_status kfbi_gmres_solve_batch(kfbi_batch* batch, const kfbi_data* data,
  * which falls back to a zero start whenever that guess is not better than zero:
  *   z1 = W1 x~ + b1, a1 = tanh z1;  z2 = W2 a1 + b2, a2 = tanh z2;
  *   y = W3 a2 + b3 + WL x~;  x~ = (x - in_shift) * in_scale;
- *   density = s (y * out_scale + out_shift),  s the data scale of the problem
- *   (kfbi_warm_start_features).
+ *   density = y * out_scale + out_shift  (x: the features of
+ *   kfbi_warm_start_features).
  * Parameters are one FP32 vector [W1 (width x n_in, row-major), b1, W2 (width x
  * width), b2, W3 (1 x width), b3, WL (n_in)] owned by the network; the
  * products with W1, W2, W3 use those weights rounded to bfloat16 (round to
@@ -347,12 +372,13 @@ kfbi_status kfbi_mlp_loss_grad(kfbi_mlp* m, const float* X, const float* t, cons
 kfbi_status kfbi_mlp_set_trainable(kfbi_mlp* m, int groups);
 /* One Adam step with the last gradient (step counter kept by the network). */
 kfbi_status kfbi_mlp_adam(kfbi_mlp* m, float lr, float beta1, float beta2, float eps);
-/* Per-DOF features (N_b x KFBI_WS_FEATURES floats): [g1/s, g2/s, n (3),
- * x (3), level-set parameters p0..p5, 0, 0] with the data scale
- * s = sqrt(mean over DOFs of g1^2 + g2^2) (1 if the data vanish; components
- * beyond the dimension are 0; g2 NULL gives 0).  With density (N_b doubles,
- * e.g. a solved density) also writes target (N_b floats) = density / s: one
- * training sample per DOF.  density and target are both NULL or both given. */
+/* Per-DOF features (N_b x KFBI_WS_FEATURES floats): [g1, g2, n (3), x (3),
+ * level-set parameters p0..p5, log10(sigma_in/sigma_out) (interface kinds;
+ * 0 otherwise), 0].  The data are not rescaled per problem (the network's
+ * input normalisation, set from its training set, does that per feature).
+ * Components beyond the dimension are 0; g2 NULL gives 0.  With density (N_b doubles,
+ * e.g. a solved density) also writes target (N_b floats) = the density (FP32):
+ * one training sample per DOF.  density and target are both NULL or both given. */
 kfbi_status kfbi_warm_start_features(kfbi_problem* p, const kfbi_data* data, const double* density,
                                      float* features, float* target);
 /* x0 (N_b doubles) = the network's density for this problem and data.  The

@@ -226,8 +226,13 @@ kfbi_status kfbi_create_problem(const kfbi_config* cfg, const kfbi_levelset* ls,
   }
   const bool ls2d = ls->kind == KFBI_LS_ELLIPSE || ls->kind == KFBI_LS_STAR || ls->kind == KFBI_LS_DISCS;
   const bool balls = ls->kind == KFBI_LS_DISCS || ls->kind == KFBI_LS_SPHERES;
-  if (ls->n_params < 0 || ls->n_params > KFBI_LS_MAX_PARAMS || ls->kind < 1 || ls->kind > 7 ||
-      ls2d != (cfg->dim == 2) ||
+  const bool sampled = ls->kind == KFBI_LS_GRID;
+  if (sampled && !ls->samples) {
+    fail(p, KFBI_ERR_ARG, "a grid-sampled level set needs its node values (samples)");
+    return bail(KFBI_ERR_ARG);
+  }
+  if (ls->n_params < 0 || ls->n_params > KFBI_LS_MAX_PARAMS || ls->kind < 1 || ls->kind > 8 ||
+      (!sampled && ls2d != (cfg->dim == 2)) ||
       (balls && (ls->n_params < 2 || !(ls->p[0] > 0) || ls->p[1] < 1 ||
                  2 + cfg->dim * (int)ls->p[1] > ls->n_params))) {
     fail(p, KFBI_ERR_ARG, "level-set kind does not match the dimension");
@@ -245,6 +250,21 @@ kfbi_status kfbi_create_problem(const kfbi_config* cfg, const kfbi_levelset* ls,
   p->ls.kind = ls->kind;
   p->ls.np = ls->n_params;
   memcpy(p->ls.p, ls->p, sizeof(p->ls.p));
+  p->ls.grid = nullptr;
+  if (sampled) {
+    // the problem keeps its own copy of the node values
+    const long long nodes = p->g.nodes();
+    if (dalloc(&p->ls_samples, nodes) != cudaSuccess ||
+        cudaMemcpy(p->ls_samples, ls->samples, sizeof(double) * nodes, cudaMemcpyDeviceToDevice) != cudaSuccess) {
+      fail(p, KFBI_ERR_CUDA, "cannot copy the level-set samples");
+      return bail(KFBI_ERR_CUDA);
+    }
+    p->ls.grid = p->ls_samples;
+    p->ls.gd = p->g.d;
+    p->ls.gn = p->g.n;
+    p->ls.glo = p->g.lo;
+    p->ls.gh = p->g.h;
+  }
   p->kt = cfg->kind == KFBI_INTERFACE_MU ? cfg->kappa : cfg->kappa / cfg->sigma_in;
   p->mu = cfg->kind == KFBI_INTERFACE_MU
               ? (cfg->sigma_out - cfg->sigma_in) / (cfg->sigma_out + cfg->sigma_in)
@@ -325,14 +345,14 @@ kfbi_status kfbi_destroy_problem(kfbi_problem* p) {
   if (p->op_exec) cudaGraphExecDestroy(p->op_exec);
   if (p->op_graph) cudaGraphDestroy(p->op_graph);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->ls_samples) cudaFree(p->ls_samples);
   if (p->xbuf) cudaFree(p->xbuf);
   if (p->ybuf) cudaFree(p->ybuf);
   if (p->gen) cudaFree(p->gen);
   void* bufs[] = {p->inside, p->irr_flag, p->family, p->edge, p->axis, p->st_axis, p->pde_node,
                   p->dir_idx, p->neu_idx, p->minv, p->irr_lin, p->irr_owner, p->irr_inside,
                   p->irr_w, p->corr_nb, p->nb_off, p->nb_coef, p->cvals, p->coef, p->rhs,
-                  p->ugrid, p->tvals, p->ftilde, p->bvec, p->zero_nb, p->d_flags, p->stencil_dev,
-                  p->ws_scale};
+                  p->ugrid, p->tvals, p->ftilde, p->bvec, p->zero_nb, p->d_flags, p->stencil_dev};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int k = 0; k < 3; ++k) {

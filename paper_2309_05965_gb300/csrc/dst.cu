@@ -1367,6 +1367,9 @@ void launch_pass(kfbi_problem* p, const PassArgs& A, int npairs_b, int na, cudaS
   const int L = 2 * A.n;
   int P = std::max(pmin, 1024 / L);
   if (sizeof(T) == 8 && L >= 2048) P = std::min(P, 1);
+  // small grids: fewer pairs per CTA until the pass has two CTAs per SM (a
+  // 64^2 grid otherwise runs on 4 CTAs, each bound by one SM's FP64 rate)
+  while (P > pmin && (long long)((npairs_b + P - 1) / P) * na < 2 * 152) P /= 2;
   if (P >= 8) launch_pass_p<T, 8>(p, A, npairs_b, na, st);
   else if (P >= 4) launch_pass_p<T, 4>(p, A, npairs_b, na, st);
   else if (P >= 2) launch_pass_p<T, 2>(p, A, npairs_b, na, st);
@@ -2093,6 +2096,11 @@ struct BatchBox {
   int* drstart = nullptr;      // [ninst + 1] grid rows
   int grid = 0, rgrid = 0;
 };
+
+void batch_box_copy_tiles(BatchBox* dst, const BatchBox* src) {
+  dst->grid = src->grid;
+  dst->rgrid = src->rgrid;
+}
 
 kfbi_status batch_box_create(kfbi_problem* p0, kfbi_problem* const* ps, int ninst,
                              double* const* rhs, BatchBox** out) {

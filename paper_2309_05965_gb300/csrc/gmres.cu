@@ -366,6 +366,151 @@ __global__ void k_cgs_normalize(double* __restrict__ V, int nb, const int* __res
 
 }  // namespace
 
+namespace {
+
+constexpr int kBatchThreads = 256;
+
+// fixed-order sum of one value per thread over a CTA of kBatchThreads
+__device__ double cta_sum(double v, double* ws) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int q = 0; q < kBatchThreads / 32; ++q) t += ws[q];
+  __syncthreads();
+  return t;
+}
+
+// Start of every instance's GMRES (a CTA per instance): ||b||; with a start x0
+// (y = A x0 already in the instance's operator output) r0 = b - y is taken
+// when ||r0|| < ||b|| (finite), else the zero start (the single solve's rule);
+// V_0 = r/||r||, g = (||r||, 0, ...), threshold rtol ||b||; an instance whose
+// start already meets it (or is not finite) is marked done.
+__global__ void __launch_bounds__(kBatchThreads) k_batch_init(const ArnDesc* __restrict__ D,
+                                                             const BatchInst* __restrict__ I, double rtol,
+                                                             double* __restrict__ thr, double* __restrict__ bn,
+                                                             int* __restrict__ done, int* __restrict__ jdev,
+                                                             int* __restrict__ flags, double* __restrict__ res_out) {
+  __shared__ double ws[kBatchThreads / 32];
+  __shared__ double sc[2];
+  const int k = blockIdx.x;
+  const ArnDesc& a = D[k];
+  const BatchInst& in = I[k];
+  const bool has_x0 = in.x0 != nullptr;
+  double sb = 0.0, sr = 0.0;
+  for (int e = threadIdx.x; e < a.nb; e += kBatchThreads) {
+    const double bv = in.b[e];
+    sb += bv * bv;
+    if (has_x0) {
+      const double r = bv - a.y[e];
+      sr += r * r;
+    }
+  }
+  const double bnorm = sqrt(cta_sum(sb, ws));
+  const double rnorm = has_x0 ? sqrt(cta_sum(sr, ws)) : 0.0;
+  const bool use = has_x0 && rnorm < bnorm;   // false for a NaN residual
+  const double beta = use ? rnorm : bnorm;
+  if (threadIdx.x == 0) {
+    sc[0] = beta > 0.0 ? 1.0 / beta : 0.0;
+    sc[1] = beta;
+  }
+  __syncthreads();
+  const double f = sc[0];
+  for (int e = threadIdx.x; e < a.nb; e += kBatchThreads)
+    a.V[e] = (use ? in.b[e] - a.y[e] : in.b[e]) * f;
+  for (int i = threadIdx.x; i <= a.m; i += kBatchThreads) a.g[i] = i == 0 ? beta : 0.0;
+  if (threadIdx.x == 0) {
+    const double t = rtol * bnorm;
+    thr[k] = t;
+    bn[k] = bnorm;
+    flags[k] = has_x0 ? (use ? 1 : 2) : 0;
+    done[k] = (beta > t) ? 0 : 1;
+    jdev[k] = 0;
+    a.res[0] = beta;
+    res_out[k] = beta;
+  }
+}
+
+// After each batched iteration: instances whose residual estimate reached
+// their threshold (or is not finite) are marked done; ctl[0] counts the
+// iterations, ctl[2] the instances still active; with use_cond the loop
+// continues while some instance is active and ctl[0] < ctl[1].
+__global__ void __launch_bounds__(kBatchThreads) k_batch_control(const double* __restrict__ res,
+                                                                const double* __restrict__ thr,
+                                                                int* __restrict__ done, int n,
+                                                                int* __restrict__ ctl,
+                                                                cudaGraphConditionalHandle cond, int use_cond) {
+  __shared__ int wa[kBatchThreads / 32];
+  int active = 0;
+  for (int k = threadIdx.x; k < n; k += kBatchThreads) {
+    if (done[k]) continue;
+    if (res[k] > thr[k]) ++active;
+    else done[k] = 1;
+  }
+  for (int o = 16; o > 0; o >>= 1) active += __shfl_xor_sync(0xffffffffu, active, o);
+  if ((threadIdx.x & 31) == 0) wa[threadIdx.x >> 5] = active;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  int tot = 0;
+  for (int q = 0; q < kBatchThreads / 32; ++q) tot += wa[q];
+  ctl[0] += 1;
+  ctl[2] = tot;
+  if (use_cond) cudaGraphSetConditional(cond, (tot > 0 && ctl[0] < ctl[1]) ? 1u : 0u);
+}
+
+// x = (x0 if taken) + sum_{i < k} y_i V_i with H y = g (k x k upper
+// triangular, k = the instance's iterations), a CTA per instance
+__global__ void __launch_bounds__(kBatchThreads) k_batch_finish(const ArnDesc* __restrict__ D,
+                                                               const BatchInst* __restrict__ I,
+                                                               const int* __restrict__ jdev,
+                                                               const int* __restrict__ flags) {
+  __shared__ double y[kMaxKrylov];
+  const int k = blockIdx.x;
+  const ArnDesc& a = D[k];
+  const BatchInst& in = I[k];
+  const int kk = min(jdev[k], a.m);
+  if (threadIdx.x == 0) {
+    for (int i = kk - 1; i >= 0; --i) {
+      double s = a.g[i];
+      for (int j = i + 1; j < kk; ++j) s -= a.H[(size_t)j * a.ld + i] * y[j];
+      y[i] = s / a.H[(size_t)i * a.ld + i];
+    }
+  }
+  __syncthreads();
+  const bool base = flags[k] == 1;
+  for (int e = threadIdx.x; e < a.nb; e += kBatchThreads) {
+    double s = base ? in.x0[e] : 0.0;
+    for (int i = 0; i < kk; ++i) s += y[i] * a.V[(size_t)i * a.nb + e];
+    in.out[e] = s;
+  }
+}
+
+}  // namespace
+
+kfbi_status batch_gmres_init(kfbi_problem* p0, const ArnDesc* d, const BatchInst* inst, int n, double rtol,
+                             double* thr, double* bn, int* done, int* jdev, int* flags, double* res_out,
+                             cudaStream_t st) {
+  KFBI_LAUNCH(p0, KFBI_KC_GMRES, k_batch_init<<<n, kBatchThreads, 0, st>>>(d, inst, rtol, thr, bn, done, jdev,
+                                                                            flags, res_out));
+  KFBI_CUDA(p0, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status batch_gmres_control(kfbi_problem* p0, const double* res, const double* thr, int* done, int n, int* ctl,
+                                cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st) {
+  KFBI_LAUNCH(p0, KFBI_KC_GMRES, k_batch_control<<<1, kBatchThreads, 0, st>>>(res, thr, done, n, ctl, cond,
+                                                                               use_cond));
+  KFBI_CUDA(p0, cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status batch_gmres_finish(kfbi_problem* p0, const ArnDesc* d, const BatchInst* inst, int n, const int* jdev,
+                               const int* flags, cudaStream_t st) {
+  KFBI_LAUNCH(p0, KFBI_KC_GMRES, k_batch_finish<<<n, kBatchThreads, 0, st>>>(d, inst, jdev, flags));
+  KFBI_CUDA(p0, cudaGetLastError());
+  return KFBI_OK;
+}
+
 kfbi_status batch_arnoldi_copy_in(kfbi_problem* p0, const ArnDesc* d, const int* jdev, const int* done,
                                   int ninst, int maxnb, cudaStream_t st) {
   KFBI_LAUNCH(p0, KFBI_KC_GMRES, k_copy_in_batched<<<dim3(div_up(maxnb, 256), ninst), 256, 0, st>>>(d, jdev, done));

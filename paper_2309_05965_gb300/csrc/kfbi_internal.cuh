@@ -57,6 +57,11 @@ struct LevelSet {
   int kind;
   int np;
   double p[KFBI_LS_MAX_PARAMS];
+  // KFBI_LS_GRID: the node values (device copy owned by the problem) and
+  // their grid
+  const double* grid;
+  int gd, gn;
+  double glo, gh;
 };
 
 // Trace stencil CSR for one side.
@@ -118,6 +123,7 @@ struct kfbi_problem {
   kfbi_config cfg;
   kfbi::Grid g;
   kfbi::LevelSet ls;
+  double* ls_samples = nullptr;   // device copy of a grid-sampled level set
   cudaStream_t stream = nullptr;
   std::string err;
   double kt = 0.0;           // kappa~ of the box operator
@@ -182,7 +188,6 @@ struct kfbi_problem {
   double* xbuf = nullptr;
   double* ybuf = nullptr;
   bool use_graphs = true;
-  double* ws_scale = nullptr;    // [1] data scale of the learned start (allocated on first use)
   int nx = 0;                    // unknowns of the BIE: N_b, or 2 N_b for the general interface kind
   kfbi_problem* twin = nullptr;  // general interface kind: the kappa_2/sigma_2 operator (owned)
   kfbi_problem* parent = nullptr;  // set on a twin: its launches are counted and timed there
@@ -336,6 +341,13 @@ struct ArnDesc {
   double* x;   // operator input buffer
   double* y;   // operator output buffer
 };
+// Per-call pointers of one batched instance: its BIE right-hand side, its
+// start (NULL = zero) and where its density goes.
+struct BatchInst {
+  const double* b;
+  const double* x0;
+  double* out;
+};
 struct BatchBox;
 struct BatchHot;
 // dst.cu
@@ -357,5 +369,13 @@ kfbi_status batch_arnoldi_copy_in(kfbi_problem* p0, const ArnDesc* d, const int*
                                   int ninst, int maxnb, cudaStream_t st);
 kfbi_status batch_arnoldi_step(kfbi_problem* p0, const ArnDesc* d, int* jdev, const int* done,
                                double* res_out, int ninst, int maxnb, int m, cudaStream_t st);
+kfbi_status batch_gmres_init(kfbi_problem* p0, const ArnDesc* d, const BatchInst* inst, int n, double rtol,
+                             double* thr, double* bn, int* done, int* jdev, int* flags, double* res_out,
+                             cudaStream_t st);
+kfbi_status batch_gmres_control(kfbi_problem* p0, const double* res, const double* thr, int* done, int n, int* ctl,
+                                cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
+kfbi_status batch_gmres_finish(kfbi_problem* p0, const ArnDesc* d, const BatchInst* inst, int n, const int* jdev,
+                               const int* flags, cudaStream_t st);
+void batch_box_copy_tiles(BatchBox* dst, const BatchBox* src);
 
 }  // namespace kfbi

@@ -33,9 +33,84 @@ __device__ inline int ls_nearest_ball(const double* p, int d, const double* X, d
   return best;
 }
 
+// Grid-sampled H: per axis the first of the four interpolation nodes and the
+// local coordinate t in the cell [i0, i0 + 1] (i0 clamped to [1, N - 2]); a
+// coordinate within 1e-10 h of a node is taken as that node.
+__device__ inline void ls_cell(const LevelSet& L, double x, int* base, double* t) {
+  double u = (x - L.glo) / L.gh;
+  const double k = rint(u);
+  if (fabs(u - k) <= 1e-10) u = k;
+  const double i0 = fmin(fmax(floor(u), 1.0), (double)(L.gn - 2));
+  *base = (int)i0 - 1;
+  *t = u - i0;
+}
+
+// cubic Lagrange basis on t = -1, 0, 1, 2 and its derivative
+__device__ inline void ls_lagrange(double t, double* w, double* dw) {
+  const double tm1 = t - 1.0, tm2 = t - 2.0, tp1 = t + 1.0;
+  w[0] = -(t * tm1 * tm2) / 6.0;
+  w[1] = (tp1 * tm1 * tm2) / 2.0;
+  w[2] = -(tp1 * t * tm2) / 2.0;
+  w[3] = (tp1 * t * tm1) / 6.0;
+  dw[0] = -(tm1 * tm2 + t * tm2 + t * tm1) / 6.0;
+  dw[1] = (tm1 * tm2 + tp1 * tm2 + tp1 * tm1) / 2.0;
+  dw[2] = -(t * tm2 + tp1 * tm2 + tp1 * t) / 2.0;
+  dw[3] = (t * tm1 + tp1 * tm1 + tp1 * t) / 6.0;
+}
+
+// the interpolant's value (and gradient if g) at X, sums in a fixed order
+__device__ inline double ls_sampled(const LevelSet& L, const double* X, double* g) {
+  const int d = L.gd, n1 = L.gn + 1;
+  int base[3] = {0, 0, 0};
+  double w[3][4], dw[3][4];
+  for (int k = 0; k < d; ++k) {
+    double t;
+    ls_cell(L, X[k], &base[k], &t);
+    ls_lagrange(t, w[k], dw[k]);
+  }
+  const double* S = L.grid;
+  double val = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+  if (d == 2) {
+    for (int a = 0; a < 4; ++a) {
+      double row = 0.0, drow = 0.0;
+      const double* r = S + (long long)(base[0] + a) * n1 + base[1];
+      for (int b = 0; b < 4; ++b) {
+        row = row + w[1][b] * r[b];
+        drow = drow + dw[1][b] * r[b];
+      }
+      val = val + w[0][a] * row;
+      g0 = g0 + dw[0][a] * row;
+      g1 = g1 + w[0][a] * drow;
+    }
+  } else {
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) {
+        double row = 0.0, drow = 0.0;
+        const double* r = S + ((long long)(base[0] + a) * n1 + (base[1] + b)) * n1 + base[2];
+        for (int c = 0; c < 4; ++c) {
+          row = row + w[2][c] * r[c];
+          drow = drow + dw[2][c] * r[c];
+        }
+        const double wab = w[0][a] * w[1][b];
+        val = val + wab * row;
+        g0 = g0 + (dw[0][a] * w[1][b]) * row;
+        g1 = g1 + (w[0][a] * dw[1][b]) * row;
+        g2 = g2 + wab * drow;
+      }
+  }
+  if (g) {
+    g[0] = g0 / L.gh;
+    g[1] = g1 / L.gh;
+    g[2] = d == 3 ? g2 / L.gh : 0.0;
+  }
+  return val;
+}
+
 __device__ inline double ls_H(const LevelSet& L, const double* X) {
   const double* p = L.p;
   switch (L.kind) {
+    case KFBI_LS_GRID:
+      return ls_sampled(L, X, nullptr);
     case KFBI_LS_DISCS:
     case KFBI_LS_SPHERES: {
       double v;
@@ -83,6 +158,9 @@ __device__ inline double ls_H(const LevelSet& L, const double* X) {
 __device__ inline void ls_grad(const LevelSet& L, const double* X, double* g) {
   const double* p = L.p;
   switch (L.kind) {
+    case KFBI_LS_GRID:
+      ls_sampled(L, X, g);
+      return;
     case KFBI_LS_DISCS:
     case KFBI_LS_SPHERES: {
       const int d = L.kind == KFBI_LS_DISCS ? 2 : 3;

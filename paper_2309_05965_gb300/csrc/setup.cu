@@ -165,21 +165,31 @@ __device__ bool crossing_point(const Grid& g, const LevelSet& L, const LineDesc&
   return fabs(nv[D.r]) > cos_alpha;
 }
 
-__global__ void k_line_count(Grid g, LevelSet L, LineDesc D, const uint8_t* __restrict__ inside,
-                             double cos_alpha, int nlines, int32_t* __restrict__ count) {
-  int li = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per grid line: the lanes test 32 consecutive edges at a time for a
+// change of node class and compute the crossing of each edge that has one
+// (the per-crossing arithmetic is the same as a thread walking the line).
+constexpr int kLineWarps = 4;
+__global__ void __launch_bounds__(32 * kLineWarps) k_line_count(Grid g, LevelSet L, LineDesc D,
+                                                                const uint8_t* __restrict__ inside,
+                                                                double cos_alpha, int nlines,
+                                                                int32_t* __restrict__ count) {
+  const int li = blockIdx.x * kLineWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (li >= nlines) return;
   int ia, ib;
   line_other(g, D, li, &ia, &ib);
-  long long base = ia * D.sa + (g.d == 3 ? ib * D.sb : 0);
+  const long long base = ia * D.sa + (g.d == 3 ? ib * D.sb : 0);
   int c = 0;
-  for (int j = 0; j < g.n; ++j) {
-    if (inside[base + j * D.sr] != inside[base + (j + 1) * D.sr]) {
+  for (int j0 = 0; j0 < g.n; j0 += 32) {
+    const int j = j0 + lane;
+    bool hit = false;
+    if (j < g.n && inside[base + j * D.sr] != inside[base + (j + 1) * D.sr]) {
       double X[3], nv[3];
-      if (crossing_point(g, L, D, ia, ib, j, cos_alpha, X, nv)) ++c;
+      hit = crossing_point(g, L, D, ia, ib, j, cos_alpha, X, nv);
     }
+    c += __popc(__ballot_sync(0xffffffffu, hit));
   }
-  count[li] = c;
+  if (lane == 0) count[li] = c;
 }
 
 // Unions of balls can bring two interfaces closer than the grid step: a node
@@ -229,41 +239,49 @@ __global__ void k_close_interfaces(Grid g, LevelSet L, const uint8_t* __restrict
   }
 }
 
-__global__ void k_line_fill(Grid g, LevelSet L, LineDesc D, const uint8_t* __restrict__ inside,
-                            double cos_alpha, int nlines, const int32_t* __restrict__ start,
-                            double* x0, double* x1, double* x2, double* n0, double* n1,
-                            double* n2, int32_t* family, int32_t* edge, int32_t* axis) {
-  int li = blockIdx.x * blockDim.x + threadIdx.x;
+// The DOFs of one grid line in edge order, a warp per line as in
+// k_line_count: each lane's crossing goes to the line's next free slot after
+// those of the lower lanes (ballot prefix).
+__global__ void __launch_bounds__(32 * kLineWarps) k_line_fill(
+    Grid g, LevelSet L, LineDesc D, const uint8_t* __restrict__ inside, double cos_alpha, int nlines,
+    const int32_t* __restrict__ start, double* x0, double* x1, double* x2, double* n0, double* n1,
+    double* n2, int32_t* family, int32_t* edge, int32_t* axis) {
+  const int li = blockIdx.x * kLineWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (li >= nlines) return;
   int ia, ib;
   line_other(g, D, li, &ia, &ib);
-  long long base = ia * D.sa + (g.d == 3 ? ib * D.sb : 0);
-  int pos = start[li];
-  for (int j = 0; j < g.n; ++j) {
-    if (inside[base + j * D.sr] != inside[base + (j + 1) * D.sr]) {
-      double X[3], nv[3];
-      if (crossing_point(g, L, D, ia, ib, j, cos_alpha, X, nv)) {
-        x0[pos] = X[0];
-        x1[pos] = X[1];
-        n0[pos] = nv[0];
-        n1[pos] = nv[1];
-        if (g.d == 3) {
-          x2[pos] = X[2];
-          n2[pos] = nv[2];
-        }
-        family[pos] = D.r;
-        edge[pos] = j;
-        int m = 0;
-        double best = fabs(nv[0]);
-        for (int k = 1; k < g.d; ++k)
-          if (fabs(nv[k]) > best) {
-            best = fabs(nv[k]);
-            m = k;
-          }
-        axis[pos] = m;
-        ++pos;
+  const long long base = ia * D.sa + (g.d == 3 ? ib * D.sb : 0);
+  int pos0 = start[li];
+  for (int j0 = 0; j0 < g.n; j0 += 32) {
+    const int j = j0 + lane;
+    bool hit = false;
+    double X[3], nv[3];
+    if (j < g.n && inside[base + j * D.sr] != inside[base + (j + 1) * D.sr])
+      hit = crossing_point(g, L, D, ia, ib, j, cos_alpha, X, nv);
+    const unsigned mask = __ballot_sync(0xffffffffu, hit);
+    if (hit) {
+      const int pos = pos0 + __popc(mask & ((1u << lane) - 1u));
+      x0[pos] = X[0];
+      x1[pos] = X[1];
+      n0[pos] = nv[0];
+      n1[pos] = nv[1];
+      if (g.d == 3) {
+        x2[pos] = X[2];
+        n2[pos] = nv[2];
       }
+      family[pos] = D.r;
+      edge[pos] = j;
+      int m = 0;
+      double best = fabs(nv[0]);
+      for (int k = 1; k < g.d; ++k)
+        if (fabs(nv[k]) > best) {
+          best = fabs(nv[k]);
+          m = k;
+        }
+      axis[pos] = m;
     }
+    pos0 += __popc(mask);
   }
 }
 
@@ -1084,7 +1102,7 @@ kfbi_status build_geometry(kfbi_problem* p) {
     D[r].sr = strides[r];
     D[r].sa = strides[o[0]];
     D[r].sb = d == 3 ? strides[o[1]] : 0;
-    k_line_count<<<div_up(nlines, 128), 128, 0, st>>>(g, L, D[r], p->inside, p->cos_alpha,
+    k_line_count<<<div_up(nlines, kLineWarps), 32 * kLineWarps, 0, st>>>(g, L, D[r], p->inside, p->cos_alpha,
                                                       nlines, cnt + (size_t)r * nlines);
     KFBI_CUDA(p, cudaGetLastError());
   }
@@ -1120,7 +1138,7 @@ kfbi_status build_geometry(kfbi_problem* p) {
   KFBI_CUDA(p, dalloc(&p->axis, nb));
   KFBI_CUDA(p, dalloc(&p->st_axis, nb));
   for (int r = 0; r < d; ++r) {
-    k_line_fill<<<div_up(nlines, 128), 128, 0, st>>>(
+    k_line_fill<<<div_up(nlines, kLineWarps), 32 * kLineWarps, 0, st>>>(
         g, L, D[r], p->inside, p->cos_alpha, nlines, p->line_start[r], p->x[0], p->x[1],
         d == 3 ? p->x[2] : p->x[0], p->nrm[0], p->nrm[1], d == 3 ? p->nrm[2] : p->nrm[0],
         p->family, p->edge, p->axis);

@@ -37,7 +37,7 @@ class KfbiError(RuntimeError):
 
 class LevelSet(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("n_params", ctypes.c_int),
-                ("p", ctypes.c_double * LS_MAX_PARAMS)]
+                ("p", ctypes.c_double * LS_MAX_PARAMS), ("samples", ctypes.c_void_p)]
 
 
 class Config(ctypes.Structure):
@@ -93,7 +93,8 @@ SIGNATURES = {
     "kfbi_create_batch": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)],
     "kfbi_destroy_batch": [_P],
     "kfbi_batch_tiles": [_P, _I, _I],
-    "kfbi_gmres_solve_batch": [_P, _P, ctypes.POINTER(GmresOpts), _P, _P],
+    "kfbi_gmres_solve_batch": [_P, _P, ctypes.POINTER(GmresOpts), _P, _P, _P],
+    "kfbi_evaluate_batch": [_P, _P, _P, _P],
     "kfbi_mlp_create": [ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_void_p)],
     "kfbi_mlp_destroy": [_P],
     "kfbi_mlp_num_params": [_P, _I],
@@ -276,16 +277,31 @@ def kfbi_batch_tiles(b):
     return pc.value, rc.value
 
 
-def kfbi_gmres_solve_batch(b, handles, datas, opts: GmresOpts, densities):
-    """Algorithm 1 for every instance; returns one GmresInfo per instance."""
+def kfbi_gmres_solve_batch(b, handles, datas, opts: GmresOpts, densities, x0s=None):
+    """Algorithm 1 for every instance (x0s: None, or one tensor or None per
+    instance); returns one GmresInfo per instance."""
     n = len(handles)
     darr = (Data * n)(*datas)
     parr = (ctypes.c_void_p * n)(*[_ptr(x).value for x in densities])
+    xarr = None
+    if x0s is not None:
+        xarr = (ctypes.c_void_p * n)(*[(_ptr(x).value if x is not None else None) for x in x0s])
     infos = (GmresInfo * n)()
     _check(load().kfbi_gmres_solve_batch(b, ctypes.cast(darr, ctypes.c_void_p), ctypes.byref(opts),
+                                         ctypes.cast(xarr, ctypes.c_void_p) if xarr is not None else None,
                                          ctypes.cast(parr, ctypes.c_void_p),
                                          ctypes.cast(infos, ctypes.c_void_p)), handles[0])
     return list(infos)
+
+
+def kfbi_evaluate_batch(b, handles, datas, densities, u_grids):
+    """Grid solution of every instance from its density (one batched box solve)."""
+    n = len(handles)
+    darr = (Data * n)(*datas)
+    parr = (ctypes.c_void_p * n)(*[_ptr(x).value for x in densities])
+    uarr = (ctypes.c_void_p * n)(*[_ptr(x).value for x in u_grids])
+    _check(load().kfbi_evaluate_batch(b, ctypes.cast(darr, ctypes.c_void_p), ctypes.cast(parr, ctypes.c_void_p),
+                                      ctypes.cast(uarr, ctypes.c_void_p)), handles[0])
 
 
 WS_FEATURES = 16   # KFBI_WS_FEATURES
@@ -400,7 +416,7 @@ class Problem:
 
     def __init__(self, dim, n, lo, hi, ls_kind, ls_params, kind, sigma_in=1.0, sigma_out=1.0,
                  kappa=0.0, order=4, box_solver=BOX_DST, precision=FP64, cos_alpha=0.0,
-                 box_rtol=0.0, box_max_iters=0, stream=None, kappa_out=0.0):
+                 box_rtol=0.0, box_max_iters=0, stream=None, kappa_out=0.0, ls_samples=None):
         cfg = Config(dim=dim, n=n, lo=lo, hi=hi, order=order, kind=kind, sigma_in=sigma_in,
                      sigma_out=sigma_out, kappa=kappa, box_solver=box_solver,
                      precision=precision, cos_alpha=cos_alpha, box_rtol=box_rtol,
@@ -408,9 +424,18 @@ class Problem:
         ls = LevelSet(kind=ls_kind, n_params=len(ls_params))
         for i, v in enumerate(ls_params):
             ls.p[i] = float(v)
+        keep = None
+        if ls_samples is not None:
+            # node values of a grid-sampled level set: a device copy for the
+            # call (the library copies them at create)
+            import numpy as np
+            import torch
+            keep = torch.as_tensor(np.ascontiguousarray(ls_samples, dtype=np.float64)).cuda()
+            ls.samples = keep.data_ptr()
         self.cfg = cfg
         self.dim, self.n = dim, n
         self.handle = kfbi_create_problem(cfg, ls, stream)
+        del keep
         self.nb, self.nirr, self.ncoef = kfbi_sizes(self.handle)
         self.npde, self.ndir, self.nneu = kfbi_stencil_sizes(self.handle)
 
@@ -419,7 +444,8 @@ class Problem:
         return cls(w.dim, w.n, w.lo, w.hi, w.ls_kind, w.ls_params, w.kind,
                    sigma_in=w.sigma_in, sigma_out=w.sigma_out, kappa=w.kappa, order=w.order,
                    box_solver=box_solver, precision=precision,
-                   cos_alpha=w.cos_alpha or 0.0, kappa_out=w.kappa_out, **kw)
+                   cos_alpha=w.cos_alpha or 0.0, kappa_out=w.kappa_out,
+                   ls_samples=w.extra.get("samples"), **kw)
 
     def close(self):
         if self.handle is not None:
@@ -444,9 +470,12 @@ class Batch:
         self.problems = list(problems)
         self.handle = kfbi_create_batch([q.handle for q in self.problems])
 
-    def gmres_solve(self, datas, opts: GmresOpts, densities):
+    def gmres_solve(self, datas, opts: GmresOpts, densities, x0s=None):
         return kfbi_gmres_solve_batch(self.handle, [q.handle for q in self.problems], datas, opts,
-                                      densities)
+                                      densities, x0s)
+
+    def evaluate(self, datas, densities, u_grids):
+        kfbi_evaluate_batch(self.handle, [q.handle for q in self.problems], datas, densities, u_grids)
 
     def tiles(self):
         return kfbi_batch_tiles(self.handle)

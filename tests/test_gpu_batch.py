@@ -179,3 +179,69 @@ def test_batch_tiles():
     x1 = empty(rows[0]["G"].nb)
     kfbi.kfbi_gmres_solve(rows[0]["G"].handle, rows[0]["d"], opts, x1)
     assert np.array_equal(host(x0), host(x1))
+
+
+def test_batch_starts_match_single_solves():
+    """Per-instance starts: a start taken by the single solve is taken by the
+    batch too (same iteration count within 1, density within 1e-9); a start
+    worse than zero (and a NaN start) is dropped for the zero start, as in
+    the single solve; instances without a start run from zero beside them."""
+    import torch
+    from paper_2309_05965_gb300 import kfbi
+    rows = _setup()[:4]
+    opts = kfbi.GmresOpts(rtol=1e-10, restart=100, max_iter=100, x0=None)
+    zero, zero_iters = [], []
+    for r in rows:
+        x = empty(r["G"].nb)
+        zero_iters.append(kfbi.kfbi_gmres_solve(r["G"].handle, r["d"], opts, x).iters)
+        zero.append(x)
+    g = torch.Generator(device="cuda").manual_seed(3)
+    # a good start (the solution scaled by 1 + 1e-5: residual 1e-5 b), a bad
+    # one, none, a NaN one
+    starts = [zero[0] * (1 + 1e-5),
+              50.0 * torch.randn(zero[1].shape, device="cuda", dtype=torch.float64, generator=g),
+              None,
+              zero[3].clone()]
+    starts[3][0] = float("nan")
+    singles = []
+    for r, x0 in zip(rows, starts):
+        x = empty(r["G"].nb)
+        o = kfbi.GmresOpts(rtol=1e-10, restart=100, max_iter=100, x0=None if x0 is None else x0.data_ptr())
+        info = kfbi.kfbi_gmres_solve(r["G"].handle, r["d"], o, x)
+        singles.append((host(x), info))
+    B = kfbi.Batch([r["G"] for r in rows])
+    dens = [empty(r["G"].nb) for r in rows]
+    infos = B.gmres_solve([r["d"] for r in rows], opts, dens, x0s=starts)
+    assert [i.x0_rejected for i in infos] == [0, 1, 0, 1]
+    assert [i.x0_rejected for _, i in singles] == [0, 1, 0, 1]
+    for k, (x, info, (xs, si)) in enumerate(zip(dens, infos, singles)):
+        assert abs(info.iters - si.iters) <= 1, (k, info.iters, si.iters)
+        assert info.rel_res <= 1e-10
+        assert rel_err(host(x), xs) < 1e-9, k
+    # the good start saves iterations against the zero start
+    assert infos[0].iters < zero_iters[0]
+    B.close()
+
+
+def test_batch_evaluate_matches_single_evaluate():
+    """kfbi_evaluate_batch (one batched box solve) against kfbi_evaluate of
+    each instance from the same density: within the mixed box solve's
+    agreement (1e-9 relative), boundary layer included."""
+    from paper_2309_05965_gb300 import kfbi
+    rows = _setup()
+    opts = kfbi.GmresOpts(rtol=1e-10, restart=100, max_iter=100, x0=None)
+    B = kfbi.Batch([r["G"] for r in rows])
+    dens = [empty(r["G"].nb) for r in rows]
+    B.gmres_solve([r["d"] for r in rows], opts, dens)
+    ub = [empty(r["G"].grid_shape) for r in rows]
+    B.evaluate([r["d"] for r in rows], dens, ub)
+    for r, x, u in zip(rows, dens, ub):
+        us = empty(r["G"].grid_shape)
+        kfbi.kfbi_evaluate(r["G"].handle, r["d"], x, us)
+        assert rel_err(host(u), host(us)) < 1e-9, r["w"].name
+        ex = W.exact_grid(r["w"], r["P"].inside)
+        w = r["w"]
+        inner = np.zeros(r["P"].inside.shape, bool)
+        inner[tuple(slice(1, w.n) for _ in range(w.dim))] = True
+        assert np.abs(host(u) - ex)[inner].max() < 1e-3
+    B.close()

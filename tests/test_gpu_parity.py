@@ -29,6 +29,9 @@ CASES = {
     "torus64": lambda: W.torus_helmholtz_3d(64),
     # the Gaussian-sum (molecule) level set, three atoms
     "molecule64": lambda: W.molecule_dirichlet_3d(64),
+    # interfaces known only by level-set samples at the grid nodes
+    "sampled256": lambda: W.sampled_interface_2d(256),
+    "sampled3d64": lambda: W.sampled_dirichlet_3d(64),
 }
 
 
@@ -297,3 +300,38 @@ def test_full_solve_multigrid_mixed(name):
     e_gpu = np.abs(host(u) - ex)[m & inner].max()
     e_ref = np.abs(u_ref - ex)[m & inner].max()
     assert e_gpu <= 1.1 * e_ref + 1e-12
+
+
+def test_sampled_quadric_equals_analytic_kind():
+    """Node samples of the ellipse level set (quadratic: the interpolant is
+    exact) give on the GPU the analytic kind's DOFs, classes and irregular
+    nodes, and the same operator."""
+    import torch
+    from paper_2309_05965_gb300 import build, kfbi
+    from oracle import geometry as OG, levelset as OL
+    build.build()
+    w = W.ellipse_dirichlet_2d(128)
+    g = OG.Grid(2, w.n, w.lo, w.h)
+    samples = OL.H(w.ls_kind, w.ls_params, g.coords())
+    Ga = kfbi.Problem.from_workload(w)
+    Gs = kfbi.Problem(2, w.n, w.lo, w.hi, W.LS_GRID, [], w.kind, ls_samples=samples)
+    assert Ga.nb == Gs.nb and Ga.nirr == Gs.nirr
+    pa, na, ps, ns = empty((Ga.nb, 2)), empty((Ga.nb, 2)), empty((Gs.nb, 2)), empty((Gs.nb, 2))
+    kfbi.kfbi_dof_points(Ga.handle, pa, na)
+    kfbi.kfbi_dof_points(Gs.handle, ps, ns)
+    assert float((pa - ps).abs().max()) < 1e-13 and float((na - ns).abs().max()) < 1e-12
+    ma, ms = empty(Ga.grid_shape, "u8"), empty(Gs.grid_shape, "u8")
+    kfbi.kfbi_inside_mask(Ga.handle, ma)
+    kfbi.kfbi_inside_mask(Gs.handle, ms)
+    assert bool(torch.equal(ma, ms))
+    x = torch.randn(Ga.nb, dtype=torch.float64, device="cuda")
+    ya, ys = empty(Ga.nb), empty(Gs.nb)
+    kfbi.kfbi_apply_operator(Ga.handle, x, ya)
+    kfbi.kfbi_apply_operator(Gs.handle, x, ys)
+    assert float((ya - ys).abs().max() / ya.abs().max()) < 1e-11
+    # a grid-sampled level set without samples is refused
+    with pytest.raises(kfbi.KfbiError) as e:
+        kfbi.Problem(2, w.n, w.lo, w.hi, W.LS_GRID, [], w.kind)
+    assert e.value.status == 1
+    Ga.close()
+    Gs.close()
