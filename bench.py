@@ -235,7 +235,8 @@ def run_ours(args, rank, world):
         step()
     prof = kfbi.kfbi_profile_read(G.handle)
     kfbi.kfbi_profile_enable(G.handle, False)
-    roof = roofline(args, G, prof, prec)
+    steps_run = kfbi.kfbi_box_solve_info(G.handle)[0]
+    roof = roofline(args, G, prof, prec, steps_run)
 
     # ---- the plain FP64 path at the same tolerance
     fp64 = None
@@ -290,6 +291,8 @@ def run_ours(args, rank, world):
         "roofline": roof,
     }
     G.close()
+    if args.config1:
+        out["config1"] = config1_leg(args, stream, flush)
     if args.batch > 0:
         out["batched"] = batched(args, stream, flush)
     if args.learned_n > 0:
@@ -305,58 +308,79 @@ def run_ours(args, rank, world):
     return out
 
 
-def batched(args, stream, flush):
-    """The batched workload: 64 seeded star-interface problems on grids drawn
-    from {128, 256, 512, 1024}^2, all solved by one batched GMRES
-    (kfbi_gmres_solve_batch) plus the per-instance evaluation.  Compared with
-    the same instances solved one after another by the plain FP64 path and by
-    the mixed path.  Draws whose interface the drawn grid cannot resolve are
-    skipped and counted (the seeded stream continues)."""
-    import numpy as np
-    import torch
-
+def _star_instances(count, seed, sizes, box_rtol, box_steps):
+    """Seeded star-interface problems (mixed precision); draws whose interface
+    the drawn grid cannot resolve (KFBI_ERR_GEOMETRY) are dropped and counted,
+    the seeded stream continues."""
     import workloads as W
     from paper_2309_05965_gb300 import kfbi
-    sizes = (128, 256, 512, 1024)
-    inst = []
-    redrawn = 0
-    # one seeded stream; a draw whose interface its grid cannot resolve
-    # (KFBI_ERR_GEOMETRY) is dropped and the stream continues
-    for w in W.star_batch_2d(count=4 * args.batch, seed=5965, sizes=sizes):
-        if len(inst) == args.batch:
+    inst, redrawn = [], 0
+    for w in W.star_batch_2d(count=4 * count, seed=seed, sizes=sizes):
+        if len(inst) == count:
             break
         try:
-            G = kfbi.Problem.from_workload(w, precision=kfbi.MIXED, box_rtol=args.box_rtol,
-                                           box_max_iters=args.box_steps)
+            G = kfbi.Problem.from_workload(w, precision=kfbi.MIXED, box_rtol=box_rtol,
+                                           box_max_iters=box_steps)
         except kfbi.KfbiError as e:
             if e.status != 2:
                 raise
             redrawn += 1
             continue
         inst.append((w, G))
+    return inst, redrawn
+
+
+def _instance_data(w, G):
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2309_05965_gb300 import kfbi
+    xyz = torch.zeros((G.nb, w.dim), dtype=torch.float64, device="cuda")
+    nrm = torch.zeros((G.nb, w.dim), dtype=torch.float64, device="cuda")
+    kfbi.kfbi_dof_points(G.handle, xyz, nrm)
+    g1, g2 = W.boundary_data(w, xyz.cpu().numpy(), nrm.cpu().numpy())
+    grid = W.grid_data(w)
+    keep = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in
+            (("g1", g1), ("g2", g2), ("f_in", grid["f_in"]), ("f_out", grid["f_out"]),
+             ("lapf_in", grid["lapf_in"]), ("lapf_out", grid["lapf_out"]), ("g_b", grid["g_b"]))}
+    return kfbi.make_data(**keep), keep
+
+
+def batched(args, stream, flush):
+    """The batched workload: 64 seeded star-interface problems on grids drawn
+    from {128, 256, 512, 1024}^2, all solved by one batched GMRES
+    (kfbi_gmres_solve_batch) plus one batched evaluation (kfbi_evaluate_batch).
+    Compared with the same instances solved one after another by the plain
+    FP64 path and by the mixed path.  Then the learned + mixed + batched form:
+    a network trained on other seeded star problems (their own solves) gives
+    every instance its start, inside the timed region.  Draws whose
+    interface the drawn grid cannot resolve are skipped and counted (the
+    seeded stream continues)."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2309_05965_gb300 import kfbi
+    sizes = (128, 256, 512, 1024)
+    inst, redrawn = _star_instances(args.batch, 5965, sizes, args.box_rtol, args.box_steps)
     rows = []
     for w, G in inst:
-        xyz = torch.zeros((G.nb, 2), dtype=torch.float64, device="cuda")
-        nrm = torch.zeros((G.nb, 2), dtype=torch.float64, device="cuda")
-        kfbi.kfbi_dof_points(G.handle, xyz, nrm)
-        g1, g2 = W.boundary_data(w, xyz.cpu().numpy(), nrm.cpu().numpy())
-        grid = W.grid_data(w)
-        keep = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in
-                (("g1", g1), ("g2", g2), ("f_in", grid["f_in"]), ("f_out", grid["f_out"]),
-                 ("lapf_in", grid["lapf_in"]), ("lapf_out", grid["lapf_out"]),
-                 ("g_b", grid["g_b"]))}
-        rows.append(dict(w=w, G=G, keep=keep, d=kfbi.make_data(**keep),
+        d, keep = _instance_data(w, G)
+        rows.append(dict(w=w, G=G, keep=keep, d=d,
                          x=torch.zeros(G.nb, dtype=torch.float64, device="cuda"),
+                         x0=torch.zeros(G.nb, dtype=torch.float64, device="cuda"),
                          u=torch.zeros(G.grid_shape, dtype=torch.float64, device="cuda")))
     opts = kfbi.GmresOpts(rtol=args.rtol, restart=100, max_iter=100, x0=None)
     B = kfbi.Batch([r["G"] for r in rows])
     datas = [r["d"] for r in rows]
     xs = [r["x"] for r in rows]
 
+    us = [r["u"] for r in rows]
+
     def step():
         infos = B.gmres_solve(datas, opts, xs)
-        for r in rows:
-            kfbi.kfbi_evaluate(r["G"].handle, r["d"], r["x"], r["u"])
+        B.evaluate(datas, xs, us)
         return infos
 
     def timed(fn, reps):
@@ -410,6 +434,64 @@ def batched(args, stream, flush):
     for G in g64:
         G.close()
     ratio = [e / max(e64, 1e-300) for e, e64 in zip(errs, errs64)]
+
+    # ---- learned + mixed + batched: train on other seeded star problems
+    learned = None
+    if args.batch_learned:
+        from paper_2309_05965_gb300 import learned as L
+        t0 = time.perf_counter()
+        train, _ = _star_instances(args.batch_train, 5966, (128, 256, 512), args.box_rtol, args.box_steps)
+        ds = L.Dataset(sum(G.nb for _, G in train))
+        topts = kfbi.GmresOpts(rtol=1e-10, restart=100, max_iter=100, x0=None)
+        for w, G in train:
+            d, keep = _instance_data(w, G)
+            x = torch.zeros(G.nb, dtype=torch.float64, device="cuda")
+            kfbi.kfbi_gmres_solve(G.handle, d, topts, x)
+            ds.add(G, d, x)
+            G.close()
+        torch.cuda.synchronize()
+        t_data = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        ws = L.WarmStart(seed=5965)
+        hist = ws.fit(ds, epochs=args.learned_epochs, batch=4096, lr=2e-3, lr_final=1e-6,
+                      min_steps=args.learned_steps)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        x0s = [r["x0"] for r in rows]
+
+        def step_learned():
+            for r in rows:
+                ws.predict(r["G"], r["d"], r["x0"])
+            infos = B.gmres_solve(datas, opts, xs, x0s=x0s)
+            B.evaluate(datas, xs, us)
+            return infos
+
+        for _ in range(2):
+            linfos = step_learned()
+        ms_learned = timed(step_learned, max(3, args.steps // 2))
+        lerrs = []
+        for r in rows:
+            ins = _inside(r["G"], kfbi)
+            ex = W.exact_grid(r["w"], ins)
+            lerrs.append(float(np.abs(r["u"].cpu().numpy() - ex)[1:-1, 1:-1].max()))
+        worst = sorted(((e / max(e64, 1e-300), r["w"].sigma_in, r["w"].n, i.iters)
+                        for e, e64, r, i in zip(lerrs, errs64, rows, linfos)), reverse=True)[:5]
+        # start quality: relative max difference of the start from the solved density
+        start_err = [float((r["x0"] - r["x"]).abs().max() / r["x"].abs().max()) for r in rows]
+        learned = {"solves_per_s": len(rows) / (ms_learned * 1e-3), "ms_per_batch": ms_learned,
+                   "speedup_vs_fp64_sequential": ms_fp64_seq / ms_learned,
+                   "speedup_vs_batched_zero_start": ms_batch / ms_learned,
+                   "gmres_iterations": [i.iters for i in linfos],
+                   "x0_rejected": sum(i.x0_rejected for i in linfos),
+                   "max_err_ratio_vs_fp64": max(e / max(e64, 1e-300) for e, e64 in zip(lerrs, errs64)),
+                   "start_rel_err_median": statistics.median(start_err), "start_rel_err_max": max(start_err),
+                   "worst_err_ratios": [{"ratio": a, "contrast": b, "n": c, "iters": d}
+                                        for a, b, c, d in worst],
+                   "train": {"solves": ds.solves, "samples": ds.n, "data_s": t_data, "train_s": t_train,
+                             "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
+                             "workload": f"{ds.solves} star problems drawn with seed 5966 on "
+                                         "{128,256,512}^2, GMRES rtol 1e-10"}}
+        ws.close()
     nsz = {}
     for r in rows:
         nsz[r["w"].n] = nsz.get(r["w"].n, 0) + 1
@@ -425,7 +507,8 @@ def batched(args, stream, flush):
            "max_err_ratio_mixed_sequential_vs_fp64": max(e / max(e64, 1e-300)
                                                          for e, e64 in zip(errs_mixed, errs64)),
            "fp64_max_err_vs_exact": max(errs64),
-           "tuned_tiles": dict(zip(("pass_ctas", "row_ctas"), B.tiles()))}
+           "tuned_tiles": dict(zip(("pass_ctas", "row_ctas"), B.tiles())),
+           "learned": learned}
     B.close()
     for r in rows:
         r["G"].close()
@@ -433,88 +516,87 @@ def batched(args, stream, flush):
 
 
 def learned_leg(args, stream, flush):
-    """Learned initial density on the harmonic ellipsoid family: train the
-    network on 2000 solves (40 ellipsoids x 50 data draws) on a 64^3 grid, then
-    on held-out ellipsoids at --learned-n^3 compare the plain FP64 path, the
-    mixed path from zero and the mixed path from the learned start (the
-    prediction is inside the timed region)."""
+    """Learned initial density on the wave-field ellipsoid family (random
+    axes, fixed non-polynomial harmonic fields inside and outside, contrast
+    10): train the network on the library's own solves of
+    --learned-geometries ellipsoids (seed 5966) on a 64^3 grid (draws the grid
+    cannot resolve are skipped and counted), then on held-out ellipsoids
+    (seed 5967) at --learned-n^3 compare the plain FP64 path, the mixed path
+    from zero and the mixed path from the learned start (the prediction is
+    inside the timed region)."""
     import numpy as np
     import torch
 
     import workloads as W
     from paper_2309_05965_gb300 import kfbi, learned
 
-    def solve_data(G, w):
-        xyz = torch.zeros((G.nb, 3), dtype=torch.float64, device="cuda")
-        nrm = torch.zeros((G.nb, 3), dtype=torch.float64, device="cuda")
-        kfbi.kfbi_dof_points(G.handle, xyz, nrm)
-        g1, g2 = W.boundary_data(w, xyz.cpu().numpy(), nrm.cpu().numpy())
-        grid = W.grid_data(w)
-        keep = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in
-                (("g1", g1), ("g2", g2), ("f_in", grid["f_in"]), ("f_out", grid["f_out"]),
-                 ("lapf_in", grid["lapf_in"]), ("lapf_out", grid["lapf_out"]),
-                 ("g_b", grid["g_b"]))}
-        return kfbi.make_data(**keep), keep
-
     t0 = time.perf_counter()
     opts = kfbi.GmresOpts(rtol=1e-10, restart=100, max_iter=100, x0=None)
-    train = W.warm_start_training_set(seed=5966, geometries=args.learned_geometries,
-                                      draws=args.learned_draws)
-    ds = learned.Dataset(args.learned_geometries * args.learned_draws * 8000)
-    for axes, amps_list in train:
-        G = kfbi.Problem.from_workload(W.harmonic_ellipsoid_3d(axes, amps_list[0], 64),
-                                       precision=kfbi.MIXED)
+    axes_train = W.ellipsoid_axes(5966, args.learned_geometries)
+    ds = None
+    skipped = 0
+    for axes in axes_train:
+        w = W.wave_ellipsoid_3d(axes, 64)
+        try:
+            G = kfbi.Problem.from_workload(w, precision=kfbi.MIXED)
+        except kfbi.KfbiError as e:
+            if e.status != 2:
+                raise
+            skipped += 1
+            continue
+        if ds is None:
+            # at 64^3 an ellipsoid with axes <= 0.7 has fewer than 12000 DOFs
+            ds = learned.Dataset(len(axes_train) * 12000)
+        d, keep = _instance_data(w, G)
         x = torch.zeros(G.nb, dtype=torch.float64, device="cuda")
-        for amps in amps_list:
-            d, keep = solve_data(G, W.harmonic_ellipsoid_3d(axes, amps, 64))
-            kfbi.kfbi_gmres_solve(G.handle, d, opts, x)
-            ds.add(G, d, x)
+        kfbi.kfbi_gmres_solve(G.handle, d, opts, x)
+        ds.add(G, d, x)
         G.close()
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
     ws = learned.WarmStart(seed=5965)
-    hist = ws.fit(ds, epochs=args.learned_epochs, batch=8192, lr=2e-3, lr_final=1e-6)
+    hist = ws.fit(ds, epochs=args.learned_epochs, batch=8192, lr=2e-3, lr_final=1e-6,
+                  min_steps=args.learned_steps)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
 
     n = args.learned_n
     eopts = kfbi.GmresOpts(rtol=args.rtol, restart=100, max_iter=100, x0=None)
     rows = {"fp64_zero": [], "mixed_zero": [], "mixed_learned": []}
-    for axes, amps_list in W.warm_start_training_set(seed=5967, geometries=1,
-                                                     draws=args.learned_eval):
-        w0 = W.harmonic_ellipsoid_3d(axes, amps_list[0], n)
-        Gm = kfbi.Problem.from_workload(w0, precision=kfbi.MIXED, box_rtol=args.box_rtol)
-        G64 = kfbi.Problem.from_workload(w0, precision=kfbi.FP64)
+    start_err = []
+    for axes in W.ellipsoid_axes(5967, args.learned_eval):
+        w = W.wave_ellipsoid_3d(axes, n)
+        Gm = kfbi.Problem.from_workload(w, precision=kfbi.MIXED, box_rtol=args.box_rtol)
+        G64 = kfbi.Problem.from_workload(w, precision=kfbi.FP64)
         x = torch.zeros(Gm.nb, dtype=torch.float64, device="cuda")
         x0 = torch.zeros_like(x)
         u = torch.zeros(Gm.grid_shape, dtype=torch.float64, device="cuda")
         ins = _inside(Gm, kfbi)
-        for amps in amps_list:
-            w = W.harmonic_ellipsoid_3d(axes, amps, n)
-            d, keep = solve_data(Gm, w)
-            ex = W.exact_grid(w, ins)
-            for name, G, use in (("fp64_zero", G64, False), ("mixed_zero", Gm, False),
-                                 ("mixed_learned", Gm, True)):
-                def run():
-                    o = eopts
-                    if use:
-                        ws.predict(G, d, x0)
-                        o = kfbi.GmresOpts(rtol=args.rtol, restart=100, max_iter=100,
-                                           x0=x0.data_ptr())
-                    info = kfbi.kfbi_gmres_solve(G.handle, d, o, x)
-                    kfbi.kfbi_evaluate(G.handle, d, x, u)
-                    return info
-                run()
-                flush.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                info = run()
-                e1.record(stream)
-                e1.synchronize()
-                err = float(np.abs(u.cpu().numpy() - ex)[1:-1, 1:-1, 1:-1].max())
-                rows[name].append((e0.elapsed_time(e1), info.iters, err, info.x0_rejected))
+        d, keep = _instance_data(w, Gm)
+        ex = W.exact_grid(w, ins)
+        for name, G, use in (("fp64_zero", G64, False), ("mixed_zero", Gm, False),
+                             ("mixed_learned", Gm, True)):
+            def run():
+                o = eopts
+                if use:
+                    ws.predict(G, d, x0)
+                    o = kfbi.GmresOpts(rtol=args.rtol, restart=100, max_iter=100, x0=x0.data_ptr())
+                info = kfbi.kfbi_gmres_solve(G.handle, d, o, x)
+                kfbi.kfbi_evaluate(G.handle, d, x, u)
+                return info
+            run()
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = run()
+            e1.record(stream)
+            e1.synchronize()
+            err = float(np.abs(u.cpu().numpy() - ex)[1:-1, 1:-1, 1:-1].max())
+            rows[name].append((e0.elapsed_time(e1), info.iters, err, info.x0_rejected))
+            if use:
+                start_err.append(float((x0 - x).abs().max() / x.abs().max()))
         Gm.close()
         G64.close()
     ws.close()
@@ -525,13 +607,17 @@ def learned_leg(args, stream, flush):
                 "gmres_iterations": [v[1] for v in r], "max_err_vs_exact": max(v[2] for v in r),
                 "x0_rejected": sum(v[3] for v in r)}
     out = {k: agg(v) for k, v in rows.items()}
-    out["workload"] = (f"ellipsoid interface 3D, N={n}, contrast 10, harmonic data; network "
-                       f"3 layers x 256 trained on {ds.solves} solves at 64^3 "
-                       f"({ds.n} DOF samples), GMRES rtol {args.rtol:g}")
+    out["workload"] = (f"ellipsoid interface 3D, N={n}, contrast 10, fixed non-polynomial harmonic fields "
+                       f"inside and outside; network 3 layers x 256 trained on {ds.solves} solves of other "
+                       f"ellipsoids at 64^3 ({ds.n} DOF samples, {skipped} unresolved draws skipped), "
+                       f"GMRES rtol {args.rtol:g}")
+    out["start_rel_err"] = start_err
     out["train"] = {"data_s": t_data, "train_s": t_train, "loss_first_epoch": hist[0],
                     "loss_last_epoch": hist[-1], "epochs": len(hist)}
     out["speedup_learned_mixed_vs_fp64_zero"] = (out["mixed_learned"]["solves_per_s"]
                                                  / out["fp64_zero"]["solves_per_s"])
+    out["speedup_learned_vs_mixed_zero"] = (out["mixed_learned"]["solves_per_s"]
+                                            / out["mixed_zero"]["solves_per_s"])
     out["err_ratio_learned_vs_fp64"] = (out["mixed_learned"]["max_err_vs_exact"]
                                         / max(out["fp64_zero"]["max_err_vs_exact"], 1e-300))
     return out
@@ -615,14 +701,22 @@ def threed_leg(args, stream, flush):
             prof = kfbi.kfbi_profile_read(G.handle)
             kfbi.kfbi_profile_enable(G.handle, False)
             mg_ms, mg_launches = prof["mg"]
-            steps = args.box_steps or 8
-            cycles = 4 * steps
+            steps, cycles, _, _ = kfbi.kfbi_box_solve_info(G.handle)
             achieved = npts * 72.5 * 8 / 7 * cycles / (mg_ms * 1e-3) / 1e9
             peak = measured_peaks().get("hbm_gbs", 6800.0)
             r["mg_roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                                "frac": achieved / peak, "cycles": cycles, "mg_ms": mg_ms,
-                                "launches": mg_launches,
-                                "note": "upper bound on cycles (converged outer steps skip their work)"}
+                                "frac": achieved / peak, "cycles": cycles, "outer_steps": steps,
+                                "mg_ms": mg_ms, "launches": mg_launches,
+                                "note": "cycles that ran (device counters); 82.9 B per fine point "
+                                        "per V(2,2) cycle (FP32)"}
+        else:
+            steps, _, _, _ = kfbi.kfbi_box_solve_info(G.handle)
+            peak = measured_peaks().get("hbm_gbs", 6800.0)
+            achieved = 16.0 * npts / (box_ms * 1e-3) / 1e9
+            r["box_roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                 "frac": achieved / peak, "steps": steps,
+                                 "note": "16 B per interior point per box solve (FP64 R in, u out) "
+                                         "over the whole box solve's time"}
         out[name] = r
         G.close()
     out["speedup_mixed_dst_vs_fp64"] = out["dst_mixed"]["solves_per_s"] / out["dst_fp64"]["solves_per_s"]
@@ -775,73 +869,212 @@ def _inside(G, kfbi):
     return m.cpu().numpy().astype(bool)
 
 
-def roofline(args, G, prof, prec):
-    """Roofline of the dominant kernel class from the profiling pass.
-    Algorithmic bytes per interior point are counted below, pass by pass."""
+# DRAM bytes (read + write) per launch of the three FP32 passes of a
+# correction step at the 2D N = 1024 workload with 3 refinement steps, from
+# one ncu capture of the current kernels (profiles/k_dst32_k_res_fix2_flower1024.md;
+# cold cache: ncu flushes L2 before each replay, in the timed loop the grids
+# stay in L2); None once the kernels change
+NCU_DST_BYTES_PER_LAUNCH_1024 = (4.279e6 + 4.285e6 + 12.667e6) / 3
+
+
+def roofline(args, G, prof, prec, box_steps=None):
+    """Roofline of the box solve's transform passes (the dominant kernel class).
+
+    Algorithmic bytes: one box solve reads the FP64 right-hand side and writes
+    the FP64 solution once, 16 B per interior point (the minimum a box solve
+    can move).  A box solve is `passes` launches of the class (3 per FP32
+    solve in 2D, times the refinement steps that ran), so a launch's share is
+    16 (N-1)^d / passes bytes; achieved = that / the class's average launch
+    duration (per-launch CUDA events of the profiling pass on the library's
+    stream).  The bytes the passes actually stream (the implementation's
+    intermediate FP32/int64 grids, counted pass by pass) and the ncu DRAM
+    bytes per launch go in `pass_bytes` and `traffic`."""
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
-    name = max(prof, key=lambda k: prof[k][0])
-    ms, launches = prof[name]
     n = args.n
     npts = (n - 1) ** 2
+    ms, launches = prof["dst"]
     per_launch_ms = ms / max(1, launches)
-    if name == "dst":
-        # bytes per interior point of one box solve, three passes per transform:
-        # mixed, first step: FP64 R in -> FP32 (12), FP32 -> FP32 (8), -> FP32 u0 (8);
-        # each refinement step: FP32 r in (8), FP32 (8), FP32 + int64 u read and
-        # written (20); the FP64 solution once (8); FP64: 16 per pass
-        if prec:
-            s = args.box_steps or 5
-            per_point, passes = 28 + 36 * (s - 1) + 8, 3 * s
-        else:
-            per_point, passes = 48, 3
-        achieved = npts * per_point / passes / (per_launch_ms * 1e-3) / 1e9
-        r = {"kernel": "dst", "bound": "hbm", "achieved": achieved, "peak": hbm,
-             "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-             "note": "peak of measured (MEASURED_PEAKS.json hbm_gbs)"}
-        if prec and n == 1024 and s == 3:
-            # DRAM bytes per launch (read + write) of the three FP32 passes of a
-            # correction step at this workload, averaged, from one ncu capture of
-            # the current kernels (cold cache: ncu flushes L2 before each replay;
-            # in the timed loop the grids stay in L2)
-            r["traffic"] = (4.279e6 + 4.285e6 + 12.667e6) / 3
-            r["traffic_note"] = "bytes per launch, ncu dram__bytes_read.sum + dram__bytes_write.sum, cold cache"
-        return r
-    if name == "residual":
-        flops = npts * 10.0
-        achieved = flops / (per_launch_ms * 1e-3) / 1e12
-        return {"kernel": "residual", "bound": "alu", "achieved": achieved,
-                "peak": FP64_ALU_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_ALU_TFLOPS,
-                "traffic": None, "note": "FP64 ALU peak 152 SM x 2 FMA/clk x 2.07 GHz"}
-    # other classes: report measured time share only
-    achieved = 0.0
-    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_ALU_TFLOPS,
-            "unit": "TFLOP/s", "frac": None, "traffic": None}
+    if prec:
+        # launches enqueued per box solve: 3 per FP32 solve for every step the
+        # solver may take (steps stopped by the convergence flag still launch
+        # and return at once, so the class time per box solve is the average
+        # launch times this count)
+        s = args.box_steps or 5
+        # pass by pass: first FP32 solve FP64 R in -> FP32 (12), FP32 -> FP32
+        # (8), -> FP32 u0 (8); each refinement step FP32 r in (8), FP32 (8),
+        # FP32 + int64 u_fix read and written (20); the FP64 solution once (8)
+        pass_bytes, passes = 28 + 36 * (s - 1) + 8, 3 * s
+    else:
+        s = 1
+        pass_bytes, passes = 48, 3
+    alg_launch = 16.0 * npts / passes
+    achieved = alg_launch / (per_launch_ms * 1e-3) / 1e9
+    r = {"kernel": "dst (k_dst32 FP32 transform passes)" if prec else "dst (k_dst_pass FP64)",
+         "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+         "traffic": None,
+         "algorithmic_bytes_per_launch": alg_launch, "launches_per_box_solve": passes,
+         "box_solve_dst_us": per_launch_ms * passes * 1e3, "steps_run": box_steps,
+         "avg_launch_us": per_launch_ms * 1e3,
+         "pass_bytes_per_point": pass_bytes,
+         "pass_bytes_per_launch": pass_bytes * npts / passes,
+         "note": "peak of measured (MEASURED_PEAKS.json hbm_gbs); algorithmic bytes 16 B per interior "
+                 "point per box solve (FP64 R in, u out)"}
+    if prec and n == 1024 and s == 3 and NCU_DST_BYTES_PER_LAUNCH_1024:
+        r["traffic"] = NCU_DST_BYTES_PER_LAUNCH_1024
+        r["traffic_vs_algorithmic"] = NCU_DST_BYTES_PER_LAUNCH_1024 / alg_launch
+        r["traffic_note"] = ("bytes per launch, ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                             "cold cache")
+    return r
 
 
 def cpu_baseline(args, budget_s=20.0):
-    """The oracle as it stands on the host cores: full solves of the same
-    workload (set-up excluded), within a time budget."""
+    """The oracle as it stands on the host cores, run twice in fresh
+    processes (BLAS and FFT thread counts are fixed at import): with one
+    thread and with every core.  Each run times the stages of the GPU path on
+    the same workload (box solve, one operator application, full solves,
+    set-up excluded) and the 64^2 Dirichlet solve; `value` is the all-cores
+    full-solve rate."""
+    runs = {}
+    for threads in (1, os.cpu_count() or 1):
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+            env[k] = str(threads)
+        cmd = [sys.executable, os.path.abspath(__file__), "--cpu-stages", str(threads), "--n", str(args.n),
+               "--rtol", repr(args.rtol), "--cpu-budget", repr(budget_s / 2)]
+        r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+        if r.returncode != 0:
+            raise RuntimeError("CPU oracle run failed:\n" + r.stdout[-2000:] + r.stderr[-2000:])
+        runs[threads] = json.loads(r.stdout.strip().splitlines()[-1])
+    allc = runs[max(runs)]
+    one = runs[1]
+    return {"value": allc["solves_per_s"], "unit": "solves/s", "cores": max(runs), "kind": "oracle",
+            "sample": f"{allc['solves']} full oracle solves of the same workload (N={args.n}), set-up "
+                      f"excluded, NumPy/SciPy with {max(runs)} BLAS/FFT threads; box solve and operator "
+                      "application timed alone",
+            "host": os.uname().machine, "cpu_count": os.cpu_count(),
+            "all_cores": allc, "single_thread": one}
+
+
+def cpu_stages(args):
+    """Child process of cpu_baseline: the oracle's stages with the BLAS/FFT
+    thread count given (environment set by the parent), one JSON line."""
     import numpy as np
+    import scipy.fft
 
     import workloads as W
     from oracle import kfbi as OK
-    w = workload(args.n)
-    P = OK.Problem(w)
-    data = W.grid_data(w)
-    g1, g2 = W.boundary_data(w, P.surf.x, P.surf.n)
-    t0 = time.perf_counter()
-    count = 0
-    while True:
-        P.solve(g1, g2, data, rtol=args.rtol)
-        count += 1
-        if time.perf_counter() - t0 > budget_s or count >= 5:
-            break
-    el = time.perf_counter() - t0
-    return {"value": count / el, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"{count} full oracle solves of the same workload (N={args.n}), set-up "
-                      "excluded, single-threaded NumPy/SciPy (scipy.fft workers=1)",
-            "host": os.uname().machine, "cpu_count": os.cpu_count()}
+    threads = args.cpu_stages
+    out = {"threads": threads}
+    with scipy.fft.set_workers(threads):
+        w = workload(args.n)
+        t0 = time.perf_counter()
+        P = OK.Problem(w)
+        out["setup_s"] = time.perf_counter() - t0
+        data = W.grid_data(w)
+        g1, g2 = W.boundary_data(w, P.surf.x, P.surf.n)
+        rng = np.random.default_rng(0)
+        R = W.sine_grid_rhs(2, args.n, 1)
+        x = rng.standard_normal(P.nb)
+
+        def med(fn, k):
+            ts = []
+            for _ in range(k):
+                t = time.perf_counter()
+                fn()
+                ts.append(time.perf_counter() - t)
+            return statistics.median(ts)
+        box_s = med(lambda: P.box_solve(R), 3)
+        out["box_solve_ms"] = box_s * 1e3
+        out["box_solve_mpts_s"] = (args.n - 1) ** 2 / box_s / 1e6
+        out["apply_ms"] = med(lambda: P.apply(x), 3) * 1e3
+        t0 = time.perf_counter()
+        count = 0
+        while True:
+            P.solve(g1, g2, data, rtol=args.rtol)
+            count += 1
+            if time.perf_counter() - t0 > args.cpu_budget or count >= 5:
+                break
+        el = time.perf_counter() - t0
+        out["solves"] = count
+        out["solves_per_s"] = count / el
+        # the 64^2 Dirichlet BVP (ellipse, u = e^x sin y, FP64, rtol 1e-10)
+        w1 = W.ellipse_dirichlet_2d(64)
+        P1 = OK.Problem(w1)
+        d1 = W.grid_data(w1)
+        h1, h2 = W.boundary_data(w1, P1.surf.x, P1.surf.n)
+        out["ellipse64_solve_ms"] = med(lambda: P1.solve(h1, h2, d1, rtol=1e-10), 5) * 1e3
+    print(json.dumps(out))
+
+
+def config1_leg(args, stream, flush):
+    """The 2D interior Dirichlet BVP on the ellipse x^2/0.36 + y^2/0.16 < 1,
+    u = e^x sin y, 64^2 grid, 4th order, FP64 DST, GMRES rtol 1e-10.  About
+    100 DOFs and a 63^2 box: latency-bound, so reported as microseconds per
+    solve, per GMRES iteration, per operator application and per box solve
+    (CUDA events, median over repetitions, L2 flushed before each)."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2309_05965_gb300 import kfbi
+    w = W.ellipse_dirichlet_2d(64)
+    G = kfbi.Problem.from_workload(w, box_solver=kfbi.BOX_DST, precision=kfbi.FP64)
+    xyz = torch.zeros((G.nb, 2), dtype=torch.float64, device="cuda")
+    nrm = torch.zeros_like(xyz)
+    kfbi.kfbi_dof_points(G.handle, xyz, nrm)
+    g1, _ = W.boundary_data(w, xyz.cpu().numpy(), nrm.cpu().numpy())
+    grid = W.grid_data(w)
+    keep = {"g1": torch.from_numpy(g1).cuda(),
+            "f_in": torch.from_numpy(np.ascontiguousarray(grid["f_in"])).cuda(),
+            "lapf_in": torch.from_numpy(np.ascontiguousarray(grid["lapf_in"])).cuda()}
+    d = kfbi.make_data(**keep)
+    x = torch.zeros(G.nb, dtype=torch.float64, device="cuda")
+    u = torch.zeros(G.grid_shape, dtype=torch.float64, device="cuda")
+    opts = kfbi.GmresOpts(rtol=1e-10, restart=100, max_iter=200, x0=None)
+    rhs = torch.randn(G.grid_shape, dtype=torch.float64, device="cuda")
+    ub = torch.zeros_like(rhs)
+    y = torch.zeros_like(x)
+    xr = torch.randn_like(x)
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts) * 1e3
+
+    infos = []
+
+    def solve():
+        infos.append(kfbi.kfbi_gmres_solve(G.handle, d, opts, x))
+        kfbi.kfbi_evaluate(G.handle, d, x, u)
+
+    for _ in range(5):
+        solve()
+    solve_us = timed(solve, 50)
+    gmres_us = timed(lambda: infos.append(kfbi.kfbi_gmres_solve(G.handle, d, opts, x)), 50)
+    apply_us = timed(lambda: kfbi.kfbi_apply_operator(G.handle, xr, y), 50)
+    box_us = timed(lambda: kfbi.kfbi_box_solve(G.handle, rhs, ub), 50)
+    it = infos[-1].iters
+    ins = _inside(G, kfbi)
+    err = float(np.abs(u.cpu().numpy() - W.exact_grid(w, ins))[ins].max())
+    out = {"workload": "ellipse Dirichlet 2D, N=64, u=e^x sin y, 4th order, FP64 DST, GMRES rtol 1e-10",
+           "n_b": G.nb, "gmres_iterations": it, "us_per_solve": solve_us,
+           "solves_per_s": 1e6 / solve_us, "us_gmres": gmres_us,
+           "us_per_gmres_iteration": gmres_us / max(1, it), "us_per_operator_application": apply_us,
+           "us_per_box_solve": box_us, "max_err_vs_exact": err,
+           "paper_table1_n64": {"n_b": 116, "gmres_iterations": 10, "einf": 1.31e-4, "cpu_s": 3.91e-3,
+                                "note": "Sec. 7.1.1's rotated ellipse in [-1.2,1.2]^2 (a different "
+                                        "geometry), on the paper's CPU"}}
+    G.close()
+    return out
 
 
 def run_reference(args):
@@ -925,16 +1158,25 @@ def main():
     ap.add_argument("--box", default="dst", choices=["dst", "mg"])
     ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-config1", dest="config1", action="store_false",
+                    help="skip the 64^2 Dirichlet latency leg")
+    ap.add_argument("--cpu-stages", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--batch", type=int, default=64,
                     help="instances of the batched star-interface workload (0: skip)")
+    ap.add_argument("--no-batch-learned", dest="batch_learned", action="store_false",
+                    help="skip the learned start of the batched workload")
+    ap.add_argument("--batch-train", type=int, default=160,
+                    help="training problems of the batched workload's learned start")
     ap.add_argument("--learned-n", type=int, default=256,
                     help="grid of the learned-start evaluation (0: skip)")
-    ap.add_argument("--learned-geometries", type=int, default=40)
-    ap.add_argument("--learned-draws", type=int, default=50)
+    ap.add_argument("--learned-geometries", type=int, default=400,
+                    help="training ellipsoids (one solve each) of the 3D learned start")
     ap.add_argument("--learned-epochs", type=int, default=10)
+    ap.add_argument("--learned-steps", type=int, default=8000,
+                    help="minimum Adam steps of the networks' second training phase")
     ap.add_argument("--learned-eval", type=int, default=3)
-    ap.add_argument("--threed-n", type=int, default=128,
+    ap.add_argument("--threed-n", type=int, default=256,
                     help="grid of the 3D torus workload (0: skip)")
     ap.add_argument("--neumann-n", type=int, default=256,
                     help="grid of the Neumann torus leg (Sec. 7.2.1); 0 skips it")
@@ -944,6 +1186,9 @@ def main():
                     help="profiling aid: on the 3D torus at --threed-n, time the mixed box solve alone and run "
                          "one more inside cudaProfilerStart/Stop (for ncu --profile-from-start off); no JSON line")
     args = ap.parse_args()
+    if args.cpu_stages:
+        cpu_stages(args)
+        return
     if args.profile_box:
         profile_box(args)
         return

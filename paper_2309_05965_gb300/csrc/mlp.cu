@@ -236,42 +236,24 @@ __global__ void k_adam(int lo, int hi, float* __restrict__ theta, const float* _
   wbf[t] = __float2bfloat16_rn(th);
 }
 
-// s = sqrt(mean_j (g1_j^2 + g2_j^2)) (1 when the data vanish): the data scale
-// that makes the features and the density of one problem O(1); the density is
-// linear in the data, so the network learns the map at unit data size.
-__global__ void k_ws_scale(int nb, const double* __restrict__ g1, const double* __restrict__ g2,
-                           double* __restrict__ s) {
-  __shared__ double part[32];
-  double acc = 0.0;
-  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-    const double a = g1 ? g1[j] : 0.0, b = g2 ? g2[j] : 0.0;
-    acc += a * a + b * b;
-  }
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
-    const double v = sqrt(t / (double)max(nb, 1));
-    s[0] = v > 0.0 ? v : 1.0;
-  }
-}
-
-// Per-DOF raw features: [g1/s, g2/s, n (3), x (3), level-set parameters p0..p5, 0, 0]
+// Per-DOF raw features: [g1, g2, n (3), x (3), level-set parameters p0..p5,
+// log10(sigma_in/sigma_out) (0 for a boundary value problem), 0].  The data
+// are not rescaled per problem: the network's input normalisation (from its
+// training set) brings each feature to unit size, and a problem family whose
+// data share fields (the same sources with different geometries and
+// coefficients) keeps its density a function of the DOF's features alone.
 __global__ void k_features(int nb, int d, const double* __restrict__ x0, const double* __restrict__ x1,
                            const double* __restrict__ x2, const double* __restrict__ n0,
                            const double* __restrict__ n1, const double* __restrict__ n2,
                            const double* __restrict__ g1, const double* __restrict__ g2, LevelSet ls,
-                           const double* __restrict__ scale, float* __restrict__ F,
-                           const double* __restrict__ dens, float* __restrict__ target) {
+                           float lcontrast, float* __restrict__ F, const double* __restrict__ dens,
+                           float* __restrict__ target) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nb) return;
-  const double is = 1.0 / scale[0];
-  if (target) target[j] = (float)(dens[j] * is);
+  if (target) target[j] = (float)dens[j];
   float* f = F + (long long)j * KFBI_WS_FEATURES;
-  f[0] = g1 ? (float)(g1[j] * is) : 0.f;
-  f[1] = g2 ? (float)(g2[j] * is) : 0.f;
+  f[0] = g1 ? (float)g1[j] : 0.f;
+  f[1] = g2 ? (float)g2[j] : 0.f;
   f[2] = (float)n0[j];
   f[3] = (float)n1[j];
   f[4] = d == 3 ? (float)n2[j] : 0.f;
@@ -279,14 +261,14 @@ __global__ void k_features(int nb, int d, const double* __restrict__ x0, const d
   f[6] = (float)x1[j];
   f[7] = d == 3 ? (float)x2[j] : 0.f;
   for (int k = 0; k < 6; ++k) f[8 + k] = k < ls.np ? (float)ls.p[k] : 0.f;
-  f[14] = 0.f;
+  f[14] = lcontrast;
   f[15] = 0.f;
 }
 
 __global__ void k_to_density(int n, const float* __restrict__ y, double shift, double scale,
-                             const double* __restrict__ s, double* __restrict__ x) {
+                             double* __restrict__ x) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < n) x[j] = ((double)y[j] * scale + shift) * s[0];
+  if (j < n) x[j] = (double)y[j] * scale + shift;
 }
 
 kfbi_status ensure(kfbi_mlp* m, int n) {
@@ -506,11 +488,11 @@ kfbi_status kfbi_warm_start_features(kfbi_problem* p, const kfbi_data* data, con
                                      float* features, float* target) {
   if (!p || !data || !features || !data->g1 || (!density != !target)) return KFBI_ERR_ARG;
   const Grid g = p->g;
-  if (!p->ws_scale) KFBI_CUDA(p, dalloc(&p->ws_scale, 1));
-  KFBI_LAUNCH(p, KFBI_KC_OTHER, k_ws_scale<<<1, 1024, 0, p->stream>>>(p->nb, data->g1, data->g2, p->ws_scale));
+  const bool iface = p->cfg.kind == KFBI_INTERFACE_MU || p->cfg.kind == KFBI_INTERFACE_GENERAL;
+  const float lcontrast = iface ? (float)std::log10(p->cfg.sigma_in / p->cfg.sigma_out) : 0.f;
   KFBI_LAUNCH(p, KFBI_KC_OTHER, k_features<<<div_up(p->nb, 128), 128, 0, p->stream>>>(
       p->nb, g.d, p->x[0], p->x[1], g.d == 3 ? p->x[2] : p->x[0], p->nrm[0], p->nrm[1],
-      g.d == 3 ? p->nrm[2] : p->nrm[0], data->g1, data->g2, p->ls, p->ws_scale, features, density, target));
+      g.d == 3 ? p->nrm[2] : p->nrm[0], data->g1, data->g2, p->ls, lcontrast, features, density, target));
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
 }
@@ -536,7 +518,7 @@ kfbi_status kfbi_warm_start(kfbi_problem* p, kfbi_mlp* m, const kfbi_data* data,
     if (s != KFBI_OK) return fail(p, s, m->err);
   }
   KFBI_LAUNCH(p, KFBI_KC_OTHER, k_to_density<<<div_up(nb, 256), 256, 0, p->stream>>>(nb, m->y, m->out_shift,
-                                                                                         m->out_scale, p->ws_scale, x0));
+                                                                                         m->out_scale, x0));
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
 }

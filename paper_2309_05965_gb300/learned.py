@@ -72,13 +72,16 @@ class WarmStart:
         return np.concatenate(parts).astype(np.float32)
 
     def fit(self, ds: Dataset, epochs: int = 8, batch: int = 4096, lr: float = 1e-3,
-            lr_final: float = 1e-6, linear_epochs: int = 3, floor: float = 1e-7):
+            lr_final: float = 1e-6, linear_epochs: int = 3, floor: float = 1e-7,
+            min_steps: int = 0):
         """Normalise inputs and targets from the data set, then minibatch Adam in
         two phases: the linear part alone (b3, WL: a least-squares fit of the
         density on the features), then, if its loss is above `floor`, the whole
         network with the nonlinear branch starting from zero output.  Learning
-        rates decay geometrically to lr_final within each phase.  Returns the
-        mean loss of each epoch (normalised target units)."""
+        rates decay geometrically to lr_final within each phase.  The second
+        phase runs `epochs` passes over the data, or more if that is fewer
+        than `min_steps` minibatch steps (small data sets).  Returns the mean
+        loss of each epoch (normalised target units)."""
         import torch
         n = ds.n
         Xh = ds.X[:n].cpu().numpy().astype(np.float64)
@@ -115,7 +118,7 @@ class WarmStart:
         self.linear_loss = hist[-1]
         self.branch_trained = self.linear_loss > floor
         if self.branch_trained:
-            phase(kfbi.MLP_BRANCH | kfbi.MLP_LINEAR, epochs, lr)
+            phase(kfbi.MLP_BRANCH | kfbi.MLP_LINEAR, max(epochs, -(-min_steps // nbatch)), lr)
         kfbi.kfbi_mlp_set_trainable(self.handle, kfbi.MLP_BRANCH | kfbi.MLP_LINEAR)
         return hist
 

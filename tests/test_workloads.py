@@ -80,22 +80,20 @@ def test_flux_data_match_finite_differences(make):
     assert np.abs(g2 - ref).max() < 1e-8
 
 
-def test_cubic_harmonics_are_harmonic_with_exact_gradients():
-    """The 16 degree <= 3 harmonics: Laplacian zero and gradient equal to
-    central differences (both to rounding), linearly independent."""
+def test_wave_fields_are_harmonic_with_exact_gradients():
     import numpy as np
     import workloads as W
-    rng = np.random.default_rng(3)
-    X = rng.uniform(-1, 1, size=(50, 3))
-    H, G = W._cubic_harmonics(X)
+    w = W.wave_ellipsoid_3d([0.5, 0.4, 0.6], 64)
+    (ui, gi, li), (uo, go, lo) = W.solutions(w)
+    rng = np.random.default_rng(4)
+    X = rng.uniform(-1, 1, size=(40, 3))
     e = 1e-4
-    lap = np.zeros_like(H)
-    for k in range(3):
-        d = np.zeros(3)
-        d[k] = e
-        Hp, _ = W._cubic_harmonics(X + d)
-        Hm, _ = W._cubic_harmonics(X - d)
-        assert np.abs((Hp - Hm) / (2 * e) - G[..., k]).max() < 1e-7
-        lap += (Hp - 2 * H + Hm) / (e * e)
-    assert np.abs(lap).max() < 1e-5
-    assert np.linalg.matrix_rank(H) == 16
+    for u, g in ((ui, gi), (uo, go)):
+        lap = -6 * u(X)
+        for k in range(3):
+            d = np.zeros(3)
+            d[k] = e
+            assert np.abs((u(X + d) - u(X - d)) / (2 * e) - g(X)[:, k]).max() < 1e-6
+            lap = lap + u(X + d) + u(X - d)
+        assert np.abs(lap / (e * e)).max() < 1e-4
+    assert np.abs(ui(X) - uo(X)).max() > 0.1

@@ -164,38 +164,6 @@ def _sol_harmonic3(amps):
     return u, g, lap
 
 
-def _cubic_harmonics(X):
-    """The 16 harmonic polynomials of degree <= 3 in 3D and their gradients,
-    shapes (..., 16) and (..., 16, 3): 1; x, y, z; xy, yz, zx, x^2 - y^2,
-    2z^2 - x^2 - y^2; x^3 - 3xy^2, 3x^2 y - y^3, z(x^2 - y^2), xyz,
-    x(4z^2 - x^2 - y^2), y(4z^2 - x^2 - y^2), z(2z^2 - 3x^2 - 3y^2)."""
-    x, y, z = X[..., 0], X[..., 1], X[..., 2]
-    o, zr = np.ones_like(x), np.zeros_like(x)
-    h = [o, x, y, z, x * y, y * z, z * x, x * x - y * y, 2 * z * z - x * x - y * y,
-         x ** 3 - 3 * x * y * y, 3 * x * x * y - y ** 3, z * (x * x - y * y), x * y * z,
-         x * (4 * z * z - x * x - y * y), y * (4 * z * z - x * x - y * y),
-         z * (2 * z * z - 3 * x * x - 3 * y * y)]
-    gr = [(zr, zr, zr), (o, zr, zr), (zr, o, zr), (zr, zr, o),
-          (y, x, zr), (zr, z, y), (z, zr, x), (2 * x, -2 * y, zr), (-2 * x, -2 * y, 4 * z),
-          (3 * x * x - 3 * y * y, -6 * x * y, zr), (6 * x * y, 3 * x * x - 3 * y * y, zr),
-          (2 * x * z, -2 * y * z, x * x - y * y), (y * z, x * z, x * y),
-          (4 * z * z - 3 * x * x - y * y, -2 * x * y, 8 * x * z),
-          (-2 * x * y, 4 * z * z - x * x - 3 * y * y, 8 * y * z),
-          (-6 * x * z, -6 * y * z, 6 * z * z - 3 * x * x - 3 * y * y)]
-    H = np.stack(h, -1)
-    G = np.stack([np.stack(t, -1) for t in gr], -2)
-    return H, G
-
-
-def _sol_cubic(amps):
-    # u = sum_k a_k h_k over the 16 harmonics of degree <= 3
-    a = np.asarray(amps, dtype=np.float64)
-    u = lambda X: _cubic_harmonics(X)[0] @ a
-    g = lambda X: np.einsum("...kd,k->...d", _cubic_harmonics(X)[1], a)
-    lap = lambda X: np.zeros(X.shape[:-1])
-    return u, g, lap
-
-
 def solutions(w: Workload):
     """(u_in, grad_in, lap_in), (u_out, grad_out, lap_out) of a workload."""
     e = w.exact
@@ -216,8 +184,8 @@ def solutions(w: Workload):
         return _sol_sin_cos(), _sol_exp_sin()
     if e == "exp3_harmonic3":
         return _sol_exp3(), _sol_harmonic3(w.extra["amps"])
-    if e == "cubic_io":
-        return _sol_cubic(w.extra["amps_in"]), _sol_cubic(w.extra["amps_out"])
+    if e == "waves_io":
+        return _sol_waves(w.extra["seed_in"]), _sol_waves(w.extra["seed_out"])
     raise ValueError(f"unknown exact solution {e!r}")
 
 
@@ -279,7 +247,7 @@ def grid_data(w: Workload):
 def _lap_of_f(w: Workload, X, inside: bool):
     """Closed-form Laplacian of the physical f on one side."""
     e = w.exact
-    if e in ("exp_sin", "harmonic3", "cubic_io"):
+    if e in ("exp_sin", "harmonic3", "waves_io"):
         return np.zeros(X.shape[:-1])
     if e == "paper_table1":
         # f = lap u = 2 ca e^x cos(arg); lap(e^x cos(arg)) = 2 e^x * (-ca sin(arg)) + 0
@@ -523,25 +491,56 @@ def warm_start_training_set(seed: int, geometries: int, draws: int):
     return out
 
 
-def cubic_field_amplitudes(seed: int = 5968):
-    """The fixed interior and exterior amplitudes of the learned-start family:
-    two draws of N(0,1)^16 from one seeded generator (interior first)."""
+def wave_field(seed: int, terms: int = 8):
+    """A fixed harmonic field sum_k a_k exp(p_k . x) cos(q_k . x + c_k) with
+    |p_k| = |q_k| and p_k orthogonal to q_k (so each term is harmonic), drawn
+    once from a seeded generator: a_k ~ N(0,1), |p_k| ~ U[0.5, 1.5], directions
+    uniform, c_k ~ U[0, 2 pi).  Returns (P, Q, a, c) of shapes (terms, 3),
+    (terms, 3), (terms,), (terms,)."""
     rng = np.random.default_rng(seed)
-    return rng.standard_normal(16), rng.standard_normal(16)
+    P, Q, A, C = [], [], [], []
+    for _ in range(terms):
+        u = rng.standard_normal(3)
+        u /= np.linalg.norm(u)
+        v = rng.standard_normal(3)
+        v -= (v @ u) * u
+        v /= np.linalg.norm(v)
+        s = rng.uniform(0.5, 1.5)
+        P.append(s * u)
+        Q.append(s * v)
+        A.append(rng.standard_normal())
+        C.append(rng.uniform(0.0, 2.0 * np.pi))
+    return np.array(P), np.array(Q), np.array(A), np.array(C)
 
 
-def cubic_ellipsoid_3d(axes, n: int, contrast: float = 10.0) -> Workload:
+def _sol_waves(seed):
+    P, Q, A, C = wave_field(seed)
+
+    def u(X):
+        return np.exp(X @ P.T) * np.cos(X @ Q.T + C) @ A
+
+    def g(X):
+        e = np.exp(X @ P.T) * A
+        cs = np.cos(X @ Q.T + C)
+        sn = np.sin(X @ Q.T + C)
+        return (e * cs) @ P - (e * sn) @ Q
+
+    lap = lambda X: np.zeros(X.shape[:-1])
+    return u, g, lap
+
+
+def wave_ellipsoid_3d(axes, n: int, contrast: float = 10.0) -> Workload:
     """3D interface problem of the learned start: an ellipsoid with the given
-    axes in [-1, 1]^3, sigma_in/sigma_out = contrast, u_in and u_out fixed sums
-    of the 16 harmonics of degree <= 3 (cubic_field_amplitudes), outer Dirichlet
-    data from u_out.  The geometry varies from problem to problem, the fields
-    do not; the method is not exact for cubic fields, and with u_out != 0 the
-    density [d_n u] is not a multiple of the flux jump g2."""
-    a_in, a_out = cubic_field_amplitudes()
-    return Workload("cubic_ellipsoid_3d", 3, n, -1.0, 1.0, LS_ELLIPSOID,
+    axes in [-1, 1]^3, sigma_in/sigma_out = contrast, u_in and u_out two fixed
+    harmonic fields (wave_field, seeds 5968 and 5969), outer Dirichlet data
+    from u_out.  The geometry varies from problem to problem, the fields do
+    not; the fields are not polynomials (the method is not exact for them),
+    and with u_out != 0 the density [d_n u] is not a multiple of the flux jump
+    g2."""
+    return Workload("wave_ellipsoid_3d", 3, n, -1.0, 1.0, LS_ELLIPSOID,
                     [0.0, 0.0, 0.0, *[float(a) for a in axes]], KIND_INTERFACE_MU,
-                    sigma_in=contrast, sigma_out=1.0, exact="cubic_io",
-                    extra={"amps_in": [float(v) for v in a_in], "amps_out": [float(v) for v in a_out]})
+                    sigma_in=contrast, sigma_out=1.0, exact="waves_io",
+                    extra={"seed_in": 5968, "seed_out": 5969})
 
 
 def ellipsoid_axes(seed: int, count: int):
