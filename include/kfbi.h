@@ -385,6 +385,12 @@ kfbi_status kfbi_warm_start_features(kfbi_problem* p, const kfbi_data* data, con
  * network must take KFBI_WS_FEATURES inputs, have width >= KFBI_WS_FEATURES
  * and share the problem's stream. */
 kfbi_status kfbi_warm_start(kfbi_problem* p, kfbi_mlp* m, const kfbi_data* data, double* x0);
+/* kfbi_warm_start for every instance of a batch with one forward pass of the
+ * network over the DOFs of all instances: data (host array of the batch's
+ * count kfbi_data) and x0s (host array of count device pointers, N_b of
+ * instance k each, written) as in kfbi_gmres_solve_batch.  The network must
+ * share the batch's stream. */
+kfbi_status kfbi_warm_start_batch(kfbi_batch* batch, kfbi_mlp* m, const kfbi_data* data, double* const* x0s);
 
 /* ---- box solve without allocation ----------------------------------------- */
 

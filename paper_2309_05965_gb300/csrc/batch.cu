@@ -151,6 +151,11 @@ static kfbi_status batch_potentials(kfbi_batch* b, const double* const* a, const
   return KFBI_OK;
 }
 
+namespace kfbi {
+int batch_size(const kfbi_batch* b) { return b->n; }
+kfbi_problem* batch_problem(const kfbi_batch* b, int k) { return b->ps[k]; }
+}  // namespace kfbi
+
 static bool has_data(const kfbi_problem* p, const kfbi_data& d) {
   return d.g1 && (p->cfg.kind != KFBI_INTERFACE_MU || d.g2);
 }

@@ -377,5 +377,8 @@ kfbi_status batch_gmres_control(kfbi_problem* p0, const double* res, const doubl
 kfbi_status batch_gmres_finish(kfbi_problem* p0, const ArnDesc* d, const BatchInst* inst, int n, const int* jdev,
                                const int* flags, cudaStream_t st);
 void batch_box_copy_tiles(BatchBox* dst, const BatchBox* src);
+// batch.cu: the instances of a batch
+int batch_size(const kfbi_batch* b);
+kfbi_problem* batch_problem(const kfbi_batch* b, int k);
 
 }  // namespace kfbi

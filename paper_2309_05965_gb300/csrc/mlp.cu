@@ -523,4 +523,44 @@ kfbi_status kfbi_warm_start(kfbi_problem* p, kfbi_mlp* m, const kfbi_data* data,
   return KFBI_OK;
 }
 
+kfbi_status kfbi_warm_start_batch(kfbi_batch* b, kfbi_mlp* m, const kfbi_data* data, double* const* x0s) {
+  if (!b || !m || !data || !x0s) return KFBI_ERR_ARG;
+  const int n = batch_size(b);
+  kfbi_problem* p0 = batch_problem(b, 0);
+  if (m->n_in != KFBI_WS_FEATURES) return fail(p0, KFBI_ERR_ARG, "the network must take KFBI_WS_FEATURES inputs");
+  if (m->stream != p0->stream) return fail(p0, KFBI_ERR_ARG, "network and batch must share a stream");
+  if (m->width < KFBI_WS_FEATURES) return fail(p0, KFBI_ERR_ARG, "the network width must be >= KFBI_WS_FEATURES");
+  std::vector<long long> off(n + 1, 0);
+  for (int k = 0; k < n; ++k) {
+    kfbi_problem* p = batch_problem(b, k);
+    if (!x0s[k] || !data[k].g1) return fail(p0, KFBI_ERR_ARG, "missing data or start for an instance");
+    if (p->nx != p->nb) return fail(p0, KFBI_ERR_UNSUPPORTED, "the learned start predicts one density per DOF");
+    off[k + 1] = off[k] + p->nb;
+  }
+  if (off[n] > INT32_MAX / KFBI_WS_FEATURES) return fail(p0, KFBI_ERR_UNSUPPORTED, "too many DOFs in the batch");
+  const int rows = (int)off[n];
+  {
+    kfbi_status s = ensure(m, rows);
+    if (s != KFBI_OK) return fail(p0, s, m->err);
+  }
+  // every instance's features into one matrix, one normalisation and one
+  // forward pass over all rows, then each instance's densities
+  for (int k = 0; k < n; ++k)
+    KFBI_TRY(kfbi_warm_start_features(batch_problem(b, k), &data[k], nullptr, m->d1 + off[k] * m->n_in, nullptr));
+  const long long tot = (long long)rows * m->n_in;
+  KFBI_LAUNCH(p0, KFBI_KC_OTHER, k_normalise<<<div_up(tot, 256), 256, 0, p0->stream>>>(
+      rows, m->n_in, m->d1, nullptr, m->shift, m->scale, m->X, nullptr, nullptr));
+  {
+    kfbi_status s = forward_rows(m, rows, nullptr);
+    if (s != KFBI_OK) return fail(p0, s, m->err);
+  }
+  for (int k = 0; k < n; ++k) {
+    const int nb = batch_problem(b, k)->nb;
+    KFBI_LAUNCH(p0, KFBI_KC_OTHER, k_to_density<<<div_up(nb, 256), 256, 0, p0->stream>>>(
+        nb, m->y + off[k], m->out_shift, m->out_scale, x0s[k]));
+  }
+  KFBI_CUDA(p0, cudaGetLastError());
+  return KFBI_OK;
+}
+
 }  // extern "C"

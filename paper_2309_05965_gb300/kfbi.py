@@ -107,6 +107,7 @@ SIGNATURES = {
     "kfbi_mlp_set_trainable": [_P, ctypes.c_int],
     "kfbi_warm_start_features": [_P, ctypes.POINTER(Data), _P, _P, _P],
     "kfbi_warm_start": [_P, _P, ctypes.POINTER(Data), _P],
+    "kfbi_warm_start_batch": [_P, _P, _P, _P],
     "kfbi_box_solve_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                ctypes.c_int, ctypes.c_double, _P, _P, _P],
     "kfbi_box_solve_info": [_P, _P, _P, _P, _P],
@@ -476,6 +477,14 @@ class Batch:
 
     def evaluate(self, datas, densities, u_grids):
         kfbi_evaluate_batch(self.handle, [q.handle for q in self.problems], datas, densities, u_grids)
+
+    def warm_start(self, mlp, datas, x0s):
+        """Every instance's start from one forward pass of the network."""
+        n = len(self.problems)
+        darr = (Data * n)(*datas)
+        xarr = (ctypes.c_void_p * n)(*[_ptr(x).value for x in x0s])
+        _check(load().kfbi_warm_start_batch(self.handle, mlp, ctypes.cast(darr, ctypes.c_void_p),
+                                            ctypes.cast(xarr, ctypes.c_void_p)), self.problems[0].handle)
 
     def tiles(self):
         return kfbi_batch_tiles(self.handle)

@@ -126,6 +126,10 @@ class WarmStart:
         """x0 (N_b doubles on the device) = the network's density."""
         kfbi.kfbi_warm_start(problem.handle, self.handle, data, x0)
 
+    def predict_batch(self, batch: "kfbi.Batch", datas, x0s):
+        """The starts of every instance of a batch, one forward pass."""
+        batch.warm_start(self.handle, datas, x0s)
+
     def close(self):
         if self.handle is not None:
             kfbi.kfbi_mlp_destroy(self.handle)

@@ -231,6 +231,11 @@ def test_learned_starts_in_a_batch():
     x0s = [empty(G.nb) for _, G in rows]
     for (w, G), (d, _), x0 in zip(rows, dd, x0s):
         ws.predict(G, d, x0)
+    # one forward pass over every instance's DOFs gives the same starts
+    xb = [empty(G.nb) for _, G in rows]
+    ws.predict_batch(B, [d for d, _ in dd], xb)
+    for a, b in zip(x0s, xb):
+        assert float((a - b).abs().max()) <= 1e-6 * float(a.abs().max())
     xl = [empty(G.nb) for _, G in rows]
     il = B.gmres_solve([d for d, _ in dd], opts, xl, x0s=x0s)
     uz = [empty(G.grid_shape) for _, G in rows]
