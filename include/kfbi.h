@@ -115,6 +115,13 @@ typedef struct {
   int box_max_iters;      /* inner iteration limit (<= 0: 60)                     */
   double kappa_out;       /* general interface problem: kappa_2 of Omega_2 (kappa
                              is then kappa_1 of Omega_1); unused otherwise        */
+  double relax;           /* inexact GMRES (mixed DST box solves only): 0 = every
+                             operator application refined to box_rtol; omega > 0
+                             = before application j inside kfbi_gmres_solve the
+                             refinement stops at max(box_rtol, omega rtol ||b|| /
+                             ||r_j||) (relaxation as the residual falls, after
+                             Simoncini & Szyld 2003); right-hand side, starts,
+                             restarts and evaluation stay at box_rtol           */
 } kfbi_config;
 
 /* Problem data (Sec. 2).  f_* are the physical right-hand sides f of eqs.
@@ -147,6 +154,10 @@ typedef struct {
   double t_ms[8];         /* [0] BIE right-hand side, [1] GMRES loop, [2] total   */
   int x0_rejected;        /* 1 if opts->x0 was given but its residual was not
                              below ||b||, so GMRES started from zero instead    */
+  int refine_steps;       /* mixed DST box solves: the FP32 correction steps run
+                             during the call beyond each box solve's first FP32
+                             solve (both operators for the general kind); 0
+                             otherwise                                          */
 } kfbi_gmres_info;
 
 typedef struct kfbi_problem kfbi_problem;

@@ -51,6 +51,9 @@ struct kfbi_batch {
   int* ctl = nullptr;                  // [iterations, limit, active]
   double* thr = nullptr;
   double* bn = nullptr;
+  double omega = 0.0;                  // inexact GMRES (the first problem's relax)
+  double* tol = nullptr;               // per-instance refinement tolerance of the loop's box solves
+  double* tol_base = nullptr;          // each problem's box_rtol
   double* res_dev = nullptr;
   double* res_host = nullptr;   // pinned
   int* int_host = nullptr;      // pinned: jdev, flags, done, ctl
@@ -70,7 +73,8 @@ static kfbi_status batch_iteration(kfbi_batch* b, cudaStream_t st, cudaGraphCond
   KFBI_TRY(batch_box_solve(p0, b->bb, b->done, st));
   KFBI_TRY(batch_hot_trace(p0, b->bh, st));
   KFBI_TRY(batch_arnoldi_step(p0, b->darn, b->jdev, b->done, b->res_dev, b->n, b->maxnb, b->m, st));
-  return batch_gmres_control(p0, b->res_dev, b->thr, b->done, b->n, b->ctl, cond, use_cond, st);
+  return batch_gmres_control(p0, b->res_dev, b->thr, b->done, b->n, b->ctl, cond, use_cond, b->omega,
+                             b->tol_base, b->tol, st);
 }
 
 // Capture one iteration into `into` (the body of the conditional node) or
@@ -184,6 +188,8 @@ kfbi_status kfbi_destroy_batch(kfbi_batch* b) {
   cudaFree(b->ctl);
   cudaFree(b->thr);
   cudaFree(b->bn);
+  cudaFree(b->tol);
+  cudaFree(b->tol_base);
   cudaFree(b->res_dev);
   if (b->res_host) cudaFreeHost(b->res_host);
   if (b->int_host) cudaFreeHost(b->int_host);
@@ -239,7 +245,19 @@ kfbi_status kfbi_create_batch(kfbi_problem* const* problems, int count, kfbi_bat
   kfbi_status s;
   if ((s = batch_hot_create(p0, b->ps.data(), count, xs.data(), ys.data(), b->rhs_loop.data(), &b->bh)) != KFBI_OK)
     return bail(s);
-  if ((s = batch_box_create(p0, b->ps.data(), count, b->rhs_loop.data(), &b->bb)) != KFBI_OK) return bail(s);
+  // per-instance refinement tolerances of the loop's box solves (each
+  // problem's box_rtol, relaxed inside GMRES when relax > 0)
+  b->omega = p0->cfg.relax;
+  {
+    std::vector<double> base(count);
+    for (int k = 0; k < count; ++k) base[k] = box_tol(b->ps[k]);
+    if (dalloc(&b->tol, count) != cudaSuccess || dalloc(&b->tol_base, count) != cudaSuccess ||
+        cudaMemcpy(b->tol, base.data(), sizeof(double) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->tol_base, base.data(), sizeof(double) * count, cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(fail(p0, KFBI_ERR_CUDA, "out of device memory"));
+  }
+  if ((s = batch_box_create(p0, b->ps.data(), count, b->rhs_loop.data(), &b->bb, b->tol)) != KFBI_OK)
+    return bail(s);
   if ((s = batch_box_create(p0, b->ps.data(), count, rhs_data.data(), &b->bb_data)) != KFBI_OK) return bail(s);
   std::vector<ArnDesc> ad(count);
   for (int k = 0; k < count; ++k) {
@@ -328,6 +346,8 @@ kfbi_status kfbi_gmres_solve_batch(kfbi_batch* b, const kfbi_data* data, const k
     any_x0 = any_x0 || x0;
   }
   KFBI_CUDA(p0, cudaMemcpyAsync(b->dinst, b->hinst, sizeof(BatchInst) * n, cudaMemcpyHostToDevice, st));
+  // the starts' residuals at the full box-solve accuracy
+  KFBI_CUDA(p0, cudaMemcpyAsync(b->tol, b->tol_base, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   if (any_x0) {
     KFBI_CUDA(p0, cudaMemcpyAsync(b->x0_skip, skip, sizeof(int) * n, cudaMemcpyHostToDevice, st));
     for (int k = 0; k < n; ++k)
@@ -339,7 +359,7 @@ kfbi_status kfbi_gmres_solve_batch(kfbi_batch* b, const kfbi_data* data, const k
     KFBI_TRY(batch_hot_trace(p0, b->bh, st));
   }
   KFBI_TRY(batch_gmres_init(p0, b->darn, b->dinst, n, opts->rtol, b->thr, b->bn, b->done, b->jdev, b->flags,
-                            b->res_dev, st));
+                            b->res_dev, b->omega, b->tol_base, b->tol, st));
   const int maxit = std::min(std::min(opts->max_iter, b->m), opts->restart > 0 ? opts->restart : b->m);
   int* hj = b->int_host;
   int* hflags = hj + n;
@@ -391,6 +411,7 @@ kfbi_status kfbi_gmres_solve_batch(kfbi_batch* b, const kfbi_data* data, const k
       infos[k].rel_res = rel;
       for (double& v : infos[k].t_ms) v = 0.0;
       infos[k].x0_rejected = hflags[k] == 2 ? 1 : 0;
+      infos[k].refine_steps = 0;
     }
     if (hbn[k] > 0 && !(rel <= opts->rtol)) status = KFBI_ERR_NOT_CONVERGED;
   }

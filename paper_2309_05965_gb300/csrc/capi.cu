@@ -220,6 +220,10 @@ kfbi_status kfbi_create_problem(const kfbi_config* cfg, const kfbi_levelset* ls,
     fail(p, KFBI_ERR_ARG, "need sigma > 0 and kappa >= 0");
     return bail(KFBI_ERR_ARG);
   }
+  if (!(cfg->relax >= 0.0) || !(cfg->relax <= 1.0)) {
+    fail(p, KFBI_ERR_ARG, "relax must be in [0, 1]");
+    return bail(KFBI_ERR_ARG);
+  }
   if (cfg->box_solver != KFBI_BOX_DST && cfg->box_solver != KFBI_BOX_MG) {
     fail(p, KFBI_ERR_ARG, "unknown box solver");
     return bail(KFBI_ERR_ARG);
@@ -526,8 +530,18 @@ kfbi_status kfbi_gmres_solve(kfbi_problem* p, const kfbi_data* data, const kfbi_
   int it = 0;
   double rel = 0.0;
   int rejected = 0;
+  KFBI_TRY(box_steps_reset(p));
+  if (p->twin) KFBI_TRY(box_steps_reset(p->twin));
+  KFBI_TRY(box_tol_reset(p));
+  if (p->twin) KFBI_TRY(box_tol_reset(p->twin));
   kfbi_status s = gmres_run(p, p->bvec, opts->x0, opts->rtol, opts->restart > 0 ? opts->restart : 100,
                             opts->max_iter, density, &it, &rel, &rejected);
+  // every later box solve (the evaluation) at the full accuracy again
+  KFBI_TRY(box_tol_reset(p));
+  if (p->twin) KFBI_TRY(box_tol_reset(p->twin));
+  long long steps = 0, steps2 = 0;
+  KFBI_TRY(box_steps_total(p, &steps));
+  if (p->twin) KFBI_TRY(box_steps_total(p->twin, &steps2));
   auto t2 = std::chrono::steady_clock::now();
   if (info) {
     info->iters = it;
@@ -537,6 +551,7 @@ kfbi_status kfbi_gmres_solve(kfbi_problem* p, const kfbi_data* data, const kfbi_
     info->t_ms[1] = std::chrono::duration<double, std::milli>(t2 - t1).count();
     info->t_ms[2] = std::chrono::duration<double, std::milli>(t2 - t0).count();
     info->x0_rejected = rejected;
+    info->refine_steps = (int)(steps + steps2);
   }
   return s;
 }

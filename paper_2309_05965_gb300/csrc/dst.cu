@@ -58,6 +58,9 @@ struct BoxSolver {
   float* work32 = nullptr;    // grid of floats
   double* res = nullptr;      // FP64 residual grid
   unsigned long long* nrm = nullptr;   // [0] max|R| [1] max|r| [2] last max|delta| [3] max|delta| [4] max|u| [5] last max|u|
+                                       // [6] correction steps of the last solve, [7] of all solves since reset,
+                                       // [8] relative size of the last first correction (FP32 error estimate)
+  double* tol_dev = nullptr;  // the refinement tolerance the checks read (relaxed inside GMRES)
   int* conv = nullptr;        // device flag
   int refine_steps = 4;
   double tol = 1e-13;
@@ -921,19 +924,36 @@ __global__ void __launch_bounds__(128) k_dst32_batched(const PassArgs* __restric
   }
 }
 
-__device__ __forceinline__ void check_body(unsigned long long* nrm, double tol, int* conv) {
+// The check after refinement step `step` (0: the first FP32 solve): stop when
+// the last correction max|delta| <= tol max|u|.  After the first solve there
+// is no correction yet; it stops there only when ten times the relative size
+// of the first correction observed in an earlier solve on this grid (nrm[8],
+// an estimate of the FP32 solve's error, 1 until one is observed) is within
+// tol, which a relaxed GMRES tolerance can reach.  The first correction of
+// every solve updates that estimate.
+__device__ __forceinline__ void check_body(unsigned long long* nrm, const double* tolp, int* conv, int step) {
+  const double tol = tolp[0];
   if (*conv) return;
   double dm = __longlong_as_double((long long)nrm[3]);
   double um = __longlong_as_double((long long)nrm[4]);
   nrm[2] = nrm[3];
   nrm[5] = nrm[4];
-  if (dm <= tol * um) *conv = 1;
-  else nrm[6] += 1ull;   // one more refinement step will run
+  bool stop = dm <= tol * um;
+  if (step == 0 && 10.0 * __longlong_as_double((long long)nrm[8]) <= tol) stop = true;
+  if (step == 1 && um > 0.0) nrm[8] = (unsigned long long)__double_as_longlong(dm / um);
+  if (stop) {
+    *conv = 1;
+  } else {
+    nrm[6] += 1ull;   // one more refinement step will run
+    nrm[7] += 1ull;
+  }
   nrm[3] = 0ull;
   nrm[4] = 0ull;
 }
 
-__global__ void k_check(unsigned long long* nrm, double tol, int* conv) { check_body(nrm, tol, conv); }
+__global__ void k_check(unsigned long long* nrm, const double* tol, int* conv, int step) {
+  check_body(nrm, tol, conv, step);
+}
 
 
 // ---- exact residual of the mixed path (fixed point) -------------------------
@@ -980,9 +1000,9 @@ __global__ void k_fix_scale(const unsigned long long* __restrict__ umax, double 
 }
 
 // the check after the first FP32 solve and the fixed-point scale from its max|u|
-__global__ void k_check_scale(unsigned long long* nrm, double tol, int* conv, double multh2, double kc,
+__global__ void k_check_scale(unsigned long long* nrm, const double* tol, int* conv, double multh2, double kc,
                               double* __restrict__ fixd, float* __restrict__ fixf) {
-  check_body(nrm, tol, conv);
+  check_body(nrm, tol, conv, 0);
   fix_scale_body(nrm + 5, multh2, kc, fixd, fixf);
 }
 
@@ -1556,9 +1576,17 @@ kfbi_status box_create(kfbi_problem* p) {
     KFBI_CUDA(p, cudaGetLastError());
     KFBI_CUDA(p, cudaDeviceSynchronize());
   }
-  KFBI_CUDA(p, dalloc(&B->nrm, 7));
+  KFBI_CUDA(p, dalloc(&B->nrm, 9));
+  {
+    unsigned long long init[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const double one = 1.0;   // no FP32 error estimate yet
+    memcpy(&init[8], &one, sizeof(one));
+    KFBI_CUDA(p, cudaMemcpy(B->nrm, init, sizeof(init), cudaMemcpyHostToDevice));
+  }
   KFBI_CUDA(p, dalloc(&B->conv, 1));
+  KFBI_CUDA(p, dalloc(&B->tol_dev, 1));
   B->tol = p->cfg.box_rtol > 0 ? p->cfg.box_rtol : 1e-13;
+  KFBI_CUDA(p, cudaMemcpy(B->tol_dev, &B->tol, sizeof(double), cudaMemcpyHostToDevice));
   B->refine_steps = p->cfg.box_max_iters > 0 ? std::min(p->cfg.box_max_iters, 8) : 5;
   int dev = 0, optin = 0;
   KFBI_CUDA(p, cudaGetDevice(&dev));
@@ -1614,8 +1642,39 @@ void box_destroy(kfbi_problem* p) {
   cudaFree(B->fixf);
   cudaFree(B->nrm);
   cudaFree(B->conv);
+  cudaFree(B->tol_dev);
   delete B;
   p->box = nullptr;
+}
+
+namespace {
+__global__ void k_set_double(double* __restrict__ p, double v) { *p = v; }
+}  // namespace
+
+// The refinement tolerance of the mixed sine-transform solve as the checks
+// read it (device); null for the FP64 transform and the multigrid.
+double* box_tol_dev(kfbi_problem* p) {
+  return (p->box && !p->mg && p->cfg.precision == KFBI_MIXED) ? p->box->tol_dev : nullptr;
+}
+double box_tol(const kfbi_problem* p) { return p->box ? p->box->tol : 0.0; }
+kfbi_status box_tol_reset(kfbi_problem* p) {
+  double* t = box_tol_dev(p);
+  if (t) KFBI_LAUNCH(p, KFBI_KC_OTHER, k_set_double<<<1, 1, 0, p->stream>>>(t, p->box->tol));
+  return KFBI_OK;
+}
+// correction steps run by the mixed sine-transform solves since the reset
+kfbi_status box_steps_reset(kfbi_problem* p) {
+  if (box_tol_dev(p)) KFBI_CUDA(p, cudaMemsetAsync(p->box->nrm + 7, 0, sizeof(unsigned long long), p->stream));
+  return KFBI_OK;
+}
+kfbi_status box_steps_total(kfbi_problem* p, long long* out) {
+  *out = 0;
+  if (!box_tol_dev(p)) return KFBI_OK;
+  unsigned long long c = 0;
+  KFBI_CUDA(p, cudaMemcpyAsync(&c, p->box->nrm + 7, sizeof(c), cudaMemcpyDeviceToHost, p->stream));
+  KFBI_CUDA(p, cudaStreamSynchronize(p->stream));
+  *out = (long long)c;
+  return KFBI_OK;
 }
 
 kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u) {
@@ -1651,7 +1710,7 @@ kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u) {
     last.corr_max = B->nrm + 3;
     for (int k = 0; k < P0.npass; ++k) launch_pass<float>(p, P0.args[k], P0.npairs, P0.na, st, P0.pmin[k]);
   }
-  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_check_scale<<<1, 1, 0, st>>>(B->nrm, B->tol, B->conv, B->multh2, B->kc,
+  KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_check_scale<<<1, 1, 0, st>>>(B->nrm, B->tol_dev, B->conv, B->multh2, B->kc,
                                                                       B->fixd, B->fixf));
   KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_fix0<<<eb, 256, 0, st>>>(nodes, B->work32, rhs, g, B->fixd, B->fixf,
                                                                  B->ufix, B->rfix,
@@ -1676,7 +1735,7 @@ kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u) {
     const PassPlan& P = it + 1 < B->refine_steps ? PK : PL;
     for (int k = 0; k < P.npass; ++k) launch_pass<float>(p, P.args[k], P.npairs, P.na, st, P.pmin[k]);
     if (it + 1 < B->refine_steps)
-      KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_check<<<1, 1, 0, st>>>(B->nrm, B->tol, B->conv));
+      KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_check<<<1, 1, 0, st>>>(B->nrm, B->tol_dev, B->conv, it));
   }
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
@@ -2001,6 +2060,7 @@ struct BoxDesc {
   float* fixf;
   unsigned long long* nrm;
   int* conv;
+  const double* tolp;      // per-instance refinement tolerance on the device (null: tol)
 };
 
 __device__ __forceinline__ int find_inst(const int* start, int ninst, int item) {
@@ -2021,16 +2081,22 @@ __global__ void k_zero_batched(const BoxDesc* __restrict__ D, int ninst, const i
   *D[i].conv = done ? done[i] : 0;
 }
 
-__global__ void k_check_batched(const BoxDesc* __restrict__ D, int ninst) {
+// the batched check after refinement step `step`, with the rules of
+// check_body (the first FP32 solve stops on the observed error estimate)
+__global__ void k_check_batched(const BoxDesc* __restrict__ D, int ninst, int step) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ninst) return;
   unsigned long long* nrm = D[i].nrm;
   if (*D[i].conv) return;
+  const double tol = D[i].tolp ? D[i].tolp[0] : D[i].tol;
   const double dm = __longlong_as_double((long long)nrm[3]);
   const double um = __longlong_as_double((long long)nrm[4]);
   nrm[2] = nrm[3];
   nrm[5] = nrm[4];
-  if (dm <= D[i].tol * um) *D[i].conv = 1;
+  bool stop = dm <= tol * um;
+  if (step == 0 && 10.0 * __longlong_as_double((long long)nrm[8]) <= tol) stop = true;
+  if (step == 1 && um > 0.0) nrm[8] = (unsigned long long)__double_as_longlong(dm / um);
+  if (stop) *D[i].conv = 1;
   nrm[3] = 0ull;
   nrm[4] = 0ull;
 }
@@ -2103,7 +2169,7 @@ void batch_box_copy_tiles(BatchBox* dst, const BatchBox* src) {
 }
 
 kfbi_status batch_box_create(kfbi_problem* p0, kfbi_problem* const* ps, int ninst,
-                             double* const* rhs, BatchBox** out) {
+                             double* const* rhs, BatchBox** out, const double* tol_dev) {
   BatchBox* bb = new BatchBox();
   *out = bb;
   bb->ninst = ninst;
@@ -2142,7 +2208,8 @@ kfbi_status batch_box_create(kfbi_problem* p0, kfbi_problem* const* ps, int nins
     const int n1 = p->g.n + 1;
     rstart[i + 1] = rstart[i] + (d == 2 ? n1 : n1 * n1);
     box[i] = BoxDesc{p->g, FixStencil{B->w[0], B->w[1], B->w[2], B->w[3], B->kA, B->kB}, B->multh2, B->kc, B->tol,
-                     rhs[i], p->ugrid, B->work32, B->ufix, B->rfix, r32, B->fixd, B->fixf, B->nrm, B->conv};
+                     rhs[i], p->ugrid, B->work32, B->ufix, B->rfix, r32, B->fixd, B->fixf, B->nrm, B->conv,
+                     tol_dev ? tol_dev + i : nullptr};
   }
   bb->steps = 0;
   for (int i = 0; i < ninst; ++i) bb->steps = std::max(bb->steps, ps[i]->box->refine_steps);
@@ -2266,7 +2333,7 @@ kfbi_status batch_box_solve(kfbi_problem* p0, BatchBox* bb, const int* done, cud
   for (int v = 0; v < bb->npass; ++v)
     KFBI_LAUNCH(p0, KFBI_KC_DST, k_dst32_batched<<<bb->grid, 128, smem, st>>>(bb->dargs + (size_t)v * ni,
                                                                                bb->dstart, ni));
-  KFBI_LAUNCH(p0, KFBI_KC_RESIDUAL, k_check_batched<<<cb, 128, 0, st>>>(bb->dbox, ni));
+  KFBI_LAUNCH(p0, KFBI_KC_RESIDUAL, k_check_batched<<<cb, 128, 0, st>>>(bb->dbox, ni, 0));
   KFBI_LAUNCH(p0, KFBI_KC_RESIDUAL, k_fix_scale_batched<<<cb, 128, 0, st>>>(bb->dbox, ni));
   KFBI_LAUNCH(p0, KFBI_KC_RESIDUAL, k_rows_batched<<<bb->rgrid, 128, 0, st>>>(bb->dbox, bb->drstart, ni, 0));
   for (int it = 1; it < bb->steps; ++it) {
@@ -2274,7 +2341,7 @@ kfbi_status batch_box_solve(kfbi_problem* p0, BatchBox* bb, const int* done, cud
     for (int v = 0; v < bb->npass; ++v)
       KFBI_LAUNCH(p0, KFBI_KC_DST, k_dst32_batched<<<bb->grid, 128, smem, st>>>(
           bb->dargs + (size_t)(bb->npass + v) * ni, bb->dstart, ni));
-    KFBI_LAUNCH(p0, KFBI_KC_RESIDUAL, k_check_batched<<<cb, 128, 0, st>>>(bb->dbox, ni));
+    KFBI_LAUNCH(p0, KFBI_KC_RESIDUAL, k_check_batched<<<cb, 128, 0, st>>>(bb->dbox, ni, it));
   }
   KFBI_LAUNCH(p0, KFBI_KC_RESIDUAL, k_rows_batched<<<bb->rgrid, 128, 0, st>>>(bb->dbox, bb->drstart, ni, 2));
   KFBI_CUDA(p0, cudaGetLastError());

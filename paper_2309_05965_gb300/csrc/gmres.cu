@@ -355,6 +355,20 @@ __global__ void k_cgs_finish(double* __restrict__ H, int ld, double* __restrict_
   if (use_cond) cudaGraphSetConditional(cond, (res[0] > thr[0] && j + 1 < jdev[2]) ? 1u : 0u);
 }
 
+// Inexact GMRES (relaxation of the operator's accuracy as the residual
+// falls, after Simoncini & Szyld 2003 and Bouras & Fraysse 2005): before
+// operator application j the refinement tolerance of the mixed box solves
+// becomes max(base, omega rtol ||b|| / ||r_j||), with thr = rtol ||b|| and
+// res = ||r_j|| the current estimate.  While GMRES runs, res > thr, so the
+// tolerance stays below omega.
+__global__ void k_relax_tol(const double* __restrict__ thr, const double* __restrict__ res, double omega,
+                            double base, double* __restrict__ t1, double* __restrict__ t2) {
+  double t = omega * thr[0] / res[0];
+  if (!(t > base)) t = base;
+  if (t1) *t1 = t;
+  if (t2) *t2 = t;
+}
+
 // V_j *= scal (j already advanced)
 __global__ void k_cgs_normalize(double* __restrict__ V, int nb, const int* __restrict__ jdev,
                                 const double* __restrict__ scal) {
@@ -365,6 +379,19 @@ __global__ void k_cgs_normalize(double* __restrict__ V, int nb, const int* __res
 }
 
 }  // namespace
+
+// The relaxed refinement tolerance before an operator application inside
+// GMRES (k_relax_tol), for the problem and its twin; nothing when relax = 0.
+kfbi_status relax_box_tol(kfbi_problem* p) {
+  if (!(p->cfg.relax > 0)) return KFBI_OK;
+  Gmres& G = p->gm;
+  double* t1 = box_tol_dev(p);
+  double* t2 = p->twin ? box_tol_dev(p->twin) : nullptr;
+  if (t1 || t2)
+    KFBI_LAUNCH(p, KFBI_KC_GMRES, k_relax_tol<<<1, 1, 0, p->stream>>>(G.scal + 5, G.scal + 2, p->cfg.relax,
+                                                                       box_tol(p), t1, t2));
+  return KFBI_OK;
+}
 
 namespace {
 
@@ -386,11 +413,20 @@ __device__ double cta_sum(double v, double* ws) {
 // when ||r0|| < ||b|| (finite), else the zero start (the single solve's rule);
 // V_0 = r/||r||, g = (||r||, 0, ...), threshold rtol ||b||; an instance whose
 // start already meets it (or is not finite) is marked done.
+// The refinement tolerance of instance k's box solves before its next
+// iteration: relaxed as in the single solve (k_relax_tol), base when omega = 0.
+__device__ __forceinline__ double relaxed_tol(double omega, double base, double thr, double res) {
+  double t = omega * thr / res;
+  return omega > 0.0 && t > base ? t : base;
+}
+
 __global__ void __launch_bounds__(kBatchThreads) k_batch_init(const ArnDesc* __restrict__ D,
                                                              const BatchInst* __restrict__ I, double rtol,
                                                              double* __restrict__ thr, double* __restrict__ bn,
                                                              int* __restrict__ done, int* __restrict__ jdev,
-                                                             int* __restrict__ flags, double* __restrict__ res_out) {
+                                                             int* __restrict__ flags, double* __restrict__ res_out,
+                                                             double omega, const double* __restrict__ base_tol,
+                                                             double* __restrict__ tol) {
   __shared__ double ws[kBatchThreads / 32];
   __shared__ double sc[2];
   const int k = blockIdx.x;
@@ -428,6 +464,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_init(const ArnDesc* __r
     jdev[k] = 0;
     a.res[0] = beta;
     res_out[k] = beta;
+    if (tol) tol[k] = relaxed_tol(omega, base_tol[k], t, beta);
   }
 }
 
@@ -439,13 +476,19 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_control(const double* _
                                                                 const double* __restrict__ thr,
                                                                 int* __restrict__ done, int n,
                                                                 int* __restrict__ ctl,
-                                                                cudaGraphConditionalHandle cond, int use_cond) {
+                                                                cudaGraphConditionalHandle cond, int use_cond,
+                                                                double omega, const double* __restrict__ base_tol,
+                                                                double* __restrict__ tol) {
   __shared__ int wa[kBatchThreads / 32];
   int active = 0;
   for (int k = threadIdx.x; k < n; k += kBatchThreads) {
     if (done[k]) continue;
-    if (res[k] > thr[k]) ++active;
-    else done[k] = 1;
+    if (res[k] > thr[k]) {
+      ++active;
+      if (tol) tol[k] = relaxed_tol(omega, base_tol[k], thr[k], res[k]);
+    } else {
+      done[k] = 1;
+    }
   }
   for (int o = 16; o > 0; o >>= 1) active += __shfl_xor_sync(0xffffffffu, active, o);
   if ((threadIdx.x & 31) == 0) wa[threadIdx.x >> 5] = active;
@@ -489,17 +532,18 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_finish(const ArnDesc* _
 
 kfbi_status batch_gmres_init(kfbi_problem* p0, const ArnDesc* d, const BatchInst* inst, int n, double rtol,
                              double* thr, double* bn, int* done, int* jdev, int* flags, double* res_out,
-                             cudaStream_t st) {
+                             double omega, const double* base_tol, double* tol, cudaStream_t st) {
   KFBI_LAUNCH(p0, KFBI_KC_GMRES, k_batch_init<<<n, kBatchThreads, 0, st>>>(d, inst, rtol, thr, bn, done, jdev,
-                                                                            flags, res_out));
+                                                                            flags, res_out, omega, base_tol, tol));
   KFBI_CUDA(p0, cudaGetLastError());
   return KFBI_OK;
 }
 
 kfbi_status batch_gmres_control(kfbi_problem* p0, const double* res, const double* thr, int* done, int n, int* ctl,
-                                cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st) {
+                                cudaGraphConditionalHandle cond, int use_cond, double omega,
+                                const double* base_tol, double* tol, cudaStream_t st) {
   KFBI_LAUNCH(p0, KFBI_KC_GMRES, k_batch_control<<<1, kBatchThreads, 0, st>>>(res, thr, done, n, ctl, cond,
-                                                                               use_cond));
+                                                                               use_cond, omega, base_tol, tol));
   KFBI_CUDA(p0, cudaGetLastError());
   return KFBI_OK;
 }
@@ -632,6 +676,7 @@ static kfbi_status iteration_body(kfbi_problem* p, cudaGraphConditionalHandle co
   const ArnDesc* d = static_cast<const ArnDesc*>(G.desc);
   const int* done = G.jdev + 1;
   KFBI_TRY(batch_arnoldi_copy_in(p, d, G.jdev, done, 1, nb, p->stream));
+  KFBI_TRY(relax_box_tol(p));
   KFBI_TRY(apply_operator_impl(p, p->xbuf, p->ybuf));
   cudaStream_t cs = p->stream;
   KFBI_LAUNCH(p, KFBI_KC_GMRES, k_copy_out_batched<<<dim3(div_up(nb, 256), 1), 256, 0, cs>>>(d, G.jdev, done));
@@ -783,6 +828,9 @@ kfbi_status gmres_run(kfbi_problem* p, const double* b, const double* x0, double
   for (;;) {
     double* V0 = G.V;
     if (nonzero_x) {
+      // the residual of a start or a restart at the full box-solve accuracy
+      KFBI_TRY(box_tol_reset(p));
+      if (p->twin) KFBI_TRY(box_tol_reset(p->twin));
       KFBI_TRY(apply_operator_fast(p, x, V0));
       KFBI_LAUNCH(p, KFBI_KC_GMRES, k_sub<<<eb, 256, 0, st>>>(b, V0, nb));
     } else {
@@ -807,6 +855,13 @@ kfbi_status gmres_run(kfbi_problem* p, const double* b, const double* x0, double
     }
     KFBI_LAUNCH(p, KFBI_KC_GMRES, k_scale<<<eb, 256, 0, st>>>(V0, nb, beta, 1));
     KFBI_LAUNCH(p, KFBI_KC_GMRES, k_init_g<<<1, 128, 0, st>>>(G.g, G.m, beta));
+    // the residual estimate starts at beta and the threshold is rtol ||b||
+    // (both read on the device by the loop and by the relaxation)
+    {
+      const double thr0 = rtol * bnorm;
+      KFBI_CUDA(p, cudaMemcpyAsync(res, beta, sizeof(double), cudaMemcpyDeviceToDevice, st));
+      KFBI_CUDA(p, cudaMemcpyAsync(G.scal + 5, &thr0, sizeof(double), cudaMemcpyHostToDevice, st));
+    }
     int jend = 0;
     double hres = hbeta;
     const bool graph_it = nb <= kGraphArnoldi && p->use_graphs && !p->prof.on;
@@ -846,6 +901,7 @@ kfbi_status gmres_run(kfbi_problem* p, const double* b, const double* x0, double
         if (hres <= rtol * bnorm || total >= max_iter) break;
         continue;
       }
+      KFBI_TRY(relax_box_tol(p));
       KFBI_TRY(apply_operator_fast(p, Vj, w));
       ++total;
       if (nb <= kSmallArnoldi) {

@@ -305,6 +305,11 @@ void box_destroy(kfbi_problem* p);
 kfbi_status box_solve(kfbi_problem* p, const double* rhs, double* u);
 kfbi_status box_last_residual(kfbi_problem* p, double* rel, int* converged);
 kfbi_status box_steps(kfbi_problem* p, int* steps, int* cycles);
+double* box_tol_dev(kfbi_problem* p);
+double box_tol(const kfbi_problem* p);
+kfbi_status box_tol_reset(kfbi_problem* p);
+kfbi_status box_steps_reset(kfbi_problem* p);
+kfbi_status box_steps_total(kfbi_problem* p, long long* out);
 // exact fixed-point refinement state (dst.cu), used by the mixed multigrid
 struct FixState;
 kfbi_status fix_create(kfbi_problem* p, FixState** out);
@@ -352,7 +357,7 @@ struct BatchBox;
 struct BatchHot;
 // dst.cu
 kfbi_status batch_box_create(kfbi_problem* p0, kfbi_problem* const* ps, int ninst,
-                             double* const* rhs, BatchBox** out);
+                             double* const* rhs, BatchBox** out, const double* tol_dev = nullptr);
 void batch_box_destroy(BatchBox* bb);
 kfbi_status batch_box_autotune(kfbi_problem* p0, BatchBox* bb, kfbi_problem* const* ps, double* const* rhs,
                                const int* done, cudaStream_t st);
@@ -371,9 +376,10 @@ kfbi_status batch_arnoldi_step(kfbi_problem* p0, const ArnDesc* d, int* jdev, co
                                double* res_out, int ninst, int maxnb, int m, cudaStream_t st);
 kfbi_status batch_gmres_init(kfbi_problem* p0, const ArnDesc* d, const BatchInst* inst, int n, double rtol,
                              double* thr, double* bn, int* done, int* jdev, int* flags, double* res_out,
-                             cudaStream_t st);
+                             double omega, const double* base_tol, double* tol, cudaStream_t st);
 kfbi_status batch_gmres_control(kfbi_problem* p0, const double* res, const double* thr, int* done, int n, int* ctl,
-                                cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
+                                cudaGraphConditionalHandle cond, int use_cond, double omega,
+                                const double* base_tol, double* tol, cudaStream_t st);
 kfbi_status batch_gmres_finish(kfbi_problem* p0, const ArnDesc* d, const BatchInst* inst, int n, const int* jdev,
                                const int* flags, cudaStream_t st);
 void batch_box_copy_tiles(BatchBox* dst, const BatchBox* src);

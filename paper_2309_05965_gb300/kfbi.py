@@ -47,7 +47,7 @@ class Config(ctypes.Structure):
                 ("kappa", ctypes.c_double), ("box_solver", ctypes.c_int),
                 ("precision", ctypes.c_int), ("cos_alpha", ctypes.c_double),
                 ("box_rtol", ctypes.c_double), ("box_max_iters", ctypes.c_int),
-                ("kappa_out", ctypes.c_double)]
+                ("kappa_out", ctypes.c_double), ("relax", ctypes.c_double)]
 
 
 class Data(ctypes.Structure):
@@ -62,7 +62,8 @@ class GmresOpts(ctypes.Structure):
 
 class GmresInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("rel_res", ctypes.c_double),
-                ("t_ms", ctypes.c_double * 8), ("x0_rejected", ctypes.c_int)]
+                ("t_ms", ctypes.c_double * 8), ("x0_rejected", ctypes.c_int),
+                ("refine_steps", ctypes.c_int)]
 
 
 # name -> (argtypes) ; all return kfbi_status except kfbi_last_error
@@ -417,11 +418,12 @@ class Problem:
 
     def __init__(self, dim, n, lo, hi, ls_kind, ls_params, kind, sigma_in=1.0, sigma_out=1.0,
                  kappa=0.0, order=4, box_solver=BOX_DST, precision=FP64, cos_alpha=0.0,
-                 box_rtol=0.0, box_max_iters=0, stream=None, kappa_out=0.0, ls_samples=None):
+                 box_rtol=0.0, box_max_iters=0, stream=None, kappa_out=0.0, ls_samples=None,
+                 relax=0.0):
         cfg = Config(dim=dim, n=n, lo=lo, hi=hi, order=order, kind=kind, sigma_in=sigma_in,
                      sigma_out=sigma_out, kappa=kappa, box_solver=box_solver,
                      precision=precision, cos_alpha=cos_alpha, box_rtol=box_rtol,
-                     box_max_iters=box_max_iters, kappa_out=kappa_out)
+                     box_max_iters=box_max_iters, kappa_out=kappa_out, relax=relax)
         ls = LevelSet(kind=ls_kind, n_params=len(ls_params))
         for i, v in enumerate(ls_params):
             ls.p[i] = float(v)

@@ -245,3 +245,41 @@ def test_batch_evaluate_matches_single_evaluate():
         inner[tuple(slice(1, w.n) for _ in range(w.dim))] = True
         assert np.abs(host(u) - ex)[inner].max() < 1e-3
     B.close()
+
+
+def test_batch_relaxed_refinement():
+    """Inexact GMRES in the batch (relax = 0.1): every instance's density
+    still solves the oracle's FP64 system to 10 rtol plus the measured
+    operator term, and its error against the exact solution stays within
+    1.1x of the same batch without relaxation."""
+    from paper_2309_05965_gb300 import kfbi
+    from tests.gpu_util import dev
+    rows = _setup()
+    opts = kfbi.GmresOpts(rtol=1e-8, restart=100, max_iter=100, x0=None)
+    errs = {}
+    for relax in (0.0, 0.1):
+        gs = [kfbi.Problem.from_workload(r["w"], precision=kfbi.MIXED, relax=relax) for r in rows]
+        B = kfbi.Batch(gs)
+        dens = [empty(G.nb) for G in gs]
+        B.gmres_solve([r["d"] for r in rows], opts, dens)
+        us = [empty(G.grid_shape) for G in gs]
+        B.evaluate([r["d"] for r in rows], dens, us)
+        errs[relax] = []
+        for r, G, x, u in zip(rows, gs, dens, us):
+            P = r["P"]
+            xb = host(x)
+            b_ref = P.bie_rhs(r["g1"], r["g2"], r["data"])
+            Ao_x = P.apply(xb)
+            Am_x = empty(G.nb)
+            kfbi.kfbi_apply_operator(G.handle, dev(xb), Am_x)
+            bn = np.linalg.norm(b_ref)
+            op_diff = np.linalg.norm(host(Am_x) - Ao_x) / bn
+            res = np.linalg.norm(b_ref - Ao_x) / bn
+            assert res <= 10 * 1e-8 + 2.0 * op_diff, (r["w"].name, relax, res, op_diff)
+            ex = W.exact_grid(r["w"], P.inside)
+            errs[relax].append(np.abs(host(u) - ex)[1:-1, 1:-1].max())
+        B.close()
+        for G in gs:
+            G.close()
+    for e1, e0 in zip(errs[0.1], errs[0.0]):
+        assert e1 <= 1.1 * e0, (e1, e0)
