@@ -665,7 +665,7 @@ def threed_leg(args, stream, flush):
         t0 = time.perf_counter()
         G = kfbi.Problem.from_workload(w, box_solver=box, precision=prec,
                                        box_max_iters=args.box_steps if prec == kfbi.MIXED else 0,
-                                       relax=args.relax_3d if (prec == kfbi.MIXED and box == kfbi.BOX_DST) else 0.0)
+                                       relax=args.relax_3d if prec == kfbi.MIXED else 0.0)
         torch.cuda.synchronize()
         setup = time.perf_counter() - t0
         xyz = torch.zeros((G.nb, 3), dtype=torch.float64, device="cuda")

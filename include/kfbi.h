@@ -115,9 +115,10 @@ typedef struct {
   int box_max_iters;      /* inner iteration limit (<= 0: 60)                     */
   double kappa_out;       /* general interface problem: kappa_2 of Omega_2 (kappa
                              is then kappa_1 of Omega_1); unused otherwise        */
-  double relax;           /* inexact GMRES (mixed DST box solves only): 0 = every
-                             operator application refined to box_rtol; omega > 0
-                             = before application j inside kfbi_gmres_solve the
+  double relax;           /* inexact GMRES (mixed-precision box solves, sine
+                             transform or multigrid): 0 = every operator
+                             application refined to box_rtol; omega in (0, 1] =
+                             before application j inside kfbi_gmres_solve the
                              refinement stops at max(box_rtol, omega rtol ||b|| /
                              ||r_j||) (relaxation as the residual falls, after
                              Simoncini & Szyld 2003); right-hand side, starts,

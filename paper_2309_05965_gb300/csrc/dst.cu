@@ -1653,23 +1653,31 @@ __global__ void k_set_double(double* __restrict__ p, double v) { *p = v; }
 
 // The refinement tolerance of the mixed sine-transform solve as the checks
 // read it (device); null for the FP64 transform and the multigrid.
+double* mg_tol_dev(kfbi_problem* p);
+double mg_tol(const kfbi_problem* p);
+
 double* box_tol_dev(kfbi_problem* p) {
-  return (p->box && !p->mg && p->cfg.precision == KFBI_MIXED) ? p->box->tol_dev : nullptr;
+  if (p->mg) return mg_tol_dev(p);
+  return (p->box && p->cfg.precision == KFBI_MIXED) ? p->box->tol_dev : nullptr;
 }
-double box_tol(const kfbi_problem* p) { return p->box ? p->box->tol : 0.0; }
+double box_tol(const kfbi_problem* p) {
+  if (p->mg) return mg_tol(p);
+  return p->box ? p->box->tol : 0.0;
+}
 kfbi_status box_tol_reset(kfbi_problem* p) {
   double* t = box_tol_dev(p);
-  if (t) KFBI_LAUNCH(p, KFBI_KC_OTHER, k_set_double<<<1, 1, 0, p->stream>>>(t, p->box->tol));
+  if (t) KFBI_LAUNCH(p, KFBI_KC_OTHER, k_set_double<<<1, 1, 0, p->stream>>>(t, box_tol(p)));
   return KFBI_OK;
 }
 // correction steps run by the mixed sine-transform solves since the reset
 kfbi_status box_steps_reset(kfbi_problem* p) {
-  if (box_tol_dev(p)) KFBI_CUDA(p, cudaMemsetAsync(p->box->nrm + 7, 0, sizeof(unsigned long long), p->stream));
+  if (box_tol_dev(p) && !p->mg)
+    KFBI_CUDA(p, cudaMemsetAsync(p->box->nrm + 7, 0, sizeof(unsigned long long), p->stream));
   return KFBI_OK;
 }
 kfbi_status box_steps_total(kfbi_problem* p, long long* out) {
   *out = 0;
-  if (!box_tol_dev(p)) return KFBI_OK;
+  if (!box_tol_dev(p) || p->mg) return KFBI_OK;
   unsigned long long c = 0;
   KFBI_CUDA(p, cudaMemcpyAsync(&c, p->box->nrm + 7, sizeof(c), cudaMemcpyDeviceToHost, p->stream));
   KFBI_CUDA(p, cudaStreamSynchronize(p->stream));

@@ -562,7 +562,8 @@ __global__ void k_to_float(long long tot, const double* __restrict__ a, float* _
 
 // mixed: conv = (max|e_k| <= tol max|u|), the FP32 cycles contract the error by
 // orders of magnitude per outer step, so the last correction bounds the error
-__global__ void k_mg_check_corr(unsigned long long* nrm, double tol, int* conv) {
+__global__ void k_mg_check_corr(unsigned long long* nrm, const double* tolp, int* conv) {
+  const double tol = tolp[0];
   if (*conv) return;
   double em = __longlong_as_double((long long)nrm[6]);
   double um = __longlong_as_double((long long)nrm[7]);
@@ -650,6 +651,7 @@ struct MgSolver {
   int inner_cycles = 4;
   int outer_max = 6;
   double tol = 1e-13;
+  double* tol_dev = nullptr;   // mixed: the outer-step tolerance the check reads (relaxed in GMRES)
   double anorm = 0.0;          // ||A_h||_inf = sum of |stencil coefficients|
 };
 
@@ -882,10 +884,19 @@ kfbi_status mg_create(kfbi_problem* p) {
   }
   KFBI_CUDA(p, dalloc(&M->nrm, 11));
   KFBI_CUDA(p, dalloc(&M->conv, 1));
+  KFBI_CUDA(p, dalloc(&M->tol_dev, 1));
+  KFBI_CUDA(p, cudaMemcpy(M->tol_dev, &M->tol, sizeof(double), cudaMemcpyHostToDevice));
   M->bufs.push_back(M->nrm);
   M->bufs.push_back(M->conv);
+  M->bufs.push_back(M->tol_dev);
   return KFBI_OK;
 }
+
+// the mixed multigrid's outer-step tolerance (device) and its base value
+double* mg_tol_dev(kfbi_problem* p) {
+  return (p->mg && p->mg->precision == KFBI_MIXED) ? p->mg->tol_dev : nullptr;
+}
+double mg_tol(const kfbi_problem* p) { return p->mg ? p->mg->tol : 0.0; }
 
 void mg_destroy(kfbi_problem* p) {
   MgSolver* M = p->mg;
@@ -930,7 +941,7 @@ kfbi_status mg_solve(kfbi_problem* p, const double* rhs, double* u) {
     KFBI_TRY(fix_residual(p, M->fix, A.L[0].f, M->conv, st));
     for (int c = 0; c < M->inner_cycles; ++c) KFBI_TRY(vcycle<float>(p, A, M->lcoarse, c == 0, M->conv));
     KFBI_TRY(fix_add(p, M->fix, A.L[0].u, M->nrm + 6, M->conv, st));
-    KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_mg_check_corr<<<1, 1, 0, st>>>(M->nrm, M->tol, M->conv));
+    KFBI_LAUNCH(p, KFBI_KC_RESIDUAL, k_mg_check_corr<<<1, 1, 0, st>>>(M->nrm, M->tol_dev, M->conv));
   }
   KFBI_TRY(fix_out(p, M->fix, u, st));
   KFBI_CUDA(p, cudaGetLastError());
