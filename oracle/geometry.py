@@ -4,9 +4,15 @@ Grid: box [lo, hi]^d, N intervals, h = (hi - lo)/N, nodes x_i = lo + i h,
 arrays of shape (N+1,)*d with axis d-1 fastest (C order).
 
 Steps, in the paper's order:
-  * classification of nodes (Sec. 5.2): inside Omega iff H(node) < 0;
+  * classification of nodes (Sec. 5.2): inside Omega iff H(node) < 0; with
+    several interfaces Gamma^(k) every node also carries the label of its
+    side (0 outside, 1 + k inside Gamma^(k)), the subdomains Omega^(i) of the
+    remark on arbitrarily close interfaces (Sec. 5.2);
   * intersections of Gamma with grid lines by a bracketed Newton/bisection
-    iteration (Sec. 5.1), unit normal n = grad H/|grad H|;
+    iteration (Sec. 5.1), unit normal n = grad H/|grad H|.  A grid edge whose
+    end nodes carry labels a != b crosses Gamma^(a-1) (if a > 0) and
+    Gamma^(b-1) (if b > 0): one root of H_k per crossed interface k, so an
+    edge between two close interfaces holds two points;
   * overlapping surface decomposition Gamma_r = {|n . e_r| > cos(alpha)}, Gamma_r^h
     = its intersections with e_r-lines, Gamma^h = union = the DOF set (Sec. 5.1);
   * reference plane Pi_m with m = argmax_k |n_k| (Sec. 5.1);
@@ -17,7 +23,13 @@ Readings where the paper is silent (the same written rules bind the CUDA path):
   * cos(alpha) = 0.707 in 2D (reproduces the point counts N_b of Table 1),
     0.4 in 3D (alpha in (acos(1/sqrt d), pi/2));
   * DOF order: family r ascending, then the grid line (other axes
-    lexicographic, lower axis slowest), then the edge position along the line;
+    lexicographic, lower axis slowest), then the edge position along the line,
+    then, on an edge with two points, the interface of the edge's first node
+    first;
+  * an interface k is crossed on an edge only where H_k changes sign along
+    it (a node inside two overlapping components takes the label of the one
+    it lies deeper in, and the edge to the other component crosses one
+    interface);
   * root iteration: start at the linear interpolant, Newton step, bisection
     whenever Newton leaves the bracket, stop when |ds| <= 1e-15 h (<= 64 steps);
   * stencil rules: see ``collocation_stencil``.
@@ -59,15 +71,21 @@ def classify(grid: Grid, kind: int, p) -> np.ndarray:
     return LS.H(kind, p, grid.coords()) < 0.0
 
 
-def find_roots(grid: Grid, kind: int, p, x0: np.ndarray, r: int) -> np.ndarray:
-    """Offsets s in [0, h] with H(x0 + s e_r) = 0 on edges whose end nodes differ
-    in class (Sec. 5.1), by Newton's method safeguarded with bisection."""
+def label_nodes(grid: Grid, kind: int, p) -> np.ndarray:
+    """Node labels: 0 outside Omega, 1 + k in Omega^(k) (uint8)."""
+    return LS.labels(kind, p, grid.coords())
+
+
+def find_roots(grid: Grid, kind: int, p, x0: np.ndarray, r: int, iface: int = 0) -> np.ndarray:
+    """Offsets s in [0, h] with H_k(x0 + s e_r) = 0 (k = iface) on edges where
+    H_k changes sign (Sec. 5.1), by Newton's method safeguarded with bisection."""
     h = grid.h
     m = x0.shape[0]
+    Hk = lambda X: LS.H_iface(kind, p, iface, X)
     xb = x0.copy()
     xb[:, r] = grid.lo + (np.round((x0[:, r] - grid.lo) / h) + 1.0) * h
-    ha = LS.H(kind, p, x0)
-    hb = LS.H(kind, p, xb)
+    ha = Hk(x0)
+    hb = Hk(xb)
     neg_a = ha < 0.0
     s = h * ha / (ha - hb)
     lo_s = np.zeros(m)
@@ -79,8 +97,8 @@ def find_roots(grid: Grid, kind: int, p, x0: np.ndarray, r: int) -> np.ndarray:
         idx = np.nonzero(active)[0]
         X = x0[idx].copy()
         X[:, r] = x0[idx, r] + s[idx]
-        f = LS.H(kind, p, X)
-        df = LS.grad_H(kind, p, X)[:, r]
+        f = Hk(X)
+        df = LS.grad_H_iface(kind, p, iface, X)[:, r]
         done_zero = f == 0.0
         same = (f < 0.0) == neg_a[idx]
         lo_s[idx] = np.where(same, s[idx], lo_s[idx])
@@ -107,6 +125,7 @@ class Surface:
     edge: np.ndarray     # (Nb,) index of the edge's first node along e_r
     axis: np.ndarray     # (Nb,) reference axis m = argmax |n_k|
     line_start: list     # per family: CSR offsets of length (N+1)^(d-1) + 1
+    iface: np.ndarray    # (Nb,) the interface Gamma^(k) the point lies on
 
     @property
     def nb(self) -> int:
@@ -118,36 +137,70 @@ def other_axes(d: int, r: int):
 
 
 def surface_points(grid: Grid, kind: int, p, cos_alpha: float,
-                   inside: np.ndarray) -> Surface:
-    """Gamma^h = union over r of the e_r-line intersections with |n_r| > cos(alpha)."""
+                   labels: np.ndarray) -> Surface:
+    """Gamma^h = union over r of the e_r-line intersections with |n_r| > cos(alpha).
+    `labels`: node labels (``label_nodes``); a boolean inside mask is accepted
+    for level sets with one interface."""
     d, n = grid.dim, grid.n
-    xs, ns, fam, line, edge = [], [], [], [], []
+    if labels.dtype == bool:
+        assert LS.n_interfaces(kind, p) == 1
+    lab = labels.astype(np.int64)
+    xs, ns, fam, line, edge, ifc = [], [], [], [], [], []
     starts = []
     nl = (n + 1) ** (d - 1)
     for r in range(d):
-        a = np.take(inside, np.arange(0, n), axis=r)
-        b = np.take(inside, np.arange(1, n + 1), axis=r)
-        cross = np.moveaxis(a != b, r, -1)          # other axes first, e_r last
-        idx = np.argwhere(cross)                     # C order = DOF order
+        a = np.moveaxis(np.take(lab, np.arange(0, n), axis=r), r, -1)
+        b = np.moveaxis(np.take(lab, np.arange(1, n + 1), axis=r), r, -1)
+        idx = np.argwhere(a != b)                    # C order = DOF order
+        la = a[tuple(idx.T)]
+        lb = b[tuple(idx.T)]
         oth = other_axes(d, r)
         x0 = np.zeros((idx.shape[0], d))
         for j, ax in enumerate(oth):
             x0[:, ax] = grid.coord(idx[:, j])
         x0[:, r] = grid.coord(idx[:, -1])
-        s = find_roots(grid, kind, p, x0, r)
-        X = x0.copy()
-        X[:, r] = x0[:, r] + s
-        g = LS.grad_H(kind, p, X)
-        nrm = g / np.sqrt(np.sum(g * g, -1))[:, None]
-        keep = np.abs(nrm[:, r]) > cos_alpha
-        li = np.zeros(idx.shape[0], dtype=np.int64)
+        xb = x0.copy()
+        xb[:, r] = grid.coord(idx[:, -1] + 1)
+        # candidate points: slot 0 on the first node's interface, slot 1 on
+        # the second node's, each only where that H_k changes sign
+        cand = []
+        for slot, lk in ((0, la), (1, lb)):
+            for k in np.unique(lk[lk > 0] - 1):
+                sel = np.nonzero((lk == k + 1))[0]
+                ha = LS.H_iface(kind, p, int(k), x0[sel]) < 0.0
+                hb = LS.H_iface(kind, p, int(k), xb[sel]) < 0.0
+                sel = sel[ha != hb]
+                if sel.size:
+                    cand.append((sel, slot, int(k)))
+        E, S, K, X, NRM = [], [], [], [], []
+        for sel, slot, k in cand:
+            s = find_roots(grid, kind, p, x0[sel], r, k)
+            Xk = x0[sel].copy()
+            Xk[:, r] = x0[sel, r] + s
+            g = LS.grad_H_iface(kind, p, k, Xk)
+            E.append(sel)
+            S.append(np.full(sel.size, slot))
+            K.append(np.full(sel.size, k))
+            X.append(Xk)
+            NRM.append(g / np.sqrt(np.sum(g * g, -1))[:, None])
+        if E:
+            E, S, K = np.concatenate(E), np.concatenate(S), np.concatenate(K)
+            X, NRM = np.concatenate(X), np.concatenate(NRM)
+        else:
+            E = S = K = np.zeros(0, dtype=np.int64)
+            X = NRM = np.zeros((0, d))
+        order = np.lexsort((S, E))
+        E, K, X, NRM = E[order], K[order], X[order], NRM[order]
+        keep = np.abs(NRM[:, r]) > cos_alpha
+        li = np.zeros(E.shape[0], dtype=np.int64)
         for j in range(d - 1):
-            li = li * (n + 1) + idx[:, j]
+            li = li * (n + 1) + idx[E, j]
         xs.append(X[keep])
-        ns.append(nrm[keep])
+        ns.append(NRM[keep])
         fam.append(np.full(int(keep.sum()), r))
         line.append(li[keep])
-        edge.append(idx[keep, -1])
+        edge.append(idx[E[keep], -1])
+        ifc.append(K[keep])
         counts = np.bincount(li[keep], minlength=nl)
         starts.append(np.concatenate([[0], np.cumsum(counts)]))
     x = np.concatenate(xs)
@@ -156,7 +209,8 @@ def surface_points(grid: Grid, kind: int, p, cos_alpha: float,
     line_start = [st + off[r] for r, st in enumerate(starts)]
     axis = np.argmax(np.abs(nn), axis=1)
     return Surface(x, nn, np.concatenate(fam), np.concatenate(line),
-                   np.concatenate(edge), axis, line_start)
+                   np.concatenate(edge), axis, line_start,
+                   np.concatenate(ifc).astype(np.int64))
 
 
 # ---------------------------------------------------------------------------
@@ -213,10 +267,10 @@ class LineIndex:
         self.g = grid
         self.s = surf
 
-    def nearest(self, fam: int, other_idx, s_pred: float) -> int:
-        """DOF of family `fam` on the e_fam line through the other-axis node indices
-        `other_idx`, nearest to coordinate s_pred along e_fam, within 2h; ties to
-        the lower DOF index; -1 if none."""
+    def nearest(self, fam: int, other_idx, s_pred: float, iface: int = 0) -> int:
+        """DOF of family `fam` on interface `iface` on the e_fam line through the
+        other-axis node indices `other_idx`, nearest to coordinate s_pred along
+        e_fam, within 2h; ties to the lower DOF index; -1 if none."""
         n = self.g.n
         for j in other_idx:
             if j < 0 or j > n:
@@ -227,6 +281,8 @@ class LineIndex:
         st = self.s.line_start[fam]
         best, bestd = -1, math.inf
         for q in range(st[li], st[li + 1]):
+            if self.s.iface[q] != iface:
+                continue
             dist = abs(self.s.x[q, fam] - s_pred)
             if dist <= 2.0 * self.g.h and dist < bestd:
                 best, bestd = q, dist
@@ -235,38 +291,6 @@ class LineIndex:
 
 class GeometryError(RuntimeError):
     pass
-
-
-def check_separated(grid: Grid, kind: int, p, inside: np.ndarray) -> None:
-    """Unions of discs/balls: interfaces closer than the grid step are not
-    handled (they need the difference of two correction functions, the remark
-    on arbitrarily close interfaces in Sec. 5.2).  Rule: an inside node within
-    1.8 h of its ball's surface whose segment to an inside compact-stencil
-    neighbour has a sample at k/8 (k = 1..7) outside Omega means two
-    interfaces in one stencil; raise GeometryError."""
-    if kind not in (W.LS_DISCS, W.LS_SPHERES):
-        return
-    d, h, n = grid.dim, grid.h, grid.n
-    r = p[0]
-    idx = np.argwhere(inside)
-    X = grid.coord(idx)
-    _, v = LS._nearest_ball(p, d, X)
-    near = (r - np.sqrt(v + r * r)) <= 1.8 * h
-    idx, X = idx[near], X[near]
-    offs = np.stack(np.meshgrid(*([np.arange(-1, 2)] * d), indexing="ij"), -1).reshape(-1, d)
-    offs = offs[np.any(offs != 0, axis=1)]
-    for o in offs:
-        q = idx + o
-        ok = np.all((q >= 0) & (q <= n), axis=1)
-        ok[ok] = inside[tuple(q[ok].T)]
-        if not ok.any():
-            continue
-        base = X[ok]
-        for s in range(1, 8):
-            Y = base + (s * 0.125) * (o * h)
-            if np.any(~(LS.H(kind, p, Y) < 0.0)):
-                raise GeometryError("a compact stencil spans two interfaces "
-                                    "(interfaces closer than the grid step)")
 
 
 def collocation_stencil(grid: Grid, surf: Surface, lines: LineIndex, i: int,
@@ -290,6 +314,8 @@ def collocation_stencil(grid: Grid, surf: Surface, lines: LineIndex, i: int,
     Both: if no point set is complete, the next reference axis (``axis_order``)
     is tried; otherwise GeometryError.
     PDE points: nodes round(p_i) + ``pde_offsets``.
+    Several interfaces: only points of p_i's own interface are taken (the
+    local Cauchy problem of Sec. 5.3 is posed on one interface).
     """
     d = grid.dim
     p = surf.x[i]
@@ -308,7 +334,7 @@ def collocation_stencil(grid: Grid, surf: Surface, lines: LineIndex, i: int,
             for k in cands:
                 xt = grid.lo + k * grid.h
                 s_pred = p[m] - nv[t] * (xt - p[t]) / nv[m]
-                q = lines.nearest(m, [k], s_pred)
+                q = lines.nearest(m, [k], s_pred, int(surf.iface[i]))
                 if q >= 0:
                     found.append(q)
                     if len(found) == nd:
@@ -337,7 +363,7 @@ def collocation_stencil(grid: Grid, surf: Surface, lines: LineIndex, i: int,
                     x1 = grid.lo + j * grid.h
                     x2 = grid.lo + k * grid.h
                     s_pred = p[m] - (nv[t1] * (x1 - p[t1]) + nv[t2] * (x2 - p[t2])) / nv[m]
-                    q = lines.nearest(m, [j, k], s_pred)
+                    q = lines.nearest(m, [j, k], s_pred, int(surf.iface[i]))
                     if q < 0:
                         ok = False
                         break

@@ -68,10 +68,11 @@ class Problem:
             self.kt = w.kappa
         self.cos_alpha = w.cosa()
         lsp = LS.params(w)
-        self.inside = G.classify(self.grid, w.ls_kind, lsp)
-        G.check_separated(self.grid, w.ls_kind, lsp, self.inside)
+        self.n_iface = LS.n_interfaces(w.ls_kind, lsp)
+        self.labels = G.label_nodes(self.grid, w.ls_kind, lsp)
+        self.inside = self.labels > 0
         self.surf = G.surface_points(self.grid, w.ls_kind, lsp,
-                                     self.cos_alpha, self.inside)
+                                     self.cos_alpha, self.labels)
         s = self.surf
         self.nb = s.nb
         lines = G.LineIndex(self.grid, s)
@@ -96,32 +97,77 @@ class Problem:
                 s.x[self.dir_idx[i]], s.x[self.neu_idx[i]], s.n[self.neu_idx[i]]))
         self.M = np.array(Ms)
         self.Qf, self.Rf = CO.qr_factor(self.M)
-        self.irr = CR.irregular_nodes(self.inside, self.order)
-        self.trace_st = TR.trace_stencils(self.grid, s.x, s.n, self.inside,
-                                          self.irr, self.order)
-        # C is needed only on I_h: by the correction terms and by the traces.
-        self.cnode_idx = np.argwhere(self.irr)       # C order
-        self.cnode_owner = CR.closest_primary(s.x, self.grid.coord(self.cnode_idx), self.h)
+        self.irr = CR.irregular_nodes(self.labels, self.order)
+        # C^(k) is needed by the correction terms (one entry per irregular
+        # node and interface k of its stencil) and by the traces.
+        self.cnode_idx, self.cnode_iface = CR.correction_entries(self.labels, self.irr,
+                                                                 self.order)
+        holds = np.zeros((max(self.n_iface, 1),) + self.labels.shape, dtype=bool)
+        holds[(self.cnode_iface,) + tuple(self.cnode_idx.T)] = True
+        self.trace_st = TR.trace_stencils(self.grid, s.x, s.n, self.labels, self.irr,
+                                          self.order, s.iface, holds)
+        if any(rec["close"] for rec in self.trace_st):
+            self._add_trace_entries()
+        self.cnode_owner = np.zeros(self.cnode_idx.shape[0], dtype=np.int64)
+        for k in range(self.n_iface):
+            on_k = np.nonzero(s.iface == k)[0]
+            ent = self.cnode_iface == k
+            if ent.any():
+                own = CR.closest_primary(s.x[on_k], self.grid.coord(self.cnode_idx[ent]), self.h)
+                self.cnode_owner[ent] = on_k[own]
+
+    def _add_trace_entries(self):
+        """Close interfaces: the entries (q, k) the trace stencils of points
+        near another interface need (C^(t) and C^(l_q) at every node q of
+        another label than the side's t), merged with the correction-term
+        entries, in node order then k."""
+        n1 = self.n + 1
+        keys = set()
+        lin = lambda q: int(np.ravel_multi_index(tuple(q), (n1,) * self.d))
+        for q, k in zip(self.cnode_idx, self.cnode_iface):
+            keys.add((lin(q), int(k)))
+        for rec in self.trace_st:
+            if not rec["close"]:
+                continue
+            for side in (1, -1):
+                nodes, _, _, t = rec[side]
+                lq = self.labels[tuple(nodes.T)].astype(np.int64)
+                for q, l in zip(nodes, lq):
+                    if l == t:
+                        continue
+                    if t > 0:
+                        keys.add((lin(q), t - 1))
+                    if l > 0:
+                        keys.add((lin(q), int(l) - 1))
+        keys = sorted(keys)
+        li = np.array([k[0] for k in keys], dtype=np.int64)
+        self.cnode_idx = np.stack(np.unravel_index(li, (n1,) * self.d), -1).astype(np.int64)
+        self.cnode_iface = np.array([k[1] for k in keys], dtype=np.int64)
 
     # -- Step 3.1 ----------------------------------------------------------
     def collocation(self, a: np.ndarray, b: np.ndarray, ftilde_grid=None) -> np.ndarray:
         """Coefficients d_i of every local correction function (eq. (cau-ls))."""
         if ftilde_grid is None:
             ft = np.zeros(self.pde_nodes.shape[:2])
+        elif ftilde_grid.ndim == self.d + 1:
+            # one f~ grid per interface: each DOF takes its own interface's
+            nodes = tuple(np.moveaxis(self.pde_nodes, -1, 0))
+            ft = ftilde_grid[(self.surf.iface[:, None],) + nodes]
         else:
             ft = ftilde_grid[tuple(np.moveaxis(self.pde_nodes, -1, 0))]
         Q = CO.collocation_rhs(self.h, ft, a[self.dir_idx], b[self.neu_idx])
         return CO.qr_solve(self.Qf, self.Rf, Q)
 
     def c_values(self, coef: np.ndarray) -> np.ndarray:
-        """C_h at the irregular nodes (C order)."""
+        """C_h^(k) at the correction entries (irregular node, interface k)."""
         own = self.cnode_owner
         x = self.grid.coord(self.cnode_idx)
         return CO.eval_poly(self.E, coef[own], self.surf.x[own], self.h, x)
 
     def c_grid(self, cvals: np.ndarray) -> np.ndarray:
-        g = np.zeros(self.inside.shape)
-        g[tuple(self.cnode_idx.T)] = cvals
+        """cgrids[l] = C^(l) on the grid at its entries, cgrids[0] = 0."""
+        g = np.zeros((self.n_iface + 1,) + self.inside.shape)
+        g[(self.cnode_iface + 1,) + tuple(self.cnode_idx.T)] = cvals
         return g
 
     # -- Step 3.2 ----------------------------------------------------------
@@ -131,12 +177,12 @@ class Problem:
         shape = self.inside.shape
         R = np.zeros(shape)
         if F_in is not None:
-            F = np.where(self.inside, F_in, F_out)
+            F = self._own_side(F_in, F_out)
             R = R + F
             if self.order == 4:
-                L = np.where(self.inside, L_in, L_out)
+                L = self._own_side(L_in, L_out)
                 R = R + self.h * self.h / 12.0 * L
-        R = R + CR.correction_terms(self.c_grid(cvals), self.inside, self.irr,
+        R = R + CR.correction_terms(self.c_grid(cvals), self.labels, self.irr,
                                     self.d, self.order, self.h, self.kt)
         if g_b is not None:
             R = R - BS.boundary_lift(g_b, self.d, self.order, self.h, self.kt)
@@ -144,6 +190,16 @@ class Problem:
         out = np.zeros(shape)
         out[inner] = R[inner]
         return out
+
+    def _own_side(self, G_in, G_out):
+        """Each node's own side's grid: G_in (or G_in[k] for label 1 + k, one
+        grid per interface) inside, G_out outside."""
+        if G_in.ndim == self.d + 1:
+            out = G_out.copy()
+            for k in range(G_in.shape[0]):
+                out = np.where(self.labels == k + 1, G_in[k], out)
+            return out
+        return np.where(self.inside, G_in, G_out)
 
     # -- Step 3.3 ----------------------------------------------------------
     def box_solve(self, R, g_b=None):
@@ -157,13 +213,13 @@ class Problem:
     # -- Step 3.4 ----------------------------------------------------------
     def traces(self, u, cvals):
         """(value^+, value^-, d_n^+, d_n^-) at every DOF."""
-        return TR.one_sided(self.trace_st, u, self.c_grid(cvals), self.inside)
+        return TR.one_sided(self.trace_st, u, self.c_grid(cvals), self.labels)
 
     # -- one potential: Steps 3.1-3.4 ----------------------------------------
     def potential(self, a, b, F_in=None, F_out=None, L_in=None, L_out=None, g_b=None):
         ft = None
         if F_in is not None:
-            ft = F_in - F_out
+            ft = F_in - F_out                        # per interface if F_in is
         coef = self.collocation(a, b, ft)
         cv = self.c_values(coef)
         R = self.rhs(cv, F_in, F_out, L_in, L_out, g_b)
@@ -292,9 +348,10 @@ class InterfaceSystem:
         return np.concatenate([phi - (v1 - v2), psi - (self.s1 * d1 - self.s2 * d2)])
 
     def _sides(self, data):
-        z = np.zeros_like(data["f_in"])
-        side1 = (data["f_in"] / self.s1, z, data["lapf_in"] / self.s1, z)
-        side2 = (z, data["f_out"] / self.s2, z, data["lapf_out"] / self.s2)
+        zi = np.zeros_like(data["f_in"])
+        zo = np.zeros_like(data["f_out"])
+        side1 = (data["f_in"] / self.s1, zo, data["lapf_in"] / self.s1, zo)
+        side2 = (zi, data["f_out"] / self.s2, zi, data["lapf_out"] / self.s2)
         return side1, side2
 
     def bie_rhs(self, g1, g2, data) -> np.ndarray:

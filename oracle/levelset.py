@@ -130,6 +130,8 @@ def H(kind: int, p, X: np.ndarray) -> np.ndarray:
         return t * t + z * z - small * small
     if kind in (W.LS_DISCS, W.LS_SPHERES):
         return _nearest_ball(p, 2 if kind == W.LS_DISCS else 3, X)[1]
+    if kind == W.LS_UNION:
+        return _union_argmin(p, X)[1]
     if kind == W.LS_MOLECULE:
         r, level, na = p[0], p[1], int(p[2])
         acc = np.zeros(X.shape[:-1])
@@ -163,6 +165,75 @@ def _nearest_ball(p, d: int, X: np.ndarray):
             bv = np.where(take, v, bv)
             best = np.where(take, k, best)
     return best, bv
+
+
+def n_interfaces(kind: int, p) -> int:
+    """Interfaces Gamma^(k) (components Omega^(k) of Omega) the level set
+    describes: the balls of a ball union, the components of a union, else one."""
+    if kind in (W.LS_DISCS, W.LS_SPHERES):
+        return int(p[1])
+    if kind == W.LS_UNION:
+        return int(p[0])
+    return 1
+
+
+def _union_argmin(p, X: np.ndarray):
+    """Per point the first component with the smallest H_k, and that value."""
+    best = np.zeros(X.shape[:-1], dtype=np.int64)
+    bv = None
+    for k, (kind, q) in enumerate(W.union_components(p)):
+        v = H(kind, q, X)
+        if bv is None:
+            bv = v
+        else:
+            take = v < bv
+            bv = np.where(take, v, bv)
+            best = np.where(take, k, best)
+    return best, bv
+
+
+def labels(kind: int, p, X: np.ndarray) -> np.ndarray:
+    """Side label of points X (the remark on arbitrarily close interfaces in
+    Sec. 5.2 with Omega^(0) outside): 0 outside Omega, 1 + k in Omega^(k).
+    Several interfaces: k is the first interface with the smallest H_k (for a
+    point inside two overlapping components, the one it lies deeper in)."""
+    if kind in (W.LS_DISCS, W.LS_SPHERES):
+        k, v = _nearest_ball(p, 2 if kind == W.LS_DISCS else 3, X)
+        return np.where(v < 0.0, k + 1, 0).astype(np.uint8)
+    if kind == W.LS_UNION:
+        k, v = _union_argmin(p, X)
+        return np.where(v < 0.0, k + 1, 0).astype(np.uint8)
+    return np.where(H(kind, p, X) < 0.0, 1, 0).astype(np.uint8)
+
+
+def H_iface(kind: int, p, k: int, X: np.ndarray) -> np.ndarray:
+    """Level-set function H_k of interface k alone: |X - c_k|^2 - r^2 for ball
+    k of a ball union (the arithmetic of _nearest_ball), the component's own
+    function for a union, H itself for one interface."""
+    if kind == W.LS_UNION:
+        ck, q = W.union_components(p)[k]
+        return H(ck, q, X)
+    if kind in (W.LS_DISCS, W.LS_SPHERES):
+        d = 2 if kind == W.LS_DISCS else 3
+        r = p[0]
+        c = p[2 + d * k: 2 + d * (k + 1)]
+        v = (X[..., 0] - c[0]) * (X[..., 0] - c[0]) + (X[..., 1] - c[1]) * (X[..., 1] - c[1])
+        if d == 3:
+            v = v + (X[..., 2] - c[2]) * (X[..., 2] - c[2])
+        return v - r * r
+    return H(kind, p, X)
+
+
+def grad_H_iface(kind: int, p, k: int, X: np.ndarray) -> np.ndarray:
+    """Gradient of H_k."""
+    if kind == W.LS_UNION:
+        ck, q = W.union_components(p)[k]
+        return grad_H(ck, q, X)
+    if kind in (W.LS_DISCS, W.LS_SPHERES):
+        d = 2 if kind == W.LS_DISCS else 3
+        c = np.asarray(p[2 + d * k: 2 + d * (k + 1)], dtype=np.float64)
+        return 2.0 * (X[..., :d] - c)
+    return grad_H(kind, p, X)
 
 
 def grad_H(kind: int, p, X: np.ndarray) -> np.ndarray:
@@ -207,6 +278,12 @@ def grad_H(kind: int, p, X: np.ndarray) -> np.ndarray:
         k, _ = _nearest_ball(p, d, X)
         C = np.asarray(p[2: 2 + d * int(p[1])], dtype=np.float64).reshape(-1, d)[k]
         return 2.0 * (X[..., :d] - C)
+    if kind == W.LS_UNION:
+        k, _ = _union_argmin(p, X)
+        g = np.zeros(X.shape)
+        for j, (ck, q) in enumerate(W.union_components(p)):
+            g = np.where((k == j)[..., None], grad_H(ck, q, X), g)
+        return g
     if kind == W.LS_MOLECULE:
         r, level, na = p[0], p[1], int(p[2])
         g = np.zeros(X.shape)

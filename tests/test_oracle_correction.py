@@ -45,7 +45,8 @@ def test_corrected_scheme_truncation(kappa):
         u = np.where(P.inside, up, um)
         C = np.where(P.irr, up - um, 0.0)
         Au = BS.apply_operator(u, 2, 4, P.h, kappa)
-        corr = CR.correction_terms(C, P.inside, P.irr, 2, 4, P.h, kappa)
+        corr = CR.correction_terms(np.stack([np.zeros_like(C), C]), P.labels, P.irr, 2, 4,
+                                   P.h, kappa)
         fp, fm = lup - kappa * up, lum - kappa * um
         # Lap f for the two sides, by the same closed forms differentiated twice
         h = P.h

@@ -8,12 +8,9 @@ PM1 the geometry of the union is the union of the geometries: node classes
     ellipse level set (a = b = r), a different formula for the same circle.
 PM2 the interface problem on four discs converges at 4th order (> 12x from
     N = 128 to 256) on both sides.
-PM3 interfaces closer than the grid step are refused by the written rule the
-    CUDA set-up follows too (the paper's nearly touching spheres).
+Close and touching interfaces: test_oracle_close_interfaces.py.
 """
 import numpy as np
-import pytest
-
 import workloads as W
 from oracle import geometry as G
 from oracle import kfbi as K
@@ -21,9 +18,9 @@ from oracle import kfbi as K
 
 def _dofs(w):
     grid = G.Grid(w.dim, w.n, w.lo, w.h)
-    inside = G.classify(grid, w.ls_kind, w.ls_params)
-    s = G.surface_points(grid, w.ls_kind, w.ls_params, w.cosa(), inside)
-    return inside, s
+    lab = G.label_nodes(grid, w.ls_kind, w.ls_params)
+    s = G.surface_points(grid, w.ls_kind, w.ls_params, w.cosa(), lab)
+    return lab > 0, s
 
 
 def test_union_geometry_is_the_union():
@@ -114,19 +111,3 @@ def test_random_separated_discs_and_spheres():
             params = [r, float(m)] + [float(v) for c in cs for v in c]
             w = W.Workload("balls", d, n, -1.0, 1.0, kind, params, W.KIND_INTERFACE_MU)
             _union_vs_singles(w, W.LS_ELLIPSE if d == 2 else W.LS_ELLIPSOID)
-
-
-def test_close_interfaces_are_refused():
-    """The rule for interfaces closer than the grid step: the paper's spheres
-    of Sec. 7.2.5 (radius 0.7, 0.014 apart) at 128^3 are refused; the same
-    centres with radius 0.6 (0.21 apart), the random layouts above and four
-    discs 0.4 apart pass."""
-    w = W.hetero_spheres_3d(128)
-    grid = G.Grid(3, w.n, w.lo, w.h)
-    close = [0.7] + list(w.ls_params[1:])
-    with pytest.raises(G.GeometryError):
-        G.check_separated(grid, w.ls_kind, close, G.classify(grid, w.ls_kind, close))
-    G.check_separated(grid, w.ls_kind, w.ls_params, G.classify(grid, w.ls_kind, w.ls_params))
-    w2 = W.discs_interface_2d(128)
-    grid2 = G.Grid(2, w2.n, w2.lo, w2.h)
-    G.check_separated(grid2, w2.ls_kind, w2.ls_params, G.classify(grid2, w2.ls_kind, w2.ls_params))

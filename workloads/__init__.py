@@ -29,6 +29,42 @@ LS_MOLECULE = 5     # 3D: p = [r, level, n_atoms, x1, y1, z1, x2, ...]
 LS_DISCS = 6        # 2D: p = [r, n, x1, y1, ...], union of n separated discs
 LS_SPHERES = 7      # 3D: p = [r, n, x1, y1, z1, ...], union of n separated balls
 LS_GRID = 8         # H sampled at the grid nodes: p = [], samples in extra["samples"]
+LS_UNION = 9        # p = [m, kind_1, params_1..., kind_m, params_m...]: m interfaces,
+                    # each of an analytic kind (ellipse, star, ellipsoid, torus)
+
+# Parameters per component of a union (the layouts above).
+UNION_PARAMS = {LS_ELLIPSE: 5, LS_STAR: 5, LS_ELLIPSOID: 6, LS_TORUS: 2}
+
+
+def union_components(p):
+    """[(kind, params), ...] of a union's parameter vector."""
+    m = int(p[0])
+    out, at = [], 1
+    for _ in range(m):
+        kind = int(p[at])
+        cnt = UNION_PARAMS[kind]
+        out.append((kind, list(p[at + 1: at + 1 + cnt])))
+        at += 1 + cnt
+    return out
+
+
+def union_params(components):
+    """Parameter vector of a union from [(kind, params), ...]."""
+    p = [float(len(components))]
+    for kind, q in components:
+        assert len(q) == UNION_PARAMS[kind]
+        p += [float(kind)] + [float(v) for v in q]
+    return p
+
+
+def n_interfaces(ls_kind: int, p) -> int:
+    """Number of interfaces (components of Omega, each with its own side
+    label 1 + k): the balls of a ball union, the components of a union, else 1."""
+    if ls_kind in (LS_DISCS, LS_SPHERES):
+        return int(p[1])
+    if ls_kind == LS_UNION:
+        return int(p[0])
+    return 1
 
 # Problem kinds (shared with kfbi_problem_kind).
 KIND_DIRICHLET = 0  # interior Dirichlet BVP, eq. (bie-D)
@@ -164,9 +200,117 @@ def _sol_harmonic3(amps):
     return u, g, lap
 
 
+# Solutions with a closed-form bi-Laplacian: (u, grad u, lap u, lap lap u), so
+# that lap f = sigma lap lap u - kappa lap u needs no per-solution case.
+
+def _sol4_exp_68():
+    # u = exp(0.6 x + 0.8 y): lap u = u (0.36 + 0.64 = 1)
+    u = lambda X: np.exp(0.6 * X[..., 0] + 0.8 * X[..., 1])
+    g = lambda X: np.stack([0.6 * u(X), 0.8 * u(X)], -1)
+    return u, g, u, u
+
+
+def _sol4_sinsin_pi():
+    # u = sin(pi (x + 1)/2) sin(pi (y + 1)/2): lap u = -(pi^2/2) u
+    k = 0.5 * math.pi
+    sx = lambda X: np.sin(k * (X[..., 0] + 1.0))
+    sy = lambda X: np.sin(k * (X[..., 1] + 1.0))
+    u = lambda X: sx(X) * sy(X)
+    g = lambda X: np.stack([k * np.cos(k * (X[..., 0] + 1.0)) * sy(X),
+                            k * sx(X) * np.cos(k * (X[..., 1] + 1.0))], -1)
+    lam = -2.0 * k * k
+    return u, g, (lambda X: lam * u(X)), (lambda X: lam * lam * u(X))
+
+
+def _sol4_torus_in():
+    # u = sin^2(2x) cos^2(2y) cos z = (1 - cos 4x)(1 + cos 4y) cos z / 4; every
+    # product of cosines is an eigenfunction of lap (eigenvalues -1, -17, -17, -33)
+    def parts(X):
+        c4x, c4y, cz = np.cos(4 * X[..., 0]), np.cos(4 * X[..., 1]), np.cos(X[..., 2])
+        return c4x, c4y, cz
+    u = lambda X: np.sin(2 * X[..., 0]) ** 2 * np.cos(2 * X[..., 1]) ** 2 * np.cos(X[..., 2])
+
+    def g(X):
+        s2x, c2y, cz = np.sin(2 * X[..., 0]), np.cos(2 * X[..., 1]), np.cos(X[..., 2])
+        return np.stack([2.0 * np.sin(4 * X[..., 0]) * c2y * c2y * cz,
+                         -2.0 * s2x * s2x * np.sin(4 * X[..., 1]) * cz,
+                         -s2x * s2x * c2y * c2y * np.sin(X[..., 2])], -1)
+
+    def lap(X):
+        c4x, c4y, cz = parts(X)
+        return (-1.0 - 17.0 * c4y + 17.0 * c4x + 33.0 * c4x * c4y) * cz / 4.0
+
+    def lap2(X):
+        c4x, c4y, cz = parts(X)
+        return (1.0 + 289.0 * c4y - 289.0 * c4x - 1089.0 * c4x * c4y) * cz / 4.0
+    return u, g, lap, lap2
+
+
+def _sol4_exp_cos3():
+    u, g, lap = _sol_exp_cos3()
+    # lap(e^z cos kx) = (1 - k^2) e^z cos kx: eigenvalues -3 and -8
+    lap2 = lambda X: np.exp(X[..., 2]) * (9 * np.cos(2 * X[..., 0]) + 64 * np.cos(3 * X[..., 1]))
+    return u, g, lap, lap2
+
+
+def _sol4_cos3():
+    # u = cos x cos y cos z: lap u = -3 u
+    u = lambda X: np.cos(X[..., 0]) * np.cos(X[..., 1]) * np.cos(X[..., 2])
+    g = lambda X: np.stack([-np.sin(X[..., 0]) * np.cos(X[..., 1]) * np.cos(X[..., 2]),
+                            -np.cos(X[..., 0]) * np.sin(X[..., 1]) * np.cos(X[..., 2]),
+                            -np.cos(X[..., 0]) * np.cos(X[..., 1]) * np.sin(X[..., 2])], -1)
+    return u, g, (lambda X: -3.0 * u(X)), (lambda X: 9.0 * u(X))
+
+
+def _sol4_exp3():
+    u, g, lap = _sol_exp3()
+    return u, g, lap, (lambda X: 9.0 * u(X))
+
+
+def _sol4_harmonic3(amps):
+    u, g, lap = _sol_harmonic3(amps)
+    return u, g, lap, lap
+
+
+def _sol4_cos_cosh():
+    # u = cos x cosh y (harmonic)
+    u = lambda X: np.cos(X[..., 0]) * np.cosh(X[..., 1])
+    g = lambda X: np.stack([-np.sin(X[..., 0]) * np.cosh(X[..., 1]),
+                            np.cos(X[..., 0]) * np.sinh(X[..., 1])], -1)
+    z = lambda X: np.zeros(X.shape[:-1])
+    return u, g, z, z
+
+
+_SOL4 = {"exp_68": _sol4_exp_68, "cos_cosh": _sol4_cos_cosh, "sinsin_pi": _sol4_sinsin_pi, "torus_in": _sol4_torus_in,
+         "exp_cos3": _sol4_exp_cos3, "cos3": _sol4_cos3, "exp3": _sol4_exp3}
+
+
+def _sol4(w: Workload, name: str):
+    if name == "harmonic3":
+        return _sol4_harmonic3(w.extra["amps"])
+    return _SOL4[name]()
+
+
+def is_multi(w: Workload) -> bool:
+    """A workload whose interfaces have different interior solutions (one
+    smooth solution u^(k) per component Omega^(k), u^(0) outside)."""
+    return w.exact == "multi"
+
+
+def multi_solutions(w: Workload):
+    """([(u, grad, lap, lap2) of each interface k], (u, grad, lap, lap2)
+    outside) of a workload with per-interface solutions
+    (extra["sol_in"] = names per interface, extra["sol_out"] = the name outside)."""
+    return ([_sol4(w, nm) for nm in w.extra["sol_in"]], _sol4(w, w.extra["sol_out"]))
+
+
 def solutions(w: Workload):
-    """(u_in, grad_in, lap_in), (u_out, grad_out, lap_out) of a workload."""
+    """(u_in, grad_in, lap_in), (u_out, grad_out, lap_out) of a workload
+    (of its first interface for a per-interface workload)."""
     e = w.exact
+    if e == "multi":
+        ins, out = multi_solutions(w)
+        return ins[0][:3], out[:3]
     if e == "exp_sin":
         s = _sol_exp_sin()
         return s, _sol_zero(2)
@@ -198,6 +342,27 @@ def grid_coords(w: Workload) -> np.ndarray:
     return np.stack(mesh, -1)
 
 
+def _grid_data_multi(w: Workload):
+    """grid_data of a per-interface workload: f_in, lapf_in and u_in have a
+    leading axis of length K (grid k is interface k's f, smoothly extended)."""
+    assert w.kind in (KIND_INTERFACE_MU, KIND_INTERFACE_GENERAL)
+    X = grid_coords(w)
+    ins, (uo, _, lo_, l2o) = multi_solutions(w)
+    # the mu-form workloads are Poisson problems (as in grid_data)
+    k_in, k_out = (w.kappa, w.kappa_out) if w.kind == KIND_INTERFACE_GENERAL else (0.0, 0.0)
+    f_in = np.stack([w.sigma_in * li(X) - k_in * ui(X) for ui, _, li, _ in ins])
+    lapf_in = np.stack([w.sigma_in * l2(X) - k_in * li(X) for _, _, li, l2 in ins])
+    f_out = w.sigma_out * lo_(X) - k_out * uo(X)
+    lapf_out = w.sigma_out * l2o(X) - k_out * lo_(X)
+    u_out = uo(X)
+    gb = np.zeros_like(f_out)
+    bmask = np.ones(f_out.shape, dtype=bool)
+    bmask[tuple(slice(1, -1) for _ in range(w.dim))] = False
+    gb[bmask] = u_out[bmask]
+    return dict(f_in=f_in, f_out=f_out, lapf_in=lapf_in, lapf_out=lapf_out,
+                u_in=np.stack([ui(X) for ui, _, _, _ in ins]), u_out=u_out, g_b=gb)
+
+
 def grid_data(w: Workload):
     """Right-hand-side grids of the physical PDE on each side.
 
@@ -206,7 +371,10 @@ def grid_data(w: Workload):
     lapf_in, lapf_out (for the h^2/12 Lap f term of eqs. (9p-cds)/(27p-cds)),
     the exact solution on both sides, and the outer boundary values g_B.
     Laplacians of f are formed from the closed forms of the solutions.
+    Per-interface workloads: see _grid_data_multi.
     """
+    if is_multi(w):
+        return _grid_data_multi(w)
     X = grid_coords(w)
     (ui, gi, li), (uo, go, lo_) = solutions(w)
     d = w.dim
@@ -277,14 +445,31 @@ def _lap_of_f(w: Workload, X, inside: bool):
     raise ValueError(e)
 
 
-def boundary_data(w: Workload, pts: np.ndarray, normals: np.ndarray):
+def boundary_data(w: Workload, pts: np.ndarray, normals: np.ndarray, iface=None):
     """Interface data at points with unit normals (outward from Omega).
 
     Dirichlet BVP: returns (g_D, None).  Neumann BVP: returns
     (None, g_N) with g_N = sigma d_n u.  Interface problem: returns
     (g1, g2) with g1 = u_in - u_out and g2 = sigma_in d_n u_in - sigma_out d_n u_out,
-    the jump conditions of eq. (IFP-bc).
+    the jump conditions of eq. (IFP-bc).  Per-interface workloads take the
+    interface index of every point (`iface`) and use that interface's u_in.
     """
+    if is_multi(w):
+        ins, (uo, go, _, _) = multi_solutions(w)
+        iface = np.asarray(iface)
+        ui_v = np.zeros(pts.shape[0])
+        gi_v = np.zeros(pts.shape)
+        for k, (ui, gi, _, _) in enumerate(ins):
+            m = iface == k
+            ui_v[m] = ui(pts[m])
+            gi_v[m] = gi(pts[m])
+        dn_in = np.sum(gi_v * normals, -1)
+        if w.kind == KIND_DIRICHLET:
+            return ui_v, None
+        if w.kind == KIND_NEUMANN:
+            return None, w.sigma_in * dn_in
+        return (ui_v - uo(pts),
+                w.sigma_in * dn_in - w.sigma_out * np.sum(go(pts) * normals, -1))
     (ui, gi, _), (uo, go, _) = solutions(w)
     if w.kind == KIND_DIRICHLET:
         return ui(pts), None
@@ -297,8 +482,17 @@ def boundary_data(w: Workload, pts: np.ndarray, normals: np.ndarray):
 
 
 def exact_grid(w: Workload, inside_mask: np.ndarray) -> np.ndarray:
-    """Exact solution on the grid, side chosen by the given inside mask."""
+    """Exact solution on the grid, side chosen by the given inside mask (a
+    node label array, 0 outside and 1 + k in interface k, for per-interface
+    workloads)."""
     X = grid_coords(w)
+    if is_multi(w):
+        ins, out = multi_solutions(w)
+        lab = np.asarray(inside_mask).astype(np.int64)
+        u = out[0](X)
+        for k, s in enumerate(ins):
+            u = np.where(lab == k + 1, s[0](X), u)
+        return u
     (ui, _, _), (uo, _, _) = solutions(w)
     return np.where(inside_mask, ui(X), uo(X))
 
@@ -390,18 +584,61 @@ def discs_interface_2d(n: int = 128, contrast: float = 10.0) -> Workload:
                     KIND_INTERFACE_MU, sigma_in=contrast, sigma_out=1.0, exact="sincos_r2")
 
 
-def hetero_spheres_3d(n: int = 256) -> Workload:
+def hetero_spheres_3d(n: int = 256, radius: float = 0.6) -> Workload:
     """Sec. 7.2.5's heterogeneous problem (sigma_1 = 1, kappa_1 = 0 inside;
     sigma_2 = 4, kappa_2 = 10 outside) with its three sphere centres
-    (0.5, 0.5, 0.5), (-0.5, -0.5, 0.5), (0.5, -0.5, -0.5) but radius 0.6
-    instead of 0.7 (the paper's spheres are 0.014 apart, which needs the
-    treatment of arbitrarily close interfaces); box [-1.5, 1.5]^3,
-    u_1 = e^(x+y+z)/10, u_2 a fixed harmonic quadratic."""
+    (0.5, 0.5, 0.5), (-0.5, -0.5, 0.5), (0.5, -0.5, -0.5); the paper's radius
+    is 0.7 (the spheres 0.0142 apart), radius 0.6 leaves them 0.21 apart; box
+    [-1.5, 1.5]^3, u_1 = e^(x+y+z)/10, u_2 a fixed harmonic quadratic."""
     return Workload("hetero_spheres_3d", 3, n, -1.5, 1.5, LS_SPHERES,
-                    [0.6, 3.0, 0.5, 0.5, 0.5, -0.5, -0.5, 0.5, 0.5, -0.5, -0.5],
+                    [radius, 3.0, 0.5, 0.5, 0.5, -0.5, -0.5, 0.5, 0.5, -0.5, -0.5],
                     KIND_INTERFACE_GENERAL, sigma_in=1.0, sigma_out=4.0, kappa=0.0,
                     kappa_out=10.0, exact="exp3_harmonic3",
                     extra={"amps": [0.3, 0.2, -0.1, 0.25, 0.15, -0.2, 0.1, 0.05]})
+
+
+def touching_interfaces_2d(n: int = 256) -> Workload:
+    """Sec. 7.1.2's multiple interfaces (Table 2): eight circles of radius
+    0.383 centred at (cos(m pi/4), sin(m pi/4)), m = 1..8, and the five-fold
+    star r = 0.514 (1 + 0.2 sin 5 theta) at the origin, in [-1.7, 1.7]^2.
+    Neighbouring circles overlap by 6.3e-4 (2 * 0.383 > 2 sin(pi/8)) and the
+    star's tip at theta = pi/2 is 2e-4 from the circle above it.  Poisson
+    interface problem, sigma_i = 1, sigma_e = 3, u = exp(0.6 x + 0.8 y) in
+    every interior component, sin(pi (x+1)/2) sin(pi (y+1)/2) outside."""
+    comps = [(LS_ELLIPSE, [math.cos(m * math.pi / 4), math.sin(m * math.pi / 4), 0.383, 0.383, 0.0])
+             for m in range(1, 9)]
+    comps.append((LS_STAR, [0.0, 0.0, 0.514, 0.514 * 0.2, 5.0]))
+    return Workload("touching_interfaces_2d", 2, n, -1.7, 1.7, LS_UNION, union_params(comps),
+                    KIND_INTERFACE_MU, sigma_in=1.0, sigma_out=3.0, exact="multi",
+                    extra={"sol_in": ["exp_68"] * 9, "sol_out": "sinsin_pi"})
+
+
+def torus_ellipsoid_3d(n: int = 128) -> Workload:
+    """Sec. 7.2.4's arbitrarily close interfaces (Table 6): the torus
+    (1 - sqrt(x^2 + y^2))^2 + z^2 < 0.4^2 and the ellipsoid x^2/0.36 +
+    y^2/0.36 + z^2 < 1, which touch along the circle x^2 + y^2 = 0.36, z = 0;
+    box [-1.5, 1.5]^3, Poisson interface problem, sigma_i = 1, sigma_e = 3,
+    u = sin^2(2x) cos^2(2y) cos z in the torus, e^z (cos 2x + cos 3y) in the
+    ellipsoid, cos x cos y cos z outside."""
+    comps = [(LS_TORUS, [1.0, 0.4]), (LS_ELLIPSOID, [0.0, 0.0, 0.0, 0.6, 0.6, 1.0])]
+    return Workload("torus_ellipsoid_3d", 3, n, -1.5, 1.5, LS_UNION, union_params(comps),
+                    KIND_INTERFACE_MU, sigma_in=1.0, sigma_out=3.0, exact="multi",
+                    extra={"sol_in": ["torus_in", "exp_cos3"], "sol_out": "cos3"})
+
+
+def close_discs_2d(n: int = 128, gap: float = 0.004) -> Workload:
+    """Two circles of radius 0.4 a distance `gap` apart across x = 0.0039
+    (centres (0.0039 -+ (0.4 + gap/2), 0.013)) in [-1, 1]^2, so that for N
+    up to 256 the gap holds no grid node and x-edges across it cross both
+    circles; different interior solutions: exp(0.6 x + 0.8 y) in the left
+    disc, cos x cosh y in the right one, sin(pi (x+1)/2) sin(pi (y+1)/2)
+    outside; Poisson interface problem, sigma_i = 1, sigma_e = 3."""
+    c = 0.4 + 0.5 * gap
+    comps = [(LS_ELLIPSE, [0.0039 - c, 0.013, 0.4, 0.4, 0.0]),
+             (LS_ELLIPSE, [0.0039 + c, 0.013, 0.4, 0.4, 0.0])]
+    return Workload("close_discs_2d", 2, n, -1.0, 1.0, LS_UNION, union_params(comps),
+                    KIND_INTERFACE_MU, sigma_in=1.0, sigma_out=3.0, exact="multi",
+                    extra={"sol_in": ["exp_68", "cos_cosh"], "sol_out": "sinsin_pi"})
 
 
 def molecule_dirichlet_3d(n: int = 64) -> Workload:
