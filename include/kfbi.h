@@ -55,11 +55,10 @@ typedef enum {
   KFBI_LS_ELLIPSOID = 3,  /* 3D p=[cx,cy,cz,a,b,c]                                */
   KFBI_LS_TORUS = 4,      /* 3D p=[R,r]: (sqrt(x^2+y^2)-R)^2 + z^2 - r^2          */
   KFBI_LS_MOLECULE = 5,   /* 3D p=[r,level,n,x1,y1,z1,...]: level - sum exp(-|x-x_k|^2/r^2) */
-  KFBI_LS_DISCS = 6,      /* 2D p=[r,n,x1,y1,...]: min_k |x-x_k|^2 - r^2, n separated discs
-                             (a compact stencil spanning two discs: refused at
-                             create with KFBI_ERR_GEOMETRY)                       */
+  KFBI_LS_DISCS = 6,      /* 2D p=[r,n,x1,y1,...]: min_k |x-x_k|^2 - r^2, n discs, one
+                             interface each (close or touching allowed)          */
   KFBI_LS_SPHERES = 7,    /* 3D p=[r,n,x1,y1,z1,...]: the same with balls          */
-  KFBI_LS_GRID = 8        /* 2D or 3D: H known only by its values at the (N+1)^d
+  KFBI_LS_GRID = 8,       /* 2D or 3D: H known only by its values at the (N+1)^d
                              nodes of the problem's grid (kfbi_levelset.samples, a
                              sampled signed distance or any smooth level-set
                              function); between nodes H is the tensor-product
@@ -67,7 +66,27 @@ typedef enum {
                              the point (its cell clamped to [1, N-2] per axis;
                              a coordinate within 1e-10 h of a node is that
                              node, so H at a node is its sample); p unused   */
+  KFBI_LS_UNION = 9       /* 2D or 3D p=[m, kind_1, params_1..., kind_2, ...]: m
+                             interfaces, each of kind ELLIPSE or STAR (5
+                             params) in 2D, ELLIPSOID (6) or TORUS (2) in 3D,
+                             with its own function H_k; Omega = union of the
+                             {H_k < 0}                                         */
 } kfbi_levelset_kind;
+
+/* Several interfaces (KFBI_LS_DISCS, KFBI_LS_SPHERES, KFBI_LS_UNION; the remark
+ * on arbitrarily close interfaces in Sec. 5.2).  Interface k bounds the
+ * component Omega^(k) = {H_k < 0}; every grid node carries a side label, 0
+ * outside Omega and 1 + k in Omega^(k) (a node inside two overlapping
+ * components: the first k with the smallest H_k).  Interfaces may be closer
+ * than the grid step or touch: a grid edge whose end nodes carry labels a != b
+ * holds one DOF on interface a - 1 (if a > 0) and one on b - 1 (if b > 0),
+ * each where that H_k changes sign, the first node's first.  Each interface
+ * has its own correction function C^(k) = u^(k) - u^(0) (Omega^(0) = outside),
+ * fitted from the DOFs of interface k only; a stencil joining labels l_P and
+ * l_Q is corrected with C^(l_P)(Q) - C^(l_Q)(Q) (C^(0) = 0).  Jump data g1, g2
+ * at a DOF are those of its own interface (kfbi_dof_iface).  At most 32
+ * interfaces. */
+#define KFBI_MAX_INTERFACES 32
 
 typedef enum {
   KFBI_DIRICHLET_INTERIOR = 0, /* eq. (bie-D): (1/2 + K) phi = g_D - G f           */
@@ -140,6 +159,10 @@ typedef struct {
   const double* lapf_in;  /* grid  */
   const double* lapf_out; /* grid  */
   const double* g_b;      /* grid (only its box-boundary layer is read) */
+  int in_per_interface;   /* 0: f_in and lapf_in are one grid for every
+                             interface; 1 (several interfaces): each holds one
+                             grid per interface, consecutive, grid k the f of
+                             Omega^(k) smoothly extended to the whole box     */
 } kfbi_data;
 
 typedef struct {
@@ -209,11 +232,25 @@ kfbi_status kfbi_dof_info(const kfbi_problem* p, int32_t* family, int32_t* axis,
 kfbi_status kfbi_stencil_sizes(const kfbi_problem* p, int* n_pde, int* n_dir, int* n_neu);
 kfbi_status kfbi_collocation_stencils(const kfbi_problem* p, int32_t* pde_nodes,
                                       int32_t* dir_dofs, int32_t* neu_dofs);
-/* Node classes (1 = inside Omega), one byte per grid node. */
+/* Node side labels, one byte per grid node: 0 outside Omega, 1 inside (one
+ * interface), 1 + k in Omega^(k) (several interfaces). */
 kfbi_status kfbi_inside_mask(const kfbi_problem* p, uint8_t* mask);
-/* Irregular nodes I_h in linear-index order and the closest primary point of
- * each (Sec. 5.3 partition of unity). */
+/* Irregular nodes I_h (a node of another label in the stencil) in
+ * linear-index order and, with one interface, the closest primary point of
+ * each (Sec. 5.3 partition of unity); with several interfaces owner must be
+ * NULL (see kfbi_correction_entries). */
 kfbi_status kfbi_irregular_nodes(const kfbi_problem* p, int32_t* lin_index, int32_t* owner);
+/* Number of interfaces and of correction entries (the values of
+ * kfbi_correction_values).  One interface: one entry per irregular node. */
+kfbi_status kfbi_interfaces(const kfbi_problem* p, int* n_iface, int* n_entries);
+/* Per DOF: the interface it lies on (device, N_b). */
+kfbi_status kfbi_dof_iface(const kfbi_problem* p, int32_t* iface);
+/* Correction entries (node, interface k) holding C^(k), in node order then k
+ * (device arrays of n_entries): every irregular node for each k + 1 among the
+ * labels of its stencil, and, near another interface, the nodes the trace fits
+ * use (Sec. 5.5); owner = the closest primary point on interface k. */
+kfbi_status kfbi_correction_entries(const kfbi_problem* p, int32_t* lin_index, int32_t* iface,
+                                    int32_t* owner);
 
 /* ---- the four steps of Algorithm 1, Step 3, one at a time -------------- */
 
@@ -222,8 +259,9 @@ kfbi_status kfbi_irregular_nodes(const kfbi_problem* p, int32_t* lin_index, int3
  * at the DOFs; ftilde = f~ = f+/sigma - f-/sigma grid (NULL = 0). */
 kfbi_status kfbi_collocation_fit(kfbi_problem* p, const double* a, const double* b,
                                  const double* ftilde, double* coef);
-/* Correction function C_h at every irregular node (n_irr), eq. (local-cau-prb)
- * with the closest-point partition of unity. */
+/* Correction function C_h at every correction entry (n_entries; one
+ * interface: the irregular nodes), eq. (local-cau-prb) with the closest-point
+ * partition of unity.  ftilde: one grid for every interface. */
 kfbi_status kfbi_correction_values(kfbi_problem* p, const double* a, const double* b,
                                    const double* ftilde, double* cvals);
 /* Step 3.2: right-hand side of eq. (corrected-FDS) on the grid: F + h^2/12 Lap F
@@ -299,7 +337,7 @@ kfbi_status kfbi_evaluate(kfbi_problem* p, const kfbi_data* data, const double* 
  * for other work while a batched call runs (their operator buffers and
  * box-solver scratch are shared).
  * Requirements: at least one problem; all of one kind (Dirichlet or mu-form
- * interface), on one stream, of one dimension, with box_solver KFBI_BOX_DST,
+ * interface), with one interface each, on one stream, of one dimension, with box_solver KFBI_BOX_DST,
  * precision KFBI_MIXED, the same Krylov dimension, and N_b <= 32768 each;
  * otherwise KFBI_ERR_UNSUPPORTED (message on problems[0]).  problems: host
  * array of count handles; *out receives the batch (NULL on failure). */

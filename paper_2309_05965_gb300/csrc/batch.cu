@@ -223,10 +223,11 @@ kfbi_status kfbi_create_batch(kfbi_problem* const* problems, int count, kfbi_bat
     if (p->stream != b->stream || p->g.d != p0->g.d || p->cfg.precision != KFBI_MIXED ||
         (p->cfg.kind != KFBI_DIRICHLET_INTERIOR && p->cfg.kind != KFBI_INTERFACE_MU) ||
         p->cfg.kind != p0->cfg.kind ||
-        p->cfg.box_solver != KFBI_BOX_DST || p->gm.m != b->m || p->nb > 32768)
+        p->cfg.box_solver != KFBI_BOX_DST || p->gm.m != b->m || p->nb > 32768 || p->n_iface != 1)
       return bail(fail(p0, KFBI_ERR_UNSUPPORTED,
                        "a batch needs problems of one kind (Dirichlet or interface), on one stream, of "
-                       "one dimension, with mixed-precision DST box solves and N_b <= 32768"));
+                       "one dimension, with one interface, mixed-precision DST box solves and "
+                       "N_b <= 32768"));
     b->maxnb = std::max(b->maxnb, p->nb);
   }
   std::vector<double*> xs, ys, rhs_data;

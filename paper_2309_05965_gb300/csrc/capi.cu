@@ -117,6 +117,7 @@ static void side_data(const kfbi_data* data, kfbi_data* d1, kfbi_data* d2) {
   memset(d2, 0, sizeof(*d2));
   d1->f_in = data->f_in;
   d1->lapf_in = data->lapf_in;
+  d1->in_per_interface = data->in_per_interface;
   d2->f_out = data->f_out;
   d2->lapf_out = data->lapf_out;
   d2->g_b = data->g_b;
@@ -235,13 +236,41 @@ kfbi_status kfbi_create_problem(const kfbi_config* cfg, const kfbi_levelset* ls,
     fail(p, KFBI_ERR_ARG, "a grid-sampled level set needs its node values (samples)");
     return bail(KFBI_ERR_ARG);
   }
-  if (ls->n_params < 0 || ls->n_params > KFBI_LS_MAX_PARAMS || ls->kind < 1 || ls->kind > 8 ||
-      (!sampled && ls2d != (cfg->dim == 2)) ||
+  const bool uni = ls->kind == KFBI_LS_UNION;
+  if (ls->n_params < 0 || ls->n_params > KFBI_LS_MAX_PARAMS || ls->kind < 1 || ls->kind > 9 ||
+      (!sampled && !uni && ls2d != (cfg->dim == 2)) ||
       (balls && (ls->n_params < 2 || !(ls->p[0] > 0) || ls->p[1] < 1 ||
+                 ls->p[1] > KFBI_MAX_INTERFACES ||
                  2 + cfg->dim * (int)ls->p[1] > ls->n_params))) {
     fail(p, KFBI_ERR_ARG, "level-set kind does not match the dimension");
     return bail(KFBI_ERR_ARG);
   }
+  int n_iface = balls ? (int)ls->p[1] : 1;
+  if (uni) {
+    // m components, each a kind code and that kind's parameters
+    bool ok = ls->n_params >= 1 && ls->p[0] >= 1 && ls->p[0] <= KFBI_MAX_INTERFACES;
+    int at = 1;
+    n_iface = ok ? (int)ls->p[0] : 0;
+    for (int k = 0; ok && k < n_iface; ++k) {
+      if (at >= ls->n_params) {
+        ok = false;
+        break;
+      }
+      const int kind = (int)ls->p[at];
+      int cnt = 0;
+      if (cfg->dim == 2 && (kind == KFBI_LS_ELLIPSE || kind == KFBI_LS_STAR)) cnt = 5;
+      if (cfg->dim == 3 && kind == KFBI_LS_ELLIPSOID) cnt = 6;
+      if (cfg->dim == 3 && kind == KFBI_LS_TORUS) cnt = 2;
+      ok = cnt > 0 && at + 1 + cnt <= ls->n_params;
+      at += 1 + cnt;
+    }
+    if (!ok) {
+      fail(p, KFBI_ERR_ARG, "union level set: m in [1, 32] components of ellipse/star (2D) or "
+                            "ellipsoid/torus (3D) with their parameters");
+      return bail(KFBI_ERR_ARG);
+    }
+  }
+  p->n_iface = n_iface;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     fail(p, KFBI_ERR_CUDA, "no CUDA device");
@@ -312,13 +341,13 @@ kfbi_status kfbi_create_problem(const kfbi_config* cfg, const kfbi_levelset* ls,
       return bail(s);
     }
     p->twin->parent = p;
-    if (p->twin->nb != p->nb || p->twin->nirr != p->nirr) {
+    if (p->twin->nb != p->nb || p->twin->nirr != p->nirr || p->twin->nent != p->nent) {
       fail(p, KFBI_ERR_GEOMETRY, "the two side operators set up different DOFs");
       return bail(KFBI_ERR_GEOMETRY);
     }
   }
   const long long nodes = p->g.nodes();
-  if (dalloc(&p->cvals, p->nirr) != cudaSuccess || dalloc(&p->rhs, nodes) != cudaSuccess ||
+  if (dalloc(&p->cvals, p->nent) != cudaSuccess || dalloc(&p->rhs, nodes) != cudaSuccess ||
       dalloc(&p->ugrid, nodes) != cudaSuccess || dalloc(&p->tvals, p->nb) != cudaSuccess ||
       dalloc(&p->bvec, p->nx) != cudaSuccess || dalloc(&p->xbuf, p->nx) != cudaSuccess ||
       dalloc(&p->ybuf, p->nx) != cudaSuccess ||
@@ -354,8 +383,9 @@ kfbi_status kfbi_destroy_problem(kfbi_problem* p) {
   if (p->ybuf) cudaFree(p->ybuf);
   if (p->gen) cudaFree(p->gen);
   void* bufs[] = {p->inside, p->irr_flag, p->family, p->edge, p->axis, p->st_axis, p->pde_node,
-                  p->dir_idx, p->neu_idx, p->minv, p->irr_lin, p->irr_owner, p->irr_inside,
-                  p->irr_w, p->corr_nb, p->nb_off, p->nb_coef, p->cvals, p->coef, p->rhs,
+                  p->dir_idx, p->neu_idx, p->minv, p->irr_lin, p->irr_inside, p->dof_iface,
+                  p->ent_lin, p->ent_iface, p->ent_owner, p->ent_w, p->corr_nb, p->corr_nb2,
+                  p->nb_off, p->nb_coef, p->cvals, p->coef, p->rhs,
                   p->ugrid, p->tvals, p->ftilde, p->bvec, p->zero_nb, p->d_flags, p->stencil_dev};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -368,6 +398,7 @@ kfbi_status kfbi_destroy_problem(kfbi_problem* p) {
   if (p->tr[0].node) {
     cudaFree(p->tr[0].node);
     cudaFree(p->tr[0].irr);
+    if (p->tr[0].irr2) cudaFree(p->tr[0].irr2);
     cudaFree(p->tr[0].wv);
     cudaFree(p->tr[0].wn);
     cudaFree(p->tr[0].w);
@@ -460,9 +491,37 @@ kfbi_status kfbi_inside_mask(const kfbi_problem* pc, uint8_t* mask) {
 kfbi_status kfbi_irregular_nodes(const kfbi_problem* pc, int32_t* lin_index, int32_t* owner) {
   kfbi_problem* p = const_cast<kfbi_problem*>(pc);
   if (!p) return KFBI_ERR_ARG;
+  if (owner && p->n_iface > 1) return fail(p, KFBI_ERR_ARG, "several interfaces: owner must be NULL");
   size_t bytes = sizeof(int32_t) * p->nirr;
   if (lin_index) KFBI_CUDA(p, cudaMemcpyAsync(lin_index, p->irr_lin, bytes, cudaMemcpyDeviceToDevice, p->stream));
-  if (owner) KFBI_CUDA(p, cudaMemcpyAsync(owner, p->irr_owner, bytes, cudaMemcpyDeviceToDevice, p->stream));
+  // one interface: entry q is irregular node q
+  if (owner) KFBI_CUDA(p, cudaMemcpyAsync(owner, p->ent_owner, bytes, cudaMemcpyDeviceToDevice, p->stream));
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_interfaces(const kfbi_problem* p, int* n_iface, int* n_entries) {
+  if (!p) return KFBI_ERR_ARG;
+  if (n_iface) *n_iface = p->n_iface;
+  if (n_entries) *n_entries = p->nent;
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_dof_iface(const kfbi_problem* pc, int32_t* iface) {
+  kfbi_problem* p = const_cast<kfbi_problem*>(pc);
+  if (!p || !iface) return KFBI_ERR_ARG;
+  KFBI_CUDA(p, cudaMemcpyAsync(iface, p->dof_iface, sizeof(int32_t) * p->nb, cudaMemcpyDeviceToDevice,
+                               p->stream));
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_correction_entries(const kfbi_problem* pc, int32_t* lin_index, int32_t* iface,
+                                    int32_t* owner) {
+  kfbi_problem* p = const_cast<kfbi_problem*>(pc);
+  if (!p) return KFBI_ERR_ARG;
+  const size_t bytes = sizeof(int32_t) * p->nent;
+  if (lin_index) KFBI_CUDA(p, cudaMemcpyAsync(lin_index, p->ent_lin, bytes, cudaMemcpyDeviceToDevice, p->stream));
+  if (iface) KFBI_CUDA(p, cudaMemcpyAsync(iface, p->ent_iface, bytes, cudaMemcpyDeviceToDevice, p->stream));
+  if (owner) KFBI_CUDA(p, cudaMemcpyAsync(owner, p->ent_owner, bytes, cudaMemcpyDeviceToDevice, p->stream));
   return KFBI_OK;
 }
 

@@ -15,17 +15,20 @@ namespace kfbi {
 namespace {
 
 // C(q) = sum_j W[j][q] Q_j, Q = [h^2 f~(PDE nodes); a(Dirichlet DOFs); h b(Neumann DOFs)]
-// of the owner's collocation system (eq. (cau-ls)).  f~ = fa/sa - fb/sb at the
-// PDE nodes (either pointer may be null).
+// of the owner's collocation system (eq. (cau-ls)), one thread per correction
+// entry.  f~ = fa/sa - fb/sb at the PDE nodes (either pointer may be null);
+// fa holds one grid per interface when fstride > 0 (the entry's interface's).
 __global__ void k_cvals(int nirr, int npde, int ndir, int nneu, double h,
                         const int32_t* __restrict__ owner, const double* __restrict__ W,
                         const int32_t* __restrict__ pde_node, const int32_t* __restrict__ dir_idx,
                         const int32_t* __restrict__ neu_idx, const double* __restrict__ a,
                         const double* __restrict__ b, const double* __restrict__ fa, double sa,
-                        const double* __restrict__ fb, double sb, double* __restrict__ out) {
+                        const double* __restrict__ fb, double sb, double* __restrict__ out,
+                        const int32_t* __restrict__ eiface, long long fstride) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nirr) return;
   int i = owner[q];
+  if (fa && fstride) fa += eiface[q] * fstride;
   double acc = 0.0;
   int j = 0;
   if (fa != nullptr || fb != nullptr) {
@@ -93,7 +96,7 @@ __global__ void k_rhs_source(Grid g, int order, const uint8_t* __restrict__ insi
                              const double* __restrict__ li, const double* __restrict__ lo_,
                              double rsi, double rso, double h2_12, const double* __restrict__ gb,
                              const double* __restrict__ nbc, const int8_t* __restrict__ nboff,
-                             int nnb, double* __restrict__ R) {
+                             int nnb, double* __restrict__ R, long long fstride) {
   const int tot = (int)g.nodes();
   const int n1 = g.n + 1;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
@@ -115,9 +118,12 @@ __global__ void k_rhs_source(Grid g, int order, const uint8_t* __restrict__ insi
       continue;
     }
     double v = 0.0;
-    bool in = inside[t] != 0;
-    const double* F = in ? fi : fo;
-    const double* Lp = in ? li : lo_;
+    const int lab = inside[t];
+    const bool in = lab != 0;
+    // f of the node's own side (of its interface's component with fstride > 0)
+    const long long off = in ? (long long)(lab - 1) * fstride : 0;
+    const double* F = in ? (fi ? fi + off : nullptr) : fo;
+    const double* Lp = in ? (li ? li + off : nullptr) : lo_;
     const double rs = in ? rsi : rso;
     if (F) v = F[t] * rs;
     if (order == 4 && Lp) v = v + h2_12 * (Lp[t] * rs);
@@ -160,7 +166,44 @@ __global__ void k_rhs_correct(int nirr, int nnb, const int32_t* __restrict__ lin
   R[t] = add ? R[t] + c : c;
 }
 
+// Several interfaces: R[P] += -sum_{l_Q != l_P} c (C^(l_P)(Q) - C^(l_Q)(Q)),
+// i.e. + c C^(l_Q)(Q) - c C^(l_P)(Q) with C^(0) = 0 (entries -1).
+__global__ void k_rhs_correct_multi(int nirr, int nnb, const int32_t* __restrict__ lin,
+                                    const int32_t* __restrict__ corr_a,
+                                    const int32_t* __restrict__ corr_b,
+                                    const double* __restrict__ nbc, const double* __restrict__ cv,
+                                    double* __restrict__ R) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nirr) return;
+  double acc = 0.0;
+  for (int s = 0; s < nnb; ++s) {
+    const int ja = corr_a[(size_t)s * nirr + q];
+    const int jb = corr_b[(size_t)s * nirr + q];
+    if (ja >= 0 || jb >= 0) acc += nbc[s] * ((ja >= 0 ? cv[ja] : 0.0) - (jb >= 0 ? cv[jb] : 0.0));
+  }
+  R[lin[q]] += acc;
+}
+
+// The corrected datum of trace stencil entry e: one interface, u +- C across
+// Gamma (sg = +1 on the '+' side, -1 on the '-' side); several interfaces
+// u + (C^(t) - C^(l_q)) across, C^(0) = 0.
+template <bool MULTI>
+__device__ __forceinline__ double trace_datum(const TraceCSR& T, int e, double sg,
+                                              const double* __restrict__ u,
+                                              const double* __restrict__ cv) {
+  double w = u[T.node[e]];
+  const int j = T.irr[e];
+  if (!MULTI) {
+    if (j >= 0) w += sg * cv[j];
+  } else {
+    const int j2 = T.irr2[e];
+    if (j >= 0 || j2 >= 0) w += (j >= 0 ? cv[j] : 0.0) - (j2 >= 0 ? cv[j2] : 0.0);
+  }
+  return w;
+}
+
 // Four one-sided traces (stage output), one warp per DOF.
+template <bool MULTI>
 __global__ void k_traces4(int nb, TraceCSR tp, TraceCSR tm, const double* __restrict__ u,
                           const double* __restrict__ cv, double* vp, double* vm, double* dp,
                           double* dm) {
@@ -173,9 +216,7 @@ __global__ void k_traces4(int nb, TraceCSR tp, TraceCSR tm, const double* __rest
     double sg = side == 0 ? 1.0 : -1.0;
     double a = 0.0, b = 0.0;
     for (int e = T.ptr[i] + lane; e < T.ptr[i + 1]; e += 32) {
-      double w = u[T.node[e]];
-      int j = T.irr[e];
-      if (j >= 0) w += sg * cv[j];
+      const double w = trace_datum<MULTI>(T, e, sg, u, cv);
       a += T.wv[e] * w;
       b += T.wn[e] * w;
     }
@@ -193,6 +234,7 @@ __global__ void k_traces4(int nb, TraceCSR tp, TraceCSR tm, const double* __rest
 // The operator's trace quantity t (average value for the Dirichlet form,
 // average normal derivative for the mu-form; weights carry the 1/2) fused with
 // the BIE combination y = alpha x + beta t.
+template <bool MULTI>
 __global__ void k_trace_op(int nb, TraceCSR tp, TraceCSR tm, const double* __restrict__ u,
                            const double* __restrict__ cv, const double* __restrict__ x,
                            double alpha, double beta, double* __restrict__ y) {
@@ -200,18 +242,10 @@ __global__ void k_trace_op(int nb, TraceCSR tp, TraceCSR tm, const double* __res
   int lane = threadIdx.x & 31;
   if (i >= nb) return;
   double acc = 0.0;
-  for (int e = tp.ptr[i] + lane; e < tp.ptr[i + 1]; e += 32) {
-    double w = u[tp.node[e]];
-    int j = tp.irr[e];
-    if (j >= 0) w += cv[j];
-    acc += tp.w[e] * w;
-  }
-  for (int e = tm.ptr[i] + lane; e < tm.ptr[i + 1]; e += 32) {
-    double w = u[tm.node[e]];
-    int j = tm.irr[e];
-    if (j >= 0) w -= cv[j];
-    acc += tm.w[e] * w;
-  }
+  for (int e = tp.ptr[i] + lane; e < tp.ptr[i + 1]; e += 32)
+    acc += tp.w[e] * trace_datum<MULTI>(tp, e, 1.0, u, cv);
+  for (int e = tm.ptr[i] + lane; e < tm.ptr[i + 1]; e += 32)
+    acc += tm.w[e] * trace_datum<MULTI>(tm, e, -1.0, u, cv);
   acc = warp_sum(acc);
   if (lane == 0) y[i] = (x ? alpha * x[i] : 0.0) + beta * acc;
 }
@@ -295,11 +329,16 @@ __global__ void k_set_boundary(Grid g, const double* __restrict__ gb, double* __
 
 }  // namespace
 
+// Grid stride between the per-interface f_in grids of the data (0: one grid).
+static long long in_stride(const kfbi_problem* p, const kfbi_data* data) {
+  return data && data->in_per_interface && p->n_iface > 1 ? p->g.nodes() : 0;
+}
+
 kfbi_status launch_correction_values(kfbi_problem* p, const double* a, const double* b,
                                      const double* ftilde, double* cvals) {
-  KFBI_LAUNCH(p, KFBI_KC_CORRECTION, k_cvals<<<div_up(p->nirr, 128), 128, 0, p->stream>>>(
-      p->nirr, p->npde, p->ndir, p->nneu, p->g.h, p->irr_owner, p->irr_w, p->pde_node,
-      p->dir_idx, p->neu_idx, a, b, ftilde, 1.0, nullptr, 1.0, cvals));
+  KFBI_LAUNCH(p, KFBI_KC_CORRECTION, k_cvals<<<div_up(p->nent, 128), 128, 0, p->stream>>>(
+      p->nent, p->npde, p->ndir, p->nneu, p->g.h, p->ent_owner, p->ent_w, p->pde_node,
+      p->dir_idx, p->neu_idx, a, b, ftilde, 1.0, nullptr, 1.0, cvals, p->ent_iface, 0));
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
 }
@@ -311,9 +350,10 @@ kfbi_status launch_correction_values_data(kfbi_problem* p, const double* a, cons
   const double* fo = data ? data->f_out : nullptr;
   double so = interior_bvp(p) ? 1.0 : p->cfg.sigma_out;
   if (interior_bvp(p)) fo = nullptr;
-  KFBI_LAUNCH(p, KFBI_KC_CORRECTION, k_cvals<<<div_up(p->nirr, 128), 128, 0, p->stream>>>(
-      p->nirr, p->npde, p->ndir, p->nneu, p->g.h, p->irr_owner, p->irr_w, p->pde_node,
-      p->dir_idx, p->neu_idx, a, b, fi, p->cfg.sigma_in, fo, so, cvals));
+  KFBI_LAUNCH(p, KFBI_KC_CORRECTION, k_cvals<<<div_up(p->nent, 128), 128, 0, p->stream>>>(
+      p->nent, p->npde, p->ndir, p->nneu, p->g.h, p->ent_owner, p->ent_w, p->pde_node,
+      p->dir_idx, p->neu_idx, a, b, fi, p->cfg.sigma_in, fo, so, cvals, p->ent_iface,
+      in_stride(p, data)));
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
 }
@@ -361,12 +401,16 @@ kfbi_status launch_rhs(kfbi_problem* p, const double* cvals, const kfbi_data* da
     double so = interior_bvp(p) ? 1.0 : p->cfg.sigma_out;
     KFBI_LAUNCH(p, KFBI_KC_RHS, k_rhs_source<<<std::min(div_up(g.nodes(), 256), 152 * 32), 256, 0, p->stream>>>(
         g, p->cfg.order, p->inside, fi, fo, li, lo_, 1.0 / p->cfg.sigma_in, 1.0 / so, g.h * g.h / 12.0,
-        interior_bvp(p) ? nullptr : data->g_b, d_nbc, d_off, p->n_nb, rhs));
+        interior_bvp(p) ? nullptr : data->g_b, d_nbc, d_off, p->n_nb, rhs, in_stride(p, data)));
     KFBI_CUDA(p, cudaGetLastError());
   } else {
     KFBI_CUDA(p, cudaMemsetAsync(rhs, 0, sizeof(double) * g.nodes(), p->stream));
   }
-  if (cvals) {
+  if (cvals && p->n_iface > 1) {
+    KFBI_LAUNCH(p, KFBI_KC_RHS, k_rhs_correct_multi<<<div_up(p->nirr, 128), 128, 0, p->stream>>>(
+        p->nirr, p->n_nb, p->irr_lin, p->corr_nb, p->corr_nb2, d_nbc, cvals, rhs));
+    KFBI_CUDA(p, cudaGetLastError());
+  } else if (cvals) {
     KFBI_LAUNCH(p, KFBI_KC_RHS, k_rhs_correct<<<div_up(p->nirr, 128), 128, 0, p->stream>>>(
         p->nirr, p->n_nb, p->irr_lin, p->irr_inside, p->corr_nb, d_nbc, cvals, rhs, 1));
     KFBI_CUDA(p, cudaGetLastError());
@@ -376,16 +420,24 @@ kfbi_status launch_rhs(kfbi_problem* p, const double* cvals, const kfbi_data* da
 
 kfbi_status launch_traces(kfbi_problem* p, const double* u, const double* cvals, double* vp,
                           double* vm, double* dp, double* dm) {
-  KFBI_LAUNCH(p, KFBI_KC_TRACE, k_traces4<<<div_up(p->nb, 8), 256, 0, p->stream>>>(p->nb, p->tr[0], p->tr[1], u, cvals, vp, vm,
-                                                      dp, dm));
+  if (p->n_iface > 1)
+    KFBI_LAUNCH(p, KFBI_KC_TRACE, k_traces4<true><<<div_up(p->nb, 8), 256, 0, p->stream>>>(
+        p->nb, p->tr[0], p->tr[1], u, cvals, vp, vm, dp, dm));
+  else
+    KFBI_LAUNCH(p, KFBI_KC_TRACE, k_traces4<false><<<div_up(p->nb, 8), 256, 0, p->stream>>>(
+        p->nb, p->tr[0], p->tr[1], u, cvals, vp, vm, dp, dm));
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
 }
 
 kfbi_status launch_operator_trace(kfbi_problem* p, const double* u, const double* cvals,
                                   const double* x, double alpha_x, double beta_t, double* y) {
-  KFBI_LAUNCH(p, KFBI_KC_TRACE, k_trace_op<<<div_up(p->nb, 8), 256, 0, p->stream>>>(p->nb, p->tr[0], p->tr[1], u, cvals, x,
-                                                       alpha_x, beta_t, y));
+  if (p->n_iface > 1)
+    KFBI_LAUNCH(p, KFBI_KC_TRACE, k_trace_op<true><<<div_up(p->nb, 8), 256, 0, p->stream>>>(
+        p->nb, p->tr[0], p->tr[1], u, cvals, x, alpha_x, beta_t, y));
+  else
+    KFBI_LAUNCH(p, KFBI_KC_TRACE, k_trace_op<false><<<div_up(p->nb, 8), 256, 0, p->stream>>>(
+        p->nb, p->tr[0], p->tr[1], u, cvals, x, alpha_x, beta_t, y));
   KFBI_CUDA(p, cudaGetLastError());
   return KFBI_OK;
 }
@@ -583,7 +635,9 @@ kfbi_status batch_hot_create(kfbi_problem* p0, kfbi_problem* const* ps, int nins
   for (int k = 0; k < ninst; ++k) {
     kfbi_problem* p = ps[k];
     const bool dir = p->cfg.kind == KFBI_DIRICHLET_INTERIOR;
-    cv[k] = CvDesc{p->nirr, p->npde, p->ndir, p->nneu, p->g.h, p->irr_owner, p->irr_w,
+    // one interface per instance (checked at batch creation): entry q is
+    // irregular node q, so one prefix array serves both item kinds
+    cv[k] = CvDesc{p->nent, p->npde, p->ndir, p->nneu, p->g.h, p->ent_owner, p->ent_w,
                    p->dir_idx, p->neu_idx, dir ? x[k] : nullptr, dir ? nullptr : x[k], p->cvals};
     co[k] = CorrDesc{p->nirr, p->n_nb, p->irr_lin, p->irr_inside, p->corr_nb, p->nb_coef, p->cvals, rhs[k]};
     tr[k] = TrDesc{p->nb, p->tr[0], p->tr[1], p->ugrid, p->cvals, x[k], 0.5, dir ? 1.0 : -p->mu, y[k]};

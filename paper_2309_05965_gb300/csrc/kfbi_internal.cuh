@@ -6,7 +6,8 @@
 //   DOF arrays       structure of arrays, length N_b, DOF order of kfbi.h
 //   per-DOF blocks   row-major [N_b][k] (stencils, collocation inverses)
 //   per-irregular    column-major [k][n_irr] so that one thread per node reads
-//                    coalesced (composite collocation rows, correction lists)
+//                    coalesced (correction lists); per-entry the same
+//                    [k][n_entries] (composite collocation rows)
 //   trace weights    CSR over DOFs, one CSR per side (+, -)
 #pragma once
 
@@ -38,8 +39,8 @@ enum SetupFlag : int {
   kFlagSingular = 1,      // first DOF with a singular collocation matrix (+1)
   kFlagTraceSingular = 2, // first DOF with a singular trace fit (+1)
   kFlagOutOfBox = 3,      // a stencil left the grid (+1)
-  kFlagClosestFallback = 4,  // count of irregular nodes that needed the global search
-  kFlagMultiCross = 5,    // first grid node whose compact stencil spans two interfaces (+1)
+  kFlagClosestFallback = 4,  // count of correction entries that needed the global search
+  kFlagNoOwner = 5,       // first correction entry whose interface has no DOF (+1)
   kFlagCount = 8
 };
 
@@ -68,7 +69,11 @@ struct LevelSet {
 struct TraceCSR {
   int32_t* ptr = nullptr;    // N_b + 1
   int32_t* node = nullptr;   // grid linear index
-  int32_t* irr = nullptr;    // irregular index when the node is across Gamma, else -1
+  // correction entry added to the node's value, -1 if none: one interface,
+  // the node's entry when it lies across Gamma (+C on the '+' side, -C on the
+  // '-' side); several interfaces, C^(t) of the side's label t
+  int32_t* irr = nullptr;
+  int32_t* irr2 = nullptr;   // several interfaces: C^(l_q) subtracted, -1 if none
   double* wv = nullptr;      // value weights
   double* wn = nullptr;      // normal-derivative weights
   double* w = nullptr;       // weights of the operator's own trace quantity
@@ -138,6 +143,8 @@ struct kfbi_problem {
   int nb = 0;
   double* x[3] = {nullptr, nullptr, nullptr};
   double* nrm[3] = {nullptr, nullptr, nullptr};
+  int n_iface = 1;               // interfaces (side labels 1..n_iface)
+  int32_t* dof_iface = nullptr;  // [N_b] interface of each DOF
   int32_t* family = nullptr;
   int32_t* edge = nullptr;
   int32_t* axis = nullptr;
@@ -152,13 +159,21 @@ struct kfbi_problem {
   int32_t* neu_idx = nullptr;    // [N_b][nneu]
   double* minv = nullptr;        // [N_b][ncoef][ncoef], row-major M^{-1}
 
-  // irregular nodes
+  // irregular nodes (the rows of the correction terms)
   int nirr = 0;
   int32_t* irr_lin = nullptr;    // [n_irr]
-  int32_t* irr_owner = nullptr;  // [n_irr]
-  uint8_t* irr_inside = nullptr; // [n_irr]
-  double* irr_w = nullptr;       // [ncoef][n_irr] composite rows phi(xi)^T M^{-1}
-  int32_t* corr_nb = nullptr;    // [n_nb][n_irr] irregular index of an other-side neighbour or -1
+  uint8_t* irr_inside = nullptr; // [n_irr] side label
+  // correction entries (node, interface k) holding C^(k); one interface: one
+  // per irregular node, entry q = irregular node q
+  int nent = 0;
+  int32_t* ent_lin = nullptr;    // [n_ent]
+  int32_t* ent_iface = nullptr;  // [n_ent]
+  int32_t* ent_owner = nullptr;  // [n_ent] closest primary point on interface k
+  double* ent_w = nullptr;       // [ncoef][n_ent] composite rows phi(xi)^T M^{-1}
+  // [n_nb][n_irr] one interface: entry of an other-side neighbour or -1
+  // (C_P = -+ sum c C); several interfaces: entry of C^(l_Q)(Q) (+c)
+  int32_t* corr_nb = nullptr;
+  int32_t* corr_nb2 = nullptr;   // several interfaces: entry of C^(l_P)(Q) (-c), or -1
   int n_nb = 0;
   int8_t* nb_off = nullptr;      // [n_nb][3] neighbour offsets (setup enumeration order)
   double* nb_coef = nullptr;     // [n_nb] stencil coefficient c of each neighbour
@@ -168,7 +183,7 @@ struct kfbi_problem {
 
   // box solver + work
   kfbi::BoxSolver* box = nullptr;
-  double* cvals = nullptr;       // [n_irr]
+  double* cvals = nullptr;       // [n_ent]
   double* coef = nullptr;        // [N_b][ncoef] (stage output scratch)
   double* rhs = nullptr;         // grid
   double* ugrid = nullptr;       // grid

@@ -106,17 +106,10 @@ __device__ inline double ls_sampled(const LevelSet& L, const double* X, double* 
   return val;
 }
 
-__device__ inline double ls_H(const LevelSet& L, const double* X) {
-  const double* p = L.p;
-  switch (L.kind) {
-    case KFBI_LS_GRID:
-      return ls_sampled(L, X, nullptr);
-    case KFBI_LS_DISCS:
-    case KFBI_LS_SPHERES: {
-      double v;
-      ls_nearest_ball(p, L.kind == KFBI_LS_DISCS ? 2 : 3, X, &v);
-      return v;
-    }
+// H of the analytic kinds (the components a union is made of, and the
+// one-interface kinds)
+__device__ inline double ls_H_kind(int kind, const double* p, const double* X) {
+  switch (kind) {
     case KFBI_LS_ELLIPSE: {
       double x = X[0] - p[0], y = X[1] - p[1];
       double c = cos(p[4]), s = sin(p[4]);
@@ -142,7 +135,7 @@ __device__ inline double ls_H(const LevelSet& L, const double* X) {
       return t * t + X[2] * X[2] - p[1] * p[1];
     }
     case KFBI_LS_MOLECULE: {
-      double r = p[0], level = p[1];
+      const double r = p[0], level = p[1];
       int na = static_cast<int>(p[2]);
       double acc = 0.0;
       for (int k = 0; k < na; ++k) {
@@ -155,22 +148,8 @@ __device__ inline double ls_H(const LevelSet& L, const double* X) {
   return 0.0;
 }
 
-__device__ inline void ls_grad(const LevelSet& L, const double* X, double* g) {
-  const double* p = L.p;
-  switch (L.kind) {
-    case KFBI_LS_GRID:
-      ls_sampled(L, X, g);
-      return;
-    case KFBI_LS_DISCS:
-    case KFBI_LS_SPHERES: {
-      const int d = L.kind == KFBI_LS_DISCS ? 2 : 3;
-      double v;
-      const double* c = p + 2 + d * ls_nearest_ball(p, d, X, &v);
-      g[0] = 2.0 * (X[0] - c[0]);
-      g[1] = 2.0 * (X[1] - c[1]);
-      g[2] = d == 3 ? 2.0 * (X[2] - c[2]) : 0.0;
-      return;
-    }
+__device__ inline void ls_grad_kind(int kind, const double* p, const double* X, double* g) {
+  switch (kind) {
     case KFBI_LS_ELLIPSE: {
       double x = X[0] - p[0], y = X[1] - p[1];
       double c = cos(p[4]), s = sin(p[4]);
@@ -223,6 +202,153 @@ __device__ inline void ls_grad(const LevelSet& L, const double* X, double* g) {
     }
   }
   g[0] = g[1] = g[2] = 0.0;
+}
+
+// ---- several interfaces (the remark on arbitrarily close interfaces,
+// Sec. 5.2): interface k has its own function H_k; Omega^(k) = {H_k < 0}.
+__device__ inline int ls_union_count(int kind) {
+  switch (kind) {
+    case KFBI_LS_ELLIPSE:
+    case KFBI_LS_STAR:
+      return 5;
+    case KFBI_LS_ELLIPSOID:
+      return 6;
+    case KFBI_LS_TORUS:
+      return 2;
+  }
+  return 0;
+}
+
+// component k of a union: its kind and parameters
+__device__ inline const double* ls_union_comp(const double* p, int k, int* kind) {
+  int at = 1;
+  for (int j = 0; j < k; ++j) at += 1 + ls_union_count(static_cast<int>(p[at]));
+  *kind = static_cast<int>(p[at]);
+  return p + at + 1;
+}
+
+// the first component with the smallest H_k, and that value
+__device__ inline int ls_union_argmin(const double* p, const double* X, double* val) {
+  const int m = static_cast<int>(p[0]);
+  int best = 0, at = 1;
+  double bv = 0.0;
+  for (int k = 0; k < m; ++k) {
+    const int kind = static_cast<int>(p[at]);
+    const double v = ls_H_kind(kind, p + at + 1, X);
+    if (k == 0 || v < bv) {
+      bv = v;
+      best = k;
+    }
+    at += 1 + ls_union_count(kind);
+  }
+  *val = bv;
+  return best;
+}
+
+__device__ inline int ls_n_iface(const LevelSet& L) {
+  if (L.kind == KFBI_LS_DISCS || L.kind == KFBI_LS_SPHERES) return static_cast<int>(L.p[1]);
+  if (L.kind == KFBI_LS_UNION) return static_cast<int>(L.p[0]);
+  return 1;
+}
+
+__device__ inline double ls_H(const LevelSet& L, const double* X) {
+  switch (L.kind) {
+    case KFBI_LS_GRID:
+      return ls_sampled(L, X, nullptr);
+    case KFBI_LS_DISCS:
+    case KFBI_LS_SPHERES: {
+      double v;
+      ls_nearest_ball(L.p, L.kind == KFBI_LS_DISCS ? 2 : 3, X, &v);
+      return v;
+    }
+    case KFBI_LS_UNION: {
+      double v;
+      ls_union_argmin(L.p, X, &v);
+      return v;
+    }
+  }
+  return ls_H_kind(L.kind, L.p, X);
+}
+
+__device__ inline void ls_grad(const LevelSet& L, const double* X, double* g) {
+  const double* p = L.p;
+  switch (L.kind) {
+    case KFBI_LS_GRID:
+      ls_sampled(L, X, g);
+      return;
+    case KFBI_LS_DISCS:
+    case KFBI_LS_SPHERES: {
+      const int d = L.kind == KFBI_LS_DISCS ? 2 : 3;
+      double v;
+      const double* c = p + 2 + d * ls_nearest_ball(p, d, X, &v);
+      g[0] = 2.0 * (X[0] - c[0]);
+      g[1] = 2.0 * (X[1] - c[1]);
+      g[2] = d == 3 ? 2.0 * (X[2] - c[2]) : 0.0;
+      return;
+    }
+    case KFBI_LS_UNION: {
+      double v;
+      int kind;
+      const double* q = ls_union_comp(p, ls_union_argmin(p, X, &v), &kind);
+      ls_grad_kind(kind, q, X, g);
+      return;
+    }
+  }
+  ls_grad_kind(L.kind, p, X, g);
+}
+
+// side label of a point: 0 outside Omega, 1 + k in Omega^(k) (for a point
+// in two overlapping components, the first with the smallest H_k)
+__device__ inline int ls_label(const LevelSet& L, const double* X) {
+  double v;
+  int k = 0;
+  if (L.kind == KFBI_LS_DISCS || L.kind == KFBI_LS_SPHERES)
+    k = ls_nearest_ball(L.p, L.kind == KFBI_LS_DISCS ? 2 : 3, X, &v);
+  else if (L.kind == KFBI_LS_UNION)
+    k = ls_union_argmin(L.p, X, &v);
+  else
+    v = ls_H(L, X);
+  return v < 0.0 ? k + 1 : 0;
+}
+
+// H_k of interface k alone (the arithmetic of ls_nearest_ball for a ball)
+__device__ inline double ls_H_iface(const LevelSet& L, int k, const double* X) {
+  if (L.kind == KFBI_LS_DISCS || L.kind == KFBI_LS_SPHERES) {
+    const int d = L.kind == KFBI_LS_DISCS ? 2 : 3;
+    const double r = L.p[0];
+    const double* c = L.p + 2 + d * k;
+    const double dx = X[0] - c[0], dy = X[1] - c[1];
+    double v = dx * dx + dy * dy;
+    if (d == 3) {
+      const double dz = X[2] - c[2];
+      v = v + dz * dz;
+    }
+    return v - r * r;
+  }
+  if (L.kind == KFBI_LS_UNION) {
+    int kind;
+    const double* q = ls_union_comp(L.p, k, &kind);
+    return ls_H_kind(kind, q, X);
+  }
+  return ls_H(L, X);
+}
+
+__device__ inline void ls_grad_iface(const LevelSet& L, int k, const double* X, double* g) {
+  if (L.kind == KFBI_LS_DISCS || L.kind == KFBI_LS_SPHERES) {
+    const int d = L.kind == KFBI_LS_DISCS ? 2 : 3;
+    const double* c = L.p + 2 + d * k;
+    g[0] = 2.0 * (X[0] - c[0]);
+    g[1] = 2.0 * (X[1] - c[1]);
+    g[2] = d == 3 ? 2.0 * (X[2] - c[2]) : 0.0;
+    return;
+  }
+  if (L.kind == KFBI_LS_UNION) {
+    int kind;
+    const double* q = ls_union_comp(L.p, k, &kind);
+    ls_grad_kind(kind, q, X, g);
+    return;
+  }
+  ls_grad(L, X, g);
 }
 
 }  // namespace kfbi

@@ -78,7 +78,8 @@ __global__ void k_exclusive_scan(const int32_t* __restrict__ in, int32_t* __rest
 }
 
 // ---------------------------------------------------------------------------
-// Classification (Sec. 5.2): inside iff H(node) < 0.
+// Classification (Sec. 5.2): inside iff H(node) < 0, stored as the node's side
+// label (0 outside, 1 + k in Omega^(k); 1 inside for one interface).
 // ---------------------------------------------------------------------------
 __global__ void k_classify(Grid g, LevelSet L, uint8_t* __restrict__ inside) {
   long long tot = g.nodes();
@@ -87,7 +88,7 @@ __global__ void k_classify(Grid g, LevelSet L, uint8_t* __restrict__ inside) {
     int idx[3];
     node_multi(g, t, idx);
     double X[3] = {coord(g, idx[0]), coord(g, idx[1]), g.d == 3 ? coord(g, idx[2]) : 0.0};
-    inside[t] = ls_H(L, X) < 0.0 ? 1 : 0;
+    inside[t] = (uint8_t)ls_label(L, X);
   }
 }
 
@@ -110,15 +111,16 @@ __device__ __forceinline__ void line_other(const Grid& g, const LineDesc& D, int
   }
 }
 
-// Root of H on the edge [x0, x0 + h e_r]: start at the linear interpolant,
-// Newton step, bisection whenever Newton leaves the bracket or df = 0, stop at
-// |ds| <= 1e-15 h or after 64 steps.
-__device__ double edge_root(const Grid& g, const LevelSet& L, const double* x0, int r, int j) {
+// Root of H_k (interface k) on the edge [x0, x0 + h e_r]: start at the
+// linear interpolant, Newton step, bisection whenever Newton leaves the
+// bracket or df = 0, stop at |ds| <= 1e-15 h or after 64 steps.
+__device__ double edge_root(const Grid& g, const LevelSet& L, int k, const double* x0, int r,
+                            int j) {
   double xa[3] = {x0[0], x0[1], x0[2]};
   double xb[3] = {x0[0], x0[1], x0[2]};
   xa[r] = coord(g, j);
   xb[r] = coord(g, j + 1);
-  double ha = ls_H(L, xa), hb = ls_H(L, xb);
+  double ha = ls_H_iface(L, k, xa), hb = ls_H_iface(L, k, xb);
   bool neg_a = ha < 0.0;
   double h = g.h;
   double s = h * ha / (ha - hb);
@@ -126,9 +128,9 @@ __device__ double edge_root(const Grid& g, const LevelSet& L, const double* x0, 
   for (int it = 0; it < kRootMaxIt; ++it) {
     double X[3] = {xa[0], xa[1], xa[2]};
     X[r] = xa[r] + s;
-    double f = ls_H(L, X);
+    double f = ls_H_iface(L, k, X);
     double gr[3];
-    ls_grad(L, X, gr);
+    ls_grad_iface(L, k, X, gr);
     double df = gr[r];
     bool done_zero = f == 0.0;
     bool same = (f < 0.0) == neg_a;
@@ -144,19 +146,19 @@ __device__ double edge_root(const Grid& g, const LevelSet& L, const double* x0, 
   return s;
 }
 
-__device__ bool crossing_point(const Grid& g, const LevelSet& L, const LineDesc& D, int ia, int ib,
-                               int j, double cos_alpha, double* X, double* nv) {
+__device__ bool crossing_point(const Grid& g, const LevelSet& L, int k, const LineDesc& D, int ia,
+                               int ib, int j, double cos_alpha, double* X, double* nv) {
   double x0[3] = {0.0, 0.0, 0.0};
   x0[D.oa] = coord(g, ia);
   if (g.d == 3) x0[D.ob] = coord(g, ib);
   x0[D.r] = coord(g, j);
-  double s = edge_root(g, L, x0, D.r, j);
+  double s = edge_root(g, L, k, x0, D.r, j);
   X[0] = x0[0];
   X[1] = x0[1];
   X[2] = x0[2];
   X[D.r] = x0[D.r] + s;
   double gr[3];
-  ls_grad(L, X, gr);
+  ls_grad_iface(L, k, X, gr);
   double nn = g.d == 2 ? gr[0] * gr[0] + gr[1] * gr[1] : gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
   double inv = sqrt(nn);
   nv[0] = gr[0] / inv;
@@ -165,9 +167,44 @@ __device__ bool crossing_point(const Grid& g, const LevelSet& L, const LineDesc&
   return fabs(nv[D.r]) > cos_alpha;
 }
 
+// The DOFs of edge j of a line whose end nodes carry labels la != lb: slot 0
+// on interface la - 1 (if la > 0), slot 1 on lb - 1 (if lb > 0), each where
+// that H_k changes sign along the edge and |n_r| > cos(alpha).  Returns the
+// count (0..2); the points, normals and interfaces in slot order.
+__device__ int edge_points(const Grid& g, const LevelSet& L, const LineDesc& D, int ia, int ib,
+                           int j, int la, int lb, double cos_alpha, double (*X)[3],
+                           double (*nv)[3], int* ifc) {
+  int c = 0;
+  const int ks[2] = {la - 1, lb - 1};
+  for (int slot = 0; slot < 2; ++slot) {
+    const int k = ks[slot];
+    if (k < 0) continue;
+    double xa[3] = {0.0, 0.0, 0.0};
+    xa[D.oa] = coord(g, ia);
+    if (g.d == 3) xa[D.ob] = coord(g, ib);
+    double xb[3] = {xa[0], xa[1], xa[2]};
+    xa[D.r] = coord(g, j);
+    xb[D.r] = coord(g, j + 1);
+    if ((ls_H_iface(L, k, xa) < 0.0) == (ls_H_iface(L, k, xb) < 0.0)) continue;
+    if (crossing_point(g, L, k, D, ia, ib, j, cos_alpha, X[c], nv[c])) ifc[c++] = k;
+  }
+  return c;
+}
+
+// inclusive warp prefix sum
+__device__ __forceinline__ int warp_incl_scan(int v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
 // One warp per grid line: the lanes test 32 consecutive edges at a time for a
-// change of node class and compute the crossing of each edge that has one
-// (the per-crossing arithmetic is the same as a thread walking the line).
+// change of node label and compute the points of each edge that has one
+// (the per-point arithmetic is the same as a thread walking the line).
 constexpr int kLineWarps = 4;
 __global__ void __launch_bounds__(32 * kLineWarps) k_line_count(Grid g, LevelSet L, LineDesc D,
                                                                 const uint8_t* __restrict__ inside,
@@ -182,70 +219,27 @@ __global__ void __launch_bounds__(32 * kLineWarps) k_line_count(Grid g, LevelSet
   int c = 0;
   for (int j0 = 0; j0 < g.n; j0 += 32) {
     const int j = j0 + lane;
-    bool hit = false;
-    if (j < g.n && inside[base + j * D.sr] != inside[base + (j + 1) * D.sr]) {
-      double X[3], nv[3];
-      hit = crossing_point(g, L, D, ia, ib, j, cos_alpha, X, nv);
+    int hits = 0;
+    if (j < g.n) {
+      const int la = inside[base + j * D.sr], lb = inside[base + (j + 1) * D.sr];
+      if (la != lb) {
+        double X[2][3], nv[2][3];
+        int ifc[2];
+        hits = edge_points(g, L, D, ia, ib, j, la, lb, cos_alpha, X, nv, ifc);
+      }
     }
-    c += __popc(__ballot_sync(0xffffffffu, hit));
+    c += __shfl_sync(0xffffffffu, warp_incl_scan(hits), 31);
   }
   if (lane == 0) count[li] = c;
 }
 
-// Unions of balls can bring two interfaces closer than the grid step: a node
-// inside one ball and a compact-stencil neighbour inside another, with a thin
-// layer of the outside between them.  The correction there needs the
-// difference of two correction functions (the remark on arbitrarily close
-// interfaces in Sec. 5.2), which is not built, so such a pair is reported.
-// Only inside nodes within 1.8 h of their ball's surface are examined; each
-// segment to an inside neighbour is sampled at k/8, k = 1..7.
-__global__ void k_close_interfaces(Grid g, LevelSet L, const uint8_t* __restrict__ inside,
-                                   int* __restrict__ flags) {
-  const int d = g.d, n1 = g.n + 1;
-  const long long tot = g.nodes();
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-       t += (long long)gridDim.x * blockDim.x) {
-    if (!inside[t]) continue;
-    int idx[3];
-    long long r = t;
-    for (int k = d - 1; k >= 0; --k) {
-      idx[k] = (int)(r % n1);
-      r /= n1;
-    }
-    double X[3] = {coord(g, idx[0]), coord(g, idx[1]), d == 3 ? coord(g, idx[2]) : 0.0};
-    double v;
-    ls_nearest_ball(L.p, d, X, &v);
-    const double rad = L.p[0];
-    if (rad - sqrt(v + rad * rad) > 1.8 * g.h) continue;
-    bool bad = false;
-    for (int o = 0; o < (d == 3 ? 27 : 9) && !bad; ++o) {
-      const int oo[3] = {o % 3 - 1, (o / 3) % 3 - 1, d == 3 ? o / 9 - 1 : 0};
-      if (oo[0] == 0 && oo[1] == 0 && oo[2] == 0) continue;
-      long long q = 0;
-      bool in_grid = true;
-      for (int k = 0; k < d; ++k) {
-        const int j = idx[k] + oo[k];
-        in_grid = in_grid && j >= 0 && j <= g.n;
-        q = q * n1 + j;
-      }
-      if (!in_grid || !inside[q]) continue;
-      for (int s = 1; s < 8 && !bad; ++s) {
-        double Y[3];
-        for (int k = 0; k < 3; ++k) Y[k] = X[k] + (s * 0.125) * (oo[k] * g.h);
-        bad = !(ls_H(L, Y) < 0.0);
-      }
-    }
-    if (bad) flag_min(flags, kFlagMultiCross, (int)t + 1);
-  }
-}
-
 // The DOFs of one grid line in edge order, a warp per line as in
-// k_line_count: each lane's crossing goes to the line's next free slot after
-// those of the lower lanes (ballot prefix).
+// k_line_count: each lane's points go to the line's next free slots after
+// those of the lower lanes (warp prefix sum).
 __global__ void __launch_bounds__(32 * kLineWarps) k_line_fill(
     Grid g, LevelSet L, LineDesc D, const uint8_t* __restrict__ inside, double cos_alpha, int nlines,
     const int32_t* __restrict__ start, double* x0, double* x1, double* x2, double* n0, double* n1,
-    double* n2, int32_t* family, int32_t* edge, int32_t* axis) {
+    double* n2, int32_t* family, int32_t* edge, int32_t* axis, int32_t* iface) {
   const int li = blockIdx.x * kLineWarps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (li >= nlines) return;
@@ -255,33 +249,37 @@ __global__ void __launch_bounds__(32 * kLineWarps) k_line_fill(
   int pos0 = start[li];
   for (int j0 = 0; j0 < g.n; j0 += 32) {
     const int j = j0 + lane;
-    bool hit = false;
-    double X[3], nv[3];
-    if (j < g.n && inside[base + j * D.sr] != inside[base + (j + 1) * D.sr])
-      hit = crossing_point(g, L, D, ia, ib, j, cos_alpha, X, nv);
-    const unsigned mask = __ballot_sync(0xffffffffu, hit);
-    if (hit) {
-      const int pos = pos0 + __popc(mask & ((1u << lane) - 1u));
-      x0[pos] = X[0];
-      x1[pos] = X[1];
-      n0[pos] = nv[0];
-      n1[pos] = nv[1];
+    int hits = 0;
+    double X[2][3], nv[2][3];
+    int ifc[2];
+    if (j < g.n) {
+      const int la = inside[base + j * D.sr], lb = inside[base + (j + 1) * D.sr];
+      if (la != lb) hits = edge_points(g, L, D, ia, ib, j, la, lb, cos_alpha, X, nv, ifc);
+    }
+    const int incl = warp_incl_scan(hits);
+    for (int c = 0; c < hits; ++c) {
+      const int pos = pos0 + incl - hits + c;
+      x0[pos] = X[c][0];
+      x1[pos] = X[c][1];
+      n0[pos] = nv[c][0];
+      n1[pos] = nv[c][1];
       if (g.d == 3) {
-        x2[pos] = X[2];
-        n2[pos] = nv[2];
+        x2[pos] = X[c][2];
+        n2[pos] = nv[c][2];
       }
       family[pos] = D.r;
       edge[pos] = j;
+      iface[pos] = ifc[c];
       int m = 0;
-      double best = fabs(nv[0]);
+      double best = fabs(nv[c][0]);
       for (int k = 1; k < g.d; ++k)
-        if (fabs(nv[k]) > best) {
-          best = fabs(nv[k]);
+        if (fabs(nv[c][k]) > best) {
+          best = fabs(nv[c][k]);
           m = k;
         }
       axis[pos] = m;
     }
-    pos0 += __popc(mask);
+    pos0 += __shfl_sync(0xffffffffu, incl, 31);
   }
 }
 
@@ -301,13 +299,15 @@ struct DofView {
   const double* x[3];
   const double* n[3];
   const int32_t* line_start[3];
+  const int32_t* iface;
 };
 
 
-// Family-`fam` DOF on the line through other-axis node indices (j, k), nearest
-// to s_pred along e_fam within 2h; ties to the lower index; -1 if none.
+// Family-`fam` DOF of interface `ifc` on the line through other-axis node
+// indices (j, k), nearest to s_pred along e_fam within 2h; ties to the lower
+// index; -1 if none.
 __device__ int nearest_on_line(const Grid& g, const DofView& V, int fam, int j, int k,
-                               double s_pred) {
+                               double s_pred, int ifc) {
   if (j < 0 || j > g.n) return -1;
   int li = j;
   if (g.d == 3) {
@@ -319,6 +319,7 @@ __device__ int nearest_on_line(const Grid& g, const DofView& V, int fam, int j, 
   double bestd = INFINITY;
   double win = 2.0 * g.h;
   for (int q = st[li]; q < st[li + 1]; ++q) {
+    if (V.iface[q] != ifc) continue;
     double dist = fabs(V.x[fam][q] - s_pred);
     if (dist <= win && dist < bestd) {
       best = q;
@@ -395,7 +396,7 @@ __global__ void k_stencils(Grid g, int order, double cos_alpha, DofView V, int n
       for (int c = 0; c < 9 && nf < c_st.ndir; ++c) {
         double xt = g.lo + (double)cand[c] * g.h;
         double s_pred = p[m] - nv[t] * (xt - p[t]) / nv[m];
-        int q = nearest_on_line(g, V, m, cand[c], 0, s_pred);
+        int q = nearest_on_line(g, V, m, cand[c], 0, s_pred, V.iface[i]);
         if (q >= 0) found[nf++] = q;
       }
       if (nf == c_st.ndir) {
@@ -424,7 +425,7 @@ __global__ void k_stencils(Grid g, int order, double cos_alpha, DofView V, int n
             double x1 = g.lo + (double)j * g.h;
             double x2 = g.lo + (double)k * g.h;
             double s_pred = p[m] - (nv[t1] * (x1 - p[t1]) + nv[t2] * (x2 - p[t2])) / nv[m];
-            int q = nearest_on_line(g, V, m, j, k, s_pred);
+            int q = nearest_on_line(g, V, m, j, k, s_pred, V.iface[i]);
             if (q < 0) {
               ok = false;
               break;
@@ -753,11 +754,15 @@ __device__ __forceinline__ double dist2(const DofView& V, int d, int q, const do
   return s;
 }
 
-__global__ void k_closest(Grid g, DofView V, int nb, int nirr, const int32_t* __restrict__ lin,
+// Per correction entry (node, interface k): the closest primary point among
+// the DOFs of interface k.
+__global__ void k_closest(Grid g, DofView V, int nb, int nent, const int32_t* __restrict__ lin,
+                          const int32_t* __restrict__ ent_iface,
                           const int32_t* __restrict__ cstart, const int32_t* __restrict__ items,
                           int32_t* __restrict__ owner, int* flags) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nirr) return;
+  if (q >= nent) return;
+  const int ifc = ent_iface[q];
   const int K = 3;
   int idx[3];
   node_multi(g, lin[q], idx);
@@ -777,6 +782,7 @@ __global__ void k_closest(Grid g, DofView V, int nb, int nirr, const int32_t* __
           long long ci = cell_index(g, cc);
           for (int t = cstart[ci]; t < cstart[ci + 1]; ++t) {
             int i = items[t];
+            if (V.iface[i] != ifc) continue;
             double d2 = dist2(V, g.d, i, X);
             if (pass == 0) dmin = fmin(dmin, d2);
             else if (d2 <= dmin + eps && i < best) best = i;
@@ -786,13 +792,19 @@ __global__ void k_closest(Grid g, DofView V, int nb, int nirr, const int32_t* __
       // nothing certain within K h: global search
       atomicAdd(&flags[kFlagClosestFallback], 1);
       dmin = INFINITY;
-      for (int i = 0; i < nb; ++i) dmin = fmin(dmin, dist2(V, g.d, i, X));
+      for (int i = 0; i < nb; ++i)
+        if (V.iface[i] == ifc) dmin = fmin(dmin, dist2(V, g.d, i, X));
       int b2 = INT_MAX;
       for (int i = 0; i < nb; ++i)
-        if (dist2(V, g.d, i, X) <= dmin + eps) {
+        if (V.iface[i] == ifc && dist2(V, g.d, i, X) <= dmin + eps) {
           b2 = i;
           break;
         }
+      if (b2 == INT_MAX) {
+        // no DOF on this interface at all: reported, and an in-range owner
+        flag_min(flags, kFlagNoOwner, q + 1);
+        b2 = 0;
+      }
       owner[q] = b2;
       return;
     }
@@ -802,11 +814,11 @@ __global__ void k_closest(Grid g, DofView V, int nb, int nirr, const int32_t* __
 
 // Composite rows W[j][q] = sum_k phi_k(xi_q) (M^{-1})[k][j], so that C(q) =
 // sum_j W[j][q] Q_j of the owner's collocation data.
-__global__ void k_composite(Grid g, DofView V, int nirr, const int32_t* __restrict__ lin,
+__global__ void k_composite(Grid g, DofView V, int nent, const int32_t* __restrict__ lin,
                             const int32_t* __restrict__ owner, const double* __restrict__ minv,
                             double* __restrict__ W) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nirr) return;
+  if (q >= nent) return;
   const int n = c_exp.n;
   int idx[3];
   node_multi(g, lin[q], idx);
@@ -821,7 +833,7 @@ __global__ void k_composite(Grid g, DofView V, int nirr, const int32_t* __restri
   for (int j = 0; j < n; ++j) {
     double s = 0.0;
     for (int k = 0; k < n; ++k) s += ph[k] * Mi[k * n + j];
-    W[(size_t)j * nirr + q] = s;
+    W[(size_t)j * nent + q] = s;
   }
 }
 
@@ -840,6 +852,90 @@ __global__ void k_corr_lists(Grid g, int nirr, const int32_t* __restrict__ lin,
   }
 }
 
+// ---- several interfaces: correction entries (node, k) as a bit mask per
+// node (bit k = C^(k+1) held there), then numbered in node order, then k.
+__device__ __forceinline__ uint32_t label_bit(int lab) { return lab > 0 ? (1u << (lab - 1)) : 0u; }
+
+// entries of the correction terms: every irregular node, for each label >= 1
+// of its stencil (itself included)
+__global__ void k_need_rhs(Grid g, int nirr, const int32_t* __restrict__ lin,
+                           const uint8_t* __restrict__ inside, uint32_t* __restrict__ need) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nirr) return;
+  int idx[3];
+  node_multi(g, lin[q], idx);
+  uint32_t m = label_bit(inside[lin[q]]);
+  for (int s = 0; s < c_nb.count; ++s) {
+    int nq[3] = {idx[0] + c_nb.off[s][0], idx[1] + c_nb.off[s][1], idx[2] + c_nb.off[s][2]};
+    m |= label_bit(inside[node_index(g, nq)]);
+  }
+  need[lin[q]] = m;
+}
+
+// entries per grid row (last axis), then numbered: emap[node] = the node's
+// first entry, ent_lin / ent_iface per entry
+__global__ void k_ent_row_count(Grid g, const uint32_t* __restrict__ need, int nrows,
+                                int32_t* __restrict__ count) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  const uint32_t* f = need + (long long)r * (g.n + 1);
+  int c = 0;
+  for (int j = 0; j <= g.n; ++j) c += __popc(f[j]);
+  count[r] = c;
+}
+
+__global__ void k_ent_row_fill(Grid g, const uint32_t* __restrict__ need, int nrows,
+                               const int32_t* __restrict__ start, int32_t* __restrict__ emap,
+                               int32_t* __restrict__ ent_lin, int32_t* __restrict__ ent_iface) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  const long long base = (long long)r * (g.n + 1);
+  int pos = start[r];
+  for (int j = 0; j <= g.n; ++j) {
+    uint32_t m = need[base + j];
+    if (!m) continue;
+    emap[base + j] = pos;
+    for (int k = 0; k < KFBI_MAX_INTERFACES; ++k)
+      if ((m >> k) & 1u) {
+        ent_lin[pos] = (int32_t)(base + j);
+        ent_iface[pos] = k;
+        ++pos;
+      }
+  }
+}
+
+// the entry holding C^(k+1) at a node (the bit must be set)
+__device__ __forceinline__ int entry_of(const uint32_t* need, const int32_t* emap, long long node,
+                                        int k) {
+  return emap[node] + __popc(need[node] & ((1u << k) - 1u));
+}
+
+// C_P = -sum_{l_Q != l_P} c (C^(l_P)(Q) - C^(l_Q)(Q)): per neighbour the entry
+// of C^(l_Q)(Q) (added with +c) and of C^(l_P)(Q) (with -c), -1 for label 0
+__global__ void k_corr_lists_multi(Grid g, int nirr, const int32_t* __restrict__ lin,
+                                   const uint8_t* __restrict__ inside,
+                                   const uint32_t* __restrict__ need,
+                                   const int32_t* __restrict__ emap, int32_t* __restrict__ corr_a,
+                                   int32_t* __restrict__ corr_b) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nirr) return;
+  int idx[3];
+  node_multi(g, lin[q], idx);
+  const int lp = inside[lin[q]];
+  for (int s = 0; s < c_nb.count; ++s) {
+    int nq[3] = {idx[0] + c_nb.off[s][0], idx[1] + c_nb.off[s][1], idx[2] + c_nb.off[s][2]};
+    const long long t = node_index(g, nq);
+    const int lq = inside[t];
+    int a = -1, b = -1;
+    if (lq != lp) {
+      if (lq > 0) a = entry_of(need, emap, t, lq - 1);
+      if (lp > 0) b = entry_of(need, emap, t, lp - 1);
+    }
+    corr_a[(size_t)s * nirr + q] = a;
+    corr_b[(size_t)s * nirr + q] = b;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Trace stencils and weighted least-squares weights (Sec. 5.5).
 // ---------------------------------------------------------------------------
@@ -850,9 +946,14 @@ struct TraceParams {
   int wtotal;          // wside^d
 };
 
+// Window offset o of a trace stencil for side label t: nodes of label t
+// within R_s, and nodes of another label within R_o that are irregular and
+// hold C^(t) (need == nullptr: one interface, where they always do) or, where
+// another interface is close (`close`), every node of another label within R_o.
 __device__ __forceinline__ bool trace_select(const Grid& g, const TraceParams& T, const double* p,
-                                             const int* n0, int o, bool plus,
+                                             const int* n0, int o, int tlab, bool close,
                                              const uint8_t* inside, const uint8_t* irr,
+                                             const uint32_t* need,
                                              long long* node_out, double* xi_out, double* r2_out,
                                              bool* across) {
   int off[3] = {0, 0, 0};
@@ -870,9 +971,9 @@ __device__ __forceinline__ bool trace_select(const Grid& g, const TraceParams& T
   r2 = r2 + xi[1] * xi[1];
   if (g.d == 3) r2 = r2 + xi[2] * xi[2];
   long long t = node_index(g, idx);
-  bool ins = inside[t] != 0;
-  bool same = plus ? ins : !ins;
-  bool keep = (same && r2 <= T.rs2) || (!same && irr[t] && r2 <= T.ro2);
+  bool same = inside[t] == tlab;
+  bool holds = close || tlab == 0 || need == nullptr || ((need[t] >> (tlab - 1)) & 1u);
+  bool keep = (same && r2 <= T.rs2) || (!same && (close || irr[t]) && holds && r2 <= T.ro2);
   if (!keep) return false;
   *node_out = t;
   xi_out[0] = xi[0];
@@ -883,23 +984,90 @@ __device__ __forceinline__ bool trace_select(const Grid& g, const TraceParams& T
   return true;
 }
 
+__device__ __forceinline__ void trace_centre(const Grid& g, const DofView& V, int i, double* p,
+                                             int* n0) {
+  p[0] = V.x[0][i];
+  p[1] = V.x[1][i];
+  p[2] = g.d == 3 ? V.x[2][i] : 0.0;
+  n0[0] = n0[1] = n0[2] = 0;
+  for (int k = 0; k < g.d; ++k) n0[k] = (int)floor((p[k] - g.lo) / g.h + 0.5);
+}
+
+// Several interfaces: a DOF of interface k is close to another interface if a
+// node of a third label (not 0, not 1 + k) lies within R_s of it.
+__global__ void k_trace_close(Grid g, TraceParams T, DofView V, int nb,
+                              const uint8_t* __restrict__ inside, uint8_t* __restrict__ close) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  double p[3];
+  int n0[3];
+  trace_centre(g, V, i, p, n0);
+  const int own = V.iface[i] + 1;
+  uint8_t c = 0;
+  for (int o = 0; o < T.wtotal && !c; ++o) {
+    int rem = o, idx[3] = {0, 0, 0};
+    bool ok = true;
+    double r2 = 0.0;
+    for (int k = g.d - 1; k >= 0; --k) {
+      idx[k] = n0[k] + rem % T.wside - T.win;
+      rem /= T.wside;
+      ok = ok && idx[k] >= 0 && idx[k] <= g.n;
+    }
+    if (!ok) continue;
+    double xi[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < g.d; ++k) xi[k] = (coord(g, idx[k]) - p[k]) / g.h;
+    r2 = xi[0] * xi[0];
+    r2 = r2 + xi[1] * xi[1];
+    if (g.d == 3) r2 = r2 + xi[2] * xi[2];
+    const int lab = inside[node_index(g, idx)];
+    if (lab != 0 && lab != own && r2 <= T.rs2) c = 1;
+  }
+  close[i] = c;
+}
+
 __global__ void k_trace_count(Grid g, TraceParams T, DofView V, int nb,
                               const uint8_t* __restrict__ inside, const uint8_t* __restrict__ irr,
+                              const uint8_t* __restrict__ close, const uint32_t* __restrict__ need,
                               int32_t* __restrict__ count) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * nb) return;
   int side = t / nb, i = t % nb;
-  double p[3] = {V.x[0][i], V.x[1][i], g.d == 3 ? V.x[2][i] : 0.0};
-  int n0[3] = {0, 0, 0};
-  for (int k = 0; k < g.d; ++k) n0[k] = (int)floor((p[k] - g.lo) / g.h + 0.5);
+  double p[3];
+  int n0[3];
+  trace_centre(g, V, i, p, n0);
+  const int tlab = side == 0 ? V.iface[i] + 1 : 0;
+  const bool cl = close && close[i];
   int c = 0;
   for (int o = 0; o < T.wtotal; ++o) {
     long long node;
     double xi[3], r2;
     bool across;
-    if (trace_select(g, T, p, n0, o, side == 0, inside, irr, &node, xi, &r2, &across)) ++c;
+    if (trace_select(g, T, p, n0, o, tlab, cl, inside, irr, need, &node, xi, &r2, &across)) ++c;
   }
   count[t] = c;
+}
+
+// Several interfaces: the entries the trace stencils of close DOFs need,
+// C^(t) and C^(l_q) at each selected node q of another label, or-ed into need2.
+__global__ void k_need_trace(Grid g, TraceParams T, DofView V, int nb,
+                             const uint8_t* __restrict__ inside, const uint8_t* __restrict__ irr,
+                             const uint8_t* __restrict__ close, uint32_t* __restrict__ need2) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * nb) return;
+  int side = t / nb, i = t % nb;
+  if (!close[i]) return;
+  double p[3];
+  int n0[3];
+  trace_centre(g, V, i, p, n0);
+  const int tlab = side == 0 ? V.iface[i] + 1 : 0;
+  for (int o = 0; o < T.wtotal; ++o) {
+    long long node;
+    double xi[3], r2;
+    bool across;
+    if (trace_select(g, T, p, n0, o, tlab, true, inside, irr, nullptr, &node, xi, &r2, &across) &&
+        across)
+      atomicOr(&need2[node], label_bit(tlab) | label_bit(inside[node]));
+  }
 }
 
 // One warp per (DOF, side).  A = diag(wt) V (m x n, column-major), QR, then
@@ -908,8 +1076,11 @@ __global__ void k_trace_count(Grid g, TraceParams T, DofView V, int nb,
 __global__ void k_trace_fill(Grid g, TraceParams T, DofView V, int nb,
                              const uint8_t* __restrict__ inside, const uint8_t* __restrict__ irr,
                              const int32_t* __restrict__ map, const int32_t* __restrict__ ptr_all,
+                             const uint8_t* __restrict__ close, const uint32_t* __restrict__ need,
+                             const uint32_t* __restrict__ need2, const int32_t* __restrict__ emap,
                              int mmax, double alpha, double beta, int32_t* __restrict__ node_out,
-                             int32_t* __restrict__ irr_out, double* __restrict__ wv_out,
+                             int32_t* __restrict__ irr_out, int32_t* __restrict__ irr2_out,
+                             double* __restrict__ wv_out,
                              double* __restrict__ wn_out, double* __restrict__ w_out, int* flags) {
   extern __shared__ double sm[];
   const int n = c_exp.n;
@@ -932,6 +1103,8 @@ __global__ void k_trace_fill(Grid g, TraceParams T, DofView V, int nb,
   double nv[3] = {V.n[0][i], V.n[1][i], d == 3 ? V.n[2][i] : 0.0};
   int n0[3] = {0, 0, 0};
   for (int k = 0; k < d; ++k) n0[k] = (int)floor((p[k] - g.lo) / g.h + 0.5);
+  const int tlab = side == 0 ? V.iface[i] + 1 : 0;
+  const bool cl = close && close[i];
   // ordered compaction of the selected window offsets
   int m = 0;
   for (int base = 0; base < T.wtotal; base += 32) {
@@ -939,8 +1112,8 @@ __global__ void k_trace_fill(Grid g, TraceParams T, DofView V, int nb,
     long long node = 0;
     double xi[3] = {0.0, 0.0, 0.0}, r2 = 0.0;
     bool across = false;
-    bool sel = o < T.wtotal &&
-               trace_select(g, T, p, n0, o, side == 0, inside, irr, &node, xi, &r2, &across);
+    bool sel = o < T.wtotal && trace_select(g, T, p, n0, o, tlab, cl, inside, irr, need, &node,
+                                            xi, &r2, &across);
     unsigned ball = __ballot_sync(0xffffffffu, sel);
     if (sel) {
       int pos = m + __popc(ball & ((1u << lane) - 1u));
@@ -988,7 +1161,14 @@ __global__ void k_trace_fill(Grid g, TraceParams T, DofView V, int nb,
     double a = y0[r] * wt[r], b = y1[r] * wt[r];
     int node = nodes[r];
     node_out[off + r] = node;
-    irr_out[off + r] = acr[r] ? map[node] : -1;
+    if (need2) {
+      // several interfaces: u + C^(t) - C^(l_q) across, with C^(0) = 0
+      const int lq = inside[node];
+      irr_out[off + r] = acr[r] && tlab > 0 ? entry_of(need2, emap, node, tlab - 1) : -1;
+      irr2_out[off + r] = acr[r] && lq > 0 ? entry_of(need2, emap, node, lq - 1) : -1;
+    } else {
+      irr_out[off + r] = acr[r] ? map[node] : -1;
+    }
     wv_out[off + r] = a;
     wn_out[off + r] = b;
     w_out[off + r] = alpha * a + beta * b;
@@ -1047,11 +1227,9 @@ static kfbi_status check_flags(kfbi_problem* p, const char* stage) {
   int h[kFlagCount];
   KFBI_CUDA(p, cudaMemcpyAsync(h, p->d_flags, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
   KFBI_CUDA(p, cudaStreamSynchronize(p->stream));
-  if (h[kFlagMultiCross] != kFlagSentinel)
-    return fail(p, KFBI_ERR_GEOMETRY, std::string(stage) + ": the compact stencil of grid node " +
-                                          std::to_string(h[kFlagMultiCross] - 1) +
-                                          " spans two interfaces (interfaces closer than the grid step are "
-                                          "not supported)");
+  if (h[kFlagNoOwner] != kFlagSentinel)
+    return fail(p, KFBI_ERR_GEOMETRY, std::string(stage) + ": interface of correction entry " +
+                                          std::to_string(h[kFlagNoOwner] - 1) + " has no DOF");
   if (h[kFlagOutOfBox] != kFlagSentinel)
     return fail(p, KFBI_ERR_GEOMETRY, std::string(stage) + ": stencil of DOF " +
                                           std::to_string(h[kFlagOutOfBox] - 1) + " leaves the box");
@@ -1106,11 +1284,6 @@ kfbi_status build_geometry(kfbi_problem* p) {
                                                       nlines, cnt + (size_t)r * nlines);
     KFBI_CUDA(p, cudaGetLastError());
   }
-  if (L.kind == KFBI_LS_DISCS || L.kind == KFBI_LS_SPHERES) {
-    k_close_interfaces<<<std::min(div_up(nodes, 256), 152 * 16), 256, 0, st>>>(g, L, p->inside, p->d_flags);
-    KFBI_CUDA(p, cudaGetLastError());
-    KFBI_TRY(check_flags(p, "interface separation"));
-  }
   // family-by-family exclusive scans with running offsets
   std::vector<int32_t> tot(d);
   for (int r = 0; r < d; ++r) {
@@ -1134,6 +1307,7 @@ kfbi_status build_geometry(kfbi_problem* p) {
     KFBI_CUDA(p, dalloc(&p->nrm[k], nb));
   }
   KFBI_CUDA(p, dalloc(&p->family, nb));
+  KFBI_CUDA(p, dalloc(&p->dof_iface, nb));
   KFBI_CUDA(p, dalloc(&p->edge, nb));
   KFBI_CUDA(p, dalloc(&p->axis, nb));
   KFBI_CUDA(p, dalloc(&p->st_axis, nb));
@@ -1141,7 +1315,7 @@ kfbi_status build_geometry(kfbi_problem* p) {
     k_line_fill<<<div_up(nlines, kLineWarps), 32 * kLineWarps, 0, st>>>(
         g, L, D[r], p->inside, p->cos_alpha, nlines, p->line_start[r], p->x[0], p->x[1],
         d == 3 ? p->x[2] : p->x[0], p->nrm[0], p->nrm[1], d == 3 ? p->nrm[2] : p->nrm[0],
-        p->family, p->edge, p->axis);
+        p->family, p->edge, p->axis, p->dof_iface);
     KFBI_CUDA(p, cudaGetLastError());
   }
   cudaFree(cnt);
@@ -1152,6 +1326,7 @@ kfbi_status build_geometry(kfbi_problem* p) {
     V.n[k] = k < d ? p->nrm[k] : nullptr;
     V.line_start[k] = k < d ? p->line_start[k] : nullptr;
   }
+  V.iface = p->dof_iface;
 
   // ---- stencil tables
   StencilTables T;
@@ -1268,12 +1443,67 @@ kfbi_status build_geometry(kfbi_problem* p) {
   if (nirr == 0) return fail(p, KFBI_ERR_GEOMETRY, "no irregular nodes");
   KFBI_CUDA(p, dalloc(&p->irr_lin, nirr));
   KFBI_CUDA(p, dalloc(&p->irr_inside, nirr));
-  KFBI_CUDA(p, dalloc(&p->irr_owner, nirr));
   k_row_fill<<<div_up(nrows, 128), 128, 0, st>>>(g, p->irr_flag, p->inside, nrows, rstart,
                                                   p->irr_lin, p->irr_inside, map);
   KFBI_CUDA(p, cudaGetLastError());
+
+  // ---- trace stencil parameters (Sec. 5.5)
+  TraceParams TP;
+  double rs = order == 4 ? 4.0 : 3.0, ro = order == 4 ? 2.5 : 1.5;
+  TP.rs2 = rs * rs;
+  TP.ro2 = ro * ro;
+  TP.win = (int)std::ceil(rs) + 1;
+  TP.wside = 2 * TP.win + 1;
+  TP.wtotal = d == 2 ? TP.wside * TP.wside : TP.wside * TP.wside * TP.wside;
+
+  // ---- correction entries (node, interface k)
+  const bool multi = p->n_iface > 1;
+  uint32_t *need = nullptr, *need2 = nullptr;
+  uint8_t* close = nullptr;
+  int32_t* emap = nullptr;
+  if (!multi) {
+    // one per irregular node, in its order
+    p->nent = nirr;
+    KFBI_CUDA(p, dalloc(&p->ent_lin, nirr));
+    KFBI_CUDA(p, dalloc(&p->ent_iface, nirr));
+    KFBI_CUDA(p, cudaMemcpyAsync(p->ent_lin, p->irr_lin, sizeof(int32_t) * nirr,
+                                 cudaMemcpyDeviceToDevice, st));
+    KFBI_CUDA(p, cudaMemsetAsync(p->ent_iface, 0, sizeof(int32_t) * nirr, st));
+  } else {
+    KFBI_CUDA(p, dalloc(&need, nodes));
+    KFBI_CUDA(p, dalloc(&need2, nodes));
+    KFBI_CUDA(p, dalloc(&close, nb));
+    KFBI_CUDA(p, dalloc(&emap, nodes));
+    KFBI_CUDA(p, cudaMemsetAsync(need, 0, sizeof(uint32_t) * nodes, st));
+    KFBI_CUDA(p, cudaMemsetAsync(emap, 0xff, sizeof(int32_t) * nodes, st));
+    k_need_rhs<<<div_up(nirr, 128), 128, 0, st>>>(g, nirr, p->irr_lin, p->inside, need);
+    KFBI_CUDA(p, cudaMemcpyAsync(need2, need, sizeof(uint32_t) * nodes, cudaMemcpyDeviceToDevice, st));
+    k_trace_close<<<div_up(nb, 128), 128, 0, st>>>(g, TP, V, nb, p->inside, close);
+    k_need_trace<<<div_up(2 * nb, 128), 128, 0, st>>>(g, TP, V, nb, p->inside, p->irr_flag, close,
+                                                      need2);
+    KFBI_CUDA(p, cudaGetLastError());
+    int32_t *ecnt = nullptr, *estart = nullptr;
+    KFBI_CUDA(p, dalloc(&ecnt, nrows));
+    KFBI_CUDA(p, dalloc(&estart, nrows + 1));
+    k_ent_row_count<<<div_up(nrows, 128), 128, 0, st>>>(g, need2, nrows, ecnt);
+    k_exclusive_scan<<<1, 1024, 0, st>>>(ecnt, estart, nrows, 0);
+    int32_t nent = 0;
+    KFBI_CUDA(p, cudaMemcpyAsync(&nent, estart + nrows, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    KFBI_CUDA(p, cudaStreamSynchronize(st));
+    p->nent = nent;
+    KFBI_CUDA(p, dalloc(&p->ent_lin, nent));
+    KFBI_CUDA(p, dalloc(&p->ent_iface, nent));
+    k_ent_row_fill<<<div_up(nrows, 128), 128, 0, st>>>(g, need2, nrows, estart, emap, p->ent_lin,
+                                                        p->ent_iface);
+    KFBI_CUDA(p, cudaGetLastError());
+    KFBI_CUDA(p, cudaStreamSynchronize(st));
+    cudaFree(ecnt);
+    cudaFree(estart);
+  }
   cudaFree(rcnt);
   cudaFree(rstart);
+  const int nent = p->nent;
+  KFBI_CUDA(p, dalloc(&p->ent_owner, nent));
 
   // ---- closest primary points via a cell list
   {
@@ -1288,8 +1518,8 @@ kfbi_status build_geometry(kfbi_problem* p) {
     k_cell_count<<<div_up(nb, 256), 256, 0, st>>>(g, V, nb, ccnt);
     k_exclusive_scan<<<1, 1024, 0, st>>>(ccnt, cstart, (int)ncell, 0);
     k_cell_fill<<<div_up(nb, 256), 256, 0, st>>>(g, V, nb, cstart, cur, items);
-    k_closest<<<div_up(nirr, 128), 128, 0, st>>>(g, V, nb, nirr, p->irr_lin, cstart, items,
-                                                 p->irr_owner, p->d_flags);
+    k_closest<<<div_up(nent, 128), 128, 0, st>>>(g, V, nb, nent, p->ent_lin, p->ent_iface, cstart,
+                                                 items, p->ent_owner, p->d_flags);
     KFBI_CUDA(p, cudaGetLastError());
     KFBI_CUDA(p, cudaStreamSynchronize(st));
     cudaFree(ccnt);
@@ -1297,26 +1527,27 @@ kfbi_status build_geometry(kfbi_problem* p) {
     cudaFree(cur);
     cudaFree(items);
   }
-  KFBI_CUDA(p, dalloc(&p->irr_w, (size_t)nc * nirr));
-  k_composite<<<div_up(nirr, 128), 128, 0, st>>>(g, V, nirr, p->irr_lin, p->irr_owner, p->minv,
-                                                  p->irr_w);
+  KFBI_TRY(check_flags(p, "closest primary points"));
+  KFBI_CUDA(p, dalloc(&p->ent_w, (size_t)nc * nent));
+  k_composite<<<div_up(nent, 128), 128, 0, st>>>(g, V, nent, p->ent_lin, p->ent_owner, p->minv,
+                                                  p->ent_w);
   KFBI_CUDA(p, cudaGetLastError());
   KFBI_CUDA(p, dalloc(&p->corr_nb, (size_t)p->n_nb * nirr));
-  k_corr_lists<<<div_up(nirr, 128), 128, 0, st>>>(g, nirr, p->irr_lin, p->inside, map, p->corr_nb);
+  if (!multi) {
+    k_corr_lists<<<div_up(nirr, 128), 128, 0, st>>>(g, nirr, p->irr_lin, p->inside, map, p->corr_nb);
+  } else {
+    KFBI_CUDA(p, dalloc(&p->corr_nb2, (size_t)p->n_nb * nirr));
+    k_corr_lists_multi<<<div_up(nirr, 128), 128, 0, st>>>(g, nirr, p->irr_lin, p->inside, need2,
+                                                          emap, p->corr_nb, p->corr_nb2);
+  }
   KFBI_CUDA(p, cudaGetLastError());
 
   // ---- trace stencils
-  TraceParams TP;
-  double rs = order == 4 ? 4.0 : 3.0, ro = order == 4 ? 2.5 : 1.5;
-  TP.rs2 = rs * rs;
-  TP.ro2 = ro * ro;
-  TP.win = (int)std::ceil(rs) + 1;
-  TP.wside = 2 * TP.win + 1;
-  TP.wtotal = d == 2 ? TP.wside * TP.wside : TP.wside * TP.wside * TP.wside;
   int32_t *tcnt = nullptr, *tptr = nullptr;
   KFBI_CUDA(p, dalloc(&tcnt, 2 * nb));
   KFBI_CUDA(p, dalloc(&tptr, 2 * nb + 1));
-  k_trace_count<<<div_up(2 * nb, 128), 128, 0, st>>>(g, TP, V, nb, p->inside, p->irr_flag, tcnt);
+  k_trace_count<<<div_up(2 * nb, 128), 128, 0, st>>>(g, TP, V, nb, p->inside, p->irr_flag, close,
+                                                       need, tcnt);
   k_exclusive_scan<<<1, 1024, 0, st>>>(tcnt, tptr, 2 * nb, 0);
   KFBI_CUDA(p, cudaGetLastError());
   std::vector<int32_t> hptr(2 * nb + 1), hcnt(2 * nb);
@@ -1327,10 +1558,11 @@ kfbi_status build_geometry(kfbi_problem* p) {
   int mmax = 0;
   for (int k = 0; k < 2 * nb; ++k) mmax = std::max(mmax, hcnt[k]);
   const int nnz_all = hptr[2 * nb];
-  int32_t *tnode = nullptr, *tirr = nullptr;
+  int32_t *tnode = nullptr, *tirr = nullptr, *tirr2 = nullptr;
   double *twv = nullptr, *twn = nullptr, *tw = nullptr;
   KFBI_CUDA(p, dalloc(&tnode, nnz_all));
   KFBI_CUDA(p, dalloc(&tirr, nnz_all));
+  if (multi) KFBI_CUDA(p, dalloc(&tirr2, nnz_all));
   KFBI_CUDA(p, dalloc(&twv, nnz_all));
   KFBI_CUDA(p, dalloc(&twn, nnz_all));
   KFBI_CUDA(p, dalloc(&tw, nnz_all));
@@ -1345,8 +1577,9 @@ kfbi_status build_geometry(kfbi_problem* p) {
     KFBI_CUDA(p, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     if (smem > (size_t)optin)
       return fail(p, KFBI_ERR_UNSUPPORTED, "trace stencil too large for shared memory");
-    k_trace_fill<<<2 * nb, 32, smem, st>>>(g, TP, V, nb, p->inside, p->irr_flag, map, tptr, mmax,
-                                           alpha, beta, tnode, tirr, twv, twn, tw, p->d_flags);
+    k_trace_fill<<<2 * nb, 32, smem, st>>>(g, TP, V, nb, p->inside, p->irr_flag, map, tptr, close,
+                                           need, need2, emap, mmax, alpha, beta, tnode, tirr,
+                                           tirr2, twv, twn, tw, p->d_flags);
     KFBI_CUDA(p, cudaGetLastError());
   }
   KFBI_TRY(check_flags(p, "trace weights"));
@@ -1362,6 +1595,7 @@ kfbi_status build_geometry(kfbi_problem* p) {
     c.nnz = sp[nb];
     c.node = tnode + b0;
     c.irr = tirr + b0;
+    c.irr2 = multi ? tirr2 + b0 : nullptr;
     c.wv = twv + b0;
     c.wn = twn + b0;
     c.w = tw + b0;
@@ -1370,6 +1604,12 @@ kfbi_status build_geometry(kfbi_problem* p) {
   cudaFree(tcnt);
   cudaFree(tptr);
   cudaFree(map);
+  if (multi) {
+    cudaFree(need);
+    cudaFree(need2);
+    cudaFree(close);
+    cudaFree(emap);
+  }
   return KFBI_OK;
 }
 

@@ -52,7 +52,8 @@ class Config(ctypes.Structure):
 
 class Data(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in
-                ("g1", "g2", "f_in", "f_out", "lapf_in", "lapf_out", "g_b")]
+                ("g1", "g2", "f_in", "f_out", "lapf_in", "lapf_out", "g_b")] + \
+        [("in_per_interface", ctypes.c_int)]
 
 
 class GmresOpts(ctypes.Structure):
@@ -81,6 +82,9 @@ SIGNATURES = {
     "kfbi_collocation_stencils": [_P, _P, _P, _P],
     "kfbi_inside_mask": [_P, _P],
     "kfbi_irregular_nodes": [_P, _P, _P],
+    "kfbi_interfaces": [_P, _I, _I],
+    "kfbi_dof_iface": [_P, _P],
+    "kfbi_correction_entries": [_P, _P, _P, _P],
     "kfbi_collocation_fit": [_P, _P, _P, _P, _P],
     "kfbi_correction_values": [_P, _P, _P, _P, _P],
     "kfbi_corrected_rhs": [_P, _P, ctypes.POINTER(Data), _P],
@@ -210,6 +214,20 @@ def kfbi_irregular_nodes(h, lin, owner):
     _check(load().kfbi_irregular_nodes(h, _ptr(lin), _ptr(owner)), h)
 
 
+def kfbi_interfaces(h):
+    n_iface, n_ent = ctypes.c_int(), ctypes.c_int()
+    _check(load().kfbi_interfaces(h, ctypes.byref(n_iface), ctypes.byref(n_ent)), h)
+    return n_iface.value, n_ent.value
+
+
+def kfbi_dof_iface(h, iface):
+    _check(load().kfbi_dof_iface(h, _ptr(iface)), h)
+
+
+def kfbi_correction_entries(h, lin, iface, owner):
+    _check(load().kfbi_correction_entries(h, _ptr(lin), _ptr(iface), _ptr(owner)), h)
+
+
 def kfbi_collocation_fit(h, a, b, ftilde, coef):
     _check(load().kfbi_collocation_fit(h, _ptr(a), _ptr(b), _ptr(ftilde), _ptr(coef)), h)
 
@@ -218,12 +236,16 @@ def kfbi_correction_values(h, a, b, ftilde, cvals):
     _check(load().kfbi_correction_values(h, _ptr(a), _ptr(b), _ptr(ftilde), _ptr(cvals)), h)
 
 
-def make_data(g1=None, g2=None, f_in=None, f_out=None, lapf_in=None, lapf_out=None, g_b=None):
+def make_data(g1=None, g2=None, f_in=None, f_out=None, lapf_in=None, lapf_out=None, g_b=None,
+              in_per_interface=False):
+    """kfbi_data from device tensors; in_per_interface: f_in and lapf_in hold
+    one grid per interface (a leading axis of length n_iface)."""
     d = Data()
     for k, v in (("g1", g1), ("g2", g2), ("f_in", f_in), ("f_out", f_out),
                  ("lapf_in", lapf_in), ("lapf_out", lapf_out), ("g_b", g_b)):
         p = _ptr(v)
         setattr(d, k, p.value if p is not None else None)
+    d.in_per_interface = int(bool(in_per_interface))
     return d
 
 
@@ -440,6 +462,7 @@ class Problem:
         self.handle = kfbi_create_problem(cfg, ls, stream)
         del keep
         self.nb, self.nirr, self.ncoef = kfbi_sizes(self.handle)
+        self.n_iface, self.nent = kfbi_interfaces(self.handle)
         self.npde, self.ndir, self.nneu = kfbi_stencil_sizes(self.handle)
 
     @classmethod

@@ -54,5 +54,6 @@ def gpu_data(w, P_or, data, g1, g2):
     keep["g2"] = dev(g2) if g2 is not None else None
     d = kfbi.make_data(g1=keep["g1"], g2=keep["g2"], f_in=keep["f_in"], f_out=keep["f_out"],
                        lapf_in=keep["lapf_in"], lapf_out=keep["lapf_out"],
-                       g_b=keep["g_b"] if w.kind in (W.KIND_INTERFACE_MU, W.KIND_INTERFACE_GENERAL) else None)
+                       g_b=keep["g_b"] if w.kind in (W.KIND_INTERFACE_MU, W.KIND_INTERFACE_GENERAL) else None,
+                       in_per_interface=data["f_in"].ndim == w.dim + 1)
     return d, keep

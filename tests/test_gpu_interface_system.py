@@ -22,12 +22,16 @@ pytestmark = pytest.mark.gpu
 def _case(name):
     if name == "flower2":
         return W.hetero_interface_2d(128)
+    if name == "spheres07":
+        # Sec. 7.2.5's spheres at their radius 0.7: 0.0142 apart, below the
+        # grid step, so stencils join two spheres (several interfaces)
+        return W.hetero_spheres_3d(64, radius=0.7)
     return W.Workload("ell3g", 3, 32, -1.0, 1.0, W.LS_ELLIPSOID,
                       [0.05, -0.03, 0.02, 0.8, 0.7, 0.6], W.KIND_INTERFACE_GENERAL,
                       sigma_in=1.0, sigma_out=4.0, kappa=0.0, kappa_out=10.0, exact="exp3")
 
 
-NAMES = ["flower2", "ell3"]
+NAMES = ["flower2", "ell3", "spheres07"]
 _oracles = {}
 
 

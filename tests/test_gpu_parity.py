@@ -1,7 +1,8 @@
 """GPU-vs-oracle parity through the C ABI, stage by stage and end to end.
 
-Integer outputs (DOF order, families, reference axes, collocation stencils,
-node classes, irregular nodes, closest primary points) must be identical.
+Integer outputs (DOF order, families, interfaces, reference axes, collocation
+stencils, node labels, irregular nodes, correction entries, closest primary
+points) must be identical.
 Floating-point outputs are compared in relative max-norm: the FP64 path of the
 solver is held to 1e-10 (the stated bound for every config), single stages to
 tighter bounds where the arithmetic is short.
@@ -32,6 +33,10 @@ CASES = {
     # interfaces known only by level-set samples at the grid nodes
     "sampled256": lambda: W.sampled_interface_2d(256),
     "sampled3d64": lambda: W.sampled_dirichlet_3d(64),
+    # close interfaces: two discs 0.004 apart (below the grid step), each with
+    # its own interior solution; Sec. 7.1.2's touching circles and star
+    "close_discs128": lambda: W.close_discs_2d(128),
+    "touching256": lambda: W.touching_interfaces_2d(256),
 }
 
 
@@ -69,6 +74,7 @@ def test_geometry_exact(name):
     h = G.handle
     assert G.nb == P.nb
     assert G.nirr == int(P.irr.sum())
+    assert (G.n_iface, G.nent) == (P.n_iface, P.cnode_idx.shape[0])
     d = w.dim
     xyz, nrm = empty((G.nb, d)), empty((G.nb, d))
     kfbi.kfbi_dof_points(h, xyz, nrm)
@@ -85,13 +91,24 @@ def test_geometry_exact(name):
     assert np.array_equal(host(pde), linear_nodes(P.pde_nodes, w.n))
     assert np.array_equal(host(dd), P.dir_idx)
     assert np.array_equal(host(nn), P.neu_idx)
+    ifc = empty(G.nb, "i32")
+    kfbi.kfbi_dof_iface(h, ifc)
+    assert np.array_equal(host(ifc), P.surf.iface)
     mask = empty(G.grid_shape, "u8")
     kfbi.kfbi_inside_mask(h, mask)
-    assert np.array_equal(host(mask).astype(bool), P.inside)
-    lin, own = empty(G.nirr, "i32"), empty(G.nirr, "i32")
-    kfbi.kfbi_irregular_nodes(h, lin, own)
-    assert np.array_equal(host(lin), linear_nodes(P.cnode_idx, w.n))
+    assert np.array_equal(host(mask), P.labels)
+    lin = empty(G.nirr, "i32")
+    kfbi.kfbi_irregular_nodes(h, lin, None)
+    assert np.array_equal(host(lin), linear_nodes(np.argwhere(P.irr), w.n))
+    elin, eif, own = empty(G.nent, "i32"), empty(G.nent, "i32"), empty(G.nent, "i32")
+    kfbi.kfbi_correction_entries(h, elin, eif, own)
+    assert np.array_equal(host(elin), linear_nodes(P.cnode_idx, w.n))
+    assert np.array_equal(host(eif), P.cnode_iface)
     assert np.array_equal(host(own), P.cnode_owner)
+    if G.n_iface == 1:
+        own1 = empty(G.nirr, "i32")
+        kfbi.kfbi_irregular_nodes(h, lin, own1)
+        assert np.array_equal(host(own1), P.cnode_owner)
 
 
 @pytest.mark.parametrize("name", NAMES)
@@ -106,7 +123,7 @@ def test_collocation_and_correction_values(name):
     kfbi.kfbi_collocation_fit(G.handle, dev(a), dev(b), dev(ft), coef)
     assert rel_err(host(coef), coef_ref) < 1e-11
     cv_ref = P.c_values(coef_ref)
-    cv = empty(G.nirr)
+    cv = empty(G.nent)
     kfbi.kfbi_correction_values(G.handle, dev(a), dev(b), dev(ft), cv)
     assert rel_err(host(cv), cv_ref) < 1e-11
 
@@ -116,7 +133,7 @@ def test_corrected_rhs(name):
     from paper_2309_05965_gb300 import kfbi
     w, P, G = pair(name)
     rng = np.random.default_rng(2)
-    cv = rng.standard_normal(G.nirr)
+    cv = rng.standard_normal(G.nent)
     data = W.grid_data(w)
     Fi, Fo, Li, Lo = P.unit_sigma_data(data)
     if w.kind == W.KIND_DIRICHLET:
@@ -154,7 +171,7 @@ def test_traces(name):
     rng = np.random.default_rng(4)
     X = P.grid.coords()
     u = np.sin(3 * X[..., 0]) * np.cos(2 * X[..., 1]) + 0.1 * rng.standard_normal(P.inside.shape)
-    cv = rng.standard_normal(G.nirr)
+    cv = rng.standard_normal(G.nent)
     ref = P.traces(u, cv)
     outs = [empty(G.nb) for _ in range(4)]
     kfbi.kfbi_traces(G.handle, dev(u), dev(cv), *outs)
@@ -195,7 +212,7 @@ def test_full_solve(name, precision):
     from paper_2309_05965_gb300 import kfbi
     w, P, G = pair(name, precision)
     data = W.grid_data(w)
-    g1, g2 = W.boundary_data(w, P.surf.x, P.surf.n)
+    g1, g2 = W.boundary_data(w, P.surf.x, P.surf.n, P.surf.iface)
     b_ref = P.bie_rhs(g1, g2, data)
     x_ref, it_ref, _ = OK.gmres(P.apply, b_ref, rtol=1e-13)
     u_ref = P.evaluate(x_ref, g1, data)
@@ -228,7 +245,7 @@ def test_full_solve(name, precision):
     kfbi.kfbi_evaluate(G.handle, d, dens, u)
     assert rel_err(host(u), u_ref) < tol
     # and the solution is the exact one to discretisation accuracy
-    ex = W.exact_grid(w, P.inside)
+    ex = W.exact_grid(w, P.labels)
     m = P.inside if w.kind == W.KIND_DIRICHLET else np.ones_like(P.inside)
     inner = np.zeros_like(m)
     inner[tuple(slice(1, w.n) for _ in range(w.dim))] = True
