@@ -308,6 +308,8 @@ def run_ours(args, rank, world):
         out["neumann"] = neumann_leg(args, stream, flush)
     if args.hetero_n > 0:
         out["hetero"] = hetero_leg(args, stream, flush)
+    if args.close_n2 > 0:
+        out["close"] = close_leg(args, stream, flush)
     if rank == 0 and args.cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_budget)
     return out
@@ -815,18 +817,19 @@ def neumann_leg(args, stream, flush):
 
 def hetero_leg(args, stream, flush):
     """The general interface system (eq. (bie-ifp-1)) with Sec. 7.2.5's
-    heterogeneous coefficients and sphere centres (radius 0.6) at --hetero-n^3: two box solves per
-    operator application over 2 N_b unknowns, mixed and FP64 DST, GMRES to
-    the paper's tolerance 1e-10, errors on each side of the interface."""
+    heterogeneous coefficients and spheres (radius 0.7, 0.0142 apart: stencils
+    join two spheres) at --hetero-n^3: two box solves per operator
+    application over 2 N_b unknowns, mixed and FP64 DST, GMRES to the paper's
+    tolerance 1e-10, errors on each side of the interfaces."""
     import numpy as np
     import torch
 
     import workloads as W
     from paper_2309_05965_gb300 import kfbi
     n = args.hetero_n
-    w = W.hetero_spheres_3d(n)
+    w = W.hetero_spheres_3d(n, radius=0.7)
     grid = W.grid_data(w)
-    out = {"workload": f"three spheres r=0.6 at Sec. 7.2.5's centres in [-1.5,1.5]^3, N={n}, "
+    out = {"workload": f"Sec. 7.2.5's three spheres r=0.7 (0.0142 apart) in [-1.5,1.5]^3, N={n}, "
                        f"sigma 1/4, kappa 0/10, general interface system, 4th order, GMRES rtol 1e-10",
            "relax_mixed": args.relax_3d}
     opts = kfbi.GmresOpts(rtol=1e-10, restart=100, max_iter=200, x0=None)
@@ -872,6 +875,91 @@ def hetero_leg(args, stream, flush):
     out["speedup_mixed_vs_fp64"] = out["dst_mixed"]["solves_per_s"] / out["dst_fp64"]["solves_per_s"]
     out["err_ratio_mixed_vs_fp64"] = max(
         out["dst_mixed"][k] / out["dst_fp64"][k] for k in ("einf_inside", "einf_outside"))
+    return out
+
+
+def _solve_labels(w, prec, args, flush, stream, reps=3):
+    """One workload solved end to end on device-resident data (GMRES to
+    1e-10 and evaluation), timed over `reps` steps with L2 flushed before
+    each: ms per solve, iterations, N_b and the max error per side label."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2309_05965_gb300 import kfbi
+    mixed = prec == kfbi.MIXED
+    relax = (args.relax_3d if w.dim == 3 else args.relax) if mixed else 0.0
+    G = kfbi.Problem.from_workload(w, precision=prec, box_max_iters=args.box_steps if mixed else 0,
+                                   relax=relax)
+    xyz = torch.zeros((G.nb, w.dim), dtype=torch.float64, device="cuda")
+    nrm = torch.zeros_like(xyz)
+    ifc = torch.zeros(G.nb, dtype=torch.int32, device="cuda")
+    kfbi.kfbi_dof_points(G.handle, xyz, nrm)
+    kfbi.kfbi_dof_iface(G.handle, ifc)
+    g1, g2 = W.boundary_data(w, xyz.cpu().numpy(), nrm.cpu().numpy(), ifc.cpu().numpy())
+    grid = W.grid_data(w)
+    keep = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in
+            (("g1", g1), ("g2", g2), ("f_in", grid["f_in"]), ("f_out", grid["f_out"]),
+             ("lapf_in", grid["lapf_in"]), ("lapf_out", grid["lapf_out"]), ("g_b", grid["g_b"]))}
+    d = kfbi.make_data(**keep, in_per_interface=grid["f_in"].ndim == w.dim + 1)
+    nx = 2 * G.nb if w.kind == W.KIND_INTERFACE_GENERAL else G.nb
+    x = torch.zeros(nx, dtype=torch.float64, device="cuda")
+    u = torch.zeros(G.grid_shape, dtype=torch.float64, device="cuda")
+    opts = kfbi.GmresOpts(rtol=1e-10, restart=100, max_iter=300, x0=None)
+
+    def step():
+        info = kfbi.kfbi_gmres_solve(G.handle, d, opts, x)
+        kfbi.kfbi_evaluate(G.handle, d, x, u)
+        return info
+    step()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = step()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    lab = torch.zeros(G.grid_shape, dtype=torch.uint8, device="cuda")
+    kfbi.kfbi_inside_mask(G.handle, lab)
+    lab = lab.cpu().numpy()
+    e = np.abs(u.cpu().numpy() - W.exact_grid(w, lab))
+    inner = np.zeros(e.shape, dtype=bool)
+    inner[tuple(slice(1, w.n) for _ in range(w.dim))] = True
+    errs = {int(l): float(e[inner & (lab == l)].max()) for l in np.unique(lab)}
+    res = {"ms_per_solve": statistics.median(ts), "solves_per_s": 1e3 / statistics.median(ts),
+           "gmres_iterations": info.iters, "n_b": G.nb, "n_entries": G.nent, "relax": relax,
+           "einf_by_label": errs}
+    G.close()
+    return res
+
+
+def close_leg(args, stream, flush):
+    """Close and touching interfaces (the remark on arbitrarily close
+    interfaces in Sec. 5.2): Sec. 7.1.2's eight circles and star (Table 2) at
+    --close-n2^2 and Sec. 7.2.4's torus and ellipsoid touching along a circle
+    (Table 6) at --close-n3^3, mixed and FP64 DST, GMRES to 1e-10, with the
+    paper's numbers for the same grids (its CPU times on its own machine)."""
+    import json as _json
+    import pathlib
+
+    import workloads as W
+    from paper_2309_05965_gb300 import kfbi
+    gold = pathlib.Path(__file__).parent / "tests" / "golden"
+    t2 = _json.loads((gold / "paper_table2.json").read_text())["rows"]
+    t6 = _json.loads((gold / "paper_table6.json").read_text())["rows"]
+    out = {}
+    for key, w, table in (("table2", W.touching_interfaces_2d(args.close_n2), t2),
+                          ("table6", W.torus_ellipsoid_3d(args.close_n3), t6)):
+        rec = {"workload": f"{w.name}, N={w.n}, mu-form interface problem, sigma_i 1 / sigma_e 3, "
+                           f"4th order, GMRES rtol 1e-10",
+               "paper": table.get(str(w.n))}
+        for name, prec in (("dst_mixed", kfbi.MIXED), ("dst_fp64", kfbi.FP64)):
+            rec[name] = _solve_labels(w, prec, args, flush, stream)
+        rec["speedup_mixed_vs_fp64"] = rec["dst_mixed"]["solves_per_s"] / rec["dst_fp64"]["solves_per_s"]
+        out[key] = rec
     return out
 
 
@@ -1210,6 +1298,10 @@ def main():
                     help="grid of the 3D torus workload (0: skip)")
     ap.add_argument("--neumann-n", type=int, default=256,
                     help="grid of the Neumann torus leg (Sec. 7.2.1); 0 skips it")
+    ap.add_argument("--close-n2", type=int, default=1024,
+                    help="grid of Table 2's circles and star in the close-interface leg; 0 skips the leg")
+    ap.add_argument("--close-n3", type=int, default=256,
+                    help="grid of Table 6's torus and ellipsoid in the close-interface leg")
     ap.add_argument("--hetero-n", type=int, default=256,
                     help="grid of the heterogeneous interface leg (Sec. 7.2.5's coefficients); 0 skips it")
     ap.add_argument("--profile-box", default="", choices=["", "dst", "mg"],
