@@ -77,6 +77,71 @@ __global__ void k_exclusive_scan(const int32_t* __restrict__ in, int32_t* __rest
   if (t == 1023) out[n] = base + part[1023];
 }
 
+// Multi-block exclusive scan for long arrays: per chunk of kScanChunk elements
+// its sum, a single-block scan of the sums, then each chunk's scan from its
+// offset (integer sums: the result does not depend on the decomposition).
+constexpr int kScanChunk = 4096;   // 1024 threads x 4 elements
+
+__device__ __forceinline__ int32_t warp_scan_incl_i(int32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// exclusive prefix of v over the 1024 threads of the block, and the total
+__device__ __forceinline__ int32_t block_scan_excl(int32_t v, int32_t* total) {
+  __shared__ int32_t wsum[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int32_t incl = warp_scan_incl_i(v);
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    const int32_t x = wsum[lane];
+    wsum[lane] = warp_scan_incl_i(x) - x;
+  }
+  __syncthreads();
+  const int32_t r = wsum[w] + incl - v;
+  if (total) *total = wsum[31] + __shfl_sync(0xffffffffu, incl, 31);
+  return r;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_sums(const int32_t* __restrict__ in, int n,
+                                                    int32_t* __restrict__ bsum) {
+  const long long i0 = (long long)blockIdx.x * kScanChunk + 4 * threadIdx.x;
+  int32_t s = 0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+    if (i0 + e < n) s += in[i0 + e];
+  int32_t tot = 0;
+  block_scan_excl(s, &tot);
+  if (threadIdx.x == 1023) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_apply(const int32_t* __restrict__ in, int n,
+                                                     const int32_t* __restrict__ boff, int nblk,
+                                                     int32_t* __restrict__ out) {
+  const long long i0 = (long long)blockIdx.x * kScanChunk + 4 * threadIdx.x;
+  int32_t v[4];
+  int32_t s = 0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    v[e] = i0 + e < n ? in[i0 + e] : 0;
+    s += v[e];
+  }
+  int32_t run = boff[blockIdx.x] + block_scan_excl(s, nullptr);
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+    if (i0 + e < n) {
+      out[i0 + e] = run;
+      run += v[e];
+    }
+  if (blockIdx.x == nblk - 1 && threadIdx.x == 0) out[n] = boff[nblk];
+}
+
 // ---------------------------------------------------------------------------
 // Classification (Sec. 5.2): inside iff H(node) < 0, stored as the node's side
 // label (0 outside, 1 + k in Omega^(k); 1 inside for one interface).
@@ -167,26 +232,27 @@ __device__ bool crossing_point(const Grid& g, const LevelSet& L, int k, const Li
   return fabs(nv[D.r]) > cos_alpha;
 }
 
-// The DOFs of edge j of a line whose end nodes carry labels la != lb: slot 0
-// on interface la - 1 (if la > 0), slot 1 on lb - 1 (if lb > 0), each where
-// that H_k changes sign along the edge and |n_r| > cos(alpha).  Returns the
-// count (0..2); the points, normals and interfaces in slot order.
-__device__ int edge_points(const Grid& g, const LevelSet& L, const LineDesc& D, int ia, int ib,
-                           int j, int la, int lb, double cos_alpha, double (*X)[3],
-                           double (*nv)[3], int* ifc) {
+// The interfaces crossed on edge j of a line whose end nodes carry labels
+// la != lb: slot 0 on interface la - 1 (if la > 0), slot 1 on lb - 1 (if
+// lb > 0), with several interfaces only where that H_k changes sign along
+// the edge (with one interface the labels decide: exactly one slot).
+__device__ __forceinline__ int edge_slots(const Grid& g, const LevelSet& L, const LineDesc& D, int ia,
+                                          int ib, int j, int la, int lb, bool multi, int* ks) {
   int c = 0;
-  const int ks[2] = {la - 1, lb - 1};
+  const int cand[2] = {la - 1, lb - 1};
   for (int slot = 0; slot < 2; ++slot) {
-    const int k = ks[slot];
+    const int k = cand[slot];
     if (k < 0) continue;
-    double xa[3] = {0.0, 0.0, 0.0};
-    xa[D.oa] = coord(g, ia);
-    if (g.d == 3) xa[D.ob] = coord(g, ib);
-    double xb[3] = {xa[0], xa[1], xa[2]};
-    xa[D.r] = coord(g, j);
-    xb[D.r] = coord(g, j + 1);
-    if ((ls_H_iface(L, k, xa) < 0.0) == (ls_H_iface(L, k, xb) < 0.0)) continue;
-    if (crossing_point(g, L, k, D, ia, ib, j, cos_alpha, X[c], nv[c])) ifc[c++] = k;
+    if (multi) {
+      double xa[3] = {0.0, 0.0, 0.0};
+      xa[D.oa] = coord(g, ia);
+      if (g.d == 3) xa[D.ob] = coord(g, ib);
+      double xb[3] = {xa[0], xa[1], xa[2]};
+      xa[D.r] = coord(g, j);
+      xb[D.r] = coord(g, j + 1);
+      if ((ls_H_iface(L, k, xa) < 0.0) == (ls_H_iface(L, k, xb) < 0.0)) continue;
+    }
+    ks[c++] = k;
   }
   return c;
 }
@@ -202,13 +268,14 @@ __device__ __forceinline__ int warp_incl_scan(int v) {
   return v;
 }
 
-// One warp per grid line: the lanes test 32 consecutive edges at a time for a
-// change of node label and compute the points of each edge that has one
-// (the per-point arithmetic is the same as a thread walking the line).
+// Candidate points (edge, interface) of the grid lines of one family, a warp
+// per line: the lanes test 32 consecutive edges at a time for a change of
+// node label.  Count pass, then the fill pass writes each line's candidates
+// in edge order (slot order within an edge) after those of the lower lanes.
 constexpr int kLineWarps = 4;
-__global__ void __launch_bounds__(32 * kLineWarps) k_line_count(Grid g, LevelSet L, LineDesc D,
+__global__ void __launch_bounds__(32 * kLineWarps) k_cand_count(Grid g, LevelSet L, LineDesc D,
                                                                 const uint8_t* __restrict__ inside,
-                                                                double cos_alpha, int nlines,
+                                                                bool multi, int nlines,
                                                                 int32_t* __restrict__ count) {
   const int li = blockIdx.x * kLineWarps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -222,24 +289,21 @@ __global__ void __launch_bounds__(32 * kLineWarps) k_line_count(Grid g, LevelSet
     int hits = 0;
     if (j < g.n) {
       const int la = inside[base + j * D.sr], lb = inside[base + (j + 1) * D.sr];
-      if (la != lb) {
-        double X[2][3], nv[2][3];
-        int ifc[2];
-        hits = edge_points(g, L, D, ia, ib, j, la, lb, cos_alpha, X, nv, ifc);
-      }
+      int ks[2];
+      if (la != lb) hits = edge_slots(g, L, D, ia, ib, j, la, lb, multi, ks);
     }
     c += __shfl_sync(0xffffffffu, warp_incl_scan(hits), 31);
   }
   if (lane == 0) count[li] = c;
 }
 
-// The DOFs of one grid line in edge order, a warp per line as in
-// k_line_count: each lane's points go to the line's next free slots after
-// those of the lower lanes (warp prefix sum).
-__global__ void __launch_bounds__(32 * kLineWarps) k_line_fill(
-    Grid g, LevelSet L, LineDesc D, const uint8_t* __restrict__ inside, double cos_alpha, int nlines,
-    const int32_t* __restrict__ start, double* x0, double* x1, double* x2, double* n0, double* n1,
-    double* n2, int32_t* family, int32_t* edge, int32_t* axis, int32_t* iface) {
+__global__ void __launch_bounds__(32 * kLineWarps) k_cand_fill(Grid g, LevelSet L, LineDesc D,
+                                                               const uint8_t* __restrict__ inside,
+                                                               bool multi, int nlines,
+                                                               const int32_t* __restrict__ start,
+                                                               int32_t* __restrict__ cline,
+                                                               int32_t* __restrict__ cedge,
+                                                               int32_t* __restrict__ ciface) {
   const int li = blockIdx.x * kLineWarps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (li >= nlines) return;
@@ -249,38 +313,81 @@ __global__ void __launch_bounds__(32 * kLineWarps) k_line_fill(
   int pos0 = start[li];
   for (int j0 = 0; j0 < g.n; j0 += 32) {
     const int j = j0 + lane;
-    int hits = 0;
-    double X[2][3], nv[2][3];
-    int ifc[2];
+    int hits = 0, ks[2];
     if (j < g.n) {
       const int la = inside[base + j * D.sr], lb = inside[base + (j + 1) * D.sr];
-      if (la != lb) hits = edge_points(g, L, D, ia, ib, j, la, lb, cos_alpha, X, nv, ifc);
+      if (la != lb) hits = edge_slots(g, L, D, ia, ib, j, la, lb, multi, ks);
     }
     const int incl = warp_incl_scan(hits);
     for (int c = 0; c < hits; ++c) {
       const int pos = pos0 + incl - hits + c;
-      x0[pos] = X[c][0];
-      x1[pos] = X[c][1];
-      n0[pos] = nv[c][0];
-      n1[pos] = nv[c][1];
-      if (g.d == 3) {
-        x2[pos] = X[c][2];
-        n2[pos] = nv[c][2];
-      }
-      family[pos] = D.r;
-      edge[pos] = j;
-      iface[pos] = ifc[c];
-      int m = 0;
-      double best = fabs(nv[c][0]);
-      for (int k = 1; k < g.d; ++k)
-        if (fabs(nv[c][k]) > best) {
-          best = fabs(nv[c][k]);
-          m = k;
-        }
-      axis[pos] = m;
+      cline[pos] = li;
+      cedge[pos] = j;
+      ciface[pos] = ks[c];
     }
     pos0 += __shfl_sync(0xffffffffu, incl, 31);
   }
+}
+
+// One thread per candidate: the root of H_k on its edge (Sec. 5.1), the unit
+// normal, and whether the point is a DOF of this family (|n_r| > cos alpha).
+__global__ void k_cand_roots(Grid g, LevelSet L, LineDesc D, int ncand, double cos_alpha,
+                             const int32_t* __restrict__ cline, const int32_t* __restrict__ cedge,
+                             const int32_t* __restrict__ ciface, double* __restrict__ cx,
+                             double* __restrict__ cn, int32_t* __restrict__ keep) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncand) return;
+  int ia, ib;
+  line_other(g, D, cline[c], &ia, &ib);
+  double X[3], nv[3];
+  const bool k = crossing_point(g, L, ciface[c], D, ia, ib, cedge[c], cos_alpha, X, nv);
+  for (int e = 0; e < 3; ++e) {
+    cx[(size_t)e * ncand + c] = X[e];
+    cn[(size_t)e * ncand + c] = nv[e];
+  }
+  keep[c] = k ? 1 : 0;
+}
+
+// The kept candidates in candidate order are the family's DOFs in DOF order:
+// DOF base + kpos[c].
+__global__ void k_cand_scatter(Grid g, LineDesc D, int ncand, int base, const int32_t* __restrict__ kpos,
+                               const int32_t* __restrict__ keep, const int32_t* __restrict__ cedge,
+                               const int32_t* __restrict__ ciface, const double* __restrict__ cx,
+                               const double* __restrict__ cn, double* x0, double* x1, double* x2,
+                               double* n0, double* n1, double* n2, int32_t* family, int32_t* edge,
+                               int32_t* axis, int32_t* iface) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncand || !keep[c]) return;
+  const int pos = base + kpos[c];
+  double nv[3];
+  for (int e = 0; e < 3; ++e) nv[e] = cn[(size_t)e * ncand + c];
+  x0[pos] = cx[c];
+  x1[pos] = cx[(size_t)ncand + c];
+  n0[pos] = nv[0];
+  n1[pos] = nv[1];
+  if (g.d == 3) {
+    x2[pos] = cx[2 * (size_t)ncand + c];
+    n2[pos] = nv[2];
+  }
+  family[pos] = D.r;
+  edge[pos] = cedge[c];
+  iface[pos] = ciface[c];
+  int m = 0;
+  double best = fabs(nv[0]);
+  for (int k = 1; k < g.d; ++k)
+    if (fabs(nv[k]) > best) {
+      best = fabs(nv[k]);
+      m = k;
+    }
+  axis[pos] = m;
+}
+
+// line_start[li] = DOF base + kept candidates before the line's first
+__global__ void k_cand_line_start(int nlines, int base, const int32_t* __restrict__ cstart,
+                                  const int32_t* __restrict__ kpos, int32_t* __restrict__ line_start) {
+  const int li = blockIdx.x * blockDim.x + threadIdx.x;
+  if (li > nlines) return;
+  line_start[li] = base + kpos[cstart[li]];
 }
 
 // ---------------------------------------------------------------------------
@@ -1245,6 +1352,29 @@ static kfbi_status check_flags(kfbi_problem* p, const char* stage) {
   return KFBI_OK;
 }
 
+// out[i] = base + sum_{j<i} in[j] and out[n] = base + total, on stream st:
+// one block for short arrays, the multi-block scan otherwise.
+static kfbi_status scan_exclusive(kfbi_problem* p, const int32_t* in, int32_t* out, int n,
+                                  int32_t base, cudaStream_t st) {
+  if (n <= (1 << 16)) {
+    k_exclusive_scan<<<1, 1024, 0, st>>>(in, out, n, base);
+    KFBI_CUDA(p, cudaGetLastError());
+    return KFBI_OK;
+  }
+  const int nblk = div_up(n, kScanChunk);
+  int32_t *bsum = nullptr, *boff = nullptr;
+  KFBI_CUDA(p, dalloc(&bsum, nblk));
+  KFBI_CUDA(p, dalloc(&boff, nblk + 1));
+  k_scan_sums<<<nblk, 1024, 0, st>>>(in, n, bsum);
+  k_exclusive_scan<<<1, 1024, 0, st>>>(bsum, boff, nblk, base);
+  k_scan_apply<<<nblk, 1024, 0, st>>>(in, n, boff, nblk, out);
+  KFBI_CUDA(p, cudaGetLastError());
+  KFBI_CUDA(p, cudaStreamSynchronize(st));
+  cudaFree(bsum);
+  cudaFree(boff);
+  return KFBI_OK;
+}
+
 kfbi_status build_geometry(kfbi_problem* p) {
   const Grid g = p->g;
   const int d = g.d, n = g.n, n1 = n + 1;
@@ -1263,13 +1393,30 @@ kfbi_status build_geometry(kfbi_problem* p) {
   k_classify<<<div_up(nodes, 256), 256, 0, st>>>(g, L, p->inside);
   KFBI_CUDA(p, cudaGetLastError());
 
-  // ---- DOFs: per family, count per line, scan, fill
+  // ---- DOFs, per family: candidate points per line (a warp per line),
+  // their roots (a thread per candidate), then the kept ones in DOF order
   const int nlines = d == 2 ? n1 : n1 * n1;
   p->nlines = nlines;
-  int32_t* cnt = nullptr;
-  KFBI_CUDA(p, dalloc(&cnt, (size_t)nlines * d));
+  const bool multi = p->n_iface > 1;
   LineDesc D[3];
   long long strides[3] = {d == 2 ? n1 : (long long)n1 * n1, d == 2 ? 1 : n1, 1};
+  struct Cand {
+    int n = 0, kept = 0;
+    int32_t *start = nullptr, *line = nullptr, *edge = nullptr, *iface = nullptr, *keep = nullptr,
+            *kpos = nullptr;
+    double *x = nullptr, *nv = nullptr;
+  } C[3];
+  auto free_cand = [&]() {
+    for (int r = 0; r < 3; ++r) {
+      void* bufs[] = {C[r].start, C[r].line, C[r].edge, C[r].iface, C[r].keep, C[r].kpos, C[r].x, C[r].nv};
+      for (void* q : bufs)
+        if (q) cudaFree(q);
+      C[r] = Cand();
+    }
+  };
+  int32_t* ccnt = nullptr;
+  KFBI_CUDA(p, dalloc(&ccnt, nlines));
+  int32_t base = 0;
   for (int r = 0; r < d; ++r) {
     D[r].r = r;
     int o[2], no = 0;
@@ -1280,27 +1427,47 @@ kfbi_status build_geometry(kfbi_problem* p) {
     D[r].sr = strides[r];
     D[r].sa = strides[o[0]];
     D[r].sb = d == 3 ? strides[o[1]] : 0;
-    k_line_count<<<div_up(nlines, kLineWarps), 32 * kLineWarps, 0, st>>>(g, L, D[r], p->inside, p->cos_alpha,
-                                                      nlines, cnt + (size_t)r * nlines);
+    Cand& c = C[r];
+    k_cand_count<<<div_up(nlines, kLineWarps), 32 * kLineWarps, 0, st>>>(g, L, D[r], p->inside, multi,
+                                                                        nlines, ccnt);
     KFBI_CUDA(p, cudaGetLastError());
-  }
-  // family-by-family exclusive scans with running offsets
-  std::vector<int32_t> tot(d);
-  for (int r = 0; r < d; ++r) {
-    KFBI_CUDA(p, dalloc(&p->line_start[r], nlines + 1));
-  }
-  int32_t base = 0;
-  for (int r = 0; r < d; ++r) {
-    k_exclusive_scan<<<1, 1024, 0, st>>>(cnt + (size_t)r * nlines, p->line_start[r], nlines, base);
-    KFBI_CUDA(p, cudaGetLastError());
-    int32_t last;
-    KFBI_CUDA(p, cudaMemcpyAsync(&last, p->line_start[r] + nlines, sizeof(int32_t),
-                                 cudaMemcpyDeviceToHost, st));
+    KFBI_CUDA(p, dalloc(&c.start, nlines + 1));
+    KFBI_TRY(scan_exclusive(p, ccnt, c.start, nlines, 0, st));
+    KFBI_CUDA(p, cudaMemcpyAsync(&c.n, c.start + nlines, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     KFBI_CUDA(p, cudaStreamSynchronize(st));
-    base = last;
+    KFBI_CUDA(p, dalloc(&c.kpos, c.n + 1));
+    if (c.n > 0) {
+      KFBI_CUDA(p, dalloc(&c.line, c.n));
+      KFBI_CUDA(p, dalloc(&c.edge, c.n));
+      KFBI_CUDA(p, dalloc(&c.iface, c.n));
+      KFBI_CUDA(p, dalloc(&c.keep, c.n));
+      KFBI_CUDA(p, dalloc(&c.x, 3 * (size_t)c.n));
+      KFBI_CUDA(p, dalloc(&c.nv, 3 * (size_t)c.n));
+      k_cand_fill<<<div_up(nlines, kLineWarps), 32 * kLineWarps, 0, st>>>(g, L, D[r], p->inside, multi,
+                                                                         nlines, c.start, c.line, c.edge,
+                                                                         c.iface);
+      // one warp per block: the FP64-bound root iterations spread over all SMs
+      k_cand_roots<<<div_up(c.n, 32), 32, 0, st>>>(g, L, D[r], c.n, p->cos_alpha, c.line, c.edge, c.iface,
+                                                   c.x, c.nv, c.keep);
+      KFBI_CUDA(p, cudaGetLastError());
+      KFBI_TRY(scan_exclusive(p, c.keep, c.kpos, c.n, 0, st));
+      KFBI_CUDA(p, cudaMemcpyAsync(&c.kept, c.kpos + c.n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      KFBI_CUDA(p, cudaStreamSynchronize(st));
+    } else {
+      KFBI_CUDA(p, cudaMemsetAsync(c.kpos, 0, sizeof(int32_t), st));
+    }
+    KFBI_CUDA(p, dalloc(&p->line_start[r], nlines + 1));
+    k_cand_line_start<<<div_up(nlines + 1, 256), 256, 0, st>>>(nlines, base, c.start, c.kpos,
+                                                               p->line_start[r]);
+    KFBI_CUDA(p, cudaGetLastError());
+    base += c.kept;
   }
+  cudaFree(ccnt);
   p->nb = base;
-  if (p->nb == 0) return fail(p, KFBI_ERR_GEOMETRY, "the interface does not cross the grid");
+  if (p->nb == 0) {
+    free_cand();
+    return fail(p, KFBI_ERR_GEOMETRY, "the interface does not cross the grid");
+  }
   const int nb = p->nb;
   for (int k = 0; k < d; ++k) {
     KFBI_CUDA(p, dalloc(&p->x[k], nb));
@@ -1311,14 +1478,21 @@ kfbi_status build_geometry(kfbi_problem* p) {
   KFBI_CUDA(p, dalloc(&p->edge, nb));
   KFBI_CUDA(p, dalloc(&p->axis, nb));
   KFBI_CUDA(p, dalloc(&p->st_axis, nb));
-  for (int r = 0; r < d; ++r) {
-    k_line_fill<<<div_up(nlines, kLineWarps), 32 * kLineWarps, 0, st>>>(
-        g, L, D[r], p->inside, p->cos_alpha, nlines, p->line_start[r], p->x[0], p->x[1],
-        d == 3 ? p->x[2] : p->x[0], p->nrm[0], p->nrm[1], d == 3 ? p->nrm[2] : p->nrm[0],
-        p->family, p->edge, p->axis, p->dof_iface);
-    KFBI_CUDA(p, cudaGetLastError());
+  {
+    int32_t fbase = 0;
+    for (int r = 0; r < d; ++r) {
+      const Cand& c = C[r];
+      if (c.n > 0)
+        k_cand_scatter<<<div_up(c.n, 128), 128, 0, st>>>(
+            g, D[r], c.n, fbase, c.kpos, c.keep, c.edge, c.iface, c.x, c.nv, p->x[0], p->x[1],
+            d == 3 ? p->x[2] : p->x[0], p->nrm[0], p->nrm[1], d == 3 ? p->nrm[2] : p->nrm[0], p->family,
+            p->edge, p->axis, p->dof_iface);
+      KFBI_CUDA(p, cudaGetLastError());
+      fbase += c.kept;
+    }
   }
-  cudaFree(cnt);
+  KFBI_CUDA(p, cudaStreamSynchronize(st));
+  free_cand();
 
   DofView V;
   for (int k = 0; k < 3; ++k) {
@@ -1435,7 +1609,7 @@ kfbi_status build_geometry(kfbi_problem* p) {
   KFBI_CUDA(p, dalloc(&map, nodes));
   KFBI_CUDA(p, cudaMemsetAsync(map, 0xff, sizeof(int32_t) * nodes, st));
   k_row_count<<<div_up(nrows, 128), 128, 0, st>>>(g, p->irr_flag, nrows, rcnt);
-  k_exclusive_scan<<<1, 1024, 0, st>>>(rcnt, rstart, nrows, 0);
+  KFBI_TRY(scan_exclusive(p, rcnt, rstart, nrows, 0, st));
   int32_t nirr = 0;
   KFBI_CUDA(p, cudaMemcpyAsync(&nirr, rstart + nrows, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   KFBI_CUDA(p, cudaStreamSynchronize(st));
@@ -1457,7 +1631,6 @@ kfbi_status build_geometry(kfbi_problem* p) {
   TP.wtotal = d == 2 ? TP.wside * TP.wside : TP.wside * TP.wside * TP.wside;
 
   // ---- correction entries (node, interface k)
-  const bool multi = p->n_iface > 1;
   uint32_t *need = nullptr, *need2 = nullptr;
   uint8_t* close = nullptr;
   int32_t* emap = nullptr;
@@ -1486,7 +1659,7 @@ kfbi_status build_geometry(kfbi_problem* p) {
     KFBI_CUDA(p, dalloc(&ecnt, nrows));
     KFBI_CUDA(p, dalloc(&estart, nrows + 1));
     k_ent_row_count<<<div_up(nrows, 128), 128, 0, st>>>(g, need2, nrows, ecnt);
-    k_exclusive_scan<<<1, 1024, 0, st>>>(ecnt, estart, nrows, 0);
+    KFBI_TRY(scan_exclusive(p, ecnt, estart, nrows, 0, st));
     int32_t nent = 0;
     KFBI_CUDA(p, cudaMemcpyAsync(&nent, estart + nrows, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     KFBI_CUDA(p, cudaStreamSynchronize(st));
@@ -1516,7 +1689,7 @@ kfbi_status build_geometry(kfbi_problem* p) {
     KFBI_CUDA(p, cudaMemsetAsync(ccnt, 0, sizeof(int32_t) * ncell, st));
     KFBI_CUDA(p, cudaMemsetAsync(cur, 0, sizeof(int32_t) * ncell, st));
     k_cell_count<<<div_up(nb, 256), 256, 0, st>>>(g, V, nb, ccnt);
-    k_exclusive_scan<<<1, 1024, 0, st>>>(ccnt, cstart, (int)ncell, 0);
+    KFBI_TRY(scan_exclusive(p, ccnt, cstart, (int)ncell, 0, st));
     k_cell_fill<<<div_up(nb, 256), 256, 0, st>>>(g, V, nb, cstart, cur, items);
     k_closest<<<div_up(nent, 128), 128, 0, st>>>(g, V, nb, nent, p->ent_lin, p->ent_iface, cstart,
                                                  items, p->ent_owner, p->d_flags);
@@ -1548,7 +1721,7 @@ kfbi_status build_geometry(kfbi_problem* p) {
   KFBI_CUDA(p, dalloc(&tptr, 2 * nb + 1));
   k_trace_count<<<div_up(2 * nb, 128), 128, 0, st>>>(g, TP, V, nb, p->inside, p->irr_flag, close,
                                                        need, tcnt);
-  k_exclusive_scan<<<1, 1024, 0, st>>>(tcnt, tptr, 2 * nb, 0);
+  KFBI_TRY(scan_exclusive(p, tcnt, tptr, 2 * nb, 0, st));
   KFBI_CUDA(p, cudaGetLastError());
   std::vector<int32_t> hptr(2 * nb + 1), hcnt(2 * nb);
   KFBI_CUDA(p, cudaMemcpyAsync(hptr.data(), tptr, sizeof(int32_t) * (2 * nb + 1),
