@@ -310,6 +310,8 @@ def run_ours(args, rank, world):
         out["hetero"] = hetero_leg(args, stream, flush)
     if args.close_n2 > 0:
         out["close"] = close_leg(args, stream, flush)
+    if args.moving_n > 0:
+        out["moving"] = moving_leg(args, stream, flush)
     if rank == 0 and args.cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_budget)
     return out
@@ -1118,6 +1120,96 @@ def cpu_stages(args):
     print(json.dumps(out))
 
 
+def moving_leg(args, stream, flush):
+    """A moving interface (the level-set method of the paper's closing
+    remarks): the interface problem of sampled_interface_2d whose shape moves
+    and turns over --moving-steps positions (moving_samples, t = 0.05 k), at
+    --moving-n^2, mixed DST.  Each step takes the interface's node values
+    (already on the device), sets the problem up for them
+    (kfbi_update_levelset), computes the jump data at the new DOFs on the host
+    from their coordinates, and solves to rtol 1e-8 with evaluation.  Timed by
+    the host clock with the device synchronised, against the same steps with
+    a new problem created (and destroyed) per position."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2309_05965_gb300 import kfbi
+    n, T = args.moving_n, args.moving_steps
+    ts = [0.05 * k for k in range(T)]
+    samples = [torch.from_numpy(W.moving_samples(2, n, -1.0, 1.0, t)).cuda() for t in ts]
+    w0 = W.moving_interface_2d(n, 0.0)
+    grid = W.grid_data(w0)      # f and g_b do not depend on the interface's position
+    gkeep = {k: torch.from_numpy(np.ascontiguousarray(grid[k])).cuda()
+             for k in ("f_in", "f_out", "lapf_in", "lapf_out", "g_b")}
+    opts = kfbi.GmresOpts(rtol=args.rtol, restart=100, max_iter=200, x0=None)
+    kw = dict(precision=kfbi.MIXED, box_max_iters=args.box_steps, box_rtol=args.box_rtol, relax=args.relax)
+
+    def step(G, k, errs, its):
+        xyz = torch.zeros((G.nb, 2), dtype=torch.float64, device="cuda")
+        nrm = torch.zeros_like(xyz)
+        kfbi.kfbi_dof_points(G.handle, xyz, nrm)
+        g1, g2 = W.boundary_data(w0, xyz.cpu().numpy(), nrm.cpu().numpy())
+        g1t, g2t = torch.from_numpy(g1).cuda(), torch.from_numpy(g2).cuda()   # alive through the solve
+        d = kfbi.make_data(g1=g1t, g2=g2t, **gkeep)
+        x = torch.zeros(G.nb, dtype=torch.float64, device="cuda")
+        u = torch.zeros(G.grid_shape, dtype=torch.float64, device="cuda")
+        info = kfbi.kfbi_gmres_solve(G.handle, d, opts, x)
+        kfbi.kfbi_evaluate(G.handle, d, x, u)
+        del g1t, g2t
+        its.append(info.iters)
+        if errs is not None:
+            wk = W.moving_interface_2d(n, ts[k])
+            errs.append(float(np.abs(u.cpu().numpy() - W.exact_grid(wk, _inside(G, kfbi)))[1:-1, 1:-1].max()))
+
+    out = {"workload": f"moving interface 2D (moving_samples, {T} positions), N={n}, contrast 10, "
+                       f"4th order, mixed DST, GMRES rtol {args.rtol:g}"}
+    # correctness pass (untimed): errors against the exact solution at every position
+    G = kfbi.Problem.from_workload(w0, **kw)
+    errs, its = [], []
+    for k in range(T):
+        G.update_levelset(W.LS_GRID, [], samples[k])
+        step(G, k, errs, its)
+    out["max_err_vs_exact"] = max(errs)
+    out["gmres_iterations"] = its
+    # timed: update per position
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    t_setup = 0.0
+    its = []
+    for k in range(T):
+        s0 = time.perf_counter()
+        G.update_levelset(W.LS_GRID, [], samples[k])
+        t_setup += time.perf_counter() - s0
+        step(G, k, None, its)
+    torch.cuda.synchronize()
+    t_upd = time.perf_counter() - t0
+    nb = G.nb
+    G.close()
+    # timed: a new problem per position
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    t_create = 0.0
+    for k in range(T):
+        s0 = time.perf_counter()
+        Gk = kfbi.Problem(2, n, -1.0, 1.0, W.LS_GRID, [], W.KIND_INTERFACE_MU, sigma_in=w0.sigma_in,
+                          sigma_out=w0.sigma_out, ls_samples=samples[k], **kw)
+        t_create += time.perf_counter() - s0
+        step(Gk, k, None, [])
+        Gk.close()
+    torch.cuda.synchronize()
+    t_new = time.perf_counter() - t0
+    out.update({"steps": T, "n_b_last": nb,
+                "update": {"steps_per_s": T / t_upd, "ms_per_step": 1e3 * t_upd / T,
+                           "setup_ms_per_step": 1e3 * t_setup / T},
+                "create_per_step": {"steps_per_s": T / t_new, "ms_per_step": 1e3 * t_new / T,
+                                    "setup_ms_per_step": 1e3 * t_create / T},
+                "note": "host clock around whole steps (set-up, jump data on the host from the new DOFs, "
+                        "solve, evaluation); samples resident on the device"})
+    out["speedup_update_vs_create"] = t_new / t_upd
+    return out
+
+
 def config1_leg(args, stream, flush):
     """The 2D interior Dirichlet BVP on the ellipse x^2/0.36 + y^2/0.16 < 1,
     u = e^x sin y, 64^2 grid, 4th order, FP64 DST, GMRES rtol 1e-10.  About
@@ -1298,6 +1390,9 @@ def main():
                     help="grid of the 3D torus workload (0: skip)")
     ap.add_argument("--neumann-n", type=int, default=256,
                     help="grid of the Neumann torus leg (Sec. 7.2.1); 0 skips it")
+    ap.add_argument("--moving-n", type=int, default=1024,
+                    help="grid of the moving-interface leg (update per position vs create per position); 0 skips it")
+    ap.add_argument("--moving-steps", type=int, default=16)
     ap.add_argument("--close-n2", type=int, default=1024,
                     help="grid of Table 2's circles and star in the close-interface leg; 0 skips the leg")
     ap.add_argument("--close-n3", type=int, default=256,

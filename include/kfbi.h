@@ -212,6 +212,16 @@ typedef enum {
 kfbi_status kfbi_create_problem(const kfbi_config* cfg, const kfbi_levelset* ls,
                                 void* cuda_stream, kfbi_problem** out);
 kfbi_status kfbi_destroy_problem(kfbi_problem* p);
+/* A new interface on the same grid and configuration (a moving interface: the
+ * level-set method of the paper's closing remarks, one set-up per time step):
+ * the geometry, stencils, correction entries, trace weights and GMRES
+ * workspace are rebuilt as kfbi_create_problem builds them, while the box
+ * solver, its grids and the streams are kept.  N_b and every size query may
+ * change; densities and starts of the old interface do not apply to the new
+ * one.  The problem must not belong to a batch.  On failure the problem
+ * holds no interface: update it again or destroy it.  Synchronises the
+ * stream. */
+kfbi_status kfbi_update_levelset(kfbi_problem* p, const kfbi_levelset* ls);
 /* Message of the last failure on p; with p == NULL, of the last failed
  * kfbi_create_problem on the calling thread.  Owned by the library. */
 const char* kfbi_last_error(const kfbi_problem* p);

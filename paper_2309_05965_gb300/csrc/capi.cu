@@ -181,6 +181,139 @@ using namespace kfbi;
 // object does not survive a failed create).
 static thread_local std::string g_create_error;
 
+// Checks a level set against the problem's dimension and takes it: kind,
+// parameters, interface count and, for the grid-sampled kind, a device copy
+// of the node values (replacing an earlier copy).
+static kfbi_status set_levelset(kfbi_problem* p, const kfbi_levelset* ls) {
+  const kfbi_config* cfg = &p->cfg;
+  const bool ls2d = ls->kind == KFBI_LS_ELLIPSE || ls->kind == KFBI_LS_STAR || ls->kind == KFBI_LS_DISCS;
+  const bool balls = ls->kind == KFBI_LS_DISCS || ls->kind == KFBI_LS_SPHERES;
+  const bool sampled = ls->kind == KFBI_LS_GRID;
+  if (sampled && !ls->samples)
+    return fail(p, KFBI_ERR_ARG, "a grid-sampled level set needs its node values (samples)");
+  const bool uni = ls->kind == KFBI_LS_UNION;
+  if (ls->n_params < 0 || ls->n_params > KFBI_LS_MAX_PARAMS || ls->kind < 1 || ls->kind > 9 ||
+      (!sampled && !uni && ls2d != (cfg->dim == 2)) ||
+      (balls && (ls->n_params < 2 || !(ls->p[0] > 0) || ls->p[1] < 1 ||
+                 ls->p[1] > KFBI_MAX_INTERFACES ||
+                 2 + cfg->dim * (int)ls->p[1] > ls->n_params)))
+    return fail(p, KFBI_ERR_ARG, "level-set kind does not match the dimension");
+  int n_iface = balls ? (int)ls->p[1] : 1;
+  if (uni) {
+    // m components, each a kind code and that kind's parameters
+    bool ok = ls->n_params >= 1 && ls->p[0] >= 1 && ls->p[0] <= KFBI_MAX_INTERFACES;
+    int at = 1;
+    n_iface = ok ? (int)ls->p[0] : 0;
+    for (int k = 0; ok && k < n_iface; ++k) {
+      if (at >= ls->n_params) {
+        ok = false;
+        break;
+      }
+      const int kind = (int)ls->p[at];
+      int cnt = 0;
+      if (cfg->dim == 2 && (kind == KFBI_LS_ELLIPSE || kind == KFBI_LS_STAR)) cnt = 5;
+      if (cfg->dim == 3 && kind == KFBI_LS_ELLIPSOID) cnt = 6;
+      if (cfg->dim == 3 && kind == KFBI_LS_TORUS) cnt = 2;
+      ok = cnt > 0 && at + 1 + cnt <= ls->n_params;
+      at += 1 + cnt;
+    }
+    if (!ok)
+      return fail(p, KFBI_ERR_ARG, "union level set: m in [1, 32] components of ellipse/star (2D) or "
+                                   "ellipsoid/torus (3D) with their parameters");
+  }
+  p->n_iface = n_iface;
+  p->ls.kind = ls->kind;
+  p->ls.np = ls->n_params;
+  memcpy(p->ls.p, ls->p, sizeof(p->ls.p));
+  p->ls.grid = nullptr;
+  if (p->ls_samples) {
+    cudaFree(p->ls_samples);
+    p->ls_samples = nullptr;
+  }
+  if (sampled) {
+    // the problem keeps its own copy of the node values
+    const long long nodes = p->g.nodes();
+    if (dalloc(&p->ls_samples, nodes) != cudaSuccess ||
+        cudaMemcpy(p->ls_samples, ls->samples, sizeof(double) * nodes, cudaMemcpyDeviceToDevice) != cudaSuccess)
+      return fail(p, KFBI_ERR_CUDA, "cannot copy the level-set samples");
+    p->ls.grid = p->ls_samples;
+    p->ls.gd = p->g.d;
+    p->ls.gn = p->g.n;
+    p->ls.glo = p->g.lo;
+    p->ls.gh = p->g.h;
+  }
+  return KFBI_OK;
+}
+
+// Everything that depends on the interface: geometry, stencils, correction
+// entries, trace weights, the per-DOF work vectors, the GMRES workspace and
+// the captured graphs.  The box solver, the grids R and u, the stencil tables
+// and the streams stay.
+static void free_geometry(kfbi_problem* p) {
+  gmres_destroy(p);
+  if (p->op_exec) cudaGraphExecDestroy(p->op_exec);
+  if (p->op_graph) cudaGraphDestroy(p->op_graph);
+  p->op_exec = nullptr;
+  p->op_graph = nullptr;
+  for (int k = 0; k < KFBI_KC_COUNT; ++k) p->op_counts[k] = 0;
+  int32_t** i32[] = {&p->family, &p->edge, &p->axis, &p->st_axis, &p->pde_node, &p->dir_idx,
+                     &p->neu_idx, &p->irr_lin, &p->dof_iface, &p->ent_lin, &p->ent_iface,
+                     &p->ent_owner, &p->corr_nb, &p->corr_nb2};
+  for (int32_t** b : i32) {
+    if (*b) cudaFree(*b);
+    *b = nullptr;
+  }
+  uint8_t** u8[] = {&p->inside, &p->irr_flag, &p->irr_inside};
+  for (uint8_t** b : u8) {
+    if (*b) cudaFree(*b);
+    *b = nullptr;
+  }
+  double** f64[] = {&p->minv, &p->ent_w, &p->cvals, &p->coef, &p->tvals, &p->bvec, &p->zero_nb,
+                    &p->xbuf, &p->ybuf, &p->gen};
+  for (double** b : f64) {
+    if (*b) cudaFree(*b);
+    *b = nullptr;
+  }
+  if (p->d_flags) cudaFree(p->d_flags);
+  p->d_flags = nullptr;
+  for (int k = 0; k < 3; ++k) {
+    if (p->x[k]) cudaFree(p->x[k]);
+    if (p->nrm[k]) cudaFree(p->nrm[k]);
+    if (p->line_start[k]) cudaFree(p->line_start[k]);
+    p->x[k] = p->nrm[k] = nullptr;
+    p->line_start[k] = nullptr;
+  }
+  // trace CSRs: the per-side arrays point into one allocation made for side 0
+  if (p->tr[0].node) {
+    cudaFree(p->tr[0].node);
+    cudaFree(p->tr[0].irr);
+    if (p->tr[0].irr2) cudaFree(p->tr[0].irr2);
+    cudaFree(p->tr[0].wv);
+    cudaFree(p->tr[0].wn);
+    cudaFree(p->tr[0].w);
+  }
+  for (int s = 0; s < 2; ++s) {
+    if (p->tr[s].ptr) cudaFree(p->tr[s].ptr);
+    p->tr[s] = TraceCSR();
+  }
+  p->nb = p->nirr = p->nent = p->nx = 0;
+}
+
+// The per-DOF work vectors and the GMRES workspace of a set-up geometry (the
+// grids R and u once).
+static kfbi_status alloc_work(kfbi_problem* p) {
+  p->nx = p->cfg.kind == KFBI_INTERFACE_GENERAL ? 2 * p->nb : p->nb;
+  const long long nodes = p->g.nodes();
+  if ((!p->rhs && dalloc(&p->rhs, nodes) != cudaSuccess) ||
+      (!p->ugrid && dalloc(&p->ugrid, nodes) != cudaSuccess) ||
+      dalloc(&p->cvals, p->nent) != cudaSuccess || dalloc(&p->tvals, p->nb) != cudaSuccess ||
+      dalloc(&p->bvec, p->nx) != cudaSuccess || dalloc(&p->xbuf, p->nx) != cudaSuccess ||
+      dalloc(&p->ybuf, p->nx) != cudaSuccess ||
+      (p->cfg.kind == KFBI_INTERFACE_GENERAL && dalloc(&p->gen, 11 * (size_t)p->nb) != cudaSuccess))
+    return fail(p, KFBI_ERR_CUDA, "out of device memory");
+  return gmres_create(p, kMaxKrylov);
+}
+
 extern "C" {
 
 kfbi_status kfbi_create_problem(const kfbi_config* cfg, const kfbi_levelset* ls, void* cuda_stream,
@@ -229,48 +362,6 @@ kfbi_status kfbi_create_problem(const kfbi_config* cfg, const kfbi_levelset* ls,
     fail(p, KFBI_ERR_ARG, "unknown box solver");
     return bail(KFBI_ERR_ARG);
   }
-  const bool ls2d = ls->kind == KFBI_LS_ELLIPSE || ls->kind == KFBI_LS_STAR || ls->kind == KFBI_LS_DISCS;
-  const bool balls = ls->kind == KFBI_LS_DISCS || ls->kind == KFBI_LS_SPHERES;
-  const bool sampled = ls->kind == KFBI_LS_GRID;
-  if (sampled && !ls->samples) {
-    fail(p, KFBI_ERR_ARG, "a grid-sampled level set needs its node values (samples)");
-    return bail(KFBI_ERR_ARG);
-  }
-  const bool uni = ls->kind == KFBI_LS_UNION;
-  if (ls->n_params < 0 || ls->n_params > KFBI_LS_MAX_PARAMS || ls->kind < 1 || ls->kind > 9 ||
-      (!sampled && !uni && ls2d != (cfg->dim == 2)) ||
-      (balls && (ls->n_params < 2 || !(ls->p[0] > 0) || ls->p[1] < 1 ||
-                 ls->p[1] > KFBI_MAX_INTERFACES ||
-                 2 + cfg->dim * (int)ls->p[1] > ls->n_params))) {
-    fail(p, KFBI_ERR_ARG, "level-set kind does not match the dimension");
-    return bail(KFBI_ERR_ARG);
-  }
-  int n_iface = balls ? (int)ls->p[1] : 1;
-  if (uni) {
-    // m components, each a kind code and that kind's parameters
-    bool ok = ls->n_params >= 1 && ls->p[0] >= 1 && ls->p[0] <= KFBI_MAX_INTERFACES;
-    int at = 1;
-    n_iface = ok ? (int)ls->p[0] : 0;
-    for (int k = 0; ok && k < n_iface; ++k) {
-      if (at >= ls->n_params) {
-        ok = false;
-        break;
-      }
-      const int kind = (int)ls->p[at];
-      int cnt = 0;
-      if (cfg->dim == 2 && (kind == KFBI_LS_ELLIPSE || kind == KFBI_LS_STAR)) cnt = 5;
-      if (cfg->dim == 3 && kind == KFBI_LS_ELLIPSOID) cnt = 6;
-      if (cfg->dim == 3 && kind == KFBI_LS_TORUS) cnt = 2;
-      ok = cnt > 0 && at + 1 + cnt <= ls->n_params;
-      at += 1 + cnt;
-    }
-    if (!ok) {
-      fail(p, KFBI_ERR_ARG, "union level set: m in [1, 32] components of ellipse/star (2D) or "
-                            "ellipsoid/torus (3D) with their parameters");
-      return bail(KFBI_ERR_ARG);
-    }
-  }
-  p->n_iface = n_iface;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     fail(p, KFBI_ERR_CUDA, "no CUDA device");
@@ -280,23 +371,9 @@ kfbi_status kfbi_create_problem(const kfbi_config* cfg, const kfbi_levelset* ls,
   p->g.n = cfg->n;
   p->g.lo = cfg->lo;
   p->g.h = (cfg->hi - cfg->lo) / cfg->n;
-  p->ls.kind = ls->kind;
-  p->ls.np = ls->n_params;
-  memcpy(p->ls.p, ls->p, sizeof(p->ls.p));
-  p->ls.grid = nullptr;
-  if (sampled) {
-    // the problem keeps its own copy of the node values
-    const long long nodes = p->g.nodes();
-    if (dalloc(&p->ls_samples, nodes) != cudaSuccess ||
-        cudaMemcpy(p->ls_samples, ls->samples, sizeof(double) * nodes, cudaMemcpyDeviceToDevice) != cudaSuccess) {
-      fail(p, KFBI_ERR_CUDA, "cannot copy the level-set samples");
-      return bail(KFBI_ERR_CUDA);
-    }
-    p->ls.grid = p->ls_samples;
-    p->ls.gd = p->g.d;
-    p->ls.gn = p->g.n;
-    p->ls.glo = p->g.lo;
-    p->ls.gh = p->g.h;
+  {
+    const kfbi_status sl = set_levelset(p, ls);
+    if (sl != KFBI_OK) return bail(sl);
   }
   p->kt = cfg->kind == KFBI_INTERFACE_MU ? cfg->kappa : cfg->kappa / cfg->sigma_in;
   p->mu = cfg->kind == KFBI_INTERFACE_MU
@@ -346,16 +423,7 @@ kfbi_status kfbi_create_problem(const kfbi_config* cfg, const kfbi_levelset* ls,
       return bail(KFBI_ERR_GEOMETRY);
     }
   }
-  const long long nodes = p->g.nodes();
-  if (dalloc(&p->cvals, p->nent) != cudaSuccess || dalloc(&p->rhs, nodes) != cudaSuccess ||
-      dalloc(&p->ugrid, nodes) != cudaSuccess || dalloc(&p->tvals, p->nb) != cudaSuccess ||
-      dalloc(&p->bvec, p->nx) != cudaSuccess || dalloc(&p->xbuf, p->nx) != cudaSuccess ||
-      dalloc(&p->ybuf, p->nx) != cudaSuccess ||
-      (p->cfg.kind == KFBI_INTERFACE_GENERAL && dalloc(&p->gen, 11 * (size_t)p->nb) != cudaSuccess)) {
-    fail(p, KFBI_ERR_CUDA, "out of device memory");
-    return bail(KFBI_ERR_CUDA);
-  }
-  if ((s = gmres_create(p, kMaxKrylov)) != KFBI_OK) return bail(s);
+  if ((s = alloc_work(p)) != KFBI_OK) return bail(s);
   if (cudaStreamSynchronize(p->stream) != cudaSuccess) {
     fail(p, KFBI_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
     return bail(KFBI_ERR_CUDA);
@@ -373,40 +441,39 @@ kfbi_status kfbi_destroy_problem(kfbi_problem* p) {
     kfbi_destroy_problem(p->twin);
     p->twin = nullptr;
   }
-  gmres_destroy(p);
+  free_geometry(p);
   box_destroy(p);
-  if (p->op_exec) cudaGraphExecDestroy(p->op_exec);
-  if (p->op_graph) cudaGraphDestroy(p->op_graph);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->ls_samples) cudaFree(p->ls_samples);
-  if (p->xbuf) cudaFree(p->xbuf);
-  if (p->ybuf) cudaFree(p->ybuf);
-  if (p->gen) cudaFree(p->gen);
-  void* bufs[] = {p->inside, p->irr_flag, p->family, p->edge, p->axis, p->st_axis, p->pde_node,
-                  p->dir_idx, p->neu_idx, p->minv, p->irr_lin, p->irr_inside, p->dof_iface,
-                  p->ent_lin, p->ent_iface, p->ent_owner, p->ent_w, p->corr_nb, p->corr_nb2,
-                  p->nb_off, p->nb_coef, p->cvals, p->coef, p->rhs,
-                  p->ugrid, p->tvals, p->ftilde, p->bvec, p->zero_nb, p->d_flags, p->stencil_dev};
+  void* bufs[] = {p->nb_off, p->nb_coef, p->rhs, p->ugrid, p->ftilde, p->stencil_dev};
   for (void* b : bufs)
     if (b) cudaFree(b);
-  for (int k = 0; k < 3; ++k) {
-    if (p->x[k]) cudaFree(p->x[k]);
-    if (p->nrm[k]) cudaFree(p->nrm[k]);
-    if (p->line_start[k]) cudaFree(p->line_start[k]);
-  }
-  // trace CSRs: the per-side arrays point into one allocation made for side 0
-  if (p->tr[0].node) {
-    cudaFree(p->tr[0].node);
-    cudaFree(p->tr[0].irr);
-    if (p->tr[0].irr2) cudaFree(p->tr[0].irr2);
-    cudaFree(p->tr[0].wv);
-    cudaFree(p->tr[0].wn);
-    cudaFree(p->tr[0].w);
-  }
-  for (int s = 0; s < 2; ++s)
-    if (p->tr[s].ptr) cudaFree(p->tr[s].ptr);
   for (cudaEvent_t e : p->prof.pool) cudaEventDestroy(e);
   delete p;
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_update_levelset(kfbi_problem* p, const kfbi_levelset* ls) {
+  if (!p || !ls) return KFBI_ERR_ARG;
+  if (p->parent) return fail(p, KFBI_ERR_ARG, "update the problem, not its second side operator");
+  KFBI_CUDA(p, cudaStreamSynchronize(p->stream));
+  free_geometry(p);
+  KFBI_TRY(set_levelset(p, ls));
+  KFBI_TRY(build_geometry(p));
+  if (p->twin) {
+    kfbi_problem* q = p->twin;
+    q->stream = p->stream;
+    KFBI_CUDA(p, cudaStreamSynchronize(q->stream));
+    free_geometry(q);
+    kfbi_status s = set_levelset(q, ls);
+    if (s == KFBI_OK) s = build_geometry(q);
+    if (s == KFBI_OK) s = alloc_work(q);
+    if (s != KFBI_OK) return fail(p, s, "kappa_2 operator: " + q->err);
+    if (q->nb != p->nb || q->nirr != p->nirr || q->nent != p->nent)
+      return fail(p, KFBI_ERR_GEOMETRY, "the two side operators set up different DOFs");
+  }
+  KFBI_TRY(alloc_work(p));
+  KFBI_CUDA(p, cudaStreamSynchronize(p->stream));
   return KFBI_OK;
 }
 

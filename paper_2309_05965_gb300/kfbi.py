@@ -74,6 +74,7 @@ SIGNATURES = {
     "kfbi_create_problem": [ctypes.POINTER(Config), ctypes.POINTER(LevelSet), _P,
                             ctypes.POINTER(ctypes.c_void_p)],
     "kfbi_destroy_problem": [_P],
+    "kfbi_update_levelset": [_P, ctypes.POINTER(LevelSet)],
     "kfbi_sizes": [_P, _I, _I, _I],
     "kfbi_num_dofs": [_P, _I],
     "kfbi_dof_points": [_P, _P, _P],
@@ -455,7 +456,8 @@ class Problem:
             # call (the library copies them at create)
             import numpy as np
             import torch
-            keep = torch.as_tensor(np.ascontiguousarray(ls_samples, dtype=np.float64)).cuda()
+            keep = (ls_samples if isinstance(ls_samples, torch.Tensor) else
+                    torch.as_tensor(np.ascontiguousarray(ls_samples, dtype=np.float64)).cuda())
             ls.samples = keep.data_ptr()
         self.cfg = cfg
         self.dim, self.n = dim, n
@@ -464,6 +466,24 @@ class Problem:
         self.nb, self.nirr, self.ncoef = kfbi_sizes(self.handle)
         self.n_iface, self.nent = kfbi_interfaces(self.handle)
         self.npde, self.ndir, self.nneu = kfbi_stencil_sizes(self.handle)
+
+    def update_levelset(self, ls_kind, ls_params, ls_samples=None):
+        """A new interface on the same grid (kfbi_update_levelset); sizes are
+        read back."""
+        ls = LevelSet(kind=ls_kind, n_params=len(ls_params))
+        for i, v in enumerate(ls_params):
+            ls.p[i] = float(v)
+        keep = None
+        if ls_samples is not None:
+            import numpy as np
+            import torch
+            keep = (ls_samples if isinstance(ls_samples, torch.Tensor) else
+                    torch.as_tensor(np.ascontiguousarray(ls_samples, dtype=np.float64)).cuda())
+            ls.samples = keep.data_ptr()
+        _check(load().kfbi_update_levelset(self.handle, ctypes.byref(ls)), self.handle)
+        del keep
+        self.nb, self.nirr, self.ncoef = kfbi_sizes(self.handle)
+        self.n_iface, self.nent = kfbi_interfaces(self.handle)
 
     @classmethod
     def from_workload(cls, w, box_solver=BOX_DST, precision=FP64, **kw):

@@ -665,6 +665,35 @@ def wobbly_samples(dim: int, n: int, lo: float, hi: float) -> np.ndarray:
             + 0.2 * np.sin(3 * X[..., 0]) * np.sin(3 * X[..., 1]) * np.cos(2 * X[..., 2]) - 1.0)
 
 
+def moving_samples(dim: int, n: int, lo: float, hi: float, t: float) -> np.ndarray:
+    """Node values at time t of a moving interface: the wobbly shape of
+    wobbly_samples rotated by 0.6 t about the z axis and translated by
+    0.08 (sin 2t, cos 3t[, 0]) - (0, 0.08[, 0]), so t = 0 is wobbly_samples
+    itself."""
+    h = (hi - lo) / n
+    x = lo + np.arange(n + 1) * h
+    X = np.stack(np.meshgrid(*([x] * dim), indexing="ij"), -1)
+    c = np.array([0.08 * math.sin(2 * t), 0.08 * math.cos(3 * t) - 0.08] + [0.0] * (dim - 2))
+    th = 0.6 * t
+    Y = X - c
+    xr = math.cos(th) * Y[..., 0] + math.sin(th) * Y[..., 1]
+    yr = -math.sin(th) * Y[..., 0] + math.cos(th) * Y[..., 1]
+    if dim == 2:
+        return (xr / 0.62) ** 2 + (yr / 0.45) ** 2 + 0.25 * np.sin(3 * xr) * np.sin(4 * yr) - 1.0
+    z = Y[..., 2]
+    return ((xr / 0.6) ** 2 + (yr / 0.5) ** 2 + (z / 0.45) ** 2
+            + 0.2 * np.sin(3 * xr) * np.sin(3 * yr) * np.cos(2 * z) - 1.0)
+
+
+def moving_interface_2d(n: int = 1024, t: float = 0.0, contrast: float = 10.0) -> Workload:
+    """The interface problem of sampled_interface_2d on the moving shape of
+    moving_samples at time t (sigma_in/sigma_out = contrast, u_in = sin x cos
+    y, u_out = x^2 + y^2: the exact solution holds for every position)."""
+    return Workload(f"moving_interface_2d_t{t:g}", 2, n, -1.0, 1.0, LS_GRID, [], KIND_INTERFACE_MU,
+                    sigma_in=contrast, sigma_out=1.0, exact="sincos_r2",
+                    extra={"samples": moving_samples(2, n, -1.0, 1.0, t)})
+
+
 def sampled_interface_2d(n: int = 256, contrast: float = 10.0) -> Workload:
     """2D Poisson interface problem whose interface is known only by grid
     samples of a level-set function (wobbly_samples), sigma_in/sigma_out =
