@@ -550,24 +550,38 @@ def learned_leg(args, stream, flush):
     t0 = time.perf_counter()
     opts = kfbi.GmresOpts(rtol=1e-10, restart=100, max_iter=100, x0=None)
     axes_train = W.ellipsoid_axes(5966, args.learned_geometries)
-    ds = None
+    # at 64^3 an ellipsoid with axes <= 0.7 has fewer than 12000 DOFs
+    ds = learned.Dataset(len(axes_train) * 12000)
     skipped = 0
+    # one problem moved from ellipsoid to ellipsoid (kfbi_update_levelset);
+    # the fields, and so the grid data, are the same for every geometry
+    w0 = W.wave_ellipsoid_3d(axes_train[0], 64)
+    grid = W.grid_data(w0)
+    gkeep = {k: torch.from_numpy(np.ascontiguousarray(grid[k])).cuda()
+             for k in ("f_in", "f_out", "lapf_in", "lapf_out", "g_b")}
+    G = None
     for axes in axes_train:
         w = W.wave_ellipsoid_3d(axes, 64)
         try:
-            G = kfbi.Problem.from_workload(w, precision=kfbi.MIXED)
+            if G is None:
+                G = kfbi.Problem.from_workload(w, precision=kfbi.MIXED)
+            else:
+                G.update_levelset(w.ls_kind, w.ls_params)
         except kfbi.KfbiError as e:
             if e.status != 2:
                 raise
             skipped += 1
             continue
-        if ds is None:
-            # at 64^3 an ellipsoid with axes <= 0.7 has fewer than 12000 DOFs
-            ds = learned.Dataset(len(axes_train) * 12000)
-        d, keep = _instance_data(w, G)
+        xyz = torch.zeros((G.nb, 3), dtype=torch.float64, device="cuda")
+        nrm = torch.zeros_like(xyz)
+        kfbi.kfbi_dof_points(G.handle, xyz, nrm)
+        g1, g2 = W.boundary_data(w, xyz.cpu().numpy(), nrm.cpu().numpy())
+        g1t, g2t = torch.from_numpy(g1).cuda(), torch.from_numpy(g2).cuda()
+        d = kfbi.make_data(g1=g1t, g2=g2t, **gkeep)
         x = torch.zeros(G.nb, dtype=torch.float64, device="cuda")
         kfbi.kfbi_gmres_solve(G.handle, d, opts, x)
         ds.add(G, d, x)
+    if G is not None:
         G.close()
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
