@@ -11,9 +11,9 @@
 // linear part of the map is resolved beyond bfloat16 precision.  Gradients are those at the rounded weights and update the
 // FP32 masters with Adam (Kingma & Ba 2015, bias-corrected moments).
 //
-// The contractions are small (K = 16 or 256, N = 256) and sit beside
-// HBM-bound solver work, so they run on a tiled SIMT kernel (64x64 tiles,
-// 4x4 outputs per thread, FP32 FMA) rather than on the tensor cores.
+// The contractions (K = 16 or 256, N = 256; the weight gradients K = rows) run
+// on the tensor cores: mma.sync bf16 with FP32 accumulation, FP32 operands
+// split into bf16 parts so that the products keep FP32 precision (k_gemm).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -73,28 +73,61 @@ __device__ __forceinline__ float tof<float>(float v) { return v; }
 template <>
 __device__ __forceinline__ float tof<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
+// ---- tensor-core GEMM: mma.sync m16n8k16, bf16 operands, FP32 accumulation --
+// An FP32 operand enters as a sum of bfloat16 parts, x = hi + mid + lo with
+// each part the bf16 rounding of what the previous parts leave; every product
+// of two bf16 values is exact in FP32, so three parts carry an FP32 value's
+// 24 bits.  Weights already rounded to bf16 are one exact part.
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(x);
+  const float r = x - __bfloat162float(h);
+  m = __float2bfloat16_rn(r);
+  l = __float2bfloat16_rn(r - __bfloat162float(m));
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
+  // a in the low half: the element of the smaller k (or row) index
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+__device__ __forceinline__ void mma16816(float* c, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
 // C (M x N) = A (M x K) B (K x N) with element (i, k) of A at A[i sam + k sak]
 // and (k, j) of B at B[k sbk + j sbn].  blockIdx.z splits K into chunks.
 // mode 0: C = act(acc + bias) [* (1 - gate^2)];  mode 1: C += acc (atomic).
+// 64 x 64 tiles, four warps of 32 x 32 (2 x 4 mma tiles), K steps of 16
+// staged in shared memory as FP32.  A is split in three bf16 parts; B is one
+// part when it is the bf16 weight copy, three when it is an FP32 array.
 template <typename TB>
-__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, int kchunk, const float* __restrict__ A,
+__global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, int kchunk, const float* __restrict__ A,
                                               long long sam, long long sak, const TB* __restrict__ B,
                                               long long sbk, long long sbn, float* __restrict__ C, long long ldc,
                                               const float* __restrict__ bias, int act, const float* __restrict__ gate,
                                               int mode) {
-  __shared__ float As[16][64 + 4];
-  __shared__ float Bs[16][64 + 4];
+  constexpr bool BEXACT = sizeof(TB) == 2;
+  __shared__ float As[16][64 + 4];   // As[k][i]
+  __shared__ float Bs[16][64 + 4];   // Bs[k][j]
   const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
   const int kb = blockIdx.z * kchunk;
   const int ke = min(K, kb + kchunk);
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  float acc[4][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, tq = lane & 3;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  float acc[2][4][4];
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[mi][ni][e] = 0.f;
   for (int k0 = kb; k0 < ke; k0 += 16) {
-    for (int e = threadIdx.x; e < 64 * 16; e += 256) {
+    for (int e = threadIdx.x; e < 64 * 16; e += 128) {
       int i, k;
       if (sam == 1) {
         i = e & 63;
@@ -117,42 +150,78 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, int kchunk, c
       Bs[kk][j] = (gj < N && gk2 < ke) ? tof<TB>(B[gk2 * sbk + gj * sbn]) : 0.f;
     }
     __syncthreads();
+    // A fragments (rows g, g + 8; k pairs 2tq, 2tq + 8) in three parts
+    uint32_t af[3][2][4];
 #pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      float a[4], b[4];
+    for (int mi = 0; mi < 2; ++mi) {
+      const int r = wm + mi * 16 + g;
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+      for (int q = 0; q < 4; ++q) {
+        const int rr = r + ((q & 1) ? 8 : 0);
+        const int kk = 2 * tq + ((q & 2) ? 8 : 0);
+        __nv_bfloat16 h0, m0b, l0, h1, m1b, l1;
+        split3(As[kk][rr], h0, m0b, l0);
+        split3(As[kk + 1][rr], h1, m1b, l1);
+        af[0][mi][q] = pack2(h0, h1);
+        af[1][mi][q] = pack2(m0b, m1b);
+        af[2][mi][q] = pack2(l0, l1);
+      }
+    }
 #pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+    for (int ni = 0; ni < 4; ++ni) {
+      const int col = wn + ni * 8 + g;
+      uint32_t bf[3][2];
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+      for (int q = 0; q < 2; ++q) {
+        const int kk = 2 * tq + (q ? 8 : 0);
+        __nv_bfloat16 h0, m0b, l0, h1, m1b, l1;
+        split3(Bs[kk][col], h0, m0b, l0);
+        split3(Bs[kk + 1][col], h1, m1b, l1);
+        bf[0][q] = pack2(h0, h1);
+        bf[1][q] = pack2(m0b, m1b);
+        bf[2][q] = pack2(l0, l1);
+      }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+      for (int mi = 0; mi < 2; ++mi) {
+        // small terms first: lo, mid, then hi
+        if (BEXACT) {
+          mma16816(acc[mi][ni], af[2][mi], bf[0]);
+          mma16816(acc[mi][ni], af[1][mi], bf[0]);
+          mma16816(acc[mi][ni], af[0][mi], bf[0]);
+        } else {
+          mma16816(acc[mi][ni], af[2][mi], bf[0]);
+          mma16816(acc[mi][ni], af[0][mi], bf[2]);
+          mma16816(acc[mi][ni], af[1][mi], bf[1]);
+          mma16816(acc[mi][ni], af[1][mi], bf[0]);
+          mma16816(acc[mi][ni], af[0][mi], bf[1]);
+          mma16816(acc[mi][ni], af[0][mi], bf[0]);
+        }
+      }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int i = m0 + ty + 16 * r;
-    if (i >= M) continue;
+  for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int j = n0 + tx + 16 * c;
-      if (j >= N) continue;
-      float* o = C + (long long)i * ldc + j;
-      if (mode == 1) {
-        atomicAdd(o, acc[r][c]);
-      } else {
-        float v = acc[r][c] + (bias ? bias[j] : 0.f);
-        if (act) v = tanhf(v);
-        if (gate) {
-          const float g = gate[(long long)i * ldc + j];
-          v *= 1.f - g * g;
+    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = m0 + wm + mi * 16 + g + (e >= 2 ? 8 : 0);
+        const int j = n0 + wn + ni * 8 + 2 * tq + (e & 1);
+        if (i >= M || j >= N) continue;
+        float* o = C + (long long)i * ldc + j;
+        if (mode == 1) {
+          atomicAdd(o, acc[mi][ni][e]);
+        } else {
+          float v = acc[mi][ni][e] + (bias ? bias[j] : 0.f);
+          if (act) v = tanhf(v);
+          if (gate) {
+            const float gt = gate[(long long)i * ldc + j];
+            v *= 1.f - gt * gt;
+          }
+          *o = v;
         }
-        *o = v;
       }
-    }
-  }
 }
 
 // X[i, :] = (raw[r_i, :] - shift) * scale with r_i = rows[i] (i when rows is
@@ -305,7 +374,7 @@ void gemm(cudaStream_t st, int M, int N, int K, const float* A, long long sam, l
     splits = div_up(K, chunk);
   }
   dim3 grid(div_up(N, 64), div_up(M, 64), splits);
-  k_gemm<TB><<<grid, 256, 0, st>>>(M, N, K, chunk, A, sam, sak, B, sbk, sbn, C, ldc, bias, act, gate, mode);
+  k_gemm<TB><<<grid, 128, 0, st>>>(M, N, K, chunk, A, sam, sak, B, sbk, sbn, C, ldc, bias, act, gate, mode);
 }
 
 // forward on rows already normalised into m->X
