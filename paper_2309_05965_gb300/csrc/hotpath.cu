@@ -184,17 +184,17 @@ __global__ void k_rhs_correct_multi(int nirr, int nnb, const int32_t* __restrict
   R[lin[q]] += acc;
 }
 
-// The corrected datum of trace stencil entry e: one interface, u +- C across
-// Gamma (sg = +1 on the '+' side, -1 on the '-' side); several interfaces
+// The corrected datum of trace stencil entry e: one interface, u + C across
+// Gamma on the '+' side, u - C on the '-' side (MINUS); several interfaces
 // u + (C^(t) - C^(l_q)) across, C^(0) = 0.
-template <bool MULTI>
-__device__ __forceinline__ double trace_datum(const TraceCSR& T, int e, double sg,
+template <bool MULTI, bool MINUS>
+__device__ __forceinline__ double trace_datum(const TraceCSR& T, int e,
                                               const double* __restrict__ u,
                                               const double* __restrict__ cv) {
   double w = u[T.node[e]];
   const int j = T.irr[e];
   if (!MULTI) {
-    if (j >= 0) w += sg * cv[j];
+    if (j >= 0) w = MINUS ? w - cv[j] : w + cv[j];
   } else {
     const int j2 = T.irr2[e];
     if (j >= 0 || j2 >= 0) w += (j >= 0 ? cv[j] : 0.0) - (j2 >= 0 ? cv[j2] : 0.0);
@@ -211,24 +211,20 @@ __global__ void k_traces4(int nb, TraceCSR tp, TraceCSR tm, const double* __rest
   int lane = threadIdx.x & 31;
   if (i >= nb) return;
   double s[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int side = 0; side < 2; ++side) {
-    const TraceCSR& T = side == 0 ? tp : tm;
-    double sg = side == 0 ? 1.0 : -1.0;
-    double a = 0.0, b = 0.0;
-    for (int e = T.ptr[i] + lane; e < T.ptr[i + 1]; e += 32) {
-      const double w = trace_datum<MULTI>(T, e, sg, u, cv);
-      a += T.wv[e] * w;
-      b += T.wn[e] * w;
-    }
-    s[2 * side] = warp_sum(a);
-    s[2 * side + 1] = warp_sum(b);
+  for (int e = tp.ptr[i] + lane; e < tp.ptr[i + 1]; e += 32) {
+    const double w = trace_datum<MULTI, false>(tp, e, u, cv);
+    s[0] += tp.wv[e] * w;
+    s[1] += tp.wn[e] * w;
   }
-  if (lane == 0) {
-    if (vp) vp[i] = s[0];
-    if (dp) dp[i] = s[1];
-    if (vm) vm[i] = s[2];
-    if (dm) dm[i] = s[3];
+  for (int e = tm.ptr[i] + lane; e < tm.ptr[i + 1]; e += 32) {
+    const double w = trace_datum<MULTI, true>(tm, e, u, cv);
+    s[2] += tm.wv[e] * w;
+    s[3] += tm.wn[e] * w;
   }
+  // lane 8 q holds sum q: value+, d_n+, value-, d_n-
+  const double t = warp_sum4(s);
+  double* out = (lane >> 3) == 0 ? vp : (lane >> 3) == 1 ? dp : (lane >> 3) == 2 ? vm : dm;
+  if ((lane & 7) == 0 && out) out[i] = t;
 }
 
 // The operator's trace quantity t (average value for the Dirichlet form,
@@ -243,9 +239,9 @@ __global__ void k_trace_op(int nb, TraceCSR tp, TraceCSR tm, const double* __res
   if (i >= nb) return;
   double acc = 0.0;
   for (int e = tp.ptr[i] + lane; e < tp.ptr[i + 1]; e += 32)
-    acc += tp.w[e] * trace_datum<MULTI>(tp, e, 1.0, u, cv);
+    acc += tp.w[e] * trace_datum<MULTI, false>(tp, e, u, cv);
   for (int e = tm.ptr[i] + lane; e < tm.ptr[i + 1]; e += 32)
-    acc += tm.w[e] * trace_datum<MULTI>(tm, e, -1.0, u, cv);
+    acc += tm.w[e] * trace_datum<MULTI, true>(tm, e, u, cv);
   acc = warp_sum(acc);
   if (lane == 0) y[i] = (x ? alpha * x[i] : 0.0) + beta * acc;
 }

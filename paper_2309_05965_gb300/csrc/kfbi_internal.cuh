@@ -250,6 +250,23 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// Totals of four per-lane values over the warp, by a reduce-scatter
+// butterfly (6 adds per lane instead of 4 x 5): lane 8 q returns the total of
+// s[q], as do the other lanes of its group of 8.
+__device__ __forceinline__ double warp_sum4(const double* s) {
+  const int lane = threadIdx.x & 31;
+  const bool h4 = (lane & 16) != 0, h3 = (lane & 8) != 0;
+  double k0 = h4 ? s[2] : s[0], k1 = h4 ? s[3] : s[1];
+  const double o0 = h4 ? s[0] : s[2], o1 = h4 ? s[1] : s[3];
+  k0 += __shfl_xor_sync(0xffffffffu, o0, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, o1, 16);
+  double k = h3 ? k1 : k0;
+  const double o = h3 ? k0 : k1;
+  k += __shfl_xor_sync(0xffffffffu, o, 8);
+#pragma unroll
+  for (int m = 4; m > 0; m >>= 1) k += __shfl_xor_sync(0xffffffffu, k, m);
+  return k;
+}
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
