@@ -296,22 +296,19 @@ def run_ours(args, rank, world):
         "roofline": roof,
     }
     G.close()
-    if args.config1:
-        out["config1"] = config1_leg(args, stream, flush)
-    if args.batch > 0:
-        out["batched"] = batched(args, stream, flush)
-    if args.learned_n > 0:
-        out["learned"] = learned_leg(args, stream, flush)
-    if args.threed_n > 0:
-        out["threed"] = threed_leg(args, stream, flush)
-    if args.neumann_n > 0:
-        out["neumann"] = neumann_leg(args, stream, flush)
-    if args.hetero_n > 0:
-        out["hetero"] = hetero_leg(args, stream, flush)
-    if args.close_n2 > 0:
-        out["close"] = close_leg(args, stream, flush)
-    if args.moving_n > 0:
-        out["moving"] = moving_leg(args, stream, flush)
+    legs = [("config1", args.config1, config1_leg), ("batched", args.batch > 0, batched),
+            ("learned", args.learned_n > 0, learned_leg), ("threed", args.threed_n > 0, threed_leg),
+            ("neumann", args.neumann_n > 0, neumann_leg), ("hetero", args.hetero_n > 0, hetero_leg),
+            ("close", args.close_n2 > 0, close_leg), ("moving", args.moving_n > 0, moving_leg)]
+    for name, on, leg in legs:
+        if not on:
+            continue
+        # each leg starts from torch's allocator emptied of the previous legs'
+        # blocks (the learned leg's training set alone is ~300 MB), so that a
+        # leg's timing does not depend on what ran before it
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        out[name] = leg(args, stream, flush)
     if rank == 0 and args.cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_budget)
     return out
