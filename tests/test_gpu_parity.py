@@ -36,8 +36,17 @@ CASES = {
     # close interfaces: two discs 0.004 apart (below the grid step), each with
     # its own interior solution; Sec. 7.1.2's touching circles and star
     "close_discs128": lambda: W.close_discs_2d(128),
+    # the interior Dirichlet problem on the same two close discs (two
+    # components of Omega, each with its own solution)
+    "close_discs_dirichlet128": lambda: _close_dirichlet(),
     "touching256": lambda: W.touching_interfaces_2d(256),
 }
+
+
+def _close_dirichlet():
+    w = W.close_discs_2d(128)
+    w.kind = W.KIND_DIRICHLET
+    return w
 
 
 def _order2():

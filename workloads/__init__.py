@@ -345,9 +345,16 @@ def grid_coords(w: Workload) -> np.ndarray:
 def _grid_data_multi(w: Workload):
     """grid_data of a per-interface workload: f_in, lapf_in and u_in have a
     leading axis of length K (grid k is interface k's f, smoothly extended)."""
-    assert w.kind in (KIND_INTERFACE_MU, KIND_INTERFACE_GENERAL)
+    assert w.kind in (KIND_INTERFACE_MU, KIND_INTERFACE_GENERAL, KIND_DIRICHLET)
     X = grid_coords(w)
     ins, (uo, _, lo_, l2o) = multi_solutions(w)
+    if w.kind == KIND_DIRICHLET:
+        # interior BVP: f = sigma lap u - kappa u inside, no outer data
+        f_in = np.stack([w.sigma_in * li(X) - w.kappa * ui(X) for ui, _, li, _ in ins])
+        lapf_in = np.stack([w.sigma_in * l2(X) - w.kappa * li(X) for _, _, li, l2 in ins])
+        z = np.zeros(X.shape[:-1])
+        return dict(f_in=f_in, f_out=z, lapf_in=lapf_in, lapf_out=z.copy(),
+                    u_in=np.stack([ui(X) for ui, _, _, _ in ins]), u_out=z.copy(), g_b=z.copy())
     # the mu-form workloads are Poisson problems (as in grid_data)
     k_in, k_out = (w.kappa, w.kappa_out) if w.kind == KIND_INTERFACE_GENERAL else (0.0, 0.0)
     f_in = np.stack([w.sigma_in * li(X) - k_in * ui(X) for ui, _, li, _ in ins])
