@@ -227,6 +227,134 @@ __global__ void k_traces4(int nb, TraceCSR tp, TraceCSR tm, const double* __rest
   if ((lane & 7) == 0 && out) out[i] = t;
 }
 
+// ---- the 3D trace sums in FP32 pairs ------------------------------------------
+// GB300 issues FP64 at 2 lanes per clock per SM against 128 for FP32, and the
+// 3D trace kernels spend their time there (two FMAs per stencil entry).  Their
+// sums run here in "double-float" arithmetic on the FP32 pipe instead: a value
+// is an unevaluated pair hi + lo of floats (~48 bits), products use the exact
+// FMA residual, sums the error-free two-sum (Dekker 1971; Knuth, TAOCP vol. 2,
+// 4.2.2); every step is written with the _rn intrinsics so that no product
+// and sum are contracted into an FMA.
+struct DFlt {
+  float hi, lo;
+};
+
+// An FP64 value as hi + lo: hi its leading 24 bits, lo the next 23, both
+// assembled from the bit pattern with integer operations (the FP64-to-FP32
+// conversion would issue to the FP64 pipe).  |x| < 2^-126 gives 0 (far below
+// any term of a trace sum), non-finite values stay non-finite in hi.
+__device__ __forceinline__ float2 split_f64(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+  const unsigned sign = h32 & 0x80000000u;
+  const int e = (int)((h32 >> 20) & 0x7ffu);
+  if (e == 0x7ff)
+    return make_float2(__uint_as_float(sign | 0x7f800000u | (((h32 & 0xfffffu) | l32) ? 0x400000u : 0u)), 0.f);
+  const int fe = e - 896;                          // FP32 exponent field of x
+  if (fe <= 0) return make_float2(0.f, 0.f);
+  if (fe >= 255) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
+  const float hi = __uint_as_float(sign | ((unsigned)fe << 23) | ((h32 & 0xfffffu) << 3) | (l32 >> 29));
+  // the remaining 29 mantissa bits are r 2^(e - 1075); their top 23 bits,
+  // (r >> 6) 2^(e - 1069), are exact in FP32
+  const unsigned r = (l32 & 0x1fffffffu) >> 6;
+  const float rf = __fsub_rn(__uint_as_float(0x4b000000u | r), 8388608.f);
+  const int le = e - 942;                          // FP32 exponent field of 2^(e - 1069)
+  float lo = le > 0 ? __fmul_rn(rf, __uint_as_float((unsigned)le << 23)) : 0.f;
+  return make_float2(hi, sign ? -lo : lo);
+}
+
+// acc += w u (w, u as pairs; the lo x lo product is dropped)
+__device__ __forceinline__ void df_fma(DFlt& acc, float2 w, float2 u) {
+  const float p = __fmul_rn(w.x, u.x);
+  float e = __fmaf_rn(w.x, u.x, -p);
+  e = __fmaf_rn(w.x, u.y, e);
+  e = __fmaf_rn(w.y, u.x, e);
+  const float t = __fadd_rn(acc.hi, p);
+  const float z = __fsub_rn(t, acc.hi);
+  const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(t, z)), __fsub_rn(p, z));
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
+  acc.hi = t;
+}
+
+__device__ __forceinline__ DFlt df_add(DFlt a, DFlt b) {
+  const float t = __fadd_rn(a.hi, b.hi);
+  const float z = __fsub_rn(t, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(t, z)), __fsub_rn(b.hi, z));
+  const float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), err);
+  // renormalise (fast two-sum: |t| >= |lo|)
+  const float s = __fadd_rn(t, lo);
+  return DFlt{s, __fsub_rn(lo, __fsub_rn(s, t))};
+}
+
+__device__ __forceinline__ DFlt df_shfl_xor(DFlt a, int m) {
+  return DFlt{__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m)};
+}
+
+__device__ __forceinline__ double df_value(DFlt a) { return (double)a.hi + (double)a.lo; }
+
+// One stencil entry into the pair sums of the value and normal-derivative
+// weights: w (u + corrections), the corrections C as in trace_datum, each its
+// own product.
+template <bool MULTI, bool MINUS>
+__device__ __forceinline__ void trace_entry2_df(const TraceCSR& T, int e, const double* __restrict__ u,
+                                                const double* __restrict__ cv, DFlt& av, DFlt& an) {
+  const float2 wv = T.wv2[e], wn = T.wn2[e];
+  const float2 uu = split_f64(u[T.node[e]]);
+  df_fma(av, wv, uu);
+  df_fma(an, wn, uu);
+  const int j = T.irr[e];
+  if (!MULTI) {
+    if (j >= 0) {
+      float2 c = split_f64(cv[j]);
+      if (MINUS) c = make_float2(-c.x, -c.y);
+      df_fma(av, wv, c);
+      df_fma(an, wn, c);
+    }
+  } else {
+    const int j2 = T.irr2[e];
+    if (j >= 0) {
+      const float2 c = split_f64(cv[j]);
+      df_fma(av, wv, c);
+      df_fma(an, wn, c);
+    }
+    if (j2 >= 0) {
+      float2 c = split_f64(cv[j2]);
+      c = make_float2(-c.x, -c.y);
+      df_fma(av, wv, c);
+      df_fma(an, wn, c);
+    }
+  }
+}
+
+// k_traces4 in pair arithmetic (3D), the four sums reduced by the same
+// reduce-scatter butterfly as warp_sum4
+template <bool MULTI>
+__global__ void k_traces4_df(int nb, TraceCSR tp, TraceCSR tm, const double* __restrict__ u,
+                             const double* __restrict__ cv, double* vp, double* vm, double* dp,
+                             double* dm) {
+  int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (i >= nb) return;
+  DFlt s[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  for (int e = tp.ptr[i] + lane; e < tp.ptr[i + 1]; e += 32)
+    trace_entry2_df<MULTI, false>(tp, e, u, cv, s[0], s[1]);
+  for (int e = tm.ptr[i] + lane; e < tm.ptr[i + 1]; e += 32)
+    trace_entry2_df<MULTI, true>(tm, e, u, cv, s[2], s[3]);
+  for (int q = 0; q < 4; ++q) s[q] = df_add(s[q], DFlt{0.f, 0.f});
+  const bool h4 = (lane & 16) != 0, h3 = (lane & 8) != 0;
+  DFlt k0 = h4 ? s[2] : s[0], k1 = h4 ? s[3] : s[1];
+  const DFlt o0 = h4 ? s[0] : s[2], o1 = h4 ? s[1] : s[3];
+  k0 = df_add(k0, df_shfl_xor(o0, 16));
+  k1 = df_add(k1, df_shfl_xor(o1, 16));
+  DFlt k = h3 ? k1 : k0;
+  const DFlt o = h3 ? k0 : k1;
+  k = df_add(k, df_shfl_xor(o, 8));
+#pragma unroll
+  for (int m = 4; m > 0; m >>= 1) k = df_add(k, df_shfl_xor(k, m));
+  double* out = (lane >> 3) == 0 ? vp : (lane >> 3) == 1 ? dp : (lane >> 3) == 2 ? vm : dm;
+  if ((lane & 7) == 0 && out) out[i] = df_value(k);
+}
+
 // The operator's trace quantity t (average value for the Dirichlet form,
 // average normal derivative for the mu-form; weights carry the 1/2) fused with
 // the BIE combination y = alpha x + beta t.
@@ -416,7 +544,15 @@ kfbi_status launch_rhs(kfbi_problem* p, const double* cvals, const kfbi_data* da
 
 kfbi_status launch_traces(kfbi_problem* p, const double* u, const double* cvals, double* vp,
                           double* vm, double* dp, double* dm) {
-  if (p->n_iface > 1)
+  // 3D: the pair-arithmetic kernels (FP64 pipe bound otherwise)
+  const bool df = p->tr[0].wv2 != nullptr;
+  if (p->n_iface > 1 && df)
+    KFBI_LAUNCH(p, KFBI_KC_TRACE, k_traces4_df<true><<<div_up(p->nb, 8), 256, 0, p->stream>>>(
+        p->nb, p->tr[0], p->tr[1], u, cvals, vp, vm, dp, dm));
+  else if (df)
+    KFBI_LAUNCH(p, KFBI_KC_TRACE, k_traces4_df<false><<<div_up(p->nb, 8), 256, 0, p->stream>>>(
+        p->nb, p->tr[0], p->tr[1], u, cvals, vp, vm, dp, dm));
+  else if (p->n_iface > 1)
     KFBI_LAUNCH(p, KFBI_KC_TRACE, k_traces4<true><<<div_up(p->nb, 8), 256, 0, p->stream>>>(
         p->nb, p->tr[0], p->tr[1], u, cvals, vp, vm, dp, dm));
   else

@@ -77,6 +77,11 @@ struct TraceCSR {
   double* wv = nullptr;      // value weights
   double* wn = nullptr;      // normal-derivative weights
   double* w = nullptr;       // weights of the operator's own trace quantity
+  // 3D: wv and wn hold FP32 pairs instead (x = hi, y = lo, the weight = hi +
+  // lo to ~48 bits), read through these aliases by the four-trace kernel that
+  // keeps its sums off the FP64 pipe
+  float2* wv2 = nullptr;
+  float2* wn2 = nullptr;
   int nnz = 0;
 };
 

@@ -1043,6 +1043,19 @@ __global__ void k_corr_lists_multi(Grid g, int nirr, const int32_t* __restrict__
   }
 }
 
+// FP64 weights replaced in place by FP32 pairs (same 8 bytes): hi = the FP32
+// rounding, lo = that of the rest.
+__global__ void k_split_weights(int n, double* a, double* b) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  double* arr[2] = {a, b};
+  for (int k = 0; k < 2; ++k) {
+    const double v = arr[k][e];
+    const float h = (float)v;
+    reinterpret_cast<float2*>(arr[k])[e] = make_float2(h, (float)(v - (double)h));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Trace stencils and weighted least-squares weights (Sec. 5.5).
 // ---------------------------------------------------------------------------
@@ -1772,6 +1785,17 @@ kfbi_status build_geometry(kfbi_problem* p) {
     c.wv = twv + b0;
     c.wn = twn + b0;
     c.w = tw + b0;
+  }
+  if (d == 3 && nnz_all > 0) {
+    // the 3D four-trace kernel reads value and normal-derivative weights as
+    // FP32 pairs (the operator's own trace keeps FP64: it is memory-bound)
+    k_split_weights<<<div_up(nnz_all, 256), 256, 0, st>>>(nnz_all, twv, twn);
+    KFBI_CUDA(p, cudaGetLastError());
+    for (int s = 0; s < 2; ++s) {
+      TraceCSR& c = p->tr[s];
+      c.wv2 = reinterpret_cast<float2*>(c.wv);
+      c.wn2 = reinterpret_cast<float2*>(c.wn);
+    }
   }
   KFBI_CUDA(p, cudaStreamSynchronize(st));
   cudaFree(tcnt);
