@@ -31,7 +31,9 @@ Readings where the paper is silent (the same written rules bind the CUDA path):
     it lies deeper in, and the edge to the other component crosses one
     interface);
   * root iteration: start at the linear interpolant, Newton step, bisection
-    whenever Newton leaves the bracket, stop when |ds| <= 1e-15 h (<= 64 steps);
+    whenever Newton leaves the bracket, stop when |ds| <= 1e-15 N h, 1e-15 of
+    the box width, about the FP64 spacing of a coordinate there (<= 64
+    steps);
   * stencil rules: see ``collocation_stencil``.
 """
 from __future__ import annotations
@@ -108,7 +110,7 @@ def find_roots(grid: Grid, kind: int, p, x0: np.ndarray, r: int, iface: int = 0)
         bad = ~((s_new > lo_s[idx]) & (s_new < hi_s[idx])) | (df == 0.0)
         s_new = np.where(bad, 0.5 * (lo_s[idx] + hi_s[idx]), s_new)
         s_new = np.where(done_zero, s[idx], s_new)
-        conv = done_zero | (np.abs(s_new - s[idx]) <= ROOT_TOL * h)
+        conv = done_zero | (np.abs(s_new - s[idx]) <= ROOT_TOL * (grid.n * h))
         s[idx] = s_new
         active[idx[conv]] = False
     return s

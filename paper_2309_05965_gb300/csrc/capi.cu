@@ -4,6 +4,7 @@
 // the final evaluation by superposition (Sec. 6).
 #include <chrono>
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -226,14 +227,11 @@ static kfbi_status set_levelset(kfbi_problem* p, const kfbi_levelset* ls) {
   p->ls.np = ls->n_params;
   memcpy(p->ls.p, ls->p, sizeof(p->ls.p));
   p->ls.grid = nullptr;
-  if (p->ls_samples) {
-    cudaFree(p->ls_samples);
-    p->ls_samples = nullptr;
-  }
   if (sampled) {
-    // the problem keeps its own copy of the node values
+    // the problem keeps its own copy of the node values (one buffer of the
+    // grid's size, kept across updates)
     const long long nodes = p->g.nodes();
-    if (dalloc(&p->ls_samples, nodes) != cudaSuccess ||
+    if ((!p->ls_samples && dalloc(&p->ls_samples, nodes) != cudaSuccess) ||
         cudaMemcpy(p->ls_samples, ls->samples, sizeof(double) * nodes, cudaMemcpyDeviceToDevice) != cudaSuccess)
       return fail(p, KFBI_ERR_CUDA, "cannot copy the level-set samples");
     p->ls.grid = p->ls_samples;
@@ -244,6 +242,49 @@ static kfbi_status set_levelset(kfbi_problem* p, const kfbi_levelset* ls) {
   }
   return KFBI_OK;
 }
+
+namespace kfbi {
+
+cudaError_t arena_alloc(GeoArena& A, size_t bytes, void** out) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (A.chunks.empty() || A.used + bytes > A.cap) {
+    // a new chunk of at least half of what this set-up has taken so far:
+    // few chunks, and at most a third of the memory unused
+    const size_t sz = std::max(bytes, std::max(A.total / 2, (size_t)16 << 20));
+    char* c = nullptr;
+    const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&c), sz);
+    if (e != cudaSuccess) return e;
+    A.chunks.push_back(c);
+    A.cap = sz;
+    A.used = 0;
+  }
+  *out = A.chunks.back() + A.used;
+  A.used += bytes;
+  A.total += bytes;
+  return cudaSuccess;
+}
+
+void arena_reset(GeoArena& A) {
+  if (A.chunks.size() > 1) {
+    const size_t want = A.total + A.total / 4;
+    arena_release(A);
+    char* c = nullptr;
+    if (cudaMalloc(reinterpret_cast<void**>(&c), want) == cudaSuccess) {
+      A.chunks.push_back(c);
+      A.cap = want;
+    }
+  }
+  A.used = 0;
+  A.total = 0;
+}
+
+void arena_release(GeoArena& A) {
+  for (char* c : A.chunks) cudaFree(c);
+  A.chunks.clear();
+  A.cap = A.used = A.total = 0;
+}
+
+}  // namespace kfbi
 
 // Everything that depends on the interface: geometry, stencils, correction
 // entries, trace weights, the per-DOF work vectors, the GMRES workspace and
@@ -256,46 +297,24 @@ static void free_geometry(kfbi_problem* p) {
   p->op_exec = nullptr;
   p->op_graph = nullptr;
   for (int k = 0; k < KFBI_KC_COUNT; ++k) p->op_counts[k] = 0;
+  // every array below lies in the geometry arena: no kernel may still read
+  // them when the arena is reused (one device-wide wait, as cudaFree makes)
+  cudaDeviceSynchronize();
   int32_t** i32[] = {&p->family, &p->edge, &p->axis, &p->st_axis, &p->pde_node, &p->dir_idx,
                      &p->neu_idx, &p->irr_lin, &p->dof_iface, &p->ent_lin, &p->ent_iface,
                      &p->ent_owner, &p->corr_nb, &p->corr_nb2};
-  for (int32_t** b : i32) {
-    if (*b) cudaFree(*b);
-    *b = nullptr;
-  }
+  for (int32_t** b : i32) *b = nullptr;
   uint8_t** u8[] = {&p->inside, &p->irr_flag, &p->irr_inside};
-  for (uint8_t** b : u8) {
-    if (*b) cudaFree(*b);
-    *b = nullptr;
-  }
-  double** f64[] = {&p->minv, &p->ent_w, &p->cvals, &p->coef, &p->tvals, &p->bvec, &p->zero_nb,
-                    &p->xbuf, &p->ybuf, &p->gen};
-  for (double** b : f64) {
-    if (*b) cudaFree(*b);
-    *b = nullptr;
-  }
-  if (p->d_flags) cudaFree(p->d_flags);
+  for (uint8_t** b : u8) *b = nullptr;
+  double** f64[] = {&p->minv, &p->ent_w, &p->cvals, &p->tvals, &p->bvec, &p->xbuf, &p->ybuf, &p->gen};
+  for (double** b : f64) *b = nullptr;
   p->d_flags = nullptr;
   for (int k = 0; k < 3; ++k) {
-    if (p->x[k]) cudaFree(p->x[k]);
-    if (p->nrm[k]) cudaFree(p->nrm[k]);
-    if (p->line_start[k]) cudaFree(p->line_start[k]);
     p->x[k] = p->nrm[k] = nullptr;
     p->line_start[k] = nullptr;
   }
-  // trace CSRs: the per-side arrays point into one allocation made for side 0
-  if (p->tr[0].node) {
-    cudaFree(p->tr[0].node);
-    cudaFree(p->tr[0].irr);
-    if (p->tr[0].irr2) cudaFree(p->tr[0].irr2);
-    cudaFree(p->tr[0].wv);
-    cudaFree(p->tr[0].wn);
-    cudaFree(p->tr[0].w);
-  }
-  for (int s = 0; s < 2; ++s) {
-    if (p->tr[s].ptr) cudaFree(p->tr[s].ptr);
-    p->tr[s] = TraceCSR();
-  }
+  for (int s = 0; s < 2; ++s) p->tr[s] = TraceCSR();
+  arena_reset(p->arena);
   p->nb = p->nirr = p->nent = p->nx = 0;
 }
 
@@ -306,10 +325,10 @@ static kfbi_status alloc_work(kfbi_problem* p) {
   const long long nodes = p->g.nodes();
   if ((!p->rhs && dalloc(&p->rhs, nodes) != cudaSuccess) ||
       (!p->ugrid && dalloc(&p->ugrid, nodes) != cudaSuccess) ||
-      dalloc(&p->cvals, p->nent) != cudaSuccess || dalloc(&p->tvals, p->nb) != cudaSuccess ||
-      dalloc(&p->bvec, p->nx) != cudaSuccess || dalloc(&p->xbuf, p->nx) != cudaSuccess ||
-      dalloc(&p->ybuf, p->nx) != cudaSuccess ||
-      (p->cfg.kind == KFBI_INTERFACE_GENERAL && dalloc(&p->gen, 11 * (size_t)p->nb) != cudaSuccess))
+      galloc(p, &p->cvals, p->nent) != cudaSuccess || galloc(p, &p->tvals, p->nb) != cudaSuccess ||
+      galloc(p, &p->bvec, p->nx) != cudaSuccess || galloc(p, &p->xbuf, p->nx) != cudaSuccess ||
+      galloc(p, &p->ybuf, p->nx) != cudaSuccess ||
+      (p->cfg.kind == KFBI_INTERFACE_GENERAL && galloc(p, &p->gen, 11 * (size_t)p->nb) != cudaSuccess))
     return fail(p, KFBI_ERR_CUDA, "out of device memory");
   return gmres_create(p, kMaxKrylov);
 }
@@ -442,6 +461,7 @@ kfbi_status kfbi_destroy_problem(kfbi_problem* p) {
     p->twin = nullptr;
   }
   free_geometry(p);
+  arena_release(p->arena);
   box_destroy(p);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->ls_samples) cudaFree(p->ls_samples);

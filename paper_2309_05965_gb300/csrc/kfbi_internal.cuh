@@ -27,7 +27,7 @@ constexpr int kMaxDir = 15;
 constexpr int kMaxNeu = 10;
 constexpr int kMaxNeighbours = 26;    // 3^3 - 1
 constexpr double kTieEps = 1e-12;     // closest-point tie tolerance (units of h^2)
-constexpr double kRootTol = 1e-15;    // root iteration stop |ds| <= tol h
+constexpr double kRootTol = 1e-15;    // root iteration stop |ds| <= tol N h (the box width)
 constexpr int kRootMaxIt = 64;
 constexpr int kMaxKrylov = 100;     // Krylov dimension of every problem (restart length)
 constexpr int kGraphArnoldi = 8192; // N_b up to which a GMRES iteration is one graph
@@ -127,6 +127,22 @@ struct Gmres {
   long long it_counts[KFBI_KC_COUNT] = {};
 };
 
+// Device memory of one geometry: every array that the set-up and the per-DOF
+// work allocation make, temporaries included, bump-allocated (256-byte
+// aligned) from chunks of cudaMalloc.  A new interface on the same grid
+// resets it instead of freeing and allocating each array; after a set-up
+// that needed several chunks the reset replaces them by one that holds them
+// all, so the next set-up of a similar interface makes no allocation.
+struct GeoArena {
+  std::vector<char*> chunks;
+  size_t cap = 0;     // bytes of the last chunk
+  size_t used = 0;    // bytes handed out from the last chunk
+  size_t total = 0;   // bytes handed out since the last reset
+};
+cudaError_t arena_alloc(GeoArena& A, size_t bytes, void** out);
+void arena_reset(GeoArena& A);
+void arena_release(GeoArena& A);
+
 }  // namespace kfbi
 
 struct kfbi_problem {
@@ -189,13 +205,11 @@ struct kfbi_problem {
   // box solver + work
   kfbi::BoxSolver* box = nullptr;
   double* cvals = nullptr;       // [n_ent]
-  double* coef = nullptr;        // [N_b][ncoef] (stage output scratch)
   double* rhs = nullptr;         // grid
   double* ugrid = nullptr;       // grid
   double* tvals = nullptr;       // [N_b]
   double* ftilde = nullptr;      // grid scratch
   double* bvec = nullptr;        // [N_b]
-  double* zero_nb = nullptr;     // [N_b] zeros
   int* d_flags = nullptr;        // kFlagCount ints
   kfbi::Gmres gm;
   kfbi::Profiler prof;
@@ -212,6 +226,7 @@ struct kfbi_problem {
   kfbi_problem* twin = nullptr;  // general interface kind: the kappa_2/sigma_2 operator (owned)
   kfbi_problem* parent = nullptr;  // set on a twin: its launches are counted and timed there
   double* gen = nullptr;         // general interface kind: 8 N_b traces + 3 N_b scaled data
+  kfbi::GeoArena arena;          // the geometry's arrays and the set-up's temporaries
 };
 
 namespace kfbi {
@@ -234,6 +249,12 @@ kfbi_status fail(kfbi_problem* p, kfbi_status s, const std::string& msg);
 template <typename T>
 cudaError_t dalloc(T** ptr, size_t count) {
   return cudaMalloc(reinterpret_cast<void**>(ptr), count * sizeof(T) + 16);
+}
+
+// the same from the problem's geometry arena (released with the geometry)
+template <typename T>
+cudaError_t galloc(kfbi_problem* p, T** ptr, size_t count) {
+  return arena_alloc(p->arena, count * sizeof(T) + 16, reinterpret_cast<void**>(ptr));
 }
 
 inline int div_up(long long a, long long b) { return static_cast<int>((a + b - 1) / b); }

@@ -178,7 +178,12 @@ __device__ __forceinline__ void line_other(const Grid& g, const LineDesc& D, int
 
 // Root of H_k (interface k) on the edge [x0, x0 + h e_r]: start at the
 // linear interpolant, Newton step, bisection whenever Newton leaves the
-// bracket or df = 0, stop at |ds| <= 1e-15 h or after 64 steps.
+// bracket or df = 0, stop at |ds| <= 1e-15 N h or after 64 steps.  1e-15 of
+// the box width is about the FP64 spacing of a coordinate in the box; the
+// rounding noise of H makes the Newton steps near the root ~1e-16 / |grad H|
+// long, so a tolerance of 1e-15 h (1e-18 at N = 1024) is met only by chance
+// (8-11 steps on average and up to the step limit, where about 3 suffice),
+// and a warp waits for its slowest lane.
 __device__ double edge_root(const Grid& g, const LevelSet& L, int k, const double* x0, int r,
                             int j) {
   double xa[3] = {x0[0], x0[1], x0[2]};
@@ -204,7 +209,7 @@ __device__ double edge_root(const Grid& g, const LevelSet& L, int k, const doubl
     bool bad = !((s_new > lo_s) && (s_new < hi_s)) || (df == 0.0);
     if (bad) s_new = 0.5 * (lo_s + hi_s);
     if (done_zero) s_new = s;
-    bool conv = done_zero || (fabs(s_new - s) <= kRootTol * h);
+    bool conv = done_zero || (fabs(s_new - s) <= kRootTol * (g.n * h));
     s = s_new;
     if (conv) break;
   }
@@ -1376,15 +1381,12 @@ static kfbi_status scan_exclusive(kfbi_problem* p, const int32_t* in, int32_t* o
   }
   const int nblk = div_up(n, kScanChunk);
   int32_t *bsum = nullptr, *boff = nullptr;
-  KFBI_CUDA(p, dalloc(&bsum, nblk));
-  KFBI_CUDA(p, dalloc(&boff, nblk + 1));
+  KFBI_CUDA(p, galloc(p, &bsum, nblk));
+  KFBI_CUDA(p, galloc(p, &boff, nblk + 1));
   k_scan_sums<<<nblk, 1024, 0, st>>>(in, n, bsum);
   k_exclusive_scan<<<1, 1024, 0, st>>>(bsum, boff, nblk, base);
   k_scan_apply<<<nblk, 1024, 0, st>>>(in, n, boff, nblk, out);
   KFBI_CUDA(p, cudaGetLastError());
-  KFBI_CUDA(p, cudaStreamSynchronize(st));
-  cudaFree(bsum);
-  cudaFree(boff);
   return KFBI_OK;
 }
 
@@ -1399,10 +1401,10 @@ kfbi_status build_geometry(kfbi_problem* p) {
     int h[kFlagCount];
     for (int k = 0; k < kFlagCount; ++k) h[k] = kFlagSentinel;
     h[kFlagClosestFallback] = 0;
-    KFBI_CUDA(p, dalloc(&p->d_flags, kFlagCount));
+    KFBI_CUDA(p, galloc(p, &p->d_flags, kFlagCount));
     KFBI_CUDA(p, cudaMemcpyAsync(p->d_flags, h, sizeof(h), cudaMemcpyHostToDevice, st));
   }
-  KFBI_CUDA(p, dalloc(&p->inside, nodes));
+  KFBI_CUDA(p, galloc(p, &p->inside, nodes));
   k_classify<<<div_up(nodes, 256), 256, 0, st>>>(g, L, p->inside);
   KFBI_CUDA(p, cudaGetLastError());
 
@@ -1419,16 +1421,12 @@ kfbi_status build_geometry(kfbi_problem* p) {
             *kpos = nullptr;
     double *x = nullptr, *nv = nullptr;
   } C[3];
+  // (the candidate arrays are arena temporaries: nothing to free)
   auto free_cand = [&]() {
-    for (int r = 0; r < 3; ++r) {
-      void* bufs[] = {C[r].start, C[r].line, C[r].edge, C[r].iface, C[r].keep, C[r].kpos, C[r].x, C[r].nv};
-      for (void* q : bufs)
-        if (q) cudaFree(q);
-      C[r] = Cand();
-    }
+    for (int r = 0; r < 3; ++r) C[r] = Cand();
   };
   int32_t* ccnt = nullptr;
-  KFBI_CUDA(p, dalloc(&ccnt, nlines));
+  KFBI_CUDA(p, galloc(p, &ccnt, nlines));
   int32_t base = 0;
   for (int r = 0; r < d; ++r) {
     D[r].r = r;
@@ -1444,18 +1442,18 @@ kfbi_status build_geometry(kfbi_problem* p) {
     k_cand_count<<<div_up(nlines, kLineWarps), 32 * kLineWarps, 0, st>>>(g, L, D[r], p->inside, multi,
                                                                         nlines, ccnt);
     KFBI_CUDA(p, cudaGetLastError());
-    KFBI_CUDA(p, dalloc(&c.start, nlines + 1));
+    KFBI_CUDA(p, galloc(p, &c.start, nlines + 1));
     KFBI_TRY(scan_exclusive(p, ccnt, c.start, nlines, 0, st));
     KFBI_CUDA(p, cudaMemcpyAsync(&c.n, c.start + nlines, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     KFBI_CUDA(p, cudaStreamSynchronize(st));
-    KFBI_CUDA(p, dalloc(&c.kpos, c.n + 1));
+    KFBI_CUDA(p, galloc(p, &c.kpos, c.n + 1));
     if (c.n > 0) {
-      KFBI_CUDA(p, dalloc(&c.line, c.n));
-      KFBI_CUDA(p, dalloc(&c.edge, c.n));
-      KFBI_CUDA(p, dalloc(&c.iface, c.n));
-      KFBI_CUDA(p, dalloc(&c.keep, c.n));
-      KFBI_CUDA(p, dalloc(&c.x, 3 * (size_t)c.n));
-      KFBI_CUDA(p, dalloc(&c.nv, 3 * (size_t)c.n));
+      KFBI_CUDA(p, galloc(p, &c.line, c.n));
+      KFBI_CUDA(p, galloc(p, &c.edge, c.n));
+      KFBI_CUDA(p, galloc(p, &c.iface, c.n));
+      KFBI_CUDA(p, galloc(p, &c.keep, c.n));
+      KFBI_CUDA(p, galloc(p, &c.x, 3 * (size_t)c.n));
+      KFBI_CUDA(p, galloc(p, &c.nv, 3 * (size_t)c.n));
       k_cand_fill<<<div_up(nlines, kLineWarps), 32 * kLineWarps, 0, st>>>(g, L, D[r], p->inside, multi,
                                                                          nlines, c.start, c.line, c.edge,
                                                                          c.iface);
@@ -1469,13 +1467,12 @@ kfbi_status build_geometry(kfbi_problem* p) {
     } else {
       KFBI_CUDA(p, cudaMemsetAsync(c.kpos, 0, sizeof(int32_t), st));
     }
-    KFBI_CUDA(p, dalloc(&p->line_start[r], nlines + 1));
+    KFBI_CUDA(p, galloc(p, &p->line_start[r], nlines + 1));
     k_cand_line_start<<<div_up(nlines + 1, 256), 256, 0, st>>>(nlines, base, c.start, c.kpos,
                                                                p->line_start[r]);
     KFBI_CUDA(p, cudaGetLastError());
     base += c.kept;
   }
-  cudaFree(ccnt);
   p->nb = base;
   if (p->nb == 0) {
     free_cand();
@@ -1483,14 +1480,14 @@ kfbi_status build_geometry(kfbi_problem* p) {
   }
   const int nb = p->nb;
   for (int k = 0; k < d; ++k) {
-    KFBI_CUDA(p, dalloc(&p->x[k], nb));
-    KFBI_CUDA(p, dalloc(&p->nrm[k], nb));
+    KFBI_CUDA(p, galloc(p, &p->x[k], nb));
+    KFBI_CUDA(p, galloc(p, &p->nrm[k], nb));
   }
-  KFBI_CUDA(p, dalloc(&p->family, nb));
-  KFBI_CUDA(p, dalloc(&p->dof_iface, nb));
-  KFBI_CUDA(p, dalloc(&p->edge, nb));
-  KFBI_CUDA(p, dalloc(&p->axis, nb));
-  KFBI_CUDA(p, dalloc(&p->st_axis, nb));
+  KFBI_CUDA(p, galloc(p, &p->family, nb));
+  KFBI_CUDA(p, galloc(p, &p->dof_iface, nb));
+  KFBI_CUDA(p, galloc(p, &p->edge, nb));
+  KFBI_CUDA(p, galloc(p, &p->axis, nb));
+  KFBI_CUDA(p, galloc(p, &p->st_axis, nb));
   {
     int32_t fbase = 0;
     for (int r = 0; r < d; ++r) {
@@ -1504,7 +1501,6 @@ kfbi_status build_geometry(kfbi_problem* p) {
       fbase += c.kept;
     }
   }
-  KFBI_CUDA(p, cudaStreamSynchronize(st));
   free_cand();
 
   DofView V;
@@ -1565,9 +1561,9 @@ kfbi_status build_geometry(kfbi_problem* p) {
     return fail(p, KFBI_ERR_UNSUPPORTED, "collocation system is not square");
   KFBI_CUDA(p, cudaMemcpyToSymbolAsync(c_exp, &E, sizeof(E), 0, cudaMemcpyHostToDevice, st));
 
-  KFBI_CUDA(p, dalloc(&p->pde_node, (size_t)nb * p->npde));
-  KFBI_CUDA(p, dalloc(&p->dir_idx, (size_t)nb * p->ndir));
-  KFBI_CUDA(p, dalloc(&p->neu_idx, (size_t)nb * p->nneu));
+  KFBI_CUDA(p, galloc(p, &p->pde_node, (size_t)nb * p->npde));
+  KFBI_CUDA(p, galloc(p, &p->dir_idx, (size_t)nb * p->ndir));
+  KFBI_CUDA(p, galloc(p, &p->neu_idx, (size_t)nb * p->nneu));
   k_stencils<<<div_up(nb, 128), 128, 0, st>>>(g, order, p->cos_alpha, V, nb, p->axis,
                                                p->pde_node, p->dir_idx, p->neu_idx, p->st_axis,
                                                p->d_flags);
@@ -1575,7 +1571,7 @@ kfbi_status build_geometry(kfbi_problem* p) {
   KFBI_TRY(check_flags(p, "collocation stencils"));
 
   const int nc = p->ncoef;
-  KFBI_CUDA(p, dalloc(&p->minv, (size_t)nb * nc * nc));
+  KFBI_CUDA(p, galloc(p, &p->minv, (size_t)nb * nc * nc));
   {
     size_t smem = sizeof(double) * ((size_t)(nc + 1) * nc * 2 + 2 * nc);
     // per-kernel process-wide attribute: raise it to the device maximum once
@@ -1612,14 +1608,14 @@ kfbi_status build_geometry(kfbi_problem* p) {
   }
   p->n_nb = NT.count;
   KFBI_CUDA(p, cudaMemcpyToSymbolAsync(c_nb, &NT, sizeof(NT), 0, cudaMemcpyHostToDevice, st));
-  KFBI_CUDA(p, dalloc(&p->irr_flag, nodes));
+  KFBI_CUDA(p, galloc(p, &p->irr_flag, nodes));
   k_irregular_flags<<<div_up(nodes, 256), 256, 0, st>>>(g, p->inside, p->irr_flag);
   KFBI_CUDA(p, cudaGetLastError());
   const int nrows = (int)(nodes / n1);
   int32_t *rcnt = nullptr, *rstart = nullptr, *map = nullptr;
-  KFBI_CUDA(p, dalloc(&rcnt, nrows));
-  KFBI_CUDA(p, dalloc(&rstart, nrows + 1));
-  KFBI_CUDA(p, dalloc(&map, nodes));
+  KFBI_CUDA(p, galloc(p, &rcnt, nrows));
+  KFBI_CUDA(p, galloc(p, &rstart, nrows + 1));
+  KFBI_CUDA(p, galloc(p, &map, nodes));
   KFBI_CUDA(p, cudaMemsetAsync(map, 0xff, sizeof(int32_t) * nodes, st));
   k_row_count<<<div_up(nrows, 128), 128, 0, st>>>(g, p->irr_flag, nrows, rcnt);
   KFBI_TRY(scan_exclusive(p, rcnt, rstart, nrows, 0, st));
@@ -1628,8 +1624,8 @@ kfbi_status build_geometry(kfbi_problem* p) {
   KFBI_CUDA(p, cudaStreamSynchronize(st));
   p->nirr = nirr;
   if (nirr == 0) return fail(p, KFBI_ERR_GEOMETRY, "no irregular nodes");
-  KFBI_CUDA(p, dalloc(&p->irr_lin, nirr));
-  KFBI_CUDA(p, dalloc(&p->irr_inside, nirr));
+  KFBI_CUDA(p, galloc(p, &p->irr_lin, nirr));
+  KFBI_CUDA(p, galloc(p, &p->irr_inside, nirr));
   k_row_fill<<<div_up(nrows, 128), 128, 0, st>>>(g, p->irr_flag, p->inside, nrows, rstart,
                                                   p->irr_lin, p->irr_inside, map);
   KFBI_CUDA(p, cudaGetLastError());
@@ -1650,16 +1646,16 @@ kfbi_status build_geometry(kfbi_problem* p) {
   if (!multi) {
     // one per irregular node, in its order
     p->nent = nirr;
-    KFBI_CUDA(p, dalloc(&p->ent_lin, nirr));
-    KFBI_CUDA(p, dalloc(&p->ent_iface, nirr));
+    KFBI_CUDA(p, galloc(p, &p->ent_lin, nirr));
+    KFBI_CUDA(p, galloc(p, &p->ent_iface, nirr));
     KFBI_CUDA(p, cudaMemcpyAsync(p->ent_lin, p->irr_lin, sizeof(int32_t) * nirr,
                                  cudaMemcpyDeviceToDevice, st));
     KFBI_CUDA(p, cudaMemsetAsync(p->ent_iface, 0, sizeof(int32_t) * nirr, st));
   } else {
-    KFBI_CUDA(p, dalloc(&need, nodes));
-    KFBI_CUDA(p, dalloc(&need2, nodes));
-    KFBI_CUDA(p, dalloc(&close, nb));
-    KFBI_CUDA(p, dalloc(&emap, nodes));
+    KFBI_CUDA(p, galloc(p, &need, nodes));
+    KFBI_CUDA(p, galloc(p, &need2, nodes));
+    KFBI_CUDA(p, galloc(p, &close, nb));
+    KFBI_CUDA(p, galloc(p, &emap, nodes));
     KFBI_CUDA(p, cudaMemsetAsync(need, 0, sizeof(uint32_t) * nodes, st));
     KFBI_CUDA(p, cudaMemsetAsync(emap, 0xff, sizeof(int32_t) * nodes, st));
     k_need_rhs<<<div_up(nirr, 128), 128, 0, st>>>(g, nirr, p->irr_lin, p->inside, need);
@@ -1669,36 +1665,31 @@ kfbi_status build_geometry(kfbi_problem* p) {
                                                       need2);
     KFBI_CUDA(p, cudaGetLastError());
     int32_t *ecnt = nullptr, *estart = nullptr;
-    KFBI_CUDA(p, dalloc(&ecnt, nrows));
-    KFBI_CUDA(p, dalloc(&estart, nrows + 1));
+    KFBI_CUDA(p, galloc(p, &ecnt, nrows));
+    KFBI_CUDA(p, galloc(p, &estart, nrows + 1));
     k_ent_row_count<<<div_up(nrows, 128), 128, 0, st>>>(g, need2, nrows, ecnt);
     KFBI_TRY(scan_exclusive(p, ecnt, estart, nrows, 0, st));
     int32_t nent = 0;
     KFBI_CUDA(p, cudaMemcpyAsync(&nent, estart + nrows, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     KFBI_CUDA(p, cudaStreamSynchronize(st));
     p->nent = nent;
-    KFBI_CUDA(p, dalloc(&p->ent_lin, nent));
-    KFBI_CUDA(p, dalloc(&p->ent_iface, nent));
+    KFBI_CUDA(p, galloc(p, &p->ent_lin, nent));
+    KFBI_CUDA(p, galloc(p, &p->ent_iface, nent));
     k_ent_row_fill<<<div_up(nrows, 128), 128, 0, st>>>(g, need2, nrows, estart, emap, p->ent_lin,
                                                         p->ent_iface);
     KFBI_CUDA(p, cudaGetLastError());
-    KFBI_CUDA(p, cudaStreamSynchronize(st));
-    cudaFree(ecnt);
-    cudaFree(estart);
   }
-  cudaFree(rcnt);
-  cudaFree(rstart);
   const int nent = p->nent;
-  KFBI_CUDA(p, dalloc(&p->ent_owner, nent));
+  KFBI_CUDA(p, galloc(p, &p->ent_owner, nent));
 
   // ---- closest primary points via a cell list
   {
     long long ncell = d == 2 ? (long long)n * n : (long long)n * n * n;
     int32_t *ccnt = nullptr, *cstart = nullptr, *cur = nullptr, *items = nullptr;
-    KFBI_CUDA(p, dalloc(&ccnt, ncell));
-    KFBI_CUDA(p, dalloc(&cstart, ncell + 1));
-    KFBI_CUDA(p, dalloc(&cur, ncell));
-    KFBI_CUDA(p, dalloc(&items, nb));
+    KFBI_CUDA(p, galloc(p, &ccnt, ncell));
+    KFBI_CUDA(p, galloc(p, &cstart, ncell + 1));
+    KFBI_CUDA(p, galloc(p, &cur, ncell));
+    KFBI_CUDA(p, galloc(p, &items, nb));
     KFBI_CUDA(p, cudaMemsetAsync(ccnt, 0, sizeof(int32_t) * ncell, st));
     KFBI_CUDA(p, cudaMemsetAsync(cur, 0, sizeof(int32_t) * ncell, st));
     k_cell_count<<<div_up(nb, 256), 256, 0, st>>>(g, V, nb, ccnt);
@@ -1707,22 +1698,17 @@ kfbi_status build_geometry(kfbi_problem* p) {
     k_closest<<<div_up(nent, 128), 128, 0, st>>>(g, V, nb, nent, p->ent_lin, p->ent_iface, cstart,
                                                  items, p->ent_owner, p->d_flags);
     KFBI_CUDA(p, cudaGetLastError());
-    KFBI_CUDA(p, cudaStreamSynchronize(st));
-    cudaFree(ccnt);
-    cudaFree(cstart);
-    cudaFree(cur);
-    cudaFree(items);
   }
   KFBI_TRY(check_flags(p, "closest primary points"));
-  KFBI_CUDA(p, dalloc(&p->ent_w, (size_t)nc * nent));
+  KFBI_CUDA(p, galloc(p, &p->ent_w, (size_t)nc * nent));
   k_composite<<<div_up(nent, 128), 128, 0, st>>>(g, V, nent, p->ent_lin, p->ent_owner, p->minv,
                                                   p->ent_w);
   KFBI_CUDA(p, cudaGetLastError());
-  KFBI_CUDA(p, dalloc(&p->corr_nb, (size_t)p->n_nb * nirr));
+  KFBI_CUDA(p, galloc(p, &p->corr_nb, (size_t)p->n_nb * nirr));
   if (!multi) {
     k_corr_lists<<<div_up(nirr, 128), 128, 0, st>>>(g, nirr, p->irr_lin, p->inside, map, p->corr_nb);
   } else {
-    KFBI_CUDA(p, dalloc(&p->corr_nb2, (size_t)p->n_nb * nirr));
+    KFBI_CUDA(p, galloc(p, &p->corr_nb2, (size_t)p->n_nb * nirr));
     k_corr_lists_multi<<<div_up(nirr, 128), 128, 0, st>>>(g, nirr, p->irr_lin, p->inside, need2,
                                                           emap, p->corr_nb, p->corr_nb2);
   }
@@ -1730,8 +1716,8 @@ kfbi_status build_geometry(kfbi_problem* p) {
 
   // ---- trace stencils
   int32_t *tcnt = nullptr, *tptr = nullptr;
-  KFBI_CUDA(p, dalloc(&tcnt, 2 * nb));
-  KFBI_CUDA(p, dalloc(&tptr, 2 * nb + 1));
+  KFBI_CUDA(p, galloc(p, &tcnt, 2 * nb));
+  KFBI_CUDA(p, galloc(p, &tptr, 2 * nb + 1));
   k_trace_count<<<div_up(2 * nb, 128), 128, 0, st>>>(g, TP, V, nb, p->inside, p->irr_flag, close,
                                                        need, tcnt);
   KFBI_TRY(scan_exclusive(p, tcnt, tptr, 2 * nb, 0, st));
@@ -1746,12 +1732,12 @@ kfbi_status build_geometry(kfbi_problem* p) {
   const int nnz_all = hptr[2 * nb];
   int32_t *tnode = nullptr, *tirr = nullptr, *tirr2 = nullptr;
   double *twv = nullptr, *twn = nullptr, *tw = nullptr;
-  KFBI_CUDA(p, dalloc(&tnode, nnz_all));
-  KFBI_CUDA(p, dalloc(&tirr, nnz_all));
-  if (multi) KFBI_CUDA(p, dalloc(&tirr2, nnz_all));
-  KFBI_CUDA(p, dalloc(&twv, nnz_all));
-  KFBI_CUDA(p, dalloc(&twn, nnz_all));
-  KFBI_CUDA(p, dalloc(&tw, nnz_all));
+  KFBI_CUDA(p, galloc(p, &tnode, nnz_all));
+  KFBI_CUDA(p, galloc(p, &tirr, nnz_all));
+  if (multi) KFBI_CUDA(p, galloc(p, &tirr2, nnz_all));
+  KFBI_CUDA(p, galloc(p, &twv, nnz_all));
+  KFBI_CUDA(p, galloc(p, &twn, nnz_all));
+  KFBI_CUDA(p, galloc(p, &tw, nnz_all));
   {
     double alpha = p->cfg.kind == KFBI_DIRICHLET_INTERIOR ? 0.5 : 0.0;
     double beta = p->cfg.kind == KFBI_DIRICHLET_INTERIOR ? 0.0 : 0.5;
@@ -1772,7 +1758,7 @@ kfbi_status build_geometry(kfbi_problem* p) {
   // split the all-sides CSR into the two per-side CSRs (pointers into one allocation)
   for (int s = 0; s < 2; ++s) {
     TraceCSR& c = p->tr[s];
-    KFBI_CUDA(p, dalloc(&c.ptr, nb + 1));
+    KFBI_CUDA(p, galloc(p, &c.ptr, nb + 1));
     std::vector<int32_t> sp(nb + 1);
     int32_t b0 = hptr[(size_t)s * nb];
     for (int k = 0; k <= nb; ++k) sp[k] = hptr[(size_t)s * nb + k] - b0;
@@ -1798,15 +1784,6 @@ kfbi_status build_geometry(kfbi_problem* p) {
     }
   }
   KFBI_CUDA(p, cudaStreamSynchronize(st));
-  cudaFree(tcnt);
-  cudaFree(tptr);
-  cudaFree(map);
-  if (multi) {
-    cudaFree(need);
-    cudaFree(need2);
-    cudaFree(close);
-    cudaFree(emap);
-  }
   return KFBI_OK;
 }
 

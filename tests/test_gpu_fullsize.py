@@ -77,7 +77,7 @@ def test_flower1024_mixed_bench_configuration_error():
     G.close()
 
 
-@pytest.mark.parametrize("omega", [0.1])
+@pytest.mark.parametrize("omega", [0.05, 0.1])
 def test_flower1024_relaxed_mixed_solve(omega):
     """Inexact GMRES on the benchmark configuration: the relaxed refinement
     (tolerance max(1e-11, omega rtol ||b|| / ||r_j||)) runs fewer FP32
