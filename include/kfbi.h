@@ -65,7 +65,9 @@ typedef enum {
                              cubic Lagrange interpolant on the 4^d nodes around
                              the point (its cell clamped to [1, N-2] per axis;
                              a coordinate within 1e-10 h of a node is that
-                             node, so H at a node is its sample); p unused   */
+                             node, so H at a node is its sample); every
+                             sample must be finite (KFBI_ERR_ARG otherwise,
+                             at create or update); p unused                   */
   KFBI_LS_UNION = 9       /* 2D or 3D p=[m, kind_1, params_1..., kind_2, ...]: m
                              interfaces, each of kind ELLIPSE or STAR (5
                              params) in 2D, ELLIPSOID (6) or TORUS (2) in 3D,

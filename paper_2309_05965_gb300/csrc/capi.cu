@@ -234,6 +234,10 @@ static kfbi_status set_levelset(kfbi_problem* p, const kfbi_levelset* ls) {
     if ((!p->ls_samples && dalloc(&p->ls_samples, nodes) != cudaSuccess) ||
         cudaMemcpy(p->ls_samples, ls->samples, sizeof(double) * nodes, cudaMemcpyDeviceToDevice) != cudaSuccess)
       return fail(p, KFBI_ERR_CUDA, "cannot copy the level-set samples");
+    long long bad = 0;
+    if (count_nonfinite(p->ls_samples, nodes, p->stream, &bad) != cudaSuccess)
+      return fail(p, KFBI_ERR_CUDA, "cannot check the level-set samples");
+    if (bad > 0) return fail(p, KFBI_ERR_ARG, "the level-set samples must be finite");
     p->ls.grid = p->ls_samples;
     p->ls.gd = p->g.d;
     p->ls.gn = p->g.n;

@@ -140,6 +140,8 @@ struct GeoArena {
   size_t total = 0;   // bytes handed out since the last reset
 };
 cudaError_t arena_alloc(GeoArena& A, size_t bytes, void** out);
+// number of non-finite values of a device array (synchronises the stream)
+cudaError_t count_nonfinite(const double* a, long long n, cudaStream_t st, long long* out);
 void arena_reset(GeoArena& A);
 void arena_release(GeoArena& A);
 

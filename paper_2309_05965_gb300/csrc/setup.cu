@@ -146,15 +146,31 @@ __global__ void __launch_bounds__(1024) k_scan_apply(const int32_t* __restrict__
 // Classification (Sec. 5.2): inside iff H(node) < 0, stored as the node's side
 // label (0 outside, 1 + k in Omega^(k); 1 inside for one interface).
 // ---------------------------------------------------------------------------
+// A grid-sampled H is its sample at a node (the interpolant's weights there
+// are 1 and +-0, and every sample is finite), so its labels are read directly.
 __global__ void k_classify(Grid g, LevelSet L, uint8_t* __restrict__ inside) {
   long long tot = g.nodes();
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
        t += (long long)gridDim.x * blockDim.x) {
+    if (L.kind == KFBI_LS_GRID) {
+      inside[t] = L.grid[t] < 0.0 ? 1 : 0;
+      continue;
+    }
     int idx[3];
     node_multi(g, t, idx);
     double X[3] = {coord(g, idx[0]), coord(g, idx[1]), g.d == 3 ? coord(g, idx[2]) : 0.0};
     inside[t] = (uint8_t)ls_label(L, X);
   }
+}
+
+__global__ void k_count_nonfinite(const double* __restrict__ a, long long n,
+                                  unsigned long long* __restrict__ out) {
+  unsigned long long c = 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    c += isfinite(a[t]) ? 0ull : 1ull;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -662,7 +678,10 @@ __device__ void warp_apply_q(const double* A, int lda, int m, int n, const doubl
 
 // ---------------------------------------------------------------------------
 // Collocation matrices M (eq. (cau-appro), rows scaled to O(1)) and M^{-1}.
-// One warp per primary point.
+// One warp per primary point; M^{-1} by Gauss-Jordan elimination with partial
+// pivoting on [M | I], one lane per column (a pivot search is the only warp
+// reduction of a step), the columns at an odd stride in shared memory so
+// that the lanes' column walks fall in different banks.
 // ---------------------------------------------------------------------------
 __global__ void k_collocation_factor(Grid g, double kt, DofView V, int nb,
                                      const int32_t* __restrict__ pde_node,
@@ -671,11 +690,9 @@ __global__ void k_collocation_factor(Grid g, double kt, DofView V, int nb,
                                      double* __restrict__ minv, int* flags) {
   extern __shared__ double sm[];
   const int n = c_exp.n;
-  const int lda = n + 1;
-  double* A = sm;                       // n x n, column-major, lda
-  double* B = A + (size_t)lda * n;      // n x n, column-major, lda
-  double* rdiag = B + (size_t)lda * n;
-  double* vn2 = rdiag + n;
+  const int lda = n | 1;                // odd column stride (>= n)
+  double* A = sm;                       // [M | I]: 2n columns of n rows, column-major, lda
+  double* fcol = A + (size_t)lda * 2 * n;   // the pivot column of a step
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x;
   if (i >= nb) return;
@@ -728,34 +745,63 @@ __global__ void k_collocation_factor(Grid g, double kt, DofView V, int nb,
     colmax = fmax(colmax, s);
   }
   for (int o = 16; o > 0; o >>= 1) colmax = fmax(colmax, __shfl_xor_sync(0xffffffffu, colmax, o));
-  bool ok = warp_householder(A, lda, n, n, rdiag, vn2);
-  // B = Q^T I
-  for (int c = 0; c < n; ++c)
-    for (int r = lane; r < n; r += 32) B[(size_t)c * lda + r] = (r == c) ? 1.0 : 0.0;
+  for (int c = n + lane; c < 2 * n; c += 32)
+    for (int r = 0; r < n; ++r) A[(size_t)c * lda + r] = (r == c - n) ? 1.0 : 0.0;
   __syncwarp();
-  for (int c = 0; c < n; ++c) warp_apply_q(A, lda, n, n, vn2, B + (size_t)c * lda, true);
-  // back substitution R X = B, one column per lane
-  double invmax = 0.0;
-  for (int c = lane; c < n; c += 32) {
-    double* bc = B + (size_t)c * lda;
-    for (int r = n - 1; r >= 0; --r) {
-      double acc = bc[r];
-      for (int j = r + 1; j < n; ++j) acc -= A[(size_t)j * lda + r] * bc[j];
-      bc[r] = acc / rdiag[r];
+  bool ok = true;
+  for (int k = 0; k < n; ++k) {
+    const double* ak = A + (size_t)k * lda;
+    // pivot: the first row of the largest |a_ik|, i >= k
+    double best = -1.0;
+    int prow = n;
+    for (int r = k + lane; r < n; r += 32) {
+      const double v = fabs(ak[r]);
+      if (v > best) {
+        best = v;
+        prow = r;
+      }
     }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int orow = __shfl_xor_sync(0xffffffffu, prow, o);
+      if (ob > best || (ob == best && orow < prow)) {
+        best = ob;
+        prow = orow;
+      }
+    }
+    if (!(best > 0.0)) {
+      ok = false;
+      break;
+    }
+    // the multipliers: column k after the row swap, copied before any lane
+    // changes that column
+    for (int r = lane; r < n; r += 32) fcol[r] = ak[r == k ? prow : (r == prow ? k : r)];
+    __syncwarp();
+    const double piv = fcol[k];
+    for (int c = lane; c < 2 * n; c += 32) {
+      double* col = A + (size_t)c * lda;
+      const double t = col[prow];
+      col[prow] = col[k];
+      const double rk = t / piv;
+      col[k] = rk;
+      for (int r = 0; r < n; ++r)
+        if (r != k) col[r] = col[r] - fcol[r] * rk;
+    }
+    __syncwarp();
   }
-  __syncwarp();
-  // ||M^{-1}||_1 and output (row-major M^{-1}[k][j] = X[k][j], X column j = B col j)
-  for (int c = lane; c < n; c += 32) {
+  // ||M^{-1}||_1 and output (row-major M^{-1}[k][j] = X[k][j], X column j =
+  // augmented column n + j)
+  double invmax = 0.0;
+  for (int c = n + lane; c < 2 * n; c += 32) {
     double s = 0.0;
-    for (int r = 0; r < n; ++r) s += fabs(B[(size_t)c * lda + r]);
+    for (int r = 0; r < n; ++r) s += fabs(A[(size_t)c * lda + r]);
     invmax = fmax(invmax, s);
   }
   for (int o = 16; o > 0; o >>= 1) invmax = fmax(invmax, __shfl_xor_sync(0xffffffffu, invmax, o));
   double* out = minv + (size_t)i * n * n;
   for (int t = lane; t < n * n; t += 32) {
     int k = t / n, j = t % n;
-    out[t] = B[(size_t)j * lda + k];
+    out[t] = A[(size_t)(n + j) * lda + k];
   }
   double cond = colmax * invmax;
   if (lane == 0 && (!ok || !(cond < 1e10))) flag_min(flags, kFlagSingular, i + 1);
@@ -1307,6 +1353,21 @@ __global__ void k_trace_fill(Grid g, TraceParams T, DofView V, int nb,
 }
 
 }  // namespace
+
+cudaError_t count_nonfinite(const double* a, long long n, cudaStream_t st, long long* out) {
+  unsigned long long* d = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), sizeof(*d), st);
+  if (e != cudaSuccess) return e;
+  unsigned long long h = 0;
+  cudaMemsetAsync(d, 0, sizeof(*d), st);
+  k_count_nonfinite<<<(int)std::min<long long>(div_up(n, 256), 152 * 8), 256, 0, st>>>(a, n, d);
+  cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(d, st);
+  e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  *out = (long long)h;
+  return e;
+}
 
 // ---------------------------------------------------------------------------
 // Host orchestration.

@@ -11,8 +11,8 @@ kfbi_update_levelset gives a problem a new interface on the same grid.
   updated with it).
 * A moving interface problem solved at each of its positions is the exact
   solution to discretisation accuracy.
-* An invalid level set is refused with KFBI_ERR_ARG, and a valid update
-  afterwards works.
+* An invalid level set (a kind of the other dimension, a non-finite
+  sample) is refused with KFBI_ERR_ARG, and a valid update afterwards works.
 """
 import numpy as np
 import pytest
@@ -150,6 +150,12 @@ def test_invalid_update_is_refused_and_recoverable():
     with pytest.raises(kfbi.KfbiError) as e:
         G.update_levelset(W.LS_ELLIPSOID, [0, 0, 0, 0.5, 0.5, 0.5])   # a 3D kind in 2D
     assert e.value.status == 1
+    for v in (np.nan, np.inf):   # a non-finite sample
+        smp = W.moving_samples(2, 128, -1.0, 1.0, 0.2).copy()
+        smp[40, 77] = v
+        with pytest.raises(kfbi.KfbiError) as e:
+            G.update_levelset(W.LS_GRID, [], smp)
+        assert e.value.status == 1 and "finite" in str(e.value)
     w2 = W.moving_interface_2d(128, 0.3)
     G.update_levelset(*_ls_of(w2))
     F = kfbi.Problem.from_workload(w2)
