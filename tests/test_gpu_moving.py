@@ -11,6 +11,8 @@ kfbi_update_levelset gives a problem a new interface on the same grid.
   updated with it).
 * A moving interface problem solved at each of its positions is the exact
   solution to discretisation accuracy.
+* At 1024^2, where a set-up needs several arena chunks, updates between two
+  shapes of different size equal fresh creates, bit for bit.
 * An invalid level set (a kind of the other dimension, a non-finite
   sample) is refused with KFBI_ERR_ARG, and a valid update afterwards works.
 """
@@ -161,4 +163,27 @@ def test_invalid_update_is_refused_and_recoverable():
     F = kfbi.Problem.from_workload(w2)
     _same(_snapshot(G, w2), _snapshot(F, w2))
     F.close()
+    G.close()
+
+
+def test_update_grows_and_merges_the_geometry_arena_1024():
+    """At 1024^2 a set-up takes ~30 MB (the closest-point cell lists alone
+    12.6 MB), more than the arena's first 16 MB chunk: the create grows the
+    arena to several chunks, the first update merges them into one, and the
+    updates between a small ellipse and the flower reuse or regrow it.  Every
+    state equals the freshly created problem, bit for bit (small -> flower ->
+    small -> flower)."""
+    from paper_2309_05965_gb300 import build, kfbi
+    build.build()
+    big = W.flower_interface_2d(1024)
+    small = W.flower_interface_2d(1024)
+    small.ls_kind, small.ls_params = W.LS_ELLIPSE, [0.05, -0.03, 0.2, 0.15, 0.3]
+    G = kfbi.Problem.from_workload(small, precision=kfbi.MIXED)
+    for w in (big, small, big):
+        G.update_levelset(*_ls_of(w))
+        F = kfbi.Problem.from_workload(w, precision=kfbi.MIXED)
+        a, b = _snapshot(G, w), _snapshot(F, w)
+        _same(a, b)
+        F.close()
+        assert a["err"] < 1e-7, a["err"]
     G.close()
