@@ -619,7 +619,10 @@ __device__ __forceinline__ double mono_lap(const double pw[3][5], int e, int d) 
 
 // ---------------------------------------------------------------------------
 // Warp Householder QR of a column-major m x n matrix in shared memory.
-// R: upper triangle of A plus rdiag; reflector v_k in A[k.., k]; vn2[k] = |v_k|^2.
+// R: upper triangle of A plus rdiag; reflector v_k in A[k.., k];
+// vn2[k] = 2 / |v_k|^2 (0 for a zero column), so that applying H_k costs a
+// multiply: an FP64 divide is a long sequence on GB300's FP64 pipe (2 lanes
+// per clock per SM), and one per column pair made the fits FP64-bound.
 // ---------------------------------------------------------------------------
 __device__ bool warp_householder(double* A, int lda, int m, int n, double* rdiag, double* vn2) {
   const int lane = threadIdx.x & 31;
@@ -634,14 +637,16 @@ __device__ bool warp_householder(double* A, int lda, int m, int n, double* rdiag
     double alpha = akk >= 0.0 ? -nrm : nrm;
     double vk = akk - alpha;
     double vnorm2 = s - akk * akk + vk * vk;
+    const bool good = nrm > 0.0 && vnorm2 > 0.0;
+    const double rv = good ? 2.0 / vnorm2 : 0.0;
     __syncwarp();
     if (lane == 0) {
       ak[k] = vk;
       rdiag[k] = alpha;
-      vn2[k] = (nrm == 0.0) ? 0.0 : vnorm2;
+      vn2[k] = rv;
     }
     __syncwarp();
-    if (!(nrm > 0.0) || !(vnorm2 > 0.0)) {
+    if (!good) {
       ok = false;
       continue;
     }
@@ -650,7 +655,7 @@ __device__ bool warp_householder(double* A, int lda, int m, int n, double* rdiag
       double t = 0.0;
       for (int i = k + lane; i < m; i += 32) t += ak[i] * aj[i];
       t = warp_sum(t);
-      double f = 2.0 * t / vnorm2;
+      double f = t * rv;
       for (int i = k + lane; i < m; i += 32) aj[i] -= f * ak[i];
       __syncwarp();
     }
@@ -669,7 +674,7 @@ __device__ void warp_apply_q(const double* A, int lda, int m, int n, const doubl
     double t = 0.0;
     for (int i = k + lane; i < m; i += 32) t += ak[i] * y[i];
     t = warp_sum(t);
-    double f = 2.0 * t / vn2[k];
+    double f = t * vn2[k];
     __syncwarp();
     for (int i = k + lane; i < m; i += 32) y[i] -= f * ak[i];
     __syncwarp();
@@ -1315,8 +1320,9 @@ __global__ void k_trace_fill(Grid g, TraceParams T, DofView V, int nb,
         a0 -= rjk * z[j];
         a1 -= rjk * z[n + j];
       }
-      z[k] = a0 / rdiag[k];
-      z[n + k] = a1 / rdiag[k];
+      const double ir = 1.0 / rdiag[k];
+      z[k] = a0 * ir;
+      z[n + k] = a1 * ir;
     }
   }
   __syncwarp();
