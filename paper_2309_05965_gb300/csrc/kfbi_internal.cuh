@@ -9,6 +9,10 @@
 //                    coalesced (correction lists); per-entry the same
 //                    [k][n_entries] (composite collocation rows)
 //   trace weights    CSR over DOFs, one CSR per side (+, -)
+// Every array that depends on the interface (DOF arrays, stencils, entries,
+// trace CSRs, the per-DOF work vectors) lies in the problem's geometry arena
+// (GeoArena below); the grids and the box solver's buffers are separate
+// allocations kept across interface updates.
 #pragma once
 
 #include <cuda_runtime.h>
