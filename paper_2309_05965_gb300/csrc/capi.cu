@@ -294,7 +294,7 @@ void arena_release(GeoArena& A) {
 // entries, trace weights, the per-DOF work vectors, the GMRES workspace and
 // the captured graphs.  The box solver, the grids R and u, the stencil tables
 // and the streams stay.
-static void free_geometry(kfbi_problem* p) {
+static void free_geometry(kfbi_problem* p, bool keep_arena = true) {
   gmres_destroy(p);
   if (p->op_exec) cudaGraphExecDestroy(p->op_exec);
   if (p->op_graph) cudaGraphDestroy(p->op_graph);
@@ -318,7 +318,11 @@ static void free_geometry(kfbi_problem* p) {
     p->line_start[k] = nullptr;
   }
   for (int s = 0; s < 2; ++s) p->tr[s] = TraceCSR();
-  arena_reset(p->arena);
+  // an update reuses the arena (its chunks merged into one); destroy frees it
+  if (keep_arena)
+    arena_reset(p->arena);
+  else
+    arena_release(p->arena);
   p->nb = p->nirr = p->nent = p->nx = 0;
 }
 
@@ -464,8 +468,7 @@ kfbi_status kfbi_destroy_problem(kfbi_problem* p) {
     kfbi_destroy_problem(p->twin);
     p->twin = nullptr;
   }
-  free_geometry(p);
-  arena_release(p->arena);
+  free_geometry(p, false);
   box_destroy(p);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->ls_samples) cudaFree(p->ls_samples);
