@@ -78,9 +78,11 @@ def label_nodes(grid: Grid, kind: int, p) -> np.ndarray:
     return LS.labels(kind, p, grid.coords())
 
 
-def find_roots(grid: Grid, kind: int, p, x0: np.ndarray, r: int, iface: int = 0) -> np.ndarray:
+def find_roots(grid: Grid, kind: int, p, x0: np.ndarray, r: int, iface: int = 0,
+               steps: list | None = None) -> np.ndarray:
     """Offsets s in [0, h] with H_k(x0 + s e_r) = 0 (k = iface) on edges where
-    H_k changes sign (Sec. 5.1), by Newton's method safeguarded with bisection."""
+    H_k changes sign (Sec. 5.1), by Newton's method safeguarded with bisection.
+    With a list `steps`, the number of steps each root took is appended."""
     h = grid.h
     m = x0.shape[0]
     Hk = lambda X: LS.H_iface(kind, p, iface, X)
@@ -93,10 +95,12 @@ def find_roots(grid: Grid, kind: int, p, x0: np.ndarray, r: int, iface: int = 0)
     lo_s = np.zeros(m)
     hi_s = np.full(m, h)
     active = np.ones(m, dtype=bool)
+    taken = np.zeros(m, dtype=np.int64)
     for _ in range(ROOT_MAX_IT):
         if not active.any():
             break
         idx = np.nonzero(active)[0]
+        taken[idx] += 1
         X = x0[idx].copy()
         X[:, r] = x0[idx, r] + s[idx]
         f = Hk(X)
@@ -113,6 +117,8 @@ def find_roots(grid: Grid, kind: int, p, x0: np.ndarray, r: int, iface: int = 0)
         conv = done_zero | (np.abs(s_new - s[idx]) <= ROOT_TOL * (grid.n * h))
         s[idx] = s_new
         active[idx[conv]] = False
+    if steps is not None:
+        steps.extend(taken.tolist())
     return s
 
 

@@ -154,3 +154,36 @@ def test_molecule_gradient_central_differences():
     # far from every atom H -> level (the sum of Gaussians vanishes)
     far = LS.H(w.ls_kind, w.ls_params, np.array([[40.0, 0.0, 0.0]]))[0]
     assert far == w.ls_params[1]
+
+
+def test_root_iteration_stops_by_its_tolerance():
+    """The root iteration's stopping rule (|ds| <= 1e-15 N h, about the FP64
+    spacing of a coordinate in the box) is met, not the step limit: on every
+    sign-changing edge of the flower and of a grid-sampled shape at 512^2
+    the roots take at most 4 steps on average and stop before the limit, and
+    sampled roots agree with brentq on the interpolant to 1e-14.  (A
+    tolerance of 1e-15 h lies below the rounding noise of the Newton steps:
+    roots then took 8-11 steps on average and some ran to the limit.)"""
+    rng = np.random.default_rng(5)
+    for w in (W.flower_interface_2d(512), W.moving_interface_2d(512, 0.15)):
+        g = G.Grid(2, w.n, w.lo, w.h)
+        p = LS.params(w)
+        xs = g.coord(np.arange(w.n + 1))
+        X, Y = np.meshgrid(xs, xs, indexing="ij")
+        P = np.stack([X.ravel(), Y.ravel()], -1)
+        Hn = LS.H_iface(w.ls_kind, p, 0, P).reshape(w.n + 1, w.n + 1)
+        i, j = np.nonzero((Hn[:, :-1] < 0) != (Hn[:, 1:] < 0))
+        x0 = np.stack([xs[i], xs[j]], -1)
+        steps = []
+        s = G.find_roots(g, w.ls_kind, p, x0, 1, steps=steps)
+        steps = np.asarray(steps)
+        assert len(steps) == len(x0) > 500
+        assert steps.mean() <= 4.0 and steps.max() < G.ROOT_MAX_IT, (steps.mean(), steps.max())
+        assert np.all((s >= 0.0) & (s <= g.h))
+        for k in rng.choice(len(x0), 20, replace=False):
+            def f(t):
+                Xk = x0[k].copy()
+                Xk[1] = x0[k, 1] + t
+                return LS.H_iface(w.ls_kind, p, 0, Xk[None])[0]
+            t = scipy.optimize.brentq(f, 0.0, g.h, xtol=1e-18, rtol=1e-15)
+            assert abs(s[k] - t) < 1e-14, (k, s[k], t)
