@@ -50,3 +50,22 @@ def test_job_throughput_single_rank():
     import bench
     total, value = bench.job_throughput(400.0, 8, 1)
     assert total == 400.0 and value == pytest.approx(20.0)
+
+
+def test_reference_arm_line_on_a_small_grid():
+    """The reference arm (the CPU oracle) prints the base contract's line:
+    the metric, solves/s from operator applications with the sample stated,
+    zero copies in its e2e, and impl = reference."""
+    import argparse
+
+    import bench
+    args = argparse.Namespace(n=64, rtol=1e-8, steps=2, warmup=1, gpus=1)
+    out = bench.run_reference(args)
+    assert out["impl"] == "reference" and out["metric"] == bench.METRIC
+    assert out["unit"] == "solves/s" and out["higher_is_better"] is True
+    assert out["value"] > 0 and out["steps"] == 2 and out["warmup"] == 1
+    cb = out["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == out["value"]
+    assert "operator applications" in cb["sample"]
+    assert out["e2e"] == {"value": out["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
+                          "d2h_bytes_per_step": 0}
