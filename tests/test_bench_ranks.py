@@ -59,7 +59,7 @@ def test_reference_arm_line_on_a_small_grid():
     import argparse
 
     import bench
-    args = argparse.Namespace(n=64, rtol=1e-8, steps=2, warmup=1, gpus=1)
+    args = argparse.Namespace(n=128, rtol=1e-8, steps=2, warmup=1, gpus=1)
     out = bench.run_reference(args)
     assert out["impl"] == "reference" and out["metric"] == bench.METRIC
     assert out["unit"] == "solves/s" and out["higher_is_better"] is True
